@@ -1,0 +1,381 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+and reference legs may import this package.  The CUDA product path never
+does.  The C sources in this folder are compiled with gcc into
+``oracle/_build/liboracle.so`` and driven through ctypes; scene objects are
+read by attribute (duck typing), so this package imports nothing from the
+product package.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = [os.path.join(_HERE, "oracle.c")]
+_HDR = os.path.join(_HERE, "oracle.h")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, FP64, pthreads)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(p) for p in _SRC + [_HDR])
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-o", tmp] + _SRC + ["-lm", "-lpthread"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class Medium(C.Structure):
+    _fields_ = [("kind", C.c_int), ("lambda_s", C.c_double), ("lambda_a", C.c_double),
+                ("g", C.c_double), ("f_sl", C.c_double), ("z0", C.c_double), ("dz", C.c_double),
+                ("n_layers", C.c_int), ("lambda_s_layers", C.POINTER(C.c_double)),
+                ("lambda_a_layers", C.POINTER(C.c_double))]
+
+
+class Source(C.Structure):
+    _fields_ = [("pos", C.c_double * 3), ("emission", C.c_int), ("kappa", C.c_double),
+                ("dir", C.c_double * 3)]
+
+
+class Sensor(C.Structure):
+    _fields_ = [("c", C.c_double * 3), ("R", C.c_double), ("rho", C.c_int),
+                ("rho_hat", C.c_double * 3)]
+
+
+class Run(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("p_within", C.c_double), ("p_birth", C.c_double),
+                ("p_death", C.c_double), ("within", C.c_int), ("sigma", C.c_double),
+                ("mala_step", C.c_double), ("kappa_end", C.c_double), ("burn_in", C.c_uint64),
+                ("thin_bridge", C.c_uint32), ("gradients", C.c_int), ("beta_min", C.c_double)]
+
+
+class Acc(C.Structure):
+    _fields_ = [("n_rec", C.c_double), ("n_direct", C.c_double), ("sum_n", C.c_double),
+                ("sum_L", C.c_double), ("sum_L2", C.c_double), ("sum_score", C.c_double * 3),
+                ("sum_bridge", C.c_double), ("n_bridge", C.c_double),
+                ("prop", C.c_double * 4), ("acc", C.c_double * 4)]
+
+
+ACC_FIELDS = ["n_rec", "n_direct", "sum_n", "sum_L", "sum_L2", "sum_bridge", "n_bridge"]
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_SO)
+            M, S, D, R = C.POINTER(Medium), C.POINTER(Source), C.POINTER(Sensor), C.POINTER(Run)
+            L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+            L.or_u01.argtypes = [C.c_uint32]; L.or_u01.restype = C.c_double
+            L.or_onb.argtypes = [_dp, _dp, _dp]
+            L.or_kappa_eq.argtypes = [C.c_double]; L.or_kappa_eq.restype = C.c_double
+            L.or_log_sigma.argtypes = [M, C.c_double]; L.or_log_sigma.restype = C.c_double
+            L.or_log_sigma_cos.argtypes = [M, C.c_double]; L.or_log_sigma_cos.restype = C.c_double
+            L.or_log_emission.argtypes = [S, _dp]; L.or_log_emission.restype = C.c_double
+            L.or_log_rho.argtypes = [D, _dp]; L.or_log_rho.restype = C.c_double
+            L.or_segment_depths.argtypes = [M, _dp, _dp, _dp, _dp]
+            L.or_segment_hits_ball.argtypes = [_dp, _dp, _dp, C.c_double]; L.or_segment_hits_ball.restype = C.c_int
+            L.or_logp.argtypes = [M, S, D, C.c_int, _dp]; L.or_logp.restype = C.c_double
+            L.or_grad_logp.argtypes = [M, S, D, C.c_int, _dp, _dp]; L.or_grad_logp.restype = C.c_double
+            L.or_score.argtypes = [M, S, D, C.c_int, _dp, _dp]; L.or_score.restype = C.c_int
+            L.or_bisph_point.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double, _dp]
+            L.or_bisph_coords.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp]
+            L.or_log_bisph_jacobian.argtypes = [C.c_double] * 3; L.or_log_bisph_jacobian.restype = C.c_double
+            L.or_log_q_s.argtypes = [C.c_double, C.c_double]; L.or_log_q_s.restype = C.c_double
+            L.or_log_q_t.argtypes = [C.c_double]; L.or_log_q_t.restype = C.c_double
+            L.or_init_chains.argtypes = [M, S, D, R, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int,
+                                         C.c_uint32, _dp, _ip]
+            L.or_run_chains.argtypes = [M, S, D, R, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint64,
+                                        _dp, _ip, C.POINTER(Acc), _dp, C.c_int]
+            L.or_z2.argtypes = [M, S, D, C.c_int, C.c_int]; L.or_z2.restype = C.c_double
+            L.or_qref_logdensity.argtypes = [M, S, D, C.c_int, C.c_int, _dp]
+            L.or_qref_logdensity.restype = C.c_double
+            L.or_qref_sample.argtypes = [M, S, D, C.c_int, C.c_uint64, C.c_uint32, C.c_uint64, _dp]
+            L.or_qref_sample.restype = C.c_int
+            L.or_qref_bridge_sums.argtypes = [M, S, D, C.c_int, C.c_uint64, C.c_uint32, C.c_uint64, _dp, C.c_int]
+            L.or_trace.argtypes = [M, S, D, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int, _dp, C.c_int]
+            L.or_trace_hist.argtypes = [M, S, D, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int, _dp, _dp,
+                                        C.c_int]
+            L.or_run_chains_hist.argtypes = [M, S, D, R, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint64,
+                                             _dp, _ip, C.POINTER(Acc), _dp, _dp, C.c_int]
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+# ---------------------------------------------------------------------------
+# Scene conversion (duck-typed: any object with the scene attributes works)
+# ---------------------------------------------------------------------------
+class _Keep:
+    """Keeps numpy arrays referenced by ctypes structs alive."""
+
+
+def medium(m) -> Medium:
+    out = Medium()
+    out.kind = int(m.kind)
+    out.lambda_s = float(m.lambda_s)
+    out.lambda_a = float(m.lambda_a)
+    out.g = float(m.g)
+    out.f_sl = float(getattr(m, "f_sl", 0.0))
+    out.z0 = float(getattr(m, "z0", 0.0))
+    out.dz = float(getattr(m, "dz", 1.0))
+    ls = getattr(m, "lambda_s_layers", None)
+    if ls is not None:
+        a = np.ascontiguousarray(ls, dtype=np.float64)
+        b = np.ascontiguousarray(m.lambda_a_layers, dtype=np.float64)
+        out.n_layers = len(a)
+        out.lambda_s_layers = _ptr(a)
+        out.lambda_a_layers = _ptr(b)
+        out._keep = (a, b)
+    else:
+        out.n_layers = 0
+    return out
+
+
+def source(s) -> Source:
+    out = Source()
+    out.pos[:] = [float(v) for v in s.pos]
+    out.emission = int(s.emission)
+    out.kappa = float(s.kappa)
+    d = np.asarray(s.direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    out.dir[:] = list(d)
+    return out
+
+
+def sensor(d) -> Sensor:
+    out = Sensor()
+    out.c[:] = [float(v) for v in d.centre]
+    out.R = float(d.radius)
+    out.rho = int(d.rho)
+    rh = np.asarray(d.rho_hat, dtype=np.float64)
+    out.rho_hat[:] = list(rh / np.linalg.norm(rh))
+    return out
+
+
+def run(r, sensor_radius: float) -> Run:
+    out = Run()
+    out.seed = int(r.seed)
+    out.p_within = float(r.p_within)
+    out.p_birth = float(r.p_birth)
+    out.p_death = float(r.p_death)
+    out.within = int(r.within)
+    out.sigma = float(r.sigma)
+    out.mala_step = float(r.mala_step)
+    ke = float(r.kappa_end)
+    out.kappa_end = ke if ke > 0 else (sensor_radius / float(r.sigma)) ** 2
+    out.burn_in = int(r.burn_in)
+    out.thin_bridge = int(r.thin_bridge)
+    out.gradients = int(bool(r.gradients))
+    out.beta_min = 0.01
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Thin wrappers
+# ---------------------------------------------------------------------------
+def philox(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (C.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (C.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, o)
+    return [int(x) for x in o]
+
+
+def kappa_eq(G: float) -> float:
+    return lib().or_kappa_eq(G)
+
+
+def log_sigma(m: Medium, c: float) -> float:
+    return lib().or_log_sigma(C.byref(m), c)
+
+
+def log_sigma_cos(m: Medium, c: float) -> float:
+    return lib().or_log_sigma_cos(C.byref(m), c)
+
+
+def log_emission(s: Source, rhat) -> float:
+    v = np.ascontiguousarray(rhat, dtype=np.float64)
+    return lib().or_log_emission(C.byref(s), _ptr(v))
+
+
+def log_rho(d: Sensor, nu) -> float:
+    v = np.ascontiguousarray(nu, dtype=np.float64)
+    return lib().or_log_rho(C.byref(d), _ptr(v))
+
+
+def segment_depths(m: Medium, P, Q):
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    ta, tb = C.c_double(), C.c_double()
+    lib().or_segment_depths(C.byref(m), _ptr(P), _ptr(Q), C.byref(ta), C.byref(tb))
+    return ta.value, tb.value
+
+
+def logp(m: Medium, s: Source, d: Sensor, path) -> float:
+    f = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 3)
+    return lib().or_logp(C.byref(m), C.byref(s), C.byref(d), len(f), _ptr(f))
+
+
+def grad_logp(m: Medium, s: Source, d: Sensor, path):
+    f = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 3)
+    g = np.zeros_like(f)
+    lp = lib().or_grad_logp(C.byref(m), C.byref(s), C.byref(d), len(f), _ptr(f), _ptr(g))
+    return lp, g
+
+
+def score(m: Medium, s: Source, d: Sensor, path):
+    f = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros(max(3, 2 * m.n_layers), dtype=np.float64)
+    k = lib().or_score(C.byref(m), C.byref(s), C.byref(d), len(f), _ptr(f), _ptr(out))
+    return out[:k]
+
+
+def bisph_point(fk, fk1, s, t, phi):
+    a = np.ascontiguousarray(fk, dtype=np.float64)
+    b = np.ascontiguousarray(fk1, dtype=np.float64)
+    o = np.zeros(3)
+    lib().or_bisph_point(_ptr(a), _ptr(b), s, t, phi, _ptr(o))
+    return o
+
+
+def bisph_coords(fk, fk1, f):
+    a = np.ascontiguousarray(fk, dtype=np.float64)
+    b = np.ascontiguousarray(fk1, dtype=np.float64)
+    c = np.ascontiguousarray(f, dtype=np.float64)
+    s, t, p = C.c_double(), C.c_double(), C.c_double()
+    lib().or_bisph_coords(_ptr(a), _ptr(b), _ptr(c), C.byref(s), C.byref(t), C.byref(p))
+    return s.value, t.value, p.value
+
+
+def z2(m: Medium, s: Source, d: Sensor, n_v: int = 4000, n_phi: int = 64) -> float:
+    return lib().or_z2(C.byref(m), C.byref(s), C.byref(d), n_v, n_phi)
+
+
+def qref_logdensity(m, s, d, cap, path) -> float:
+    f = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 3)
+    return lib().or_qref_logdensity(C.byref(m), C.byref(s), C.byref(d), cap, len(f), _ptr(f))
+
+
+def qref_sample(m, s, d, cap, seed, stream, draw):
+    f = np.zeros((cap, 3))
+    n = lib().or_qref_sample(C.byref(m), C.byref(s), C.byref(d), cap, seed, stream, draw, _ptr(f))
+    return f[:n].copy()
+
+
+def qref_bridge_sums(m, s, d, cap, seed, stream, n_draws, threads=None):
+    out = np.zeros(4)
+    lib().or_qref_bridge_sums(C.byref(m), C.byref(s), C.byref(d), cap, seed, stream, n_draws, _ptr(out),
+                              threads or os.cpu_count() or 1)
+    return out
+
+
+def trace(m, s, d, seed, n_photons, photon0=0, r_reject=math.inf, max_scatter=1 << 30, threads=None,
+          hist=False):
+    """Forward tracer (Algorithm 1).  Returns dict with intensity estimate and SE;
+    with hist=True also the detected weight per number of scatterings."""
+    out = np.zeros(5)
+    h = np.zeros(max_scatter + 1) if hist else None
+    lib().or_trace_hist(C.byref(m), C.byref(s), C.byref(d), seed, photon0, n_photons, r_reject, max_scatter,
+                        _ptr(out), _ptr(h) if hist else None, threads or os.cpu_count() or 1)
+    N = out[3]
+    mean = out[0] / N
+    var = max(out[1] / N - mean * mean, 0.0)
+    res = {"I": mean, "se": math.sqrt(var / N), "hits": out[2], "photons": N,
+           "mean_L": out[4] / out[0] if out[0] > 0 else float("nan"), "raw": out}
+    if hist:
+        res["hist"] = h / N
+    return res
+
+
+class Chains:
+    """A set of oracle chains for one source-sensor pair (state in FP64)."""
+
+    def __init__(self, scene_medium, scene_source, scene_sensor, scene_run, n_chains, cap,
+                 chain_offset=0, init=None, init_k=None, jitter=None, user_xyz=None, user_n=None):
+        self.m = medium(scene_medium)
+        self.s = source(scene_source)
+        self.d = sensor(scene_sensor)
+        self.r = run(scene_run, float(scene_sensor.radius))
+        self.n_chains = int(n_chains)
+        self.cap = int(cap)
+        self.chain_offset = int(chain_offset)
+        self.xyz = np.zeros((self.n_chains, self.cap, 3))
+        self.n = np.zeros(self.n_chains, dtype=np.int32)
+        self.acc = (Acc * self.n_chains)()
+        self.step = 0
+        init = scene_run.init if init is None else init
+        if user_xyz is not None:
+            for c in range(self.n_chains):
+                k = int(user_n[c])
+                self.xyz[c, :k] = user_xyz[c, :k]
+                self.n[c] = k
+        else:
+            rc = lib().or_init_chains(C.byref(self.m), C.byref(self.s), C.byref(self.d), C.byref(self.r),
+                                      int(init), int(scene_run.init_k if init_k is None else init_k),
+                                      float(scene_run.init_jitter if jitter is None else jitter),
+                                      self.n_chains, self.cap, self.chain_offset,
+                                      _ptr(self.xyz), self.n.ctypes.data_as(_ip))
+            if rc != 0:
+                raise ValueError("oracle init failed")
+
+    def run(self, n_steps, threads=None, margins=False, n_hist=None):
+        """Advance every chain; n_hist (n_chains x (cap+1) float64) collects recorded dwell per n."""
+        mm = np.full(self.n_chains, np.inf) if margins else None
+        lib().or_run_chains_hist(C.byref(self.m), C.byref(self.s), C.byref(self.d), C.byref(self.r),
+                                 self.n_chains, self.cap, self.chain_offset, self.step, int(n_steps),
+                                 _ptr(self.xyz), self.n.ctypes.data_as(_ip), self.acc,
+                                 _ptr(mm) if margins else None, _ptr(n_hist) if n_hist is not None else None,
+                                 threads or os.cpu_count() or 1)
+        self.step += int(n_steps)
+        return mm
+
+    def logp(self, c):
+        return logp(self.m, self.s, self.d, self.xyz[c, : self.n[c]])
+
+    def accumulators(self):
+        """Per-chain accumulators as a dict of numpy arrays."""
+        out = {k: np.array([getattr(a, k) for a in self.acc]) for k in ACC_FIELDS}
+        out["sum_score"] = np.array([list(a.sum_score) for a in self.acc])
+        out["prop"] = np.array([list(a.prop) for a in self.acc])
+        out["acc"] = np.array([list(a.acc) for a in self.acc])
+        return out
+
+
+def direct_estimate(acc: dict, z2_value: float):
+    """Intensity from the direct-sector anchor: I = Z2 / pi(n=2).
+
+    The standard error is propagated from the across-chain variance of the
+    per-chain n=2 fractions (chains are independent).
+    """
+    N = acc["n_rec"]
+    n2 = acc["n_direct"]
+    pi_hat = n2.sum() / N.sum()
+    frac = n2 / np.maximum(N, 1)
+    C_ = len(N)
+    w = N / N.sum()
+    var_pi = (w * w * (frac - pi_hat) ** 2).sum() * C_ / max(C_ - 1, 1)
+    I = z2_value / pi_hat
+    se = I * math.sqrt(var_pi) / pi_hat
+    return I, se, pi_hat

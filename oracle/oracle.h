@@ -1,0 +1,167 @@
+/*
+ * FP64 CPU oracle for path-integral RJMCMC light transport
+ * (Collin, "Using path integrals for the propagation of light in a
+ * scattering dominated medium", arXiv:1811.04156).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * bench's CPU-baseline / reference legs may load this library.  The CUDA
+ * product path never calls, links or imports it, and it shares no code,
+ * header, table or constant generator with the CUDA path.
+ *
+ * Everything here is plain, slow and written to be checked by eye against
+ * the paper: every proposal recomputes the full log-density from scratch,
+ * in double precision.
+ *
+ * Functions with no pin other than the paper's text are marked
+ * "parity unpinned" at their definition.
+ */
+#ifndef PMC_ORACLE_H
+#define PMC_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_HOMOGENEOUS = 0, OR_LAYERED = 1 };
+enum { OR_EMIT_ISOTROPIC = 0, OR_EMIT_VMF = 1 };
+enum { OR_RHO_ONE = 0, OR_RHO_PAPER = 1 };
+enum { OR_INIT_DIRECT = 0, OR_INIT_STRAIGHT = 1, OR_INIT_USER = 2 };
+enum { OR_WITHIN_PERTURB = 0, OR_WITHIN_MALA = 1 };
+enum { OR_MOVE_INTERIOR = 0, OR_MOVE_END = 1, OR_MOVE_BIRTH = 2, OR_MOVE_DEATH = 3 };
+
+typedef struct {
+  int kind;                 /* OR_HOMOGENEOUS or OR_LAYERED */
+  double lambda_s;          /* scattering length (m), homogeneous */
+  double lambda_a;          /* absorption length (m), homogeneous */
+  double g;                 /* Gamma: mean cosine of both phase components */
+  double f_sl;              /* simplified-Liu weight of the mixture */
+  double z0, dz;            /* layered: bottom of layer 0 and thickness */
+  int n_layers;
+  const double* lambda_s_layers;
+  const double* lambda_a_layers;
+} or_medium;
+
+typedef struct {
+  double pos[3];
+  int emission;             /* OR_EMIT_ISOTROPIC or OR_EMIT_VMF */
+  double kappa;
+  double dir[3];
+} or_source;
+
+typedef struct {
+  double c[3];
+  double R;
+  int rho;                  /* OR_RHO_ONE or OR_RHO_PAPER */
+  double rho_hat[3];
+} or_sensor;
+
+typedef struct {
+  uint64_t seed;
+  double p_within, p_birth, p_death;
+  int within;               /* OR_WITHIN_PERTURB or OR_WITHIN_MALA */
+  double sigma;             /* Gaussian perturbation scale (m) */
+  double mala_step;         /* MALA epsilon (m) */
+  double kappa_end;         /* vMF concentration of end moves (> 0) */
+  uint64_t burn_in;         /* global step index from which states are recorded */
+  uint32_t thin_bridge;     /* record reference-density terms every k steps (0: never) */
+  int gradients;            /* accumulate score terms */
+  double beta_min;          /* lower clamp of the insertion concentration */
+} or_run;
+
+/* Per-chain accumulators (FP64 sums over recorded states). */
+typedef struct {
+  double n_rec;             /* recorded states */
+  double n_direct;          /* recorded states with n == 2 */
+  double sum_n, sum_L, sum_L2;
+  double sum_score[3];      /* homogeneous scores d log p / d(lambda_s, lambda_a, g) */
+  double sum_bridge;        /* sum of sqrt(q_ref / p) at thinned states */
+  double n_bridge;
+  double prop[4], acc[4];   /* proposals / acceptances per OR_MOVE_* */
+} or_acc;
+
+/* ---- random numbers ---- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double or_u01(uint32_t x);
+void or_onb(const double n[3], double e1[3], double e2[3]);
+
+/* ---- density factors ---- */
+double or_kappa_eq(double G);
+double or_log_sigma(const or_medium* m, double cos_theta);       /* per steradian */
+double or_log_sigma_cos(const or_medium* m, double cos_theta);   /* over cos(theta) */
+double or_log_emission(const or_source* s, const double rhat[3]);
+double or_log_rho(const or_sensor* d, const double nu[3]);
+double or_b_at(const or_medium* m, const double x[3]);
+double or_a_at(const or_medium* m, const double x[3]);
+void or_segment_depths(const or_medium* m, const double P[3], const double Q[3],
+                       double* tau_a, double* tau_b);
+int or_segment_hits_ball(const double P[3], const double Q[3], const double c[3], double R);
+
+/* log p of one path, xyz = n x 3 (row per vertex). */
+double or_logp(const or_medium* m, const or_source* s, const or_sensor* d,
+               int n, const double* xyz);
+/* d log p / d xyz (n x 3).  Returns log p. */
+double or_grad_logp(const or_medium* m, const or_source* s, const or_sensor* d,
+                    int n, const double* xyz, double* grad);
+/* Score d log p / d theta: homogeneous theta = (lambda_s, lambda_a, g) (3 values);
+ * layered theta = (lambda_s[0..L), lambda_a[0..L)) (2L values).  Returns count. */
+int or_score(const or_medium* m, const or_source* s, const or_sensor* d,
+             int n, const double* xyz, double* score);
+
+/* ---- birth/death geometry (appendix, dimension matching transformation) ---- */
+void or_bisph_point(const double fk[3], const double fk1[3], double s, double t, double phi,
+                    double out[3]);
+void or_bisph_coords(const double fk[3], const double fk1[3], const double f[3],
+                     double* s, double* t, double* phi);
+double or_log_bisph_jacobian(double gamma, double s, double t);
+double or_log_q_s(double beta, double s);
+double or_log_q_t(double t);
+
+/* ---- chains ---- */
+/* Initial states: xyz is [chains][cap][3], n is [chains]. */
+int or_init_chains(const or_medium* m, const or_source* s, const or_sensor* d,
+                   const or_run* r, int init_kind, int init_k, double jitter,
+                   int n_chains, int cap, uint32_t chain_offset,
+                   double* xyz, int* n);
+/* Run n_steps steps of every chain from global step index step0.
+ * min_margin (optional, per chain): smallest |log A - log u| seen over finite
+ * proposals, to find near-tie decisions in trajectory comparisons. */
+int or_run_chains(const or_medium* m, const or_source* s, const or_sensor* d,
+                  const or_run* r, int n_chains, int cap, uint32_t chain_offset,
+                  uint64_t step0, uint64_t n_steps, double* xyz, int* n,
+                  or_acc* acc, double* min_margin, int n_threads);
+/* Same, and adds the dwell of every recorded state to n_hist[chain][n]
+ * (n_hist: n_chains x (cap + 1) doubles, may be NULL). */
+int or_run_chains_hist(const or_medium* m, const or_source* s, const or_sensor* d,
+                       const or_run* r, int n_chains, int cap, uint32_t chain_offset,
+                       uint64_t step0, uint64_t n_steps, double* xyz, int* n,
+                       or_acc* acc, double* min_margin, double* n_hist, int n_threads);
+
+/* ---- normalisation and reference density ---- */
+double or_z2(const or_medium* m, const or_source* s, const or_sensor* d, int n_v, int n_phi);
+double or_qref_logdensity(const or_medium* m, const or_source* s, const or_sensor* d,
+                          int cap, int n, const double* xyz);
+int or_qref_sample(const or_medium* m, const or_source* s, const or_sensor* d, int cap,
+                   uint64_t seed, uint32_t stream, uint64_t draw, double* xyz);
+/* sums over draws of sqrt(p/q) and of p/q: out[0] = sum sqrt(p/q), out[1] = sum p/q,
+ * out[2] = sum (p/q)^2, out[3] = draws. */
+int or_qref_bridge_sums(const or_medium* m, const or_source* s, const or_sensor* d, int cap,
+                        uint64_t seed, uint32_t stream, uint64_t n_draws, double* out,
+                        int n_threads);
+
+/* ---- forward ray tracer (appendix, Algorithm 1) ----
+ * out[0] = sum of weights of detected photons, out[1] = sum of squared weights,
+ * out[2] = detected photons, out[3] = emitted photons, out[4] = sum of w*L (length). */
+int or_trace(const or_medium* m, const or_source* s, const or_sensor* d,
+             uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
+             int max_scatter, double* out, int n_threads);
+/* Same, and adds each detected weight to hist[scatterings] (max_scatter + 1 doubles). */
+int or_trace_hist(const or_medium* m, const or_source* s, const or_sensor* d,
+                  uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
+                  int max_scatter, double* out, double* hist, int n_threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
