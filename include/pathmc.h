@@ -1,0 +1,319 @@
+/*
+ * pathmc — C ABI of a GB300 (sm_103a) library that runs many independent
+ * Reversible-Jump MCMC chains over light paths, after G. H. Collin,
+ * "Using path integrals for the propagation of light in a scattering
+ * dominated medium" (arXiv:1811.04156).
+ *
+ * A path is a polyline f_0 .. f_{n-1}: f_0 is a point source, f_1 .. f_{n-2}
+ * are scattering vertices, f_{n-1} lies on a spherical light sensor
+ * (section "Numerical path integration").  Its density is
+ *   p = p_i(f_0, f_1) * prod_k p_v(f_{k-1}, f_k, f_{k+1}) * p_f(f_{n-2}, f_{n-1})
+ * (appendix, "Path probability distribution"; Eqs. emission_dist, intervtx,
+ * b_depth_def, angular_scattering, detection_prob), and its integral over all
+ * paths up to a vertex cap is the detected intensity per emitted photon.
+ *
+ * Conventions shared by every entry point:
+ *  - Status: every function returns PMC_OK (0) or a PMC_ERR_* code;
+ *    pmc_last_error() gives a per-thread message for the last failure.
+ *  - Ownership: handles are created and destroyed by the library; descriptor
+ *    structs and the host arrays they point to are copied during the call
+ *    and may be freed afterwards.  Device pointers passed in (pmc_logp and
+ *    friends) stay owned by the caller.
+ *  - Streams: `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *    default stream.  Functions marked "async" only enqueue work on it.
+ *  - Units: lengths in metres, coefficients in 1/m, double precision on the
+ *    host.  Device state is FP32 with FP64 estimator accumulators.
+ *  - Layout of device path batches: SoA float32 [3][batch][cap] (all x, then
+ *    all y, then all z), vertex k of path b at index b*cap + k; vertex
+ *    counts int32 [batch].
+ *  - One GPU; no CPU fallback: without a usable device the calls fail with
+ *    PMC_ERR_NO_DEVICE or PMC_ERR_CUDA.
+ */
+#ifndef PATHMC_H
+#define PATHMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PMC_API __attribute__((visibility("default")))
+#else
+#define PMC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMC_OK 0
+#define PMC_ERR_INVALID 1        /* bad argument or descriptor */
+#define PMC_ERR_OOM 2            /* device allocation failed */
+#define PMC_ERR_CUDA 3           /* a CUDA runtime call failed */
+#define PMC_ERR_DEVICE_STATUS 4  /* a kernel reported an error word (non-finite state, bounds) */
+#define PMC_ERR_ABORTED 5        /* the run was aborted through pmc_request_abort */
+#define PMC_ERR_NO_DEVICE 6      /* no CUDA device available */
+
+#define PMC_HOMOGENEOUS 0
+#define PMC_LAYERED 1
+
+#define PMC_EMIT_ISOTROPIC 0
+#define PMC_EMIT_VMF 1
+
+#define PMC_RHO_ONE 0
+#define PMC_RHO_PAPER 1
+
+#define PMC_INIT_DIRECT 0
+#define PMC_INIT_STRAIGHT 1
+#define PMC_INIT_USER 2
+
+#define PMC_WITHIN_PERTURB 0
+#define PMC_WITHIN_MALA 1
+
+#define PMC_FLAG_GRADIENTS 1   /* accumulate score terms for pmc_grad_estimator */
+#define PMC_FLAG_NO_GRAPH 2    /* launch kernels directly instead of replaying a CUDA graph */
+
+#define PMC_MOVE_INTERIOR 0    /* Gaussian perturbation or MALA of an interior vertex */
+#define PMC_MOVE_END 1         /* vMF step of the end vertex on the sensor sphere */
+#define PMC_MOVE_BIRTH 2
+#define PMC_MOVE_DEATH 3
+
+typedef struct pmc_ctx_s* pmc_ctx_t;
+typedef struct pmc_medium_s* pmc_medium_t;
+typedef struct pmc_geom_s* pmc_geom_t;
+typedef struct pmc_chains_s* pmc_chains_t;
+
+/* Medium: absorption a(x) = 1/lambda_a and scattering b(x) = 1/lambda_s
+ * (appendix, intermediate vertex), either constant or constant within
+ * horizontal layers [z0 + l*dz, z0 + (l+1)*dz) (layer 0 and layer L-1 extend
+ * to -inf / +inf).  Phase function: the mixture
+ * f_sl * p_SL + (1 - f_sl) * p_HG with mean cosine g (Eq. angular_scattering).
+ * Requirements: lengths > 0, |g| < 1, 0 <= f_sl <= 1 (f_sl > 0 needs g > 0),
+ * dz > 0 and 1 <= n_layers <= 4096 when layered. */
+typedef struct {
+  int kind;                        /* PMC_HOMOGENEOUS or PMC_LAYERED */
+  double lambda_s, lambda_a;       /* homogeneous lengths (m) */
+  double g, f_sl;
+  double z0, dz;                   /* layered geometry (m) */
+  int n_layers;
+  const double* lambda_s_layers;   /* host [n_layers], copied */
+  const double* lambda_a_layers;   /* host [n_layers], copied */
+} pmc_medium_desc;
+
+/* Point source with isotropic or von Mises-Fisher emission (Eq. emission_dist). */
+typedef struct {
+  double pos[3];
+  int emission;                    /* PMC_EMIT_ISOTROPIC or PMC_EMIT_VMF */
+  double kappa;                    /* vMF concentration (> 0 for VMF) */
+  double dir[3];                   /* preferred direction (normalised internally) */
+} pmc_source;
+
+/* Spherical sensor with detection probability 1 or Eq. detection_prob. */
+typedef struct {
+  double centre[3];
+  double radius;                   /* > 0 */
+  int rho;                         /* PMC_RHO_ONE or PMC_RHO_PAPER */
+  double rho_hat[3];               /* preferred direction (normalised internally) */
+} pmc_sensor;
+
+/* One source-sensor pair sampled by n_chains chains with vertex cap `cap`
+ * (2 <= cap <= 1024; paths hold n in [2, cap] vertices). */
+typedef struct {
+  int source, sensor;
+  int n_chains;
+  int cap;
+} pmc_pair;
+
+typedef struct {
+  int n_sources;
+  const pmc_source* sources;
+  int n_sensors;
+  const pmc_sensor* sensors;
+  int n_pairs;
+  const pmc_pair* pairs;
+} pmc_geometry_desc;
+
+/* Chain settings.  Move probabilities must sum to 1 (each in [0, 1]).
+ * Within-dimension moves pick one of the n-1 movable vertices uniformly:
+ * the end vertex takes a vMF step of concentration kappa_end on the sensor
+ * (0 -> (R/sigma)^2), an interior vertex a Gaussian step of scale sigma
+ * (PMC_WITHIN_PERTURB) or a MALA step of size mala_step (PMC_WITHIN_MALA).
+ * Births insert a vertex into a segment chosen with probability
+ * tau_b(k)/sum tau_b, placed by bispherical coordinates; deaths remove an
+ * interior vertex chosen uniformly (appendix, jump proposal; dimension
+ * matching transformation).  States after global step index >= burn_in are
+ * recorded in the estimators. */
+typedef struct {
+  uint64_t seed;                   /* Philox4x32-10 key */
+  double p_within, p_birth, p_death;
+  int within;                      /* PMC_WITHIN_PERTURB or PMC_WITHIN_MALA */
+  double sigma;                    /* Gaussian step (m) */
+  double mala_step;                /* MALA epsilon (m) */
+  double kappa_end;                /* vMF concentration of end moves; 0 -> (R/sigma)^2 */
+  uint64_t burn_in;
+  uint32_t thin_bridge;            /* reference-density bridge terms every k steps; 0 = off */
+  int init;                        /* PMC_INIT_DIRECT, PMC_INIT_STRAIGHT or PMC_INIT_USER */
+  int init_k;                      /* STRAIGHT: interior vertices on the source-sensor line */
+  double init_jitter;              /* STRAIGHT: N(0, jitter^2) per coordinate (m) */
+  const float* init_xyz;           /* USER: host, [total_chains][3][init_stride], absolute (m) */
+  const int* init_n;               /* USER: host, [total_chains] */
+  int init_stride;                 /* USER: vertex stride of init_xyz (>= every init_n) */
+  int flags;                       /* PMC_FLAG_* */
+  int warps_per_block;             /* 0 = autotune */
+} pmc_run_desc;
+
+/* Per-pair estimate returned by pmc_read_estimator. */
+typedef struct {
+  double intensity;                /* detected intensity per emitted photon */
+  double std_err;                  /* standard error of `intensity` */
+  double rel_err;                  /* std_err / intensity */
+  double pi_direct;                /* fraction of recorded states with n == 2 */
+  double z2;                       /* direct-sector integral (n == 2 part) */
+  double rhat;                     /* Gelman-Rubin R-hat of the path length over chains */
+  double accept[4];                /* acceptance rate per PMC_MOVE_* */
+  double proposals[4];             /* proposals per PMC_MOVE_* */
+  double mean_n, mean_length;      /* means over recorded states */
+  double n_samples;                /* recorded states */
+  double ess;                      /* effective sample size of pi_direct */
+  double bridge_intensity;         /* geometric-bridge estimate (NaN when off) */
+  double bridge_std_err;
+} pmc_estimate;
+
+/* ---------------------------------------------------------------------- */
+/* Context, medium, geometry                                              */
+/* ---------------------------------------------------------------------- */
+
+/* Bind a context to CUDA device `device`.  Fails with PMC_ERR_NO_DEVICE when
+ * the device does not exist. */
+PMC_API int pmc_create_context(int device, pmc_ctx_t* out);
+PMC_API int pmc_destroy_context(pmc_ctx_t ctx);
+
+/* Copy a medium description to the device (appendix, intermediate vertex;
+ * Eq. b_depth_def).  Also solves coth(k) - 1/k = g for the insertion
+ * centering constant kappa_eq (appendix, dimension matching transformation). */
+PMC_API int pmc_create_medium(pmc_ctx_t ctx, const pmc_medium_desc* desc, pmc_medium_t* out);
+PMC_API int pmc_destroy_medium(pmc_medium_t medium);
+
+/* Copy sources, sensors and pairs to the device (section "Implementation":
+ * point source, spherical light-sensitive elements).  Rejects a source
+ * inside or on its pair's sensor. */
+PMC_API int pmc_create_geometry(pmc_ctx_t ctx, const pmc_geometry_desc* desc, pmc_geom_t* out);
+PMC_API int pmc_destroy_geometry(pmc_geom_t geom);
+
+/* ---------------------------------------------------------------------- */
+/* Chains                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Allocate chain state for every pair of `geom` and write the initial paths
+ * (async on `stream`).  DIRECT: n = 2 with the end vertex at the sensor point
+ * nearest the source.  STRAIGHT: init_k interior vertices evenly spaced on
+ * the segment from the source to that point, each jittered by
+ * N(0, init_jitter^2 I) from Philox.  USER: copies init_xyz / init_n.
+ * The chains keep references to ctx, medium and geom, which must outlive them. */
+PMC_API int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom,
+                    const pmc_run_desc* run, void* stream, pmc_chains_t* out);
+PMC_API int pmc_destroy_chains(pmc_chains_t chains);
+
+/* Advance every chain by n_steps RJMCMC steps (async).  One step is one
+ * proposal and its accept/reject decision by Eq. acceptFact (read in Green's
+ * orientation for births; deaths use the reciprocal of the reverse birth).
+ * Random numbers are Philox4x32-10 keyed by the seed and indexed by
+ * (global step, chain), so a run split over several calls reproduces the
+ * uninterrupted trajectory exactly. */
+PMC_API int pmc_run_steps(pmc_chains_t chains, uint64_t n_steps, void* stream);
+
+/* Reduce the per-chain FP64 accumulators to one pmc_estimate per pair and
+ * copy them to `out` (host, n_pairs entries, caller-owned).  Synchronises
+ * `stream`.  The intensity is Z2 / pi(n=2): Z2 is the n = 2 part of the path
+ * integral (2-D quadrature over the sensor as seen from the source) and
+ * pi(n=2) the chains' fraction of states with n = 2; the standard error comes
+ * from the across-chain variance. */
+PMC_API int pmc_read_estimator(pmc_chains_t chains, pmc_estimate* out, size_t n_pairs, void* stream);
+
+/* d intensity / d theta per pair: intensity * E_p[d log p / d theta] from
+ * score terms accumulated while stepping (needs PMC_FLAG_GRADIENTS).
+ * theta = (lambda_s, lambda_a, g) for homogeneous media, or
+ * (lambda_s[0..L), lambda_a[0..L)) for layered ones.  `grad` and `grad_se`
+ * are host arrays of n_pairs * n_theta doubles (pair-major); grad_se may be
+ * NULL.  Synchronises `stream`. */
+PMC_API int pmc_grad_estimator(pmc_chains_t chains, double* grad, double* grad_se, size_t len, void* stream);
+
+/* Number of medium parameters theta (3 or 2 * n_layers). */
+PMC_API int pmc_n_theta(pmc_medium_t medium);
+
+/* Copy chain states to host buffers: xyz [total_chains][3][stride] absolute
+ * positions (stride >= the largest cap), n [total_chains], steps
+ * [total_chains] (may be NULL).  Synchronises `stream`. */
+PMC_API int pmc_read_states(pmc_chains_t chains, float* xyz, int* n, uint64_t* steps, int stride, void* stream);
+
+/* Raw per-chain accumulators: PMC_ACC_WORDS doubles per chain, in the order
+ * n_rec, n_direct, sum_n, sum_L, sum_L2, sum_G, sum_bridge, n_bridge,
+ * prop[4], acc[4] (sum_G = sum of d log sigma / d g over vertices).
+ * Synchronises `stream`. */
+#define PMC_ACC_WORDS 16
+PMC_API int pmc_read_accumulators(pmc_chains_t chains, double* out, size_t n_doubles, void* stream);
+PMC_API int pmc_total_chains(pmc_chains_t chains);
+
+/* Serialise / restore the complete chain state (positions, vertex counts,
+ * step counters, accumulators) through a host buffer.  With buf == NULL,
+ * pmc_save_state stores the needed size in *bytes.  Synchronises `stream`. */
+PMC_API int pmc_save_state(pmc_chains_t chains, void* buf, size_t* bytes, void* stream);
+PMC_API int pmc_load_state(pmc_chains_t chains, const void* buf, size_t bytes, void* stream);
+
+/* Ask running and future pmc_run_steps calls of these chains to stop at the
+ * next step boundary; pmc_run_steps then reports PMC_ERR_ABORTED on the next
+ * synchronising call.  flag = 0 clears the request. */
+PMC_API int pmc_request_abort(pmc_chains_t chains, int flag);
+
+/* Device status word of the chains (0 = fine); bit 0: non-finite state at
+ * load, bit 1: aborted, bit 2: bad vertex count.  Synchronises `stream`. */
+PMC_API int pmc_chain_status(pmc_chains_t chains, int* status, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Density evaluation on caller-owned device batches                      */
+/* ---------------------------------------------------------------------- */
+
+/* log p of `batch` paths of pair `pair` (async).  xyz: device SoA
+ * [3][batch][cap] absolute positions; n: device int32 [batch] with
+ * 2 <= n <= cap; out_logp: device float32 [batch].  A path whose non-final
+ * segment touches the sensor ball, whose final segment arrives from inside
+ * (cos Phi <= 0) or that has a zero-length segment gets -inf. */
+PMC_API int pmc_logp(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair,
+             const float* xyz, const int* n, int batch, int cap, float* out_logp, void* stream);
+
+/* log p and d log p / d(vertex positions) for every vertex (async); the
+ * gradient has the layout of xyz (unused slots are written as 0).  The end
+ * vertex's gradient is that of the expression with nu = (f - c)/|f - c|,
+ * i.e. not projected onto the sphere. */
+PMC_API int pmc_logp_grad(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair,
+                  const float* xyz, const int* n, int batch, int cap,
+                  float* out_logp, float* out_grad, void* stream);
+
+/* d log p / d theta per path (async); out: device float32 [batch][n_theta]. */
+PMC_API int pmc_score(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair,
+              const float* xyz, const int* n, int batch, int cap, float* out, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Comparison baseline                                                    */
+/* ---------------------------------------------------------------------- */
+
+/* Forward ray tracer (appendix, Algorithm 1) for pair `pair`: n_photons
+ * photons numbered from photon0, free paths from b(x), absorption weights
+ * from a(x), hits tallied at the first sensor intersection, rejection beyond
+ * r_reject from the sensor centre, at most max_scatter scatterings.
+ * out (host, 5 doubles): sum of detected weights w*rho, sum of squared
+ * weights, detected photons, emitted photons, sum of w*rho*path length.
+ * Synchronises `stream`. */
+PMC_API int pmc_trace(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair,
+              uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
+              int max_scatter, double* out, void* stream);
+
+/* Message of the last failure on the calling thread ("" if none). */
+PMC_API const char* pmc_last_error(void);
+
+/* Library version string. */
+PMC_API const char* pmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PATHMC_H */

@@ -1,0 +1,366 @@
+"""Python binding of libpathmc with the C entry points' names.
+
+Argument marshalling only: descriptors are packed into the C structs of
+include/pathmc.h, device buffers come from torch tensors, and the stream is
+torch's current CUDA stream.  Every step of the path (initialisation,
+stepping, estimators, density, adjoint, tracer) runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from . import scenes as S
+from ._lib import (Estimate, GeometryDesc, MediumDesc, PairDesc, RunDesc, SensorDesc, SourceDesc,
+                   PMC_ACC_WORDS, PMC_FLAG_GRADIENTS, PMC_FLAG_NO_GRAPH, check, load)
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, dtype, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        h = C.c_void_p()
+        check(load().pmc_create_context(self.device, C.byref(h)), "pmc_create_context")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().pmc_destroy_context(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def create_context(device: int = 0) -> Context:
+    return Context(device)
+
+
+def medium_desc(m: S.Medium):
+    d = MediumDesc()
+    d.kind = int(m.kind)
+    d.lambda_s = float(m.lambda_s)
+    d.lambda_a = float(m.lambda_a)
+    d.g = float(m.g)
+    d.f_sl = float(m.f_sl)
+    d.z0 = float(m.z0)
+    d.dz = float(m.dz)
+    keep = ()
+    if m.kind == S.LAYERED:
+        ls = np.ascontiguousarray(m.lambda_s_layers, dtype=np.float64)
+        la = np.ascontiguousarray(m.lambda_a_layers, dtype=np.float64)
+        d.n_layers = len(ls)
+        d.lambda_s_layers = ls.ctypes.data_as(C.POINTER(C.c_double))
+        d.lambda_a_layers = la.ctypes.data_as(C.POINTER(C.c_double))
+        keep = (ls, la)
+    return d, keep
+
+
+class Medium:
+    def __init__(self, ctx: Context, m: S.Medium):
+        self.ctx = ctx
+        self.scene = m
+        d, keep = medium_desc(m)
+        h = C.c_void_p()
+        check(load().pmc_create_medium(ctx.handle, C.byref(d), C.byref(h)), "pmc_create_medium")
+        self.handle = h
+        self.n_theta = load().pmc_n_theta(h)
+
+    def close(self):
+        if self.handle:
+            load().pmc_destroy_medium(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def create_medium(ctx: Context, m: S.Medium) -> Medium:
+    return Medium(ctx, m)
+
+
+class Geometry:
+    def __init__(self, ctx: Context, sources: Sequence[S.Source], sensors: Sequence[S.Sensor],
+                 pairs: Sequence[S.Pair]):
+        self.ctx = ctx
+        self.sources, self.sensors, self.pairs = list(sources), list(sensors), list(pairs)
+        src = (SourceDesc * len(sources))()
+        for i, s in enumerate(sources):
+            src[i].pos[:] = [float(v) for v in s.pos]
+            src[i].emission = int(s.emission)
+            src[i].kappa = float(s.kappa)
+            src[i].dir[:] = [float(v) for v in s.direction]
+        sen = (SensorDesc * len(sensors))()
+        for i, d in enumerate(sensors):
+            sen[i].centre[:] = [float(v) for v in d.centre]
+            sen[i].radius = float(d.radius)
+            sen[i].rho = int(d.rho)
+            sen[i].rho_hat[:] = [float(v) for v in d.rho_hat]
+        prs = (PairDesc * len(pairs))()
+        for i, p in enumerate(pairs):
+            prs[i].source, prs[i].sensor = int(p.source), int(p.sensor)
+            prs[i].n_chains, prs[i].cap = int(p.n_chains), int(p.cap)
+        g = GeometryDesc(len(sources), src, len(sensors), sen, len(pairs), prs)
+        h = C.c_void_p()
+        check(load().pmc_create_geometry(ctx.handle, C.byref(g), C.byref(h)), "pmc_create_geometry")
+        self.handle = h
+        self.total_chains = int(sum(p.n_chains for p in pairs))
+        self.max_cap = int(max(p.cap for p in pairs))
+
+    def close(self):
+        if self.handle:
+            load().pmc_destroy_geometry(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def create_geometry(ctx: Context, sources, sensors, pairs) -> Geometry:
+    return Geometry(ctx, sources, sensors, pairs)
+
+
+def run_desc(r: S.Run, flags: int = 0, warps_per_block: int = 0, user_xyz: Optional[np.ndarray] = None,
+             user_n: Optional[np.ndarray] = None):
+    d = RunDesc()
+    d.seed = int(r.seed)
+    d.p_within, d.p_birth, d.p_death = float(r.p_within), float(r.p_birth), float(r.p_death)
+    d.within = int(r.within)
+    d.sigma = float(r.sigma)
+    d.mala_step = float(r.mala_step)
+    d.kappa_end = float(r.kappa_end)
+    d.burn_in = int(r.burn_in)
+    d.thin_bridge = int(r.thin_bridge)
+    d.init = int(r.init)
+    d.init_k = int(r.init_k)
+    d.init_jitter = float(r.init_jitter)
+    d.flags = int(flags) | (PMC_FLAG_GRADIENTS if r.gradients else 0)
+    d.warps_per_block = int(warps_per_block)
+    keep = ()
+    if user_xyz is not None:
+        ux = np.ascontiguousarray(user_xyz, dtype=np.float32)  # [chains][3][stride]
+        un = np.ascontiguousarray(user_n, dtype=np.int32)
+        d.init = S.INIT_USER
+        d.init_xyz = ux.ctypes.data_as(C.POINTER(C.c_float))
+        d.init_n = un.ctypes.data_as(C.POINTER(C.c_int))
+        d.init_stride = int(ux.shape[2])
+        keep = (ux, un)
+    return d, keep
+
+
+class Chains:
+    """Chains of every pair of a geometry (pmc_init_chains .. pmc_destroy_chains)."""
+
+    def __init__(self, ctx: Context, medium: Medium, geom: Geometry, run: S.Run, flags: int = 0,
+                 warps_per_block: int = 0, user_xyz=None, user_n=None, stream=None):
+        self.ctx, self.medium, self.geom, self.run = ctx, medium, geom, run
+        d, keep = run_desc(run, flags, warps_per_block, user_xyz, user_n)
+        h = C.c_void_p()
+        with torch.cuda.device(ctx.device):
+            check(load().pmc_init_chains(ctx.handle, medium.handle, geom.handle, C.byref(d), _stream(stream),
+                                         C.byref(h)), "pmc_init_chains")
+        self.handle = h
+        self.total = load().pmc_total_chains(h)
+        self.n_pairs = len(geom.pairs)
+
+    def run_steps(self, n_steps: int, stream=None):
+        check(load().pmc_run_steps(self.handle, int(n_steps), _stream(stream)), "pmc_run_steps")
+
+    def read_estimator(self, stream=None):
+        out = (Estimate * self.n_pairs)()
+        check(load().pmc_read_estimator(self.handle, out, self.n_pairs, _stream(stream)), "pmc_read_estimator")
+        return [e.as_dict() for e in out]
+
+    def grad_estimator(self, stream=None):
+        nt = self.medium.n_theta
+        g = np.zeros(self.n_pairs * nt)
+        se = np.zeros(self.n_pairs * nt)
+        check(load().pmc_grad_estimator(self.handle, g.ctypes.data_as(C.POINTER(C.c_double)),
+                                        se.ctypes.data_as(C.POINTER(C.c_double)), len(g), _stream(stream)),
+              "pmc_grad_estimator")
+        return g.reshape(self.n_pairs, nt), se.reshape(self.n_pairs, nt)
+
+    def read_states(self, stream=None):
+        stride = self.geom.max_cap
+        xyz = np.zeros((self.total, 3, stride), dtype=np.float32)
+        n = np.zeros(self.total, dtype=np.int32)
+        steps = np.zeros(self.total, dtype=np.uint64)
+        check(load().pmc_read_states(self.handle, xyz.ctypes.data_as(C.POINTER(C.c_float)),
+                                     n.ctypes.data_as(C.POINTER(C.c_int)),
+                                     steps.ctypes.data_as(C.POINTER(C.c_uint64)), stride, _stream(stream)),
+              "pmc_read_states")
+        return xyz, n, steps
+
+    def read_accumulators(self, stream=None):
+        out = np.zeros((self.total, PMC_ACC_WORDS))
+        check(load().pmc_read_accumulators(self.handle, out.ctypes.data_as(C.POINTER(C.c_double)), out.size,
+                                           _stream(stream)), "pmc_read_accumulators")
+        return out
+
+    def save_state(self, stream=None) -> bytes:
+        size = C.c_size_t(0)
+        check(load().pmc_save_state(self.handle, None, C.byref(size), _stream(stream)), "pmc_save_state")
+        buf = C.create_string_buffer(size.value)
+        check(load().pmc_save_state(self.handle, buf, C.byref(size), _stream(stream)), "pmc_save_state")
+        return buf.raw
+
+    def load_state(self, blob: bytes, stream=None):
+        buf = C.create_string_buffer(blob, len(blob))
+        check(load().pmc_load_state(self.handle, buf, len(blob), _stream(stream)), "pmc_load_state")
+
+    def request_abort(self, flag: bool = True):
+        check(load().pmc_request_abort(self.handle, int(bool(flag))), "pmc_request_abort")
+
+    def status(self, stream=None) -> int:
+        st = C.c_int(0)
+        check(load().pmc_chain_status(self.handle, C.byref(st), _stream(stream)), "pmc_chain_status")
+        return st.value
+
+    def close(self):
+        if self.handle:
+            load().pmc_destroy_chains(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def init_chains(ctx, medium, geom, run, **kw) -> Chains:
+    return Chains(ctx, medium, geom, run, **kw)
+
+
+def run_steps(chains: Chains, n_steps: int, stream=None):
+    chains.run_steps(n_steps, stream)
+
+
+def read_estimator(chains: Chains, stream=None):
+    return chains.read_estimator(stream)
+
+
+def grad_estimator(chains: Chains, stream=None):
+    return chains.grad_estimator(stream)
+
+
+def _check_batch(xyz: torch.Tensor, n: torch.Tensor):
+    _require_cuda(xyz, torch.float32, "xyz")
+    _require_cuda(n, torch.int32, "n")
+    if xyz.dim() != 3 or xyz.shape[0] != 3:
+        raise ValueError("xyz must have shape (3, batch, cap)")
+    batch, cap = int(xyz.shape[1]), int(xyz.shape[2])
+    if n.shape != (batch,):
+        raise ValueError("n must have shape (batch,)")
+    return batch, cap
+
+
+def logp(ctx: Context, medium: Medium, geom: Geometry, pair: int, xyz: torch.Tensor, n: torch.Tensor,
+         stream=None) -> torch.Tensor:
+    """log p of a device batch (pmc_logp); xyz float32 (3, batch, cap), n int32 (batch,)."""
+    batch, cap = _check_batch(xyz, n)
+    out = torch.empty(batch, dtype=torch.float32, device=xyz.device)
+    check(load().pmc_logp(ctx.handle, medium.handle, geom.handle, int(pair), C.c_void_p(xyz.data_ptr()),
+                          C.c_void_p(n.data_ptr()), batch, cap, C.c_void_p(out.data_ptr()), _stream(stream)),
+          "pmc_logp")
+    return out
+
+
+def logp_grad(ctx: Context, medium: Medium, geom: Geometry, pair: int, xyz: torch.Tensor, n: torch.Tensor,
+              stream=None):
+    """log p and d log p / d xyz (pmc_logp_grad)."""
+    batch, cap = _check_batch(xyz, n)
+    lp = torch.empty(batch, dtype=torch.float32, device=xyz.device)
+    g = torch.empty_like(xyz)
+    check(load().pmc_logp_grad(ctx.handle, medium.handle, geom.handle, int(pair), C.c_void_p(xyz.data_ptr()),
+                               C.c_void_p(n.data_ptr()), batch, cap, C.c_void_p(lp.data_ptr()),
+                               C.c_void_p(g.data_ptr()), _stream(stream)), "pmc_logp_grad")
+    return lp, g
+
+
+def score(ctx: Context, medium: Medium, geom: Geometry, pair: int, xyz: torch.Tensor, n: torch.Tensor,
+          stream=None) -> torch.Tensor:
+    """d log p / d theta per path (pmc_score)."""
+    batch, cap = _check_batch(xyz, n)
+    out = torch.empty((batch, medium.n_theta), dtype=torch.float32, device=xyz.device)
+    check(load().pmc_score(ctx.handle, medium.handle, geom.handle, int(pair), C.c_void_p(xyz.data_ptr()),
+                           C.c_void_p(n.data_ptr()), batch, cap, C.c_void_p(out.data_ptr()), _stream(stream)),
+          "pmc_score")
+    return out
+
+
+def trace(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: int, n_photons: int, photon0: int = 0,
+          r_reject: float = math.inf, max_scatter: int = 1 << 30, stream=None):
+    """GPU forward tracer (pmc_trace): dict with the intensity estimate and its standard error."""
+    out = np.zeros(5)
+    check(load().pmc_trace(ctx.handle, medium.handle, geom.handle, int(pair), int(seed), int(photon0),
+                           int(n_photons), float(r_reject), int(min(max_scatter, 2**31 - 1)),
+                           out.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)), "pmc_trace")
+    N = out[3]
+    mean = out[0] / N if N > 0 else float("nan")
+    var = max(out[1] / N - mean * mean, 0.0) if N > 0 else float("nan")
+    return {"I": mean, "se": math.sqrt(var / N) if N > 0 else float("nan"), "hits": out[2], "photons": N,
+            "mean_L": out[4] / out[0] if out[0] > 0 else float("nan"), "raw": out}
+
+
+class LogP(torch.autograd.Function):
+    """log p of a batch of paths; backward is the hand-written adjoint kernel."""
+
+    @staticmethod
+    def forward(fctx, xyz, n, handles):
+        ctx_, med, geom, pair = handles
+        lp, g = logp_grad(ctx_, med, geom, pair, xyz.contiguous(), n)
+        fctx.save_for_backward(g)
+        return lp
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        (g,) = fctx.saved_tensors
+        return g * grad_out.view(1, -1, 1), None, None
+
+
+class PathSampler:
+    """Everything for one scene: context, medium, geometry and chains."""
+
+    def __init__(self, scene: S.Scene, device: int = 0, flags: int = 0, warps_per_block: int = 0,
+                 user_xyz=None, user_n=None):
+        self.scene = scene
+        self.ctx = Context(device)
+        self.medium = Medium(self.ctx, scene.medium)
+        self.geom = Geometry(self.ctx, scene.sources, scene.sensors, scene.pairs)
+        self.chains = Chains(self.ctx, self.medium, self.geom, scene.run, flags, warps_per_block, user_xyz, user_n)
+
+    def run(self, n_steps: Optional[int] = None):
+        self.chains.run_steps(self.scene.run.n_steps if n_steps is None else n_steps)
+        return self
+
+    def estimate(self):
+        return self.chains.read_estimator()

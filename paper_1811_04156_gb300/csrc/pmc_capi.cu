@@ -1,0 +1,796 @@
+// C ABI of libpathmc (declared in include/pathmc.h): handle management,
+// validation, device buffers, CUDA-graph replay of the chain launches.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "pmc_internal.h"
+
+using namespace pmc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      if (e_ == cudaErrorMemoryAllocation) return fail(PMC_ERR_OOM, cudaGetErrorString(e_));  \
+      return fail(PMC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+    }                                                                                         \
+  } while (0)
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+double norm3(const double* v) { return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+
+// Inverse Langevin: coth(k) - 1/k = g (appendix, dimension matching transformation).
+double kappa_eq_host(double g) {
+  if (g <= 0.0) return 0.0;
+  double k = 3.0 * g / (1.0 - g * g);
+  for (int it = 0; it < 200; ++it) {
+    const double f = 1.0 / std::tanh(k) - 1.0 / k - g;
+    const double sh = std::sinh(k);
+    const double df = (k > 300.0 ? 0.0 : -1.0 / (sh * sh)) + 1.0 / (k * k);
+    double kn = k - f / df;
+    if (kn <= 0.0) kn = 0.5 * k;
+    if (std::fabs(kn - k) < 1e-14 * k) {
+      k = kn;
+      break;
+    }
+    k = kn;
+  }
+  return k;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+constexpr int kClassCaps[] = {64, 128, 256, 512, 1024};
+constexpr int kMaxCap = 1024;
+
+}  // namespace
+
+struct pmc_ctx_s {
+  int device = 0;
+  int n_sm = 0;
+  size_t smem_per_sm = 0, smem_per_block = 0;
+};
+
+struct pmc_medium_s {
+  pmc_ctx_s* ctx = nullptr;
+  DMedium d{};
+  float* d_la = nullptr;
+  float* d_lb = nullptr;
+  float* d_llogb = nullptr;
+  double lambda_s = 0, lambda_a = 0;
+  int n_theta = 3;
+};
+
+struct pmc_geom_s {
+  pmc_ctx_s* ctx = nullptr;
+  std::vector<DPair> pairs;  // run-independent fields
+  int total_chains = 0;
+  int max_cap = 0;
+};
+
+struct ChainClass {
+  int smem_cap = 0;
+  int lo = 0, hi = 0;  // range into the processing order
+  int warps_per_block = 4;
+  int grid = 0;
+};
+
+struct pmc_chains_s {
+  pmc_ctx_s* ctx = nullptr;
+  pmc_medium_s* med = nullptr;
+  pmc_geom_s* geom = nullptr;
+  DRun run{};
+  int flags = 0;
+  int total = 0;
+  int n_pairs = 0;
+  std::vector<DPair> h_pairs;
+  std::vector<long long> h_base;
+  std::vector<int> h_pair_of;
+  long long xyz_floats = 0;
+  DPair* d_pairs = nullptr;
+  int* d_chain_pair = nullptr;
+  long long* d_chain_base = nullptr;
+  int* d_order = nullptr;
+  float* d_xyz = nullptr;
+  int* d_n = nullptr;
+  unsigned long long* d_step = nullptr;
+  double* d_acc = nullptr;
+  int* d_status = nullptr;
+  int* d_any = nullptr;
+  unsigned int* d_queue = nullptr;
+  double* d_z2 = nullptr;
+  double* d_est = nullptr;
+  int* h_abort = nullptr;
+  int* d_abort = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  std::vector<ChainClass> classes;
+  std::map<unsigned long long, cudaGraphExec_t> graphs;
+  bool z2_done = false;
+};
+
+extern "C" {
+
+const char* pmc_last_error(void) { return g_err.c_str(); }
+
+const char* pmc_version(void) { return "pathmc 0.1 (sm_103a)"; }
+
+int pmc_create_context(int device, pmc_ctx_t* out) {
+  if (out == nullptr) return fail(PMC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) return fail(PMC_ERR_NO_DEVICE, "no CUDA device available");
+  if (device < 0 || device >= count) return fail(PMC_ERR_NO_DEVICE, "device index out of range");
+  CK(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, device));
+  auto* c = new pmc_ctx_s;
+  c->device = device;
+  c->n_sm = prop.multiProcessorCount;
+  c->smem_per_sm = prop.sharedMemPerMultiprocessor;
+  c->smem_per_block = prop.sharedMemPerBlockOptin;
+  *out = c;
+  return PMC_OK;
+}
+
+int pmc_destroy_context(pmc_ctx_t ctx) {
+  delete ctx;
+  return PMC_OK;
+}
+
+int pmc_create_medium(pmc_ctx_t ctx, const pmc_medium_desc* desc, pmc_medium_t* out) {
+  if (ctx == nullptr || desc == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  const double g = desc->g, f = desc->f_sl;
+  if (!std::isfinite(g) || std::fabs(g) >= 1.0) return fail(PMC_ERR_INVALID, "|g| must be < 1");
+  if (!(f >= 0.0 && f <= 1.0)) return fail(PMC_ERR_INVALID, "f_sl must be in [0, 1]");
+  if (f > 0.0 && !(g > 0.0)) return fail(PMC_ERR_INVALID, "the simplified-Liu component needs g > 0");
+  CK(cudaSetDevice(ctx->device));
+  auto m = std::make_unique<pmc_medium_s>();
+  m->ctx = ctx;
+  DMedium& d = m->d;
+  d.kind = desc->kind;
+  d.g = static_cast<float>(g);
+  d.f_sl = static_cast<float>(f);
+  d.hg_lognorm = static_cast<float>(std::log(0.5 * (1.0 - g * g)) - std::log(2.0 * M_PI));
+  d.omg2 = static_cast<float>((1.0 - g) * (1.0 - g));
+  d.two_g = static_cast<float>(2.0 * g);
+  d.hg_dg0 = static_cast<float>(-2.0 * g / (1.0 - g * g));
+  if (g > 0.0) {
+    d.sl_alpha = static_cast<float>(2.0 * g / (1.0 - g));
+    d.sl_lognorm = static_cast<float>(std::log(0.5 * (1.0 + g) / (1.0 - g)) - std::log(2.0 * M_PI));
+  }
+  d.sl_dg0 = static_cast<float>(2.0 / (1.0 - g * g));
+  d.sl_dg1 = static_cast<float>(2.0 / ((1.0 - g) * (1.0 - g)));
+  d.kappa_eq = static_cast<float>(kappa_eq_host(g));
+  if (desc->kind == PMC_HOMOGENEOUS) {
+    if (!finite_pos(desc->lambda_s) || !finite_pos(desc->lambda_a))
+      return fail(PMC_ERR_INVALID, "lambda_s and lambda_a must be finite and > 0");
+    d.a = static_cast<float>(1.0 / desc->lambda_a);
+    d.b = static_cast<float>(1.0 / desc->lambda_s);
+    d.log_b = static_cast<float>(-std::log(desc->lambda_s));
+    m->lambda_s = desc->lambda_s;
+    m->lambda_a = desc->lambda_a;
+    m->n_theta = 3;
+  } else if (desc->kind == PMC_LAYERED) {
+    const int L = desc->n_layers;
+    if (L < 1 || L > 4096) return fail(PMC_ERR_INVALID, "n_layers must be in [1, 4096]");
+    if (!finite_pos(desc->dz) || !std::isfinite(desc->z0)) return fail(PMC_ERR_INVALID, "bad layer geometry");
+    if (desc->lambda_s_layers == nullptr || desc->lambda_a_layers == nullptr)
+      return fail(PMC_ERR_INVALID, "layer tables are NULL");
+    std::vector<float> la(L), lb(L), llb(L);
+    for (int l = 0; l < L; ++l) {
+      const double s = desc->lambda_s_layers[l], a = desc->lambda_a_layers[l];
+      if (!finite_pos(s) || !finite_pos(a)) return fail(PMC_ERR_INVALID, "layer lengths must be finite and > 0");
+      la[l] = static_cast<float>(1.0 / a);
+      lb[l] = static_cast<float>(1.0 / s);
+      llb[l] = static_cast<float>(-std::log(s));
+    }
+    CK(dalloc(&m->d_la, L));
+    CK(dalloc(&m->d_lb, L));
+    CK(dalloc(&m->d_llogb, L));
+    CK(cudaMemcpy(m->d_la, la.data(), L * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d_lb, lb.data(), L * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(m->d_llogb, llb.data(), L * sizeof(float), cudaMemcpyHostToDevice));
+    d.n_layers = L;
+    d.z0 = static_cast<float>(desc->z0);
+    d.dz = static_cast<float>(desc->dz);
+    d.inv_dz = static_cast<float>(1.0 / desc->dz);
+    d.la = m->d_la;
+    d.lb = m->d_lb;
+    d.llogb = m->d_llogb;
+    m->n_theta = 2 * L;
+  } else {
+    return fail(PMC_ERR_INVALID, "unknown medium kind");
+  }
+  *out = m.release();
+  return PMC_OK;
+}
+
+int pmc_destroy_medium(pmc_medium_t m) {
+  if (m == nullptr) return PMC_OK;
+  cudaFree(m->d_la);
+  cudaFree(m->d_lb);
+  cudaFree(m->d_llogb);
+  delete m;
+  return PMC_OK;
+}
+
+int pmc_n_theta(pmc_medium_t m) { return m ? m->n_theta : 0; }
+
+int pmc_create_geometry(pmc_ctx_t ctx, const pmc_geometry_desc* desc, pmc_geom_t* out) {
+  if (ctx == nullptr || desc == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  if (desc->n_pairs < 1 || desc->pairs == nullptr) return fail(PMC_ERR_INVALID, "no pairs");
+  if (desc->n_sources < 1 || desc->sources == nullptr || desc->n_sensors < 1 || desc->sensors == nullptr)
+    return fail(PMC_ERR_INVALID, "no sources or sensors");
+  auto g = std::make_unique<pmc_geom_s>();
+  g->ctx = ctx;
+  long long total = 0;
+  for (int p = 0; p < desc->n_pairs; ++p) {
+    const pmc_pair& pr = desc->pairs[p];
+    if (pr.source < 0 || pr.source >= desc->n_sources || pr.sensor < 0 || pr.sensor >= desc->n_sensors)
+      return fail(PMC_ERR_INVALID, "pair refers to a missing source or sensor");
+    if (pr.n_chains < 1) return fail(PMC_ERR_INVALID, "n_chains must be >= 1");
+    if (pr.cap < 2 || pr.cap > kMaxCap) return fail(PMC_ERR_INVALID, "cap must be in [2, 1024]");
+    const pmc_source& so = desc->sources[pr.source];
+    const pmc_sensor& se = desc->sensors[pr.sensor];
+    if (!finite_pos(se.radius)) return fail(PMC_ERR_INVALID, "sensor radius must be > 0");
+    DPair d{};
+    double rel[3];
+    for (int i = 0; i < 3; ++i) {
+      if (!std::isfinite(so.pos[i]) || !std::isfinite(se.centre[i])) return fail(PMC_ERR_INVALID, "non-finite position");
+      d.src[i] = static_cast<float>(so.pos[i]);
+      rel[i] = se.centre[i] - so.pos[i];
+      d.c[i] = static_cast<float>(rel[i]);
+    }
+    const double D = norm3(rel);
+    if (!(D > se.radius * (1.0 + 1e-6))) return fail(PMC_ERR_INVALID, "source inside or on its sensor");
+    d.R = static_cast<float>(se.radius);
+    d.R2 = d.R * d.R;
+    d.emission = so.emission;
+    if (so.emission == PMC_EMIT_VMF) {
+      if (!finite_pos(so.kappa)) return fail(PMC_ERR_INVALID, "vMF kappa must be > 0");
+      const double nd = norm3(so.dir);
+      if (!(nd > 0)) return fail(PMC_ERR_INVALID, "zero emission direction");
+      for (int i = 0; i < 3; ++i) d.dir[i] = static_cast<float>(so.dir[i] / nd);
+      d.kappa = static_cast<float>(so.kappa);
+      const double k = so.kappa;
+      d.vmf_lognorm = static_cast<float>(std::log(k) - std::log(2.0 * M_PI) - k - std::log(-std::expm1(-2.0 * k)));
+    } else if (so.emission != PMC_EMIT_ISOTROPIC) {
+      return fail(PMC_ERR_INVALID, "unknown emission kind");
+    }
+    d.rho = se.rho;
+    if (se.rho == PMC_RHO_PAPER) {
+      const double nr = norm3(se.rho_hat);
+      if (!(nr > 0)) return fail(PMC_ERR_INVALID, "zero rho_hat");
+      for (int i = 0; i < 3; ++i) d.rho_hat[i] = static_cast<float>(se.rho_hat[i] / nr);
+    } else if (se.rho != PMC_RHO_ONE) {
+      return fail(PMC_ERR_INVALID, "unknown detection kind");
+    }
+    for (int i = 0; i < 3; ++i) d.e_near[i] = static_cast<float>(rel[i] - se.radius * rel[i] / D);
+    d.cap = pr.cap;
+    d.n_chains = pr.n_chains;
+    d.chain0 = static_cast<int>(total);
+    total += pr.n_chains;
+    if (total > (1ll << 30)) return fail(PMC_ERR_INVALID, "too many chains");
+    g->max_cap = std::max(g->max_cap, pr.cap);
+    g->pairs.push_back(d);
+  }
+  g->total_chains = static_cast<int>(total);
+  *out = g.release();
+  return PMC_OK;
+}
+
+int pmc_destroy_geometry(pmc_geom_t g) {
+  delete g;
+  return PMC_OK;
+}
+
+static int class_of(int cap) {
+  for (int i = 0; i < 5; ++i)
+    if (cap <= kClassCaps[i]) return i;
+  return 4;
+}
+
+int pmc_destroy_chains(pmc_chains_t ch) {
+  if (ch == nullptr) return PMC_OK;
+  cudaSetDevice(ch->ctx->device);
+  for (auto& kv : ch->graphs) cudaGraphExecDestroy(kv.second);
+  if (ch->capture_stream) cudaStreamDestroy(ch->capture_stream);
+  cudaFree(ch->d_pairs);
+  cudaFree(ch->d_chain_pair);
+  cudaFree(ch->d_chain_base);
+  cudaFree(ch->d_order);
+  cudaFree(ch->d_xyz);
+  cudaFree(ch->d_n);
+  cudaFree(ch->d_step);
+  cudaFree(ch->d_acc);
+  cudaFree(ch->d_status);
+  cudaFree(ch->d_any);
+  cudaFree(ch->d_queue);
+  cudaFree(ch->d_z2);
+  cudaFree(ch->d_est);
+  if (ch->h_abort) cudaFreeHost(ch->h_abort);
+  delete ch;
+  return PMC_OK;
+}
+
+int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_run_desc* r, void* stream,
+                    pmc_chains_t* out) {
+  if (!ctx || !med || !geom || !r || !out) return fail(PMC_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  const double pw = r->p_within, pb = r->p_birth, pd = r->p_death;
+  if (!(pw >= 0 && pb >= 0 && pd >= 0) || std::fabs(pw + pb + pd - 1.0) > 1e-9)
+    return fail(PMC_ERR_INVALID, "move probabilities must be >= 0 and sum to 1");
+  if (pb > 0 && !(pd > 0)) return fail(PMC_ERR_INVALID, "births need deaths (reversibility)");
+  if (pd > 0 && !(pb > 0)) return fail(PMC_ERR_INVALID, "deaths need births (reversibility)");
+  if (!finite_pos(r->sigma)) return fail(PMC_ERR_INVALID, "sigma must be > 0");
+  if (r->within == PMC_WITHIN_MALA && !finite_pos(r->mala_step)) return fail(PMC_ERR_INVALID, "mala_step must be > 0");
+  if (r->within != PMC_WITHIN_PERTURB && r->within != PMC_WITHIN_MALA) return fail(PMC_ERR_INVALID, "bad within kind");
+  if (r->init != PMC_INIT_DIRECT && r->init != PMC_INIT_STRAIGHT && r->init != PMC_INIT_USER)
+    return fail(PMC_ERR_INVALID, "bad init kind");
+  if (r->init == PMC_INIT_STRAIGHT && (r->init_k < 0 || !(r->init_jitter >= 0)))
+    return fail(PMC_ERR_INVALID, "bad straight init");
+  if (r->init == PMC_INIT_USER && (!r->init_xyz || !r->init_n || r->init_stride < 2))
+    return fail(PMC_ERR_INVALID, "USER init needs init_xyz, init_n and init_stride");
+  if (r->kappa_end < 0 || !std::isfinite(r->kappa_end)) return fail(PMC_ERR_INVALID, "bad kappa_end");
+  CK(cudaSetDevice(ctx->device));
+
+  auto ch = std::unique_ptr<pmc_chains_s, int (*)(pmc_chains_t)>(new pmc_chains_s, pmc_destroy_chains);
+  ch->ctx = ctx;
+  ch->med = med;
+  ch->geom = geom;
+  ch->flags = r->flags;
+  ch->total = geom->total_chains;
+  ch->n_pairs = static_cast<int>(geom->pairs.size());
+  DRun& R = ch->run;
+  R.seed = r->seed;
+  R.thr_within = static_cast<uint32_t>(std::floor(pw * 8388608.0 + 0.5));
+  R.thr_birth = static_cast<uint32_t>(std::floor((pw + pb) * 8388608.0 + 0.5));
+  R.log_pb = pb > 0 ? static_cast<float>(std::log(pb)) : 0.f;
+  R.log_pd = pd > 0 ? static_cast<float>(std::log(pd)) : 0.f;
+  R.sigma = static_cast<float>(r->sigma);
+  R.mala_eps = static_cast<float>(r->mala_step);
+  R.within = r->within;
+  R.burn_in = r->burn_in;
+  R.beta_min = 0.01f;
+  R.gradients = (r->flags & PMC_FLAG_GRADIENTS) ? 1 : 0;
+
+  ch->h_pairs = geom->pairs;
+  for (auto& d : ch->h_pairs) {
+    const double ke = r->kappa_end > 0 ? r->kappa_end : (d.R / r->sigma) * (d.R / r->sigma);
+    d.kappa_end = static_cast<float>(ke);
+    d.exp_m2ke = static_cast<float>(std::exp(-2.0 * ke));
+  }
+  const int T = ch->total;
+  ch->h_base.resize(T);
+  ch->h_pair_of.resize(T);
+  long long off = 0;
+  for (int p = 0; p < ch->n_pairs; ++p) {
+    const DPair& d = ch->h_pairs[p];
+    for (int k = 0; k < d.n_chains; ++k) {
+      const int c = d.chain0 + k;
+      ch->h_pair_of[c] = p;
+      ch->h_base[c] = off;
+      off += 3ll * d.cap;
+    }
+  }
+  ch->xyz_floats = off;
+  // processing order: by cap class, longest caps first inside a class
+  std::vector<int> order(T);
+  for (int c = 0; c < T; ++c) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const int ca = ch->h_pairs[ch->h_pair_of[a]].cap, cb = ch->h_pairs[ch->h_pair_of[b]].cap;
+    const int ka = class_of(ca), kb = class_of(cb);
+    if (ka != kb) return ka < kb;
+    return ca > cb;
+  });
+  for (int lo = 0; lo < T;) {
+    const int k = class_of(ch->h_pairs[ch->h_pair_of[order[lo]]].cap);
+    int hi = lo;
+    int maxcap = 0;
+    while (hi < T && class_of(ch->h_pairs[ch->h_pair_of[order[hi]]].cap) == k) {
+      maxcap = std::max(maxcap, ch->h_pairs[ch->h_pair_of[order[hi]]].cap);
+      ++hi;
+    }
+    ChainClass cl;
+    cl.smem_cap = (maxcap + 31) / 32 * 32;
+    cl.lo = lo;
+    cl.hi = hi;
+    ch->classes.push_back(cl);
+    lo = hi;
+  }
+  // launch shapes: warps per block from the request (0: default), persistent grid from occupancy
+  for (auto& cl : ch->classes) {
+    int wpb = r->warps_per_block > 0 ? r->warps_per_block : 4;
+    wpb = std::min(wpb, 8);
+    while (wpb > 1 && chain_smem_bytes(cl.smem_cap, wpb) > ctx->smem_per_block) wpb /= 2;
+    if (chain_smem_bytes(cl.smem_cap, wpb) > ctx->smem_per_block) return fail(PMC_ERR_INVALID, "vertex cap too large for shared memory");
+    int bps = 0;
+    CK(chain_occupancy(wpb, cl.smem_cap, &bps));
+    if (bps < 1) return fail(PMC_ERR_INVALID, "chain kernel does not fit on an SM");
+    const int chains = cl.hi - cl.lo;
+    const int want = (chains + wpb - 1) / wpb;
+    cl.warps_per_block = wpb;
+    cl.grid = std::max(1, std::min(want, bps * ctx->n_sm));
+  }
+
+  CK(dalloc(&ch->d_pairs, ch->n_pairs));
+  CK(dalloc(&ch->d_chain_pair, T));
+  CK(dalloc(&ch->d_chain_base, T));
+  CK(dalloc(&ch->d_order, T));
+  CK(dalloc(&ch->d_xyz, static_cast<size_t>(ch->xyz_floats)));
+  CK(dalloc(&ch->d_n, T));
+  CK(dalloc(&ch->d_step, T));
+  CK(dalloc(&ch->d_acc, static_cast<size_t>(T) * ACC_WORDS));
+  CK(dalloc(&ch->d_status, T));
+  CK(dalloc(&ch->d_any, 1));
+  CK(dalloc(&ch->d_queue, ch->classes.size()));
+  CK(dalloc(&ch->d_z2, ch->n_pairs));
+  CK(dalloc(&ch->d_est, static_cast<size_t>(ch->n_pairs) * EST_WORDS));
+  CK(cudaHostAlloc(reinterpret_cast<void**>(&ch->h_abort), sizeof(int), cudaHostAllocMapped));
+  *ch->h_abort = 0;
+  CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ch->d_abort), ch->h_abort, 0));
+  CK(cudaStreamCreateWithFlags(&ch->capture_stream, cudaStreamNonBlocking));
+
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(ch->d_pairs, ch->h_pairs.data(), sizeof(DPair) * ch->n_pairs, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ch->d_chain_pair, ch->h_pair_of.data(), sizeof(int) * T, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ch->d_chain_base, ch->h_base.data(), sizeof(long long) * T, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ch->d_order, order.data(), sizeof(int) * T, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ch->d_status, 0, sizeof(int) * T, s));
+  CK(cudaMemsetAsync(ch->d_any, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(ch->d_xyz, 0, sizeof(float) * ch->xyz_floats, s));
+
+  InitParams ip{};
+  ip.R = R;
+  ip.pairs = ch->d_pairs;
+  ip.chain_pair = ch->d_chain_pair;
+  ip.chain_base = ch->d_chain_base;
+  ip.xyz = ch->d_xyz;
+  ip.n = ch->d_n;
+  ip.step = ch->d_step;
+  ip.acc = ch->d_acc;
+  ip.status = ch->d_status;
+  ip.total = T;
+  ip.init_kind = r->init;
+  ip.init_k = r->init_k;
+  ip.jitter = static_cast<float>(r->init_jitter);
+  float* d_user = nullptr;
+  int* d_user_n = nullptr;
+  if (r->init == PMC_INIT_USER) {
+    const size_t nf = static_cast<size_t>(T) * 3 * r->init_stride;
+    CK(dalloc(&d_user, nf));
+    CK(dalloc(&d_user_n, T));
+    CK(cudaMemcpyAsync(d_user, r->init_xyz, nf * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_user_n, r->init_n, T * sizeof(int), cudaMemcpyHostToDevice, s));
+    ip.user_xyz = d_user;
+    ip.user_n = d_user_n;
+    ip.user_stride = r->init_stride;
+  }
+  CK(launch_init(ip, s));
+  // direct-sector integral per pair (axisymmetric integrands need one azimuth)
+  const bool axisym = std::all_of(ch->h_pairs.begin(), ch->h_pairs.end(),
+                                  [](const DPair& d) { return d.emission == 0 && d.rho == 0; }) &&
+                      med->d.kind == 0;
+  CK(launch_z2(med->d, ch->d_pairs, ch->n_pairs, 4096, axisym ? 1 : 64, ch->d_z2, s));
+  if (d_user) {
+    CK(cudaStreamSynchronize(s));
+    cudaFree(d_user);
+    cudaFree(d_user_n);
+  }
+  *out = ch.release();
+  return PMC_OK;
+}
+
+static int enqueue_steps(pmc_chains_t ch, unsigned long long n_steps, cudaStream_t s) {
+  for (size_t k = 0; k < ch->classes.size(); ++k) {
+    const ChainClass& cl = ch->classes[k];
+    ChainParams p{};
+    p.M = ch->med->d;
+    p.R = ch->run;
+    p.pairs = ch->d_pairs;
+    p.chain_pair = ch->d_chain_pair;
+    p.chain_base = ch->d_chain_base;
+    p.order = ch->d_order;
+    p.xyz = ch->d_xyz;
+    p.n = ch->d_n;
+    p.step = ch->d_step;
+    p.acc = ch->d_acc;
+    p.status = ch->d_status;
+    p.any_status = ch->d_any;
+    p.queue = ch->d_queue + k;
+    p.abort_flag = ch->d_abort;
+    p.chain_lo = cl.lo;
+    p.chain_hi = cl.hi;
+    p.n_steps = n_steps;
+    p.smem_cap = cl.smem_cap;
+    CK(cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s));
+    CK(launch_chain(p, cl.grid, cl.warps_per_block, s));
+  }
+  return PMC_OK;
+}
+
+int pmc_run_steps(pmc_chains_t ch, uint64_t n_steps, void* stream) {
+  if (ch == nullptr) return fail(PMC_ERR_INVALID, "NULL chains");
+  if (n_steps == 0) return PMC_OK;
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (ch->flags & PMC_FLAG_NO_GRAPH) return enqueue_steps(ch, n_steps, s);
+  auto it = ch->graphs.find(n_steps);
+  if (it == ch->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ch->capture_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_steps(ch, n_steps, ch->capture_stream);
+    cudaError_t e = cudaStreamEndCapture(ch->capture_stream, &g);
+    if (rc != PMC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    CK(e);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    it = ch->graphs.emplace(n_steps, ex).first;
+  }
+  CK(cudaGraphLaunch(it->second, s));
+  return PMC_OK;
+}
+
+static int check_status(pmc_chains_t ch, cudaStream_t s) {
+  int any = 0;
+  CK(cudaMemcpyAsync(&any, ch->d_any, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (any & ST_ABORTED) return fail(PMC_ERR_ABORTED, "chains aborted on request");
+  if (any) return fail(PMC_ERR_DEVICE_STATUS, "chain status word " + std::to_string(any));
+  return PMC_OK;
+}
+
+int pmc_read_estimator(pmc_chains_t ch, pmc_estimate* out, size_t n_pairs, void* stream) {
+  if (ch == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (n_pairs < static_cast<size_t>(ch->n_pairs)) return fail(PMC_ERR_INVALID, "output has fewer entries than pairs");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  EstParams p{};
+  p.acc = ch->d_acc;
+  p.pairs = ch->d_pairs;
+  p.z2 = ch->d_z2;
+  p.bridge_q = nullptr;
+  p.n_pairs = ch->n_pairs;
+  p.homogeneous = ch->med->d.kind == 0;
+  p.lambda_s = ch->med->d.kind == 0 ? ch->med->lambda_s : 1.0;
+  p.lambda_a = ch->med->d.kind == 0 ? ch->med->lambda_a : 1.0;
+  p.out = ch->d_est;
+  CK(launch_estimator(p, s));
+  std::vector<double> h(static_cast<size_t>(ch->n_pairs) * EST_WORDS);
+  CK(cudaMemcpyAsync(h.data(), ch->d_est, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  const int st = check_status(ch, s);
+  for (int i = 0; i < ch->n_pairs; ++i) {
+    const double* e = h.data() + static_cast<size_t>(i) * EST_WORDS;
+    pmc_estimate& o = out[i];
+    o.intensity = e[EST_I];
+    o.std_err = e[EST_SE];
+    o.rel_err = e[EST_REL];
+    o.pi_direct = e[EST_PI];
+    o.z2 = e[EST_Z2];
+    o.rhat = e[EST_RHAT];
+    for (int k = 0; k < 4; ++k) {
+      o.accept[k] = e[EST_ACC0 + k];
+      o.proposals[k] = e[EST_PROP0 + k];
+    }
+    o.mean_n = e[EST_MEAN_N];
+    o.mean_length = e[EST_MEAN_L];
+    o.n_samples = e[EST_NSAMP];
+    o.ess = e[EST_ESS];
+    o.bridge_intensity = e[EST_BRIDGE_I];
+    o.bridge_std_err = e[EST_BRIDGE_SE];
+  }
+  return st;
+}
+
+int pmc_grad_estimator(pmc_chains_t ch, double* grad, double* grad_se, size_t len, void* stream) {
+  if (ch == nullptr || grad == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (!(ch->flags & PMC_FLAG_GRADIENTS)) return fail(PMC_ERR_INVALID, "chains were created without PMC_FLAG_GRADIENTS");
+  const int nt = ch->med->n_theta;
+  if (len < static_cast<size_t>(ch->n_pairs) * nt) return fail(PMC_ERR_INVALID, "output too short");
+  if (ch->med->d.kind != 0) return fail(PMC_ERR_INVALID, "layered gradients are not available in this build");
+  std::vector<pmc_estimate> tmp(ch->n_pairs);
+  const int rc = pmc_read_estimator(ch, tmp.data(), tmp.size(), stream);
+  if (rc != PMC_OK) return rc;
+  std::vector<double> h(static_cast<size_t>(ch->n_pairs) * EST_WORDS);
+  CK(cudaMemcpy(h.data(), ch->d_est, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < ch->n_pairs; ++i) {
+    for (int k = 0; k < 3; ++k) {
+      grad[i * 3 + k] = h[static_cast<size_t>(i) * EST_WORDS + EST_GRAD0 + k];
+      if (grad_se) grad_se[i * 3 + k] = h[static_cast<size_t>(i) * EST_WORDS + EST_GRADSE0 + k];
+    }
+  }
+  return PMC_OK;
+}
+
+int pmc_total_chains(pmc_chains_t ch) { return ch ? ch->total : 0; }
+
+int pmc_read_states(pmc_chains_t ch, float* xyz, int* n, uint64_t* steps, int stride, void* stream) {
+  if (ch == nullptr || xyz == nullptr || n == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (stride < ch->geom->max_cap) return fail(PMC_ERR_INVALID, "stride smaller than the largest cap");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<float> buf(static_cast<size_t>(ch->xyz_floats));
+  CK(cudaMemcpyAsync(buf.data(), ch->d_xyz, buf.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(n, ch->d_n, sizeof(int) * ch->total, cudaMemcpyDeviceToHost, s));
+  if (steps) CK(cudaMemcpyAsync(steps, ch->d_step, sizeof(uint64_t) * ch->total, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int c = 0; c < ch->total; ++c) {
+    const DPair& d = ch->h_pairs[ch->h_pair_of[c]];
+    const float* src = buf.data() + ch->h_base[c];
+    float* dst = xyz + static_cast<size_t>(c) * 3 * stride;
+    for (int a = 0; a < 3; ++a)
+      for (int i = 0; i < stride; ++i)
+        dst[a * stride + i] = (i < n[c] && i < d.cap) ? src[a * d.cap + i] + d.src[a] : 0.f;
+  }
+  return PMC_OK;
+}
+
+int pmc_read_accumulators(pmc_chains_t ch, double* out, size_t n_doubles, void* stream) {
+  if (ch == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  const size_t need = static_cast<size_t>(ch->total) * ACC_WORDS;
+  if (n_doubles < need) return fail(PMC_ERR_INVALID, "output too short");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(out, ch->d_acc, need * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return PMC_OK;
+}
+
+static size_t state_bytes(pmc_chains_t ch) {
+  return 16 + sizeof(float) * static_cast<size_t>(ch->xyz_floats) + sizeof(int) * ch->total +
+         sizeof(unsigned long long) * ch->total + sizeof(double) * static_cast<size_t>(ch->total) * ACC_WORDS +
+         sizeof(int) * ch->total;
+}
+
+int pmc_save_state(pmc_chains_t ch, void* buf, size_t* bytes, void* stream) {
+  if (ch == nullptr || bytes == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  const size_t need = state_bytes(ch);
+  if (buf == nullptr) {
+    *bytes = need;
+    return PMC_OK;
+  }
+  if (*bytes < need) return fail(PMC_ERR_INVALID, "buffer too small");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* p = static_cast<char*>(buf);
+  const long long hdr[2] = {0x504d4353544154ll, static_cast<long long>(need)};
+  std::memcpy(p, hdr, 16);
+  p += 16;
+  CK(cudaMemcpyAsync(p, ch->d_xyz, sizeof(float) * ch->xyz_floats, cudaMemcpyDeviceToHost, s));
+  p += sizeof(float) * ch->xyz_floats;
+  CK(cudaMemcpyAsync(p, ch->d_n, sizeof(int) * ch->total, cudaMemcpyDeviceToHost, s));
+  p += sizeof(int) * ch->total;
+  CK(cudaMemcpyAsync(p, ch->d_step, sizeof(unsigned long long) * ch->total, cudaMemcpyDeviceToHost, s));
+  p += sizeof(unsigned long long) * ch->total;
+  CK(cudaMemcpyAsync(p, ch->d_acc, sizeof(double) * ch->total * ACC_WORDS, cudaMemcpyDeviceToHost, s));
+  p += sizeof(double) * ch->total * ACC_WORDS;
+  CK(cudaMemcpyAsync(p, ch->d_status, sizeof(int) * ch->total, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *bytes = need;
+  return PMC_OK;
+}
+
+int pmc_load_state(pmc_chains_t ch, const void* buf, size_t bytes, void* stream) {
+  if (ch == nullptr || buf == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  const size_t need = state_bytes(ch);
+  long long hdr[2];
+  if (bytes < need) return fail(PMC_ERR_INVALID, "buffer too small");
+  std::memcpy(hdr, buf, 16);
+  if (hdr[0] != 0x504d4353544154ll || hdr[1] != static_cast<long long>(need))
+    return fail(PMC_ERR_INVALID, "buffer does not hold a state of these chains");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const char* p = static_cast<const char*>(buf) + 16;
+  CK(cudaMemcpyAsync(ch->d_xyz, p, sizeof(float) * ch->xyz_floats, cudaMemcpyHostToDevice, s));
+  p += sizeof(float) * ch->xyz_floats;
+  CK(cudaMemcpyAsync(ch->d_n, p, sizeof(int) * ch->total, cudaMemcpyHostToDevice, s));
+  p += sizeof(int) * ch->total;
+  CK(cudaMemcpyAsync(ch->d_step, p, sizeof(unsigned long long) * ch->total, cudaMemcpyHostToDevice, s));
+  p += sizeof(unsigned long long) * ch->total;
+  CK(cudaMemcpyAsync(ch->d_acc, p, sizeof(double) * ch->total * ACC_WORDS, cudaMemcpyHostToDevice, s));
+  p += sizeof(double) * ch->total * ACC_WORDS;
+  CK(cudaMemcpyAsync(ch->d_status, p, sizeof(int) * ch->total, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ch->d_any, 0, sizeof(int), s));
+  CK(cudaStreamSynchronize(s));
+  return PMC_OK;
+}
+
+int pmc_request_abort(pmc_chains_t ch, int flag) {
+  if (ch == nullptr) return fail(PMC_ERR_INVALID, "NULL chains");
+  *reinterpret_cast<volatile int*>(ch->h_abort) = flag;
+  return PMC_OK;
+}
+
+int pmc_chain_status(pmc_chains_t ch, int* status, void* stream) {
+  if (ch == nullptr || status == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(status, ch->d_any, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return PMC_OK;
+}
+
+static const DPair* pair_of(pmc_geom_t g, int pair) {
+  if (g == nullptr || pair < 0 || pair >= static_cast<int>(g->pairs.size())) return nullptr;
+  return &g->pairs[pair];
+}
+
+int pmc_logp(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, const float* xyz, const int* n,
+             int batch, int cap, float* out_logp, void* stream) {
+  const DPair* d = pair_of(geom, pair);
+  if (!ctx || !med || !d || !xyz || !n || !out_logp) return fail(PMC_ERR_INVALID, "bad argument");
+  if (batch < 0 || cap < 2 || cap > (1 << 20)) return fail(PMC_ERR_INVALID, "bad batch or cap");
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_logp(med->d, *d, xyz, n, batch, cap, out_logp, nullptr, static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
+int pmc_logp_grad(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, const float* xyz, const int* n,
+                  int batch, int cap, float* out_logp, float* out_grad, void* stream) {
+  const DPair* d = pair_of(geom, pair);
+  if (!ctx || !med || !d || !xyz || !n || !out_grad) return fail(PMC_ERR_INVALID, "bad argument");
+  if (batch < 0 || cap < 2 || cap > (1 << 20)) return fail(PMC_ERR_INVALID, "bad batch or cap");
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_logp(med->d, *d, xyz, n, batch, cap, out_logp, out_grad, static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
+int pmc_score(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, const float* xyz, const int* n,
+              int batch, int cap, float* out, void* stream) {
+  const DPair* d = pair_of(geom, pair);
+  if (!ctx || !med || !d || !xyz || !n || !out) return fail(PMC_ERR_INVALID, "bad argument");
+  if (batch < 0 || cap < 2) return fail(PMC_ERR_INVALID, "bad batch or cap");
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_score(med->d, *d, xyz, n, batch, cap, out, med->n_theta, nullptr, nullptr,
+                  static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
+int pmc_trace(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, uint64_t seed, uint64_t photon0,
+              uint64_t n_photons, double r_reject, int max_scatter, double* out, void* stream) {
+  const DPair* d = pair_of(geom, pair);
+  if (!ctx || !med || !d || !out) return fail(PMC_ERR_INVALID, "bad argument");
+  if (max_scatter < 0 || !(r_reject > 0)) return fail(PMC_ERR_INVALID, "bad tracer limits");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* d_out = nullptr;
+  CK(dalloc(&d_out, 5));
+  const float rr = std::isfinite(r_reject) ? static_cast<float>(r_reject) : std::numeric_limits<float>::infinity();
+  cudaError_t e = launch_trace(med->d, *d, seed, photon0, n_photons, rr, max_scatter, d_out, ctx->n_sm, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_out);
+  CK(e);
+  return PMC_OK;
+}
+
+}  // extern "C"

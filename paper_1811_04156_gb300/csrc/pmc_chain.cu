@@ -1,0 +1,596 @@
+// Persistent RJMCMC chain kernel: one warp per chain, the chain's path staged
+// in shared memory as SoA arrays with per-segment and per-vertex caches of the
+// log-density factors (Collin, arXiv:1811.04156: section "Numerical path
+// integration", Eq. acceptFact; appendix "Jump proposal" and "Dimension
+// matching transformation").
+//
+// Per warp and per step:
+//   * random numbers: every 32 steps each lane draws the two Philox4x32-10
+//     blocks of one future step and pre-transforms them (Box-Muller normals,
+//     vMF cosine, logistic t), so the serial path only broadcasts 8 words;
+//   * delta evaluator: a move changes at most 3 vertex factors and 2 segment
+//     factors; lane i evaluates vertex factor i and segment factor i of the
+//     changed window in parallel, the old values come from the caches, and
+//     three shuffles give the change of log p;
+//   * accept / commit: births and deaths shift the SoA arrays with the whole
+//     warp; caches of the changed window are written back.
+// Estimators: observables (n, length L, sum of d log sigma/dg) change only on
+// acceptance, so each state's values are added once with its dwell time into
+// FP32 partials that are flushed into lane-distributed FP64 accumulators.
+#include "pmc_internal.h"
+
+namespace pmc {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRefreshSteps = 256;  // recompute the running sums from the caches
+constexpr int kFlushAccepts = 64;   // FP32 partials -> FP64 accumulators
+
+enum Move { MV_INTERIOR = 0, MV_END = 1, MV_BIRTH = 2, MV_DEATH = 3 };
+
+struct WarpPath {
+  float *x, *y, *z, *tb, *seg, *len, *vt, *gt;
+  __device__ float3 pos(int i) const { return f3(x[i], y[i], z[i]); }
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+struct Sums {
+  float lp, tb, L, G;
+};
+
+__device__ Sums path_sums(const WarpPath& w, int n, int lane) {
+  float lp = 0.f, tb = 0.f, L = 0.f, G = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    lp += w.vt[i];
+    G += w.gt[i];
+    if (i <= n - 2) {
+      lp += w.seg[i];
+      tb += w.tb[i];
+      L += w.len[i];
+    }
+  }
+  Sums s;
+  s.lp = warp_sum(lp);
+  s.tb = warp_sum(tb);
+  s.L = warp_sum(L);
+  s.G = warp_sum(G);
+  return s;
+}
+
+// Recompute every cached factor of the path from its vertices.
+__device__ void refresh_caches(const DMedium& M, const DPair& S, float zoff, const WarpPath& w, int n,
+                               int lane) {
+  for (int i = lane; i < n; i += 32) {
+    const float3 P = w.pos(i);
+    const float3 Pp = (i >= 1) ? w.pos(i - 1) : P;
+    const float3 Pn = (i <= n - 2) ? w.pos(i + 1) : P;
+    float g;
+    w.vt[i] = vertex_term(M, S, zoff, Pp, P, Pn, i, n, g);
+    w.gt[i] = g;
+    if (i <= n - 2) {
+      const SegOut so = segment_term(M, S, zoff, P, Pn, i <= n - 3);
+      w.seg[i] = so.seg;
+      w.tb[i] = so.tb;
+      w.len[i] = so.len;
+    }
+  }
+  __syncwarp();
+}
+
+// Shift entries [a, e) of the vertex-indexed and segment-indexed arrays.
+__device__ void shift_right(const WarpPath& w, int a, int e_vtx, int e_seg, int lane) {
+  for (int base = e_vtx - 1; base >= a; base -= 32) {
+    const int i = base - lane;
+    const bool ok = i >= a;
+    const bool oks = ok && i < e_seg;
+    float x = 0, y = 0, z = 0, vt = 0, gt = 0, tb = 0, sg = 0, ln = 0;
+    if (ok) { x = w.x[i]; y = w.y[i]; z = w.z[i]; vt = w.vt[i]; gt = w.gt[i]; }
+    if (oks) { tb = w.tb[i]; sg = w.seg[i]; ln = w.len[i]; }
+    __syncwarp();
+    if (ok) { w.x[i + 1] = x; w.y[i + 1] = y; w.z[i + 1] = z; w.vt[i + 1] = vt; w.gt[i + 1] = gt; }
+    if (oks) { w.tb[i + 1] = tb; w.seg[i + 1] = sg; w.len[i + 1] = ln; }
+    __syncwarp();
+  }
+}
+
+__device__ void shift_left(const WarpPath& w, int a, int e_vtx, int e_seg, int lane) {
+  for (int base = a; base < e_vtx; base += 32) {
+    const int i = base + lane;
+    const bool ok = i < e_vtx;
+    const bool oks = i < e_seg;
+    float x = 0, y = 0, z = 0, vt = 0, gt = 0, tb = 0, sg = 0, ln = 0;
+    if (ok) { x = w.x[i]; y = w.y[i]; z = w.z[i]; vt = w.vt[i]; gt = w.gt[i]; }
+    if (oks) { tb = w.tb[i]; sg = w.seg[i]; ln = w.len[i]; }
+    __syncwarp();
+    if (ok) { w.x[i - 1] = x; w.y[i - 1] = y; w.z[i - 1] = z; w.vt[i - 1] = vt; w.gt[i - 1] = gt; }
+    if (oks) { w.tb[i - 1] = tb; w.seg[i - 1] = sg; w.len[i - 1] = ln; }
+    __syncwarp();
+  }
+}
+
+// Segment chosen for a birth: smallest k with cumsum_k(tau_b) > u * T_b.
+__device__ int select_segment(const WarpPath& w, int nseg, float u, float& total, int lane) {
+  const int m = (nseg + 31) >> 5;
+  const int lo = lane * m;
+  const int hi = min(lo + m, nseg);
+  float local = 0.f;
+  for (int i = lo; i < hi; ++i) local += w.tb[i];
+  float incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  total = __shfl_sync(kFull, incl, 31);
+  const float target = u * total;
+  const unsigned has = __ballot_sync(kFull, lo < nseg);
+  const unsigned over = __ballot_sync(kFull, lo < nseg && incl > target);
+  const int owner = over ? (__ffs(over) - 1) : (31 - __clz(has));
+  int k = nseg - 1;
+  if (lane == owner) {
+    float cum = incl - local;
+    k = hi - 1;
+    for (int i = lo; i < hi; ++i) {
+      cum += w.tb[i];
+      if (cum > target) { k = i; break; }
+    }
+  }
+  return __shfl_sync(kFull, k, owner);
+}
+
+struct Accum {
+  // FP32 / integer partials of the current flush interval
+  unsigned long long pn2, pn;
+  float pL, pL2, pG;
+  unsigned int dwell, nflush;
+  unsigned int prop[4], acc[4];
+  double my;  // lane-distributed FP64 accumulator word `lane` (lanes 0..15)
+};
+
+__device__ __forceinline__ void add_dwell(Accum& a, int n, float L, float G) {
+  if (a.dwell == 0) return;
+  const float dw = static_cast<float>(a.dwell);
+  a.pn2 += (n == 2) ? a.dwell : 0u;
+  a.pn += static_cast<unsigned long long>(n) * a.dwell;
+  a.pL = fmaf(L, dw, a.pL);
+  a.pL2 = fmaf(L * L, dw, a.pL2);
+  a.pG = fmaf(G, dw, a.pG);
+  a.dwell = 0;
+  a.nflush++;
+}
+
+__device__ __forceinline__ void flush64(Accum& a, int lane) {
+  double v = 0.0;
+  if (lane == ACC_NDIRECT) v = static_cast<double>(a.pn2);
+  if (lane == ACC_SUMN) v = static_cast<double>(a.pn);
+  if (lane == ACC_SUML) v = static_cast<double>(a.pL);
+  if (lane == ACC_SUML2) v = static_cast<double>(a.pL2);
+  if (lane == ACC_SUMG) v = static_cast<double>(a.pG);
+  a.my += v;
+  a.pn2 = 0;
+  a.pn = 0;
+  a.pL = a.pL2 = a.pG = 0.f;
+  a.nflush = 0;
+}
+
+__global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
+  extern __shared__ float smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int cap_s = P.smem_cap;
+  WarpPath w;
+  w.x = smem + static_cast<size_t>(wib) * 8 * cap_s;
+  w.y = w.x + cap_s;
+  w.z = w.y + cap_s;
+  w.tb = w.z + cap_s;
+  w.seg = w.tb + cap_s;
+  w.len = w.seg + cap_s;
+  w.vt = w.len + cap_s;
+  w.gt = w.vt + cap_s;
+  const DMedium& M = P.M;
+  const DRun& R = P.R;
+  const uint32_t key0 = static_cast<uint32_t>(R.seed), key1 = static_cast<uint32_t>(R.seed >> 32);
+
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = static_cast<int>(atomicAdd(P.queue, 1u));
+    item = __shfl_sync(kFull, item, 0);
+    if (P.chain_lo + item >= P.chain_hi) break;
+    const int c = P.order[P.chain_lo + item];
+
+    const DPair S = P.pairs[P.chain_pair[c]];
+    const float zoff = S.src[2];
+    const int cap = S.cap;
+    int n = P.n[c];
+    const unsigned long long step0 = P.step[c];
+    if (n < 2 || n > cap || cap > cap_s) {
+      if (lane == 0) { P.status[c] |= ST_BAD_N; atomicOr(P.any_status, ST_BAD_N); }
+      continue;
+    }
+    float* gx = P.xyz + P.chain_base[c];
+    float* gy = gx + cap;
+    float* gz = gy + cap;
+    for (int i = lane; i < n; i += 32) { w.x[i] = gx[i]; w.y[i] = gy[i]; w.z[i] = gz[i]; }
+    __syncwarp();
+    refresh_caches(M, S, zoff, w, n, lane);
+    Sums sm = path_sums(w, n, lane);
+    if (!isfinite(sm.lp)) {
+      if (lane == 0) { P.status[c] |= ST_NONFINITE; atomicOr(P.any_status, ST_NONFINITE); }
+      continue;
+    }
+    float Tb = sm.tb, L = sm.L, G = sm.G;
+
+    Accum A;
+    A.pn2 = A.pn = 0;
+    A.pL = A.pL2 = A.pG = 0.f;
+    A.dwell = A.nflush = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) A.prop[k] = A.acc[k] = 0;
+    A.my = (lane < ACC_WORDS) ? P.acc[static_cast<size_t>(c) * ACC_WORDS + lane] : 0.0;
+
+    const float3 cS = f3(S.c[0], S.c[1], S.c[2]);
+    unsigned long long done = 0;
+    bool aborted = false;
+    for (unsigned long long s0 = 0; s0 < P.n_steps; s0 += 32) {
+      if ((s0 & 1023ull) == 0 && P.abort_flag != nullptr && *P.abort_flag) { aborted = true; break; }
+      // ---- lane-parallel random numbers of steps step0+s0 .. +31 ----
+      const unsigned long long tl = step0 + s0 + lane;
+      const uint4 ra = philox4x32_10(make_uint4(static_cast<uint32_t>(tl), static_cast<uint32_t>(tl >> 32),
+                                                static_cast<uint32_t>(c), PUR_STEP_A), key0, key1);
+      const uint4 rb = philox4x32_10(make_uint4(static_cast<uint32_t>(tl), static_cast<uint32_t>(tl >> 32),
+                                                static_cast<uint32_t>(c), PUR_STEP_B), key0, key1);
+      const uint32_t um = ra.x >> 9;
+      const uint32_t type = um < R.thr_within ? 0u : (um < R.thr_birth ? 2u : 3u);
+      const uint32_t w0l = (ra.y >> 9) | (type << 24);
+      const float logul = logf(u01(ra.z));
+      float q0, q1, q2, q3, q4, q5;
+      {
+        const float ub0 = u01(rb.x), ub1 = u01(rb.y), ub2 = u01(rb.z), ub3 = u01(rb.w);
+        if (type == 0u) {
+          // Gaussian triple (Box-Muller) and vMF end-move cosine / azimuth
+          float s1, c1, s2, c2;
+          const float r1 = sqrtf(-2.0f * logf(ub0));
+          sincospif(2.0f * ub1, &s1, &c1);
+          const float r2 = sqrtf(-2.0f * logf(ub2));
+          sincospif(2.0f * ub3, &s2, &c2);
+          q0 = r1 * c1;
+          q1 = r1 * s1;
+          q2 = r2 * c2;
+          q3 = 1.0f + logf(fmaf(1.0f - ub0, S.exp_m2ke, ub0)) / S.kappa_end;
+          q4 = c1;
+          q5 = s1;
+        } else {
+          // birth: u for cos s, sinh t / cosh t of the logistic t, azimuth
+          const float et = ub1 / (1.0f - ub1);
+          const float iet = (1.0f - ub1) / ub1;
+          float s3, c3;
+          sincospif(2.0f * ub2, &s3, &c3);
+          q0 = ub0;
+          q1 = 0.5f * (et - iet);
+          q2 = 0.5f * (et + iet);
+          q3 = c3;
+          q4 = s3;
+          q5 = 0.0f;
+        }
+      }
+      const int cnt = static_cast<int>(min(32ull, P.n_steps - s0));
+      for (int i = 0; i < cnt; ++i) {
+        const uint32_t w0 = __shfl_sync(kFull, w0l, i);
+        const float logu = __shfl_sync(kFull, logul, i);
+        const float p0 = __shfl_sync(kFull, q0, i);
+        const float p1 = __shfl_sync(kFull, q1, i);
+        const float p2 = __shfl_sync(kFull, q2, i);
+        const float p3 = __shfl_sync(kFull, q3, i);
+        const float p4 = __shfl_sync(kFull, q4, i);
+        const float p5 = __shfl_sync(kFull, q5, i);
+        const uint32_t mtype = w0 >> 24;
+        const uint32_t v23 = w0 & 0x7fffffu;
+        const unsigned long long t = step0 + s0 + i;
+
+        int move;
+        bool proposed = true;
+        int n_new = n, wlo = 0, nc = 0, olo = 0, onc = 0, jj = -1, kk = -1;
+        float3 fnew = f3(0.f, 0.f, 0.f);
+        float extra = 0.f;
+        float3 gx_mala = f3(0.f, 0.f, 0.f);
+        if (mtype == 0u) {
+          const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 1)) >> 23);
+          jj = j;
+          if (j == n - 1) {
+            move = MV_END;
+            float3 nu = w.pos(j) - cS;
+            nu = rsqrtf(dot(nu, nu)) * nu;
+            float3 e1, e2;
+            onb(nu, e1, e2);
+            const float wv = p3;
+            const float sw = sqrtf(fmaxf(0.f, 1.0f - wv * wv));
+            const float3 nn = wv * nu + sw * (p4 * e1 + p5 * e2);
+            fnew = cS + S.R * nn;
+            wlo = n - 2; nc = 2; olo = n - 2; onc = 2;
+          } else {
+            move = MV_INTERIOR;
+            const float3 fj = w.pos(j);
+            if (R.within == 1) {
+              gx_mala = grad_vertex(M, S, zoff, [&](int k) { return w.pos(k); }, n, j);
+              const float h = 0.5f * R.mala_eps * R.mala_eps;
+              fnew = fj + h * gx_mala + R.mala_eps * f3(p0, p1, p2);
+            } else {
+              fnew = fj + R.sigma * f3(p0, p1, p2);
+            }
+            wlo = j - 1; nc = 3; olo = j - 1; onc = 3;
+          }
+        } else if (mtype == 2u) {
+          move = MV_BIRTH;
+          if (n >= cap) {
+            proposed = false;
+          } else {
+            float total;
+            const float ui = __fmaf_rn(static_cast<float>(v23), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
+            const int k = select_segment(w, n - 1, ui, total, lane);
+            kk = k;
+            const float3 Af = w.pos(k), Bf = w.pos(k + 1);
+            const float3 r = Bf - Af;
+            const float ell = sqrtf(dot(r, r));
+            const float gamma = 0.5f * ell;
+            const float3 rh = (1.0f / ell) * r;
+            float3 xi, ze;
+            onb(rh, xi, ze);
+            const float beta = insertion_beta(M, R, zoff, Af, Bf, gamma);
+            float cs = -1.0f - log1pf(p0 * expm1f(-2.0f * beta)) / beta;
+            cs = fminf(fmaxf(cs, -1.0f), 1.0f);
+            const float sn = sqrtf(fmaxf(0.f, (1.0f - cs) * (1.0f + cs)));
+            const float sc = gamma / (p2 - cs);
+            fnew = 0.5f * (Af + Bf) + sc * (p1 * rh + sn * (p3 * xi + p4 * ze));
+            const float tbk = w.tb[k];
+            extra = R.log_pd - logf(static_cast<float>(n - 1)) - R.log_pb - logf(tbk / total) -
+                    log_insert_density(M, R, zoff, Af, Bf, fnew);
+            n_new = n + 1;
+            wlo = k; nc = 3; olo = k; onc = 2;
+          }
+        } else {
+          move = MV_DEATH;
+          if (n <= 2) {
+            proposed = false;
+          } else {
+            const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 2)) >> 23);
+            jj = j;
+            n_new = n - 1;
+            wlo = j - 1; nc = 2; olo = j - 1; onc = 3;
+          }
+        }
+
+        bool accept = false;
+        float dlp = 0.f, dtb = 0.f;
+        float nvt = 0.f, ngt = 0.f, nseg = 0.f, ntb = 0.f, nlen = 0.f;
+        float ogt = 0.f, olen = 0.f;
+        if (proposed) {
+          // new-path vertex index -> position
+          auto newpos = [&](int idx) -> float3 {
+            int o = idx;
+            bool isnew = false;
+            if (move == MV_BIRTH) {
+              isnew = (idx == kk + 1);
+              o = (idx > kk + 1) ? idx - 1 : idx;
+            } else if (move == MV_DEATH) {
+              o = (idx >= jj) ? idx + 1 : idx;
+            } else {
+              isnew = (idx == jj);
+            }
+            o = min(max(o, 0), n - 1);
+            const float3 q = w.pos(o);
+            return isnew ? fnew : q;
+          };
+          float ovt = 0.f, oseg = 0.f, otb = 0.f;
+          if (lane < nc) {
+            const int v = wlo + lane;
+            const float3 Pc = newpos(v);
+            const float3 Pp = (v >= 1) ? newpos(v - 1) : Pc;
+            const float3 Pn = (v <= n_new - 2) ? newpos(v + 1) : Pc;
+            nvt = vertex_term(M, S, zoff, Pp, Pc, Pn, v, n_new, ngt);
+            if (lane < nc - 1) {
+              const SegOut so = segment_term(M, S, zoff, Pc, Pn, v <= n_new - 3);
+              nseg = so.seg;
+              ntb = so.tb;
+              nlen = so.len;
+            }
+          }
+          if (lane < onc) {
+            const int o = olo + lane;
+            ovt = w.vt[o];
+            ogt = w.gt[o];
+            if (lane < onc - 1) {
+              oseg = w.seg[o];
+              otb = w.tb[o];
+              olen = w.len[o];
+            }
+          }
+          dlp = (nvt + nseg) - (ovt + oseg);
+          dlp += __shfl_xor_sync(kFull, dlp, 1);
+          dlp += __shfl_xor_sync(kFull, dlp, 2);
+          dlp = __shfl_sync(kFull, dlp, 0);
+          dtb = ntb - otb;
+          dtb += __shfl_xor_sync(kFull, dtb, 1);
+          dtb += __shfl_xor_sync(kFull, dtb, 2);
+          dtb = __shfl_sync(kFull, dtb, 0);
+          if (move == MV_DEATH) {
+            const float tb_new = __shfl_sync(kFull, ntb, 0);
+            const float Tb_red = Tb + dtb;
+            extra = -R.log_pd + logf(static_cast<float>(n - 2)) + R.log_pb + logf(tb_new / Tb_red) +
+                    log_insert_density(M, R, zoff, w.pos(jj - 1), w.pos(jj + 1), w.pos(jj));
+          }
+          if (move == MV_INTERIOR && R.within == 1 && isfinite(dlp)) {
+            const float3 gy = grad_vertex(M, S, zoff, newpos, n, jj);
+            const float h = 0.5f * R.mala_eps * R.mala_eps;
+            const float3 fj = w.pos(jj);
+            const float3 dfw = fnew - fj - h * gx_mala;
+            const float3 dbw = fj - fnew - h * gy;
+            extra = (dot(dfw, dfw) - dot(dbw, dbw)) / (2.0f * R.mala_eps * R.mala_eps);
+          }
+          const float logA = dlp + extra;
+          accept = logu < logA;
+        }
+        A.prop[move]++;
+        if (accept) {
+          A.acc[move]++;
+          add_dwell(A, n, L, G);
+          float dlen = nlen - olen;
+          float dg = ngt - ogt;
+          dlen += __shfl_xor_sync(kFull, dlen, 1);
+          dlen += __shfl_xor_sync(kFull, dlen, 2);
+          dlen = __shfl_sync(kFull, dlen, 0);
+          dg += __shfl_xor_sync(kFull, dg, 1);
+          dg += __shfl_xor_sync(kFull, dg, 2);
+          dg = __shfl_sync(kFull, dg, 0);
+          if (move == MV_BIRTH) {
+            shift_right(w, kk + 1, n, n - 1, lane);
+          } else if (move == MV_DEATH) {
+            shift_left(w, jj + 1, n, n - 1, lane);
+          }
+          if (lane < nc) {
+            const int v = wlo + lane;
+            w.vt[v] = nvt;
+            w.gt[v] = ngt;
+            if (lane < nc - 1) {
+              w.seg[v] = nseg;
+              w.tb[v] = ntb;
+              w.len[v] = nlen;
+            }
+          }
+          if (lane == 0 && move != MV_DEATH) {
+            const int at = (move == MV_BIRTH) ? kk + 1 : jj;
+            w.x[at] = fnew.x;
+            w.y[at] = fnew.y;
+            w.z[at] = fnew.z;
+          }
+          __syncwarp();
+          n = n_new;
+          Tb += dtb;
+          L += dlen;
+          G += dg;
+          if (A.nflush >= kFlushAccepts) flush64(A, lane);
+        }
+        if (t >= R.burn_in) A.dwell++;
+        if (((t + 1) & (kRefreshSteps - 1)) == 0) {
+          const Sums s2 = path_sums(w, n, lane);
+          Tb = s2.tb;
+          L = s2.L;
+          G = s2.G;
+        }
+      }
+      done += cnt;
+    }
+    add_dwell(A, n, L, G);
+    flush64(A, lane);
+    // recorded states, proposal and acceptance counts
+    const unsigned long long t_end = step0 + done;
+    const unsigned long long first = step0 > R.burn_in ? step0 : R.burn_in;
+    const double nrec = t_end > first ? static_cast<double>(t_end - first) : 0.0;
+    double extra_w = 0.0;
+    if (lane == ACC_NREC) extra_w = nrec;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (lane == ACC_PROP + k) extra_w = static_cast<double>(A.prop[k]);
+      if (lane == ACC_ACC + k) extra_w = static_cast<double>(A.acc[k]);
+    }
+    A.my += extra_w;
+    if (lane < ACC_WORDS) P.acc[static_cast<size_t>(c) * ACC_WORDS + lane] = A.my;
+    for (int i = lane; i < n; i += 32) { gx[i] = w.x[i]; gy[i] = w.y[i]; gz[i] = w.z[i]; }
+    if (lane == 0) {
+      P.n[c] = n;
+      P.step[c] = t_end;
+      if (aborted) { P.status[c] |= ST_ABORTED; atomicOr(P.any_status, ST_ABORTED); }
+    }
+    __syncwarp();
+  }
+}
+
+// Initial paths (one thread per chain).
+__global__ void init_kernel(const InitParams p) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.total) return;
+  const DPair S = p.pairs[p.chain_pair[c]];
+  float* gx = p.xyz + p.chain_base[c];
+  float* gy = gx + S.cap;
+  float* gz = gy + S.cap;
+  int n;
+  if (p.init_kind == PMC_INIT_USER) {
+    n = p.user_n[c];
+    const size_t st = static_cast<size_t>(p.user_stride);
+    const float* ux = p.user_xyz + static_cast<size_t>(c) * 3 * st;
+    if (n < 2 || n > S.cap || n > p.user_stride) {
+      p.status[c] = ST_BAD_N;
+      n = 2;
+    }
+    for (int i = 0; i < n; ++i) {
+      gx[i] = ux[i] - S.src[0];
+      gy[i] = ux[st + i] - S.src[1];
+      gz[i] = ux[2 * st + i] - S.src[2];
+    }
+  } else {
+    const int k = (p.init_kind == PMC_INIT_DIRECT) ? 0 : p.init_k;
+    n = k + 2;
+    if (n > S.cap) {
+      p.status[c] = ST_BAD_N;
+      n = 2;
+    }
+    const uint32_t k0 = static_cast<uint32_t>(p.R.seed), k1 = static_cast<uint32_t>(p.R.seed >> 32);
+    gx[0] = gy[0] = gz[0] = 0.f;
+    const int kk = n - 2;
+    for (int i = 1; i <= kk; ++i) {
+      const float fr = static_cast<float>(i) / static_cast<float>(kk + 1);
+      const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(i), 0u, static_cast<uint32_t>(c), PUR_INIT),
+                                    k0, k1);
+      float s1, c1, s2, c2;
+      const float r1 = sqrtf(-2.0f * logf(u01(r.x)));
+      sincospif(2.0f * u01(r.y), &s1, &c1);
+      const float r2 = sqrtf(-2.0f * logf(u01(r.z)));
+      sincospif(2.0f * u01(r.w), &s2, &c2);
+      gx[i] = fr * S.e_near[0] + p.jitter * r1 * c1;
+      gy[i] = fr * S.e_near[1] + p.jitter * r1 * s1;
+      gz[i] = fr * S.e_near[2] + p.jitter * r2 * c2;
+    }
+    gx[kk + 1] = S.e_near[0];
+    gy[kk + 1] = S.e_near[1];
+    gz[kk + 1] = S.e_near[2];
+  }
+  p.n[c] = n;
+  p.step[c] = 0ull;
+  for (int k = 0; k < ACC_WORDS; ++k) p.acc[static_cast<size_t>(c) * ACC_WORDS + k] = 0.0;
+}
+
+}  // namespace
+
+size_t chain_smem_bytes(int smem_cap, int warps_per_block) {
+  return static_cast<size_t>(warps_per_block) * 8u * static_cast<size_t>(smem_cap) * sizeof(float);
+}
+
+cudaError_t chain_kernel_attributes(int smem_bytes) {
+  return cudaFuncSetAttribute(chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+}
+
+cudaError_t chain_occupancy(int warps_per_block, int smem_cap, int* blocks_per_sm) {
+  const size_t sm = chain_smem_bytes(smem_cap, warps_per_block);
+  cudaError_t e = chain_kernel_attributes(static_cast<int>(sm));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel, warps_per_block * 32, sm);
+}
+
+cudaError_t launch_chain(const ChainParams& p, int grid, int warps_per_block, cudaStream_t s) {
+  const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block);
+  chain_kernel<<<grid, warps_per_block * 32, sm, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const InitParams& p, cudaStream_t s) {
+  if (p.total == 0) return cudaSuccess;
+  init_kernel<<<(p.total + 127) / 128, 128, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace pmc

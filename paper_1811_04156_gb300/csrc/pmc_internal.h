@@ -1,0 +1,115 @@
+// Host-side internals shared by the CUDA translation units of libpathmc.
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pathmc.h"
+#include "pmc_device.cuh"
+
+namespace pmc {
+
+// Accumulator word indices (per chain, FP64), order documented in pathmc.h.
+enum AccWord {
+  ACC_NREC = 0,
+  ACC_NDIRECT = 1,
+  ACC_SUMN = 2,
+  ACC_SUML = 3,
+  ACC_SUML2 = 4,
+  ACC_SUMG = 5,
+  ACC_BRIDGE = 6,
+  ACC_NBRIDGE = 7,
+  ACC_PROP = 8,
+  ACC_ACC = 12,
+  ACC_WORDS = 16
+};
+static_assert(ACC_WORDS == PMC_ACC_WORDS, "accumulator layout");
+
+// Status bits of a chain.
+enum StatusBits { ST_NONFINITE = 1, ST_ABORTED = 2, ST_BAD_N = 4 };
+
+// Random-number purposes (fourth Philox counter word).
+enum Purpose : uint32_t { PUR_STEP_A = 0, PUR_STEP_B = 1, PUR_INIT = 2, PUR_QREF = 3, PUR_TRACE = 4 };
+
+struct ChainParams {
+  DMedium M;
+  DRun R;
+  const DPair* pairs;
+  const int* chain_pair;        // [total]
+  const long long* chain_base;  // [total] float offset of x[cap], y[cap], z[cap]
+  const int* order;             // processing order of chains (grouped by vertex-cap class)
+  float* xyz;
+  int* n;
+  unsigned long long* step;
+  double* acc;                  // [total][ACC_WORDS]
+  int* status;                  // [total]
+  int* any_status;              // OR of all status words
+  unsigned int* queue;          // work counter of this launch
+  const volatile int* abort_flag;
+  int chain_lo, chain_hi;       // chains [lo, hi) of this launch
+  unsigned long long n_steps;
+  int smem_cap;                 // vertex capacity of one warp's shared arrays
+};
+
+// Kernel launchers (pmc_chain.cu)
+cudaError_t launch_chain(const ChainParams& p, int grid, int warps_per_block, cudaStream_t s);
+size_t chain_smem_bytes(int smem_cap, int warps_per_block);
+cudaError_t chain_kernel_attributes(int smem_bytes);
+cudaError_t chain_occupancy(int warps_per_block, int smem_cap, int* blocks_per_sm);
+
+struct InitParams {
+  DRun R;
+  const DPair* pairs;
+  const int* chain_pair;
+  const long long* chain_base;
+  float* xyz;
+  int* n;
+  unsigned long long* step;
+  double* acc;
+  int* status;
+  int total;
+  int init_kind, init_k;
+  float jitter;
+  const float* user_xyz;        // device copy, [total][3][stride] absolute
+  const int* user_n;
+  int user_stride;
+};
+cudaError_t launch_init(const InitParams& p, cudaStream_t s);
+
+// pmc_kernels.cu
+cudaError_t launch_logp(const DMedium& M, const DPair& S, const float* xyz, const int* n, int batch, int cap,
+                        float* out_logp, float* out_grad, cudaStream_t s);
+cudaError_t launch_score(const DMedium& M, const DPair& S, const float* xyz, const int* n, int batch, int cap,
+                         float* out, int n_theta, const double* ls, const double* la, cudaStream_t s);
+cudaError_t launch_z2(const DMedium& M, const DPair* pairs, int n_pairs, int n_v, int n_phi, double* out,
+                      cudaStream_t s);
+
+struct EstParams {
+  const double* acc;            // [total][ACC_WORDS]
+  const DPair* pairs;
+  const double* z2;             // [n_pairs]
+  const double* bridge_q;       // [n_pairs][2] sums from reference draws (may be null)
+  int n_pairs;
+  double lambda_s, lambda_a;    // homogeneous, for the score
+  int homogeneous;
+  double* out;                  // [n_pairs][EST_WORDS]
+};
+enum EstWord {
+  EST_I = 0, EST_SE, EST_REL, EST_PI, EST_Z2, EST_RHAT,
+  EST_ACC0, EST_ACC1, EST_ACC2, EST_ACC3,
+  EST_PROP0, EST_PROP1, EST_PROP2, EST_PROP3,
+  EST_MEAN_N, EST_MEAN_L, EST_NSAMP, EST_ESS, EST_BRIDGE_I, EST_BRIDGE_SE,
+  EST_GRAD0, EST_GRAD1, EST_GRAD2, EST_GRADSE0, EST_GRADSE1, EST_GRADSE2,
+  EST_WORDS
+};
+cudaError_t launch_estimator(const EstParams& p, cudaStream_t s);
+
+cudaError_t launch_trace(const DMedium& M, const DPair& S, unsigned long long seed,
+                         unsigned long long photon0, unsigned long long n_photons, float r_reject,
+                         int max_scatter, double* out5, int n_sm, cudaStream_t s);
+
+}  // namespace pmc

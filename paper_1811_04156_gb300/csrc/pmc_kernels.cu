@@ -1,0 +1,480 @@
+// Density, adjoint, score, normalisation, estimator and forward-tracer kernels
+// (Collin, arXiv:1811.04156).
+#include "pmc_internal.h"
+
+namespace pmc {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Batch accessor: SoA [3][batch][cap] absolute positions -> source-relative.
+struct BatchPos {
+  const float* xyz;
+  size_t plane, off;
+  float sx, sy, sz;
+  __device__ float3 operator()(int i) const {
+    return f3(xyz[off + i] - sx, xyz[plane + off + i] - sy, xyz[2 * plane + off + i] - sz);
+  }
+};
+
+// log p of each path (one warp per path), and optionally d log p / d xyz.
+__global__ void logp_kernel(const DMedium M, const DPair S, const float* __restrict__ xyz,
+                            const int* __restrict__ nn, int batch, int cap, float* __restrict__ out_logp,
+                            float* __restrict__ out_grad) {
+  const int lane = threadIdx.x & 31;
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (b >= batch) return;
+  const int n = nn[b];
+  const float zoff = S.src[2];
+  BatchPos pos{xyz, static_cast<size_t>(batch) * cap, static_cast<size_t>(b) * cap, S.src[0], S.src[1], S.src[2]};
+  float lp = 0.f;
+  if (n >= 2 && n <= cap) {
+    for (int i = lane; i < n; i += 32) {
+      const float3 P = pos(i);
+      const float3 Pp = (i >= 1) ? pos(i - 1) : P;
+      const float3 Pn = (i <= n - 2) ? pos(i + 1) : P;
+      float g;
+      lp += vertex_term(M, S, zoff, Pp, P, Pn, i, n, g);
+      if (i <= n - 2) lp += segment_term(M, S, zoff, P, Pn, i <= n - 3).seg;
+    }
+    lp = warp_sum(lp);
+  } else {
+    lp = __int_as_float(0x7fc00000);  // NaN marks an invalid vertex count
+  }
+  if (lane == 0 && out_logp) out_logp[b] = lp;
+  if (out_grad) {
+    const size_t plane = static_cast<size_t>(batch) * cap;
+    const size_t off = static_cast<size_t>(b) * cap;
+    const bool ok = n >= 2 && n <= cap && isfinite(lp);
+    for (int i = lane; i < cap; i += 32) {
+      float3 g = f3(0.f, 0.f, 0.f);
+      if (ok && i < n) g = grad_vertex(M, S, zoff, pos, n, i);
+      out_grad[off + i] = g.x;
+      out_grad[plane + off + i] = g.y;
+      out_grad[2 * plane + off + i] = g.z;
+    }
+  }
+}
+
+// d log p / d theta per path.  Homogeneous theta = (lambda_s, lambda_a, g):
+//   (L b^2 - (n-2) b, L a^2, sum_k d log sigma/d g);  layered theta =
+// (lambda_s[l], lambda_a[l]): (len_l b_l^2 - n_l b_l, len_l a_l^2), with len_l
+// the path length inside layer l and n_l its scattering vertices.
+// `out` must be zeroed for layered media (per-layer terms are added atomically).
+__global__ void score_kernel(const DMedium M, const DPair S, const float* __restrict__ xyz,
+                             const int* __restrict__ nn, int batch, int cap, float* __restrict__ out,
+                             int n_theta) {
+  const int lane = threadIdx.x & 31;
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (b >= batch) return;
+  const int n = nn[b];
+  if (n < 2 || n > cap) return;
+  const float zoff = S.src[2];
+  BatchPos pos{xyz, static_cast<size_t>(batch) * cap, static_cast<size_t>(b) * cap, S.src[0], S.src[1], S.src[2]};
+  float* o = out + static_cast<size_t>(b) * n_theta;
+  if (M.kind == 0) {
+    float L = 0.f, G = 0.f;
+    for (int i = lane; i < n; i += 32) {
+      const float3 P = pos(i);
+      if (i <= n - 2) {
+        const float3 r = pos(i + 1) - P;
+        L += sqrtf(dot(r, r));
+      }
+      if (i >= 1 && i <= n - 2) {
+        const float3 a0 = P - pos(i - 1), b0 = pos(i + 1) - P;
+        float g;
+        phase_term(M, rsqrtf(dot(a0, a0)) * a0, rsqrtf(dot(b0, b0)) * b0, g);
+        G += g;
+      }
+    }
+    L = warp_sum(L);
+    G = warp_sum(G);
+    if (lane == 0) {
+      o[0] = L * M.b * M.b - static_cast<float>(n - 2) * M.b;
+      o[1] = L * M.a * M.a;
+      o[2] = G;
+    }
+    return;
+  }
+  const int NL = M.n_layers;
+  for (int i = lane; i < n; i += 32) {
+    const float3 P = pos(i);
+    if (i >= 1 && i <= n - 2) {
+      const int l = layer_of(M, P.z + zoff);
+      atomicAdd(o + l, -__ldg(M.lb + l));
+    }
+    if (i <= n - 2) {
+      const float3 Q = pos(i + 1);
+      const float3 r = Q - P;
+      const float ell = sqrtf(dot(r, r));
+      const float zP = P.z + zoff, zQ = Q.z + zoff;
+      const int lP = layer_of(M, zP), lQ = layer_of(M, zQ);
+      const int l0 = min(lP, lQ), l1 = max(lP, lQ);
+      const float zlo = fminf(zP, zQ), zhi = fmaxf(zP, zQ);
+      for (int l = l0; l <= l1; ++l) {
+        float frac = 1.0f;
+        if (l0 != l1) {
+          const float lo = (l == l0) ? zlo : M.z0 + l * M.dz;
+          const float hi = (l == l1) ? zhi : M.z0 + (l + 1) * M.dz;
+          frac = fmaxf(hi - lo, 0.f) / (zhi - zlo);
+        }
+        const float len = ell * frac;
+        const float bl = __ldg(M.lb + l), al = __ldg(M.la + l);
+        atomicAdd(o + l, len * bl * bl);
+        atomicAdd(o + NL + l, len * al * al);
+      }
+    }
+  }
+}
+
+// Block-wide sum of K doubles held by every thread (blockDim.x == 256).
+template <int K>
+__device__ void block_sum(double (&v)[K], double* sh) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if ((t & 31) == 0) sh[k * 8 + (t >> 5)] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = 0.0;
+    for (int i = 0; i < 8; ++i) x += sh[k * 8 + i];
+    v[k] = x;
+  }
+  __syncthreads();
+}
+
+// Direct-sector integral Z2 = int over the sensor seen from the source of
+// eps(omega) exp(-tau) rho dOmega, with theta = theta_max (1 - v^2) to remove
+// the square-root behaviour at the rim; FP32 integrand, FP64 sums.
+__global__ void __launch_bounds__(256) z2_kernel(const DMedium M, const DPair* __restrict__ pairs, int n_v,
+                                                 int n_phi, double* __restrict__ out) {
+  __shared__ double sh[8 * 1];
+  const DPair S = pairs[blockIdx.x];
+  const float3 c = f3(S.c[0], S.c[1], S.c[2]);
+  const float D = sqrtf(dot(c, c));
+  const float3 ax = (1.0f / D) * c;
+  float3 e1, e2;
+  onb(ax, e1, e2);
+  const float R = S.R;
+  const float thmax = asinf(R / D);
+  double acc = 0.0;
+  const int total = n_v * n_phi;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int iv = idx / n_phi, ip = idx % n_phi;
+    const float v = (iv + 0.5f) / n_v;
+    const float th = thmax * (1.0f - v * v);
+    const float jac = 2.0f * thmax * v / n_v;
+    float st, ct, sp, cp;
+    sincosf(th, &st, &ct);
+    sincospif(2.0f * (ip + 0.5f) / n_phi, &sp, &cp);
+    const float disc = fmaxf((R - D * st) * (R + D * st), 0.0f);
+    const float r = D * ct - sqrtf(disc);
+    const float3 om = ct * ax + st * (cp * e1 + sp * e2);
+    const float3 h = r * om;
+    float ta, tb;
+    seg_tau(M, S.src[2], h.z + S.src[2], r, ta, tb);
+    float lv = emission_term(S, om) - ta - tb;
+    if (S.rho != 0) {
+      const float3 nu = (1.0f / R) * (h - c);
+      const float x = dot(nu, f3(S.rho_hat[0], S.rho_hat[1], S.rho_hat[2]));
+      lv += fmaf(3.0f, x, -1.0f) - logf(coshf(fmaf(2.0f, x, 0.7f)));
+    }
+    acc += static_cast<double>(expf(lv) * st * jac) * (2.0 * 3.14159265358979323846 / n_phi);
+  }
+  double vv[1] = {acc};
+  block_sum<1>(vv, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = vv[0];
+}
+
+// Per-pair reduction of the chain accumulators (one block per pair).
+__global__ void __launch_bounds__(256) estimator_kernel(const EstParams p) {
+  __shared__ double sh[8 * 24];
+  const int pi = blockIdx.x;
+  const DPair S = p.pairs[pi];
+  const int c0 = S.chain0, nc = S.n_chains;
+  // pass 1: totals
+  double v[24];
+#pragma unroll
+  for (int k = 0; k < 24; ++k) v[k] = 0.0;
+  for (int c = c0 + threadIdx.x; c < c0 + nc; c += blockDim.x) {
+    const double* a = p.acc + static_cast<size_t>(c) * ACC_WORDS;
+#pragma unroll
+    for (int k = 0; k < ACC_WORDS; ++k) v[k] += a[k];
+    const double N = a[ACC_NREC];
+    if (N > 1.0) {
+      const double m = a[ACC_SUML] / N;
+      const double var = fmax(a[ACC_SUML2] / N - m * m, 0.0) * N / (N - 1.0);
+      v[16] += m;
+      v[17] += m * m;
+      v[18] += var;
+      v[19] += 1.0;
+    }
+  }
+  block_sum<24>(v, sh);
+  const double Ntot = v[ACC_NREC];
+  const double pi_hat = Ntot > 0 ? v[ACC_NDIRECT] / Ntot : 0.0;
+  const double bs = 1.0 / p.lambda_s, ba = 1.0 / p.lambda_a;
+  // mean scores
+  double sbar[3] = {0, 0, 0};
+  if (Ntot > 0) {
+    sbar[0] = (v[ACC_SUML] * bs * bs - (v[ACC_SUMN] - 2.0 * Ntot) * bs) / Ntot;
+    sbar[1] = v[ACC_SUML] * ba * ba / Ntot;
+    sbar[2] = v[ACC_SUMG] / Ntot;
+  }
+  // pass 2: across-chain spreads of pi(n=2) and of the score means
+  double u[4] = {0, 0, 0, 0};
+  for (int c = c0 + threadIdx.x; c < c0 + nc; c += blockDim.x) {
+    const double* a = p.acc + static_cast<size_t>(c) * ACC_WORDS;
+    const double N = a[ACC_NREC];
+    if (N <= 0) continue;
+    const double w = N / Ntot;
+    const double f = a[ACC_NDIRECT] / N;
+    u[0] += w * w * (f - pi_hat) * (f - pi_hat);
+    const double s0 = (a[ACC_SUML] * bs * bs - (a[ACC_SUMN] - 2.0 * N) * bs) / N;
+    const double s1 = a[ACC_SUML] * ba * ba / N;
+    const double s2 = a[ACC_SUMG] / N;
+    u[1] += w * w * (s0 - sbar[0]) * (s0 - sbar[0]);
+    u[2] += w * w * (s1 - sbar[1]) * (s1 - sbar[1]);
+    u[3] += w * w * (s2 - sbar[2]) * (s2 - sbar[2]);
+  }
+  block_sum<4>(u, sh);
+  if (threadIdx.x != 0) return;
+  double* o = p.out + static_cast<size_t>(pi) * EST_WORDS;
+  const double C = static_cast<double>(nc);
+  const double corr = C > 1 ? C / (C - 1.0) : 1.0;
+  const double var_pi = u[0] * corr;
+  const double z2 = p.z2[pi];
+  const double I = pi_hat > 0 ? z2 / pi_hat : __longlong_as_double(0x7ff8000000000000ll);
+  const double se = pi_hat > 0 ? I * sqrt(var_pi) / pi_hat : I;
+  o[EST_I] = I;
+  o[EST_SE] = se;
+  o[EST_REL] = se / I;
+  o[EST_PI] = pi_hat;
+  o[EST_Z2] = z2;
+  // R-hat over chains on the path length
+  const double m_ch = v[19];
+  double rhat = __longlong_as_double(0x7ff8000000000000ll);
+  if (m_ch > 1) {
+    const double W = v[18] / m_ch;
+    const double mbar = v[16] / m_ch;
+    const double B_over_n = (v[17] / m_ch - mbar * mbar) * m_ch / (m_ch - 1.0);
+    const double nper = Ntot / m_ch;
+    if (W > 0) rhat = sqrt(((nper - 1.0) / nper * W + B_over_n) / W);
+  }
+  o[EST_RHAT] = rhat;
+  for (int k = 0; k < 4; ++k) {
+    const double pr = v[ACC_PROP + k];
+    o[EST_ACC0 + k] = pr > 0 ? v[ACC_ACC + k] / pr : 0.0;
+    o[EST_PROP0 + k] = pr;
+  }
+  o[EST_MEAN_N] = Ntot > 0 ? v[ACC_SUMN] / Ntot : 0.0;
+  o[EST_MEAN_L] = Ntot > 0 ? v[ACC_SUML] / Ntot : 0.0;
+  o[EST_NSAMP] = Ntot;
+  o[EST_ESS] = var_pi > 0 ? pi_hat * (1.0 - pi_hat) / var_pi : 0.0;
+  double bI = __longlong_as_double(0x7ff8000000000000ll), bse = bI;
+  if (p.bridge_q != nullptr && v[ACC_NBRIDGE] > 0) {
+    const double num = p.bridge_q[2 * pi] / fmax(p.bridge_q[2 * pi + 1], 1.0);
+    const double den = v[ACC_BRIDGE] / v[ACC_NBRIDGE];
+    bI = num / den;
+  }
+  o[EST_BRIDGE_I] = bI;
+  o[EST_BRIDGE_SE] = bse;
+  for (int k = 0; k < 3; ++k) {
+    const double vs = u[1 + k] * corr;
+    o[EST_GRAD0 + k] = I * sbar[k];
+    o[EST_GRADSE0 + k] = sqrt(I * I * vs + sbar[k] * sbar[k] * se * se);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward tracer (appendix, Algorithm 1): one thread per photon.
+// ---------------------------------------------------------------------------
+__device__ float free_path(const DMedium& M, float z_abs, float nz, float tau) {
+  if (M.kind == 0) return tau / M.b;
+  float dL = 0.f;
+  float z = z_abs;
+  int l = layer_of(M, z);
+  for (int guard = 0; guard < 1 << 16; ++guard) {
+    const float b = __ldg(M.lb + l);
+    float dist = __int_as_float(0x7f800000);
+    int next = l;
+    if (nz > 0.f && l < M.n_layers - 1) {
+      dist = (M.z0 + (l + 1) * M.dz - z) / nz;
+      next = l + 1;
+    } else if (nz < 0.f && l > 0) {
+      dist = (M.z0 + l * M.dz - z) / nz;
+      next = l - 1;
+    }
+    dist = fmaxf(dist, 0.f);
+    if (tau <= b * dist) return dL + tau / b;
+    tau -= b * dist;
+    dL += dist;
+    z += dist * nz;
+    l = next;
+  }
+  return dL;
+}
+
+__device__ float ray_sphere(float3 x, float3 nh, float3 c, float R2) {
+  const float3 w = x - c;
+  const float b = dot(w, nh);
+  const float cc = dot(w, w) - R2;
+  const float disc = b * b - cc;
+  if (disc < 0.f) return __int_as_float(0x7f800000);
+  const float s1 = -b - sqrtf(disc);
+  return s1 > 0.f ? s1 : __int_as_float(0x7f800000);
+}
+
+__device__ float sample_cos(const DMedium& M, float u, float umix) {
+  if (M.f_sl > 0.f && umix < M.f_sl) {
+    const float v = powf(u, 1.0f / (M.sl_alpha + 1.0f));
+    return 2.0f * v - 1.0f;
+  }
+  const float g = M.g;
+  if (fabsf(g) < 1e-6f) return 2.0f * u - 1.0f;
+  const float q = (1.0f - g * g) / (1.0f - g + 2.0f * g * u);
+  return fminf(fmaxf((1.0f + g * g - q * q) / (2.0f * g), -1.0f), 1.0f);
+}
+
+__global__ void __launch_bounds__(256) trace_kernel(const DMedium M, const DPair S, unsigned long long seed,
+                                                    unsigned long long photon0, unsigned long long n_photons,
+                                                    float r_reject, int max_scatter, double* __restrict__ out5) {
+  __shared__ double sh[8 * 5];
+  const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  const float3 c = f3(S.c[0], S.c[1], S.c[2]);
+  double v[5] = {0, 0, 0, 0, 0};
+  const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+  for (unsigned long long q = blockIdx.x * blockDim.x + threadIdx.x; q < n_photons; q += stride) {
+    const unsigned long long ph = photon0 + q;
+    const uint32_t plo = static_cast<uint32_t>(ph), phi = static_cast<uint32_t>(ph >> 32);
+    uint4 r = philox4x32_10(make_uint4(plo, phi, 0u, PUR_TRACE), k0, k1);
+    float3 x = f3(0.f, 0.f, 0.f);
+    float3 nh;
+    {
+      float sp, cp;
+      sincospif(2.0f * u01(r.y), &sp, &cp);
+      if (S.emission != 0) {
+        const float u0 = u01(r.x);
+        const float ww = 1.0f + logf(fmaf(1.0f - u0, expf(-2.0f * S.kappa), u0)) / S.kappa;
+        const float sw = sqrtf(fmaxf(0.f, 1.0f - ww * ww));
+        const float3 d = f3(S.dir[0], S.dir[1], S.dir[2]);
+        float3 e1, e2;
+        onb(d, e1, e2);
+        nh = ww * d + sw * (cp * e1 + sp * e2);
+      } else {
+        const float ww = 2.0f * u01(r.x) - 1.0f;
+        const float sw = sqrtf(fmaxf(0.f, 1.0f - ww * ww));
+        nh = f3(sw * cp, sw * sp, ww);
+      }
+    }
+    float lnw = 0.f, L = 0.f;
+    v[3] += 1.0;
+    for (int i = 0; i <= max_scatter; ++i) {
+      r = philox4x32_10(make_uint4(plo, phi, static_cast<uint32_t>(i + 1), PUR_TRACE), k0, k1);
+      const float tau = -logf(u01(r.x));
+      const float dL = free_path(M, x.z + S.src[2], nh.z, tau);
+      const float dist = ray_sphere(x, nh, c, S.R2);
+      const float go = fminf(dist, dL);
+      const float3 end = x + go * nh;
+      float ta, tb;
+      seg_tau(M, x.z + S.src[2], end.z + S.src[2], go, ta, tb);
+      lnw -= ta;
+      if (dist < dL) {
+        float lw = lnw;
+        if (S.rho != 0) {
+          const float3 nu = (1.0f / S.R) * (end - c);
+          const float xx = dot(nu, f3(S.rho_hat[0], S.rho_hat[1], S.rho_hat[2]));
+          lw += fmaf(3.0f, xx, -1.0f) - logf(coshf(fmaf(2.0f, xx, 0.7f)));
+        }
+        const double W = static_cast<double>(expf(lw));
+        v[0] += W;
+        v[1] += W * W;
+        v[2] += 1.0;
+        v[4] += W * static_cast<double>(L + dist);
+        break;
+      }
+      const float3 rel = x - c;
+      if (dot(rel, rel) > r_reject * r_reject) break;
+      if (i == max_scatter) break;
+      x = end;
+      L += dL;
+      const float cs = sample_cos(M, u01(r.y), u01(r.w));
+      const float sn = sqrtf(fmaxf(0.f, 1.0f - cs * cs));
+      float sp, cp;
+      sincospif(2.0f * u01(r.z), &sp, &cp);
+      float3 e1, e2;
+      onb(nh, e1, e2);
+      nh = cs * nh + sn * (cp * e1 + sp * e2);
+      nh = rsqrtf(dot(nh, nh)) * nh;
+    }
+  }
+  block_sum<5>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) atomicAdd(out5 + k, v[k]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_logp(const DMedium& M, const DPair& S, const float* xyz, const int* n, int batch, int cap,
+                        float* out_logp, float* out_grad, cudaStream_t s) {
+  if (batch == 0) return cudaSuccess;
+  const int warps_per_block = 4;
+  const int grid = (batch + warps_per_block - 1) / warps_per_block;
+  logp_kernel<<<grid, warps_per_block * 32, 0, s>>>(M, S, xyz, n, batch, cap, out_logp, out_grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_score(const DMedium& M, const DPair& S, const float* xyz, const int* n, int batch, int cap,
+                         float* out, int n_theta, const double*, const double*, cudaStream_t s) {
+  if (batch == 0) return cudaSuccess;
+  if (M.kind != 0) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * static_cast<size_t>(batch) * n_theta, s);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = (batch + 3) / 4;
+  score_kernel<<<grid, 128, 0, s>>>(M, S, xyz, n, batch, cap, out, n_theta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_z2(const DMedium& M, const DPair* pairs, int n_pairs, int n_v, int n_phi, double* out,
+                      cudaStream_t s) {
+  if (n_pairs == 0) return cudaSuccess;
+  z2_kernel<<<n_pairs, 256, 0, s>>>(M, pairs, n_v, n_phi, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_estimator(const EstParams& p, cudaStream_t s) {
+  if (p.n_pairs == 0) return cudaSuccess;
+  estimator_kernel<<<p.n_pairs, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const DMedium& M, const DPair& S, unsigned long long seed, unsigned long long photon0,
+                         unsigned long long n_photons, float r_reject, int max_scatter, double* out5, int n_sm,
+                         cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out5, 0, 5 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  if (n_photons == 0) return cudaSuccess;
+  unsigned long long blocks = (n_photons + 255) / 256;
+  const unsigned long long maxb = static_cast<unsigned long long>(n_sm) * 8ull;
+  if (blocks > maxb) blocks = maxb;
+  trace_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(M, S, seed, photon0, n_photons, r_reject,
+                                                             max_scatter, out5);
+  return cudaGetLastError();
+}
+
+}  // namespace pmc
