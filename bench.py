@@ -1,0 +1,359 @@
+"""Benchmark: RJMCMC proposals/s of the path-integral chain kernel on GB300.
+
+One bench step is one pass of the whole hot path over one batch: chain
+initialisation, n_steps RJMCMC steps of every chain (random numbers, move
+choice, perturb / birth / death, delta log-density, accept, estimator
+accumulation) and the per-pair estimator reduction.  The default workload is
+the detector-scale pair: source-sensor distance 50 m, sensor radius 0.165 m,
+scattering length 5 m, absorption length 100 m, g = 0.94, 65,536 chains x
+100,000 steps, vertex cap 256.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores on the same workload and metric (bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RJMCMC proposals/s"
+UNIT = "proposals/s"
+
+# Algorithmic FP32 operations of one proposal per move type (scalar adds,
+# multiplies and fused multiply-adds of the factor formulas; each
+# transcendental counted as one operation), from the operation counts of the
+# formulas in the delta evaluator: see the roofline section of the design notes.
+OPS_PER_PROPOSAL = {"interior": 160.0, "end": 110.0, "birth": 230.0, "death": 200.0}
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="detector")
+    p.add_argument("--chains", type=int, default=65_536)
+    p.add_argument("--run-steps", type=int, default=100_000)
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--warps-per-block", type=int, default=0)
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def scene_for(args):
+    from paper_1811_04156_gb300 import scenes as S
+    if args.workload == "detector":
+        return S.detector(n_chains=args.chains, n_steps=args.run_steps)
+    if args.workload == "plain":
+        return S.plain(n_chains=args.chains, n_steps=args.run_steps)
+    if args.workload == "gradients":
+        return S.gradients(n_chains=args.chains, n_steps=args.run_steps)
+    raise SystemExit(f"unknown workload {args.workload}")
+
+
+def host_initial_paths(sc, stride=8):
+    """Straight initial paths with jittered interior vertices, built on the host
+    (seeded), as a user would pass them through the C ABI."""
+    import numpy as np
+    from paper_1811_04156_gb300 import scenes as S
+    p = sc.pairs[0]
+    src = np.asarray(sc.sources[0].pos, float)
+    c = np.asarray(sc.sensors[p.sensor].centre, float)
+    R = sc.sensors[p.sensor].radius
+    u = (src - c) / np.linalg.norm(src - c)
+    e = c + R * u
+    k = sc.run.init_k
+    rng = np.random.default_rng(S.BASE_SEED + 17)
+    xyz = np.zeros((p.n_chains, 3, stride), dtype=np.float32)
+    fr = np.arange(1, k + 1) / (k + 1)
+    inner = src[None, None, :] + fr[None, :, None] * (e - src)[None, None, :] + \
+        sc.run.init_jitter * rng.normal(size=(p.n_chains, k, 3))
+    xyz[:, :, 0] = src
+    xyz[:, :, 1:k + 1] = inner.transpose(0, 2, 1)
+    xyz[:, :, k + 1] = e
+    n = np.full(p.n_chains, k + 2, dtype=np.int32)
+    return xyz, n
+
+
+def cpu_baseline(sc, seconds, threads):
+    """The oracle as it stands on the host cores, on a bounded sample of the workload."""
+    import oracle as O
+    p = sc.pairs[0]
+    run = sc.run
+    chains = max(threads * 4, 16)
+
+    def one(steps):
+        ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[p.sensor], run, chains, p.cap)
+        t = time.perf_counter()
+        ch.run(steps, threads=threads)
+        return time.perf_counter() - t
+
+    probe = 400
+    dt = one(probe)
+    steps = max(probe, int(probe * seconds / max(dt, 1e-3)))
+    dt = one(steps)
+    props = chains * steps
+    return {"value": props / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{chains} chains x {steps} steps of the {sc.name} workload (first steps from the "
+                      f"initial paths), FP64, {dt:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    sc = scene_for(args)
+    threads = os.cpu_count() or 1
+    import oracle as O
+    O.build()
+    p = sc.pairs[0]
+    chains = max(threads * 4, 16)
+    per_step = max(4.0, 120.0 / max(args.steps + args.warmup, 1))
+    probe = O.Chains(sc.medium, sc.sources[0], sc.sensors[p.sensor], sc.run, chains, p.cap)
+    t = time.perf_counter()
+    probe.run(300, threads=threads)
+    rate = chains * 300 / (time.perf_counter() - t)
+    steps_per = max(300, int(rate * per_step / chains))
+    times = []
+    for i in range(args.warmup + args.steps):
+        ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[p.sensor], sc.run, chains, p.cap)
+        t = time.perf_counter()
+        ch.run(steps_per, threads=threads)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    value = chains * steps_per / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{sc.name}: {chains} chains x {steps_per} steps per step (bounded sample of "
+                                   f"{p.n_chains} x {sc.run.n_steps})", "global_batch": chains,
+                       "vertex_cap": p.cap},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{chains} chains x {steps_per} steps per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours(args):
+    import numpy as np
+    import torch
+    from paper_1811_04156_gb300 import build as B
+    B.build()
+    from paper_1811_04156_gb300 import api
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    sc = scene_for(args)
+    sc.run.seed = sc.run.seed + 1000 * rank  # weak scaling: every rank its own chains
+    ctx = api.Context(local)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    chains = api.Chains(ctx, medium, geom, sc.run, warps_per_block=args.warps_per_block)
+    stream = torch.cuda.current_stream()
+    n_chains = sc.total_chains
+    props_per_step = n_chains * sc.run.n_steps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def one_step(ev=None):
+        chains.reset()
+        if ev is not None:
+            ev[0].record(stream)
+        chains.run_steps(sc.run.n_steps)
+        if ev is not None:
+            ev[1].record(stream)
+        return chains.read_estimator()[0]
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clock = ClockSampler(local) if rank == 0 else None
+    if clock:
+        clock.start()
+    step_ms, kern_ms = [], []
+    est = None
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        est = one_step((k0, k1))
+        s1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        kern_ms.append(k0.elapsed_time(k1))
+    clocks = clock.stop() if clock else None
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * props_per_step / (ms_per_step / 1e3)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hx, hn = host_initial_paths(sc)
+        px = torch.from_numpy(hx).pin_memory()
+        pn = torch.from_numpy(hn).pin_memory()
+        hx, hn = px.numpy(), pn.numpy()
+        import ctypes as C
+        from paper_1811_04156_gb300._lib import Estimate, check, load
+        out = (Estimate * 1)()
+
+        def e2e_step():
+            chains.set_states(hx, hn)
+            chains.run_steps(sc.run.n_steps)
+            check(load().pmc_read_estimator(chains.handle, out, 1, C.c_void_p(stream.cuda_stream)), "read")
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(1, min(args.steps, 2))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        e2e_s = sum(ts) / len(ts)
+        e2e = {"value": world * props_per_step / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(hx.nbytes + hn.nbytes), "d2h_bytes_per_step": int(C.sizeof(Estimate))}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    peaks, peak_kind = load_peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tops = FP32_LANES_PER_SM * n_sm * sm_mhz * 1e6 / 1e12
+    prop = est["proposals"]
+    tot = sum(prop)
+    mix = {k: prop[i] / tot for i, k in enumerate(("interior", "end", "birth", "death"))}
+    ops = sum(mix[k] * OPS_PER_PROPOSAL[k] for k in mix)
+    kern_s = statistics.mean(kern_ms) / 1e3
+    achieved = props_per_step * ops / kern_s / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{sc.name}: 1 pair, D=50 m, R=0.165 m, lambda_s=5 m, lambda_a=100 m, g=0.94"
+                       if sc.name == "detector" else sc.name,
+                       "chains": n_chains, "steps_per_chain": sc.run.n_steps, "vertex_cap": sc.pairs[0].cap,
+                       "global_batch": n_chains * world, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MB write)", "accumulators": "f64"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tops, "traffic": None,
+                         "peak_source": f"FP32 lanes x SMs x sm_max_mhz ({peak_kind} clocks)",
+                         "kernel": "chain_kernel", "kernel_ms": statistics.mean(kern_ms),
+                         "ops_per_proposal": ops},
+            "gpu_launches": 3 * args.steps,
+            "estimate": {k: est[k] for k in ("intensity", "std_err", "pi_direct", "rhat", "mean_n", "accept")},
+            "clocks": clocks, "e2e": e2e}
+    if not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds, os.cpu_count() or 1)
+        except Exception as exc:  # the baseline is a report, not the product
+            line["cpu_baseline"] = {"error": str(exc)}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

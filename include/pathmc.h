@@ -213,6 +213,18 @@ PMC_API int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom,
                     const pmc_run_desc* run, void* stream, pmc_chains_t* out);
 PMC_API int pmc_destroy_chains(pmc_chains_t chains);
 
+/* Re-run the initialisation of pmc_init_chains on the existing buffers
+ * (async): DIRECT / STRAIGHT paths again, step counters and accumulators set
+ * to zero.  Chains created with PMC_INIT_USER need pmc_set_states instead. */
+PMC_API int pmc_reset_chains(pmc_chains_t chains, void* stream);
+
+/* Replace every chain's path by host data and zero the step counters and
+ * accumulators (async copy from `xyz` / `n`, which must stay valid until the
+ * stream reaches it; pinned memory makes the copy asynchronous).
+ * xyz: [total_chains][3][stride] absolute positions; n: [total_chains] with
+ * 2 <= n <= cap of the chain's pair and n <= stride. */
+PMC_API int pmc_set_states(pmc_chains_t chains, const float* xyz, const int* n, int stride, void* stream);
+
 /* Advance every chain by n_steps RJMCMC steps (async).  One step is one
  * proposal and its accept/reject decision by Eq. acceptFact (read in Green's
  * orientation for births; deaths use the reciprocal of the reverse birth).

@@ -92,6 +92,8 @@ PROTOTYPES = {
     "pmc_destroy_geometry": ([_vp], C.c_int),
     "pmc_init_chains": ([_vp, _vp, _vp, C.POINTER(RunDesc), _vp, C.POINTER(_vp)], C.c_int),
     "pmc_destroy_chains": ([_vp], C.c_int),
+    "pmc_reset_chains": ([_vp, _vp], C.c_int),
+    "pmc_set_states": ([_vp, _fp, _ip, C.c_int, _vp], C.c_int),
     "pmc_run_steps": ([_vp, C.c_uint64, _vp], C.c_int),
     "pmc_read_estimator": ([_vp, C.POINTER(Estimate), C.c_size_t, _vp], C.c_int),
     "pmc_grad_estimator": ([_vp, _dp, _dp, C.c_size_t, _vp], C.c_int),

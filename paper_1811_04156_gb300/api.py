@@ -191,6 +191,20 @@ class Chains:
         self.total = load().pmc_total_chains(h)
         self.n_pairs = len(geom.pairs)
 
+    def reset(self, stream=None):
+        """Re-initialise paths, step counters and accumulators (pmc_reset_chains)."""
+        check(load().pmc_reset_chains(self.handle, _stream(stream)), "pmc_reset_chains")
+
+    def set_states(self, xyz: np.ndarray, n: np.ndarray, stream=None):
+        """Upload host paths [total][3][stride] and counts (pmc_set_states); arrays must outlive the copy."""
+        if xyz.dtype != np.float32 or not xyz.flags.c_contiguous or xyz.ndim != 3 or xyz.shape[1] != 3:
+            raise ValueError("xyz must be C-contiguous float32 of shape (total, 3, stride)")
+        if n.dtype != np.int32 or not n.flags.c_contiguous:
+            raise ValueError("n must be C-contiguous int32")
+        check(load().pmc_set_states(self.handle, xyz.ctypes.data_as(C.POINTER(C.c_float)),
+                                    n.ctypes.data_as(C.POINTER(C.c_int)), int(xyz.shape[2]), _stream(stream)),
+              "pmc_set_states")
+
     def run_steps(self, n_steps: int, stream=None):
         check(load().pmc_run_steps(self.handle, int(n_steps), _stream(stream)), "pmc_run_steps")
 

@@ -126,7 +126,11 @@ struct pmc_chains_s {
   cudaStream_t capture_stream = nullptr;
   std::vector<ChainClass> classes;
   std::map<unsigned long long, cudaGraphExec_t> graphs;
-  bool z2_done = false;
+  int init_kind = 0, init_k = 0;
+  float init_jitter = 0.f;
+  float* d_stage = nullptr;       // staging buffer of pmc_set_states
+  int* d_stage_n = nullptr;
+  size_t stage_floats = 0;
 };
 
 extern "C" {
@@ -332,6 +336,8 @@ int pmc_destroy_chains(pmc_chains_t ch) {
   cudaFree(ch->d_queue);
   cudaFree(ch->d_z2);
   cudaFree(ch->d_est);
+  cudaFree(ch->d_stage);
+  cudaFree(ch->d_stage_n);
   if (ch->h_abort) cudaFreeHost(ch->h_abort);
   delete ch;
   return PMC_OK;
@@ -363,6 +369,9 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   ch->med = med;
   ch->geom = geom;
   ch->flags = r->flags;
+  ch->init_kind = r->init;
+  ch->init_k = r->init_k;
+  ch->init_jitter = static_cast<float>(r->init_jitter);
   ch->total = geom->total_chains;
   ch->n_pairs = static_cast<int>(geom->pairs.size());
   DRun& R = ch->run;
@@ -502,6 +511,64 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     cudaFree(d_user_n);
   }
   *out = ch.release();
+  return PMC_OK;
+}
+
+static InitParams init_params(pmc_chains_t ch) {
+  InitParams ip{};
+  ip.R = ch->run;
+  ip.pairs = ch->d_pairs;
+  ip.chain_pair = ch->d_chain_pair;
+  ip.chain_base = ch->d_chain_base;
+  ip.xyz = ch->d_xyz;
+  ip.n = ch->d_n;
+  ip.step = ch->d_step;
+  ip.acc = ch->d_acc;
+  ip.status = ch->d_status;
+  ip.total = ch->total;
+  ip.init_kind = ch->init_kind;
+  ip.init_k = ch->init_k;
+  ip.jitter = ch->init_jitter;
+  return ip;
+}
+
+int pmc_reset_chains(pmc_chains_t ch, void* stream) {
+  if (ch == nullptr) return fail(PMC_ERR_INVALID, "NULL chains");
+  if (ch->init_kind == PMC_INIT_USER) return fail(PMC_ERR_INVALID, "USER-initialised chains need pmc_set_states");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(ch->d_status, 0, sizeof(int) * ch->total, s));
+  CK(cudaMemsetAsync(ch->d_any, 0, sizeof(int), s));
+  CK(launch_init(init_params(ch), s));
+  return PMC_OK;
+}
+
+int pmc_set_states(pmc_chains_t ch, const float* xyz, const int* n, int stride, void* stream) {
+  if (ch == nullptr || xyz == nullptr || n == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (stride < 2) return fail(PMC_ERR_INVALID, "stride must be >= 2");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nf = static_cast<size_t>(ch->total) * 3 * stride;
+  if (nf > ch->stage_floats) {
+    cudaFree(ch->d_stage);
+    cudaFree(ch->d_stage_n);
+    ch->d_stage = nullptr;
+    ch->d_stage_n = nullptr;
+    ch->stage_floats = 0;
+    CK(dalloc(&ch->d_stage, nf));
+    CK(dalloc(&ch->d_stage_n, ch->total));
+    ch->stage_floats = nf;
+  }
+  CK(cudaMemcpyAsync(ch->d_stage, xyz, nf * sizeof(float), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ch->d_stage_n, n, ch->total * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ch->d_status, 0, sizeof(int) * ch->total, s));
+  CK(cudaMemsetAsync(ch->d_any, 0, sizeof(int), s));
+  InitParams ip = init_params(ch);
+  ip.init_kind = PMC_INIT_USER;
+  ip.user_xyz = ch->d_stage;
+  ip.user_n = ch->d_stage_n;
+  ip.user_stride = stride;
+  CK(launch_init(ip, s));
   return PMC_OK;
 }
 

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
       if (lane == 0) { P.status[c] |= ST_NONFINITE; atomicOr(P.any_status, ST_NONFINITE); }
       continue;
     }
-    float Tb = sm.tb, L = sm.L, G = sm.G;
+    float L = sm.L, G = sm.G;
 
     Accum A;
     A.pn2 = A.pn = 0;
@@ -419,8 +419,12 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
           dtb += __shfl_xor_sync(kFull, dtb, 2);
           dtb = __shfl_sync(kFull, dtb, 0);
           if (move == MV_DEATH) {
+            // T_b of the reduced path, summed afresh so that decisions depend
+            // only on the current state (split runs replay exactly)
+            float part = 0.f;
+            for (int i = lane; i < n - 1; i += 32) part += w.tb[i];
             const float tb_new = __shfl_sync(kFull, ntb, 0);
-            const float Tb_red = Tb + dtb;
+            const float Tb_red = warp_sum(part) + dtb;
             extra = -R.log_pd + logf(static_cast<float>(n - 2)) + R.log_pb + logf(tb_new / Tb_red) +
                     log_insert_density(M, R, zoff, w.pos(jj - 1), w.pos(jj + 1), w.pos(jj));
           }
@@ -470,7 +474,6 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
           }
           __syncwarp();
           n = n_new;
-          Tb += dtb;
           L += dlen;
           G += dg;
           if (A.nflush >= kFlushAccepts) flush64(A, lane);
@@ -478,7 +481,6 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
         if (t >= R.burn_in) A.dwell++;
         if (((t + 1) & (kRefreshSteps - 1)) == 0) {
           const Sums s2 = path_sums(w, n, lane);
-          Tb = s2.tb;
           L = s2.L;
           G = s2.G;
         }

@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: |delta log p| <= 1e-5 + 2e-6 n on identical states; intensities
+within 3 combined standard errors and <= 1% relative; gradients within 1e-3
+relative of the FP64 reference.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import quadrature as Q
+from paper_1811_04156_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1811_04156_gb300 import build
+    build.build()
+    from paper_1811_04156_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    return api.Context(0)
+
+
+def _oracle_objs(O, med, src, sen):
+    return O.medium(med), O.source(src), O.sensor(sen)
+
+
+SCENES = {
+    "plain": (S.Medium(lambda_s=0.5, lambda_a=5.0, g=0.9), S.Source(), S.Sensor((0.0, 0.0, 1.0), 0.1), 64, 0.3),
+    "detector": (S.Medium(lambda_s=5.0, lambda_a=100.0, g=0.94), S.Source(), S.Sensor((0.0, 0.0, 50.0), 0.165),
+                 256, 3.0),
+    "vmf_rho_sl": (S.Medium(lambda_s=0.8, lambda_a=6.0, g=0.95, f_sl=0.45),
+                   S.Source((0.3, -0.2, 0.1), S.EMIT_VMF, 38.0, (0.0, 0.0, 1.0)),
+                   S.Sensor((0.5, 0.4, 3.0), 0.15, S.RHO_PAPER, (0.0, -1.0, 0.0)), 96, 0.4),
+    "layered": (S.Medium(S.LAYERED, g=0.94, z0=-20.0, dz=2.0,
+                         lambda_s_layers=5.0 * np.exp(0.3 * np.random.default_rng(5).normal(size=20)),
+                         lambda_a_layers=100.0 * np.exp(0.3 * np.random.default_rng(6).normal(size=20))),
+                S.Source((1.0, 0.0, -3.0)), S.Sensor((0.0, 2.0, 9.0), 0.165), 128, 1.5),
+}
+
+
+def _batch(name, batch=384, seed=7):
+    """Random paths with n in [2, cap]; every third path has n in {2, 3} (edge cases)."""
+    med, src, sen, cap, lateral = SCENES[name]
+    xyz, n = S.random_paths(src.pos, sen.centre, sen.radius, batch, cap, 2, cap, seed, lateral=lateral)
+    xs, ns = S.random_paths(src.pos, sen.centre, sen.radius, batch, cap, 2, 3, seed + 1, lateral=lateral)
+    xyz[:, ::3, :] = xs[:, ::3, :]
+    n[::3] = ns[::3]
+    return med, src, sen, cap, xyz, n
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_logp_parity_identical_states(api, ctx, oracle_lib, name):
+    import torch
+    O = oracle_lib
+    med, src, sen, cap, xyz, n = _batch(name)
+    medium = api.Medium(ctx, med)
+    geom = api.Geometry(ctx, [src], [sen], [S.Pair(0, 0, 1, cap)])
+    lp = api.logp(ctx, medium, geom, 0, torch.from_numpy(xyz).cuda(), torch.from_numpy(n).cuda()).cpu().numpy()
+    m, s, d = _oracle_objs(O, med, src, sen)
+    n_fin = 0
+    for b in range(len(n)):
+        k = int(n[b])
+        path = xyz[:, b, :k].T.astype(np.float64)
+        ref = O.logp(m, s, d, path)
+        if not np.isfinite(ref):
+            assert lp[b] == -np.inf, (b, lp[b], ref)
+            continue
+        n_fin += 1
+        tol = 1e-5 + 2e-6 * k
+        assert abs(lp[b] - ref) <= tol, (name, b, k, lp[b], ref, lp[b] - ref)
+    assert n_fin >= len(n) // 3
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_adjoint_parity(api, ctx, oracle_lib, name):
+    import torch
+    O = oracle_lib
+    med, src, sen, cap, xyz, n = _batch(name, batch=128, seed=11)
+    medium = api.Medium(ctx, med)
+    geom = api.Geometry(ctx, [src], [sen], [S.Pair(0, 0, 1, cap)])
+    xt = torch.from_numpy(xyz).cuda().requires_grad_(True)
+    nt = torch.from_numpy(n).cuda()
+    lp = api.LogP.apply(xt, nt, (ctx, medium, geom, 0))
+    lp_f = torch.where(torch.isfinite(lp), lp, torch.zeros_like(lp))
+    lp_f.sum().backward()
+    g = xt.grad.cpu().numpy()
+    m, s, d = _oracle_objs(O, med, src, sen)
+    checked = 0
+    for b in range(len(n)):
+        k = int(n[b])
+        path = xyz[:, b, :k].T.astype(np.float64)
+        ref_lp, ref = O.grad_logp(m, s, d, path)
+        if not np.isfinite(ref_lp):
+            continue
+        mine = g[:, b, :k].T
+        err = np.linalg.norm(mine - ref) / max(np.linalg.norm(ref), 1e-30)
+        assert err < 1e-3, (name, b, k, err)
+        assert np.all(g[:, b, k:] == 0)
+        checked += 1
+    assert checked >= 20
+
+
+@pytest.mark.parametrize("name", ["plain", "detector", "layered"])
+def test_score_parity(api, ctx, oracle_lib, name):
+    import torch
+    O = oracle_lib
+    med, src, sen, cap, xyz, n = _batch(name, batch=128, seed=13)
+    medium = api.Medium(ctx, med)
+    geom = api.Geometry(ctx, [src], [sen], [S.Pair(0, 0, 1, cap)])
+    sc = api.score(ctx, medium, geom, 0, torch.from_numpy(xyz).cuda(), torch.from_numpy(n).cuda()).cpu().numpy()
+    m, s, d = _oracle_objs(O, med, src, sen)
+    for b in range(len(n)):
+        k = int(n[b])
+        ref = O.score(m, s, d, xyz[:, b, :k].T.astype(np.float64))
+        err = np.linalg.norm(sc[b] - ref) / max(np.linalg.norm(ref), 1e-30)
+        assert err < 1e-3, (name, b, err)
+
+
+def _plain_sampler(api, ctx, n_chains, n_steps, cap=64, flags=0, seed=None, within=S.WITHIN_PERTURB):
+    sc = S.plain(n_chains=n_chains, n_steps=n_steps, cap=cap)
+    if seed is not None:
+        sc.run.seed = seed
+    sc.run.within = within
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    return sc, medium, geom, api.Chains(ctx, medium, geom, sc.run, flags=flags)
+
+
+@pytest.mark.parametrize("flags", [0, 2])
+def test_trajectory_replay(api, ctx, oracle_lib, flags):
+    """Same Philox stream on both sides: every chain whose decisions never came
+    within 1e-3 of the threshold ends in the oracle's state."""
+    O = oracle_lib
+    steps = 400
+    sc, medium, geom, ch = _plain_sampler(api, ctx, 64, steps, flags=flags)
+    ch.run_steps(steps)
+    xyz, n, st = ch.read_states()
+    oc = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, 64)
+    margin = oc.run(steps, margins=True)
+    assert np.all(st == steps)
+    clean = margin > 1e-3
+    assert clean.sum() >= 40
+    for c in np.nonzero(clean)[0]:
+        assert n[c] == oc.n[c], (c, n[c], oc.n[c])
+        k = int(n[c])
+        assert np.allclose(xyz[c, :, :k].T, oc.xyz[c, :k], atol=2e-4), c
+    acc = ch.read_accumulators()
+    oacc = oc.accumulators()
+    for c in np.nonzero(clean)[0]:
+        assert np.array_equal(acc[c, 8:12], oacc["prop"][c])
+        assert np.array_equal(acc[c, 12:16], oacc["acc"][c])
+
+
+def test_split_runs_and_checkpoint_are_bit_exact(api, ctx):
+    _, _, _, a = _plain_sampler(api, ctx, 256, 0)
+    _, _, _, b = _plain_sampler(api, ctx, 256, 0)
+    a.run_steps(1500)
+    b.run_steps(500)
+    blob = b.save_state()
+    b.run_steps(1000)
+    xa, na, sa = a.read_states()
+    xb, nb, sb = b.read_states()
+    assert np.array_equal(na, nb) and np.array_equal(xa, xb) and np.array_equal(sa, sb)
+    aa, ab = a.read_accumulators(), b.read_accumulators()
+    assert np.array_equal(aa[:, 8:], ab[:, 8:])          # proposal / acceptance counts
+    assert np.allclose(aa[:, :8], ab[:, :8], rtol=1e-6)  # FP32 partial sums flush at other points
+    b.load_state(blob)
+    b.run_steps(1000)
+    xc, nc_, _ = b.read_states()
+    assert np.array_equal(xa, xc) and np.array_equal(na, nc_)
+
+
+def test_intensity_single_scatter_sector(api, ctx):
+    sc, medium, geom, ch = _plain_sampler(api, ctx, 4096, 20000, cap=3)
+    ch.run_steps(20000)
+    e = ch.read_estimator()[0]
+    ref = Q.z2_closed(1.0, 0.1, 2.2) + Q.z3(1.0, 0.1, 0.5, 5.0, 0.9)
+    assert abs(e["z2"] / Q.z2_closed(1.0, 0.1, 2.2) - 1) < 1e-5
+    assert abs(e["intensity"] - ref) < 3 * e["std_err"], (e["intensity"], e["std_err"], ref)
+    assert e["rel_err"] < 0.003
+
+
+def test_intensity_matches_oracle_plain(api, ctx):
+    g = json.load(open(os.path.join(GOLDEN, "plain_intensity.json")))
+    sc, medium, geom, ch = _plain_sampler(api, ctx, g["n_chains"], g["n_steps"], seed=g["seed"])
+    assert sc.run.burn_in == g["burn_in"]
+    ch.run_steps(g["n_steps"])
+    e = ch.read_estimator()[0]
+    diff = abs(e["intensity"] - g["intensity"])
+    assert diff < 3 * math.hypot(e["std_err"], g["std_err"]), (e, g)
+    assert diff < 0.01 * g["intensity"]
+    assert abs(e["mean_n"] / g["mean_n"] - 1) < 0.01
+
+
+def test_mala_single_scatter_sector(api, ctx):
+    sc, medium, geom, ch = _plain_sampler(api, ctx, 4096, 20000, cap=3, within=S.WITHIN_MALA)
+    ch.run_steps(20000)
+    e = ch.read_estimator()[0]
+    ref = Q.z2_closed(1.0, 0.1, 2.2) + Q.z3(1.0, 0.1, 0.5, 5.0, 0.9)
+    assert abs(e["intensity"] - ref) < 3 * e["std_err"], (e["intensity"], e["std_err"], ref)
+
+
+def test_gpu_tracer_matches_oracle_tracer(api, ctx, oracle_lib):
+    O = oracle_lib
+    med, src, sen = S.Medium(lambda_s=1.0, lambda_a=5.0, g=0.6), S.Source(), S.Sensor((0.0, 0.0, 1.5), 0.5)
+    medium = api.Medium(ctx, med)
+    geom = api.Geometry(ctx, [src], [sen], [S.Pair(0, 0, 1, 32)])
+    gt = api.trace(ctx, medium, geom, 0, 4242, 200_000_000, max_scatter=30)
+    m, s, d = _oracle_objs(O, med, src, sen)
+    ot = O.trace(m, s, d, 4242, 4_000_000, max_scatter=30)
+    assert abs(gt["I"] - ot["I"]) < 3 * math.hypot(gt["se"], ot["se"])
+    # without scattering the tracer reproduces the closed form
+    med0 = S.Medium(lambda_s=1e9, lambda_a=2.0)
+    g0 = api.trace(ctx, api.Medium(ctx, med0), geom, 0, 5, 100_000_000, max_scatter=0)
+    assert abs(g0["I"] - Q.z2_closed(1.5, 0.5, 0.5 + 1e-9)) < 3 * g0["se"]
+
+
+def test_abort_request_stops_and_context_survives(api, ctx):
+    from paper_1811_04156_gb300._lib import PathmcError
+    _, _, _, ch = _plain_sampler(api, ctx, 128, 0)
+    ch.request_abort(True)
+    ch.run_steps(5000)
+    with pytest.raises(PathmcError) as ei:
+        ch.read_estimator()
+    assert ei.value.code == 5
+    ch.request_abort(False)
+    _, _, _, ch2 = _plain_sampler(api, ctx, 128, 0)
+    ch2.run_steps(2000)
+    assert ch2.read_estimator()[0]["n_samples"] > 0
