@@ -82,9 +82,61 @@ struct pmc_medium_s {
   int n_theta = 3;
 };
 
+struct PairHost {
+  double src[3], c[3], R;
+  int emission;
+  double kappa, dir[3];
+  int rho;
+  double rho_hat[3];
+  int cap, n_chains, chain0;
+};
+
+// Pair constants in a frame: origin at the source (chains, tracer) or at the
+// absolute origin (density kernels on caller batches).  The sensor centre is
+// split into FP32 high and low parts.
+static DPair make_dpair(const PairHost& h, bool source_frame) {
+  DPair d{};
+  double org[3] = {0, 0, 0};
+  if (source_frame)
+    for (int i = 0; i < 3; ++i) org[i] = h.src[i];
+  double rel[3];
+  for (int i = 0; i < 3; ++i) {
+    d.org[i] = static_cast<float>(org[i]);
+    d.src[i] = static_cast<float>(h.src[i] - org[i]);
+    const double cc = h.c[i] - org[i];
+    d.c[i] = static_cast<float>(cc);
+    d.c_lo[i] = static_cast<float>(cc - static_cast<double>(d.c[i]));
+    rel[i] = h.c[i] - h.src[i];
+  }
+  d.zoff = static_cast<float>(org[2]);
+  const double D = norm3(rel);
+  for (int i = 0; i < 3; ++i) d.e_near[i] = static_cast<float>(h.src[i] - org[i] + rel[i] - h.R * rel[i] / D);
+  d.R = static_cast<float>(h.R);
+  d.R2 = d.R * d.R;
+  d.emission = h.emission;
+  if (h.emission == PMC_EMIT_VMF) {
+    const double nd = norm3(h.dir);
+    for (int i = 0; i < 3; ++i) d.dir[i] = static_cast<float>(h.dir[i] / nd);
+    d.kappa = static_cast<float>(h.kappa);
+    const double k = h.kappa;
+    d.vmf_lognorm = static_cast<float>(std::log(k) - std::log(2.0 * M_PI) - k - std::log(-std::expm1(-2.0 * k)));
+  }
+  d.rho = h.rho;
+  if (h.rho == PMC_RHO_PAPER) {
+    const double nr = norm3(h.rho_hat);
+    for (int i = 0; i < 3; ++i) d.rho_hat[i] = static_cast<float>(h.rho_hat[i] / nr);
+  }
+  d.cap = h.cap;
+  d.n_chains = h.n_chains;
+  d.chain0 = h.chain0;
+  return d;
+}
+
 struct pmc_geom_s {
   pmc_ctx_s* ctx = nullptr;
-  std::vector<DPair> pairs;  // run-independent fields
+  std::vector<PairHost> host;
+  std::vector<DPair> pairs;      // source frame: chains and tracer
+  std::vector<DPair> abs_pairs;  // absolute frame: pmc_logp, pmc_logp_grad, pmc_score
   int total_chains = 0;
   int max_cap = 0;
 };
@@ -261,46 +313,42 @@ int pmc_create_geometry(pmc_ctx_t ctx, const pmc_geometry_desc* desc, pmc_geom_t
     const pmc_source& so = desc->sources[pr.source];
     const pmc_sensor& se = desc->sensors[pr.sensor];
     if (!finite_pos(se.radius)) return fail(PMC_ERR_INVALID, "sensor radius must be > 0");
-    DPair d{};
+    PairHost h{};
     double rel[3];
     for (int i = 0; i < 3; ++i) {
       if (!std::isfinite(so.pos[i]) || !std::isfinite(se.centre[i])) return fail(PMC_ERR_INVALID, "non-finite position");
-      d.src[i] = static_cast<float>(so.pos[i]);
+      h.src[i] = so.pos[i];
+      h.c[i] = se.centre[i];
       rel[i] = se.centre[i] - so.pos[i];
-      d.c[i] = static_cast<float>(rel[i]);
     }
     const double D = norm3(rel);
     if (!(D > se.radius * (1.0 + 1e-6))) return fail(PMC_ERR_INVALID, "source inside or on its sensor");
-    d.R = static_cast<float>(se.radius);
-    d.R2 = d.R * d.R;
-    d.emission = so.emission;
+    h.R = se.radius;
+    h.emission = so.emission;
     if (so.emission == PMC_EMIT_VMF) {
       if (!finite_pos(so.kappa)) return fail(PMC_ERR_INVALID, "vMF kappa must be > 0");
-      const double nd = norm3(so.dir);
-      if (!(nd > 0)) return fail(PMC_ERR_INVALID, "zero emission direction");
-      for (int i = 0; i < 3; ++i) d.dir[i] = static_cast<float>(so.dir[i] / nd);
-      d.kappa = static_cast<float>(so.kappa);
-      const double k = so.kappa;
-      d.vmf_lognorm = static_cast<float>(std::log(k) - std::log(2.0 * M_PI) - k - std::log(-std::expm1(-2.0 * k)));
+      if (!(norm3(so.dir) > 0)) return fail(PMC_ERR_INVALID, "zero emission direction");
+      h.kappa = so.kappa;
+      for (int i = 0; i < 3; ++i) h.dir[i] = so.dir[i];
     } else if (so.emission != PMC_EMIT_ISOTROPIC) {
       return fail(PMC_ERR_INVALID, "unknown emission kind");
     }
-    d.rho = se.rho;
+    h.rho = se.rho;
     if (se.rho == PMC_RHO_PAPER) {
-      const double nr = norm3(se.rho_hat);
-      if (!(nr > 0)) return fail(PMC_ERR_INVALID, "zero rho_hat");
-      for (int i = 0; i < 3; ++i) d.rho_hat[i] = static_cast<float>(se.rho_hat[i] / nr);
+      if (!(norm3(se.rho_hat) > 0)) return fail(PMC_ERR_INVALID, "zero rho_hat");
+      for (int i = 0; i < 3; ++i) h.rho_hat[i] = se.rho_hat[i];
     } else if (se.rho != PMC_RHO_ONE) {
       return fail(PMC_ERR_INVALID, "unknown detection kind");
     }
-    for (int i = 0; i < 3; ++i) d.e_near[i] = static_cast<float>(rel[i] - se.radius * rel[i] / D);
-    d.cap = pr.cap;
-    d.n_chains = pr.n_chains;
-    d.chain0 = static_cast<int>(total);
+    h.cap = pr.cap;
+    h.n_chains = pr.n_chains;
+    h.chain0 = static_cast<int>(total);
     total += pr.n_chains;
     if (total > (1ll << 30)) return fail(PMC_ERR_INVALID, "too many chains");
+    g->host.push_back(h);
+    g->pairs.push_back(make_dpair(h, true));
+    g->abs_pairs.push_back(make_dpair(h, false));
     g->max_cap = std::max(g->max_cap, pr.cap);
-    g->pairs.push_back(d);
   }
   g->total_chains = static_cast<int>(total);
   *out = g.release();
@@ -716,7 +764,7 @@ int pmc_read_states(pmc_chains_t ch, float* xyz, int* n, uint64_t* steps, int st
     float* dst = xyz + static_cast<size_t>(c) * 3 * stride;
     for (int a = 0; a < 3; ++a)
       for (int i = 0; i < stride; ++i)
-        dst[a * stride + i] = (i < n[c] && i < d.cap) ? src[a * d.cap + i] + d.src[a] : 0.f;
+        dst[a * stride + i] = (i < n[c] && i < d.cap) ? src[a * d.cap + i] + d.org[a] : 0.f;
   }
   return PMC_OK;
 }
@@ -806,9 +854,9 @@ int pmc_chain_status(pmc_chains_t ch, int* status, void* stream) {
   return PMC_OK;
 }
 
-static const DPair* pair_of(pmc_geom_t g, int pair) {
+static const DPair* pair_of(pmc_geom_t g, int pair, bool absolute = true) {
   if (g == nullptr || pair < 0 || pair >= static_cast<int>(g->pairs.size())) return nullptr;
-  return &g->pairs[pair];
+  return absolute ? &g->abs_pairs[pair] : &g->pairs[pair];
 }
 
 int pmc_logp(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, const float* xyz, const int* n,
@@ -844,7 +892,7 @@ int pmc_score(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, const 
 
 int pmc_trace(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, uint64_t seed, uint64_t photon0,
               uint64_t n_photons, double r_reject, int max_scatter, double* out, void* stream) {
-  const DPair* d = pair_of(geom, pair);
+  const DPair* d = pair_of(geom, pair, false);
   if (!ctx || !med || !d || !out) return fail(PMC_ERR_INVALID, "bad argument");
   if (max_scatter < 0 || !(r_reject > 0)) return fail(PMC_ERR_INVALID, "bad tracer limits");
   CK(cudaSetDevice(ctx->device));

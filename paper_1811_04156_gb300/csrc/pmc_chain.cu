@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
     const int c = P.order[P.chain_lo + item];
 
     const DPair S = P.pairs[P.chain_pair[c]];
-    const float zoff = S.src[2];
+    const float zoff = S.zoff;
     const int cap = S.cap;
     int n = P.n[c];
     const unsigned long long step0 = P.step[c];
@@ -304,14 +304,13 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
           jj = j;
           if (j == n - 1) {
             move = MV_END;
-            float3 nu = w.pos(j) - cS;
-            nu = rsqrtf(dot(nu, nu)) * nu;
+            const float3 nu = sensor_normal(S, w.pos(j));
             float3 e1, e2;
             onb(nu, e1, e2);
             const float wv = p3;
             const float sw = sqrtf(fmaxf(0.f, 1.0f - wv * wv));
             const float3 nn = wv * nu + sw * (p4 * e1 + p5 * e2);
-            fnew = cS + S.R * nn;
+            fnew = cS + (f3(S.c_lo[0], S.c_lo[1], S.c_lo[2]) + S.R * nn);
             wlo = n - 2; nc = 2; olo = n - 2; onc = 2;
           } else {
             move = MV_INTERIOR;
@@ -530,9 +529,9 @@ __global__ void init_kernel(const InitParams p) {
       n = 2;
     }
     for (int i = 0; i < n; ++i) {
-      gx[i] = ux[i] - S.src[0];
-      gy[i] = ux[st + i] - S.src[1];
-      gz[i] = ux[2 * st + i] - S.src[2];
+      gx[i] = ux[i] - S.org[0];
+      gy[i] = ux[st + i] - S.org[1];
+      gz[i] = ux[2 * st + i] - S.org[2];
     }
   } else {
     const int k = (p.init_kind == PMC_INIT_DIRECT) ? 0 : p.init_k;

@@ -40,8 +40,11 @@ struct DMedium {
 };
 
 struct DPair {
-  float src[3];        // absolute source position
-  float c[3];          // sensor centre relative to the source
+  float org[3];        // absolute position of the frame origin (the source, or 0)
+  float src[3];        // source position in the frame of this struct
+  float c[3];          // sensor centre in the frame (high part)
+  float c_lo[3];       // low part: centre = c + c_lo to ~2^-48 relative
+  float zoff;          // absolute height of the frame origin (layered media)
   float R, R2;
   int emission;        // 0 isotropic, 1 vMF
   float kappa, vmf_lognorm;
@@ -209,11 +212,18 @@ __device__ __forceinline__ float emission_term(const DPair& P, float3 b) {
   return fmaf(P.kappa, dot(b, f3(P.dir[0], P.dir[1], P.dir[2])), P.vmf_lognorm);
 }
 
+// Outward unit normal of the sensor at e.  e - c_hi is exact when e lies near
+// the sphere (Sterbenz), so the normal keeps full FP32 accuracy however far
+// the sensor is from the frame origin.
+__device__ __forceinline__ float3 sensor_normal(const DPair& P, float3 e) {
+  float3 nu = (e - f3(P.c[0], P.c[1], P.c[2])) - f3(P.c_lo[0], P.c_lo[1], P.c_lo[2]);
+  return rsqrtf(dot(nu, nu)) * nu;
+}
+
 // Detection factor of p_f without its 1/|r|^2: log max(0, -a . nu) + log rho(nu)
 // (Eq. detection_prob), for the last direction a and end vertex e.
 __device__ __forceinline__ float sensor_term(const DPair& P, float3 a, float3 e) {
-  float3 nu = e - f3(P.c[0], P.c[1], P.c[2]);
-  nu = rsqrtf(dot(nu, nu)) * nu;
+  const float3 nu = sensor_normal(P, e);
   const float cphi = -dot(a, nu);
   if (!(cphi > 0.0f)) return kNegInf;
   float t = logf(cphi);
@@ -356,7 +366,7 @@ __device__ float3 grad_vertex(const DMedium& M, const DPair& S, float zoff, PosF
     const float3 e = (v == n - 1) ? pv[2] : pv[3];
     const float3 rhat = (v == n - 1) ? rh[1] : rh[2];
     const float ell = (v == n - 1) ? el[1] : el[2];
-    float3 nu = e - f3(S.c[0], S.c[1], S.c[2]);
+    float3 nu = (e - f3(S.c[0], S.c[1], S.c[2])) - f3(S.c_lo[0], S.c_lo[1], S.c_lo[2]);
     const float dn = sqrtf(dot(nu, nu));
     nu = (1.0f / dn) * nu;
     const float u = -dot(rhat, nu);

@@ -14,13 +14,13 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Batch accessor: SoA [3][batch][cap] absolute positions -> source-relative.
+// Batch accessor: SoA [3][batch][cap] positions, evaluated in the caller's
+// absolute frame (the pair struct passed to these kernels uses that frame).
 struct BatchPos {
   const float* xyz;
   size_t plane, off;
-  float sx, sy, sz;
   __device__ float3 operator()(int i) const {
-    return f3(xyz[off + i] - sx, xyz[plane + off + i] - sy, xyz[2 * plane + off + i] - sz);
+    return f3(xyz[off + i], xyz[plane + off + i], xyz[2 * plane + off + i]);
   }
 };
 
@@ -32,8 +32,8 @@ __global__ void logp_kernel(const DMedium M, const DPair S, const float* __restr
   const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (b >= batch) return;
   const int n = nn[b];
-  const float zoff = S.src[2];
-  BatchPos pos{xyz, static_cast<size_t>(batch) * cap, static_cast<size_t>(b) * cap, S.src[0], S.src[1], S.src[2]};
+  const float zoff = S.zoff;
+  BatchPos pos{xyz, static_cast<size_t>(batch) * cap, static_cast<size_t>(b) * cap};
   float lp = 0.f;
   if (n >= 2 && n <= cap) {
     for (int i = lane; i < n; i += 32) {
@@ -76,8 +76,8 @@ __global__ void score_kernel(const DMedium M, const DPair S, const float* __rest
   if (b >= batch) return;
   const int n = nn[b];
   if (n < 2 || n > cap) return;
-  const float zoff = S.src[2];
-  BatchPos pos{xyz, static_cast<size_t>(batch) * cap, static_cast<size_t>(b) * cap, S.src[0], S.src[1], S.src[2]};
+  const float zoff = S.zoff;
+  BatchPos pos{xyz, static_cast<size_t>(batch) * cap, static_cast<size_t>(b) * cap};
   float* o = out + static_cast<size_t>(b) * n_theta;
   if (M.kind == 0) {
     float L = 0.f, G = 0.f;
@@ -184,10 +184,10 @@ __global__ void __launch_bounds__(256) z2_kernel(const DMedium M, const DPair* _
     const float3 om = ct * ax + st * (cp * e1 + sp * e2);
     const float3 h = r * om;
     float ta, tb;
-    seg_tau(M, S.src[2], h.z + S.src[2], r, ta, tb);
+    seg_tau(M, S.zoff, h.z + S.zoff, r, ta, tb);
     float lv = emission_term(S, om) - ta - tb;
     if (S.rho != 0) {
-      const float3 nu = (1.0f / R) * (h - c);
+      const float3 nu = sensor_normal(S, h);
       const float x = dot(nu, f3(S.rho_hat[0], S.rho_hat[1], S.rho_hat[2]));
       lv += fmaf(3.0f, x, -1.0f) - logf(coshf(fmaf(2.0f, x, 0.7f)));
     }
@@ -384,17 +384,17 @@ __global__ void __launch_bounds__(256) trace_kernel(const DMedium M, const DPair
     for (int i = 0; i <= max_scatter; ++i) {
       r = philox4x32_10(make_uint4(plo, phi, static_cast<uint32_t>(i + 1), PUR_TRACE), k0, k1);
       const float tau = -logf(u01(r.x));
-      const float dL = free_path(M, x.z + S.src[2], nh.z, tau);
+      const float dL = free_path(M, x.z + S.zoff, nh.z, tau);
       const float dist = ray_sphere(x, nh, c, S.R2);
       const float go = fminf(dist, dL);
       const float3 end = x + go * nh;
       float ta, tb;
-      seg_tau(M, x.z + S.src[2], end.z + S.src[2], go, ta, tb);
+      seg_tau(M, x.z + S.zoff, end.z + S.zoff, go, ta, tb);
       lnw -= ta;
       if (dist < dL) {
         float lw = lnw;
         if (S.rho != 0) {
-          const float3 nu = (1.0f / S.R) * (end - c);
+          const float3 nu = sensor_normal(S, end);
           const float xx = dot(nu, f3(S.rho_hat[0], S.rho_hat[1], S.rho_hat[2]));
           lw += fmaf(3.0f, xx, -1.0f) - logf(coshf(fmaf(2.0f, xx, 0.7f)));
         }
