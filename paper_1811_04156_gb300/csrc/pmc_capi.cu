@@ -178,6 +178,7 @@ struct pmc_chains_s {
   cudaStream_t capture_stream = nullptr;
   std::vector<ChainClass> classes;
   std::map<unsigned long long, cudaGraphExec_t> graphs;
+  bool general = false;            // chain kernel instantiation
   int init_kind = 0, init_k = 0;
   float init_jitter = 0.f;
   float* d_stage = nullptr;       // staging buffer of pmc_set_states
@@ -479,14 +480,17 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     ch->classes.push_back(cl);
     lo = hi;
   }
+  ch->general = med->d.kind != PMC_HOMOGENEOUS || med->d.f_sl > 0.f || r->within == PMC_WITHIN_MALA ||
+                std::any_of(ch->h_pairs.begin(), ch->h_pairs.end(),
+                            [](const DPair& d) { return d.emission != PMC_EMIT_ISOTROPIC || d.rho != PMC_RHO_ONE; });
   // launch shapes: warps per block from the request (0: default), persistent grid from occupancy
   for (auto& cl : ch->classes) {
     int wpb = r->warps_per_block > 0 ? r->warps_per_block : 4;
-    wpb = std::min(wpb, 8);
+    wpb = std::min(wpb, 4);
     while (wpb > 1 && chain_smem_bytes(cl.smem_cap, wpb) > ctx->smem_per_block) wpb /= 2;
     if (chain_smem_bytes(cl.smem_cap, wpb) > ctx->smem_per_block) return fail(PMC_ERR_INVALID, "vertex cap too large for shared memory");
     int bps = 0;
-    CK(chain_occupancy(wpb, cl.smem_cap, &bps));
+    CK(chain_occupancy(ch->general, wpb, cl.smem_cap, &bps));
     if (bps < 1) return fail(PMC_ERR_INVALID, "chain kernel does not fit on an SM");
     const int chains = cl.hi - cl.lo;
     const int want = (chains + wpb - 1) / wpb;
@@ -643,7 +647,7 @@ static int enqueue_steps(pmc_chains_t ch, unsigned long long n_steps, cudaStream
     p.n_steps = n_steps;
     p.smem_cap = cl.smem_cap;
     CK(cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s));
-    CK(launch_chain(p, cl.grid, cl.warps_per_block, s));
+    CK(launch_chain(p, ch->general, cl.grid, cl.warps_per_block, s));
   }
   return PMC_OK;
 }

@@ -6,17 +6,25 @@
 //
 // Per warp and per step:
 //   * random numbers: every 32 steps each lane draws the two Philox4x32-10
-//     blocks of one future step and pre-transforms them (Box-Muller normals,
-//     vMF cosine, logistic t), so the serial path only broadcasts 8 words;
+//     blocks of one future step, pre-transforms them (Box-Muller normals, vMF
+//     cosine, logistic t, log u) and stores 8 words in the warp's shared
+//     staging row; each step then reads its row with two broadcast loads;
 //   * delta evaluator: a move changes at most 3 vertex factors and 2 segment
 //     factors; lane i evaluates vertex factor i and segment factor i of the
 //     changed window in parallel, the old values come from the caches, and
-//     three shuffles give the change of log p;
+//     two shuffles give the change of log p;
 //   * accept / commit: births and deaths shift the SoA arrays with the whole
 //     warp; caches of the changed window are written back.
+// Two instantiations: kGen = false is the lean kernel for a homogeneous
+// medium, isotropic emission, detection probability 1, pure Henyey-Greenstein
+// phase function and Gaussian perturbations; kGen = true handles layered
+// media, vMF emission, the paper's detection probability, the simplified-Liu
+// mixture and MALA moves.
 // Estimators: observables (n, length L, sum of d log sigma/dg) change only on
 // acceptance, so each state's values are added once with its dwell time into
 // FP32 partials that are flushed into lane-distributed FP64 accumulators.
+#include <climits>
+
 #include "pmc_internal.h"
 
 namespace pmc {
@@ -26,6 +34,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRefreshSteps = 256;  // recompute the running sums from the caches
 constexpr int kFlushAccepts = 64;   // FP32 partials -> FP64 accumulators
+constexpr int kRngWords = 8;        // staged words per step
 
 enum Move { MV_INTERIOR = 0, MV_END = 1, MV_BIRTH = 2, MV_DEATH = 3 };
 
@@ -40,47 +49,89 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Factors attached to vertex v of an n-vertex path: its vertex factor (and
+// d log sigma / d g) and, when v <= n-2, the factor of the segment v -> v+1.
+template <bool kGen>
+__device__ __forceinline__ void vertex_and_segment(const DMedium& M, const DPair& S, float zoff, float3 Pp, float3 Pc,
+                                                   float3 Pn, int v, int n, float& vt, float& gt, float& seg,
+                                                   float& tb, float& len) {
+  constexpr bool F = true;
+  gt = 0.f;
+  seg = 0.f;
+  tb = 0.f;
+  len = 0.f;
+  const float3 b0 = Pn - Pc;
+  const float bb = dot(b0, b0);
+  const float ib = rsqrtf(bb);
+  const float3 b = ib * b0;
+  if (v <= n - 2) {
+    const float ell = bb * ib;
+    float ta, tbv;
+    if constexpr (kGen) {
+      seg_tau(M, Pc.z + zoff, Pn.z + zoff, ell, ta, tbv);
+    } else {
+      ta = M.a * ell;
+      tbv = M.b * ell;
+    }
+    seg = -(ta + tbv) - m_log<F>(bb);
+    tb = tbv;
+    len = ell;
+    if (!(bb > 0.0f)) seg = kNegInf;
+    if (v <= n - 3 && hits_ball(S, Pc, b0)) seg = kNegInf;
+  }
+  if (v == 0) {
+    if constexpr (kGen) vt = emission_term(S, b);
+    else vt = -kLog4Pi;
+    return;
+  }
+  const float3 a0 = Pc - Pp;
+  const float3 a = rsqrtf(dot(a0, a0)) * a0;
+  if (v == n - 1) {
+    vt = sensor_term<F>(S, a, Pc);
+    return;
+  }
+  const float lb = kGen ? log_b_at(M, Pc.z + zoff) : M.log_b;
+  vt = lb + phase_term<F, kGen>(M, a, b, gt);
+}
+
 struct Sums {
-  float lp, tb, L, G;
+  float L, G;
 };
 
 __device__ Sums path_sums(const WarpPath& w, int n, int lane) {
-  float lp = 0.f, tb = 0.f, L = 0.f, G = 0.f;
+  float L = 0.f, G = 0.f;
   for (int i = lane; i < n; i += 32) {
-    lp += w.vt[i];
     G += w.gt[i];
-    if (i <= n - 2) {
-      lp += w.seg[i];
-      tb += w.tb[i];
-      L += w.len[i];
-    }
+    if (i <= n - 2) L += w.len[i];
   }
   Sums s;
-  s.lp = warp_sum(lp);
-  s.tb = warp_sum(tb);
   s.L = warp_sum(L);
   s.G = warp_sum(G);
   return s;
 }
 
-// Recompute every cached factor of the path from its vertices.
-__device__ void refresh_caches(const DMedium& M, const DPair& S, float zoff, const WarpPath& w, int n,
-                               int lane) {
+// Recompute every cached factor of the path from its vertices; returns log p.
+template <bool kGen>
+__device__ float refresh_caches(const DMedium& M, const DPair& S, float zoff, const WarpPath& w, int n, int lane) {
+  float lp = 0.f;
   for (int i = lane; i < n; i += 32) {
     const float3 P = w.pos(i);
     const float3 Pp = (i >= 1) ? w.pos(i - 1) : P;
     const float3 Pn = (i <= n - 2) ? w.pos(i + 1) : P;
-    float g;
-    w.vt[i] = vertex_term(M, S, zoff, Pp, P, Pn, i, n, g);
-    w.gt[i] = g;
+    float vt, gt, seg, tb, len;
+    vertex_and_segment<kGen>(M, S, zoff, Pp, P, Pn, i, n, vt, gt, seg, tb, len);
+    w.vt[i] = vt;
+    w.gt[i] = gt;
+    lp += vt;
     if (i <= n - 2) {
-      const SegOut so = segment_term(M, S, zoff, P, Pn, i <= n - 3);
-      w.seg[i] = so.seg;
-      w.tb[i] = so.tb;
-      w.len[i] = so.len;
+      w.seg[i] = seg;
+      w.tb[i] = tb;
+      w.len[i] = len;
+      lp += seg;
     }
   }
   __syncwarp();
+  return warp_sum(lp);
 }
 
 // Shift entries [a, e) of the vertex-indexed and segment-indexed arrays.
@@ -145,12 +196,11 @@ __device__ int select_segment(const WarpPath& w, int nseg, float u, float& total
 }
 
 struct Accum {
-  // FP32 / integer partials of the current flush interval
-  unsigned long long pn2, pn;
-  float pL, pL2, pG;
+  unsigned long long pn2, pn;  // integer partials of the current flush interval
+  float pL, pL2, pG;           // FP32 partials of the current flush interval
   unsigned int dwell, nflush;
   unsigned int prop[4], acc[4];
-  double my;  // lane-distributed FP64 accumulator word `lane` (lanes 0..15)
+  double my;                   // lane-distributed FP64 accumulator word `lane` (lanes 0..15)
 };
 
 __device__ __forceinline__ void add_dwell(Accum& a, int n, float L, float G) {
@@ -179,13 +229,21 @@ __device__ __forceinline__ void flush64(Accum& a, int lane) {
   a.nflush = 0;
 }
 
-__global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
-  extern __shared__ float smem[];
+// Pre-transformed random numbers of one step (8 staged words):
+//   lo.x = 23-bit index draw | move type << 24, lo.y = log u (accept),
+//   within: lo.z, lo.w, hi.x = standard normals, hi.y = vMF cosine,
+//           hi.z, hi.w = cos, sin of the vMF azimuth
+//   birth:  lo.z = u for cos s, lo.w = sinh t, hi.x = cosh t, hi.y, hi.z = cos, sin of phi
+template <bool kGen>
+__global__ void __launch_bounds__(128, kGen ? 5 : 8) chain_kernel(const ChainParams P) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int cap_s = P.smem_cap;
+  const size_t per_warp = static_cast<size_t>(8) * cap_s + 32 * kRngWords;
   WarpPath w;
-  w.x = smem + static_cast<size_t>(wib) * 8 * cap_s;
+  w.x = smem + static_cast<size_t>(wib) * per_warp;
   w.y = w.x + cap_s;
   w.z = w.y + cap_s;
   w.tb = w.z + cap_s;
@@ -193,6 +251,7 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
   w.len = w.seg + cap_s;
   w.vt = w.len + cap_s;
   w.gt = w.vt + cap_s;
+  uint4* rng = reinterpret_cast<uint4*>(w.gt + cap_s);  // [32][2] uint4
   const DMedium& M = P.M;
   const DRun& R = P.R;
   const uint32_t key0 = static_cast<uint32_t>(R.seed), key1 = static_cast<uint32_t>(R.seed >> 32);
@@ -218,12 +277,12 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
     float* gz = gy + cap;
     for (int i = lane; i < n; i += 32) { w.x[i] = gx[i]; w.y[i] = gy[i]; w.z[i] = gz[i]; }
     __syncwarp();
-    refresh_caches(M, S, zoff, w, n, lane);
-    Sums sm = path_sums(w, n, lane);
-    if (!isfinite(sm.lp)) {
+    const float lp0 = refresh_caches<kGen>(M, S, zoff, w, n, lane);
+    if (!isfinite(lp0)) {
       if (lane == 0) { P.status[c] |= ST_NONFINITE; atomicOr(P.any_status, ST_NONFINITE); }
       continue;
     }
+    Sums sm = path_sums(w, n, lane);
     float L = sm.L, G = sm.G;
 
     Accum A;
@@ -240,87 +299,85 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
     for (unsigned long long s0 = 0; s0 < P.n_steps; s0 += 32) {
       if ((s0 & 1023ull) == 0 && P.abort_flag != nullptr && *P.abort_flag) { aborted = true; break; }
       // ---- lane-parallel random numbers of steps step0+s0 .. +31 ----
-      const unsigned long long tl = step0 + s0 + lane;
-      const uint4 ra = philox4x32_10(make_uint4(static_cast<uint32_t>(tl), static_cast<uint32_t>(tl >> 32),
-                                                static_cast<uint32_t>(c), PUR_STEP_A), key0, key1);
-      const uint4 rb = philox4x32_10(make_uint4(static_cast<uint32_t>(tl), static_cast<uint32_t>(tl >> 32),
-                                                static_cast<uint32_t>(c), PUR_STEP_B), key0, key1);
-      const uint32_t um = ra.x >> 9;
-      const uint32_t type = um < R.thr_within ? 0u : (um < R.thr_birth ? 2u : 3u);
-      const uint32_t w0l = (ra.y >> 9) | (type << 24);
-      const float logul = logf(u01(ra.z));
-      float q0, q1, q2, q3, q4, q5;
       {
+        const unsigned long long tl = step0 + s0 + lane;
+        const uint4 ra = philox4x32_10(make_uint4(static_cast<uint32_t>(tl), static_cast<uint32_t>(tl >> 32),
+                                                  static_cast<uint32_t>(c), PUR_STEP_A), key0, key1);
+        const uint4 rb = philox4x32_10(make_uint4(static_cast<uint32_t>(tl), static_cast<uint32_t>(tl >> 32),
+                                                  static_cast<uint32_t>(c), PUR_STEP_B), key0, key1);
+        const uint32_t um = ra.x >> 9;
+        const uint32_t type = um < R.thr_within ? 0u : (um < R.thr_birth ? 2u : 3u);
+        uint4 lo = make_uint4((ra.y >> 9) | (type << 24), __float_as_uint(__logf(u01(ra.z))), 0u, 0u);
+        uint4 hi;
         const float ub0 = u01(rb.x), ub1 = u01(rb.y), ub2 = u01(rb.z), ub3 = u01(rb.w);
         if (type == 0u) {
-          // Gaussian triple (Box-Muller) and vMF end-move cosine / azimuth
           float s1, c1, s2, c2;
-          const float r1 = sqrtf(-2.0f * logf(ub0));
+          const float r1 = m_sqrt<true>(-2.0f * __logf(ub0));
           sincospif(2.0f * ub1, &s1, &c1);
-          const float r2 = sqrtf(-2.0f * logf(ub2));
+          const float r2 = m_sqrt<true>(-2.0f * __logf(ub2));
           sincospif(2.0f * ub3, &s2, &c2);
-          q0 = r1 * c1;
-          q1 = r1 * s1;
-          q2 = r2 * c2;
-          q3 = 1.0f + logf(fmaf(1.0f - ub0, S.exp_m2ke, ub0)) / S.kappa_end;
-          q4 = c1;
-          q5 = s1;
+          lo.z = __float_as_uint(r1 * c1);
+          lo.w = __float_as_uint(r1 * s1);
+          const float wv = 1.0f + __fdividef(__logf(fmaf(1.0f - ub0, S.exp_m2ke, ub0)), S.kappa_end);
+          hi = make_uint4(__float_as_uint(r2 * c2), __float_as_uint(wv), __float_as_uint(c1), __float_as_uint(s1));
         } else {
-          // birth: u for cos s, sinh t / cosh t of the logistic t, azimuth
-          const float et = ub1 / (1.0f - ub1);
-          const float iet = (1.0f - ub1) / ub1;
+          const float et = __fdividef(ub1, 1.0f - ub1);
+          const float iet = __fdividef(1.0f - ub1, ub1);
           float s3, c3;
           sincospif(2.0f * ub2, &s3, &c3);
-          q0 = ub0;
-          q1 = 0.5f * (et - iet);
-          q2 = 0.5f * (et + iet);
-          q3 = c3;
-          q4 = s3;
-          q5 = 0.0f;
+          lo.z = __float_as_uint(ub0);
+          lo.w = __float_as_uint(0.5f * (et - iet));
+          hi = make_uint4(__float_as_uint(0.5f * (et + iet)), __float_as_uint(c3), __float_as_uint(s3), 0u);
         }
+        __syncwarp();
+        rng[2 * lane] = lo;
+        rng[2 * lane + 1] = hi;
+        __syncwarp();
       }
       const int cnt = static_cast<int>(min(32ull, P.n_steps - s0));
       for (int i = 0; i < cnt; ++i) {
-        const uint32_t w0 = __shfl_sync(kFull, w0l, i);
-        const float logu = __shfl_sync(kFull, logul, i);
-        const float p0 = __shfl_sync(kFull, q0, i);
-        const float p1 = __shfl_sync(kFull, q1, i);
-        const float p2 = __shfl_sync(kFull, q2, i);
-        const float p3 = __shfl_sync(kFull, q3, i);
-        const float p4 = __shfl_sync(kFull, q4, i);
-        const float p5 = __shfl_sync(kFull, q5, i);
-        const uint32_t mtype = w0 >> 24;
-        const uint32_t v23 = w0 & 0x7fffffu;
+        const uint4 lo = rng[2 * i];
+        const uint4 hi = rng[2 * i + 1];
+        const uint32_t mtype = lo.x >> 24;
+        const uint32_t v23 = lo.x & 0x7fffffu;
+        const float logu = __uint_as_float(lo.y);
         const unsigned long long t = step0 + s0 + i;
 
         int move;
         bool proposed = true;
         int n_new = n, wlo = 0, nc = 0, olo = 0, onc = 0, jj = -1, kk = -1;
+        int inew = -1, sh_from = INT_MAX, sh_by = 0;
         float3 fnew = f3(0.f, 0.f, 0.f);
         float extra = 0.f;
         float3 gx_mala = f3(0.f, 0.f, 0.f);
         if (mtype == 0u) {
           const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 1)) >> 23);
           jj = j;
+          inew = j;
           if (j == n - 1) {
             move = MV_END;
             const float3 nu = sensor_normal(S, w.pos(j));
             float3 e1, e2;
             onb(nu, e1, e2);
-            const float wv = p3;
-            const float sw = sqrtf(fmaxf(0.f, 1.0f - wv * wv));
-            const float3 nn = wv * nu + sw * (p4 * e1 + p5 * e2);
+            const float wv = __uint_as_float(hi.y);
+            const float sw = m_sqrt<true>(fmaxf(0.f, 1.0f - wv * wv));
+            const float3 nn = wv * nu + sw * (__uint_as_float(hi.z) * e1 + __uint_as_float(hi.w) * e2);
             fnew = cS + (f3(S.c_lo[0], S.c_lo[1], S.c_lo[2]) + S.R * nn);
             wlo = n - 2; nc = 2; olo = n - 2; onc = 2;
           } else {
             move = MV_INTERIOR;
             const float3 fj = w.pos(j);
-            if (R.within == 1) {
-              gx_mala = grad_vertex(M, S, zoff, [&](int k) { return w.pos(k); }, n, j);
-              const float h = 0.5f * R.mala_eps * R.mala_eps;
-              fnew = fj + h * gx_mala + R.mala_eps * f3(p0, p1, p2);
+            const float3 z = f3(__uint_as_float(lo.z), __uint_as_float(lo.w), __uint_as_float(hi.x));
+            if constexpr (kGen) {
+              if (R.within == 1) {
+                gx_mala = grad_vertex(M, S, zoff, [&](int k) { return w.pos(k); }, n, j);
+                const float h = 0.5f * R.mala_eps * R.mala_eps;
+                fnew = fj + h * gx_mala + R.mala_eps * z;
+              } else {
+                fnew = fj + R.sigma * z;
+              }
             } else {
-              fnew = fj + R.sigma * f3(p0, p1, p2);
+              fnew = fj + R.sigma * z;
             }
             wlo = j - 1; nc = 3; olo = j - 1; onc = 3;
           }
@@ -335,21 +392,27 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
             kk = k;
             const float3 Af = w.pos(k), Bf = w.pos(k + 1);
             const float3 r = Bf - Af;
-            const float ell = sqrtf(dot(r, r));
-            const float gamma = 0.5f * ell;
-            const float3 rh = (1.0f / ell) * r;
+            const float rr = dot(r, r);
+            const float irl = rsqrtf(rr);
+            const float gamma = 0.5f * rr * irl;
+            const float3 rh = irl * r;
             float3 xi, ze;
             onb(rh, xi, ze);
             const float beta = insertion_beta(M, R, zoff, Af, Bf, gamma);
-            float cs = -1.0f - log1pf(p0 * expm1f(-2.0f * beta)) / beta;
+            const float u0 = __uint_as_float(lo.z);
+            float cs = -1.0f - __fdividef(__logf(fmaf(-u0, 1.0f - __expf(-2.0f * beta), 1.0f)), beta);
             cs = fminf(fmaxf(cs, -1.0f), 1.0f);
-            const float sn = sqrtf(fmaxf(0.f, (1.0f - cs) * (1.0f + cs)));
-            const float sc = gamma / (p2 - cs);
-            fnew = 0.5f * (Af + Bf) + sc * (p1 * rh + sn * (p3 * xi + p4 * ze));
+            const float sn = m_sqrt<true>(fmaxf(0.f, (1.0f - cs) * (1.0f + cs)));
+            const float sc = __fdividef(gamma, __uint_as_float(hi.x) - cs);
+            fnew = 0.5f * (Af + Bf) +
+                   sc * (__uint_as_float(lo.w) * rh + sn * (__uint_as_float(hi.y) * xi + __uint_as_float(hi.z) * ze));
             const float tbk = w.tb[k];
-            extra = R.log_pd - logf(static_cast<float>(n - 1)) - R.log_pb - logf(tbk / total) -
-                    log_insert_density(M, R, zoff, Af, Bf, fnew);
+            extra = R.log_pd - __logf(static_cast<float>(n - 1)) - R.log_pb - __logf(__fdividef(tbk, total)) -
+                    log_insert_density<true>(M, R, zoff, Af, Bf, fnew);
             n_new = n + 1;
+            inew = k + 1;
+            sh_from = k + 2;
+            sh_by = -1;
             wlo = k; nc = 3; olo = k; onc = 2;
           }
         } else {
@@ -360,43 +423,35 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
             const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 2)) >> 23);
             jj = j;
             n_new = n - 1;
+            sh_from = j;
+            sh_by = 1;
             wlo = j - 1; nc = 2; olo = j - 1; onc = 3;
           }
         }
 
         bool accept = false;
-        float dlp = 0.f, dtb = 0.f;
         float nvt = 0.f, ngt = 0.f, nseg = 0.f, ntb = 0.f, nlen = 0.f;
         float ogt = 0.f, olen = 0.f;
         if (proposed) {
-          // new-path vertex index -> position
+          // new-path vertex index -> position (old index shifted, or the new vertex)
           auto newpos = [&](int idx) -> float3 {
-            int o = idx;
-            bool isnew = false;
-            if (move == MV_BIRTH) {
-              isnew = (idx == kk + 1);
-              o = (idx > kk + 1) ? idx - 1 : idx;
-            } else if (move == MV_DEATH) {
-              o = (idx >= jj) ? idx + 1 : idx;
-            } else {
-              isnew = (idx == jj);
-            }
+            int o = idx + ((idx >= sh_from) ? sh_by : 0);
             o = min(max(o, 0), n - 1);
             const float3 q = w.pos(o);
-            return isnew ? fnew : q;
+            return (idx == inew) ? fnew : q;
           };
           float ovt = 0.f, oseg = 0.f, otb = 0.f;
           if (lane < nc) {
             const int v = wlo + lane;
             const float3 Pc = newpos(v);
-            const float3 Pp = (v >= 1) ? newpos(v - 1) : Pc;
-            const float3 Pn = (v <= n_new - 2) ? newpos(v + 1) : Pc;
-            nvt = vertex_term(M, S, zoff, Pp, Pc, Pn, v, n_new, ngt);
+            const float3 Pp = newpos(v - 1);
+            const float3 Pn = newpos(v + 1);
+            float seg_, tb_, len_;
+            vertex_and_segment<kGen>(M, S, zoff, Pp, Pc, Pn, v, n_new, nvt, ngt, seg_, tb_, len_);
             if (lane < nc - 1) {
-              const SegOut so = segment_term(M, S, zoff, Pc, Pn, v <= n_new - 3);
-              nseg = so.seg;
-              ntb = so.tb;
-              nlen = so.len;
+              nseg = seg_;
+              ntb = tb_;
+              nlen = len_;
             }
           }
           if (lane < onc) {
@@ -409,34 +464,35 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
               olen = w.len[o];
             }
           }
-          dlp = (nvt + nseg) - (ovt + oseg);
+          float dlp = (nvt + nseg) - (ovt + oseg);
           dlp += __shfl_xor_sync(kFull, dlp, 1);
           dlp += __shfl_xor_sync(kFull, dlp, 2);
           dlp = __shfl_sync(kFull, dlp, 0);
-          dtb = ntb - otb;
-          dtb += __shfl_xor_sync(kFull, dtb, 1);
-          dtb += __shfl_xor_sync(kFull, dtb, 2);
-          dtb = __shfl_sync(kFull, dtb, 0);
           if (move == MV_DEATH) {
+            float dtb = ntb - otb;
+            dtb += __shfl_xor_sync(kFull, dtb, 1);
+            dtb += __shfl_xor_sync(kFull, dtb, 2);
+            dtb = __shfl_sync(kFull, dtb, 0);
             // T_b of the reduced path, summed afresh so that decisions depend
             // only on the current state (split runs replay exactly)
             float part = 0.f;
-            for (int i = lane; i < n - 1; i += 32) part += w.tb[i];
+            for (int q = lane; q < n - 1; q += 32) part += w.tb[q];
             const float tb_new = __shfl_sync(kFull, ntb, 0);
             const float Tb_red = warp_sum(part) + dtb;
-            extra = -R.log_pd + logf(static_cast<float>(n - 2)) + R.log_pb + logf(tb_new / Tb_red) +
-                    log_insert_density(M, R, zoff, w.pos(jj - 1), w.pos(jj + 1), w.pos(jj));
+            extra = -R.log_pd + __logf(static_cast<float>(n - 2)) + R.log_pb + __logf(__fdividef(tb_new, Tb_red)) +
+                    log_insert_density<true>(M, R, zoff, w.pos(jj - 1), w.pos(jj + 1), w.pos(jj));
           }
-          if (move == MV_INTERIOR && R.within == 1 && isfinite(dlp)) {
-            const float3 gy = grad_vertex(M, S, zoff, newpos, n, jj);
-            const float h = 0.5f * R.mala_eps * R.mala_eps;
-            const float3 fj = w.pos(jj);
-            const float3 dfw = fnew - fj - h * gx_mala;
-            const float3 dbw = fj - fnew - h * gy;
-            extra = (dot(dfw, dfw) - dot(dbw, dbw)) / (2.0f * R.mala_eps * R.mala_eps);
+          if constexpr (kGen) {
+            if (move == MV_INTERIOR && R.within == 1 && isfinite(dlp)) {
+              const float3 gy = grad_vertex(M, S, zoff, newpos, n, jj);
+              const float h = 0.5f * R.mala_eps * R.mala_eps;
+              const float3 fj = w.pos(jj);
+              const float3 dfw = fnew - fj - h * gx_mala;
+              const float3 dbw = fj - fnew - h * gy;
+              extra = (dot(dfw, dfw) - dot(dbw, dbw)) / (2.0f * R.mala_eps * R.mala_eps);
+            }
           }
-          const float logA = dlp + extra;
-          accept = logu < logA;
+          accept = logu < dlp + extra;
         }
         A.prop[move]++;
         if (accept) {
@@ -466,10 +522,9 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainParams P) {
             }
           }
           if (lane == 0 && move != MV_DEATH) {
-            const int at = (move == MV_BIRTH) ? kk + 1 : jj;
-            w.x[at] = fnew.x;
-            w.y[at] = fnew.y;
-            w.z[at] = fnew.z;
+            w.x[inew] = fnew.x;
+            w.y[inew] = fnew.y;
+            w.z[inew] = fnew.z;
           }
           __syncwarp();
           n = n_new;
@@ -565,26 +620,35 @@ __global__ void init_kernel(const InitParams p) {
   for (int k = 0; k < ACC_WORDS; ++k) p.acc[static_cast<size_t>(c) * ACC_WORDS + k] = 0.0;
 }
 
+template <bool kGen>
+cudaError_t set_attributes(int smem_bytes) {
+  cudaError_t e = cudaFuncSetAttribute(chain_kernel<kGen>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(chain_kernel<kGen>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
 }  // namespace
 
 size_t chain_smem_bytes(int smem_cap, int warps_per_block) {
-  return static_cast<size_t>(warps_per_block) * 8u * static_cast<size_t>(smem_cap) * sizeof(float);
+  return static_cast<size_t>(warps_per_block) * (8u * static_cast<size_t>(smem_cap) + 32u * kRngWords) *
+         sizeof(float);
 }
 
-cudaError_t chain_kernel_attributes(int smem_bytes) {
-  return cudaFuncSetAttribute(chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-}
-
-cudaError_t chain_occupancy(int warps_per_block, int smem_cap, int* blocks_per_sm) {
+cudaError_t chain_occupancy(bool general, int warps_per_block, int smem_cap, int* blocks_per_sm) {
   const size_t sm = chain_smem_bytes(smem_cap, warps_per_block);
-  cudaError_t e = chain_kernel_attributes(static_cast<int>(sm));
+  cudaError_t e = general ? set_attributes<true>(static_cast<int>(sm)) : set_attributes<false>(static_cast<int>(sm));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel, warps_per_block * 32, sm);
+  if (general)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<true>, warps_per_block * 32, sm);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<false>, warps_per_block * 32, sm);
 }
 
-cudaError_t launch_chain(const ChainParams& p, int grid, int warps_per_block, cudaStream_t s) {
+cudaError_t launch_chain(const ChainParams& p, bool general, int grid, int warps_per_block, cudaStream_t s) {
   const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block);
-  chain_kernel<<<grid, warps_per_block * 32, sm, s>>>(p);
+  if (general)
+    chain_kernel<true><<<grid, warps_per_block * 32, sm, s>>>(p);
+  else
+    chain_kernel<false><<<grid, warps_per_block * 32, sm, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -78,6 +78,38 @@ __device__ __forceinline__ float dot(float3 a, float3 b) { return fmaf(a.x, b.x,
 __device__ __forceinline__ float3 ld3(const float* p) { return f3(p[0], p[1], p[2]); }
 
 // ---------------------------------------------------------------------------
+// Math policy: F = false uses the accurate CUDA functions (density kernels on
+// caller batches, compared with the FP64 oracle to 1e-5); F = true uses the
+// SFU approximations (chain kernel: a few ulp, far below the Monte-Carlo
+// error, and every decision stays a function of the stored FP32 state).
+// ---------------------------------------------------------------------------
+template <bool F>
+__device__ __forceinline__ float m_log(float x) {
+  if constexpr (F) return __logf(x);
+  else return logf(x);
+}
+template <bool F>
+__device__ __forceinline__ float m_exp(float x) {
+  if constexpr (F) return __expf(x);
+  else return expf(x);
+}
+template <bool F>
+__device__ __forceinline__ float m_sqrt(float x) {
+  if constexpr (F) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  } else {
+    return sqrtf(x);
+  }
+}
+template <bool F>
+__device__ __forceinline__ float m_div(float a, float b) {
+  if constexpr (F) return __fdividef(a, b);
+  else return a / b;
+}
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11), counter (c0..c3), key (k0, k1)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
@@ -168,25 +200,27 @@ __device__ __forceinline__ void seg_tau(const DMedium& M, float zP, float zQ, fl
 // directions a (incoming) and b (outgoing), and its derivative in g.
 // 1 - cos and 1 + cos come from |a - b|^2 / 2 and |a + b|^2 / 2, which stay
 // accurate for the forward-peaked angles that dominate at g ~ 0.9.
+template <bool F = false, bool kMix = true>
 __device__ __forceinline__ float phase_term(const DMedium& M, float3 a, float3 b, float& gterm) {
-  const float3 dm = a - b, dp = a + b;
+  const float3 dm = a - b;
   const float omc = 0.5f * dot(dm, dm);
-  const float opc = 0.5f * dot(dp, dp);
   const float den = fmaf(M.two_g, omc, M.omg2);
-  const float lhg = fmaf(-1.5f, logf(den), M.hg_lognorm);
-  const float ghg = M.hg_dg0 - 3.0f * (M.g - 1.0f + omc) / den;
-  if (M.f_sl <= 0.0f) {
+  const float lhg = fmaf(-1.5f, m_log<F>(den), M.hg_lognorm);
+  const float ghg = M.hg_dg0 - 3.0f * m_div<F>(M.g - 1.0f + omc, den);
+  if (!kMix || M.f_sl <= 0.0f) {
     gterm = ghg;
     return lhg;
   }
-  const float lv = logf(0.5f * opc);
+  const float3 dp = a + b;
+  const float opc = 0.5f * dot(dp, dp);
+  const float lv = m_log<F>(0.5f * opc);
   const float lsl = fmaf(M.sl_alpha, lv, M.sl_lognorm);
   const float gsl = fmaf(M.sl_dg1, lv, M.sl_dg0);
   const float mx = fmaxf(lhg, lsl);
-  const float wh = (1.0f - M.f_sl) * expf(lhg - mx);
-  const float ws = M.f_sl * expf(lsl - mx);
-  gterm = (wh * ghg + ws * gsl) / (wh + ws);
-  return mx + logf(wh + ws);
+  const float wh = (1.0f - M.f_sl) * m_exp<F>(lhg - mx);
+  const float ws = M.f_sl * m_exp<F>(lsl - mx);
+  gterm = m_div<F>(wh * ghg + ws * gsl, wh + ws);
+  return mx + m_log<F>(wh + ws);
 }
 
 // d log sigma / d cos(theta) for unit directions a, b.
@@ -222,11 +256,12 @@ __device__ __forceinline__ float3 sensor_normal(const DPair& P, float3 e) {
 
 // Detection factor of p_f without its 1/|r|^2: log max(0, -a . nu) + log rho(nu)
 // (Eq. detection_prob), for the last direction a and end vertex e.
+template <bool F = false>
 __device__ __forceinline__ float sensor_term(const DPair& P, float3 a, float3 e) {
   const float3 nu = sensor_normal(P, e);
   const float cphi = -dot(a, nu);
   if (!(cphi > 0.0f)) return kNegInf;
-  float t = logf(cphi);
+  float t = m_log<F>(cphi);
   if (P.rho != 0) {
     const float x = dot(nu, f3(P.rho_hat[0], P.rho_hat[1], P.rho_hat[2]));
     t += fmaf(3.0f, x, -1.0f) - logf(coshf(fmaf(2.0f, x, 0.7f)));
@@ -402,17 +437,18 @@ __device__ __forceinline__ float insertion_beta(const DMedium& M, const DRun& R,
   return fmaxf(beta, R.beta_min);
 }
 
+template <bool F = false>
 __device__ __forceinline__ float log_insert_density(const DMedium& M, const DRun& R, float zoff, float3 A,
                                                     float3 B, float3 f) {
   const float3 ab = B - A;
-  const float gamma = 0.5f * sqrtf(dot(ab, ab));
+  const float gamma = 0.5f * m_sqrt<F>(dot(ab, ab));
   const float3 u = A - f, w = B - f;
-  const float d1 = sqrtf(dot(u, u)), d2 = sqrtf(dot(w, w));
-  const float cs = dot(u, w) / (d1 * d2);
+  const float d1 = m_sqrt<F>(dot(u, u)), d2 = m_sqrt<F>(dot(w, w));
+  const float cs = m_div<F>(dot(u, w), d1 * d2);
   const float beta = insertion_beta(M, R, zoff, A, B, gamma);
-  const float log2sinh = beta + logf(-expm1f(-2.0f * beta));
-  return logf(beta) - beta * cs - log2sinh + 3.0f * logf(2.0f * gamma) -
-         2.0f * logf(d1 * d2 * (d1 + d2)) - kLog2Pi;
+  const float log2sinh = beta + m_log<F>(1.0f - m_exp<F>(-2.0f * beta));
+  return m_log<F>(beta) - beta * cs - log2sinh + 3.0f * m_log<F>(2.0f * gamma) -
+         2.0f * m_log<F>(d1 * d2 * (d1 + d2)) - kLog2Pi;
 }
 
 }  // namespace pmc

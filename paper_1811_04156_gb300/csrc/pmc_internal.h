@@ -56,10 +56,11 @@ struct ChainParams {
 };
 
 // Kernel launchers (pmc_chain.cu)
-cudaError_t launch_chain(const ChainParams& p, int grid, int warps_per_block, cudaStream_t s);
+// `general` selects the instantiation with layered media, vMF emission, the
+// detection probability, the simplified-Liu mixture and MALA moves.
+cudaError_t launch_chain(const ChainParams& p, bool general, int grid, int warps_per_block, cudaStream_t s);
 size_t chain_smem_bytes(int smem_cap, int warps_per_block);
-cudaError_t chain_kernel_attributes(int smem_bytes);
-cudaError_t chain_occupancy(int warps_per_block, int smem_cap, int* blocks_per_sm);
+cudaError_t chain_occupancy(bool general, int warps_per_block, int smem_cap, int* blocks_per_sm);
 
 struct InitParams {
   DRun R;

@@ -177,7 +177,9 @@ def test_split_runs_and_checkpoint_are_bit_exact(api, ctx):
     assert np.array_equal(na, nb) and np.array_equal(xa, xb) and np.array_equal(sa, sb)
     aa, ab = a.read_accumulators(), b.read_accumulators()
     assert np.array_equal(aa[:, 8:], ab[:, 8:])          # proposal / acceptance counts
-    assert np.allclose(aa[:, :8], ab[:, :8], rtol=1e-6)  # FP32 partial sums flush at other points
+    # FP32 partial sums are flushed into the FP64 words at other points
+    scale = np.abs(aa[:, :8]).max(axis=0) + 1.0
+    assert np.all(np.abs(aa[:, :8] - ab[:, :8]) <= 1e-5 * scale)
     b.load_state(blob)
     b.run_steps(1000)
     xc, nc_, _ = b.read_states()
