@@ -319,6 +319,30 @@ PMC_API int pmc_trace(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int p
               uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
               int max_scatter, double* out, void* stream);
 
+/* Allocation-free forward tracer for callers that cannot allocate device
+ * memory (an application whose own pool allocator has reserved the device, a
+ * fixed memory budget, or a path that must not take the device-wide
+ * synchronisation of cudaMalloc / cudaFree).  The paper has no counterpart:
+ * it computes what pmc_trace computes, for each of the n_pairs pairs listed
+ * in pair_ids (host array), with every pair traced from photon0 with the same
+ * seed, and writes 5 doubles per pair to `out` (host, n_pairs * 5, layout of
+ * pmc_trace).  Its accumulators live in a fixed device array of
+ * PMC_NOALLOC_MAX_PAIRS * 5 doubles that every GPU loading the library holds
+ * until the process exits; the call performs no device allocation.
+ *  - n_pairs must be in [1, PMC_NOALLOC_MAX_PAIRS]; larger values fail with
+ *    PMC_ERR_INVALID.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls on a device share the array: calls whose work overlaps on the
+ *    GPU (other streams or other host threads) race and corrupt each other's
+ *    results.  Each call clears the slots it uses before tracing.
+ *  - Synchronises `stream`. */
+#define PMC_NOALLOC_MAX_PAIRS 128
+PMC_API int pmc_trace_noalloc(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, const int* pair_ids,
+                              int n_pairs, uint64_t seed, uint64_t photon0, uint64_t n_photons,
+                              double r_reject, int max_scatter, double* out, void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 PMC_API const char* pmc_last_error(void);
 

@@ -18,6 +18,7 @@ ERRORS = {1: "PMC_ERR_INVALID", 2: "PMC_ERR_OOM", 3: "PMC_ERR_CUDA", 4: "PMC_ERR
 PMC_FLAG_GRADIENTS = 1
 PMC_FLAG_NO_GRAPH = 2
 PMC_ACC_WORDS = 16
+PMC_NOALLOC_MAX_PAIRS = 128
 
 
 class PathmcError(RuntimeError):
@@ -110,6 +111,8 @@ PROTOTYPES = {
     "pmc_score": ([_vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp], C.c_int),
     "pmc_trace": ([_vp, _vp, _vp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int, _dp, _vp],
                   C.c_int),
+    "pmc_trace_noalloc": ([_vp, _vp, _vp, _ip, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int,
+                           _dp, _vp], C.c_int),
     "pmc_last_error": ([], C.c_char_p),
     "pmc_version": ([], C.c_char_p),
 }

@@ -345,6 +345,19 @@ def trace(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: int, n_
             "mean_L": out[4] / out[0] if out[0] > 0 else float("nan"), "raw": out}
 
 
+def trace_noalloc(ctx: Context, medium: Medium, geom: Geometry, pairs, seed: int, n_photons: int,
+                  photon0: int = 0, r_reject: float = math.inf, max_scatter: int = 1 << 30, stream=None):
+    """Allocation-free GPU tracer over several pairs (pmc_trace_noalloc): raw
+    sums per pair, shape (len(pairs), 5), in the layout of pmc_trace."""
+    ids = np.ascontiguousarray(pairs, dtype=np.int32)
+    out = np.zeros((len(ids), 5))
+    check(load().pmc_trace_noalloc(ctx.handle, medium.handle, geom.handle, ids.ctypes.data_as(C.POINTER(C.c_int)),
+                                   len(ids), int(seed), int(photon0), int(n_photons), float(r_reject),
+                                   int(min(max_scatter, 2**31 - 1)), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                   _stream(stream)), "pmc_trace_noalloc")
+    return out
+
+
 class LogP(torch.autograd.Function):
     """log p of a batch of paths; backward is the hand-written adjoint kernel."""
 

@@ -912,4 +912,24 @@ int pmc_trace(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, uint64
   return PMC_OK;
 }
 
+int pmc_trace_noalloc(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const int* pair_ids, int n_pairs,
+                      uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject, int max_scatter,
+                      double* out, void* stream) {
+  if (!ctx || !med || !geom || !pair_ids || !out) return fail(PMC_ERR_INVALID, "bad argument");
+  if (n_pairs < 1 || n_pairs > PMC_NOALLOC_MAX_PAIRS)
+    return fail(PMC_ERR_INVALID, "n_pairs must be in [1, PMC_NOALLOC_MAX_PAIRS]");
+  if (max_scatter < 0 || !(r_reject > 0)) return fail(PMC_ERR_INVALID, "bad tracer limits");
+  DPair sel[kNoAllocMaxPairs];
+  for (int i = 0; i < n_pairs; ++i) {
+    const DPair* d = pair_of(geom, pair_ids[i], false);
+    if (d == nullptr) return fail(PMC_ERR_INVALID, "pair id out of range");
+    sel[i] = *d;
+  }
+  CK(cudaSetDevice(ctx->device));
+  const float rr = std::isfinite(r_reject) ? static_cast<float>(r_reject) : std::numeric_limits<float>::infinity();
+  CK(launch_trace_noalloc(med->d, sel, n_pairs, seed, photon0, n_photons, rr, max_scatter, out, ctx->device,
+                          ctx->n_sm, static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
 }  // extern "C"

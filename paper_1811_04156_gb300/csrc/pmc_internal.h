@@ -113,4 +113,10 @@ cudaError_t launch_trace(const DMedium& M, const DPair& S, unsigned long long se
                          unsigned long long photon0, unsigned long long n_photons, float r_reject,
                          int max_scatter, double* out5, int n_sm, cudaStream_t s);
 
+// pmc_noalloc.cu: allocation-free tracer over up to kNoAllocMaxPairs pairs.
+constexpr int kNoAllocMaxPairs = 128;
+cudaError_t launch_trace_noalloc(const DMedium& M, const DPair* pairs, int n_pairs, unsigned long long seed,
+                                 unsigned long long photon0, unsigned long long n_photons, float r_reject,
+                                 int max_scatter, double* host_out, int device, int n_sm, cudaStream_t s);
+
 }  // namespace pmc
