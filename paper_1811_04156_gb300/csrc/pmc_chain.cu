@@ -35,6 +35,8 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRefreshSteps = 256;  // recompute the running sums from the caches
 constexpr int kFlushAccepts = 64;   // FP32 partials -> FP64 accumulators
 constexpr int kRngWords = 8;        // staged words per step
+constexpr int kPairWords = 64;      // shared slot for the pair constants (floats)
+static_assert(sizeof(DPair) <= kPairWords * sizeof(float), "pair slot too small");
 
 enum Move { MV_INTERIOR = 0, MV_END = 1, MV_BIRTH = 2, MV_DEATH = 3 };
 
@@ -77,7 +79,7 @@ __device__ __forceinline__ void vertex_and_segment(const DMedium& M, const DPair
     tb = tbv;
     len = ell;
     if (!(bb > 0.0f)) seg = kNegInf;
-    if (v <= n - 3 && hits_ball(S, Pc, b0)) seg = kNegInf;
+    if (v <= n - 3 && hits_ball<F>(S, Pc, b0)) seg = kNegInf;
   }
   if (v == 0) {
     if constexpr (kGen) vt = emission_term(S, b);
@@ -167,6 +169,18 @@ __device__ void shift_left(const WarpPath& w, int a, int e_vtx, int e_seg, int l
 
 // Segment chosen for a birth: smallest k with cumsum_k(tau_b) > u * T_b.
 __device__ int select_segment(const WarpPath& w, int nseg, float u, float& total, int lane) {
+  if (nseg <= 32) {
+    // one segment per lane: inclusive scan, then the first lane past the target
+    float incl = (lane < nseg) ? w.tb[lane] : 0.f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    total = __shfl_sync(kFull, incl, 31);
+    const unsigned over = __ballot_sync(kFull, lane < nseg && incl > u * total);
+    return over ? (__ffs(over) - 1) : (nseg - 1);
+  }
   const int m = (nseg + 31) >> 5;
   const int lo = lane * m;
   const int hi = min(lo + m, nseg);
@@ -198,20 +212,28 @@ __device__ int select_segment(const WarpPath& w, int nseg, float u, float& total
 struct Accum {
   unsigned long long pn2, pn;  // integer partials of the current flush interval
   float pL, pL2, pG;           // FP32 partials of the current flush interval
-  unsigned int dwell, nflush;
-  unsigned int prop[4], acc[4];
+  unsigned long long t_a;      // step from which the current state is recorded
+  unsigned int nflush;
+  unsigned int prop_w, prop_end, prop_b, prop_d;  // proposals: within (all), end, birth, death
+  unsigned int acc_i, acc_e, acc_b, acc_d;        // acceptances per move kind
   double my;                   // lane-distributed FP64 accumulator word `lane` (lanes 0..15)
 };
 
-__device__ __forceinline__ void add_dwell(Accum& a, int n, float L, float G) {
-  if (a.dwell == 0) return;
-  const float dw = static_cast<float>(a.dwell);
-  a.pn2 += (n == 2) ? a.dwell : 0u;
-  a.pn += static_cast<unsigned long long>(n) * a.dwell;
+// The state that became current at step t_a is recorded at every step in
+// [t_a, t_b) at or after burn-in, t_b being the step that replaces it; its
+// observables enter the sums once, weighted by that count.
+__device__ __forceinline__ void close_state(Accum& a, unsigned long long t_b, unsigned long long burn_in, int n,
+                                            float L, float G) {
+  const unsigned long long from = a.t_a > burn_in ? a.t_a : burn_in;
+  a.t_a = t_b;
+  if (t_b <= from) return;
+  const unsigned long long d = t_b - from;
+  const float dw = static_cast<float>(d);
+  a.pn2 += (n == 2) ? d : 0ull;
+  a.pn += static_cast<unsigned long long>(n) * d;
   a.pL = fmaf(L, dw, a.pL);
   a.pL2 = fmaf(L * L, dw, a.pL2);
   a.pG = fmaf(G, dw, a.pG);
-  a.dwell = 0;
   a.nflush++;
 }
 
@@ -235,13 +257,13 @@ __device__ __forceinline__ void flush64(Accum& a, int lane) {
 //           hi.z, hi.w = cos, sin of the vMF azimuth
 //   birth:  lo.z = u for cos s, lo.w = sinh t, hi.x = cosh t, hi.y, hi.z = cos, sin of phi
 template <bool kGen>
-__global__ void __launch_bounds__(128, kGen ? 5 : 8) chain_kernel(const ChainParams P) {
+__global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainParams P) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int cap_s = P.smem_cap;
-  const size_t per_warp = static_cast<size_t>(8) * cap_s + 32 * kRngWords;
+  const size_t per_warp = static_cast<size_t>(8) * cap_s + 32 * kRngWords + kPairWords;
   WarpPath w;
   w.x = smem + static_cast<size_t>(wib) * per_warp;
   w.y = w.x + cap_s;
@@ -252,6 +274,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 8) chain_kernel(const ChainPar
   w.vt = w.len + cap_s;
   w.gt = w.vt + cap_s;
   uint4* rng = reinterpret_cast<uint4*>(w.gt + cap_s);  // [32][2] uint4
+  DPair* spair = reinterpret_cast<DPair*>(rng + 64);
   const DMedium& M = P.M;
   const DRun& R = P.R;
   const uint32_t key0 = static_cast<uint32_t>(R.seed), key1 = static_cast<uint32_t>(R.seed >> 32);
@@ -263,7 +286,14 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 8) chain_kernel(const ChainPar
     if (P.chain_lo + item >= P.chain_hi) break;
     const int c = P.order[P.chain_lo + item];
 
-    const DPair S = P.pairs[P.chain_pair[c]];
+    // pair constants, staged in the warp's shared slot
+    {
+      const int* src = reinterpret_cast<const int*>(P.pairs + P.chain_pair[c]);
+      int* dst = reinterpret_cast<int*>(spair);
+      for (int q = lane; q < static_cast<int>(sizeof(DPair) / sizeof(int)); q += 32) dst[q] = src[q];
+      __syncwarp();
+    }
+    const DPair& S = *spair;
     const float zoff = S.zoff;
     const int cap = S.cap;
     int n = P.n[c];
@@ -288,9 +318,10 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 8) chain_kernel(const ChainPar
     Accum A;
     A.pn2 = A.pn = 0;
     A.pL = A.pL2 = A.pG = 0.f;
-    A.dwell = A.nflush = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) A.prop[k] = A.acc[k] = 0;
+    A.t_a = step0;
+    A.nflush = 0;
+    A.prop_w = A.prop_end = A.prop_b = A.prop_d = 0;
+    A.acc_i = A.acc_e = A.acc_b = A.acc_d = 0;
     A.my = (lane < ACC_WORDS) ? P.acc[static_cast<size_t>(c) * ACC_WORDS + lane] : 0.0;
 
     const float3 cS = f3(S.c[0], S.c[1], S.c[2]);
@@ -333,6 +364,12 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 8) chain_kernel(const ChainPar
         rng[2 * lane] = lo;
         rng[2 * lane + 1] = hi;
         __syncwarp();
+        // proposals of this batch by kind (within-dimension moves split into
+        // interior and end moves at the step)
+        const unsigned live = (s0 + lane < P.n_steps) ? 1u : 0u;
+        A.prop_w += __popc(__ballot_sync(kFull, live && type == 0u));
+        A.prop_b += __popc(__ballot_sync(kFull, live && type == 2u));
+        A.prop_d += __popc(__ballot_sync(kFull, live && type == 3u));
       }
       const int cnt = static_cast<int>(min(32ull, P.n_steps - s0));
       for (int i = 0; i < cnt; ++i) {
@@ -356,6 +393,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 8) chain_kernel(const ChainPar
           inew = j;
           if (j == n - 1) {
             move = MV_END;
+            A.prop_end++;
             const float3 nu = sensor_normal(S, w.pos(j));
             float3 e1, e2;
             onb(nu, e1, e2);
@@ -494,10 +532,12 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 8) chain_kernel(const ChainPar
           }
           accept = logu < dlp + extra;
         }
-        A.prop[move]++;
         if (accept) {
-          A.acc[move]++;
-          add_dwell(A, n, L, G);
+          A.acc_i += (move == MV_INTERIOR);
+          A.acc_e += (move == MV_END);
+          A.acc_b += (move == MV_BIRTH);
+          A.acc_d += (move == MV_DEATH);
+          close_state(A, t, R.burn_in, n, L, G);
           float dlen = nlen - olen;
           float dg = ngt - ogt;
           dlen += __shfl_xor_sync(kFull, dlen, 1);
@@ -532,16 +572,15 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 8) chain_kernel(const ChainPar
           G += dg;
           if (A.nflush >= kFlushAccepts) flush64(A, lane);
         }
-        if (t >= R.burn_in) A.dwell++;
-        if (((t + 1) & (kRefreshSteps - 1)) == 0) {
-          const Sums s2 = path_sums(w, n, lane);
-          L = s2.L;
-          G = s2.G;
-        }
       }
       done += cnt;
+      if (((s0 + 32) & (kRefreshSteps - 1)) == 0) {
+        const Sums s2 = path_sums(w, n, lane);
+        L = s2.L;
+        G = s2.G;
+      }
     }
-    add_dwell(A, n, L, G);
+    close_state(A, step0 + done, R.burn_in, n, L, G);
     flush64(A, lane);
     // recorded states, proposal and acceptance counts
     const unsigned long long t_end = step0 + done;
@@ -549,11 +588,14 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 8) chain_kernel(const ChainPar
     const double nrec = t_end > first ? static_cast<double>(t_end - first) : 0.0;
     double extra_w = 0.0;
     if (lane == ACC_NREC) extra_w = nrec;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (lane == ACC_PROP + k) extra_w = static_cast<double>(A.prop[k]);
-      if (lane == ACC_ACC + k) extra_w = static_cast<double>(A.acc[k]);
-    }
+    if (lane == ACC_PROP + 0) extra_w = static_cast<double>(A.prop_w - A.prop_end);
+    if (lane == ACC_PROP + 1) extra_w = static_cast<double>(A.prop_end);
+    if (lane == ACC_PROP + 2) extra_w = static_cast<double>(A.prop_b);
+    if (lane == ACC_PROP + 3) extra_w = static_cast<double>(A.prop_d);
+    if (lane == ACC_ACC + 0) extra_w = static_cast<double>(A.acc_i);
+    if (lane == ACC_ACC + 1) extra_w = static_cast<double>(A.acc_e);
+    if (lane == ACC_ACC + 2) extra_w = static_cast<double>(A.acc_b);
+    if (lane == ACC_ACC + 3) extra_w = static_cast<double>(A.acc_d);
     A.my += extra_w;
     if (lane < ACC_WORDS) P.acc[static_cast<size_t>(c) * ACC_WORDS + lane] = A.my;
     for (int i = lane; i < n; i += 32) { gx[i] = w.x[i]; gy[i] = w.y[i]; gz[i] = w.z[i]; }
@@ -630,8 +672,8 @@ cudaError_t set_attributes(int smem_bytes) {
 }  // namespace
 
 size_t chain_smem_bytes(int smem_cap, int warps_per_block) {
-  return static_cast<size_t>(warps_per_block) * (8u * static_cast<size_t>(smem_cap) + 32u * kRngWords) *
-         sizeof(float);
+  return static_cast<size_t>(warps_per_block) *
+         (8u * static_cast<size_t>(smem_cap) + 32u * kRngWords + kPairWords) * sizeof(float);
 }
 
 cudaError_t chain_occupancy(bool general, int warps_per_block, int smem_cap, int* blocks_per_sm) {

@@ -270,10 +270,11 @@ __device__ __forceinline__ float sensor_term(const DPair& P, float3 a, float3 e)
 }
 
 // Does the segment P -> P + r touch the sensor ball?
+template <bool F = false>
 __device__ __forceinline__ bool hits_ball(const DPair& S, float3 P, float3 r) {
   const float3 c = f3(S.c[0], S.c[1], S.c[2]);
   const float rr = dot(r, r);
-  float t = dot(c - P, r) / rr;
+  float t = m_div<F>(dot(c - P, r), rr);
   t = fminf(fmaxf(t, 0.0f), 1.0f);
   const float3 d = P + t * r - c;
   return dot(d, d) <= S.R2;
