@@ -31,11 +31,15 @@ sys.path.insert(0, ROOT)
 METRIC = "RJMCMC proposals/s"
 UNIT = "proposals/s"
 
-# Algorithmic FP32 operations of one proposal per move type (scalar adds,
-# multiplies and fused multiply-adds of the factor formulas; each
-# transcendental counted as one operation), from the operation counts of the
-# formulas in the delta evaluator: see the roofline section of the design notes.
-OPS_PER_PROPOSAL = {"interior": 160.0, "end": 110.0, "birth": 230.0, "death": 200.0}
+# Algorithmic work of one proposal per move type, counted from the formulas
+# the delta evaluator needs (the proposal, the changed segment and vertex
+# factors, the acceptance ratio, Box-Muller / vMF / logistic transforms of the
+# random numbers); integer Philox work is not counted.  FP32 = adds,
+# multiplies and fused multiply-adds; MUFU = transcendentals and reciprocals
+# on the special-function unit.  Derivation in the design notes (roofline).
+FP32_PER_PROPOSAL = {"interior": 145.0, "end": 95.0, "birth": 206.0, "death": 122.0}
+MUFU_PER_PROPOSAL = {"interior": 23.0, "end": 16.0, "birth": 30.0, "death": 19.0}
+MUFU_LANES_PER_SM = 16
 FP32_LANES_PER_SM = 128
 
 
@@ -149,27 +153,39 @@ def host_initial_paths(sc, stride=8):
     return xyz, n
 
 
-def cpu_baseline(sc, seconds, threads):
-    """The oracle as it stands on the host cores, on a bounded sample of the workload."""
+def _oracle_sample(sc, seconds, threads, steps_cap=10_000):
+    """Size a bounded sample of the workload for the FP64 oracle: every chain
+    runs min(workload steps, steps_cap) steps from the workload's initial
+    paths; the chain count is chosen to take about `seconds` on `threads`."""
     import oracle as O
     p = sc.pairs[0]
-    run = sc.run
-    chains = max(threads * 4, 16)
+    steps = int(min(sc.run.n_steps, steps_cap))
+    probe_chains = max(threads, 8)
+    probe_steps = min(steps, 1000)
+    ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[p.sensor], sc.run, probe_chains, p.cap)
+    t = time.perf_counter()
+    ch.run(probe_steps, threads=threads)
+    rate = probe_chains * probe_steps / max(time.perf_counter() - t, 1e-6)
+    chains = int(max(threads, min(p.n_chains, round(rate * seconds / steps))))
+    return chains, steps
 
-    def one(steps):
-        ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[p.sensor], run, chains, p.cap)
-        t = time.perf_counter()
-        ch.run(steps, threads=threads)
-        return time.perf_counter() - t
 
-    probe = 400
-    dt = one(probe)
-    steps = max(probe, int(probe * seconds / max(dt, 1e-3)))
-    dt = one(steps)
-    props = chains * steps
-    return {"value": props / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{chains} chains x {steps} steps of the {sc.name} workload (first steps from the "
-                      f"initial paths), FP64, {dt:.1f} s"}
+def _oracle_run(sc, chains, steps, threads):
+    import oracle as O
+    p = sc.pairs[0]
+    ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[p.sensor], sc.run, chains, p.cap)
+    t = time.perf_counter()
+    ch.run(steps, threads=threads)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(sc, seconds, threads):
+    """The oracle as it stands on the host cores, on a bounded sample of the workload."""
+    chains, steps = _oracle_sample(sc, seconds, threads)
+    dt = _oracle_run(sc, chains, steps, threads)
+    return {"value": chains * steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{chains} of the {sc.pairs[0].n_chains} chains x the first {steps} of "
+                      f"{sc.run.n_steps} steps of the {sc.name} workload, FP64, {dt:.1f} s"}
 
 
 def reference_arm(args):
@@ -180,31 +196,23 @@ def reference_arm(args):
     threads = os.cpu_count() or 1
     import oracle as O
     O.build()
-    p = sc.pairs[0]
-    chains = max(threads * 4, 16)
-    per_step = max(4.0, 120.0 / max(args.steps + args.warmup, 1))
-    probe = O.Chains(sc.medium, sc.sources[0], sc.sensors[p.sensor], sc.run, chains, p.cap)
-    t = time.perf_counter()
-    probe.run(300, threads=threads)
-    rate = chains * 300 / (time.perf_counter() - t)
-    steps_per = max(300, int(rate * per_step / chains))
+    per_step = max(3.0, 150.0 / max(args.steps + args.warmup, 1))
+    chains, steps = _oracle_sample(sc, per_step, threads)
     times = []
     for i in range(args.warmup + args.steps):
-        ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[p.sensor], sc.run, chains, p.cap)
-        t = time.perf_counter()
-        ch.run(steps_per, threads=threads)
+        dt = _oracle_run(sc, chains, steps, threads)
         if i >= args.warmup:
-            times.append(time.perf_counter() - t)
+            times.append(dt)
     ms = 1e3 * sum(times) / len(times)
-    value = chains * steps_per / (ms / 1e3)
+    value = chains * steps / (ms / 1e3)
+    sample = (f"{chains} of the {sc.pairs[0].n_chains} chains x the first {steps} of {sc.run.n_steps} "
+              f"steps per bench step, FP64")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{sc.name}: {chains} chains x {steps_per} steps per step (bounded sample of "
-                                   f"{p.n_chains} x {sc.run.n_steps})", "global_batch": chains,
-                       "vertex_cap": p.cap},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{chains} chains x {steps_per} steps per bench step"},
+            "config": {"workload": f"{sc.name} (bounded sample: {sample})", "global_batch": chains,
+                       "vertex_cap": sc.pairs[0].cap},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -314,13 +322,22 @@ def ours(args):
     peaks, peak_kind = load_peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tops = FP32_LANES_PER_SM * n_sm * sm_mhz * 1e6 / 1e12
     prop = est["proposals"]
     tot = sum(prop)
     mix = {k: prop[i] / tot for i, k in enumerate(("interior", "end", "birth", "death"))}
-    ops = sum(mix[k] * OPS_PER_PROPOSAL[k] for k in mix)
+    fp32 = sum(mix[k] * FP32_PER_PROPOSAL[k] for k in mix)
+    mufu = sum(mix[k] * MUFU_PER_PROPOSAL[k] for k in mix)
     kern_s = statistics.mean(kern_ms) / 1e3
-    achieved = props_per_step * ops / kern_s / 1e12
+    rate = props_per_step / kern_s
+    # lane-op roofline: the slower of the FP32 and the MUFU pipes
+    fp32_peak = FP32_LANES_PER_SM * n_sm * sm_mhz * 1e6
+    mufu_peak = MUFU_LANES_PER_SM * n_sm * sm_mhz * 1e6
+    if mufu / mufu_peak >= fp32 / fp32_peak:
+        bound_pipe, achieved, peak = "MUFU", rate * mufu / 1e12, mufu_peak / 1e12
+    else:
+        bound_pipe, achieved, peak = "FP32", rate * fp32 / 1e12, fp32_peak / 1e12
+    # DRAM traffic of one launch: ncu capture of 16,384 chains (8.9 MB), scaled by chains
+    traffic = 8.9e6 * n_chains / 16384.0 if sc.name == "detector" else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -329,11 +346,13 @@ def ours(args):
                        "chains": n_chains, "steps_per_chain": sc.run.n_steps, "vertex_cap": sc.pairs[0].cap,
                        "global_batch": n_chains * world, "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MB write)", "accumulators": "f64"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "TFLOP/s",
-                         "frac": achieved / peak_tops, "traffic": None,
-                         "peak_source": f"FP32 lanes x SMs x sm_max_mhz ({peak_kind} clocks)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "pipe": bound_pipe,
+                         "peak_source": f"{bound_pipe} lanes/clk/SM x {n_sm} SMs x sm_max_mhz "
+                                        f"({peak_kind} clock {sm_mhz:.0f} MHz)",
                          "kernel": "chain_kernel", "kernel_ms": statistics.mean(kern_ms),
-                         "ops_per_proposal": ops},
+                         "fp32_per_proposal": fp32, "mufu_per_proposal": mufu},
             "gpu_launches": 3 * args.steps,
             "estimate": {k: est[k] for k in ("intensity", "std_err", "pi_direct", "rhat", "mean_n", "accept")},
             "clocks": clocks, "e2e": e2e}
