@@ -197,6 +197,34 @@ def layered(n_sensors: int = 60, chains_per_sensor: int = 8192, n_steps: int = 1
     return Scene("layered", med, [src], sensors, pairs, run)
 
 
+def batched_small(n_chains: int = 1024, n_steps: int = 10_000) -> Scene:
+    """A small uneven batch: four single-scatter pairs (cap 3) at 1-3 m in
+    different directions and two long-cap pairs (caps 150 and 600, two more
+    cap classes) at 3 m and 4 m; plain-workload medium, sensors R = 0.3 m."""
+    med = Medium(HOMOGENEOUS, lambda_s=0.5, lambda_a=5.0, g=0.9)
+    dirs = [(0.0, 0.0, 1.0), (1.0, 0.0, 0.0), (0.0, -0.6, 0.8), (-0.48, 0.6, -0.64), (0.0, 1.0, 0.0),
+            (0.6, 0.0, -0.8)]
+    dist = [1.0, 1.5, 2.0, 3.0, 3.0, 4.0]
+    caps = [3, 3, 3, 3, 150, 600]
+    sensors = [Sensor(tuple(d * x for x in u), 0.3) for u, d in zip(dirs, dist)]
+    pairs = [Pair(0, i, n_chains, caps[i]) for i in range(6)]
+    run = Run(seed=BASE_SEED + 5, n_steps=n_steps, burn_in=n_steps // 10, init=INIT_DIRECT, sigma=0.05)
+    return Scene("batched_small", med, [Source()], sensors, pairs, run)
+
+
+def general_small(n_chains: int = 64, n_steps: int = 400) -> Scene:
+    """Exercises every general-kernel branch: layered medium, vMF emission,
+    the paper's detection probability and the simplified-Liu mixture."""
+    rng = np.random.default_rng(BASE_SEED + 6)
+    med = Medium(LAYERED, g=0.9, f_sl=0.45, z0=-2.0, dz=0.5,
+                 lambda_s_layers=0.6 * np.exp(0.3 * rng.normal(size=12)),
+                 lambda_a_layers=5.0 * np.exp(0.3 * rng.normal(size=12)))
+    src = Source((0.1, -0.1, -0.5), EMIT_VMF, 5.0, (0.0, 0.0, 1.0))
+    sen = Sensor((0.2, 0.1, 0.9), 0.15, RHO_PAPER, (0.0, -1.0, 0.0))
+    run = Run(seed=BASE_SEED + 7, n_steps=n_steps, burn_in=n_steps // 10, init=INIT_DIRECT, sigma=0.05)
+    return Scene("general_small", med, [src], [sen], [Pair(0, 0, n_chains, 64)], run)
+
+
 PRESETS = {"plain": plain, "detector": detector, "batched": batched,
            "gradients": gradients, "layered": layered}
 

@@ -31,9 +31,38 @@ def plain_intensity(n_chains=4096, n_steps=10_000, burn_in=1_000):
             "oracle_seconds": time.time() - t}
 
 
-if __name__ == "__main__":
-    out = plain_intensity()
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plain_intensity.json")
+def batched_small_long_pairs():
+    """Oracle intensities of the two long-cap pairs of the small uneven batch,
+    with the batch's global chain numbering (same random streams)."""
+    sc = S.batched_small()
+    out = {"scene": "batched_small", "n_steps": sc.run.n_steps, "burn_in": sc.run.burn_in, "pairs": {}}
+    chain0 = 0
+    for i, p in enumerate(sc.pairs):
+        if p.cap > 3:
+            t = time.time()
+            ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[p.sensor], sc.run, p.n_chains, p.cap,
+                          chain_offset=chain0)
+            ch.run(sc.run.n_steps)
+            m, s, d = O.medium(sc.medium), O.source(sc.sources[0]), O.sensor(sc.sensors[p.sensor])
+            acc = ch.accumulators()
+            I, se, pi = O.direct_estimate(acc, O.z2(m, s, d))
+            out["pairs"][str(i)] = {"cap": p.cap, "intensity": I, "std_err": se, "pi_direct": pi,
+                                    "mean_n": float(acc["sum_n"].sum() / acc["n_rec"].sum()),
+                                    "oracle_seconds": time.time() - t}
+        chain0 += p.n_chains
+    return out
+
+
+def _write(name, out):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), name)
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps(out, indent=1))
+
+
+if __name__ == "__main__":
+    which = sys.argv[1:] or ["plain", "batched"]
+    if "plain" in which:
+        _write("plain_intensity.json", plain_intensity())
+    if "batched" in which:
+        _write("batched_small_intensity.json", batched_small_long_pairs())

@@ -243,3 +243,98 @@ def test_abort_request_stops_and_context_survives(api, ctx):
     _, _, _, ch2 = _plain_sampler(api, ctx, 128, 0)
     ch2.run_steps(2000)
     assert ch2.read_estimator()[0]["n_samples"] > 0
+
+
+def test_batched_uneven_pairs(api, ctx):
+    """One chain set over six pairs in three vertex-cap classes: the cap-3 pairs
+    match the single-scatter quadrature, the long pairs the oracle."""
+    sc = S.batched_small()
+    g = json.load(open(os.path.join(GOLDEN, "batched_small_intensity.json")))
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    ch.run_steps(sc.run.n_steps)
+    est = ch.read_estimator()
+    assert ch.status() == 0
+    xyz, n, steps = ch.read_states()
+    caps = np.repeat([p.cap for p in sc.pairs], [p.n_chains for p in sc.pairs])
+    assert np.all((n >= 2) & (n <= caps)) and np.all(steps == sc.run.n_steps)
+    for i, (p, e) in enumerate(zip(sc.pairs, est)):
+        assert sum(e["proposals"]) == p.n_chains * sc.run.n_steps
+        D = float(np.linalg.norm(sc.sensors[p.sensor].centre))
+        if p.cap == 3:
+            ref = Q.z2_closed(D, 0.3, 2.2) + Q.z3(D, 0.3, 0.5, 5.0, 0.9)
+            assert abs(e["intensity"] - ref) < 3 * e["std_err"], (i, e["intensity"], e["std_err"], ref)
+        else:
+            o = g["pairs"][str(i)]
+            assert abs(e["intensity"] - o["intensity"]) < 3 * math.hypot(e["std_err"], o["std_err"]), (i, e, o)
+            assert abs(e["mean_n"] / o["mean_n"] - 1) < 0.03
+
+
+def test_general_kernel_trajectory_replay(api, ctx, oracle_lib):
+    """Layered medium, vMF emission, detection probability and the SL mixture
+    (the general kernel) replay the oracle's trajectories."""
+    O = oracle_lib
+    sc = S.general_small()
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    ch.run_steps(sc.run.n_steps)
+    xyz, n, _ = ch.read_states()
+    oc = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, 64)
+    margin = oc.run(sc.run.n_steps, margins=True)
+    clean = margin > 1e-3
+    assert clean.sum() >= 32
+    for c in np.nonzero(clean)[0]:
+        assert n[c] == oc.n[c], (c, n[c], oc.n[c])
+        k = int(n[c])
+        assert np.allclose(xyz[c, :, :k].T, oc.xyz[c, :k], atol=2e-4), c
+    # the general kernel keeps every state's density finite
+    import torch
+    lp = api.logp(ctx, medium, geom, 0, torch.from_numpy(np.ascontiguousarray(xyz.transpose(1, 0, 2))).cuda(),
+                  torch.from_numpy(n).cuda()).cpu().numpy()
+    assert np.all(np.isfinite(lp))
+
+
+def test_gradient_estimator_fd_and_fp64(api, ctx, oracle_lib):
+    """Score-function gradients of the intensity (MALA chains): the per-state
+    scores match the FP64 oracle, central finite differences of the density at
+    h = 1e-3 relative on common samples, and the accumulated estimator."""
+    import copy
+    import torch
+    O = oracle_lib
+    sc = S.gradients(n_chains=16384, n_steps=4000)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    ch.run_steps(sc.run.n_steps)
+    grad, grad_se = ch.grad_estimator()
+    e = ch.read_estimator()[0]
+    xyz, n, _ = ch.read_states()
+    xt = torch.from_numpy(np.ascontiguousarray(xyz.transpose(1, 0, 2))).cuda()
+    nt = torch.from_numpy(n).cuda()
+    sc_gpu = api.score(ctx, medium, geom, 0, xt, nt).cpu().numpy().astype(np.float64)
+    # FP64 reference on the same states
+    m, s, d = O.medium(sc.medium), O.source(sc.sources[0]), O.sensor(sc.sensors[0])
+    ref = np.array([O.score(m, s, d, xyz[c, :, : n[c]].T.astype(np.float64)) for c in range(0, len(n), 8)])
+    mine = sc_gpu[::8]
+    scale = np.abs(ref).mean(axis=0)
+    assert np.all(np.abs(mine.mean(axis=0) - ref.mean(axis=0)) <= 1e-3 * scale)
+    # central differences of log p at theta (1 +- 1e-3) on the same states
+    lp0 = api.logp(ctx, medium, geom, 0, xt, nt).cpu().numpy().astype(np.float64)
+    for i, name in enumerate(("lambda_s", "lambda_a", "g")):
+        v = getattr(sc.medium, name)
+        h = 1e-3 * v
+        ratios = []
+        for sgn in (+1, -1):
+            mm = copy.deepcopy(sc.medium)
+            setattr(mm, name, v + sgn * h)
+            lp = api.logp(ctx, api.Medium(ctx, mm), geom, 0, xt, nt).cpu().numpy().astype(np.float64)
+            ratios.append(np.exp(lp - lp0))
+        fd = (ratios[0] - ratios[1]) / (2 * h)
+        assert abs(fd.mean() - sc_gpu[:, i].mean()) <= 1e-3 * np.abs(sc_gpu[:, i]).mean(), (name, fd.mean(),
+                                                                                            sc_gpu[:, i].mean())
+    # accumulated estimator (all recorded states) vs the final states
+    final = e["intensity"] * sc_gpu.mean(axis=0)
+    final_se = e["intensity"] * sc_gpu.std(axis=0) / math.sqrt(len(n))
+    assert np.all(np.abs(grad[0] - final) < 4 * np.hypot(grad_se[0], final_se)), (grad, grad_se, final, final_se)
