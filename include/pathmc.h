@@ -305,6 +305,37 @@ PMC_API int pmc_score(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int p
               const float* xyz, const int* n, int batch, int cap, float* out, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Normalisation by the geometric bridge                                  */
+/* ---------------------------------------------------------------------- */
+
+/* The paper's geometric estimator (section "Comparison of relative light
+ * yield": B = E_0[sqrt(p_1/p_0)] / E_1[sqrt(p_0/p_1)]) with p_0 := q_ref, a
+ * normalised reference density built from the paper's recursive tree of
+ * bispherical coordinates (appendix, path space coordinate system): vertex
+ * m = floor((k+l)/2) placed about the foci f_k, f_l by q(s) q(t) q(phi) with
+ * beta from the foci (appendix, dimension matching transformation), the vertex
+ * count a Poisson law in the straight-line scattering depth truncated to
+ * [2, cap], the end vertex uniform over the sensor cap visible from the source.
+ * Its normalisation makes the bridge an estimate of the absolute intensity. */
+
+/* log q_ref of caller paths (async; same layout and frame as pmc_logp); -inf
+ * when the end vertex lies outside the visible cap.  Synchronises `stream`. */
+PMC_API int pmc_qref_logdensity(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair, const float* xyz,
+                                const int* n, int batch, int cap, float* out, void* stream);
+
+/* Draws n_draws paths of pair `pair` from q_ref (Philox counter (draw, vertex,
+ * stream = pair)).  out_xyz: device [3][n_draws][stride] absolute positions,
+ * out_n: device [n_draws]; stride >= cap.  Synchronises `stream`. */
+PMC_API int pmc_qref_sample(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair, uint64_t seed,
+                            uint64_t draw0, uint64_t n_draws, float* out_xyz, int* out_n, int stride, void* stream);
+
+/* Bridge estimate of every pair's intensity: n_draws reference draws per pair
+ * give E_q[sqrt(p/q_ref)], the chains' current states give
+ * E_p[sqrt(q_ref/p)].  out (host): [n_pairs][2] = intensity, standard error
+ * (delta method over both sample variances).  Synchronises `stream`. */
+PMC_API int pmc_bridge(pmc_chains_t chains, uint64_t n_draws, uint64_t seed, double* out, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Comparison baseline                                                    */
 /* ---------------------------------------------------------------------- */
 

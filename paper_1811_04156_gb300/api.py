@@ -222,6 +222,13 @@ class Chains:
               "pmc_grad_estimator")
         return g.reshape(self.n_pairs, nt), se.reshape(self.n_pairs, nt)
 
+    def bridge(self, n_draws: int, seed: int = 0, stream=None):
+        """Geometric-bridge intensity per pair with the reference density (pmc_bridge): (I, SE) rows."""
+        out = np.zeros((self.n_pairs, 2))
+        check(load().pmc_bridge(self.handle, int(n_draws), int(seed), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                _stream(stream)), "pmc_bridge")
+        return out
+
     def read_states(self, stream=None):
         stride = self.geom.max_cap
         xyz = np.zeros((self.total, 3, stride), dtype=np.float32)
@@ -343,6 +350,29 @@ def trace(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: int, n_
     var = max(out[1] / N - mean * mean, 0.0) if N > 0 else float("nan")
     return {"I": mean, "se": math.sqrt(var / N) if N > 0 else float("nan"), "hits": out[2], "photons": N,
             "mean_L": out[4] / out[0] if out[0] > 0 else float("nan"), "raw": out}
+
+
+def qref_logdensity(ctx: Context, medium: Medium, geom: Geometry, pair: int, xyz: torch.Tensor, n: torch.Tensor,
+                    stream=None) -> torch.Tensor:
+    """log q_ref of a device batch (pmc_qref_logdensity)."""
+    batch, cap = _check_batch(xyz, n)
+    out = torch.empty(batch, dtype=torch.float32, device=xyz.device)
+    check(load().pmc_qref_logdensity(ctx.handle, medium.handle, geom.handle, int(pair), C.c_void_p(xyz.data_ptr()),
+                                     C.c_void_p(n.data_ptr()), batch, cap, C.c_void_p(out.data_ptr()),
+                                     _stream(stream)), "pmc_qref_logdensity")
+    return out
+
+
+def qref_sample(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: int, n_draws: int, draw0: int = 0,
+                stride: Optional[int] = None, stream=None):
+    """Reference-density draws (pmc_qref_sample): xyz (3, n_draws, stride) and n on the device."""
+    stride = int(stride or geom.pairs[pair].cap)
+    xyz = torch.zeros((3, int(n_draws), stride), dtype=torch.float32, device="cuda")
+    n = torch.zeros(int(n_draws), dtype=torch.int32, device="cuda")
+    check(load().pmc_qref_sample(ctx.handle, medium.handle, geom.handle, int(pair), int(seed), int(draw0),
+                                 int(n_draws), C.c_void_p(xyz.data_ptr()), C.c_void_p(n.data_ptr()), stride,
+                                 _stream(stream)), "pmc_qref_sample")
+    return xyz, n
 
 
 def trace_noalloc(ctx: Context, medium: Medium, geom: Geometry, pairs, seed: int, n_photons: int,

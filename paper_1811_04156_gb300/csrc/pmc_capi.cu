@@ -80,6 +80,8 @@ struct pmc_medium_s {
   float* d_llogb = nullptr;
   double lambda_s = 0, lambda_a = 0;
   int n_theta = 3;
+  double z0 = 0, dz = 1;
+  std::vector<double> ls_layers, la_layers;
 };
 
 struct PairHost {
@@ -181,10 +183,79 @@ struct pmc_chains_s {
   bool general = false;            // chain kernel instantiation
   int init_kind = 0, init_k = 0;
   float init_jitter = 0.f;
+  QrefPair* d_qp = nullptr;       // reference-density tables (pmc_bridge)
+  double* d_qtab = nullptr;
+  double* d_bsum = nullptr;
   float* d_stage = nullptr;       // staging buffer of pmc_set_states
   int* d_stage_n = nullptr;
   size_t stage_floats = 0;
 };
+
+// Scattering depth of the straight segment from the source to the sensor
+// point nearest it (host, FP64): the mean of the truncated Poisson law of the
+// reference density's vertex count.
+static double straight_tau_b(const pmc_medium_s* m, const PairHost& h) {
+  double rel[3], e[3];
+  for (int i = 0; i < 3; ++i) rel[i] = h.c[i] - h.src[i];
+  const double D = norm3(rel);
+  for (int i = 0; i < 3; ++i) e[i] = h.src[i] + rel[i] * (D - h.R) / D;
+  const double ell = D - h.R;
+  if (m->d.kind == PMC_HOMOGENEOUS) return ell / m->lambda_s;
+  const int L = static_cast<int>(m->ls_layers.size());
+  auto layer = [&](double z) {
+    double f = std::floor((z - m->z0) / m->dz);
+    if (f < 0) f = 0;
+    if (f > L - 1) f = L - 1;
+    return static_cast<int>(f);
+  };
+  const double zP = h.src[2], zQ = e[2];
+  const int lP = layer(zP), lQ = layer(zQ);
+  if (lP == lQ) return ell / m->ls_layers[lP];
+  const double zlo = std::min(zP, zQ), zhi = std::max(zP, zQ);
+  double acc = 0.0;
+  for (int l = std::min(lP, lQ); l <= std::max(lP, lQ); ++l) {
+    const double lo = (l == std::min(lP, lQ)) ? zlo : m->z0 + l * m->dz;
+    const double hi = (l == std::max(lP, lQ)) ? zhi : m->z0 + (l + 1) * m->dz;
+    acc += std::max(hi - lo, 0.0) / (zhi - zlo) / m->ls_layers[l];
+  }
+  return ell * acc;
+}
+
+// Reference-density tables of every pair: truncated Poisson law of the vertex
+// count (log P and CDF over n = 0..cap) and the visible-cap area term.
+static void build_qref(const pmc_medium_s* m, const std::vector<PairHost>& host, std::vector<QrefPair>& qp,
+                       std::vector<double>& tab) {
+  qp.resize(host.size());
+  tab.clear();
+  for (size_t p = 0; p < host.size(); ++p) {
+    const PairHost& h = host[p];
+    const double mu = straight_tau_b(m, h);
+    const int cap = h.cap;
+    double norm = 0.0;
+    for (int k = 0; k <= cap - 2; ++k) norm += std::exp(k * std::log(mu) - mu - std::lgamma(k + 1.0));
+    qp[p].off = static_cast<long long>(tab.size());
+    std::vector<double> lp(cap + 1, -std::numeric_limits<double>::infinity()), cdf(cap + 1, 0.0);
+    double cum = 0.0;
+    for (int n = 2; n <= cap; ++n) {
+      const int k = n - 2;
+      lp[n] = k * std::log(mu) - mu - std::lgamma(k + 1.0) - std::log(norm);
+      cum += std::exp(lp[n]);
+      cdf[n] = cum;
+    }
+    tab.insert(tab.end(), lp.begin(), lp.end());
+    tab.insert(tab.end(), cdf.begin(), cdf.end());
+    double rel[3];
+    for (int i = 0; i < 3; ++i) rel[i] = h.c[i] - h.src[i];
+    const double D = norm3(rel);
+    qp[p].log_qend = -std::log(2.0 * M_PI * h.R * h.R * (1.0 - h.R / D));
+  }
+}
+
+static DRun qref_run() {
+  DRun r{};
+  r.beta_min = 0.01f;
+  return r;
+}
 
 extern "C" {
 
@@ -270,6 +341,10 @@ int pmc_create_medium(pmc_ctx_t ctx, const pmc_medium_desc* desc, pmc_medium_t* 
     CK(cudaMemcpy(m->d_la, la.data(), L * sizeof(float), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->d_lb, lb.data(), L * sizeof(float), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(m->d_llogb, llb.data(), L * sizeof(float), cudaMemcpyHostToDevice));
+    m->z0 = desc->z0;
+    m->dz = desc->dz;
+    m->ls_layers.assign(desc->lambda_s_layers, desc->lambda_s_layers + L);
+    m->la_layers.assign(desc->lambda_a_layers, desc->lambda_a_layers + L);
     d.n_layers = L;
     d.z0 = static_cast<float>(desc->z0);
     d.dz = static_cast<float>(desc->dz);
@@ -387,6 +462,9 @@ int pmc_destroy_chains(pmc_chains_t ch) {
   cudaFree(ch->d_est);
   cudaFree(ch->d_stage);
   cudaFree(ch->d_stage_n);
+  cudaFree(ch->d_qp);
+  cudaFree(ch->d_qtab);
+  cudaFree(ch->d_bsum);
   if (ch->h_abort) cudaFreeHost(ch->h_abort);
   delete ch;
   return PMC_OK;
@@ -929,6 +1007,99 @@ int pmc_trace_noalloc(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const in
   const float rr = std::isfinite(r_reject) ? static_cast<float>(r_reject) : std::numeric_limits<float>::infinity();
   CK(launch_trace_noalloc(med->d, sel, n_pairs, seed, photon0, n_photons, rr, max_scatter, out, ctx->device,
                           ctx->n_sm, static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
+int pmc_qref_logdensity(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, const float* xyz, const int* n,
+                        int batch, int cap, float* out, void* stream) {
+  const DPair* d = pair_of(geom, pair);
+  if (!ctx || !med || !d || !xyz || !n || !out) return fail(PMC_ERR_INVALID, "bad argument");
+  if (batch < 0 || cap < 2) return fail(PMC_ERR_INVALID, "bad batch or cap");
+  CK(cudaSetDevice(ctx->device));
+  std::vector<QrefPair> qp;
+  std::vector<double> tab;
+  build_qref(med, {geom->host[pair]}, qp, tab);
+  QrefPair* d_qp = nullptr;
+  double* d_tab = nullptr;
+  CK(dalloc(&d_qp, 1));
+  cudaError_t e = dalloc(&d_tab, tab.size());
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_qp, qp.data(), sizeof(QrefPair), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_qref_logdensity(med->d, qref_run(), *d, d_qp, d_tab, xyz, n, batch, cap, out, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_qp);
+  cudaFree(d_tab);
+  CK(e);
+  return PMC_OK;
+}
+
+int pmc_qref_sample(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, uint64_t seed, uint64_t draw0,
+                    uint64_t n_draws, float* out_xyz, int* out_n, int stride, void* stream) {
+  const DPair* d = pair_of(geom, pair, false);
+  if (!ctx || !med || !d || !out_xyz || !out_n) return fail(PMC_ERR_INVALID, "bad argument");
+  if (stride < d->cap) return fail(PMC_ERR_INVALID, "stride smaller than the pair's cap");
+  CK(cudaSetDevice(ctx->device));
+  std::vector<QrefPair> qp;
+  std::vector<double> tab;
+  build_qref(med, {geom->host[pair]}, qp, tab);
+  QrefPair* d_qp = nullptr;
+  double* d_tab = nullptr;
+  DPair* d_pair = nullptr;
+  CK(dalloc(&d_qp, 1));
+  cudaError_t e = dalloc(&d_tab, tab.size());
+  if (e == cudaSuccess) e = dalloc(&d_pair, 1);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_qp, qp.data(), sizeof(QrefPair), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_pair, d, sizeof(DPair), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_qref_draws(med->d, qref_run(), d_pair, d_qp, d_tab, 1, pair, d->cap, seed, draw0, n_draws, nullptr,
+                          out_xyz, out_n, stride, ctx->n_sm, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_qp);
+  cudaFree(d_tab);
+  cudaFree(d_pair);
+  CK(e);
+  return PMC_OK;
+}
+
+int pmc_bridge(pmc_chains_t ch, uint64_t n_draws, uint64_t seed, double* out, void* stream) {
+  if (ch == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (n_draws == 0) return fail(PMC_ERR_INVALID, "n_draws must be > 0");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int P = ch->n_pairs;
+  if (ch->d_qp == nullptr) {
+    std::vector<QrefPair> qp;
+    std::vector<double> tab;
+    build_qref(ch->med, ch->geom->host, qp, tab);
+    CK(dalloc(&ch->d_qp, qp.size()));
+    CK(dalloc(&ch->d_qtab, tab.size()));
+    CK(dalloc(&ch->d_bsum, 8 * static_cast<size_t>(P)));
+    CK(cudaMemcpyAsync(ch->d_qp, qp.data(), qp.size() * sizeof(QrefPair), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ch->d_qtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  CK(cudaMemsetAsync(ch->d_bsum, 0, 8 * sizeof(double) * P, s));
+  CK(launch_qref_draws(ch->med->d, ch->run, ch->d_pairs, ch->d_qp, ch->d_qtab, P, 0, ch->geom->max_cap, seed, 0,
+                       n_draws, ch->d_bsum, nullptr, nullptr, 0, ch->ctx->n_sm, s));
+  CK(launch_qref_chains(ch->med->d, ch->run, ch->d_pairs, ch->d_qp, ch->d_qtab, ch->d_chain_pair, ch->d_chain_base,
+                        ch->d_xyz, ch->d_n, ch->total, ch->d_bsum + 4 * P, s));
+  std::vector<double> h(8 * static_cast<size_t>(P));
+  CK(cudaMemcpyAsync(h.data(), ch->d_bsum, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int p = 0; p < P; ++p) {
+    const double nq = static_cast<double>(n_draws);
+    const double mq = h[4 * p] / nq;                      // E_q sqrt(p/q)
+    const double vq = std::max(h[4 * p + 1] / nq - mq * mq, 0.0);
+    const double np_ = h[4 * P + 4 * p + 2];
+    const double mp = np_ > 0 ? h[4 * P + 4 * p] / np_ : 0.0;  // E_p sqrt(q/p)
+    const double vp = np_ > 0 ? std::max(h[4 * P + 4 * p + 1] / np_ - mp * mp, 0.0) : 0.0;
+    const double I = mq / mp;
+    out[2 * p] = I;
+    out[2 * p + 1] = I * std::sqrt(vq / (nq * mq * mq) + vp / (np_ * mp * mp));
+  }
   return PMC_OK;
 }
 

@@ -113,6 +113,24 @@ cudaError_t launch_trace(const DMedium& M, const DPair& S, unsigned long long se
                          unsigned long long photon0, unsigned long long n_photons, float r_reject,
                          int max_scatter, double* out5, int n_sm, cudaStream_t s);
 
+// pmc_bridge.cu: reference density q_ref and the geometric bridge.
+// Per pair: qtab[off + n] = log P_ref(n) (n = 0..cap, -inf below 2) and
+// qtab[off + cap + 1 + n] = P_ref(N <= n); log_qend = -log(visible cap area).
+struct QrefPair {
+  double log_qend;
+  long long off;
+};
+cudaError_t launch_qref_draws(const DMedium& M, const DRun& R, const DPair* pairs, const QrefPair* qp,
+                              const double* qtab, int n_pairs, int stream_base, int max_cap, unsigned long long seed,
+                              unsigned long long draw0, unsigned long long n_draws, double* sums, float* out_xyz,
+                              int* out_n, int out_stride, int n_sm, cudaStream_t s);
+cudaError_t launch_qref_chains(const DMedium& M, const DRun& R, const DPair* pairs, const QrefPair* qp,
+                               const double* qtab, const int* chain_pair, const long long* chain_base,
+                               const float* xyz, const int* n, int total, double* sums, cudaStream_t s);
+cudaError_t launch_qref_logdensity(const DMedium& M, const DRun& R, const DPair& S, const QrefPair* qp,
+                                   const double* qtab, const float* xyz, const int* n, int batch, int cap, float* out,
+                                   cudaStream_t s);
+
 // pmc_noalloc.cu: allocation-free tracer over up to kNoAllocMaxPairs pairs.
 constexpr int kNoAllocMaxPairs = 128;
 cudaError_t launch_trace_noalloc(const DMedium& M, const DPair* pairs, int n_pairs, unsigned long long seed,
