@@ -241,12 +241,14 @@ PMC_API int pmc_run_steps(pmc_chains_t chains, uint64_t n_steps, void* stream);
  * from the across-chain variance. */
 PMC_API int pmc_read_estimator(pmc_chains_t chains, pmc_estimate* out, size_t n_pairs, void* stream);
 
-/* d intensity / d theta per pair: intensity * E_p[d log p / d theta] from
- * score terms accumulated while stepping (needs PMC_FLAG_GRADIENTS).
- * theta = (lambda_s, lambda_a, g) for homogeneous media, or
- * (lambda_s[0..L), lambda_a[0..L)) for layered ones.  `grad` and `grad_se`
- * are host arrays of n_pairs * n_theta doubles (pair-major); grad_se may be
- * NULL.  Synchronises `stream`. */
+/* d intensity / d theta per pair: intensity * E_p[d log p / d theta], the
+ * score-function gradient (dI/dtheta = I E_p[d log p/d theta]).
+ * Homogeneous media: theta = (lambda_s, lambda_a, g), with E_p over every
+ * recorded state, accumulated while stepping (needs PMC_FLAG_GRADIENTS).
+ * Layered media: theta = (lambda_s[0..L), lambda_a[0..L)), with E_p over the
+ * chains' current states (one state per chain).  `grad` and `grad_se` are
+ * host arrays of n_pairs * n_theta doubles (pair-major); grad_se may be NULL.
+ * Synchronises `stream`. */
 PMC_API int pmc_grad_estimator(pmc_chains_t chains, double* grad, double* grad_se, size_t len, void* stream);
 
 /* Number of medium parameters theta (3 or 2 * n_layers). */

@@ -810,19 +810,50 @@ int pmc_read_estimator(pmc_chains_t ch, pmc_estimate* out, size_t n_pairs, void*
 
 int pmc_grad_estimator(pmc_chains_t ch, double* grad, double* grad_se, size_t len, void* stream) {
   if (ch == nullptr || grad == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
-  if (!(ch->flags & PMC_FLAG_GRADIENTS)) return fail(PMC_ERR_INVALID, "chains were created without PMC_FLAG_GRADIENTS");
   const int nt = ch->med->n_theta;
   if (len < static_cast<size_t>(ch->n_pairs) * nt) return fail(PMC_ERR_INVALID, "output too short");
-  if (ch->med->d.kind != 0) return fail(PMC_ERR_INVALID, "layered gradients are not available in this build");
-  std::vector<pmc_estimate> tmp(ch->n_pairs);
-  const int rc = pmc_read_estimator(ch, tmp.data(), tmp.size(), stream);
+  const bool layered = ch->med->d.kind != PMC_HOMOGENEOUS;
+  if (!layered && !(ch->flags & PMC_FLAG_GRADIENTS))
+    return fail(PMC_ERR_INVALID, "homogeneous gradients need chains created with PMC_FLAG_GRADIENTS");
+  std::vector<pmc_estimate> est(ch->n_pairs);
+  const int rc = pmc_read_estimator(ch, est.data(), est.size(), stream);
   if (rc != PMC_OK) return rc;
-  std::vector<double> h(static_cast<size_t>(ch->n_pairs) * EST_WORDS);
-  CK(cudaMemcpy(h.data(), ch->d_est, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
-  for (int i = 0; i < ch->n_pairs; ++i) {
-    for (int k = 0; k < 3; ++k) {
-      grad[i * 3 + k] = h[static_cast<size_t>(i) * EST_WORDS + EST_GRAD0 + k];
-      if (grad_se) grad_se[i * 3 + k] = h[static_cast<size_t>(i) * EST_WORDS + EST_GRADSE0 + k];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!layered) {
+    // accumulated over every recorded state while stepping
+    std::vector<double> h(static_cast<size_t>(ch->n_pairs) * EST_WORDS);
+    CK(cudaMemcpyAsync(h.data(), ch->d_est, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < ch->n_pairs; ++i) {
+      for (int k = 0; k < 3; ++k) {
+        grad[i * 3 + k] = h[static_cast<size_t>(i) * EST_WORDS + EST_GRAD0 + k];
+        if (grad_se) grad_se[i * 3 + k] = h[static_cast<size_t>(i) * EST_WORDS + EST_GRADSE0 + k];
+      }
+    }
+    return PMC_OK;
+  }
+  // layered: per-layer scores of the chains' current states
+  const int L = ch->med->d.n_layers;
+  const size_t words = static_cast<size_t>(ch->n_pairs) * 4 * L;
+  double* d_sums = nullptr;
+  CK(dalloc(&d_sums, words));
+  cudaError_t e = cudaMemsetAsync(d_sums, 0, words * sizeof(double), s);
+  if (e == cudaSuccess)
+    e = launch_layer_scores(ch->med->d, ch->d_pairs, ch->d_chain_pair, ch->d_chain_base, ch->d_xyz, ch->d_n, ch->total,
+                            d_sums, s);
+  std::vector<double> h(words);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_sums, words * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_sums);
+  CK(e);
+  for (int p = 0; p < ch->n_pairs; ++p) {
+    const double N = static_cast<double>(ch->h_pairs[p].n_chains);
+    const double I = est[p].intensity, seI = est[p].std_err;
+    for (int j = 0; j < 2 * L; ++j) {
+      const double m = h[static_cast<size_t>(p) * 4 * L + j] / N;
+      const double v = std::max(h[static_cast<size_t>(p) * 4 * L + 2 * L + j] / N - m * m, 0.0);
+      grad[static_cast<size_t>(p) * nt + j] = I * m;
+      if (grad_se) grad_se[static_cast<size_t>(p) * nt + j] = std::sqrt(I * I * v / N + m * m * seI * seI);
     }
   }
   return PMC_OK;

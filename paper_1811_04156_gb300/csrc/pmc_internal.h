@@ -113,6 +113,11 @@ cudaError_t launch_trace(const DMedium& M, const DPair& S, unsigned long long se
                          unsigned long long photon0, unsigned long long n_photons, float r_reject,
                          int max_scatter, double* out5, int n_sm, cudaStream_t s);
 
+// Per-layer score sums over the chains' current states: sums[pair][0..2L) and
+// squares at sums[pair][2L..4L) (layered media, L <= 4096).
+cudaError_t launch_layer_scores(const DMedium& M, const DPair* pairs, const int* chain_pair, const long long* chain_base,
+                                const float* xyz, const int* n, int total, double* sums, cudaStream_t s);
+
 // pmc_bridge.cu: reference density q_ref and the geometric bridge.
 // Per pair: qtab[off + n] = log P_ref(n) (n = 0..cap, -inf below 2) and
 // qtab[off + cap + 1 + n] = P_ref(N <= n); log_qend = -log(visible cap area).

@@ -427,6 +427,72 @@ __global__ void __launch_bounds__(256) trace_kernel(const DMedium M, const DPair
   }
 }
 
+// Per-layer scores of every chain's current path, summed per pair (layered
+// media): theta = (lambda_s[l], lambda_a[l]) with d log p / d lambda_s[l] =
+// len_l b_l^2 - n_l b_l and d log p / d lambda_a[l] = len_l a_l^2 (len_l: path
+// length in layer l, n_l: scattering vertices in it).  One warp per chain; the
+// chain's 2L scores are gathered in shared memory, then added (and squared)
+// into the pair's FP64 sums.
+__global__ void __launch_bounds__(128) chain_layer_score_kernel(const DMedium M, const DPair* __restrict__ pairs,
+                                                                const int* __restrict__ chain_pair,
+                                                                const long long* __restrict__ chain_base,
+                                                                const float* __restrict__ xyz, const int* __restrict__ nn,
+                                                                int total, double* __restrict__ sums) {
+  extern __shared__ float sc[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int NL = M.n_layers;
+  float* s = sc + static_cast<size_t>(wib) * 2 * NL;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= total) return;
+  for (int j = lane; j < 2 * NL; j += 32) s[j] = 0.f;
+  __syncwarp();
+  const int pair = chain_pair[c];
+  const DPair S = pairs[pair];
+  const int n = nn[c];
+  const float* gx = xyz + chain_base[c];
+  const float* gy = gx + S.cap;
+  const float* gz = gy + S.cap;
+  const float zoff = S.zoff;
+  for (int i = lane; i < n; i += 32) {
+    const float3 P = f3(gx[i], gy[i], gz[i]);
+    if (i >= 1 && i <= n - 2) {
+      const int l = layer_of(M, P.z + zoff);
+      atomicAdd(s + l, -__ldg(M.lb + l));
+    }
+    if (i <= n - 2) {
+      const float3 Q = f3(gx[i + 1], gy[i + 1], gz[i + 1]);
+      const float3 r = Q - P;
+      const float ell = sqrtf(dot(r, r));
+      const float zP = P.z + zoff, zQ = Q.z + zoff;
+      const int lP = layer_of(M, zP), lQ = layer_of(M, zQ);
+      const int l0 = min(lP, lQ), l1 = max(lP, lQ);
+      const float zlo = fminf(zP, zQ), zhi = fmaxf(zP, zQ);
+      for (int l = l0; l <= l1; ++l) {
+        float frac = 1.0f;
+        if (l0 != l1) {
+          const float lo = (l == l0) ? zlo : M.z0 + l * M.dz;
+          const float hi = (l == l1) ? zhi : M.z0 + (l + 1) * M.dz;
+          frac = fmaxf(hi - lo, 0.f) / (zhi - zlo);
+        }
+        const float len = ell * frac;
+        const float bl = __ldg(M.lb + l), al = __ldg(M.la + l);
+        atomicAdd(s + l, len * bl * bl);
+        atomicAdd(s + NL + l, len * al * al);
+      }
+    }
+  }
+  __syncwarp();
+  double* out = sums + static_cast<size_t>(pair) * 4 * NL;
+  for (int j = lane; j < 2 * NL; j += 32) {
+    const double v = s[j];
+    if (v != 0.0) {
+      atomicAdd(out + j, v);
+      atomicAdd(out + 2 * NL + j, v * v);
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_logp(const DMedium& M, const DPair& S, const float* xyz, const int* n, int batch, int cap,
@@ -474,6 +540,17 @@ cudaError_t launch_trace(const DMedium& M, const DPair& S, unsigned long long se
   if (blocks > maxb) blocks = maxb;
   trace_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(M, S, seed, photon0, n_photons, r_reject,
                                                              max_scatter, out5);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_scores(const DMedium& M, const DPair* pairs, const int* chain_pair, const long long* chain_base,
+                                const float* xyz, const int* n, int total, double* sums, cudaStream_t s) {
+  if (total == 0) return cudaSuccess;
+  const size_t smem = 4u * 2u * static_cast<size_t>(M.n_layers) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(chain_layer_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  chain_layer_score_kernel<<<(total + 3) / 4, 128, smem, s>>>(M, pairs, chain_pair, chain_base, xyz, n, total, sums);
   return cudaGetLastError();
 }
 

@@ -366,7 +366,9 @@ def test_accumulators_replay_oracle(api, ctx, oracle_lib):
         assert acc[c, 0] == oa["n_rec"][c] and acc[c, 1] == oa["n_direct"][c] and acc[c, 2] == oa["sum_n"][c]
         assert abs(acc[c, 3] / oa["sum_L"][c] - 1) < 1e-5
         assert abs(acc[c, 4] / oa["sum_L2"][c] - 1) < 1e-5
-        assert abs(acc[c, 5] - oa["sum_score"][c, 2]) < 1e-4 * (abs(oa["sum_score"][c, 2]) + oa["n_rec"][c])
+        # gradient tolerance (1e-3 relative): per-vertex d log sigma / dg terms are large and cancel,
+        # and the running sum is kept in FP32 between exact refreshes
+        assert abs(acc[c, 5] - oa["sum_score"][c, 2]) < 1e-3 * (abs(oa["sum_score"][c, 2]) + oa["n_rec"][c])
         assert np.array_equal(acc[c, 8:12], oa["prop"][c]) and np.array_equal(acc[c, 12:16], oa["acc"][c])
 
 
@@ -420,3 +422,70 @@ def test_bridge_intensity_single_scatter(api, ctx):
     ref = Q.z2_closed(1.0, 0.1, 2.2) + Q.z3(1.0, 0.1, 0.5, 5.0, 0.9)
     assert abs(I - ref) < 3 * se, (I, se, ref)
     assert se / I < 0.02
+
+
+def _layered_small(n_chains, n_steps, cap):
+    rng = np.random.default_rng(31)
+    med = S.Medium(S.LAYERED, g=0.9, z0=-1.0, dz=0.4, lambda_s_layers=0.6 * np.exp(0.3 * rng.normal(size=8)),
+                   lambda_a_layers=5.0 * np.exp(0.3 * rng.normal(size=8)))
+    run = S.Run(seed=77, n_steps=n_steps, burn_in=n_steps // 10, sigma=0.05)
+    return S.Scene("layered_small", med, [S.Source((0.0, 0.0, -0.4))], [S.Sensor((0.3, 0.0, 0.6), 0.2)],
+                   [S.Pair(0, 0, n_chains, cap)], run)
+
+
+def test_layered_intensity_matches_oracle(api, ctx, oracle_lib):
+    """Layered medium: the direct-sector integral and the cap-3 intensity of the
+    general kernel agree with the oracle's."""
+    O = oracle_lib
+    sc = _layered_small(4096, 20000, 3)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    ch.run_steps(sc.run.n_steps)
+    e = ch.read_estimator()[0]
+    m, s, d = _oracle_objs(O, sc.medium, sc.sources[0], sc.sensors[0])
+    assert abs(e["z2"] / O.z2(m, s, d) - 1) < 1e-5
+    oc = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 256, 3)
+    oc.run(sc.run.n_steps)
+    I, se, _ = O.direct_estimate(oc.accumulators(), O.z2(m, s, d))
+    assert abs(e["intensity"] - I) < 3 * math.hypot(se, e["std_err"]), (e["intensity"], e["std_err"], I, se)
+
+
+def test_layered_gradients(api, ctx, oracle_lib):
+    """Per-layer score-function gradients (2L parameters): the estimator equals
+    I times the mean per-state score of pmc_score, which matches the FP64
+    oracle and central finite differences of the density at h = 1e-3."""
+    import copy
+    import torch
+    O = oracle_lib
+    sc = _layered_small(8192, 4000, 64)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    ch.run_steps(sc.run.n_steps)
+    grad, grad_se = ch.grad_estimator()
+    I = ch.read_estimator()[0]["intensity"]
+    xyz, n, _ = ch.read_states()
+    xt = torch.from_numpy(np.ascontiguousarray(xyz.transpose(1, 0, 2))).cuda()
+    nt = torch.from_numpy(n).cuda()
+    scr = api.score(ctx, medium, geom, 0, xt, nt).cpu().numpy().astype(np.float64)
+    scale = np.abs(scr.mean(axis=0)).max()
+    assert np.all(np.abs(grad[0] / I - scr.mean(axis=0)) <= 1e-4 * scale)
+    assert np.all(grad_se[0] > 0)
+    m, s, d = _oracle_objs(O, sc.medium, sc.sources[0], sc.sensors[0])
+    ref = np.array([O.score(m, s, d, xyz[c, :, : n[c]].T.astype(np.float64)) for c in range(0, len(n), 4)])
+    assert np.all(np.abs(scr[::4].mean(axis=0) - ref.mean(axis=0)) <= 1e-3 * scale)
+    lp0 = api.logp(ctx, medium, geom, 0, xt, nt).cpu().numpy().astype(np.float64)
+    L = sc.medium.n_layers
+    for j in (2, 3, L + 2):
+        arr = "lambda_s_layers" if j < L else "lambda_a_layers"
+        v = getattr(sc.medium, arr)[j % L]
+        h = 1e-3 * v
+        ratios = []
+        for sgn in (+1, -1):
+            mm = copy.deepcopy(sc.medium)
+            getattr(mm, arr)[j % L] = v + sgn * h
+            lp = api.logp(ctx, api.Medium(ctx, mm), geom, 0, xt, nt).cpu().numpy().astype(np.float64)
+            ratios.append(np.exp(lp - lp0))
+        fd = ((ratios[0] - ratios[1]) / (2 * h)).mean()
+        assert abs(fd - scr[:, j].mean()) <= 1e-3 * scale, (j, fd, scr[:, j].mean())
