@@ -40,6 +40,16 @@ UNIT = "proposals/s"
 FP32_PER_PROPOSAL = {"interior": 145.0, "end": 95.0, "birth": 206.0, "death": 122.0}
 MUFU_PER_PROPOSAL = {"interior": 23.0, "end": 16.0, "birth": 30.0, "death": 19.0}
 MUFU_LANES_PER_SM = 16
+
+WORKLOAD_TEXT = {
+    "detector": "detector: 1 pair, D=50 m, R=0.165 m, lambda_s=5 m, lambda_a=100 m, g=0.94, 65,536 chains x "
+                "100,000 steps, cap 256",
+    "plain": "plain: 1 pair, D=1 m, R=0.1 m, lambda_s=0.5 m, lambda_a=5 m, g=0.9, cap 64",
+    "gradients": "gradients: plain geometry, MALA eps=0.02 m, 65,536 chains, score accumulation",
+    "batched": "batched: 4,096 pairs, D~U(5,150) m, chains~U{16..512}, caps 64..1024, lambda_s=0.5 m, "
+               "lambda_a=5 m, g=0.9",
+    "layered": "layered: 100 x 10 m layers, 60 sensors x 8,192 chains, cap 1,024, g=0.94",
+}
 FP32_LANES_PER_SM = 128
 
 
@@ -56,6 +66,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--warps-per-block", type=int, default=0)
+    p.add_argument("--time-to-target", type=float, default=0.0,
+                   help="instead of the throughput line: wall time to this relative intensity error for plain "
+                        "RJMCMC, batched MALA chains and the GPU forward tracer on the plain / detector geometry")
+    p.add_argument("--geometry", default="plain", help="geometry of --time-to-target: plain or detector")
     return p.parse_args()
 
 
@@ -126,6 +140,10 @@ def scene_for(args):
         return S.plain(n_chains=args.chains, n_steps=args.run_steps)
     if args.workload == "gradients":
         return S.gradients(n_chains=args.chains, n_steps=args.run_steps)
+    if args.workload == "batched":
+        return S.batched(n_steps=args.run_steps)
+    if args.workload == "layered":
+        return S.layered(n_steps=args.run_steps)
     raise SystemExit(f"unknown workload {args.workload}")
 
 
@@ -218,6 +236,23 @@ def reference_arm(args):
     return 0
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Weak scaling: every rank runs its own replica of the workload, with its
+    own Philox key."""
+    return int(seed) + 1000 * int(rank)
+
+
+def max_over_ranks(ms: float, dist, device="cpu") -> float:
+    """The bench's step time is the slowest rank's (one all-reduce of a
+    scalar; the only collective of the run)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def ours(args):
     import numpy as np
     import torch
@@ -234,7 +269,7 @@ def ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     sc = scene_for(args)
-    sc.run.seed = sc.run.seed + 1000 * rank  # weak scaling: every rank its own chains
+    sc.run.seed = rank_seed(sc.run.seed, rank)
     ctx = api.Context(local)
     medium = api.Medium(ctx, sc.medium)
     geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
@@ -277,11 +312,7 @@ def ours(args):
         step_ms.append(s0.elapsed_time(s1))
         kern_ms.append(k0.elapsed_time(k1))
     clocks = clock.stop() if clock else None
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     ms_per_step = total_ms / args.steps
     value = world * props_per_step / (ms_per_step / 1e3)
 
@@ -341,11 +372,11 @@ def ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{sc.name}: 1 pair, D=50 m, R=0.165 m, lambda_s=5 m, lambda_a=100 m, g=0.94"
-                       if sc.name == "detector" else sc.name,
+            "config": {"workload": WORKLOAD_TEXT.get(sc.name, sc.name),
                        "chains": n_chains, "steps_per_chain": sc.run.n_steps, "vertex_cap": sc.pairs[0].cap,
                        "global_batch": n_chains * world, "parallelism": f"replicas x{world}",
-                       "l2": "flushed between steps (256 MB write)", "accumulators": "f64"},
+                       "l2": "flushed between steps (256 MB write)", "accumulators": "f64",
+                       "launch": chains.launch_info()},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "pipe": bound_pipe,
@@ -367,8 +398,89 @@ def ours(args):
     return 0
 
 
+def time_to_target(args):
+    """Wall time until the intensity estimate reaches the target relative
+    standard error and lies within max(target, 3 SE) of a reference value from
+    a long forward-tracer run, for (a) plain RJMCMC (64 chains, Gaussian
+    steps), (b) batched MALA chains (65,536), (c) the GPU forward tracer.
+    Budgets double until the criterion holds or 120 s have passed."""
+    import torch
+    from paper_1811_04156_gb300 import build as B
+    B.build()
+    from paper_1811_04156_gb300 import api, scenes as S
+    tgt = args.time_to_target
+    geom_name = args.geometry
+    sc_plain = S.plain() if geom_name == "plain" else S.detector(n_chains=64)
+    ctx = api.Context(0)
+    med = api.Medium(ctx, sc_plain.medium)
+    cap = sc_plain.pairs[0].cap
+    # reference value from a long tracer run
+    g1 = api.Geometry(ctx, sc_plain.sources, sc_plain.sensors, [S.Pair(0, 0, 1, cap)])
+    ref_photons = 4_000_000_000 if geom_name == "plain" else 100_000_000_000
+    t0 = time.perf_counter()
+    parts = []
+    left = ref_photons
+    while left > 0:
+        k = min(left, 20_000_000_000)
+        parts.append(api.trace(ctx, med, g1, 0, 123457, k, photon0=ref_photons - left, max_scatter=cap - 2))
+        left -= k
+    N = sum(p["photons"] for p in parts)
+    I_ref = sum(p["I"] * p["photons"] for p in parts) / N
+    se_ref = math.sqrt(sum((p["se"] * p["photons"]) ** 2 for p in parts)) / N
+    ref_s = time.perf_counter() - t0
+    out = {"target_rel_err": tgt, "geometry": geom_name, "reference": {"intensity": I_ref, "std_err": se_ref,
+                                                                     "photons": N, "seconds": ref_s}}
+
+    def ok(I, se):
+        return I > 0 and se / I <= tgt and abs(I - I_ref) <= max(tgt * I_ref, 3 * math.hypot(se, se_ref))
+
+    def run_chains(n_chains, within, increment):
+        sc = S.plain(n_chains=n_chains) if geom_name == "plain" else S.detector(n_chains=n_chains)
+        sc.run.within = within
+        sc.run.burn_in = 1000 if geom_name == "plain" else 10_000
+        if within == S.WITHIN_MALA:
+            sc.run.mala_step = 0.02
+        geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+        ch = api.Chains(ctx, med, geom, sc.run)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        steps = 0
+        e = None
+        while time.perf_counter() - t < 120.0:
+            ch.run_steps(increment)
+            steps += increment
+            e = ch.read_estimator()[0]
+            if steps > sc.run.burn_in and ok(e["intensity"], e["std_err"]):
+                break
+            increment = min(increment * 2, 1_000_000)
+        dt = time.perf_counter() - t
+        return {"seconds": dt, "steps_per_chain": steps, "chains": n_chains, "intensity": e["intensity"],
+                "std_err": e["std_err"], "reached": bool(ok(e["intensity"], e["std_err"]))}
+
+    out["plain_rjmcmc"] = run_chains(64, S.WITHIN_PERTURB, 20_000)
+    out["batched_mala"] = run_chains(65_536, S.WITHIN_MALA, 2_000)
+    # tracer with doubling photon budgets
+    t = time.perf_counter()
+    photons, acc = 1_000_000, []
+    while True:
+        acc.append(api.trace(ctx, med, g1, 0, 99, photons, photon0=sum(a["photons"] for a in acc),
+                             max_scatter=cap - 2))
+        Nn = sum(a["photons"] for a in acc)
+        I = sum(a["I"] * a["photons"] for a in acc) / Nn
+        se = math.sqrt(sum((a["se"] * a["photons"]) ** 2 for a in acc)) / Nn
+        if ok(I, se) or time.perf_counter() - t > 120.0:
+            break
+        photons *= 2
+    out["gpu_tracer"] = {"seconds": time.perf_counter() - t, "photons": Nn, "intensity": I, "std_err": se,
+                         "reached": bool(ok(I, se))}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.time_to_target > 0:
+        return time_to_target(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)

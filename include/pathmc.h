@@ -267,6 +267,14 @@ PMC_API int pmc_read_states(pmc_chains_t chains, float* xyz, int* n, uint64_t* s
 PMC_API int pmc_read_accumulators(pmc_chains_t chains, double* out, size_t n_doubles, void* stream);
 PMC_API int pmc_total_chains(pmc_chains_t chains);
 
+/* Launch shapes chosen for the chains (by the autotuner when
+ * warps_per_block = 0): one row of 6 ints per vertex-cap class, written to
+ * `out` (host): shared vertex cap, first and one-past-last position in the
+ * processing order, warps (= chains) per block, persistent grid size, 1 if
+ * the general kernel instantiation runs.  Returns the number of classes in
+ * *n_classes; writes at most max_rows rows. */
+PMC_API int pmc_chains_launch_info(pmc_chains_t chains, int* out, int max_rows, int* n_classes);
+
 /* Serialise / restore the complete chain state (positions, vertex counts,
  * step counters, accumulators) through a host buffer.  With buf == NULL,
  * pmc_save_state stores the needed size in *bytes.  Synchronises `stream`. */

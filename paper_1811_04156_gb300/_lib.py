@@ -102,6 +102,7 @@ PROTOTYPES = {
     "pmc_read_states": ([_vp, _fp, _ip, C.POINTER(C.c_uint64), C.c_int, _vp], C.c_int),
     "pmc_read_accumulators": ([_vp, _dp, C.c_size_t, _vp], C.c_int),
     "pmc_total_chains": ([_vp], C.c_int),
+    "pmc_chains_launch_info": ([_vp, _ip, C.c_int, _ip], C.c_int),
     "pmc_save_state": ([_vp, _vp, C.POINTER(C.c_size_t), _vp], C.c_int),
     "pmc_load_state": ([_vp, _vp, C.c_size_t, _vp], C.c_int),
     "pmc_request_abort": ([_vp, C.c_int], C.c_int),

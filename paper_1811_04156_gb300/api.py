@@ -240,6 +240,15 @@ class Chains:
               "pmc_read_states")
         return xyz, n, steps
 
+    def launch_info(self):
+        """Per cap class: shared cap, order range, warps per block, grid, general kernel (pmc_chains_launch_info)."""
+        rows = np.zeros((8, 6), dtype=np.int32)
+        nc = C.c_int(0)
+        check(load().pmc_chains_launch_info(self.handle, rows.ctypes.data_as(C.POINTER(C.c_int)), 8, C.byref(nc)),
+              "pmc_chains_launch_info")
+        keys = ("smem_cap", "lo", "hi", "warps_per_block", "grid", "general")
+        return [dict(zip(keys, map(int, r))) for r in rows[: nc.value]]
+
     def read_accumulators(self, stream=None):
         out = np.zeros((self.total, PMC_ACC_WORDS))
         check(load().pmc_read_accumulators(self.handle, out.ctypes.data_as(C.POINTER(C.c_double)), out.size,

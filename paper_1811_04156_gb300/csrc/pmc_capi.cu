@@ -5,6 +5,7 @@
 #include <cstring>
 #include <limits>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <string>
 #include <vector>
@@ -70,6 +71,8 @@ struct pmc_ctx_s {
   int device = 0;
   int n_sm = 0;
   size_t smem_per_sm = 0, smem_per_block = 0;
+  // autotuned warps per block, keyed by (kernel instantiation, shared vertex cap, chain-count bucket)
+  std::map<std::tuple<bool, int, int>, int> tuned;
 };
 
 struct pmc_medium_s {
@@ -181,6 +184,7 @@ struct pmc_chains_s {
   std::vector<ChainClass> classes;
   std::map<unsigned long long, cudaGraphExec_t> graphs;
   bool general = false;            // chain kernel instantiation
+  bool autotune = false;           // warps per block chosen by timing
   int init_kind = 0, init_k = 0;
   float init_jitter = 0.f;
   QrefPair* d_qp = nullptr;       // reference-density tables (pmc_bridge)
@@ -470,6 +474,120 @@ int pmc_destroy_chains(pmc_chains_t ch) {
   return PMC_OK;
 }
 
+static ChainParams class_params(pmc_chains_t ch, size_t k, unsigned long long n_steps) {
+  const ChainClass& cl = ch->classes[k];
+  ChainParams p{};
+  p.M = ch->med->d;
+  p.R = ch->run;
+  p.pairs = ch->d_pairs;
+  p.chain_pair = ch->d_chain_pair;
+  p.chain_base = ch->d_chain_base;
+  p.order = ch->d_order;
+  p.xyz = ch->d_xyz;
+  p.n = ch->d_n;
+  p.step = ch->d_step;
+  p.acc = ch->d_acc;
+  p.status = ch->d_status;
+  p.any_status = ch->d_any;
+  p.queue = ch->d_queue + k;
+  p.abort_flag = ch->d_abort;
+  p.chain_lo = cl.lo;
+  p.chain_hi = cl.hi;
+  p.n_steps = n_steps;
+  p.smem_cap = cl.smem_cap;
+  return p;
+}
+
+// Autotuner: for every cap class, time the chain kernel at 1, 2 and 4 warps
+// (chains) per block on a scratch copy of the freshly initialised state and
+// keep the fastest; results are cached per device, kernel and class.
+static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
+  const int T = ch->total;
+  float* sx = nullptr;
+  int* sn = nullptr;
+  unsigned long long* sst = nullptr;
+  double* sacc = nullptr;
+  int* sstat = nullptr;
+  bool need = false;
+  for (auto& cl : ch->classes) {
+    const int bucket = 31 - __builtin_clz(static_cast<unsigned>(std::max(1, cl.hi - cl.lo)));
+    auto it = ch->ctx->tuned.find(std::make_tuple(ch->general, cl.smem_cap, bucket));
+    if (it == ch->ctx->tuned.end()) need = true;
+  }
+  if (need) {
+    CK(dalloc(&sx, static_cast<size_t>(ch->xyz_floats)));
+    CK(dalloc(&sn, T));
+    CK(dalloc(&sst, T));
+    CK(dalloc(&sacc, static_cast<size_t>(T) * ACC_WORDS));
+    CK(dalloc(&sstat, T));
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = PMC_OK;
+  for (size_t k = 0; k < ch->classes.size() && rc == PMC_OK; ++k) {
+    ChainClass& cl = ch->classes[k];
+    const int chains = cl.hi - cl.lo;
+    const int bucket = 31 - __builtin_clz(static_cast<unsigned>(std::max(1, chains)));
+    const auto key = std::make_tuple(ch->general, cl.smem_cap, bucket);
+    auto it = ch->ctx->tuned.find(key);
+    int best_w = cl.warps_per_block;
+    if (it != ch->ctx->tuned.end()) {
+      best_w = it->second;
+    } else {
+      float best_ms = 1e30f;
+      for (int wpb : {1, 2, 4}) {
+        if (chain_smem_bytes(cl.smem_cap, wpb) > ch->ctx->smem_per_block) continue;
+        int bps = 0;
+        if (chain_occupancy(ch->general, wpb, cl.smem_cap, &bps) != cudaSuccess || bps < 1) continue;
+        const int grid = std::max(1, std::min((chains + wpb - 1) / wpb, bps * ch->ctx->n_sm));
+        ChainParams p = class_params(ch, k, 128);
+        p.xyz = sx;
+        p.n = sn;
+        p.step = sst;
+        p.acc = sacc;
+        p.status = sstat;
+        p.abort_flag = nullptr;
+        cudaError_t e = cudaMemcpyAsync(sx, ch->d_xyz, sizeof(float) * ch->xyz_floats, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sn, ch->d_n, sizeof(int) * T, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sst, 0, sizeof(unsigned long long) * T, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sacc, 0, sizeof(double) * T * ACC_WORDS, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sstat, 0, sizeof(int) * T, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = launch_chain(p, ch->general, grid, wpb, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          rc = fail(PMC_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+          break;
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_w = wpb;
+        }
+      }
+      ch->ctx->tuned[key] = best_w;
+    }
+    int bps = 0;
+    if (rc == PMC_OK && chain_occupancy(ch->general, best_w, cl.smem_cap, &bps) == cudaSuccess && bps >= 1) {
+      cl.warps_per_block = best_w;
+      cl.grid = std::max(1, std::min((chains + best_w - 1) / best_w, bps * ch->ctx->n_sm));
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sx);
+  cudaFree(sn);
+  cudaFree(sst);
+  cudaFree(sacc);
+  cudaFree(sstat);
+  CK(cudaMemsetAsync(ch->d_any, 0, sizeof(int), s));
+  return rc;
+}
+
 int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_run_desc* r, void* stream,
                     pmc_chains_t* out) {
   if (!ctx || !med || !geom || !r || !out) return fail(PMC_ERR_INVALID, "NULL argument");
@@ -561,7 +679,9 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   ch->general = med->d.kind != PMC_HOMOGENEOUS || med->d.f_sl > 0.f || r->within == PMC_WITHIN_MALA ||
                 std::any_of(ch->h_pairs.begin(), ch->h_pairs.end(),
                             [](const DPair& d) { return d.emission != PMC_EMIT_ISOTROPIC || d.rho != PMC_RHO_ONE; });
-  // launch shapes: warps per block from the request (0: default), persistent grid from occupancy
+  // launch shapes: warps per block from the request (0: autotune after the
+  // initial paths exist), persistent grid from occupancy
+  ch->autotune = r->warps_per_block <= 0;
   for (auto& cl : ch->classes) {
     int wpb = r->warps_per_block > 0 ? r->warps_per_block : 4;
     wpb = std::min(wpb, 4);
@@ -640,6 +760,10 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     cudaFree(d_user);
     cudaFree(d_user_n);
   }
+  if (ch->autotune) {
+    const int rc = autotune_classes(ch.get(), s);
+    if (rc != PMC_OK) return rc;
+  }
   *out = ch.release();
   return PMC_OK;
 }
@@ -705,27 +829,8 @@ int pmc_set_states(pmc_chains_t ch, const float* xyz, const int* n, int stride, 
 static int enqueue_steps(pmc_chains_t ch, unsigned long long n_steps, cudaStream_t s) {
   for (size_t k = 0; k < ch->classes.size(); ++k) {
     const ChainClass& cl = ch->classes[k];
-    ChainParams p{};
-    p.M = ch->med->d;
-    p.R = ch->run;
-    p.pairs = ch->d_pairs;
-    p.chain_pair = ch->d_chain_pair;
-    p.chain_base = ch->d_chain_base;
-    p.order = ch->d_order;
-    p.xyz = ch->d_xyz;
-    p.n = ch->d_n;
-    p.step = ch->d_step;
-    p.acc = ch->d_acc;
-    p.status = ch->d_status;
-    p.any_status = ch->d_any;
-    p.queue = ch->d_queue + k;
-    p.abort_flag = ch->d_abort;
-    p.chain_lo = cl.lo;
-    p.chain_hi = cl.hi;
-    p.n_steps = n_steps;
-    p.smem_cap = cl.smem_cap;
     CK(cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s));
-    CK(launch_chain(p, ch->general, cl.grid, cl.warps_per_block, s));
+    CK(launch_chain(class_params(ch, k, n_steps), ch->general, cl.grid, cl.warps_per_block, s));
   }
   return PMC_OK;
 }
@@ -860,6 +965,22 @@ int pmc_grad_estimator(pmc_chains_t ch, double* grad, double* grad_se, size_t le
 }
 
 int pmc_total_chains(pmc_chains_t ch) { return ch ? ch->total : 0; }
+
+int pmc_chains_launch_info(pmc_chains_t ch, int* out, int max_rows, int* n_classes) {
+  if (ch == nullptr || n_classes == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  *n_classes = static_cast<int>(ch->classes.size());
+  for (int k = 0; k < *n_classes && k < max_rows && out != nullptr; ++k) {
+    const ChainClass& cl = ch->classes[k];
+    int* row = out + 6 * k;
+    row[0] = cl.smem_cap;
+    row[1] = cl.lo;
+    row[2] = cl.hi;
+    row[3] = cl.warps_per_block;
+    row[4] = cl.grid;
+    row[5] = ch->general ? 1 : 0;
+  }
+  return PMC_OK;
+}
 
 int pmc_read_states(pmc_chains_t ch, float* xyz, int* n, uint64_t* steps, int stride, void* stream) {
   if (ch == nullptr || xyz == nullptr || n == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
