@@ -662,11 +662,24 @@ __global__ void init_kernel(const InitParams p) {
   for (int k = 0; k < ACC_WORDS; ++k) p.acc[static_cast<size_t>(c) * ACC_WORDS + k] = 0.0;
 }
 
+// The dynamic shared-memory limit is a property of the kernel, shared by every
+// launch: set it once to the device's per-block maximum so that classes with
+// different vertex caps can all launch.
 template <bool kGen>
-cudaError_t set_attributes(int smem_bytes) {
-  cudaError_t e = cudaFuncSetAttribute(chain_kernel<kGen>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+cudaError_t set_attributes() {
+  static int done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(chain_kernel<kGen>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(chain_kernel<kGen>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(chain_kernel<kGen>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
+  return e;
 }
 
 }  // namespace
@@ -678,7 +691,7 @@ size_t chain_smem_bytes(int smem_cap, int warps_per_block) {
 
 cudaError_t chain_occupancy(bool general, int warps_per_block, int smem_cap, int* blocks_per_sm) {
   const size_t sm = chain_smem_bytes(smem_cap, warps_per_block);
-  cudaError_t e = general ? set_attributes<true>(static_cast<int>(sm)) : set_attributes<false>(static_cast<int>(sm));
+  cudaError_t e = general ? set_attributes<true>() : set_attributes<false>();
   if (e != cudaSuccess) return e;
   if (general)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<true>, warps_per_block * 32, sm);
