@@ -434,23 +434,26 @@ def time_to_target(args):
     def ok(I, se):
         return I > 0 and se / I <= tgt and abs(I - I_ref) <= max(tgt * I_ref, 3 * math.hypot(se, se_ref))
 
-    def run_chains(n_chains, within, increment):
+    def run_chains(n_chains, within, increment, seeded=False):
         sc = S.plain(n_chains=n_chains) if geom_name == "plain" else S.detector(n_chains=n_chains)
         sc.run.within = within
-        sc.run.burn_in = 1000 if geom_name == "plain" else 10_000
+        sc.run.burn_in = 0 if seeded else (1000 if geom_name == "plain" else 10_000)
         if within == S.WITHIN_MALA:
-            sc.run.mala_step = 0.02
+            sc.run.mala_step = 0.02 if geom_name == "plain" else 0.5
         geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
         ch = api.Chains(ctx, med, geom, sc.run)
         torch.cuda.synchronize()
         t = time.perf_counter()
+        if seeded:
+            # equilibrium seeds from the forward tracer (inside the timed region)
+            api.seed_from_tracer(ch, seed=4321, photons_per_round=1 << 26)
         steps = 0
         e = None
         while time.perf_counter() - t < 120.0:
             ch.run_steps(increment)
             steps += increment
             e = ch.read_estimator()[0]
-            if steps > sc.run.burn_in and ok(e["intensity"], e["std_err"]):
+            if steps > sc.run.burn_in and e["n_samples"] > 0 and ok(e["intensity"], e["std_err"]):
                 break
             increment = min(increment * 2, 1_000_000)
         dt = time.perf_counter() - t
@@ -459,6 +462,8 @@ def time_to_target(args):
 
     out["plain_rjmcmc"] = run_chains(64, S.WITHIN_PERTURB, 20_000)
     out["batched_mala"] = run_chains(65_536, S.WITHIN_MALA, 2_000)
+    out["batched_mala_tracer_seeded"] = run_chains(65_536, S.WITHIN_MALA, 500, seeded=True)
+    out["batched_perturb_tracer_seeded"] = run_chains(65_536, S.WITHIN_PERTURB, 500, seeded=True)
     # tracer with doubling photon budgets
     t = time.perf_counter()
     photons, acc = 1_000_000, []

@@ -384,6 +384,18 @@ PMC_API int pmc_trace_noalloc(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geo
                               int n_pairs, uint64_t seed, uint64_t photon0, uint64_t n_photons,
                               double r_reject, int max_scatter, double* out, void* stream);
 
+/* Equilibrium seeds for chains (paper: chains are seeded from ray-traced
+ * paths, section "Implementation"): traces n_photons photons as pmc_trace
+ * does and keeps each detected photon with probability w * rho (its weight,
+ * <= 1), so every kept path is an exact draw from the normalised path density
+ * truncated to max_scatter + 2 vertices.  Kept paths go to out_xyz (device,
+ * [3][max_paths][stride] absolute positions, stride >= max_scatter + 2) and
+ * out_n (device, [max_paths]); *n_accepted (host) counts all kept paths, also
+ * those beyond max_paths.  Synchronises `stream`. */
+PMC_API int pmc_trace_paths(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair, uint64_t seed,
+                            uint64_t photon0, uint64_t n_photons, double r_reject, int max_scatter, int max_paths,
+                            float* out_xyz, int* out_n, int stride, uint64_t* n_accepted, void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 PMC_API const char* pmc_last_error(void);
 

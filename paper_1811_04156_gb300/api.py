@@ -397,6 +397,60 @@ def trace_noalloc(ctx: Context, medium: Medium, geom: Geometry, pairs, seed: int
     return out
 
 
+def trace_paths(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: int, n_photons: int,
+                max_paths: int, photon0: int = 0, max_scatter: Optional[int] = None, r_reject: float = math.inf,
+                stride: Optional[int] = None, stream=None):
+    """Weight-thinned detected tracer paths (pmc_trace_paths): exact draws from
+    the normalised path density; returns (xyz (3, kept, stride), n, kept)."""
+    cap = geom.pairs[pair].cap
+    ms = cap - 2 if max_scatter is None else int(max_scatter)
+    stride = int(stride or ms + 2)
+    xyz = torch.zeros((3, int(max_paths), stride), dtype=torch.float32, device="cuda")
+    n = torch.zeros(int(max_paths), dtype=torch.int32, device="cuda")
+    acc = C.c_uint64(0)
+    check(load().pmc_trace_paths(ctx.handle, medium.handle, geom.handle, int(pair), int(seed), int(photon0),
+                                 int(n_photons), float(r_reject), ms, int(max_paths), C.c_void_p(xyz.data_ptr()),
+                                 C.c_void_p(n.data_ptr()), stride, C.byref(acc), _stream(stream)), "pmc_trace_paths")
+    kept = min(int(acc.value), int(max_paths))
+    return xyz[:, :kept], n[:kept], int(acc.value)
+
+
+def seed_from_tracer(chains: "Chains", seed: int = 2024, photons_per_round: int = 1 << 28, max_rounds: int = 64):
+    """Initialise every chain with an equilibrium path: weight-thinned tracer
+    paths per pair, reused cyclically when fewer than the pair's chains were
+    found; returns the photons traced per pair."""
+    geom = chains.geom
+    stride = geom.max_cap
+    total_xyz = np.zeros((chains.total, 3, stride), dtype=np.float32)
+    total_n = np.zeros(chains.total, dtype=np.int32)
+    used = []
+    c0 = 0
+    for p, pr in enumerate(geom.pairs):
+        got_x, got_n, photons = [], [], 0
+        need = pr.n_chains
+        for _ in range(max_rounds):
+            xyz, n, acc = trace_paths(chains.ctx, chains.medium, geom, p, seed, photons_per_round, need,
+                                      photon0=photons, stride=stride)
+            photons += photons_per_round
+            if len(n):
+                got_x.append(xyz.cpu().numpy())
+                got_n.append(n.cpu().numpy())
+            if sum(len(a) for a in got_n) >= need:
+                break
+        if not got_n:
+            raise RuntimeError(f"no detected photon for pair {p} after {photons} photons")
+        X = np.concatenate(got_x, axis=1)
+        Nn = np.concatenate(got_n)
+        idx = np.arange(need) % len(Nn)
+        total_xyz[c0:c0 + need] = X[:, idx, :].transpose(1, 0, 2)
+        total_n[c0:c0 + need] = Nn[idx]
+        used.append(photons)
+        c0 += need
+    chains.set_states(total_xyz, total_n)
+    torch.cuda.current_stream().synchronize()
+    return used
+
+
 class LogP(torch.autograd.Function):
     """log p of a batch of paths; backward is the hand-written adjoint kernel."""
 

@@ -1255,4 +1255,29 @@ int pmc_bridge(pmc_chains_t ch, uint64_t n_draws, uint64_t seed, double* out, vo
   return PMC_OK;
 }
 
+int pmc_trace_paths(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, uint64_t seed, uint64_t photon0,
+                    uint64_t n_photons, double r_reject, int max_scatter, int max_paths, float* out_xyz, int* out_n,
+                    int stride, uint64_t* n_accepted, void* stream) {
+  const DPair* d = pair_of(geom, pair, false);
+  if (!ctx || !med || !d || !out_xyz || !out_n || !n_accepted) return fail(PMC_ERR_INVALID, "bad argument");
+  if (max_scatter < 0 || !(r_reject > 0) || max_paths < 0) return fail(PMC_ERR_INVALID, "bad tracer limits");
+  if (stride < max_scatter + 2) return fail(PMC_ERR_INVALID, "stride must hold max_scatter + 2 vertices");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned int* d_count = nullptr;
+  CK(dalloc(&d_count, 1));
+  const float rr = std::isfinite(r_reject) ? static_cast<float>(r_reject) : std::numeric_limits<float>::infinity();
+  cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess)
+    e = launch_trace_paths(med->d, *d, seed, photon0, n_photons, rr, max_scatter, max_paths, stride, out_xyz, out_n,
+                           d_count, ctx->n_sm, s);
+  unsigned int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_count);
+  CK(e);
+  *n_accepted = h;
+  return PMC_OK;
+}
+
 }  // extern "C"

@@ -118,6 +118,12 @@ cudaError_t launch_trace(const DMedium& M, const DPair& S, unsigned long long se
 cudaError_t launch_layer_scores(const DMedium& M, const DPair* pairs, const int* chain_pair, const long long* chain_base,
                                 const float* xyz, const int* n, int total, double* sums, cudaStream_t s);
 
+// Forward tracer recording weight-thinned detected paths (exact draws from the
+// normalised path density), used to seed chains at equilibrium.
+cudaError_t launch_trace_paths(const DMedium& M, const DPair& S, unsigned long long seed, unsigned long long photon0,
+                               unsigned long long n_photons, float r_reject, int max_scatter, int max_paths, int stride,
+                               float* out_xyz, int* out_n, unsigned int* count, int n_sm, cudaStream_t s);
+
 // pmc_bridge.cu: reference density q_ref and the geometric bridge.
 // Per pair: qtab[off + n] = log P_ref(n) (n = 0..cap, -inf below 2) and
 // qtab[off + cap + 1 + n] = P_ref(N <= n); log_qend = -log(visible cap area).

@@ -348,82 +348,150 @@ __device__ float sample_cos(const DMedium& M, float u, float umix) {
   return fminf(fmaxf((1.0f + g * g - q * q) / (2.0f * g), -1.0f), 1.0f);
 }
 
+// One photon of Algorithm 1 from the source (frame origin): free paths from
+// b(x), absorption weight ln w, detection at the first sensor intersection,
+// rejection beyond r_reject, at most max_scatter scatterings.  With kRecord
+// the vertices (source, scattering points, hit point) are written to
+// (ox, oy, oz) in absolute coordinates.  u_acc is a spare uniform of the
+// detection step (used to thin detected photons by their weight).
+struct PhotonResult {
+  bool hit;
+  float lw;     // ln(w rho) of a detected photon
+  float L;      // path length
+  int nsc;      // scatterings
+  float u_acc;
+};
+
+template <bool kRecord>
+__device__ PhotonResult trace_photon(const DMedium& M, const DPair& S, uint32_t k0, uint32_t k1, unsigned long long ph,
+                                     float r_reject, int max_scatter, float* ox, float* oy, float* oz) {
+  const uint32_t plo = static_cast<uint32_t>(ph), phi = static_cast<uint32_t>(ph >> 32);
+  const float3 c = f3(S.c[0], S.c[1], S.c[2]);
+  uint4 r = philox4x32_10(make_uint4(plo, phi, 0u, PUR_TRACE), k0, k1);
+  float3 x = f3(0.f, 0.f, 0.f);
+  float3 nh;
+  {
+    float sp, cp;
+    sincospif(2.0f * u01(r.y), &sp, &cp);
+    if (S.emission != 0) {
+      const float u0 = u01(r.x);
+      const float ww = 1.0f + logf(fmaf(1.0f - u0, expf(-2.0f * S.kappa), u0)) / S.kappa;
+      const float sw = sqrtf(fmaxf(0.f, 1.0f - ww * ww));
+      const float3 d = f3(S.dir[0], S.dir[1], S.dir[2]);
+      float3 e1, e2;
+      onb(d, e1, e2);
+      nh = ww * d + sw * (cp * e1 + sp * e2);
+    } else {
+      const float ww = 2.0f * u01(r.x) - 1.0f;
+      const float sw = sqrtf(fmaxf(0.f, 1.0f - ww * ww));
+      nh = f3(sw * cp, sw * sp, ww);
+    }
+  }
+  if (kRecord) {
+    ox[0] = S.org[0];
+    oy[0] = S.org[1];
+    oz[0] = S.org[2];
+  }
+  PhotonResult res{false, 0.f, 0.f, 0, 1.f};
+  float lnw = 0.f, L = 0.f;
+  for (int i = 0; i <= max_scatter; ++i) {
+    r = philox4x32_10(make_uint4(plo, phi, static_cast<uint32_t>(i + 1), PUR_TRACE), k0, k1);
+    const float tau = -logf(u01(r.x));
+    const float dL = free_path(M, x.z + S.zoff, nh.z, tau);
+    const float dist = ray_sphere(x, nh, c, S.R2);
+    const float go = fminf(dist, dL);
+    const float3 end = x + go * nh;
+    float ta, tb;
+    seg_tau(M, x.z + S.zoff, end.z + S.zoff, go, ta, tb);
+    lnw -= ta;
+    if (dist < dL) {
+      float lw = lnw;
+      if (S.rho != 0) {
+        const float3 nu = sensor_normal(S, end);
+        const float xx = dot(nu, f3(S.rho_hat[0], S.rho_hat[1], S.rho_hat[2]));
+        lw += fmaf(3.0f, xx, -1.0f) - logf(coshf(fmaf(2.0f, xx, 0.7f)));
+      }
+      if (kRecord) {
+        ox[i + 1] = end.x + S.org[0];
+        oy[i + 1] = end.y + S.org[1];
+        oz[i + 1] = end.z + S.org[2];
+      }
+      res.hit = true;
+      res.lw = lw;
+      res.L = L + dist;
+      res.nsc = i;
+      res.u_acc = u01(r.y);
+      return res;
+    }
+    const float3 rel = x - c;
+    if (dot(rel, rel) > r_reject * r_reject) break;
+    if (i == max_scatter) break;
+    x = end;
+    L += dL;
+    if (kRecord) {
+      ox[i + 1] = x.x + S.org[0];
+      oy[i + 1] = x.y + S.org[1];
+      oz[i + 1] = x.z + S.org[2];
+    }
+    const float cs = sample_cos(M, u01(r.y), u01(r.w));
+    const float sn = sqrtf(fmaxf(0.f, 1.0f - cs * cs));
+    float sp, cp;
+    sincospif(2.0f * u01(r.z), &sp, &cp);
+    float3 e1, e2;
+    onb(nh, e1, e2);
+    nh = cs * nh + sn * (cp * e1 + sp * e2);
+    nh = rsqrtf(dot(nh, nh)) * nh;
+  }
+  return res;
+}
+
 __global__ void __launch_bounds__(256) trace_kernel(const DMedium M, const DPair S, unsigned long long seed,
                                                     unsigned long long photon0, unsigned long long n_photons,
                                                     float r_reject, int max_scatter, double* __restrict__ out5) {
   __shared__ double sh[8 * 5];
   const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
-  const float3 c = f3(S.c[0], S.c[1], S.c[2]);
   double v[5] = {0, 0, 0, 0, 0};
   const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
   for (unsigned long long q = blockIdx.x * blockDim.x + threadIdx.x; q < n_photons; q += stride) {
-    const unsigned long long ph = photon0 + q;
-    const uint32_t plo = static_cast<uint32_t>(ph), phi = static_cast<uint32_t>(ph >> 32);
-    uint4 r = philox4x32_10(make_uint4(plo, phi, 0u, PUR_TRACE), k0, k1);
-    float3 x = f3(0.f, 0.f, 0.f);
-    float3 nh;
-    {
-      float sp, cp;
-      sincospif(2.0f * u01(r.y), &sp, &cp);
-      if (S.emission != 0) {
-        const float u0 = u01(r.x);
-        const float ww = 1.0f + logf(fmaf(1.0f - u0, expf(-2.0f * S.kappa), u0)) / S.kappa;
-        const float sw = sqrtf(fmaxf(0.f, 1.0f - ww * ww));
-        const float3 d = f3(S.dir[0], S.dir[1], S.dir[2]);
-        float3 e1, e2;
-        onb(d, e1, e2);
-        nh = ww * d + sw * (cp * e1 + sp * e2);
-      } else {
-        const float ww = 2.0f * u01(r.x) - 1.0f;
-        const float sw = sqrtf(fmaxf(0.f, 1.0f - ww * ww));
-        nh = f3(sw * cp, sw * sp, ww);
-      }
-    }
-    float lnw = 0.f, L = 0.f;
+    const PhotonResult pr = trace_photon<false>(M, S, k0, k1, photon0 + q, r_reject, max_scatter, nullptr, nullptr,
+                                                nullptr);
     v[3] += 1.0;
-    for (int i = 0; i <= max_scatter; ++i) {
-      r = philox4x32_10(make_uint4(plo, phi, static_cast<uint32_t>(i + 1), PUR_TRACE), k0, k1);
-      const float tau = -logf(u01(r.x));
-      const float dL = free_path(M, x.z + S.zoff, nh.z, tau);
-      const float dist = ray_sphere(x, nh, c, S.R2);
-      const float go = fminf(dist, dL);
-      const float3 end = x + go * nh;
-      float ta, tb;
-      seg_tau(M, x.z + S.zoff, end.z + S.zoff, go, ta, tb);
-      lnw -= ta;
-      if (dist < dL) {
-        float lw = lnw;
-        if (S.rho != 0) {
-          const float3 nu = sensor_normal(S, end);
-          const float xx = dot(nu, f3(S.rho_hat[0], S.rho_hat[1], S.rho_hat[2]));
-          lw += fmaf(3.0f, xx, -1.0f) - logf(coshf(fmaf(2.0f, xx, 0.7f)));
-        }
-        const double W = static_cast<double>(expf(lw));
-        v[0] += W;
-        v[1] += W * W;
-        v[2] += 1.0;
-        v[4] += W * static_cast<double>(L + dist);
-        break;
-      }
-      const float3 rel = x - c;
-      if (dot(rel, rel) > r_reject * r_reject) break;
-      if (i == max_scatter) break;
-      x = end;
-      L += dL;
-      const float cs = sample_cos(M, u01(r.y), u01(r.w));
-      const float sn = sqrtf(fmaxf(0.f, 1.0f - cs * cs));
-      float sp, cp;
-      sincospif(2.0f * u01(r.z), &sp, &cp);
-      float3 e1, e2;
-      onb(nh, e1, e2);
-      nh = cs * nh + sn * (cp * e1 + sp * e2);
-      nh = rsqrtf(dot(nh, nh)) * nh;
+    if (pr.hit) {
+      const double W = static_cast<double>(expf(pr.lw));
+      v[0] += W;
+      v[1] += W * W;
+      v[2] += 1.0;
+      v[4] += W * static_cast<double>(pr.L);
     }
   }
   block_sum<5>(v, sh);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) atomicAdd(out5 + k, v[k]);
+  }
+}
+
+// Detected photons thinned by their weight w rho (<= 1): an accepted path is an
+// exact draw from the normalised path density (cap-truncated by max_scatter).
+// Accepted paths are written to out_xyz [3][max_paths][stride] (absolute) and
+// out_n; *count counts every accepted path (also those beyond max_paths).
+__global__ void __launch_bounds__(256) trace_paths_kernel(const DMedium M, const DPair S, unsigned long long seed,
+                                                          unsigned long long photon0, unsigned long long n_photons,
+                                                          float r_reject, int max_scatter, int max_paths, int stride,
+                                                          float* __restrict__ out_xyz, int* __restrict__ out_n,
+                                                          unsigned int* __restrict__ count) {
+  const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  const unsigned long long gstride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+  const size_t plane = static_cast<size_t>(max_paths) * stride;
+  for (unsigned long long q = blockIdx.x * blockDim.x + threadIdx.x; q < n_photons; q += gstride) {
+    const PhotonResult pr = trace_photon<false>(M, S, k0, k1, photon0 + q, r_reject, max_scatter, nullptr, nullptr,
+                                                nullptr);
+    if (!pr.hit || !(pr.u_acc < expf(pr.lw))) continue;
+    const unsigned int slot = atomicAdd(count, 1u);
+    if (slot >= static_cast<unsigned int>(max_paths)) continue;
+    float* ox = out_xyz + static_cast<size_t>(slot) * stride;
+    trace_photon<true>(M, S, k0, k1, photon0 + q, r_reject, max_scatter, ox, ox + plane, ox + 2 * plane);
+    out_n[slot] = pr.nsc + 2;
   }
 }
 
@@ -551,6 +619,19 @@ cudaError_t launch_layer_scores(const DMedium& M, const DPair* pairs, const int*
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   chain_layer_score_kernel<<<(total + 3) / 4, 128, smem, s>>>(M, pairs, chain_pair, chain_base, xyz, n, total, sums);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_paths(const DMedium& M, const DPair& S, unsigned long long seed, unsigned long long photon0,
+                               unsigned long long n_photons, float r_reject, int max_scatter, int max_paths, int stride,
+                               float* out_xyz, int* out_n, unsigned int* count, int n_sm, cudaStream_t s) {
+  if (n_photons == 0) return cudaSuccess;
+  unsigned long long blocks = (n_photons + 255) / 256;
+  const unsigned long long maxb = static_cast<unsigned long long>(n_sm) * 8ull;
+  if (blocks > maxb) blocks = maxb;
+  trace_paths_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(M, S, seed, photon0, n_photons, r_reject,
+                                                                   max_scatter, max_paths, stride, out_xyz, out_n,
+                                                                   count);
   return cudaGetLastError();
 }
 

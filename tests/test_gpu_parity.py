@@ -490,3 +490,44 @@ def test_layered_gradients(api, ctx, oracle_lib):
             ratios.append(np.exp(lp - lp0))
         fd = ((ratios[0] - ratios[1]) / (2 * h)).mean()
         assert abs(fd - scr[:, j].mean()) <= 1e-3 * scale, (j, fd, scr[:, j].mean())
+
+
+def test_tracer_seeds_are_exact_draws(api, ctx, oracle_lib):
+    """Weight-thinned detected tracer paths at cap 3: the share of n = 2 paths
+    is Z2 / (Z2 + Z3) (independent quadrature), and every seed is a valid state."""
+    import torch
+    O = oracle_lib
+    sc = S.plain(cap=3)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    xyz, n, acc = api.trace_paths(ctx, medium, geom, 0, 11, 400_000_000, 200_000)
+    assert acc >= 200_000 and len(n) == 200_000
+    n = n.cpu().numpy()
+    z2 = Q.z2_closed(1.0, 0.1, 2.2)
+    frac = z2 / (z2 + Q.z3(1.0, 0.1, 0.5, 5.0, 0.9))
+    se = math.sqrt(frac * (1 - frac) / len(n))
+    assert abs((n == 2).mean() - frac) < 4 * se, ((n == 2).mean(), frac, se)
+    lp = api.logp(ctx, medium, geom, 0, xyz.contiguous(), torch.from_numpy(n).cuda()).cpu().numpy()
+    assert np.all(np.isfinite(lp))
+    m, s, d = _oracle_objs(O, sc.medium, sc.sources[0], sc.sensors[0])
+    X = xyz.cpu().numpy()
+    for q in range(0, 2000, 97):
+        assert np.isfinite(O.logp(m, s, d, X[:, q, : n[q]].T.astype(np.float64)))
+
+
+def test_tracer_seeded_chains_are_unbiased(api, ctx):
+    """Chains started from tracer seeds are stationary from the first step: a
+    short run agrees with a long forward-tracer reference to <= 1 %."""
+    sc = S.plain(n_chains=16384, n_steps=3000, cap=64)
+    sc.run.burn_in = 0
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    api.seed_from_tracer(ch, seed=21)
+    ch.run_steps(sc.run.n_steps)
+    e = ch.read_estimator()[0]
+    ref = api.trace(ctx, medium, api.Geometry(ctx, sc.sources, sc.sensors, [S.Pair(0, 0, 1, 64)]), 0, 777,
+                    2_000_000_000, max_scatter=62)
+    diff = abs(e["intensity"] - ref["I"])
+    assert diff < 3 * math.hypot(e["std_err"], ref["se"]), (e["intensity"], e["std_err"], ref["I"], ref["se"])
+    assert diff < 0.01 * ref["I"]
