@@ -72,7 +72,7 @@ struct pmc_ctx_s {
   int n_sm = 0;
   size_t smem_per_sm = 0, smem_per_block = 0;
   // autotuned warps per block, keyed by (kernel instantiation, shared vertex cap, chain-count bucket)
-  std::map<std::tuple<bool, int, int>, int> tuned;
+  std::map<std::tuple<int, int, int>, int> tuned;
 };
 
 struct pmc_medium_s {
@@ -184,6 +184,7 @@ struct pmc_chains_s {
   std::vector<ChainClass> classes;
   std::map<unsigned long long, cudaGraphExec_t> graphs;
   bool general = false;            // chain kernel instantiation
+  bool grad = false;               // keep d log sigma / dg per vertex
   bool autotune = false;           // warps per block chosen by timing
   int init_kind = 0, init_k = 0;
   float init_jitter = 0.f;
@@ -511,7 +512,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
   bool need = false;
   for (auto& cl : ch->classes) {
     const int bucket = 31 - __builtin_clz(static_cast<unsigned>(std::max(1, cl.hi - cl.lo)));
-    auto it = ch->ctx->tuned.find(std::make_tuple(ch->general, cl.smem_cap, bucket));
+    auto it = ch->ctx->tuned.find(std::make_tuple(ch->general * 2 + ch->grad, cl.smem_cap, bucket));
     if (it == ch->ctx->tuned.end()) need = true;
   }
   if (need) {
@@ -529,7 +530,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
     ChainClass& cl = ch->classes[k];
     const int chains = cl.hi - cl.lo;
     const int bucket = 31 - __builtin_clz(static_cast<unsigned>(std::max(1, chains)));
-    const auto key = std::make_tuple(ch->general, cl.smem_cap, bucket);
+    const auto key = std::make_tuple(ch->general * 2 + ch->grad, cl.smem_cap, bucket);
     auto it = ch->ctx->tuned.find(key);
     int best_w = cl.warps_per_block;
     if (it != ch->ctx->tuned.end()) {
@@ -537,9 +538,9 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
     } else {
       float best_ms = 1e30f;
       for (int wpb : {1, 2, 4}) {
-        if (chain_smem_bytes(cl.smem_cap, wpb) > ch->ctx->smem_per_block) continue;
+        if (chain_smem_bytes(cl.smem_cap, wpb, ch->general, ch->grad) > ch->ctx->smem_per_block) continue;
         int bps = 0;
-        if (chain_occupancy(ch->general, wpb, cl.smem_cap, &bps) != cudaSuccess || bps < 1) continue;
+        if (chain_occupancy(ch->general, ch->grad, wpb, cl.smem_cap, &bps) != cudaSuccess || bps < 1) continue;
         const int grid = std::max(1, std::min((chains + wpb - 1) / wpb, bps * ch->ctx->n_sm));
         ChainParams p = class_params(ch, k, 128);
         p.xyz = sx;
@@ -555,7 +556,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaMemsetAsync(sstat, 0, sizeof(int) * T, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s);
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-        if (e == cudaSuccess) e = launch_chain(p, ch->general, grid, wpb, s);
+        if (e == cudaSuccess) e = launch_chain(p, ch->general, ch->grad, grid, wpb, s);
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -572,7 +573,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
       ch->ctx->tuned[key] = best_w;
     }
     int bps = 0;
-    if (rc == PMC_OK && chain_occupancy(ch->general, best_w, cl.smem_cap, &bps) == cudaSuccess && bps >= 1) {
+    if (rc == PMC_OK && chain_occupancy(ch->general, ch->grad, best_w, cl.smem_cap, &bps) == cudaSuccess && bps >= 1) {
       cl.warps_per_block = best_w;
       cl.grid = std::max(1, std::min((chains + best_w - 1) / best_w, bps * ch->ctx->n_sm));
     }
@@ -676,6 +677,7 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     ch->classes.push_back(cl);
     lo = hi;
   }
+  ch->grad = (r->flags & PMC_FLAG_GRADIENTS) != 0;
   ch->general = med->d.kind != PMC_HOMOGENEOUS || med->d.f_sl > 0.f || r->within == PMC_WITHIN_MALA ||
                 std::any_of(ch->h_pairs.begin(), ch->h_pairs.end(),
                             [](const DPair& d) { return d.emission != PMC_EMIT_ISOTROPIC || d.rho != PMC_RHO_ONE; });
@@ -685,10 +687,10 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   for (auto& cl : ch->classes) {
     int wpb = r->warps_per_block > 0 ? r->warps_per_block : 4;
     wpb = std::min(wpb, 4);
-    while (wpb > 1 && chain_smem_bytes(cl.smem_cap, wpb) > ctx->smem_per_block) wpb /= 2;
-    if (chain_smem_bytes(cl.smem_cap, wpb) > ctx->smem_per_block) return fail(PMC_ERR_INVALID, "vertex cap too large for shared memory");
+    while (wpb > 1 && chain_smem_bytes(cl.smem_cap, wpb, ch->general, ch->grad) > ctx->smem_per_block) wpb /= 2;
+    if (chain_smem_bytes(cl.smem_cap, wpb, ch->general, ch->grad) > ctx->smem_per_block) return fail(PMC_ERR_INVALID, "vertex cap too large for shared memory");
     int bps = 0;
-    CK(chain_occupancy(ch->general, wpb, cl.smem_cap, &bps));
+    CK(chain_occupancy(ch->general, ch->grad, wpb, cl.smem_cap, &bps));
     if (bps < 1) return fail(PMC_ERR_INVALID, "chain kernel does not fit on an SM");
     const int chains = cl.hi - cl.lo;
     const int want = (chains + wpb - 1) / wpb;
@@ -830,7 +832,7 @@ static int enqueue_steps(pmc_chains_t ch, unsigned long long n_steps, cudaStream
   for (size_t k = 0; k < ch->classes.size(); ++k) {
     const ChainClass& cl = ch->classes[k];
     CK(cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s));
-    CK(launch_chain(class_params(ch, k, n_steps), ch->general, cl.grid, cl.warps_per_block, s));
+    CK(launch_chain(class_params(ch, k, n_steps), ch->general, ch->grad, cl.grid, cl.warps_per_block, s));
   }
   return PMC_OK;
 }

@@ -40,9 +40,23 @@ static_assert(sizeof(DPair) <= kPairWords * sizeof(float), "pair slot too small"
 
 enum Move { MV_INTERIOR = 0, MV_END = 1, MV_BIRTH = 2, MV_DEATH = 3 };
 
+// Shared-memory view of one chain's path.  kTb: tau_b per segment is cached
+// (layered media); otherwise it is b * length.  kGt: d log sigma / dg per
+// vertex is cached (gradients requested); otherwise it is not kept.
+template <bool kTb, bool kGt>
 struct WarpPath {
-  float *x, *y, *z, *tb, *seg, *len, *vt, *gt;
+  static constexpr int kArrays = 6 + (kTb ? 1 : 0) + (kGt ? 1 : 0);
+  float *x, *y, *z, *seg, *len, *vt, *tbs, *gts;
+  float b;
   __device__ float3 pos(int i) const { return f3(x[i], y[i], z[i]); }
+  __device__ float tb(int i) const { return kTb ? tbs[i] : b * len[i]; }
+  __device__ float gt(int i) const { return kGt ? gts[i] : 0.f; }
+  __device__ void set_tb(int i, float v) const {
+    if (kTb) tbs[i] = v;
+  }
+  __device__ void set_gt(int i, float v) const {
+    if (kGt) gts[i] = v;
+  }
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -100,10 +114,11 @@ struct Sums {
   float L, G;
 };
 
-__device__ Sums path_sums(const WarpPath& w, int n, int lane) {
+template <class WP>
+__device__ Sums path_sums(const WP& w, int n, int lane) {
   float L = 0.f, G = 0.f;
   for (int i = lane; i < n; i += 32) {
-    G += w.gt[i];
+    G += w.gt(i);
     if (i <= n - 2) L += w.len[i];
   }
   Sums s;
@@ -113,8 +128,8 @@ __device__ Sums path_sums(const WarpPath& w, int n, int lane) {
 }
 
 // Recompute every cached factor of the path from its vertices; returns log p.
-template <bool kGen>
-__device__ float refresh_caches(const DMedium& M, const DPair& S, float zoff, const WarpPath& w, int n, int lane) {
+template <bool kGen, class WP>
+__device__ float refresh_caches(const DMedium& M, const DPair& S, float zoff, const WP& w, int n, int lane) {
   float lp = 0.f;
   for (int i = lane; i < n; i += 32) {
     const float3 P = w.pos(i);
@@ -123,11 +138,11 @@ __device__ float refresh_caches(const DMedium& M, const DPair& S, float zoff, co
     float vt, gt, seg, tb, len;
     vertex_and_segment<kGen>(M, S, zoff, Pp, P, Pn, i, n, vt, gt, seg, tb, len);
     w.vt[i] = vt;
-    w.gt[i] = gt;
+    w.set_gt(i, gt);
     lp += vt;
     if (i <= n - 2) {
       w.seg[i] = seg;
-      w.tb[i] = tb;
+      w.set_tb(i, tb);
       w.len[i] = len;
       lp += seg;
     }
@@ -137,41 +152,44 @@ __device__ float refresh_caches(const DMedium& M, const DPair& S, float zoff, co
 }
 
 // Shift entries [a, e) of the vertex-indexed and segment-indexed arrays.
-__device__ void shift_right(const WarpPath& w, int a, int e_vtx, int e_seg, int lane) {
+template <class WP>
+__device__ void shift_right(const WP& w, int a, int e_vtx, int e_seg, int lane) {
   for (int base = e_vtx - 1; base >= a; base -= 32) {
     const int i = base - lane;
     const bool ok = i >= a;
     const bool oks = ok && i < e_seg;
     float x = 0, y = 0, z = 0, vt = 0, gt = 0, tb = 0, sg = 0, ln = 0;
-    if (ok) { x = w.x[i]; y = w.y[i]; z = w.z[i]; vt = w.vt[i]; gt = w.gt[i]; }
-    if (oks) { tb = w.tb[i]; sg = w.seg[i]; ln = w.len[i]; }
+    if (ok) { x = w.x[i]; y = w.y[i]; z = w.z[i]; vt = w.vt[i]; gt = w.gt(i); }
+    if (oks) { tb = w.tb(i); sg = w.seg[i]; ln = w.len[i]; }
     __syncwarp();
-    if (ok) { w.x[i + 1] = x; w.y[i + 1] = y; w.z[i + 1] = z; w.vt[i + 1] = vt; w.gt[i + 1] = gt; }
-    if (oks) { w.tb[i + 1] = tb; w.seg[i + 1] = sg; w.len[i + 1] = ln; }
+    if (ok) { w.x[i + 1] = x; w.y[i + 1] = y; w.z[i + 1] = z; w.vt[i + 1] = vt; w.set_gt(i + 1, gt); }
+    if (oks) { w.set_tb(i + 1, tb); w.seg[i + 1] = sg; w.len[i + 1] = ln; }
     __syncwarp();
   }
 }
 
-__device__ void shift_left(const WarpPath& w, int a, int e_vtx, int e_seg, int lane) {
+template <class WP>
+__device__ void shift_left(const WP& w, int a, int e_vtx, int e_seg, int lane) {
   for (int base = a; base < e_vtx; base += 32) {
     const int i = base + lane;
     const bool ok = i < e_vtx;
     const bool oks = i < e_seg;
     float x = 0, y = 0, z = 0, vt = 0, gt = 0, tb = 0, sg = 0, ln = 0;
-    if (ok) { x = w.x[i]; y = w.y[i]; z = w.z[i]; vt = w.vt[i]; gt = w.gt[i]; }
-    if (oks) { tb = w.tb[i]; sg = w.seg[i]; ln = w.len[i]; }
+    if (ok) { x = w.x[i]; y = w.y[i]; z = w.z[i]; vt = w.vt[i]; gt = w.gt(i); }
+    if (oks) { tb = w.tb(i); sg = w.seg[i]; ln = w.len[i]; }
     __syncwarp();
-    if (ok) { w.x[i - 1] = x; w.y[i - 1] = y; w.z[i - 1] = z; w.vt[i - 1] = vt; w.gt[i - 1] = gt; }
-    if (oks) { w.tb[i - 1] = tb; w.seg[i - 1] = sg; w.len[i - 1] = ln; }
+    if (ok) { w.x[i - 1] = x; w.y[i - 1] = y; w.z[i - 1] = z; w.vt[i - 1] = vt; w.set_gt(i - 1, gt); }
+    if (oks) { w.set_tb(i - 1, tb); w.seg[i - 1] = sg; w.len[i - 1] = ln; }
     __syncwarp();
   }
 }
 
 // Segment chosen for a birth: smallest k with cumsum_k(tau_b) > u * T_b.
-__device__ int select_segment(const WarpPath& w, int nseg, float u, float& total, int lane) {
+template <class WP>
+__device__ int select_segment(const WP& w, int nseg, float u, float& total, int lane) {
   if (nseg <= 32) {
     // one segment per lane: inclusive scan, then the first lane past the target
-    float incl = (lane < nseg) ? w.tb[lane] : 0.f;
+    float incl = (lane < nseg) ? w.tb(lane) : 0.f;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const float y = __shfl_up_sync(kFull, incl, o);
@@ -185,7 +203,7 @@ __device__ int select_segment(const WarpPath& w, int nseg, float u, float& total
   const int lo = lane * m;
   const int hi = min(lo + m, nseg);
   float local = 0.f;
-  for (int i = lo; i < hi; ++i) local += w.tb[i];
+  for (int i = lo; i < hi; ++i) local += w.tb(i);
   float incl = local;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -202,7 +220,7 @@ __device__ int select_segment(const WarpPath& w, int nseg, float u, float& total
     float cum = incl - local;
     k = hi - 1;
     for (int i = lo; i < hi; ++i) {
-      cum += w.tb[i];
+      cum += w.tb(i);
       if (cum > target) { k = i; break; }
     }
   }
@@ -256,24 +274,36 @@ __device__ __forceinline__ void flush64(Accum& a, int lane) {
 //   within: lo.z, lo.w, hi.x = standard normals, hi.y = vMF cosine,
 //           hi.z, hi.w = cos, sin of the vMF azimuth
 //   birth:  lo.z = u for cos s, lo.w = sinh t, hi.x = cosh t, hi.y, hi.z = cos, sin of phi
-template <bool kGen>
+template <bool kGen, bool kGrad>
 __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainParams P) {
+  using WP = WarpPath<kGen, kGrad>;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int cap_s = P.smem_cap;
-  const size_t per_warp = static_cast<size_t>(8) * cap_s + 32 * kRngWords + kPairWords;
-  WarpPath w;
-  w.x = smem + static_cast<size_t>(wib) * per_warp;
+  const size_t per_warp = static_cast<size_t>(WP::kArrays) * cap_s + 32 * kRngWords + kPairWords;
+  WP w;
+  float* base = smem + static_cast<size_t>(wib) * per_warp;
+  w.x = base;
   w.y = w.x + cap_s;
   w.z = w.y + cap_s;
-  w.tb = w.z + cap_s;
-  w.seg = w.tb + cap_s;
+  w.seg = w.z + cap_s;
   w.len = w.seg + cap_s;
   w.vt = w.len + cap_s;
-  w.gt = w.vt + cap_s;
-  uint4* rng = reinterpret_cast<uint4*>(w.gt + cap_s);  // [32][2] uint4
+  float* next = w.vt + cap_s;
+  w.tbs = nullptr;
+  w.gts = nullptr;
+  if constexpr (kGen) {
+    w.tbs = next;
+    next += cap_s;
+  }
+  if constexpr (kGrad) {
+    w.gts = next;
+    next += cap_s;
+  }
+  w.b = P.M.b;
+  uint4* rng = reinterpret_cast<uint4*>(next);  // [32][2] uint4
   DPair* spair = reinterpret_cast<DPair*>(rng + 64);
   const DMedium& M = P.M;
   const DRun& R = P.R;
@@ -444,7 +474,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
             const float sc = __fdividef(gamma, __uint_as_float(hi.x) - cs);
             fnew = 0.5f * (Af + Bf) +
                    sc * (__uint_as_float(lo.w) * rh + sn * (__uint_as_float(hi.y) * xi + __uint_as_float(hi.z) * ze));
-            const float tbk = w.tb[k];
+            const float tbk = w.tb(k);
             extra = R.log_pd - __logf(static_cast<float>(n - 1)) - R.log_pb - __logf(__fdividef(tbk, total)) -
                     log_insert_density<true>(M, R, zoff, Af, Bf, fnew);
             n_new = n + 1;
@@ -495,10 +525,10 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
           if (lane < onc) {
             const int o = olo + lane;
             ovt = w.vt[o];
-            ogt = w.gt[o];
+            ogt = w.gt(o);
             if (lane < onc - 1) {
               oseg = w.seg[o];
-              otb = w.tb[o];
+              otb = w.tb(o);
               olen = w.len[o];
             }
           }
@@ -514,7 +544,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
             // T_b of the reduced path, summed afresh so that decisions depend
             // only on the current state (split runs replay exactly)
             float part = 0.f;
-            for (int q = lane; q < n - 1; q += 32) part += w.tb[q];
+            for (int q = lane; q < n - 1; q += 32) part += w.tb(q);
             const float tb_new = __shfl_sync(kFull, ntb, 0);
             const float Tb_red = warp_sum(part) + dtb;
             extra = -R.log_pd + __logf(static_cast<float>(n - 2)) + R.log_pb + __logf(__fdividef(tb_new, Tb_red)) +
@@ -539,13 +569,16 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
           A.acc_d += (move == MV_DEATH);
           close_state(A, t, R.burn_in, n, L, G);
           float dlen = nlen - olen;
-          float dg = ngt - ogt;
           dlen += __shfl_xor_sync(kFull, dlen, 1);
           dlen += __shfl_xor_sync(kFull, dlen, 2);
           dlen = __shfl_sync(kFull, dlen, 0);
-          dg += __shfl_xor_sync(kFull, dg, 1);
-          dg += __shfl_xor_sync(kFull, dg, 2);
-          dg = __shfl_sync(kFull, dg, 0);
+          float dg = 0.f;
+          if constexpr (kGrad) {
+            dg = ngt - ogt;
+            dg += __shfl_xor_sync(kFull, dg, 1);
+            dg += __shfl_xor_sync(kFull, dg, 2);
+            dg = __shfl_sync(kFull, dg, 0);
+          }
           if (move == MV_BIRTH) {
             shift_right(w, kk + 1, n, n - 1, lane);
           } else if (move == MV_DEATH) {
@@ -554,10 +587,10 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
           if (lane < nc) {
             const int v = wlo + lane;
             w.vt[v] = nvt;
-            w.gt[v] = ngt;
+            w.set_gt(v, ngt);
             if (lane < nc - 1) {
               w.seg[v] = nseg;
-              w.tb[v] = ntb;
+              w.set_tb(v, ntb);
               w.len[v] = nlen;
             }
           }
@@ -665,7 +698,7 @@ __global__ void init_kernel(const InitParams p) {
 // The dynamic shared-memory limit is a property of the kernel, shared by every
 // launch: set it once to the device's per-block maximum so that classes with
 // different vertex caps can all launch.
-template <bool kGen>
+template <bool kGen, bool kGrad>
 cudaError_t set_attributes() {
   static int done[64] = {};
   int dev = 0;
@@ -675,35 +708,48 @@ cudaError_t set_attributes() {
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(chain_kernel<kGen>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(chain_kernel<kGen>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
   return e;
 }
 
+template <bool kGen, bool kGrad>
+cudaError_t occupancy_of(int warps_per_block, size_t sm, int* blocks_per_sm) {
+  cudaError_t e = set_attributes<kGen, kGrad>();
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<kGen, kGrad>, warps_per_block * 32,
+                                                       sm);
+}
+
 }  // namespace
 
-size_t chain_smem_bytes(int smem_cap, int warps_per_block) {
+size_t chain_smem_bytes(int smem_cap, int warps_per_block, bool general, bool grad) {
+  const size_t arrays = 6u + (general ? 1u : 0u) + (grad ? 1u : 0u);
   return static_cast<size_t>(warps_per_block) *
-         (8u * static_cast<size_t>(smem_cap) + 32u * kRngWords + kPairWords) * sizeof(float);
+         (arrays * static_cast<size_t>(smem_cap) + 32u * kRngWords + kPairWords) * sizeof(float);
 }
 
-cudaError_t chain_occupancy(bool general, int warps_per_block, int smem_cap, int* blocks_per_sm) {
-  const size_t sm = chain_smem_bytes(smem_cap, warps_per_block);
-  cudaError_t e = general ? set_attributes<true>() : set_attributes<false>();
-  if (e != cudaSuccess) return e;
-  if (general)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<true>, warps_per_block * 32, sm);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<false>, warps_per_block * 32, sm);
+cudaError_t chain_occupancy(bool general, bool grad, int warps_per_block, int smem_cap, int* blocks_per_sm) {
+  const size_t sm = chain_smem_bytes(smem_cap, warps_per_block, general, grad);
+  if (general) return grad ? occupancy_of<true, true>(warps_per_block, sm, blocks_per_sm)
+                           : occupancy_of<true, false>(warps_per_block, sm, blocks_per_sm);
+  return grad ? occupancy_of<false, true>(warps_per_block, sm, blocks_per_sm)
+              : occupancy_of<false, false>(warps_per_block, sm, blocks_per_sm);
 }
 
-cudaError_t launch_chain(const ChainParams& p, bool general, int grid, int warps_per_block, cudaStream_t s) {
-  const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block);
-  if (general)
-    chain_kernel<true><<<grid, warps_per_block * 32, sm, s>>>(p);
-  else
-    chain_kernel<false><<<grid, warps_per_block * 32, sm, s>>>(p);
+cudaError_t launch_chain(const ChainParams& p, bool general, bool grad, int grid, int warps_per_block,
+                         cudaStream_t s) {
+  const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block, general, grad);
+  const dim3 g(grid), b(warps_per_block * 32);
+  if (general) {
+    if (grad) chain_kernel<true, true><<<g, b, sm, s>>>(p);
+    else chain_kernel<true, false><<<g, b, sm, s>>>(p);
+  } else {
+    if (grad) chain_kernel<false, true><<<g, b, sm, s>>>(p);
+    else chain_kernel<false, false><<<g, b, sm, s>>>(p);
+  }
   return cudaGetLastError();
 }
 

@@ -58,9 +58,12 @@ struct ChainParams {
 // Kernel launchers (pmc_chain.cu)
 // `general` selects the instantiation with layered media, vMF emission, the
 // detection probability, the simplified-Liu mixture and MALA moves.
-cudaError_t launch_chain(const ChainParams& p, bool general, int grid, int warps_per_block, cudaStream_t s);
-size_t chain_smem_bytes(int smem_cap, int warps_per_block);
-cudaError_t chain_occupancy(bool general, int warps_per_block, int smem_cap, int* blocks_per_sm);
+// `grad` selects the instantiation that keeps d log sigma / dg per vertex for
+// the score of g.
+cudaError_t launch_chain(const ChainParams& p, bool general, bool grad, int grid, int warps_per_block,
+                         cudaStream_t s);
+size_t chain_smem_bytes(int smem_cap, int warps_per_block, bool general, bool grad);
+cudaError_t chain_occupancy(bool general, bool grad, int warps_per_block, int smem_cap, int* blocks_per_sm);
 
 struct InitParams {
   DRun R;
