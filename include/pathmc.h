@@ -158,7 +158,10 @@ typedef struct {
   const int* init_n;               /* USER: host, [total_chains] */
   int init_stride;                 /* USER: vertex stride of init_xyz (>= every init_n) */
   int flags;                       /* PMC_FLAG_* */
-  int warps_per_block;             /* 0 = autotune */
+  int warps_per_block;             /* 0 = autotune (also the shared window) */
+  int smem_window;                 /* vertices per chain kept in shared memory, a multiple of 32;
+                                      entries beyond it live in global memory.  0 = the whole cap
+                                      (or the autotuner's choice when warps_per_block = 0) */
 } pmc_run_desc;
 
 /* Per-pair estimate returned by pmc_read_estimator. */
@@ -269,7 +272,8 @@ PMC_API int pmc_total_chains(pmc_chains_t chains);
 
 /* Launch shapes chosen for the chains (by the autotuner when
  * warps_per_block = 0): one row of 6 ints per vertex-cap class, written to
- * `out` (host): shared vertex cap, first and one-past-last position in the
+ * `out` (host): shared-memory window in vertices (smaller than the class's
+ * caps when entries beyond it live in global memory), first and one-past-last position in the
  * processing order, warps (= chains) per block, persistent grid size, 1 if
  * the general kernel instantiation runs.  Returns the number of classes in
  * *n_classes; writes at most max_rows rows. */

@@ -149,7 +149,7 @@ def create_geometry(ctx: Context, sources, sensors, pairs) -> Geometry:
 
 
 def run_desc(r: S.Run, flags: int = 0, warps_per_block: int = 0, user_xyz: Optional[np.ndarray] = None,
-             user_n: Optional[np.ndarray] = None):
+             user_n: Optional[np.ndarray] = None, smem_window: int = 0):
     d = RunDesc()
     d.seed = int(r.seed)
     d.p_within, d.p_birth, d.p_death = float(r.p_within), float(r.p_birth), float(r.p_death)
@@ -164,6 +164,7 @@ def run_desc(r: S.Run, flags: int = 0, warps_per_block: int = 0, user_xyz: Optio
     d.init_jitter = float(r.init_jitter)
     d.flags = int(flags) | (PMC_FLAG_GRADIENTS if r.gradients else 0)
     d.warps_per_block = int(warps_per_block)
+    d.smem_window = int(smem_window)
     keep = ()
     if user_xyz is not None:
         ux = np.ascontiguousarray(user_xyz, dtype=np.float32)  # [chains][3][stride]
@@ -180,9 +181,9 @@ class Chains:
     """Chains of every pair of a geometry (pmc_init_chains .. pmc_destroy_chains)."""
 
     def __init__(self, ctx: Context, medium: Medium, geom: Geometry, run: S.Run, flags: int = 0,
-                 warps_per_block: int = 0, user_xyz=None, user_n=None, stream=None):
+                 warps_per_block: int = 0, user_xyz=None, user_n=None, stream=None, smem_window: int = 0):
         self.ctx, self.medium, self.geom, self.run = ctx, medium, geom, run
-        d, keep = run_desc(run, flags, warps_per_block, user_xyz, user_n)
+        d, keep = run_desc(run, flags, warps_per_block, user_xyz, user_n, smem_window)
         h = C.c_void_p()
         with torch.cuda.device(ctx.device):
             check(load().pmc_init_chains(ctx.handle, medium.handle, geom.handle, C.byref(d), _stream(stream),
@@ -241,7 +242,7 @@ class Chains:
         return xyz, n, steps
 
     def launch_info(self):
-        """Per cap class: shared cap, order range, warps per block, grid, general kernel (pmc_chains_launch_info)."""
+        """Per cap class: shared window, order range, warps per block, grid, general kernel (pmc_chains_launch_info)."""
         rows = np.zeros((8, 6), dtype=np.int32)
         nc = C.c_int(0)
         check(load().pmc_chains_launch_info(self.handle, rows.ctypes.data_as(C.POINTER(C.c_int)), 8, C.byref(nc)),

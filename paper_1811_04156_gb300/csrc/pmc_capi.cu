@@ -72,7 +72,7 @@ struct pmc_ctx_s {
   int n_sm = 0;
   size_t smem_per_sm = 0, smem_per_block = 0;
   // autotuned warps per block, keyed by (kernel instantiation, shared vertex cap, chain-count bucket)
-  std::map<std::tuple<int, int, int>, int> tuned;
+  std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;  // -> (warps per block, shared window)
 };
 
 struct pmc_medium_s {
@@ -147,7 +147,9 @@ struct pmc_geom_s {
 };
 
 struct ChainClass {
-  int smem_cap = 0;
+  int smem_cap = 0;   // shared window (vertices per warp)
+  int max_cap = 0;    // largest vertex cap of the class's chains
+  bool spill = false; // smem_cap < max_cap: entries beyond the window live in global memory
   int lo = 0, hi = 0;  // range into the processing order
   int warps_per_block = 4;
   int grid = 0;
@@ -499,9 +501,11 @@ static ChainParams class_params(pmc_chains_t ch, size_t k, unsigned long long n_
   return p;
 }
 
-// Autotuner: for every cap class, time the chain kernel at 1, 2 and 4 warps
-// (chains) per block on a scratch copy of the freshly initialised state and
-// keep the fastest; results are cached per device, kernel and class.
+// Autotuner: for every cap class, time the chain kernel over candidate launch
+// shapes — 1, 2 or 4 warps (chains) per block, and a shared window of the
+// whole cap or of 128 / 256 / 512 vertices (entries beyond it in global
+// memory) — on a scratch copy of the freshly initialised state, and keep the
+// fastest; choices are cached per device, kernel and class.
 static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
   const int T = ch->total;
   float* sx = nullptr;
@@ -509,12 +513,11 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
   unsigned long long* sst = nullptr;
   double* sacc = nullptr;
   int* sstat = nullptr;
+  const int kind = ch->general * 2 + ch->grad;
+  auto bucket_of = [](int chains) { return 31 - __builtin_clz(static_cast<unsigned>(std::max(1, chains))); };
   bool need = false;
-  for (auto& cl : ch->classes) {
-    const int bucket = 31 - __builtin_clz(static_cast<unsigned>(std::max(1, cl.hi - cl.lo)));
-    auto it = ch->ctx->tuned.find(std::make_tuple(ch->general * 2 + ch->grad, cl.smem_cap, bucket));
-    if (it == ch->ctx->tuned.end()) need = true;
-  }
+  for (auto& cl : ch->classes)
+    if (!ch->ctx->tuned.count(std::make_tuple(kind, cl.max_cap, bucket_of(cl.hi - cl.lo)))) need = true;
   if (need) {
     CK(dalloc(&sx, static_cast<size_t>(ch->xyz_floats)));
     CK(dalloc(&sn, T));
@@ -529,53 +532,65 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
   for (size_t k = 0; k < ch->classes.size() && rc == PMC_OK; ++k) {
     ChainClass& cl = ch->classes[k];
     const int chains = cl.hi - cl.lo;
-    const int bucket = 31 - __builtin_clz(static_cast<unsigned>(std::max(1, chains)));
-    const auto key = std::make_tuple(ch->general * 2 + ch->grad, cl.smem_cap, bucket);
+    const int full = (cl.max_cap + 31) / 32 * 32;
+    const auto key = std::make_tuple(kind, cl.max_cap, bucket_of(chains));
     auto it = ch->ctx->tuned.find(key);
-    int best_w = cl.warps_per_block;
+    std::pair<int, int> best(cl.warps_per_block, full);
     if (it != ch->ctx->tuned.end()) {
-      best_w = it->second;
+      best = it->second;
     } else {
       float best_ms = 1e30f;
-      for (int wpb : {1, 2, 4}) {
-        if (chain_smem_bytes(cl.smem_cap, wpb, ch->general, ch->grad) > ch->ctx->smem_per_block) continue;
-        int bps = 0;
-        if (chain_occupancy(ch->general, ch->grad, wpb, cl.smem_cap, &bps) != cudaSuccess || bps < 1) continue;
-        const int grid = std::max(1, std::min((chains + wpb - 1) / wpb, bps * ch->ctx->n_sm));
-        ChainParams p = class_params(ch, k, 128);
-        p.xyz = sx;
-        p.n = sn;
-        p.step = sst;
-        p.acc = sacc;
-        p.status = sstat;
-        p.abort_flag = nullptr;
-        cudaError_t e = cudaMemcpyAsync(sx, ch->d_xyz, sizeof(float) * ch->xyz_floats, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(sn, ch->d_n, sizeof(int) * T, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(sst, 0, sizeof(unsigned long long) * T, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(sacc, 0, sizeof(double) * T * ACC_WORDS, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(sstat, 0, sizeof(int) * T, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-        if (e == cudaSuccess) e = launch_chain(p, ch->general, ch->grad, grid, wpb, s);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-          rc = fail(PMC_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
-          break;
+      std::vector<int> windows = {full};
+      for (int w : {128, 256, 512})
+        if (w < full) windows.push_back(w);
+      for (int win : windows) {
+        for (int wpb : {1, 2, 4}) {
+          const bool spill = win < full;
+          if (chain_smem_bytes(win, wpb, ch->general, ch->grad) > ch->ctx->smem_per_block) continue;
+          int bps = 0;
+          if (chain_occupancy(ch->general, ch->grad, spill, wpb, win, &bps) != cudaSuccess || bps < 1) continue;
+          const int grid = std::max(1, std::min((chains + wpb - 1) / wpb, bps * ch->ctx->n_sm));
+          ChainParams p = class_params(ch, k, 128);
+          p.smem_cap = win;
+          p.xyz = sx;
+          p.n = sn;
+          p.step = sst;
+          p.acc = sacc;
+          p.status = sstat;
+          p.abort_flag = nullptr;
+          cudaError_t e = cudaMemcpyAsync(sx, ch->d_xyz, sizeof(float) * ch->xyz_floats, cudaMemcpyDeviceToDevice, s);
+          if (e == cudaSuccess) e = cudaMemcpyAsync(sn, ch->d_n, sizeof(int) * T, cudaMemcpyDeviceToDevice, s);
+          if (e == cudaSuccess) e = cudaMemsetAsync(sst, 0, sizeof(unsigned long long) * T, s);
+          if (e == cudaSuccess) e = cudaMemsetAsync(sacc, 0, sizeof(double) * T * ACC_WORDS, s);
+          if (e == cudaSuccess) e = cudaMemsetAsync(sstat, 0, sizeof(int) * T, s);
+          if (e == cudaSuccess) e = cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s);
+          if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+          if (e == cudaSuccess) e = launch_chain(p, ch->general, ch->grad, spill, grid, wpb, s);
+          if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (e != cudaSuccess) {
+            rc = fail(PMC_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+            break;
+          }
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = std::make_pair(wpb, win);
+          }
         }
-        if (ms < best_ms) {
-          best_ms = ms;
-          best_w = wpb;
-        }
+        if (rc != PMC_OK) break;
       }
-      ch->ctx->tuned[key] = best_w;
+      if (rc == PMC_OK) ch->ctx->tuned[key] = best;
     }
     int bps = 0;
-    if (rc == PMC_OK && chain_occupancy(ch->general, ch->grad, best_w, cl.smem_cap, &bps) == cudaSuccess && bps >= 1) {
-      cl.warps_per_block = best_w;
-      cl.grid = std::max(1, std::min((chains + best_w - 1) / best_w, bps * ch->ctx->n_sm));
+    const bool spill = best.second < full;
+    if (rc == PMC_OK && chain_occupancy(ch->general, ch->grad, spill, best.first, best.second, &bps) == cudaSuccess &&
+        bps >= 1) {
+      cl.warps_per_block = best.first;
+      cl.smem_cap = best.second;
+      cl.spill = spill;
+      cl.grid = std::max(1, std::min((chains + best.first - 1) / best.first, bps * ch->ctx->n_sm));
     }
   }
   cudaEventDestroy(e0);
@@ -608,6 +623,7 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   if (r->init == PMC_INIT_USER && (!r->init_xyz || !r->init_n || r->init_stride < 2))
     return fail(PMC_ERR_INVALID, "USER init needs init_xyz, init_n and init_stride");
   if (r->kappa_end < 0 || !std::isfinite(r->kappa_end)) return fail(PMC_ERR_INVALID, "bad kappa_end");
+  if (r->smem_window < 0 || r->smem_window % 32 != 0) return fail(PMC_ERR_INVALID, "smem_window must be a multiple of 32");
   CK(cudaSetDevice(ctx->device));
 
   auto ch = std::unique_ptr<pmc_chains_s, int (*)(pmc_chains_t)>(new pmc_chains_s, pmc_destroy_chains);
@@ -639,6 +655,11 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     d.kappa_end = static_cast<float>(ke);
     d.exp_m2ke = static_cast<float>(std::exp(-2.0 * ke));
   }
+  ch->grad = (r->flags & PMC_FLAG_GRADIENTS) != 0;
+  ch->general = med->d.kind != PMC_HOMOGENEOUS || med->d.f_sl > 0.f || r->within == PMC_WITHIN_MALA ||
+                std::any_of(ch->h_pairs.begin(), ch->h_pairs.end(),
+                            [](const DPair& d) { return d.emission != PMC_EMIT_ISOTROPIC || d.rho != PMC_RHO_ONE; });
+  const int n_arrays = chain_arrays(ch->general, ch->grad);
   const int T = ch->total;
   ch->h_base.resize(T);
   ch->h_pair_of.resize(T);
@@ -649,7 +670,7 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
       const int c = d.chain0 + k;
       ch->h_pair_of[c] = p;
       ch->h_base[c] = off;
-      off += 3ll * d.cap;
+      off += static_cast<long long>(n_arrays) * d.cap;
     }
   }
   ch->xyz_floats = off;
@@ -672,25 +693,27 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     }
     ChainClass cl;
     cl.smem_cap = (maxcap + 31) / 32 * 32;
+    cl.max_cap = maxcap;
+    cl.spill = false;
+    if (r->smem_window > 0 && r->smem_window < cl.smem_cap) {
+      cl.smem_cap = r->smem_window;
+      cl.spill = true;
+    }
     cl.lo = lo;
     cl.hi = hi;
     ch->classes.push_back(cl);
     lo = hi;
   }
-  ch->grad = (r->flags & PMC_FLAG_GRADIENTS) != 0;
-  ch->general = med->d.kind != PMC_HOMOGENEOUS || med->d.f_sl > 0.f || r->within == PMC_WITHIN_MALA ||
-                std::any_of(ch->h_pairs.begin(), ch->h_pairs.end(),
-                            [](const DPair& d) { return d.emission != PMC_EMIT_ISOTROPIC || d.rho != PMC_RHO_ONE; });
   // launch shapes: warps per block from the request (0: autotune after the
   // initial paths exist), persistent grid from occupancy
-  ch->autotune = r->warps_per_block <= 0;
+  ch->autotune = r->warps_per_block <= 0 && r->smem_window <= 0;
   for (auto& cl : ch->classes) {
     int wpb = r->warps_per_block > 0 ? r->warps_per_block : 4;
     wpb = std::min(wpb, 4);
     while (wpb > 1 && chain_smem_bytes(cl.smem_cap, wpb, ch->general, ch->grad) > ctx->smem_per_block) wpb /= 2;
     if (chain_smem_bytes(cl.smem_cap, wpb, ch->general, ch->grad) > ctx->smem_per_block) return fail(PMC_ERR_INVALID, "vertex cap too large for shared memory");
     int bps = 0;
-    CK(chain_occupancy(ch->general, ch->grad, wpb, cl.smem_cap, &bps));
+    CK(chain_occupancy(ch->general, ch->grad, cl.spill, wpb, cl.smem_cap, &bps));
     if (bps < 1) return fail(PMC_ERR_INVALID, "chain kernel does not fit on an SM");
     const int chains = cl.hi - cl.lo;
     const int want = (chains + wpb - 1) / wpb;
@@ -832,7 +855,7 @@ static int enqueue_steps(pmc_chains_t ch, unsigned long long n_steps, cudaStream
   for (size_t k = 0; k < ch->classes.size(); ++k) {
     const ChainClass& cl = ch->classes[k];
     CK(cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s));
-    CK(launch_chain(class_params(ch, k, n_steps), ch->general, ch->grad, cl.grid, cl.warps_per_block, s));
+    CK(launch_chain(class_params(ch, k, n_steps), ch->general, ch->grad, cl.spill, cl.grid, cl.warps_per_block, s));
   }
   return PMC_OK;
 }

@@ -40,22 +40,55 @@ static_assert(sizeof(DPair) <= kPairWords * sizeof(float), "pair slot too small"
 
 enum Move { MV_INTERIOR = 0, MV_END = 1, MV_BIRTH = 2, MV_DEATH = 3 };
 
-// Shared-memory view of one chain's path.  kTb: tau_b per segment is cached
-// (layered media); otherwise it is b * length.  kGt: d log sigma / dg per
-// vertex is cached (gradients requested); otherwise it is not kept.
-template <bool kTb, bool kGt>
+// View of one chain's path: entries [0, S) of every array live in the warp's
+// shared memory, entries [S, cap) in the chain's global block (same layout:
+// array a at offset a * stride).  kTb: tau_b per segment is cached (layered
+// media); otherwise it is b * length.  kGt: d log sigma / dg per vertex is
+// cached (gradients requested).  kSpill = false: the whole cap fits (S >= cap)
+// and every access goes to shared memory.
+template <bool kTb, bool kGt, bool kSpill>
 struct WarpPath {
   static constexpr int kArrays = 6 + (kTb ? 1 : 0) + (kGt ? 1 : 0);
-  float *x, *y, *z, *seg, *len, *vt, *tbs, *gts;
+  static constexpr int kX = 0, kY = 1, kZ = 2, kSeg = 3, kLen = 4, kVt = 5, kTbA = 6, kGtA = 6 + (kTb ? 1 : 0);
+  float* sm;   // shared arrays, stride S
+  float* gm;   // global block of the chain, stride cap
+  int S, cap;
   float b;
-  __device__ float3 pos(int i) const { return f3(x[i], y[i], z[i]); }
-  __device__ float tb(int i) const { return kTb ? tbs[i] : b * len[i]; }
-  __device__ float gt(int i) const { return kGt ? gts[i] : 0.f; }
+  template <int a>
+  __device__ __forceinline__ float ld(int i) const {
+    if (kSpill && i >= S) return gm[a * cap + i];
+    return sm[a * S + i];
+  }
+  template <int a>
+  __device__ __forceinline__ void st(int i, float v) const {
+    if (kSpill && i >= S) gm[a * cap + i] = v;
+    else sm[a * S + i] = v;
+  }
+  __device__ float3 pos(int i) const { return f3(ld<kX>(i), ld<kY>(i), ld<kZ>(i)); }
+  __device__ void set_pos(int i, float3 p) const {
+    st<kX>(i, p.x);
+    st<kY>(i, p.y);
+    st<kZ>(i, p.z);
+  }
+  __device__ float seg(int i) const { return ld<kSeg>(i); }
+  __device__ float len(int i) const { return ld<kLen>(i); }
+  __device__ float vt(int i) const { return ld<kVt>(i); }
+  __device__ void set_seg(int i, float v) const { st<kSeg>(i, v); }
+  __device__ void set_len(int i, float v) const { st<kLen>(i, v); }
+  __device__ void set_vt(int i, float v) const { st<kVt>(i, v); }
+  __device__ float tb(int i) const {
+    if constexpr (kTb) return ld<kTbA>(i);
+    else return b * ld<kLen>(i);
+  }
+  __device__ float gt(int i) const {
+    if constexpr (kGt) return ld<kGtA>(i);
+    else return 0.f;
+  }
   __device__ void set_tb(int i, float v) const {
-    if (kTb) tbs[i] = v;
+    if constexpr (kTb) st<kTbA>(i, v);
   }
   __device__ void set_gt(int i, float v) const {
-    if (kGt) gts[i] = v;
+    if constexpr (kGt) st<kGtA>(i, v);
   }
 };
 
@@ -119,7 +152,7 @@ __device__ Sums path_sums(const WP& w, int n, int lane) {
   float L = 0.f, G = 0.f;
   for (int i = lane; i < n; i += 32) {
     G += w.gt(i);
-    if (i <= n - 2) L += w.len[i];
+    if (i <= n - 2) L += w.len(i);
   }
   Sums s;
   s.L = warp_sum(L);
@@ -137,13 +170,13 @@ __device__ float refresh_caches(const DMedium& M, const DPair& S, float zoff, co
     const float3 Pn = (i <= n - 2) ? w.pos(i + 1) : P;
     float vt, gt, seg, tb, len;
     vertex_and_segment<kGen>(M, S, zoff, Pp, P, Pn, i, n, vt, gt, seg, tb, len);
-    w.vt[i] = vt;
+    w.set_vt(i, vt);
     w.set_gt(i, gt);
     lp += vt;
     if (i <= n - 2) {
-      w.seg[i] = seg;
+      w.set_seg(i, seg);
       w.set_tb(i, tb);
-      w.len[i] = len;
+      w.set_len(i, len);
       lp += seg;
     }
   }
@@ -159,11 +192,11 @@ __device__ void shift_right(const WP& w, int a, int e_vtx, int e_seg, int lane) 
     const bool ok = i >= a;
     const bool oks = ok && i < e_seg;
     float x = 0, y = 0, z = 0, vt = 0, gt = 0, tb = 0, sg = 0, ln = 0;
-    if (ok) { x = w.x[i]; y = w.y[i]; z = w.z[i]; vt = w.vt[i]; gt = w.gt(i); }
-    if (oks) { tb = w.tb(i); sg = w.seg[i]; ln = w.len[i]; }
+    if (ok) { x = w.template ld<WP::kX>(i); y = w.template ld<WP::kY>(i); z = w.template ld<WP::kZ>(i); vt = w.vt(i); gt = w.gt(i); }
+    if (oks) { tb = w.tb(i); sg = w.seg(i); ln = w.len(i); }
     __syncwarp();
-    if (ok) { w.x[i + 1] = x; w.y[i + 1] = y; w.z[i + 1] = z; w.vt[i + 1] = vt; w.set_gt(i + 1, gt); }
-    if (oks) { w.set_tb(i + 1, tb); w.seg[i + 1] = sg; w.len[i + 1] = ln; }
+    if (ok) { w.set_pos(i + 1, f3(x, y, z)); w.set_vt(i + 1, vt); w.set_gt(i + 1, gt); }
+    if (oks) { w.set_tb(i + 1, tb); w.set_seg(i + 1, sg); w.set_len(i + 1, ln); }
     __syncwarp();
   }
 }
@@ -175,11 +208,11 @@ __device__ void shift_left(const WP& w, int a, int e_vtx, int e_seg, int lane) {
     const bool ok = i < e_vtx;
     const bool oks = i < e_seg;
     float x = 0, y = 0, z = 0, vt = 0, gt = 0, tb = 0, sg = 0, ln = 0;
-    if (ok) { x = w.x[i]; y = w.y[i]; z = w.z[i]; vt = w.vt[i]; gt = w.gt(i); }
-    if (oks) { tb = w.tb(i); sg = w.seg[i]; ln = w.len[i]; }
+    if (ok) { x = w.template ld<WP::kX>(i); y = w.template ld<WP::kY>(i); z = w.template ld<WP::kZ>(i); vt = w.vt(i); gt = w.gt(i); }
+    if (oks) { tb = w.tb(i); sg = w.seg(i); ln = w.len(i); }
     __syncwarp();
-    if (ok) { w.x[i - 1] = x; w.y[i - 1] = y; w.z[i - 1] = z; w.vt[i - 1] = vt; w.set_gt(i - 1, gt); }
-    if (oks) { w.set_tb(i - 1, tb); w.seg[i - 1] = sg; w.len[i - 1] = ln; }
+    if (ok) { w.set_pos(i - 1, f3(x, y, z)); w.set_vt(i - 1, vt); w.set_gt(i - 1, gt); }
+    if (oks) { w.set_tb(i - 1, tb); w.set_seg(i - 1, sg); w.set_len(i - 1, ln); }
     __syncwarp();
   }
 }
@@ -274,9 +307,9 @@ __device__ __forceinline__ void flush64(Accum& a, int lane) {
 //   within: lo.z, lo.w, hi.x = standard normals, hi.y = vMF cosine,
 //           hi.z, hi.w = cos, sin of the vMF azimuth
 //   birth:  lo.z = u for cos s, lo.w = sinh t, hi.x = cosh t, hi.y, hi.z = cos, sin of phi
-template <bool kGen, bool kGrad>
-__global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainParams P) {
-  using WP = WarpPath<kGen, kGrad>;
+template <bool kGen, bool kGrad, bool kSpill>
+__global__ void __launch_bounds__(128, kGen ? 5 : 7) chain_kernel(const ChainParams P) {
+  using WP = WarpPath<kGen, kGrad, kSpill>;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
@@ -284,26 +317,10 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
   const int cap_s = P.smem_cap;
   const size_t per_warp = static_cast<size_t>(WP::kArrays) * cap_s + 32 * kRngWords + kPairWords;
   WP w;
-  float* base = smem + static_cast<size_t>(wib) * per_warp;
-  w.x = base;
-  w.y = w.x + cap_s;
-  w.z = w.y + cap_s;
-  w.seg = w.z + cap_s;
-  w.len = w.seg + cap_s;
-  w.vt = w.len + cap_s;
-  float* next = w.vt + cap_s;
-  w.tbs = nullptr;
-  w.gts = nullptr;
-  if constexpr (kGen) {
-    w.tbs = next;
-    next += cap_s;
-  }
-  if constexpr (kGrad) {
-    w.gts = next;
-    next += cap_s;
-  }
+  w.sm = smem + static_cast<size_t>(wib) * per_warp;
+  w.S = cap_s;
   w.b = P.M.b;
-  uint4* rng = reinterpret_cast<uint4*>(next);  // [32][2] uint4
+  uint4* rng = reinterpret_cast<uint4*>(w.sm + static_cast<size_t>(WP::kArrays) * cap_s);  // [32][2] uint4
   DPair* spair = reinterpret_cast<DPair*>(rng + 64);
   const DMedium& M = P.M;
   const DRun& R = P.R;
@@ -328,14 +345,21 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
     const int cap = S.cap;
     int n = P.n[c];
     const unsigned long long step0 = P.step[c];
-    if (n < 2 || n > cap || cap > cap_s) {
+    if (n < 2 || n > cap || (!kSpill && cap > cap_s)) {
       if (lane == 0) { P.status[c] |= ST_BAD_N; atomicOr(P.any_status, ST_BAD_N); }
       continue;
     }
     float* gx = P.xyz + P.chain_base[c];
     float* gy = gx + cap;
     float* gz = gy + cap;
-    for (int i = lane; i < n; i += 32) { w.x[i] = gx[i]; w.y[i] = gy[i]; w.z[i] = gz[i]; }
+    w.gm = gx;
+    w.cap = cap;
+    // the shared window holds entries [0, min(n, S)); the rest stays in the global block
+    for (int i = lane; i < min(n, cap_s); i += 32) {
+      w.sm[WP::kX * cap_s + i] = gx[i];
+      w.sm[WP::kY * cap_s + i] = gy[i];
+      w.sm[WP::kZ * cap_s + i] = gz[i];
+    }
     __syncwarp();
     const float lp0 = refresh_caches<kGen>(M, S, zoff, w, n, lane);
     if (!isfinite(lp0)) {
@@ -524,12 +548,12 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
           }
           if (lane < onc) {
             const int o = olo + lane;
-            ovt = w.vt[o];
+            ovt = w.vt(o);
             ogt = w.gt(o);
             if (lane < onc - 1) {
-              oseg = w.seg[o];
+              oseg = w.seg(o);
               otb = w.tb(o);
-              olen = w.len[o];
+              olen = w.len(o);
             }
           }
           float dlp = (nvt + nseg) - (ovt + oseg);
@@ -586,19 +610,15 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
           }
           if (lane < nc) {
             const int v = wlo + lane;
-            w.vt[v] = nvt;
+            w.set_vt(v, nvt);
             w.set_gt(v, ngt);
             if (lane < nc - 1) {
-              w.seg[v] = nseg;
+              w.set_seg(v, nseg);
               w.set_tb(v, ntb);
-              w.len[v] = nlen;
+              w.set_len(v, nlen);
             }
           }
-          if (lane == 0 && move != MV_DEATH) {
-            w.x[inew] = fnew.x;
-            w.y[inew] = fnew.y;
-            w.z[inew] = fnew.z;
-          }
+          if (lane == 0 && move != MV_DEATH) w.set_pos(inew, fnew);
           __syncwarp();
           n = n_new;
           L += dlen;
@@ -631,7 +651,11 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
     if (lane == ACC_ACC + 3) extra_w = static_cast<double>(A.acc_d);
     A.my += extra_w;
     if (lane < ACC_WORDS) P.acc[static_cast<size_t>(c) * ACC_WORDS + lane] = A.my;
-    for (int i = lane; i < n; i += 32) { gx[i] = w.x[i]; gy[i] = w.y[i]; gz[i] = w.z[i]; }
+    for (int i = lane; i < min(n, cap_s); i += 32) {
+      gx[i] = w.sm[WP::kX * cap_s + i];
+      gy[i] = w.sm[WP::kY * cap_s + i];
+      gz[i] = w.sm[WP::kZ * cap_s + i];
+    }
     if (lane == 0) {
       P.n[c] = n;
       P.step[c] = t_end;
@@ -698,7 +722,7 @@ __global__ void init_kernel(const InitParams p) {
 // The dynamic shared-memory limit is a property of the kernel, shared by every
 // launch: set it once to the device's per-block maximum so that classes with
 // different vertex caps can all launch.
-template <bool kGen, bool kGrad>
+template <bool kGen, bool kGrad, bool kSpill>
 cudaError_t set_attributes() {
   static int done[64] = {};
   int dev = 0;
@@ -708,47 +732,65 @@ cudaError_t set_attributes() {
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad, kSpill>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad, kSpill>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
   return e;
 }
 
-template <bool kGen, bool kGrad>
+template <bool kGen, bool kGrad, bool kSpill>
 cudaError_t occupancy_of(int warps_per_block, size_t sm, int* blocks_per_sm) {
-  cudaError_t e = set_attributes<kGen, kGrad>();
+  cudaError_t e = set_attributes<kGen, kGrad, kSpill>();
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<kGen, kGrad>, warps_per_block * 32,
-                                                       sm);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<kGen, kGrad, kSpill>,
+                                                       warps_per_block * 32, sm);
+}
+
+template <bool kGen, bool kGrad, bool kSpill>
+void launch_one(const ChainParams& p, int grid, int warps_per_block, size_t sm, cudaStream_t s) {
+  chain_kernel<kGen, kGrad, kSpill><<<grid, warps_per_block * 32, sm, s>>>(p);
 }
 
 }  // namespace
 
+int chain_arrays(bool general, bool grad) { return 6 + (general ? 1 : 0) + (grad ? 1 : 0); }
+
 size_t chain_smem_bytes(int smem_cap, int warps_per_block, bool general, bool grad) {
-  const size_t arrays = 6u + (general ? 1u : 0u) + (grad ? 1u : 0u);
+  const size_t arrays = static_cast<size_t>(chain_arrays(general, grad));
   return static_cast<size_t>(warps_per_block) *
          (arrays * static_cast<size_t>(smem_cap) + 32u * kRngWords + kPairWords) * sizeof(float);
 }
 
-cudaError_t chain_occupancy(bool general, bool grad, int warps_per_block, int smem_cap, int* blocks_per_sm) {
+cudaError_t chain_occupancy(bool general, bool grad, bool spill, int warps_per_block, int smem_cap,
+                            int* blocks_per_sm) {
   const size_t sm = chain_smem_bytes(smem_cap, warps_per_block, general, grad);
-  if (general) return grad ? occupancy_of<true, true>(warps_per_block, sm, blocks_per_sm)
-                           : occupancy_of<true, false>(warps_per_block, sm, blocks_per_sm);
-  return grad ? occupancy_of<false, true>(warps_per_block, sm, blocks_per_sm)
-              : occupancy_of<false, false>(warps_per_block, sm, blocks_per_sm);
+  const int key = (general ? 4 : 0) + (grad ? 2 : 0) + (spill ? 1 : 0);
+  switch (key) {
+    case 0: return occupancy_of<false, false, false>(warps_per_block, sm, blocks_per_sm);
+    case 1: return occupancy_of<false, false, true>(warps_per_block, sm, blocks_per_sm);
+    case 2: return occupancy_of<false, true, false>(warps_per_block, sm, blocks_per_sm);
+    case 3: return occupancy_of<false, true, true>(warps_per_block, sm, blocks_per_sm);
+    case 4: return occupancy_of<true, false, false>(warps_per_block, sm, blocks_per_sm);
+    case 5: return occupancy_of<true, false, true>(warps_per_block, sm, blocks_per_sm);
+    case 6: return occupancy_of<true, true, false>(warps_per_block, sm, blocks_per_sm);
+    default: return occupancy_of<true, true, true>(warps_per_block, sm, blocks_per_sm);
+  }
 }
 
-cudaError_t launch_chain(const ChainParams& p, bool general, bool grad, int grid, int warps_per_block,
+cudaError_t launch_chain(const ChainParams& p, bool general, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s) {
   const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block, general, grad);
-  const dim3 g(grid), b(warps_per_block * 32);
-  if (general) {
-    if (grad) chain_kernel<true, true><<<g, b, sm, s>>>(p);
-    else chain_kernel<true, false><<<g, b, sm, s>>>(p);
-  } else {
-    if (grad) chain_kernel<false, true><<<g, b, sm, s>>>(p);
-    else chain_kernel<false, false><<<g, b, sm, s>>>(p);
+  const int key = (general ? 4 : 0) + (grad ? 2 : 0) + (spill ? 1 : 0);
+  switch (key) {
+    case 0: launch_one<false, false, false>(p, grid, warps_per_block, sm, s); break;
+    case 1: launch_one<false, false, true>(p, grid, warps_per_block, sm, s); break;
+    case 2: launch_one<false, true, false>(p, grid, warps_per_block, sm, s); break;
+    case 3: launch_one<false, true, true>(p, grid, warps_per_block, sm, s); break;
+    case 4: launch_one<true, false, false>(p, grid, warps_per_block, sm, s); break;
+    case 5: launch_one<true, false, true>(p, grid, warps_per_block, sm, s); break;
+    case 6: launch_one<true, true, false>(p, grid, warps_per_block, sm, s); break;
+    default: launch_one<true, true, true>(p, grid, warps_per_block, sm, s); break;
   }
   return cudaGetLastError();
 }

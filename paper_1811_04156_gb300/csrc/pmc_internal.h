@@ -59,11 +59,16 @@ struct ChainParams {
 // `general` selects the instantiation with layered media, vMF emission, the
 // detection probability, the simplified-Liu mixture and MALA moves.
 // `grad` selects the instantiation that keeps d log sigma / dg per vertex for
-// the score of g.
-cudaError_t launch_chain(const ChainParams& p, bool general, bool grad, int grid, int warps_per_block,
+// the score of g; `spill` the one whose shared window (smem_cap vertices) is
+// smaller than the chains' caps, entries beyond it living in the chain's
+// global block.  The global block of a chain holds chain_arrays() arrays of
+// cap floats (x, y, z first).
+int chain_arrays(bool general, bool grad);
+cudaError_t launch_chain(const ChainParams& p, bool general, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s);
 size_t chain_smem_bytes(int smem_cap, int warps_per_block, bool general, bool grad);
-cudaError_t chain_occupancy(bool general, bool grad, int warps_per_block, int smem_cap, int* blocks_per_sm);
+cudaError_t chain_occupancy(bool general, bool grad, bool spill, int warps_per_block, int smem_cap,
+                            int* blocks_per_sm);
 
 struct InitParams {
   DRun R;

@@ -531,3 +531,31 @@ def test_tracer_seeded_chains_are_unbiased(api, ctx):
     diff = abs(e["intensity"] - ref["I"])
     assert diff < 3 * math.hypot(e["std_err"], ref["se"]), (e["intensity"], e["std_err"], ref["I"], ref["se"])
     assert diff < 0.01 * ref["I"]
+
+
+@pytest.mark.parametrize("window", [32, 64])
+def test_shared_window_spill_replays_oracle(api, ctx, oracle_lib, window):
+    """Paths longer than the shared-memory window (entries beyond it in global
+    memory) replay the oracle's trajectories."""
+    O = oracle_lib
+    sc = S.plain(n_chains=64, n_steps=300, cap=128)
+    sc.medium.lambda_s = 0.05
+    sc.run.init = S.INIT_STRAIGHT
+    sc.run.init_k = 40
+    sc.run.init_jitter = 0.01
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run, warps_per_block=2, smem_window=window)
+    assert ch.launch_info()[0]["smem_cap"] == window
+    ch.run_steps(sc.run.n_steps)
+    assert ch.status() == 0
+    xyz, n, _ = ch.read_states()
+    assert n.max() > window
+    oc = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, 128)
+    margin = oc.run(sc.run.n_steps, margins=True)
+    clean = np.nonzero(margin > 1e-3)[0]
+    assert len(clean) >= 24
+    for c in clean:
+        assert n[c] == oc.n[c], (c, n[c], oc.n[c])
+        k = int(n[c])
+        assert np.allclose(xyz[c, :, :k].T, oc.xyz[c, :k], atol=2e-4), c
