@@ -308,7 +308,7 @@ __device__ __forceinline__ void flush64(Accum& a, int lane) {
 //           hi.z, hi.w = cos, sin of the vMF azimuth
 //   birth:  lo.z = u for cos s, lo.w = sinh t, hi.x = cosh t, hi.y, hi.z = cos, sin of phi
 template <bool kGen, bool kGrad, bool kSpill>
-__global__ void __launch_bounds__(128, kGen ? 5 : 7) chain_kernel(const ChainParams P) {
+__global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainParams P) {
   using WP = WarpPath<kGen, kGrad, kSpill>;
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);

@@ -541,7 +541,7 @@ def test_shared_window_spill_replays_oracle(api, ctx, oracle_lib, window):
     sc = S.plain(n_chains=64, n_steps=300, cap=128)
     sc.medium.lambda_s = 0.05
     sc.run.init = S.INIT_STRAIGHT
-    sc.run.init_k = 40
+    sc.run.init_k = window + 16
     sc.run.init_jitter = 0.01
     medium = api.Medium(ctx, sc.medium)
     geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
