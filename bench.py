@@ -385,7 +385,8 @@ def ours(args):
                          "kernel": "chain_kernel", "kernel_ms": statistics.mean(kern_ms),
                          "fp32_per_proposal": fp32, "mufu_per_proposal": mufu},
             "gpu_launches": 3 * args.steps,
-            "estimate": {k: est[k] for k in ("intensity", "std_err", "pi_direct", "rhat", "mean_n", "accept")},
+            "effective_samples_per_s": (est["ess"] / (ms_per_step / 1e3)) if est.get("ess") else None,
+            "estimate": {k: est[k] for k in ("intensity", "std_err", "pi_direct", "rhat", "mean_n", "accept", "ess")},
             "clocks": clocks, "e2e": e2e}
     if not args.no_cpu_baseline:
         try:
