@@ -143,6 +143,93 @@ __device__ __forceinline__ void vertex_and_segment(const DMedium& M, const DPair
   vt = lb + phase_term<F, kGen>(M, a, b, gt);
 }
 
+// d log p / d f_v with the terms spread over lanes: lanes 0-1 the two segment
+// factors that end / start at v, lanes 2-4 the scattering angles at v-1, v,
+// v+1, lane 5 the emission and detection factors; a shuffle tree sums them
+// and every lane returns the total.  Same formulas as grad_vertex.
+template <class PosF>
+__device__ float3 grad_vertex_warp(const DMedium& M, const DPair& S, float zoff, PosF pos, int n, int v, int lane) {
+  float3 pv[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int k = min(max(v - 2 + i, 0), n - 1);
+    pv[i] = pos(k);
+  }
+  float3 rh[4];
+  float el[4];
+  bool ex[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = v - 2 + i;
+    ex[i] = (k >= 0 && k <= n - 2);
+    const float3 r = pv[i + 1] - pv[i];
+    const float rr = dot(r, r);
+    const float ir = ex[i] ? rsqrtf(rr) : 1.0f;
+    el[i] = ex[i] ? rr * ir : 1.0f;
+    rh[i] = ir * r;
+  }
+  float3 g = f3(0.f, 0.f, 0.f);
+  if (lane < 2) {
+    const bool e = (lane == 0) ? ex[1] : ex[2];
+    const float3 P = (lane == 0) ? pv[1] : pv[2];
+    const float3 Q = (lane == 0) ? pv[2] : pv[3];
+    const float3 r = (lane == 0) ? rh[1] : rh[2];
+    const float l = (lane == 0) ? el[1] : el[2];
+    if (e) {
+      float3 dP, dQ;
+      dtau_dends(M, zoff, P, Q, l, r, dP, dQ);
+      g = (lane == 0) ? (f3(0.f, 0.f, 0.f) - dQ - (2.0f / l) * r) : ((2.0f / l) * r - dP);
+    }
+  } else if (lane < 5) {
+    const int k = v - 3 + lane;
+    if (k >= 1 && k <= n - 2) {
+      const float3 A = (lane == 2) ? rh[0] : ((lane == 3) ? rh[1] : rh[2]);
+      const float3 B = (lane == 2) ? rh[1] : ((lane == 3) ? rh[2] : rh[3]);
+      const float lA = (lane == 2) ? el[0] : ((lane == 3) ? el[1] : el[2]);
+      const float lB = (lane == 2) ? el[1] : ((lane == 3) ? el[2] : el[3]);
+      const float alpha = (lane == 2) ? 0.f : ((lane == 3) ? 1.f : -1.f);
+      const float beta = (lane == 2) ? 1.f : ((lane == 3) ? -1.f : 0.f);
+      const float w = phase_dlogdc(M, A, B);
+      g = w * (alpha * drdot(A, lA, B) + beta * drdot(B, lB, A));
+    }
+  } else if (lane == 5) {
+    if (S.emission != 0) {
+      const float3 ed = f3(S.dir[0], S.dir[1], S.dir[2]);
+      if (v == 1) g = g + S.kappa * drdot(rh[1], el[1], ed);
+      if (v == 0 && ex[2]) g = g - S.kappa * drdot(rh[2], el[2], ed);
+    }
+    if (v == n - 2 || v == n - 1) {
+      const float3 e = (v == n - 1) ? pv[2] : pv[3];
+      const float3 rhat = (v == n - 1) ? rh[1] : rh[2];
+      const float ell = (v == n - 1) ? el[1] : el[2];
+      float3 nu = (e - f3(S.c[0], S.c[1], S.c[2])) - f3(S.c_lo[0], S.c_lo[1], S.c_lo[2]);
+      const float dn = sqrtf(dot(nu, nu));
+      nu = (1.0f / dn) * nu;
+      const float u = -dot(rhat, nu);
+      const float3 t1 = drdot(rhat, ell, nu);
+      if (v == n - 2) {
+        g = g + (1.0f / u) * t1;
+      } else {
+        const float3 t2 = drdot(nu, dn, rhat);
+        g = g - (1.0f / u) * (t1 + t2);
+        if (S.rho != 0) {
+          const float3 rh_ = f3(S.rho_hat[0], S.rho_hat[1], S.rho_hat[2]);
+          const float x = dot(nu, rh_);
+          const float dl = 3.0f - 2.0f * tanhf(fmaf(2.0f, x, 0.7f));
+          g = g + dl * drdot(nu, dn, rh_);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    g.x += __shfl_xor_sync(kFull, g.x, o);
+    g.y += __shfl_xor_sync(kFull, g.y, o);
+    g.z += __shfl_xor_sync(kFull, g.z, o);
+  }
+  return f3(__shfl_sync(kFull, g.x, 0), __shfl_sync(kFull, g.y, 0), __shfl_sync(kFull, g.z, 0));
+}
+
 struct Sums {
   float L, G;
 };
@@ -462,7 +549,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
             const float3 z = f3(__uint_as_float(lo.z), __uint_as_float(lo.w), __uint_as_float(hi.x));
             if constexpr (kGen) {
               if (R.within == 1) {
-                gx_mala = grad_vertex(M, S, zoff, [&](int k) { return w.pos(k); }, n, j);
+                gx_mala = grad_vertex_warp(M, S, zoff, [&](int k) { return w.pos(k); }, n, j, lane);
                 const float h = 0.5f * R.mala_eps * R.mala_eps;
                 fnew = fj + h * gx_mala + R.mala_eps * z;
               } else {
@@ -576,7 +663,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
           }
           if constexpr (kGen) {
             if (move == MV_INTERIOR && R.within == 1 && isfinite(dlp)) {
-              const float3 gy = grad_vertex(M, S, zoff, newpos, n, jj);
+              const float3 gy = grad_vertex_warp(M, S, zoff, newpos, n, jj, lane);
               const float h = 0.5f * R.mala_eps * R.mala_eps;
               const float3 fj = w.pos(jj);
               const float3 dfw = fnew - fj - h * gx_mala;
