@@ -538,7 +538,9 @@ def test_shared_window_spill_replays_oracle(api, ctx, oracle_lib, window):
     """Paths longer than the shared-memory window (entries beyond it in global
     memory) replay the oracle's trajectories."""
     O = oracle_lib
-    sc = S.plain(n_chains=64, n_steps=300, cap=128)
+    # deaths outnumber births in this medium: after 100 steps most paths are
+    # still longer than the window, after 300 few are
+    sc = S.plain(n_chains=64, n_steps=100, cap=128)
     sc.medium.lambda_s = 0.05
     sc.run.init = S.INIT_STRAIGHT
     sc.run.init_k = window + 16
@@ -550,7 +552,7 @@ def test_shared_window_spill_replays_oracle(api, ctx, oracle_lib, window):
     ch.run_steps(sc.run.n_steps)
     assert ch.status() == 0
     xyz, n, _ = ch.read_states()
-    assert n.max() > window
+    assert (n > window).sum() >= 16
     oc = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, 128)
     margin = oc.run(sc.run.n_steps, margins=True)
     clean = np.nonzero(margin > 1e-3)[0]
