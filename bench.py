@@ -51,6 +51,10 @@ WORKLOAD_TEXT = {
     "layered": "layered: 100 x 10 m layers, 60 sensors x 8,192 chains, cap 1,024, g=0.94",
 }
 FP32_LANES_PER_SM = 128
+# Warp instructions per proposal of the chain kernel, from the committed ncu
+# capture of the same kernel and launch shape (profiles/chain_kernel_detector.md).
+WARP_INST_PER_PROPOSAL = {"detector": 405.7}
+ISSUE_PER_CLK_PER_SM = 4
 
 
 def parse():
@@ -198,12 +202,17 @@ def _oracle_run(sc, chains, steps, threads):
 
 
 def cpu_baseline(sc, seconds, threads):
-    """The oracle as it stands on the host cores, on a bounded sample of the workload."""
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    workload; also its single-core rate on a smaller sample."""
     chains, steps = _oracle_sample(sc, seconds, threads)
     dt = _oracle_run(sc, chains, steps, threads)
+    c1, s1 = _oracle_sample(sc, max(2.0, seconds / 5), 1)
+    dt1 = _oracle_run(sc, c1, s1, 1)
     return {"value": chains * steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "value_1core": c1 * s1 / dt1,
             "sample": f"{chains} of the {sc.pairs[0].n_chains} chains x the first {steps} of "
-                      f"{sc.run.n_steps} steps of the {sc.name} workload, FP64, {dt:.1f} s"}
+                      f"{sc.run.n_steps} steps of the {sc.name} workload, FP64, {dt:.1f} s; 1 core: "
+                      f"{c1} chains x {s1} steps, {dt1:.1f} s"}
 
 
 def reference_arm(args):
@@ -290,6 +299,7 @@ def ours(args):
 
     for _ in range(args.warmup):
         one_step()
+    pipes = api.measure_pipes(ctx, stream) if rank == 0 else None
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -367,6 +377,18 @@ def ours(args):
         bound_pipe, achieved, peak = "MUFU", rate * mufu / 1e12, mufu_peak / 1e12
     else:
         bound_pipe, achieved, peak = "FP32", rate * fp32 / 1e12, fp32_peak / 1e12
+    peak_measured = (pipes["mufu_per_s"] if bound_pipe == "MUFU" else pipes["fp32_per_s"]) / 1e12
+    clk = (clocks or {}).get("sm_mhz") or sm_mhz
+    li = chains.launch_info()
+    same_shape = len(li) == 1 and li[0]["warps_per_block"] == 2 and li[0]["smem_cap"] == sc.pairs[0].cap
+    inst = WARP_INST_PER_PROPOSAL.get(sc.name) if same_shape else None
+    issue = None
+    if inst is not None:
+        issue_peak = ISSUE_PER_CLK_PER_SM * n_sm * clk * 1e6
+        issue = {"achieved": rate * inst, "peak": issue_peak, "unit": "warp instructions/s",
+                 "frac": rate * inst / issue_peak, "inst_per_proposal": inst,
+                 "source": "instructions per proposal from the committed ncu capture of this kernel and launch "
+                           "shape; peak = 4 warp instructions/clk/SM x SMs x median SM clock under load"}
     # DRAM traffic of one launch: ncu capture of 16,384 chains (8.9 MB), scaled by chains
     traffic = 8.9e6 * n_chains / 16384.0 if sc.name == "detector" else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -383,7 +405,10 @@ def ours(args):
                          "peak_source": f"{bound_pipe} lanes/clk/SM x {n_sm} SMs x sm_max_mhz "
                                         f"({peak_kind} clock {sm_mhz:.0f} MHz)",
                          "kernel": "chain_kernel", "kernel_ms": statistics.mean(kern_ms),
-                         "fp32_per_proposal": fp32, "mufu_per_proposal": mufu},
+                         "fp32_per_proposal": fp32, "mufu_per_proposal": mufu,
+                         "peak_measured": peak_measured, "frac_of_measured": achieved / peak_measured,
+                         "pipes_measured": pipes},
+            "issue_roofline": issue,
             "gpu_launches": 3 * args.steps,
             "effective_samples_per_s": (est["ess"] / (ms_per_step / 1e3)) if est.get("ess") else None,
             "estimate": {k: est[k] for k in ("intensity", "std_err", "pi_direct", "rhat", "mean_n", "accept", "ess")},

@@ -400,6 +400,20 @@ PMC_API int pmc_trace_paths(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom,
                             uint64_t photon0, uint64_t n_photons, double r_reject, int max_scatter, int max_paths,
                             float* out_xyz, int* out_n, int stride, uint64_t* n_accepted, void* stream);
 
+/* ---------------------------------------------------------------------- */
+/* Measurement                                                            */
+/* ---------------------------------------------------------------------- */
+
+/* Pipe rates of the context's device, measured by two microbenchmark kernels
+ * (8 independent dependency chains per thread, 8 CTAs of 256 threads per SM,
+ * one untimed and one timed launch each, CUDA events on `stream`):
+ * out[0] = FP32 fused multiply-add lane-operations per second, out[1] = MUFU
+ * (special-function unit: ex2, lg2) lane-operations per second.  These are the
+ * denominators of the chain kernel's lane-op roofline; the paper has no
+ * counterpart.  out: host, 2 doubles, caller-owned.  Allocates and frees a
+ * 1.2 MB device buffer per call.  Synchronises `stream`. */
+PMC_API int pmc_measure_pipes(pmc_ctx_t ctx, double* out, void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 PMC_API const char* pmc_last_error(void);
 

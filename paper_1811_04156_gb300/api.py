@@ -485,3 +485,12 @@ class PathSampler:
 
     def estimate(self):
         return self.chains.read_estimator()
+
+
+def measure_pipes(ctx: Context, stream=None) -> dict:
+    """Measured FP32 FMA and MUFU lane-operations per second of the device
+    (pmc_measure_pipes)."""
+    out = np.zeros(2)
+    check(load().pmc_measure_pipes(ctx.handle, out.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)),
+          "pmc_measure_pipes")
+    return {"fp32_per_s": float(out[0]), "mufu_per_s": float(out[1])}

@@ -268,6 +268,13 @@ extern "C" {
 
 const char* pmc_last_error(void) { return g_err.c_str(); }
 
+int pmc_measure_pipes(pmc_ctx_t ctx, double* out, void* stream) {
+  if (ctx == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  CK(cudaSetDevice(ctx->device));
+  CK(measure_pipes(ctx->n_sm, &out[0], &out[1], static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
 const char* pmc_version(void) { return "pathmc 0.1 (sm_103a)"; }
 
 int pmc_create_context(int device, pmc_ctx_t* out) {

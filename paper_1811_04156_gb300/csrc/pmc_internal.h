@@ -152,6 +152,9 @@ cudaError_t launch_qref_logdensity(const DMedium& M, const DRun& R, const DPair&
 
 // pmc_noalloc.cu: allocation-free tracer over up to kNoAllocMaxPairs pairs.
 constexpr int kNoAllocMaxPairs = 128;
+// FP32 FMA and MUFU lane-operations per second of the device (microbenchmark).
+cudaError_t measure_pipes(int n_sm, double* fp32_per_s, double* mufu_per_s, cudaStream_t s);
+
 cudaError_t launch_trace_noalloc(const DMedium& M, const DPair* pairs, int n_pairs, unsigned long long seed,
                                  unsigned long long photon0, unsigned long long n_photons, float r_reject,
                                  int max_scatter, double* host_out, int device, int n_sm, cudaStream_t s);

@@ -1,0 +1,30 @@
+"""Pipe-rate microbenchmark: measured FP32 and MUFU lane rates lie near the
+unit-count peaks (128 FP32 and 16 MUFU lanes per clock per SM)."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1811_04156_gb300 import build
+    build.build()
+    from paper_1811_04156_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    return api.Context(0)
+
+
+def test_measured_pipe_rates_near_unit_counts(api, ctx):
+    import torch
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    r = api.measure_pipes(ctx)
+    # clock between 1 GHz (power-capped) and 2.2 GHz (above the 2070 MHz maximum)
+    assert 128 * n_sm * 1.0e9 * 0.5 < r["fp32_per_s"] < 128 * n_sm * 2.2e9
+    assert 16 * n_sm * 1.0e9 * 0.5 < r["mufu_per_s"] < 16 * n_sm * 2.2e9
