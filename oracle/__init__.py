@@ -70,6 +70,13 @@ class Acc(C.Structure):
                 ("prop", C.c_double * 4), ("acc", C.c_double * 4)]
 
 
+class YMap(C.Structure):
+    _fields_ = [("f0", C.c_double * 3), ("eta0", C.c_double * 3), ("eta1", C.c_double * 3),
+                ("R0", C.c_double), ("R1", C.c_double), ("k", C.c_double * 3), ("m", C.c_double * 3),
+                ("n", C.c_double * 3), ("b0", C.c_double), ("b1", C.c_double), ("rC", C.c_double),
+                ("Omega", C.c_double)]
+
+
 ACC_FIELDS = ["n_rec", "n_direct", "sum_n", "sum_L", "sum_L2", "sum_bridge", "n_bridge"]
 
 _dp = C.POINTER(C.c_double)
@@ -114,6 +121,14 @@ def lib():
             L.or_trace.argtypes = [M, S, D, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int, _dp, C.c_int]
             L.or_trace_hist.argtypes = [M, S, D, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int, _dp, _dp,
                                         C.c_int]
+            L.or_trace_lhist.argtypes = [M, S, D, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int,
+                                         C.c_double, C.c_double, C.c_int, _dp, _dp, C.c_int]
+            Y = C.POINTER(YMap)
+            L.or_ymap_init.argtypes = [S, D, D, Y]
+            L.or_ymap_forward.argtypes = [Y, C.c_int, _dp, _dp]; L.or_ymap_forward.restype = C.c_double
+            L.or_ymap_inverse.argtypes = [Y, C.c_int, _dp, _dp]; L.or_ymap_inverse.restype = C.c_double
+            L.or_ymap_logratio.argtypes = [M, S, D, D, Y, C.c_int, C.c_int, _dp]
+            L.or_ymap_logratio.restype = C.c_double
             L.or_run_chains_hist.argtypes = [M, S, D, R, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint64,
                                              _dp, _ip, C.POINTER(Acc), _dp, _dp, C.c_int]
             _lib = L
@@ -307,6 +322,64 @@ def trace(m, s, d, seed, n_photons, photon0=0, r_reject=math.inf, max_scatter=1 
     if hist:
         res["hist"] = h / N
     return res
+
+
+def trace_lengths(m, s, d, seed, n_photons, l_lo, l_hi, l_bins, photon0=0, r_reject=math.inf,
+                  max_scatter=1 << 30, threads=None):
+    """Forward tracer with the detected weight binned by path length:
+    returns (result dict as trace(), weight per bin / emitted photons)."""
+    out = np.zeros(5)
+    h = np.zeros(int(l_bins))
+    rc = lib().or_trace_lhist(C.byref(m), C.byref(s), C.byref(d), seed, photon0, n_photons, r_reject, max_scatter,
+                              float(l_lo), float(l_hi), int(l_bins), _ptr(out), _ptr(h),
+                              threads or os.cpu_count() or 1)
+    if rc != 0:
+        raise ValueError("bad histogram range")
+    N = out[3]
+    mean = out[0] / N
+    var = max(out[1] / N - mean * mean, 0.0)
+    return {"I": mean, "se": math.sqrt(var / N), "hits": out[2], "photons": N, "raw": out}, h / N
+
+
+def ymap(s: Source, d0: Sensor, d1: Sensor) -> YMap:
+    """Relative-light-yield map of paths ending on sensor d0 to paths ending on d1."""
+    T = YMap()
+    if lib().or_ymap_init(C.byref(s), C.byref(d0), C.byref(d1), C.byref(T)) != 0:
+        raise ValueError("sensors collinear with the source, or a source inside a sensor")
+    return T
+
+
+def ymap_forward(T: YMap, path):
+    x = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 3)
+    y = np.zeros_like(x)
+    lj = lib().or_ymap_forward(C.byref(T), len(x), _ptr(x), _ptr(y))
+    return y, lj
+
+
+def ymap_inverse(T: YMap, path):
+    y = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 3)
+    x = np.zeros_like(y)
+    lj = lib().or_ymap_inverse(C.byref(T), len(y), _ptr(y), _ptr(x))
+    return x, lj
+
+
+def ymap_logratio(m: Medium, s: Source, d0: Sensor, d1: Sensor, T: YMap, side: int, path) -> float:
+    f = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 3)
+    return lib().or_ymap_logratio(C.byref(m), C.byref(s), C.byref(d0), C.byref(d1), C.byref(T), int(side), len(f),
+                                  _ptr(f))
+
+
+def yield_ratio_estimate(sums0, sums1):
+    """Geometric estimator B = E_0[sqrt(p_1/p_0)] / E_1[sqrt(p_0/p_1)] from
+    per-chain sums of sqrt-ratios (each array: one entry per chain, equal
+    observation counts); standard error by the delta method over the
+    across-chain variances of the per-chain means."""
+    a, b = np.asarray(sums0, float), np.asarray(sums1, float)
+    m0, m1 = a.mean(), b.mean()
+    v0 = a.var(ddof=1) / len(a)
+    v1 = b.var(ddof=1) / len(b)
+    B = m0 / m1
+    return B, B * math.sqrt(v0 / m0 ** 2 + v1 / m1 ** 2)
 
 
 class Chains:

@@ -1115,6 +1115,7 @@ typedef struct {
   const or_medium* m; const or_source* s; const or_sensor* d;
   uint64_t seed, p0, p1; double r_reject; int max_scatter; double out[5];
   double* hist;
+  double* lhist; double l_lo, l_hi; int l_bins;   /* path-length histogram (may be NULL) */
 } trace_job;
 
 static void* trace_worker(void* arg) {
@@ -1163,6 +1164,10 @@ static void* trace_worker(void* arg) {
         J->out[2] += 1.0;
         J->out[4] += W * L;
         if (J->hist) J->hist[i] += W;
+        if (J->lhist && L >= J->l_lo && L < J->l_hi) {
+          int bin = (int)floor((L - J->l_lo) / (J->l_hi - J->l_lo) * J->l_bins);
+          if (bin >= 0 && bin < J->l_bins) J->lhist[bin] += W;
+        }
         break;
       }
       double rel[3];
@@ -1190,9 +1195,10 @@ int or_trace(const or_medium* m, const or_source* s, const or_sensor* d,
   return or_trace_hist(m, s, d, seed, photon0, n_photons, r_reject, max_scatter, out, NULL, n_threads);
 }
 
-int or_trace_hist(const or_medium* m, const or_source* s, const or_sensor* d,
-                  uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
-                  int max_scatter, double* out, double* hist, int n_threads) {
+static int trace_run(const or_medium* m, const or_source* s, const or_sensor* d,
+                     uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
+                     int max_scatter, double* out, double* hist, double l_lo, double l_hi, int l_bins,
+                     double* lhist, int n_threads) {
   if (n_threads < 1) n_threads = 1;
   trace_job* jobs = (trace_job*)calloc((size_t)n_threads, sizeof(trace_job));
   pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
@@ -1200,12 +1206,15 @@ int or_trace_hist(const or_medium* m, const or_source* s, const or_sensor* d,
     trace_job* J = &jobs[i];
     J->m = m; J->s = s; J->d = d; J->seed = seed; J->r_reject = r_reject; J->max_scatter = max_scatter;
     J->hist = hist ? (double*)calloc((size_t)max_scatter + 1, sizeof(double)) : NULL;
+    J->lhist = lhist ? (double*)calloc((size_t)l_bins, sizeof(double)) : NULL;
+    J->l_lo = l_lo; J->l_hi = l_hi; J->l_bins = l_bins;
     J->p0 = photon0 + n_photons * (uint64_t)i / (uint64_t)n_threads;
     J->p1 = photon0 + n_photons * (uint64_t)(i + 1) / (uint64_t)n_threads;
     pthread_create(&th[i], NULL, trace_worker, J);
   }
   for (int k = 0; k < 5; ++k) out[k] = 0.0;
   if (hist) for (int k = 0; k <= max_scatter; ++k) hist[k] = 0.0;
+  if (lhist) for (int k = 0; k < l_bins; ++k) lhist[k] = 0.0;
   for (int i = 0; i < n_threads; ++i) {
     pthread_join(th[i], NULL);
     for (int k = 0; k < 5; ++k) out[k] += jobs[i].out[k];
@@ -1213,8 +1222,154 @@ int or_trace_hist(const or_medium* m, const or_source* s, const or_sensor* d,
       for (int k = 0; k <= max_scatter; ++k) hist[k] += jobs[i].hist[k];
       free(jobs[i].hist);
     }
+    if (lhist) {
+      for (int k = 0; k < l_bins; ++k) lhist[k] += jobs[i].lhist[k];
+      free(jobs[i].lhist);
+    }
   }
   free(jobs);
   free(th);
   return 0;
+}
+
+int or_trace_hist(const or_medium* m, const or_source* s, const or_sensor* d,
+                  uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
+                  int max_scatter, double* out, double* hist, int n_threads) {
+  return trace_run(m, s, d, seed, photon0, n_photons, r_reject, max_scatter, out, hist, 0.0, 0.0, 0, NULL,
+                   n_threads);
+}
+
+int or_trace_lhist(const or_medium* m, const or_source* s, const or_sensor* d,
+                   uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
+                   int max_scatter, double l_lo, double l_hi, int l_bins, double* out, double* lhist,
+                   int n_threads) {
+  if (!(l_hi > l_lo) || l_bins < 1) return -1;
+  return trace_run(m, s, d, seed, photon0, n_photons, r_reject, max_scatter, out, NULL, l_lo, l_hi, l_bins, lhist,
+                   n_threads);
+}
+
+/* ------------------------------------------------------------------------
+ * Relative light yield of two sensors (section "Comparison of relative light
+ * yield": B = E_0[sqrt(p_1/p_0)] / E_1[sqrt(p_0/p_1)]; appendix "Relative
+ * light yield transformation": the map T of paths ending on sensor 0 to
+ * paths ending on sensor 1 by bending them along a cylinder through the
+ * source, p_1(x) = p(T x) |dT/dx|).
+ *
+ * Interior vertices: intermediate coordinates xb = (f - f0).m / b0,
+ * yb = (f - f0).n / b0, w = (f - f0).k / b0, then
+ *   T f = f0 - rC m + (rC + xb b1)(m cos(w Omega) + k sin(w Omega)) + n yb b1,
+ * a cylindrical-coordinate map with volume ratio b1^2 Omega (rC + xb b1) / b0^3.
+ * The map is one-to-one where rC + xb b1 > 0 and |w Omega| < pi; outside that
+ * domain p_1 is taken as 0, which keeps B = I_1 / I_0 exact (every sensor-1
+ * path has its preimage inside the domain).
+ * End vertex: the unit offset from sensor 0's centre, rotated in the (m, k) plane
+ * by Omega (the turn of the bent path) and scaled by R1/R0, placed about
+ * sensor 1's centre: a bijection of the spheres with area ratio (R1/R0)^2.
+ * Frame: k = unit vector from the source to sensor 0, m = unit vector normal
+ * to k in the plane of k and B = eta1 - f0, pointing away from B, n = k x m;
+ * cos Psi = k.B/|B|, rC = |B| / (2 sin Psi), Omega = 2 Psi - R1/rC, b1 = rC Omega,
+ * b0 = |eta0 - f0| - R0.
+ * ---------------------------------------------------------------------- */
+int or_ymap_init(const or_source* s, const or_sensor* d0, const or_sensor* d1, or_ymap* T) {
+  double a[3], B[3];
+  sub3(d0->c, s->pos, a);
+  sub3(d1->c, s->pos, B);
+  const double la = norm3(a), lB = norm3(B);
+  if (!(la > d0->R) || !(lB > d1->R)) return -1;
+  copy3(s->pos, T->f0);
+  copy3(d0->c, T->eta0);
+  copy3(d1->c, T->eta1);
+  T->R0 = d0->R;
+  T->R1 = d1->R;
+  for (int i = 0; i < 3; ++i) T->k[i] = a[i] / la;
+  const double cpsi = dot3(T->k, B) / lB;
+  double perp[3];
+  for (int i = 0; i < 3; ++i) perp[i] = B[i] / lB - cpsi * T->k[i];
+  const double spsi = norm3(perp);
+  if (!(spsi > 1e-9)) return -1;
+  for (int i = 0; i < 3; ++i) T->m[i] = -perp[i] / spsi;
+  T->n[0] = T->k[1] * T->m[2] - T->k[2] * T->m[1];
+  T->n[1] = T->k[2] * T->m[0] - T->k[0] * T->m[2];
+  T->n[2] = T->k[0] * T->m[1] - T->k[1] * T->m[0];
+  const double psi = atan2(spsi, cpsi);
+  T->b0 = la - d0->R;
+  T->rC = lB / (2.0 * spsi);
+  T->Omega = 2.0 * psi - d1->R / T->rC;
+  T->b1 = T->rC * T->Omega;
+  if (!(T->Omega > 0.0)) return -1;
+  return 0;
+}
+
+double or_ymap_forward(const or_ymap* T, int n, const double* x, double* y) {
+  double lj = 0.0;
+  int inside = 1;
+  copy3(T->f0, y);
+  for (int i = 1; i <= n - 2; ++i) {
+    double d[3];
+    sub3(&x[3 * i], T->f0, d);
+    const double xb = dot3(d, T->m) / T->b0, yb = dot3(d, T->n) / T->b0, w = dot3(d, T->k) / T->b0;
+    const double ang = w * T->Omega, rad = T->rC + xb * T->b1;
+    if (!(rad > 0.0) || !(fabs(ang) < M_PI)) inside = 0;
+    for (int c = 0; c < 3; ++c)
+      y[3 * i + c] = T->f0[c] - T->rC * T->m[c] + rad * (T->m[c] * cos(ang) + T->k[c] * sin(ang)) +
+                     T->n[c] * yb * T->b1;
+    lj += log(T->b1 * T->b1 * T->Omega * fabs(rad) / (T->b0 * T->b0 * T->b0));
+  }
+  if (n >= 2) {
+    double u[3];
+    sub3(&x[3 * (n - 1)], T->eta0, u);
+    const double lu = norm3(u);  /* the end vertex lies on sensor 0: its unit offset */
+    const double um = dot3(u, T->m) / lu, uk = dot3(u, T->k) / lu, un = dot3(u, T->n) / lu;
+    const double co = cos(T->Omega), si = sin(T->Omega);
+    const double vm = um * co - uk * si, vk = um * si + uk * co;
+    for (int c = 0; c < 3; ++c)
+      y[3 * (n - 1) + c] = T->eta1[c] + T->R1 * (vm * T->m[c] + vk * T->k[c] + un * T->n[c]);
+    lj += 2.0 * log(T->R1 / T->R0);
+  }
+  return inside ? lj : -INFINITY;
+}
+
+double or_ymap_inverse(const or_ymap* T, int n, const double* y, double* x) {
+  double lj = 0.0;
+  int inside = 1;
+  copy3(T->f0, x);
+  for (int i = 1; i <= n - 2; ++i) {
+    double d[3];
+    for (int c = 0; c < 3; ++c) d[c] = y[3 * i + c] - (T->f0[c] - T->rC * T->m[c]);
+    const double h = dot3(d, T->n), pm = dot3(d, T->m), pk = dot3(d, T->k);
+    const double rad = sqrt(pm * pm + pk * pk), ang = atan2(pk, pm);
+    if (!(rad > 0.0) || !(fabs(ang) < M_PI)) inside = 0;
+    const double xb = (rad - T->rC) / T->b1, yb = h / T->b1, w = ang / T->Omega;
+    for (int c = 0; c < 3; ++c) x[3 * i + c] = T->f0[c] + T->b0 * (xb * T->m[c] + yb * T->n[c] + w * T->k[c]);
+    lj += log(T->b1 * T->b1 * T->Omega * rad / (T->b0 * T->b0 * T->b0));
+  }
+  if (n >= 2) {
+    double v[3];
+    sub3(&y[3 * (n - 1)], T->eta1, v);
+    const double lv = norm3(v);
+    const double vm = dot3(v, T->m) / lv, vk = dot3(v, T->k) / lv, vn = dot3(v, T->n) / lv;
+    const double co = cos(T->Omega), si = sin(T->Omega);
+    const double um = vm * co + vk * si, uk = -vm * si + vk * co;
+    for (int c = 0; c < 3; ++c)
+      x[3 * (n - 1) + c] = T->eta0[c] + T->R0 * (um * T->m[c] + uk * T->k[c] + vn * T->n[c]);
+    lj += 2.0 * log(T->R1 / T->R0);
+  }
+  return inside ? lj : -INFINITY;
+}
+
+double or_ymap_logratio(const or_medium* m, const or_source* s, const or_sensor* d0, const or_sensor* d1,
+                        const or_ymap* T, int side, int n, const double* path) {
+  double* other = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  double r;
+  if (side == 0) {
+    const double lj = or_ymap_forward(T, n, path, other);
+    const double lo = isfinite(lj) ? or_logp(m, s, d1, n, other) : -INFINITY;
+    r = lo + lj - or_logp(m, s, d0, n, path);
+  } else {
+    const double lj = or_ymap_inverse(T, n, path, other);
+    const double lo = isfinite(lj) ? or_logp(m, s, d0, n, other) : -INFINITY;
+    r = lo - lj - or_logp(m, s, d1, n, path);
+  }
+  free(other);
+  return isnan(r) ? -INFINITY : r;
 }

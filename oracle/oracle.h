@@ -161,6 +161,35 @@ int or_trace_hist(const or_medium* m, const or_source* s, const or_sensor* d,
                   uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
                   int max_scatter, double* out, double* hist, int n_threads);
 
+/* Same as or_trace, and adds each detected weight to lhist[bin] by its path
+ * length L: bin = floor((L - l_lo) / (l_hi - l_lo) * l_bins), L in [l_lo, l_hi). */
+int or_trace_lhist(const or_medium* m, const or_source* s, const or_sensor* d,
+                   uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
+                   int max_scatter, double l_lo, double l_hi, int l_bins, double* out, double* lhist,
+                   int n_threads);
+
+/* ---- relative light yield of two sensors (section "Comparison of relative
+ *      light yield"; appendix, "Relative light yield transformation") ---- */
+typedef struct {
+  double f0[3], eta0[3], eta1[3];
+  double R0, R1;
+  double k[3], m[3], n[3];  /* frame: k towards sensor 0, m in the (k, B) plane away from B, n = k x m */
+  double b0, b1, rC, Omega;
+} or_ymap;
+/* Map of source s and sensors d0 -> d1; -1 if the sensors are collinear with the source. */
+int or_ymap_init(const or_source* s, const or_sensor* d0, const or_sensor* d1, or_ymap* T);
+/* y = T(x) for an n-vertex path ending on sensor 0 (n x 3 rows); returns log |dT/dx|
+ * (interior volume ratios and the end vertex's area ratio), -inf outside the one-to-one domain. */
+double or_ymap_forward(const or_ymap* T, int n, const double* x, double* y);
+/* x = T^-1(y) for a path ending on sensor 1; returns log |dT/dx| at x, -inf outside the domain. */
+double or_ymap_inverse(const or_ymap* T, int n, const double* y, double* x);
+/* Log of the geometric estimator's ratio at one path: side 0 (path on sensor 0):
+ * log p_1(x) - log p_0(x) = log p(T x; d1) + log|dT/dx| - log p(x; d0); side 1
+ * (path y on sensor 1): log p_0(x) - log p_1(x) with x = T^-1 y.  -inf where the
+ * other density is zero. */
+double or_ymap_logratio(const or_medium* m, const or_source* s, const or_sensor* d0, const or_sensor* d1,
+                        const or_ymap* T, int side, int n, const double* path);
+
 #ifdef __cplusplus
 }
 #endif

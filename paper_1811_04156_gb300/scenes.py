@@ -225,6 +225,57 @@ def general_small(n_chains: int = 64, n_steps: int = 400) -> Scene:
     return Scene("general_small", med, [src], [sen], [Pair(0, 0, n_chains, 64)], run)
 
 
+# Scattering coefficients b1 (1/m) of the x >= 0 half of the paper's test scene (Table tbl:results).
+E1_B1 = (0.1, 0.2, 0.3, 0.4, 0.5)
+
+
+def to_device_frame(v):
+    """Paper frame (x, y, z) -> the frame the two-region scene is built in,
+    (y, z, x): a proper rotation that puts the paper's x axis (the normal of
+    the plane dividing the medium) on the layer axis."""
+    a = np.asarray(v, dtype=np.float64)
+    return np.stack([a[..., 1], a[..., 2], a[..., 0]], axis=-1)
+
+
+def to_paper_frame(v):
+    """Inverse of to_device_frame: (X, Y, Z) -> (Z, X, Y)."""
+    a = np.asarray(v, dtype=np.float64)
+    return np.stack([a[..., 2], a[..., 0], a[..., 1]], axis=-1)
+
+
+def _dev(v):
+    return tuple(float(x) for x in to_device_frame(v))
+
+
+def e1(b1: float = 0.3, n_chains: int = 4096, n_steps: int = 200_000, cap: int = 256,
+       sigma: float = 0.5, init_k: int = 30, init_jitter: float = 0.5) -> Scene:
+    """The paper's two-sensor test scene (section "Implementation", Fig. setup).
+
+    Source at the origin with vMF emission (kappa 38) along +z; the medium is
+    divided by the plane x = 0: absorption 0.01/m everywhere, scattering
+    0.3/m for x < 0 and ``b1`` for x >= 0; simplified-Liu / Henyey-Greenstein
+    mixture with Gamma = 0.95, f_SL = 0.45; sensors of radius 0.15 m at
+    (0, 0, 120) and (60, 7, 104) m, detection probability rho with rho_hat =
+    (0, -1, 0).  Pair 0 ends on sensor 0, pair 1 on sensor 1.
+
+    The two half-spaces are a two-layer medium (boundary at 0, the end layers
+    extend to infinity) in the frame of to_device_frame, so positions, the
+    emission axis and rho_hat are given in that frame; to_paper_frame maps
+    paths back.  Chains start from straight paths with ``init_k`` jittered
+    interior vertices and use Gaussian steps of ``sigma`` (m)."""
+    med = Medium(LAYERED, g=0.95, f_sl=0.45, z0=-1.0, dz=1.0,
+                 lambda_s_layers=np.array([1.0 / 0.3, 1.0 / float(b1)]),
+                 lambda_a_layers=np.array([100.0, 100.0]))
+    src = Source(_dev((0.0, 0.0, 0.0)), EMIT_VMF, 38.0, _dev((0.0, 0.0, 1.0)))
+    rho_hat = _dev((0.0, -1.0, 0.0))
+    sensors = [Sensor(_dev((0.0, 0.0, 120.0)), 0.15, RHO_PAPER, rho_hat),
+               Sensor(_dev((60.0, 7.0, 104.0)), 0.15, RHO_PAPER, rho_hat)]
+    pairs = [Pair(0, 0, n_chains, cap), Pair(0, 1, n_chains, cap)]
+    run = Run(seed=BASE_SEED + 8, n_steps=n_steps, burn_in=n_steps // 10, init=INIT_STRAIGHT,
+              init_k=init_k, init_jitter=init_jitter, sigma=sigma)
+    return Scene("e1", med, [src], sensors, pairs, run)
+
+
 PRESETS = {"plain": plain, "detector": detector, "batched": batched,
            "gradients": gradients, "layered": layered}
 
