@@ -1,5 +1,9 @@
 """Pipe-rate microbenchmark: measured FP32 and MUFU lane rates lie near the
-unit-count peaks (128 FP32 and 16 MUFU lanes per clock per SM)."""
+unit-count peaks.  FP32: 128 lanes per clock per SM.  MUFU: the benchmark
+alternates ex2 and lg2; on GB300 it measures ~21.3 lanes per clock per SM,
+which is what 32 ex2 lanes/clk (doubled exponential throughput) and 16 lg2
+lanes/clk give for an equal mix (2 / (1/32 + 1/16)), so the bounds admit up to
+32 lanes per clock."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -27,4 +31,4 @@ def test_measured_pipe_rates_near_unit_counts(api, ctx):
     r = api.measure_pipes(ctx)
     # clock between 1 GHz (power-capped) and 2.2 GHz (above the 2070 MHz maximum)
     assert 128 * n_sm * 1.0e9 * 0.5 < r["fp32_per_s"] < 128 * n_sm * 2.2e9
-    assert 16 * n_sm * 1.0e9 * 0.5 < r["mufu_per_s"] < 16 * n_sm * 2.2e9
+    assert 16 * n_sm * 1.0e9 * 0.5 < r["mufu_per_s"] < 32 * n_sm * 2.2e9
