@@ -74,6 +74,15 @@ def parse():
                    help="instead of the throughput line: wall time to this relative intensity error for plain "
                         "RJMCMC, batched MALA chains and the GPU forward tracer on the plain / detector geometry")
     p.add_argument("--geometry", default="plain", help="geometry of --time-to-target: plain or detector")
+    p.add_argument("--e1", action="store_true",
+                   help="instead of the throughput line: the paper's two-sensor scene (relative light yield B "
+                        "through the map T and path-length distributions for each b1, beside the GPU tracer)")
+    p.add_argument("--e1-b1", default="0.1,0.2,0.3,0.4,0.5")
+    p.add_argument("--e1-chains", type=int, default=2048, help="chains per sensor")
+    p.add_argument("--e1-steps", type=int, default=1_000_000, help="steps per chain (10%% burn-in)")
+    p.add_argument("--e1-thin", type=int, default=200, help="steps between observations of B and lengths")
+    p.add_argument("--e1-photons", type=int, default=0, help="tracer photons per sensor and b1 (0: no tracer)")
+    p.add_argument("--e1-out", default="", help="file for the full result (histograms included)")
     return p.parse_args()
 
 
@@ -514,10 +523,106 @@ def time_to_target(args):
     return 0
 
 
+# The paper's table of its two-sensor scene (section "Comparison of relative
+# light yield", Table tbl:results): B with its uncertainty for each b1, the
+# ray tracer's and the path sampler's, and the CPU seconds of each.
+E1_PAPER = {0.1: {"tracer": (0.67, 0.03), "sampler": (0.64, 0.07), "sampler_cpu_s": 23.0, "tracer_cpu_s": 45.9e3},
+            0.2: {"tracer": (0.79, 0.02), "sampler": (0.77, 0.01), "sampler_cpu_s": 74.4, "tracer_cpu_s": 78.1e3},
+            0.3: {"tracer": (0.73, 0.02), "sampler": (0.76, 0.07), "sampler_cpu_s": 232.0, "tracer_cpu_s": 99.6e3},
+            0.4: {"tracer": (0.68, 0.02), "sampler": (0.64, 0.04), "sampler_cpu_s": 373.0, "tracer_cpu_s": 122e3},
+            0.5: {"tracer": (0.59, 0.02), "sampler": (0.50, 0.06), "sampler_cpu_s": 416.0, "tracer_cpu_s": 156e3}}
+
+
+def e1_experiment(args):
+    """Relative light yield B of the paper's two sensors and their path-length
+    distributions, for each b1: chains of both sensors from straight jittered
+    paths, 10% burn-in, then B (geometric estimator through the map T) and the
+    length histograms observed every --e1-thin steps; optionally I_1/I_0 and
+    the length histograms of the GPU forward tracer (rejection radius 400 m,
+    scatterings capped at the chains' vertex cap)."""
+    import torch
+    from paper_1811_04156_gb300 import build as B
+    B.build()
+    from paper_1811_04156_gb300 import api, scenes as S
+    ctx = api.Context(0)
+    stream = torch.cuda.current_stream()
+    lo, hi, nb = 115.0, 215.0, 50
+    results = []
+    for b1 in [float(x) for x in args.e1_b1.split(",")]:
+        sc = S.e1(b1, n_chains=args.e1_chains, n_steps=args.e1_steps)
+        medium = api.Medium(ctx, sc.medium)
+        geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+        ch = api.Chains(ctx, medium, geom, sc.run)
+        Y = api.YieldRatio(ch, 0, 1)
+        hist = torch.zeros((2, nb), dtype=torch.float64, device="cuda")
+        burn = sc.run.burn_in
+        thin = args.e1_thin
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        ch.run_steps(burn)
+        done = burn
+        while done < sc.run.n_steps:
+            k = min(thin, sc.run.n_steps - done)
+            ch.run_steps(k)
+            done += k
+            Y.observe()
+            ch.length_hist(lo, hi, hist)
+        ev1.record(stream)
+        est = Y.estimate()
+        e = ch.read_estimator()
+        wall = time.perf_counter() - t0
+        gpu_s = ev0.elapsed_time(ev1) / 1e3
+        h = hist.cpu().numpy()
+        row = {"b1": b1, "B": est["B"], "B_se": est["se"], "rhat": [e[0]["rhat"], e[1]["rhat"]],
+               "accept": [e[0]["accept"], e[1]["accept"]], "mean_n": [e[0]["mean_n"], e[1]["mean_n"]],
+               "mean_length_m": [e[0]["mean_length"], e[1]["mean_length"]], "observations": Y.n_obs,
+               "proposals": 2 * args.e1_chains * sc.run.n_steps, "gpu_seconds": gpu_s, "wall_seconds": wall,
+               "proposals_per_s": 2 * args.e1_chains * sc.run.n_steps / gpu_s,
+               "length_hist": {"lo": lo, "hi": hi, "bins": nb, "sensor0": (h[0] / max(h[0].sum(), 1)).tolist(),
+                               "sensor1": (h[1] / max(h[1].sum(), 1)).tolist()},
+               "paper": E1_PAPER.get(b1)}
+        if args.e1_photons > 0:
+            cap = sc.pairs[0].cap
+            tr, th = [], []
+            t1 = time.perf_counter()
+            for p, sd in ((0, 701), (1, 702)):
+                r, hh = api.trace_lengths(ctx, medium, geom, p, sd, args.e1_photons, lo, hi, nb, r_reject=400.0,
+                                          max_scatter=cap - 2)
+                tr.append(r)
+                th.append(hh)
+            Bt = tr[1]["I"] / tr[0]["I"]
+            row["tracer"] = {"B": Bt, "B_se": Bt * math.hypot(tr[0]["se"] / tr[0]["I"], tr[1]["se"] / tr[1]["I"]),
+                             "I0": tr[0]["I"], "I0_se": tr[0]["se"], "I1": tr[1]["I"], "I1_se": tr[1]["se"],
+                             "hits": [tr[0]["hits"], tr[1]["hits"]], "photons_per_sensor": args.e1_photons,
+                             "seconds": time.perf_counter() - t1,
+                             "length_hist": {"sensor0": (th[0] / max(th[0].sum(), 1e-300)).tolist(),
+                                             "sensor1": (th[1] / max(th[1].sum(), 1e-300)).tolist()}}
+        results.append(row)
+        brief = {k: row[k] for k in ("b1", "B", "B_se", "rhat", "gpu_seconds", "proposals_per_s")}
+        if "tracer" in row:
+            brief["tracer_B"] = (row["tracer"]["B"], row["tracer"]["B_se"], row["tracer"]["hits"],
+                                 row["tracer"]["seconds"])
+        print(json.dumps(brief), flush=True)
+        ch.close()
+    out = {"experiment": "two-sensor scene (relative light yield, path lengths)", "chains_per_sensor": args.e1_chains,
+           "steps_per_chain": args.e1_steps, "thin": args.e1_thin, "results": results}
+    if args.e1_out:
+        with open(args.e1_out, "w") as f:
+            json.dump(out, f)
+    print(json.dumps({"experiment": out["experiment"],
+                      "B": [(r["b1"], r["B"], r["B_se"], r.get("tracer", {}).get("B")) for r in results]}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.time_to_target > 0:
         return time_to_target(args)
+    if args.e1:
+        return e1_experiment(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)

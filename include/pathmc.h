@@ -350,6 +350,64 @@ PMC_API int pmc_qref_sample(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom,
 PMC_API int pmc_bridge(pmc_chains_t chains, uint64_t n_draws, uint64_t seed, double* out, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Relative light yield of two sensors (section "Comparison of relative   */
+/* light yield"; appendix "Relative light yield transformation") and      */
+/* path-length distributions (section "Comparison of timing              */
+/* distributions")                                                        */
+/* ---------------------------------------------------------------------- */
+
+/* The yield entry points compare two pairs that share a source: pair0's
+ * paths end on sensor 0, pair1's on sensor 1.  The map T takes a path ending
+ * on sensor 0 to one ending on sensor 1 by bending it along a cylinder
+ * through the source whose tangent there points at sensor 0 (k = unit vector
+ * to sensor 0; m in the plane of k and B = (sensor 1 - source), pointing away
+ * from B; n = k x m; cos Psi = k.B/|B|; r_C = |B| / (2 sin Psi);
+ * Omega = 2 Psi - R_1 / r_C; b_0 = |sensor 0 - source| - R_0; b_1 = r_C Omega):
+ * interior vertex f with xb = (f - f0).m / b_0, yb = (f - f0).n / b_0,
+ * w = (f - f0).k / b_0 goes to
+ *   f0 - r_C m + (r_C + xb b_1)(m cos(w Omega) + k sin(w Omega)) + n yb b_1,
+ * with volume ratio b_1^2 Omega (r_C + xb b_1) / b_0^3; the end vertex keeps
+ * its offset direction from sensor 0's centre, rotated by Omega in the (m, k)
+ * plane, on sensor 1 (area ratio (R_1/R_0)^2).  T is one-to-one where
+ * r_C + xb b_1 > 0 and |w Omega| < pi; elsewhere the other density is 0.
+ * Then p_1(x) = p(T x; sensor 1) |dT/dx| and the geometric estimator
+ * B = E_0[sqrt(p_1/p_0)] / E_1[sqrt(p_0/p_1)] is the ratio of the light seen by
+ * sensor 1 to the light seen by sensor 0.  Errors: PMC_ERR_INVALID when the
+ * pairs are equal or out of range, do not share a source position, or the
+ * sensors are collinear with the source. */
+
+/* Log density ratio of caller paths (layout, frame and ownership of
+ * pmc_logp).  side 0 (paths of pair0): out[b] = log p(T x; pair1) +
+ * log|dT/dx| - log p(x; pair0); side 1 (paths of pair1): out[b] =
+ * log p(T^-1 y; pair0) - log|dT/dx| at T^-1 y - log p(y; pair1).  -inf outside
+ * T's domain or where either density is 0; NaN when n is outside [2, cap].
+ * out_xyz (device, same layout as xyz, may be NULL) receives the mapped paths.
+ * Asynchronous on `stream`. */
+PMC_API int pmc_yield_logratio(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair0, int pair1, int side,
+                               const float* xyz, const int* n, int batch, int cap, float* out, float* out_xyz,
+                               void* stream);
+
+/* One observation of every chain of pair0 and pair1 at its current path:
+ * sums[i] += sqrt(p_1/p_0) for pair0's chain i (i < n0 = pair0's chain count)
+ * and sums[n0 + i] += sqrt(p_0/p_1) for pair1's chain i (0 outside T's
+ * domain).  sums: device, caller-owned, n0 + n1 doubles, zeroed by the caller
+ * before the first observation.  Asynchronous on `stream`. */
+PMC_API int pmc_yield_observe(pmc_chains_t chains, int pair0, int pair1, double* sums, void* stream);
+
+/* Estimate from the sums of n_obs observations: out (host, 6 doubles) = B,
+ * its standard error (delta method over the across-chain variances of the
+ * per-chain means), E_0[sqrt(p_1/p_0)], E_1[sqrt(p_0/p_1)], and the two
+ * across-chain variances.  Synchronises `stream`. */
+PMC_API int pmc_yield_estimate(pmc_chains_t chains, int pair0, int pair1, const double* sums, uint64_t n_obs,
+                               double* out, void* stream);
+
+/* Path-length distribution of the chains: one observation of every chain,
+ * hist[pair][bin] += 1 with bin = floor((L - l_lo) / (l_hi - l_lo) * n_bins)
+ * for its current path length L in [l_lo, l_hi) (others are not counted).
+ * hist: device, caller-owned, n_pairs * n_bins doubles.  Asynchronous. */
+PMC_API int pmc_length_hist(pmc_chains_t chains, double l_lo, double l_hi, int n_bins, double* hist, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Comparison baseline                                                    */
 /* ---------------------------------------------------------------------- */
 
@@ -363,6 +421,15 @@ PMC_API int pmc_bridge(pmc_chains_t chains, uint64_t n_draws, uint64_t seed, dou
 PMC_API int pmc_trace(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair,
               uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
               int max_scatter, double* out, void* stream);
+
+/* pmc_trace that also bins each detected photon's weight w*rho by its path
+ * length L: hist (host, caller-owned, n_bins doubles) receives the summed
+ * weight of bin floor((L - l_lo) / (l_hi - l_lo) * n_bins), L in [l_lo, l_hi)
+ * (section "Comparison of timing distributions", the ray tracer's side).
+ * out as for pmc_trace.  Synchronises `stream`. */
+PMC_API int pmc_trace_lengths(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair, uint64_t seed,
+                              uint64_t photon0, uint64_t n_photons, double r_reject, int max_scatter, double l_lo,
+                              double l_hi, int n_bins, double* out, double* hist, void* stream);
 
 /* Allocation-free forward tracer for callers that cannot allocate device
  * memory (an application whose own pool allocator has reserved the device, a

@@ -120,6 +120,13 @@ PROTOTYPES = {
     "pmc_bridge": ([_vp, C.c_uint64, C.c_uint64, _dp, _vp], C.c_int),
     "pmc_trace_paths": ([_vp, _vp, _vp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int, C.c_int,
                          _vp, _vp, C.c_int, C.POINTER(C.c_uint64), _vp], C.c_int),
+    "pmc_yield_logratio": ([_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp],
+                           C.c_int),
+    "pmc_yield_observe": ([_vp, C.c_int, C.c_int, _vp, _vp], C.c_int),
+    "pmc_yield_estimate": ([_vp, C.c_int, C.c_int, _vp, C.c_uint64, _dp, _vp], C.c_int),
+    "pmc_length_hist": ([_vp, C.c_double, C.c_double, C.c_int, _vp, _vp], C.c_int),
+    "pmc_trace_lengths": ([_vp, _vp, _vp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int,
+                           C.c_double, C.c_double, C.c_int, _dp, _dp, _vp], C.c_int),
     "pmc_measure_pipes": ([_vp, _dp, _vp], C.c_int),
     "pmc_last_error": ([], C.c_char_p),
     "pmc_version": ([], C.c_char_p),

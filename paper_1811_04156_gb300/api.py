@@ -230,6 +230,32 @@ class Chains:
                                 _stream(stream)), "pmc_bridge")
         return out
 
+    def yield_observe(self, pair0: int, pair1: int, sums: torch.Tensor, stream=None):
+        """One observation of sqrt(p_other/p_own) per chain of pair0 and pair1 (pmc_yield_observe)."""
+        _require_cuda(sums, torch.float64, "sums")
+        need = self.geom.pairs[pair0].n_chains + self.geom.pairs[pair1].n_chains
+        if sums.numel() != need:
+            raise ValueError(f"sums must hold {need} doubles")
+        check(load().pmc_yield_observe(self.handle, int(pair0), int(pair1), C.c_void_p(sums.data_ptr()),
+                                       _stream(stream)), "pmc_yield_observe")
+
+    def yield_estimate(self, pair0: int, pair1: int, sums: torch.Tensor, n_obs: int, stream=None) -> dict:
+        """B = light on pair1's sensor / light on pair0's sensor from the observation sums (pmc_yield_estimate)."""
+        _require_cuda(sums, torch.float64, "sums")
+        out = np.zeros(6)
+        check(load().pmc_yield_estimate(self.handle, int(pair0), int(pair1), C.c_void_p(sums.data_ptr()),
+                                        int(n_obs), out.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)),
+              "pmc_yield_estimate")
+        return {"B": out[0], "se": out[1], "E0": out[2], "E1": out[3], "var0": out[4], "var1": out[5]}
+
+    def length_hist(self, l_lo: float, l_hi: float, hist: torch.Tensor, stream=None):
+        """One observation of every chain's path length into hist (n_pairs, n_bins) (pmc_length_hist)."""
+        _require_cuda(hist, torch.float64, "hist")
+        if hist.dim() != 2 or hist.shape[0] != self.n_pairs:
+            raise ValueError("hist must have shape (n_pairs, n_bins)")
+        check(load().pmc_length_hist(self.handle, float(l_lo), float(l_hi), int(hist.shape[1]),
+                                     C.c_void_p(hist.data_ptr()), _stream(stream)), "pmc_length_hist")
+
     def read_states(self, stream=None):
         stride = self.geom.max_cap
         xyz = np.zeros((self.total, 3, stride), dtype=np.float32)
@@ -360,6 +386,58 @@ def trace(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: int, n_
     var = max(out[1] / N - mean * mean, 0.0) if N > 0 else float("nan")
     return {"I": mean, "se": math.sqrt(var / N) if N > 0 else float("nan"), "hits": out[2], "photons": N,
             "mean_L": out[4] / out[0] if out[0] > 0 else float("nan"), "raw": out}
+
+
+def trace_lengths(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: int, n_photons: int, l_lo: float,
+                  l_hi: float, n_bins: int, photon0: int = 0, r_reject: float = math.inf, max_scatter: int = 1 << 30,
+                  stream=None):
+    """GPU forward tracer with the detected weight binned by path length
+    (pmc_trace_lengths): (result dict as trace(), weight per bin / emitted photons)."""
+    out = np.zeros(5)
+    hist = np.zeros(int(n_bins))
+    check(load().pmc_trace_lengths(ctx.handle, medium.handle, geom.handle, int(pair), int(seed), int(photon0),
+                                   int(n_photons), float(r_reject), int(min(max_scatter, 2**31 - 1)), float(l_lo),
+                                   float(l_hi), int(n_bins), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                   hist.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)), "pmc_trace_lengths")
+    N = out[3]
+    mean = out[0] / N
+    var = max(out[1] / N - mean * mean, 0.0)
+    return {"I": mean, "se": math.sqrt(var / N), "hits": out[2], "photons": N, "raw": out}, hist / N
+
+
+def yield_logratio(ctx: Context, medium: Medium, geom: Geometry, pair0: int, pair1: int, side: int,
+                   xyz: torch.Tensor, n: torch.Tensor, mapped: bool = False, stream=None):
+    """Log density ratio of the other sensor's density (through the map T) to
+    the own one for a device batch (pmc_yield_logratio); with mapped=True also
+    the mapped paths (3, batch, cap)."""
+    batch, cap = _check_batch(xyz, n)
+    out = torch.empty(batch, dtype=torch.float32, device=xyz.device)
+    oxyz = torch.zeros_like(xyz) if mapped else None
+    check(load().pmc_yield_logratio(ctx.handle, medium.handle, geom.handle, int(pair0), int(pair1), int(side),
+                                    C.c_void_p(xyz.data_ptr()), C.c_void_p(n.data_ptr()), batch, cap,
+                                    C.c_void_p(out.data_ptr()),
+                                    C.c_void_p(oxyz.data_ptr() if mapped else None), _stream(stream)),
+          "pmc_yield_logratio")
+    return (out, oxyz) if mapped else out
+
+
+class YieldRatio:
+    """Relative light yield B of two pairs sharing a source (pair1's sensor over
+    pair0's): a device buffer of per-chain sums, filled by observe() between
+    run_steps calls and reduced by estimate()."""
+
+    def __init__(self, chains: Chains, pair0: int, pair1: int):
+        self.chains, self.pair0, self.pair1 = chains, int(pair0), int(pair1)
+        n = chains.geom.pairs[pair0].n_chains + chains.geom.pairs[pair1].n_chains
+        self.sums = torch.zeros(n, dtype=torch.float64, device=f"cuda:{chains.ctx.device}")
+        self.n_obs = 0
+
+    def observe(self, stream=None):
+        self.chains.yield_observe(self.pair0, self.pair1, self.sums, stream)
+        self.n_obs += 1
+
+    def estimate(self, stream=None) -> dict:
+        return self.chains.yield_estimate(self.pair0, self.pair1, self.sums, self.n_obs, stream)
 
 
 def qref_logdensity(ctx: Context, medium: Medium, geom: Geometry, pair: int, xyz: torch.Tensor, n: torch.Tensor,

@@ -1287,6 +1287,140 @@ int pmc_bridge(pmc_chains_t ch, uint64_t n_draws, uint64_t seed, double* out, vo
   return PMC_OK;
 }
 
+// Map T of paths ending on pair0's sensor to paths ending on pair1's sensor
+// (FP64 constants, FP32 on the device), in the source frame of the chains or
+// the absolute frame of caller batches.  Fails unless the pairs share their
+// source position and the sensors are not collinear with it.
+static int make_ymap(pmc_geom_t g, int pair0, int pair1, bool source_frame, DYMap* T) {
+  if (g == nullptr || pair0 < 0 || pair1 < 0 || pair0 >= static_cast<int>(g->host.size()) ||
+      pair1 >= static_cast<int>(g->host.size()) || pair0 == pair1)
+    return fail(PMC_ERR_INVALID, "yield: pair indices out of range or equal");
+  const PairHost& h0 = g->host[pair0];
+  const PairHost& h1 = g->host[pair1];
+  for (int i = 0; i < 3; ++i)
+    if (h0.src[i] != h1.src[i]) return fail(PMC_ERR_INVALID, "yield: the two pairs must share a source position");
+  double a[3], B[3], k[3], perp[3], m[3], n[3];
+  for (int i = 0; i < 3; ++i) {
+    a[i] = h0.c[i] - h0.src[i];
+    B[i] = h1.c[i] - h1.src[i];
+  }
+  const double la = norm3(a), lB = norm3(B);
+  if (!(la > h0.R) || !(lB > h1.R)) return fail(PMC_ERR_INVALID, "yield: source inside a sensor");
+  for (int i = 0; i < 3; ++i) k[i] = a[i] / la;
+  const double cpsi = (k[0] * B[0] + k[1] * B[1] + k[2] * B[2]) / lB;
+  for (int i = 0; i < 3; ++i) perp[i] = B[i] / lB - cpsi * k[i];
+  const double spsi = norm3(perp);
+  if (!(spsi > 1e-9)) return fail(PMC_ERR_INVALID, "yield: sensors collinear with the source");
+  for (int i = 0; i < 3; ++i) m[i] = -perp[i] / spsi;
+  n[0] = k[1] * m[2] - k[2] * m[1];
+  n[1] = k[2] * m[0] - k[0] * m[2];
+  n[2] = k[0] * m[1] - k[1] * m[0];
+  const double psi = std::atan2(spsi, cpsi);
+  const double b0 = la - h0.R, rC = lB / (2.0 * spsi);
+  const double Omega = 2.0 * psi - h1.R / rC;
+  if (!(Omega > 0.0)) return fail(PMC_ERR_INVALID, "yield: sensor 1 too large for its angle to sensor 0");
+  const double b1 = rC * Omega;
+  *T = DYMap{};
+  for (int i = 0; i < 3; ++i) {
+    T->f0[i] = source_frame ? 0.0f : static_cast<float>(h0.src[i]);
+    T->k[i] = static_cast<float>(k[i]);
+    T->m[i] = static_cast<float>(m[i]);
+    T->n[i] = static_cast<float>(n[i]);
+  }
+  T->rC = static_cast<float>(rC);
+  T->Omega = static_cast<float>(Omega);
+  T->b0 = static_cast<float>(b0);
+  T->b1 = static_cast<float>(b1);
+  T->inv_b0 = static_cast<float>(1.0 / b0);
+  T->cosO = static_cast<float>(std::cos(Omega));
+  T->sinO = static_cast<float>(std::sin(Omega));
+  T->R0 = static_cast<float>(h0.R);
+  T->R1 = static_cast<float>(h1.R);
+  T->vol = static_cast<float>(b1 * b1 * Omega / (b0 * b0 * b0));
+  T->log_area = static_cast<float>(2.0 * std::log(h1.R / h0.R));
+  return PMC_OK;
+}
+
+int pmc_yield_logratio(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair0, int pair1, int side,
+                       const float* xyz, const int* n, int batch, int cap, float* out, float* out_xyz, void* stream) {
+  if (!ctx || !med || !geom || !xyz || !n || !out) return fail(PMC_ERR_INVALID, "bad argument");
+  if (side != 0 && side != 1) return fail(PMC_ERR_INVALID, "side must be 0 or 1");
+  if (batch < 0 || cap < 2 || cap > (1 << 20)) return fail(PMC_ERR_INVALID, "bad batch or cap");
+  DYMap T;
+  const int rc = make_ymap(geom, pair0, pair1, false, &T);
+  if (rc != PMC_OK) return rc;
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_yield_logratio(med->d, geom->abs_pairs[pair0], geom->abs_pairs[pair1], T, side, xyz, n, batch, cap, out,
+                           out_xyz, static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
+int pmc_yield_observe(pmc_chains_t ch, int pair0, int pair1, double* sums, void* stream) {
+  if (ch == nullptr || sums == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  DYMap T;
+  const int rc = make_ymap(ch->geom, pair0, pair1, true, &T);
+  if (rc != PMC_OK) return rc;
+  CK(cudaSetDevice(ch->ctx->device));
+  const DPair& p0 = ch->h_pairs[pair0];
+  const DPair& p1 = ch->h_pairs[pair1];
+  CK(launch_yield_chains(ch->med->d, ch->d_pairs, pair0, pair1, T, ch->d_chain_base, ch->d_xyz, ch->d_n, p0.chain0,
+                         p0.n_chains, p1.chain0, p1.n_chains, sums, static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
+int pmc_yield_estimate(pmc_chains_t ch, int pair0, int pair1, const double* sums, uint64_t n_obs, double* out,
+                       void* stream) {
+  if (ch == nullptr || sums == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (n_obs == 0) return fail(PMC_ERR_INVALID, "n_obs must be > 0");
+  if (pair0 < 0 || pair1 < 0 || pair0 >= ch->n_pairs || pair1 >= ch->n_pairs || pair0 == pair1)
+    return fail(PMC_ERR_INVALID, "yield: pair indices out of range or equal");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* d_out = nullptr;
+  CK(dalloc(&d_out, 6));
+  cudaError_t e = launch_yield_estimate(sums, ch->h_pairs[pair0].n_chains, ch->h_pairs[pair1].n_chains,
+                                        static_cast<double>(n_obs), d_out, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_out);
+  CK(e);
+  return PMC_OK;
+}
+
+int pmc_length_hist(pmc_chains_t ch, double l_lo, double l_hi, int n_bins, double* hist, void* stream) {
+  if (ch == nullptr || hist == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (!(l_hi > l_lo) || !std::isfinite(l_lo) || !std::isfinite(l_hi) || n_bins < 1)
+    return fail(PMC_ERR_INVALID, "bad histogram range");
+  CK(cudaSetDevice(ch->ctx->device));
+  CK(launch_length_hist(ch->d_pairs, ch->d_chain_pair, ch->d_chain_base, ch->d_xyz, ch->d_n, ch->total, l_lo, l_hi,
+                        n_bins, hist, static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
+int pmc_trace_lengths(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, uint64_t seed, uint64_t photon0,
+                      uint64_t n_photons, double r_reject, int max_scatter, double l_lo, double l_hi, int n_bins,
+                      double* out, double* hist, void* stream) {
+  const DPair* d = pair_of(geom, pair, false);
+  if (!ctx || !med || !d || !out || !hist) return fail(PMC_ERR_INVALID, "bad argument");
+  if (max_scatter < 0 || !(r_reject > 0)) return fail(PMC_ERR_INVALID, "bad tracer limits");
+  if (!(l_hi > l_lo) || !std::isfinite(l_lo) || !std::isfinite(l_hi) || n_bins < 1)
+    return fail(PMC_ERR_INVALID, "bad histogram range");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* d_out = nullptr;
+  CK(dalloc(&d_out, 5 + static_cast<size_t>(n_bins)));
+  const float rr = std::isfinite(r_reject) ? static_cast<float>(r_reject) : std::numeric_limits<float>::infinity();
+  cudaError_t e = launch_trace_lengths(med->d, *d, seed, photon0, n_photons, rr, max_scatter, l_lo, l_hi, n_bins,
+                                       d_out, d_out + 5, ctx->n_sm, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hist, d_out + 5, static_cast<size_t>(n_bins) * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_out);
+  CK(e);
+  return PMC_OK;
+}
+
 int pmc_trace_paths(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, uint64_t seed, uint64_t photon0,
                     uint64_t n_photons, double r_reject, int max_scatter, int max_paths, float* out_xyz, int* out_n,
                     int stride, uint64_t* n_accepted, void* stream) {

@@ -120,6 +120,12 @@ cudaError_t launch_estimator(const EstParams& p, cudaStream_t s);
 cudaError_t launch_trace(const DMedium& M, const DPair& S, unsigned long long seed,
                          unsigned long long photon0, unsigned long long n_photons, float r_reject,
                          int max_scatter, double* out5, int n_sm, cudaStream_t s);
+// Forward tracer that also adds each detected weight w*rho to hist[bin] by
+// its path length L in [l_lo, l_hi) (n_bins equal bins; hist zeroed here).
+cudaError_t launch_trace_lengths(const DMedium& M, const DPair& S, unsigned long long seed,
+                                 unsigned long long photon0, unsigned long long n_photons, float r_reject,
+                                 int max_scatter, double l_lo, double l_hi, int n_bins, double* out5, double* hist,
+                                 int n_sm, cudaStream_t s);
 
 // Per-layer score sums over the chains' current states: sums[pair][0..2L) and
 // squares at sums[pair][2L..4L) (layered media, L <= 4096).
@@ -149,6 +155,34 @@ cudaError_t launch_qref_chains(const DMedium& M, const DRun& R, const DPair* pai
 cudaError_t launch_qref_logdensity(const DMedium& M, const DRun& R, const DPair& S, const QrefPair* qp,
                                    const double* qtab, const float* xyz, const int* n, int batch, int cap, float* out,
                                    cudaStream_t s);
+
+// pmc_yield.cu: relative light yield of two sensors and path-length histograms.
+// The map T of paths ending on sensor 0 to paths ending on sensor 1, in the
+// frame of the pair structs it is used with (source frame for chain states,
+// absolute frame for caller batches).
+struct DYMap {
+  float f0[3];                 // source position in the frame
+  float k[3], m[3], n[3];      // k towards sensor 0, m in the plane of k and B away from B, n = k x m
+  float rC, Omega, b0, b1, inv_b0;
+  float cosO, sinO;            // rotation of the end vertex about the sensor
+  float R0, R1;
+  float vol;                   // b1^2 Omega / b0^3: interior volume ratio over (rC + xb b1)
+  float log_area;              // 2 log(R1 / R0): end-vertex area ratio
+};
+// Adds exp(r/2) of every chain of pair0 (side 0) and pair1 (side 1) to sums
+// [n0 + n1], r the log ratio of the other density at the mapped path to the own one.
+cudaError_t launch_yield_chains(const DMedium& M, const DPair* pairs, int pair0, int pair1, const DYMap& T,
+                                const long long* chain_base, const float* xyz, const int* n, int chain0_0, int n0,
+                                int chain0_1, int n1, double* sums, cudaStream_t s);
+cudaError_t launch_yield_logratio(const DMedium& M, const DPair& S0, const DPair& S1, const DYMap& T, int side,
+                                  const float* xyz, const int* n, int batch, int cap, float* out,
+                                  float* out_xyz, cudaStream_t s);
+// out (device, 6 doubles): B, standard error, E_0, E_1, across-chain variances of the per-chain means.
+cudaError_t launch_yield_estimate(const double* sums, int n0, int n1, double n_obs, double* out, cudaStream_t s);
+// Adds 1 to hist[pair][bin] for each chain's current path length L in [lo, hi).
+cudaError_t launch_length_hist(const DPair* pairs, const int* chain_pair, const long long* chain_base,
+                               const float* xyz, const int* n, int total, double lo, double hi, int n_bins,
+                               double* hist, cudaStream_t s);
 
 // pmc_noalloc.cu: allocation-free tracer over up to kNoAllocMaxPairs pairs.
 constexpr int kNoAllocMaxPairs = 128;

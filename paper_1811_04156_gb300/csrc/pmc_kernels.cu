@@ -447,7 +447,9 @@ __device__ PhotonResult trace_photon(const DMedium& M, const DPair& S, uint32_t 
 
 __global__ void __launch_bounds__(256) trace_kernel(const DMedium M, const DPair S, unsigned long long seed,
                                                     unsigned long long photon0, unsigned long long n_photons,
-                                                    float r_reject, int max_scatter, double* __restrict__ out5) {
+                                                    float r_reject, int max_scatter, double* __restrict__ out5,
+                                                    double* __restrict__ hist, double l_lo, double bins_per_m,
+                                                    int n_bins) {
   __shared__ double sh[8 * 5];
   const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
   double v[5] = {0, 0, 0, 0, 0};
@@ -462,6 +464,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const DMedium M, const DPair
       v[1] += W * W;
       v[2] += 1.0;
       v[4] += W * static_cast<double>(pr.L);
+      if (hist != nullptr) {
+        const double fb = (static_cast<double>(pr.L) - l_lo) * bins_per_m;
+        if (fb >= 0.0 && fb < static_cast<double>(n_bins)) atomicAdd(hist + static_cast<int>(fb), W);
+      }
     }
   }
   block_sum<5>(v, sh);
@@ -607,7 +613,24 @@ cudaError_t launch_trace(const DMedium& M, const DPair& S, unsigned long long se
   const unsigned long long maxb = static_cast<unsigned long long>(n_sm) * 8ull;
   if (blocks > maxb) blocks = maxb;
   trace_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(M, S, seed, photon0, n_photons, r_reject,
-                                                             max_scatter, out5);
+                                                             max_scatter, out5, nullptr, 0.0, 0.0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_lengths(const DMedium& M, const DPair& S, unsigned long long seed,
+                                 unsigned long long photon0, unsigned long long n_photons, float r_reject,
+                                 int max_scatter, double l_lo, double l_hi, int n_bins, double* out5, double* hist,
+                                 int n_sm, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out5, 0, 5 * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, static_cast<size_t>(n_bins) * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  if (n_photons == 0) return cudaSuccess;
+  unsigned long long blocks = (n_photons + 255) / 256;
+  const unsigned long long maxb = static_cast<unsigned long long>(n_sm) * 8ull;
+  if (blocks > maxb) blocks = maxb;
+  trace_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(M, S, seed, photon0, n_photons, r_reject,
+                                                             max_scatter, out5, hist, l_lo,
+                                                             static_cast<double>(n_bins) / (l_hi - l_lo), n_bins);
   return cudaGetLastError();
 }
 
