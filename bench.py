@@ -83,6 +83,9 @@ def parse():
     p.add_argument("--e1-thin", type=int, default=200, help="steps between observations of B and lengths")
     p.add_argument("--e1-photons", type=int, default=0, help="tracer photons per sensor and b1 (0: no tracer)")
     p.add_argument("--e1-out", default="", help="file for the full result (histograms included)")
+    p.add_argument("--e1-seed", action="store_true",
+                   help="start the chains from weight-thinned tracer paths (exact draws, as the paper seeds its "
+                        "chains) instead of straight jittered paths")
     return p.parse_args()
 
 
@@ -553,6 +556,11 @@ def e1_experiment(args):
         medium = api.Medium(ctx, sc.medium)
         geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
         ch = api.Chains(ctx, medium, geom, sc.run)
+        seed_s, seed_photons = 0.0, None
+        if args.e1_seed:
+            ts = time.perf_counter()
+            seed_photons = api.seed_from_tracer(ch, seed=2468, photons_per_round=1 << 28, r_reject=400.0)
+            seed_s = time.perf_counter() - ts
         Y = api.YieldRatio(ch, 0, 1)
         hist = torch.zeros((2, nb), dtype=torch.float64, device="cuda")
         burn = sc.run.burn_in
@@ -582,7 +590,8 @@ def e1_experiment(args):
                "proposals_per_s": 2 * args.e1_chains * sc.run.n_steps / gpu_s,
                "length_hist": {"lo": lo, "hi": hi, "bins": nb, "sensor0": (h[0] / max(h[0].sum(), 1)).tolist(),
                                "sensor1": (h[1] / max(h[1].sum(), 1)).tolist()},
-               "paper": E1_PAPER.get(b1)}
+               "init": "tracer seeds" if args.e1_seed else "straight, 30 interior vertices, N(0, 0.5 m) jitter",
+               "seed_seconds": seed_s, "seed_photons": seed_photons, "paper": E1_PAPER.get(b1)}
         if args.e1_photons > 0:
             cap = sc.pairs[0].cap
             tr, th = [], []
@@ -600,7 +609,7 @@ def e1_experiment(args):
                              "length_hist": {"sensor0": (th[0] / max(th[0].sum(), 1e-300)).tolist(),
                                              "sensor1": (th[1] / max(th[1].sum(), 1e-300)).tolist()}}
         results.append(row)
-        brief = {k: row[k] for k in ("b1", "B", "B_se", "rhat", "gpu_seconds", "proposals_per_s")}
+        brief = {k: row[k] for k in ("b1", "B", "B_se", "rhat", "gpu_seconds", "proposals_per_s", "seed_seconds")}
         if "tracer" in row:
             brief["tracer_B"] = (row["tracer"]["B"], row["tracer"]["B_se"], row["tracer"]["hits"],
                                  row["tracer"]["seconds"])

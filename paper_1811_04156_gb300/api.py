@@ -494,10 +494,15 @@ def trace_paths(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: i
     return xyz[:, :kept], n[:kept], int(acc.value)
 
 
-def seed_from_tracer(chains: "Chains", seed: int = 2024, photons_per_round: int = 1 << 28, max_rounds: int = 64):
+def seed_from_tracer(chains: "Chains", seed: int = 2024, photons_per_round: int = 1 << 28, max_rounds: int = 64,
+                     r_reject: float = math.inf):
     """Initialise every chain with an equilibrium path: weight-thinned tracer
     paths per pair, reused cyclically when fewer than the pair's chains were
-    found; returns the photons traced per pair."""
+    found; returns the photons traced per pair.  Pair p traces with Philox
+    key seed + p, so the pairs' seeds are independent.  r_reject: photons farther
+    than this from the sensor centre are dropped (a finite radius shortens
+    the tracing of escaping photons; its bias is the weight of paths that
+    leave the ball and return)."""
     geom = chains.geom
     stride = geom.max_cap
     total_xyz = np.zeros((chains.total, 3, stride), dtype=np.float32)
@@ -508,8 +513,8 @@ def seed_from_tracer(chains: "Chains", seed: int = 2024, photons_per_round: int 
         got_x, got_n, photons = [], [], 0
         need = pr.n_chains
         for _ in range(max_rounds):
-            xyz, n, acc = trace_paths(chains.ctx, chains.medium, geom, p, seed, photons_per_round, need,
-                                      photon0=photons, stride=stride)
+            xyz, n, acc = trace_paths(chains.ctx, chains.medium, geom, p, seed + p, photons_per_round, need,
+                                      photon0=photons, stride=stride, r_reject=r_reject)
             photons += photons_per_round
             if len(n):
                 got_x.append(xyz.cpu().numpy())
