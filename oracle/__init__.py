@@ -129,6 +129,10 @@ def lib():
             L.or_ymap_inverse.argtypes = [Y, C.c_int, _dp, _dp]; L.or_ymap_inverse.restype = C.c_double
             L.or_ymap_logratio.argtypes = [M, S, D, D, Y, C.c_int, C.c_int, _dp]
             L.or_ymap_logratio.restype = C.c_double
+            L.or_tree_node.argtypes = [C.c_int, C.c_int, _ip, _ip, _ip]
+            L.or_tree_coords.argtypes = [_dp, C.c_int, _dp, _dp]; L.or_tree_coords.restype = C.c_double
+            L.or_tree_path.argtypes = [_dp, C.c_int, _dp, _dp]
+            L.or_tree_vref.argtypes = [S, D, _dp]
             L.or_run_chains_hist.argtypes = [M, S, D, R, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint64,
                                              _dp, _ip, C.POINTER(Acc), _dp, _dp, C.c_int]
             _lib = L
@@ -199,7 +203,12 @@ def run(r, sensor_radius: float) -> Run:
     out.sigma = float(r.sigma)
     out.mala_step = float(r.mala_step)
     ke = float(r.kappa_end)
-    out.kappa_end = ke if ke > 0 else (sensor_radius / float(r.sigma)) ** 2
+    if ke > 0:
+        out.kappa_end = ke
+    elif int(r.within) == 2:
+        out.kappa_end = 1.0 / float(r.sigma) ** 2  # tree moves: sigma is dimensionless
+    else:
+        out.kappa_end = (sensor_radius / float(r.sigma)) ** 2
     out.burn_in = int(r.burn_in)
     out.thin_bridge = int(r.thin_bridge)
     out.gradients = int(bool(r.gradients))
@@ -367,6 +376,39 @@ def ymap_logratio(m: Medium, s: Source, d0: Sensor, d1: Sensor, T: YMap, side: i
     f = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 3)
     return lib().or_ymap_logratio(C.byref(m), C.byref(s), C.byref(d0), C.byref(d1), C.byref(T), int(side), len(f),
                                   _ptr(f))
+
+
+def tree_node(m: int, n: int):
+    """(k, l, parent) of interior vertex m in the tree over an n-vertex path."""
+    k, l, p = C.c_int(), C.c_int(), C.c_int()
+    lib().or_tree_node(int(m), int(n), C.byref(k), C.byref(l), C.byref(p))
+    return k.value, l.value, p.value
+
+
+def tree_vref(s: Source, d: Sensor):
+    v = np.zeros(3)
+    lib().or_tree_vref(C.byref(s), C.byref(d), _ptr(v))
+    return v
+
+
+def tree_coords(v_ref, path):
+    """Tree coordinates (zeta, t, phi) of the interior vertices, rows 1..n-2 of
+    an (n, 3) array (rows 0 and n-1 unused), and the log Jacobian."""
+    f = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 3)
+    co = np.zeros_like(f)
+    vr = np.ascontiguousarray(v_ref, dtype=np.float64)
+    lj = lib().or_tree_coords(_ptr(vr), len(f), _ptr(f), _ptr(co))
+    return co, lj
+
+
+def tree_path(v_ref, f0, f_end, coords):
+    """Path (n, 3) from its end points and the interior vertices' tree coordinates."""
+    co = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1, 3)
+    f = np.zeros_like(co)
+    f[0], f[-1] = f0, f_end
+    vr = np.ascontiguousarray(v_ref, dtype=np.float64)
+    lib().or_tree_path(_ptr(vr), len(f), _ptr(co), _ptr(f))
+    return f
 
 
 def yield_ratio_estimate(sums0, sums1):

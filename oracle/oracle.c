@@ -536,6 +536,150 @@ static double log_insert_density(const or_medium* m, const or_run* r, double kap
 }
 
 /* ------------------------------------------------------------------------ */
+/* Tree coordinates (appendix "Path space coordinate system"; the frames     */
+/* follow the inherited-axes rule: a child's eta is its parent's eta turned  */
+/* by the parent's phi, i.e. the normal of the parent's triangle).           */
+/* ------------------------------------------------------------------------ */
+void or_tree_node(int m, int n, int* k, int* l, int* parent) {
+  int kk = 0, ll = n - 1, p = -1;
+  for (;;) {
+    int mid = (kk + ll) / 2;
+    if (mid == m) break;
+    p = mid;
+    if (m < mid) ll = mid; else kk = mid;
+  }
+  *k = kk;
+  *l = ll;
+  *parent = p;
+}
+
+void or_tree_vref(const or_source* s, const or_sensor* d, double v_ref[3]) {
+  double a[3], e2[3];
+  sub3(d->c, s->pos, a);
+  double la = norm3(a);
+  for (int i = 0; i < 3; ++i) a[i] /= la;
+  or_onb(a, v_ref, e2);
+}
+
+static void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Unit axis e, half focal distance gamma and frame (xi, eta) of node m. */
+static void tree_frame(const double v_ref[3], int m, int n, const double* f, double e[3], double* gamma,
+                       double xi[3], double eta[3]) {
+  int k, l, p;
+  or_tree_node(m, n, &k, &l, &p);
+  double r[3];
+  sub3(f + 3 * l, f + 3 * k, r);
+  double ell = norm3(r);
+  *gamma = 0.5 * ell;
+  for (int i = 0; i < 3; ++i) e[i] = r[i] / ell;
+  int have = 0;
+  if (p >= 0) {
+    int kp, lp, pp;
+    or_tree_node(p, n, &kp, &lp, &pp);
+    double ep[3], rho[3], nrm[3];
+    sub3(f + 3 * lp, f + 3 * kp, ep);
+    double lep = norm3(ep);
+    for (int i = 0; i < 3; ++i) {
+      ep[i] /= lep;
+      rho[i] = f[3 * p + i] - 0.5 * (f[3 * kp + i] + f[3 * lp + i]);
+    }
+    cross3(ep, rho, nrm);
+    double nn = norm3(nrm), nr = norm3(rho);
+    if (nn > 1e-9 * nr && nn > 0.0) {
+      /* remove the rounding component along e, then normalise */
+      double de = dot3(nrm, e);
+      for (int i = 0; i < 3; ++i) nrm[i] -= de * e[i];
+      nn = norm3(nrm);
+      for (int i = 0; i < 3; ++i) eta[i] = nrm[i] / nn;
+      cross3(eta, e, xi);
+      have = 1;
+    }
+  }
+  if (!have) {
+    /* root, or a parent on its own axis: xi from v_ref */
+    double dv = dot3(v_ref, e), x[3];
+    for (int i = 0; i < 3; ++i) x[i] = v_ref[i] - dv * e[i];
+    double nx = norm3(x);
+    for (int i = 0; i < 3; ++i) xi[i] = x[i] / nx;
+    cross3(e, xi, eta);
+  }
+}
+
+double or_tree_coords(const double v_ref[3], int n, const double* f, double* coords) {
+  double lj = 0.0;
+  for (int m = 1; m <= n - 2; ++m) {
+    int k, l, p;
+    or_tree_node(m, n, &k, &l, &p);
+    double e[3], xi[3], eta[3], gamma;
+    tree_frame(v_ref, m, n, f, e, &gamma, xi, eta);
+    double a[3], b[3];
+    sub3(f + 3 * k, f + 3 * m, a);
+    sub3(f + 3 * l, f + 3 * m, b);
+    double d1 = norm3(a), d2 = norm3(b);
+    /* 1 +- cos s from |a/d1 +- b/d2|^2 / 2: accurate near s = 0 and s = pi */
+    double sp = 0.0, sm = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      double u = a[i] / d1, v = b[i] / d2;
+      sp += (u + v) * (u + v);
+      sm += (u - v) * (u - v);
+    }
+    double opc = 0.5 * sp, omc = 0.5 * sm;
+    double zeta = 0.5 * log(opc / omc);
+    double t = log(d1 / d2);
+    double rho[3];
+    for (int i = 0; i < 3; ++i) rho[i] = f[3 * m + i] - 0.5 * (f[3 * k + i] + f[3 * l + i]);
+    double phi = atan2(dot3(rho, eta), dot3(rho, xi));
+    coords[3 * m + 0] = zeta;
+    coords[3 * m + 1] = t;
+    coords[3 * m + 2] = phi;
+    double sins = sqrt(opc * omc);  /* sin s = sqrt((1 + cos s)(1 - cos s)) */
+    lj += 3.0 * log(d1 * d2 / (2.0 * gamma)) + 2.0 * log(sins);
+  }
+  return lj;
+}
+
+void or_tree_path(const double v_ref[3], int n, const double* coords, double* f) {
+  /* nodes by depth: a node's foci and parent are shallower */
+  int maxd = 0;
+  for (int m = 1; m <= n - 2; ++m) {
+    int k = 0, l = n - 1, d = 0;
+    for (;;) {
+      int mid = (k + l) / 2;
+      if (mid == m) break;
+      if (m < mid) l = mid; else k = mid;
+      ++d;
+    }
+    if (d > maxd) maxd = d;
+  }
+  for (int depth = 0; depth <= maxd; ++depth) {
+    for (int m = 1; m <= n - 2; ++m) {
+      int k = 0, l = n - 1, d = 0;
+      for (;;) {
+        int mid = (k + l) / 2;
+        if (mid == m) break;
+        if (m < mid) l = mid; else k = mid;
+        ++d;
+      }
+      if (d != depth) continue;
+      double e[3], xi[3], eta[3], gamma;
+      tree_frame(v_ref, m, n, f, e, &gamma, xi, eta);
+      double zeta = coords[3 * m], t = coords[3 * m + 1], phi = coords[3 * m + 2];
+      double cs = tanh(zeta), sn = 1.0 / cosh(zeta);
+      double den = cosh(t) - cs;
+      for (int i = 0; i < 3; ++i) {
+        double mid = 0.5 * (f[3 * k + i] + f[3 * l + i]);
+        f[3 * m + i] = mid + gamma * (e[i] * sinh(t) + (xi[i] * cos(phi) + eta[i] * sin(phi)) * sn) / den;
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Chains                                                                    */
 /* ------------------------------------------------------------------------ */
 #define PURPOSE_STEP_A 0u
@@ -543,6 +687,7 @@ static double log_insert_density(const or_medium* m, const or_run* r, double kap
 #define PURPOSE_INIT 2u
 #define PURPOSE_QREF 3u
 #define PURPOSE_TRACE 4u
+#define PURPOSE_TREE 5u   /* | (vertex << 8): the normals of one tree node */
 
 static void normals3(const uint32_t w[4], double z[3]) {
   double r1 = sqrt(-2.0 * log(or_u01(w[0])));
@@ -603,6 +748,8 @@ typedef struct {
   int c_begin, c_end;
   double kappa_eq;
   uint32_t thr_within, thr_birth;
+  double v_ref[3];   /* tree coordinates: root reference vector */
+  double* coords;    /* tree coordinates: scratch of 3 cap doubles per worker */
 } chain_job;
 
 static double log_sum_tb(const or_medium* m, int n, const double* f, double* tbs) {
@@ -672,7 +819,46 @@ static void* chain_worker(void* arg) {
       int ny = n;
       double logA = NEG_INF, lpy = NEG_INF;
       int proposed = 0;
-      if (u_move < J->thr_within) {
+      if (u_move < J->thr_within && r->within == OR_WITHIN_TREE) {
+        /* the paper's within-dimension move in tree coordinates: the end
+         * vertex takes a vMF step on the sensor, then every interior vertex's
+         * (zeta, t, phi) a normal step of scale sigma / sqrt(n); the path is
+         * rebuilt top-down, and the acceptance carries the coordinates'
+         * Jacobian p(y) J(y) / (p(x) J(x)) */
+        kind = OR_MOVE_INTERIOR;
+        double ljx = or_tree_coords(J->v_ref, n, x, J->coords);
+        double nu[3];
+        sub3(x + 3 * (n - 1), J->d->c, nu);
+        double dn = norm3(nu);
+        for (int i = 0; i < 3; ++i) nu[i] /= dn;
+        double ke = r->kappa_end;
+        double u0 = or_u01(B[0]);
+        double w = 1.0 + log(u0 + (1.0 - u0) * exp(-2.0 * ke)) / ke;
+        double ph = 2.0 * M_PI * or_u01(B[1]);
+        double sw = sqrt(fmax(0.0, 1.0 - w * w));
+        double e1[3], e2[3];
+        or_onb(nu, e1, e2);
+        copy3(x, y);
+        for (int i = 0; i < 3; ++i) {
+          double nn = w * nu[i] + sw * (cos(ph) * e1[i] + sin(ph) * e2[i]);
+          y[3 * (n - 1) + i] = J->d->c[i] + J->d->R * nn;
+        }
+        double step = r->sigma / sqrt((double)n);
+        for (int mm = 1; mm <= n - 2; ++mm) {
+          uint32_t Wn[4];
+          draw_block(r->seed, (uint32_t)t, (uint32_t)(t >> 32), chain, PURPOSE_TREE | ((uint32_t)mm << 8), Wn);
+          double z[3];
+          normals3(Wn, z);
+          for (int q = 0; q < 3; ++q) J->coords[3 * mm + q] += step * z[q];
+        }
+        or_tree_path(J->v_ref, n, J->coords, y);
+        lpy = or_logp(m, J->s, J->d, n, y);
+        if (isfinite(lpy)) {
+          double ljy = or_tree_coords(J->v_ref, n, y, J->coords);
+          logA = lpy + ljy - lpx - ljx;
+        }
+        proposed = 1;
+      } else if (u_move < J->thr_within) {
         /* within-dimension move of one of the n-1 movable vertices */
         int j = 1 + (int)index_draw(A[1], (uint32_t)(n - 1));
         memcpy(y, x, sizeof(double) * 3 * n);
@@ -831,11 +1017,14 @@ int or_run_chains_hist(const or_medium* m, const or_source* s, const or_sensor* 
     J->m = m; J->s = s; J->d = d; J->r = r; J->cap = cap; J->chain_offset = chain_offset;
     J->step0 = step0; J->n_steps = n_steps; J->xyz = xyz; J->n = n; J->acc = acc;
     J->min_margin = min_margin; J->n_hist = n_hist; J->kappa_eq = keq; J->thr_within = thr_w; J->thr_birth = thr_b;
+    or_tree_vref(s, d, J->v_ref);
+    J->coords = (double*)calloc((size_t)3 * (size_t)(cap + 1), sizeof(double));
     J->c_begin = (int)((long)n_chains * i / n_threads);
     J->c_end = (int)((long)n_chains * (i + 1) / n_threads);
     pthread_create(&th[i], NULL, chain_worker, J);
   }
   for (int i = 0; i < n_threads; ++i) pthread_join(th[i], NULL);
+  for (int i = 0; i < n_threads; ++i) free(jobs[i].coords);
   free(jobs);
   free(th);
   return 0;

@@ -28,7 +28,7 @@ enum { OR_HOMOGENEOUS = 0, OR_LAYERED = 1 };
 enum { OR_EMIT_ISOTROPIC = 0, OR_EMIT_VMF = 1 };
 enum { OR_RHO_ONE = 0, OR_RHO_PAPER = 1 };
 enum { OR_INIT_DIRECT = 0, OR_INIT_STRAIGHT = 1, OR_INIT_USER = 2 };
-enum { OR_WITHIN_PERTURB = 0, OR_WITHIN_MALA = 1 };
+enum { OR_WITHIN_PERTURB = 0, OR_WITHIN_MALA = 1, OR_WITHIN_TREE = 2 };
 enum { OR_MOVE_INTERIOR = 0, OR_MOVE_END = 1, OR_MOVE_BIRTH = 2, OR_MOVE_DEATH = 3 };
 
 typedef struct {
@@ -189,6 +189,28 @@ double or_ymap_inverse(const or_ymap* T, int n, const double* y, double* x);
  * other density is zero. */
 double or_ymap_logratio(const or_medium* m, const or_source* s, const or_sensor* d0, const or_sensor* d1,
                         const or_ymap* T, int side, int n, const double* path);
+
+/* ---- tree coordinates (appendix "Path space coordinate system", Fig.
+ *      tree_coords; section "Path proposal distribution") ----
+ * Interior vertex m of an n-vertex path sits in the bispherical system of its
+ * tree foci f_k, f_l (root: f_0, f_{n-1}; m = floor((k + l)/2)) with
+ * coordinates (zeta, t, phi): cos s = tanh zeta, t = ln(d1/d2), and phi the
+ * azimuth of f_m - (f_k + f_l)/2 about e = (f_l - f_k)/|f_l - f_k| in the
+ * node's frame (xi, eta): eta = the unit normal e_p x (f_p - mid_p) of the
+ * parent's triangle (the inherited axes rotated by the parent's phi), xi =
+ * eta x e; the root's xi is v_ref projected onto the plane normal to e. */
+/* Foci (k, l) and parent node (-1 for the root) of interior vertex m. */
+void or_tree_node(int m, int n, int* k, int* l, int* parent);
+/* coords[3 m + (0, 1, 2)] = (zeta, t, phi) of interior vertex m (1..n-2);
+ * returns sum over nodes of log |d f_m / d(zeta, t, phi)| =
+ * 3 log(d1 d2 / (2 gamma)) + 2 log sin s. */
+double or_tree_coords(const double v_ref[3], int n, const double* path, double* coords);
+/* Path from f_0 = path[0..2], f_{n-1} = path[3(n-1)..] and the coordinates of
+ * the interior vertices (top-down); writes path[3..3(n-1)). */
+void or_tree_path(const double v_ref[3], int n, const double* coords, double* path);
+/* The root frame's reference vector of a pair: the first vector of the
+ * orthonormal completion of the unit source -> sensor-centre direction. */
+void or_tree_vref(const or_source* s, const or_sensor* d, double v_ref[3]);
 
 #ifdef __cplusplus
 }

@@ -50,6 +50,7 @@ INIT_USER = 2
 
 WITHIN_PERTURB = 0
 WITHIN_MALA = 1
+WITHIN_TREE = 2
 
 BASE_SEED = 0x181104156
 

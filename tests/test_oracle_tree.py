@@ -1,0 +1,140 @@
+"""Pins of the oracle's tree coordinates and tree-coordinate moves (appendix
+"Path space coordinate system", Fig. tree_coords; section "Path proposal
+distribution").
+
+The coordinate map is pinned by its round trip, by a finite-difference
+determinant against the product of the per-node volume factors
+(d1 d2 / (2 gamma))^3 sin^2 s (the bispherical element in (zeta, t, phi),
+reading Q14), by the tree of Fig. tree_coords, and by the paper's statement
+that turning one vertex turns every vertex that depends on it: a change of
+phi_m rotates the whole subtree of m rigidly about the axis of m's foci.  The
+move built on it is pinned like the Cartesian moves: at vertex cap 3 the
+chains' intensity equals Z2 + Z3 from the independent quadrature, and in a
+well-mixing scene the intensity and the vertex-count split equal the forward
+tracer's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import quadrature as Q
+from paper_1811_04156_gb300 import scenes as S
+
+
+def _path(n, seed, D=3.0, lateral=0.4):
+    xyz, nn = S.random_paths((0.1, -0.2, 0.0), (0.3, 0.1, D), 0.4, 1, n, n, n, seed, lateral=lateral)
+    return xyz[:, 0, :n].T.astype(np.float64)
+
+
+def test_tree_of_the_figure(oracle_lib):
+    """Nine vertices (Fig. tree_coords): f4 in (f0, f8); f2 in (f0, f4) and f6
+    in (f4, f8) below it; f1, f3, f5, f7 at the bottom."""
+    O = oracle_lib
+    expect = {4: (0, 8, -1), 2: (0, 4, 4), 6: (4, 8, 4), 1: (0, 2, 2), 3: (2, 4, 2), 5: (4, 6, 6), 7: (6, 8, 6)}
+    for m, v in expect.items():
+        assert O.tree_node(m, 9) == v
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 12, 33])
+def test_tree_round_trip(oracle_lib, n):
+    O = oracle_lib
+    v = O.tree_vref(O.source(S.Source((0.1, -0.2, 0.0))), O.sensor(S.Sensor((0.3, 0.1, 3.0), 0.4)))
+    for seed in range(5):
+        f = _path(n, 100 * n + seed)
+        co, lj = O.tree_coords(v, f)
+        g = O.tree_path(v, f[0], f[-1], co)
+        assert np.abs(g - f).max() < 1e-10
+        assert np.isfinite(lj)
+
+
+@pytest.mark.parametrize("n", [3, 5, 6, 9])
+def test_tree_jacobian_finite_differences(oracle_lib, n):
+    """log |det d(interior vertices) / d(zeta, t, phi)| = the returned log J."""
+    O = oracle_lib
+    v = O.tree_vref(O.source(S.Source((0.1, -0.2, 0.0))), O.sensor(S.Sensor((0.3, 0.1, 3.0), 0.4)))
+    for seed in range(3):
+        f = _path(n, 7 * n + seed, lateral=0.6)
+        co, lj = O.tree_coords(v, f)
+        dim = 3 * (n - 2)
+        Jm = np.zeros((dim, dim))
+        h = 1e-6
+        for a in range(dim):
+            m, q = 1 + a // 3, a % 3
+            cp, cm = co.copy(), co.copy()
+            cp[m, q] += h
+            cm[m, q] -= h
+            gp = O.tree_path(v, f[0], f[-1], cp)[1:-1].ravel()
+            gm = O.tree_path(v, f[0], f[-1], cm)[1:-1].ravel()
+            Jm[:, a] = (gp - gm) / (2 * h)
+        sign, logdet = np.linalg.slogdet(Jm)
+        assert sign != 0
+        assert abs(logdet - lj) < 1e-5 * max(1.0, abs(lj)), (n, seed, logdet, lj)
+
+
+def _rotate(p, a, b, ang):
+    """Rotate points p about the axis through a and b by ang (Rodrigues)."""
+    k = (b - a) / np.linalg.norm(b - a)
+    v = p - a
+    c, s = math.cos(ang), math.sin(ang)
+    return a + v * c + np.cross(k, v) * s + np.outer(v @ k, k) * (1 - c)
+
+
+def test_turning_one_vertex_turns_its_subtree(oracle_lib):
+    O = oracle_lib
+    v = O.tree_vref(O.source(S.Source((0.1, -0.2, 0.0))), O.sensor(S.Sensor((0.3, 0.1, 3.0), 0.4)))
+    n = 17
+    f = _path(n, 5, lateral=0.5)
+    co, _ = O.tree_coords(v, f)
+    for m in (8, 4, 12, 2):
+        k, l, _ = O.tree_node(m, n)
+        c2 = co.copy()
+        c2[m, 2] += 0.7
+        g = O.tree_path(v, f[0], f[-1], c2)
+        sub = np.arange(k + 1, l)
+        rot = _rotate(f[sub], f[k], f[l], 0.7)
+        assert np.abs(g[sub] - rot).max() < 1e-10, m
+        rest = np.setdiff1d(np.arange(n), sub)
+        assert np.abs(g[rest] - f[rest]).max() < 1e-12
+
+
+def _tree_run(**kw):
+    return S.Run(within=S.WITHIN_TREE, **kw)
+
+
+def test_tree_chain_single_scatter_sector_matches_quadrature(oracle_lib):
+    """Cap 3: I = Z2 + Z3 exactly, with tree moves as the within-dimension moves."""
+    O = oracle_lib
+    sc = S.plain()
+    sc.run = _tree_run(seed=sc.run.seed, burn_in=2000, sigma=0.6)
+    ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, 3)
+    ch.run(60000)
+    m, s, d = O.medium(sc.medium), O.source(sc.sources[0]), O.sensor(sc.sensors[0])
+    I, se, _ = O.direct_estimate(ch.accumulators(), O.z2(m, s, d))
+    ref = Q.z2_closed(1.0, 0.1, 2.2) + Q.z3(1.0, 0.1, 0.5, 5.0, 0.9)
+    assert abs(I - ref) < 3 * se, (I, se, ref)
+    assert se / I < 0.015
+    acc = ch.accumulators()
+    rate = acc["acc"][:, 0].sum() / acc["prop"][:, 0].sum()
+    assert 0.05 < rate < 0.95
+
+
+def test_tree_chain_matches_forward_tracer_all_orders(oracle_lib):
+    """Well-mixing scene: intensity and vertex-count split agree with Algorithm 1."""
+    O = oracle_lib
+    med = S.Medium(lambda_s=1.0, lambda_a=5.0, g=0.0)
+    src, sen = S.Source(), S.Sensor((0.0, 0.0, 1.5), 0.5)
+    run = _tree_run(seed=4321, burn_in=3000, sigma=0.8)
+    cap = 24
+    ch = O.Chains(med, src, sen, run, 96, cap)
+    H = np.zeros((96, cap + 1))
+    ch.run(60000, n_hist=H)
+    m, s, d = O.medium(med), O.source(src), O.sensor(sen)
+    z2 = O.z2(m, s, d)
+    I, se, _ = O.direct_estimate(ch.accumulators(), z2)
+    tr = O.trace(m, s, d, 77, 4_000_000, max_scatter=cap - 2, hist=True)
+    assert abs(I - tr["I"]) < 3 * math.hypot(se, tr["se"]), (I, se, tr["I"], tr["se"])
+    h = H.sum(0)
+    zc = z2 * h / h[2]
+    for k in (3, 4, 5):
+        assert abs(zc[k] / tr["hist"][k - 2] - 1) < 0.04, (k, zc[k], tr["hist"][k - 2])
