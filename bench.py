@@ -83,6 +83,10 @@ def parse():
     p.add_argument("--e1-thin", type=int, default=200, help="steps between observations of B and lengths")
     p.add_argument("--e1-photons", type=int, default=0, help="tracer photons per sensor and b1 (0: no tracer)")
     p.add_argument("--e1-out", default="", help="file for the full result (histograms included)")
+    p.add_argument("--e1-within", default="perturb", choices=["perturb", "tree", "mala"],
+                   help="within-dimension moves: Gaussian vertex steps, the paper's tree-coordinate moves or MALA")
+    p.add_argument("--e1-sigma", type=float, default=0.0,
+                   help="step scale (m for perturb; dimensionless for tree; MALA epsilon); 0 = the scene default")
     p.add_argument("--e1-seed", action="store_true",
                    help="start the chains from weight-thinned tracer paths (exact draws, as the paper seeds its "
                         "chains) instead of straight jittered paths")
@@ -553,6 +557,13 @@ def e1_experiment(args):
     results = []
     for b1 in [float(x) for x in args.e1_b1.split(",")]:
         sc = S.e1(b1, n_chains=args.e1_chains, n_steps=args.e1_steps)
+        sc.run.within = {"perturb": S.WITHIN_PERTURB, "tree": S.WITHIN_TREE, "mala": S.WITHIN_MALA}[args.e1_within]
+        if args.e1_within == "tree":
+            sc.run.sigma = args.e1_sigma or 0.3
+        elif args.e1_within == "mala":
+            sc.run.mala_step = args.e1_sigma or 0.5
+        elif args.e1_sigma:
+            sc.run.sigma = args.e1_sigma
         medium = api.Medium(ctx, sc.medium)
         geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
         ch = api.Chains(ctx, medium, geom, sc.run)
@@ -591,6 +602,7 @@ def e1_experiment(args):
                "length_hist": {"lo": lo, "hi": hi, "bins": nb, "sensor0": (h[0] / max(h[0].sum(), 1)).tolist(),
                                "sensor1": (h[1] / max(h[1].sum(), 1)).tolist()},
                "init": "tracer seeds" if args.e1_seed else "straight, 30 interior vertices, N(0, 0.5 m) jitter",
+               "within": args.e1_within, "sigma": sc.run.sigma, "mala_step": sc.run.mala_step,
                "seed_seconds": seed_s, "seed_photons": seed_photons, "paper": E1_PAPER.get(b1)}
         if args.e1_photons > 0:
             cap = sc.pairs[0].cap
@@ -609,7 +621,8 @@ def e1_experiment(args):
                              "length_hist": {"sensor0": (th[0] / max(th[0].sum(), 1e-300)).tolist(),
                                              "sensor1": (th[1] / max(th[1].sum(), 1e-300)).tolist()}}
         results.append(row)
-        brief = {k: row[k] for k in ("b1", "B", "B_se", "rhat", "gpu_seconds", "proposals_per_s", "seed_seconds")}
+        brief = {k: row[k] for k in ("b1", "within", "B", "B_se", "rhat", "accept", "mean_n", "gpu_seconds",
+                                     "proposals_per_s", "seed_seconds")}
         if "tracer" in row:
             brief["tracer_B"] = (row["tracer"]["B"], row["tracer"]["B_se"], row["tracer"]["hits"],
                                  row["tracer"]["seconds"])

@@ -68,6 +68,7 @@ extern "C" {
 
 #define PMC_WITHIN_PERTURB 0
 #define PMC_WITHIN_MALA 1
+#define PMC_WITHIN_TREE 2
 
 #define PMC_FLAG_GRADIENTS 1   /* accumulate score terms for pmc_grad_estimator */
 #define PMC_FLAG_NO_GRAPH 2    /* launch kernels directly instead of replaying a CUDA graph */
@@ -137,6 +138,17 @@ typedef struct {
  * the end vertex takes a vMF step of concentration kappa_end on the sensor
  * (0 -> (R/sigma)^2), an interior vertex a Gaussian step of scale sigma
  * (PMC_WITHIN_PERTURB) or a MALA step of size mala_step (PMC_WITHIN_MALA).
+ * PMC_WITHIN_TREE instead moves the whole path in the paper's tree
+ * coordinates (section "Path proposal distribution"; appendix "Path space
+ * coordinate system"): interior vertex m = (k + l)/2 sits in the bispherical
+ * system of its tree foci f_k, f_l (root: f_0, f_{n-1}) with coordinates
+ * zeta = atanh(cos s), t = ln(d1/d2) and phi about the foci axis, measured
+ * from the normal of the parent's triangle (inherited axes); each proposal
+ * takes a vMF step of the end vertex (kappa_end; 0 -> 1/sigma^2), a normal
+ * step of scale sigma/sqrt(n) (sigma dimensionless) in every node's (zeta, t,
+ * phi), rebuilds the path top-down and accepts with
+ * p(x') J(x') / (p(x) J(x)), J = prod over nodes (d1 d2 / (2 gamma))^3 sin^2 s.
+ * Tree moves need the whole vertex cap in shared memory (smem_window 0).
  * Births insert a vertex into a segment chosen with probability
  * tau_b(k)/sum tau_b, placed by bispherical coordinates; deaths remove an
  * interior vertex chosen uniformly (appendix, jump proposal; dimension
@@ -145,10 +157,10 @@ typedef struct {
 typedef struct {
   uint64_t seed;                   /* Philox4x32-10 key */
   double p_within, p_birth, p_death;
-  int within;                      /* PMC_WITHIN_PERTURB or PMC_WITHIN_MALA */
-  double sigma;                    /* Gaussian step (m) */
+  int within;                      /* PMC_WITHIN_PERTURB, PMC_WITHIN_MALA or PMC_WITHIN_TREE */
+  double sigma;                    /* Gaussian step (m); tree moves: dimensionless scale */
   double mala_step;                /* MALA epsilon (m) */
-  double kappa_end;                /* vMF concentration of end moves; 0 -> (R/sigma)^2 */
+  double kappa_end;                /* vMF concentration of end moves; 0 -> (R/sigma)^2 (tree: 1/sigma^2) */
   uint64_t burn_in;
   uint32_t thin_bridge;            /* reference-density bridge terms every k steps; 0 = off */
   int init;                        /* PMC_INIT_DIRECT, PMC_INIT_STRAIGHT or PMC_INIT_USER */

@@ -185,7 +185,7 @@ struct pmc_chains_s {
   cudaStream_t capture_stream = nullptr;
   std::vector<ChainClass> classes;
   std::map<unsigned long long, cudaGraphExec_t> graphs;
-  bool general = false;            // chain kernel instantiation
+  int general = 0;                 // chain kernel: 0 lean, 1 general, 2 general with tree moves
   bool grad = false;               // keep d log sigma / dg per vertex
   bool autotune = false;           // warps per block chosen by timing
   int init_kind = 0, init_k = 0;
@@ -549,7 +549,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
       float best_ms = 1e30f;
       std::vector<int> windows = {full};
       for (int w : {128, 256, 512})
-        if (w < full) windows.push_back(w);
+        if (w < full && ch->general != 2) windows.push_back(w);  // tree moves keep the whole cap
       for (int win : windows) {
         for (int wpb : {1, 2, 4}) {
           const bool spill = win < full;
@@ -622,7 +622,8 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   if (pd > 0 && !(pb > 0)) return fail(PMC_ERR_INVALID, "deaths need births (reversibility)");
   if (!finite_pos(r->sigma)) return fail(PMC_ERR_INVALID, "sigma must be > 0");
   if (r->within == PMC_WITHIN_MALA && !finite_pos(r->mala_step)) return fail(PMC_ERR_INVALID, "mala_step must be > 0");
-  if (r->within != PMC_WITHIN_PERTURB && r->within != PMC_WITHIN_MALA) return fail(PMC_ERR_INVALID, "bad within kind");
+  if (r->within != PMC_WITHIN_PERTURB && r->within != PMC_WITHIN_MALA && r->within != PMC_WITHIN_TREE)
+    return fail(PMC_ERR_INVALID, "bad within kind");
   if (r->init != PMC_INIT_DIRECT && r->init != PMC_INIT_STRAIGHT && r->init != PMC_INIT_USER)
     return fail(PMC_ERR_INVALID, "bad init kind");
   if (r->init == PMC_INIT_STRAIGHT && (r->init_k < 0 || !(r->init_jitter >= 0)))
@@ -658,7 +659,9 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
 
   ch->h_pairs = geom->pairs;
   for (auto& d : ch->h_pairs) {
-    const double ke = r->kappa_end > 0 ? r->kappa_end : (d.R / r->sigma) * (d.R / r->sigma);
+    // tree moves: sigma is dimensionless, the default end step has angular scale sigma
+    const double ke = r->kappa_end > 0 ? r->kappa_end
+                      : (r->within == PMC_WITHIN_TREE ? 1.0 / (r->sigma * r->sigma) : (d.R / r->sigma) * (d.R / r->sigma));
     d.kappa_end = static_cast<float>(ke);
     d.exp_m2ke = static_cast<float>(std::exp(-2.0 * ke));
   }
@@ -666,7 +669,8 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   ch->general = med->d.kind != PMC_HOMOGENEOUS || med->d.f_sl > 0.f || r->within == PMC_WITHIN_MALA ||
                 std::any_of(ch->h_pairs.begin(), ch->h_pairs.end(),
                             [](const DPair& d) { return d.emission != PMC_EMIT_ISOTROPIC || d.rho != PMC_RHO_ONE; });
-  const int n_arrays = chain_arrays(ch->general, ch->grad);
+  if (r->within == PMC_WITHIN_TREE) ch->general = 2;
+  const int n_arrays = chain_arrays(ch->general > 0, ch->grad);
   const int T = ch->total;
   ch->h_base.resize(T);
   ch->h_pair_of.resize(T);
@@ -702,6 +706,8 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     cl.smem_cap = (maxcap + 31) / 32 * 32;
     cl.max_cap = maxcap;
     cl.spill = false;
+    if (r->smem_window > 0 && r->smem_window < cl.smem_cap && ch->general == 2)
+      return fail(PMC_ERR_INVALID, "tree moves need the whole vertex cap in shared memory (smem_window)");
     if (r->smem_window > 0 && r->smem_window < cl.smem_cap) {
       cl.smem_cap = r->smem_window;
       cl.spill = true;
@@ -1009,7 +1015,7 @@ int pmc_chains_launch_info(pmc_chains_t ch, int* out, int max_rows, int* n_class
     row[2] = cl.hi;
     row[3] = cl.warps_per_block;
     row[4] = cl.grid;
-    row[5] = ch->general ? 1 : 0;
+    row[5] = ch->general;
   }
   return PMC_OK;
 }

@@ -23,6 +23,11 @@
 // Estimators: observables (n, length L, sum of d log sigma/dg) change only on
 // acceptance, so each state's values are added once with its dwell time into
 // FP32 partials that are flushed into lane-distributed FP64 accumulators.
+// kTree adds the paper's within-dimension move in tree coordinates (section
+// "Path proposal distribution"; appendix "Path space coordinate system"): the
+// whole path is re-expressed node by node in recursive bispherical systems,
+// every node's (zeta, t, phi) takes a normal step, and the new path is built
+// level by level into three extra shared arrays.
 #include <climits>
 
 #include "pmc_internal.h"
@@ -347,6 +352,160 @@ __device__ int select_segment(const WP& w, int nseg, float u, float& total, int 
   return __shfl_sync(kFull, k, owner);
 }
 
+// ---------------------------------------------------------------------------
+// Tree coordinates.  Interior vertex m = (k + l)/2 sits in the bispherical
+// system of its foci f_k, f_l (root: f_0, f_{n-1}) with coordinates
+// zeta = atanh(cos s), t = ln(d1/d2) and the azimuth phi about
+// e = (f_l - f_k)/|f_l - f_k| in the frame (xi, eta): eta is the unit normal
+// e_p x (f_p - mid_p) of the parent's triangle (the parent's axes turned by
+// its phi), xi = eta x e; the root's xi is vref projected normal to e.  The
+// volume element is (d1 d2 / (2 gamma))^3 sin^2 s per node.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Interval (k, l) of node j at depth d (binary descent on the bits of j, most
+// significant first) and its parent's interval (kp = -1 at the root); false
+// when the interval holds no vertex.
+__device__ __forceinline__ bool tree_interval(int n, int d, int j, int& k, int& l, int& kp, int& lp) {
+  k = 0;
+  l = n - 1;
+  kp = lp = -1;
+  for (int b = d - 1; b >= 0; --b) {
+    if (l - k < 2) return false;
+    const int mid = (k + l) >> 1;
+    kp = k;
+    lp = l;
+    if ((j >> b) & 1) k = mid;
+    else l = mid;
+  }
+  return l - k >= 2;
+}
+
+struct TreeFrame {
+  float3 e, xi, eta, mid;
+  float gamma;
+};
+
+template <class PosF>
+__device__ __forceinline__ TreeFrame tree_frame(PosF pos, int k, int l, int kp, int lp, float3 vref) {
+  TreeFrame F;
+  const float3 A = pos(k), B = pos(l);
+  const float3 r = B - A;
+  const float rr = dot(r, r);
+  const float ir = rsqrtf(rr);
+  F.e = ir * r;
+  F.gamma = 0.5f * rr * ir;
+  F.mid = 0.5f * (A + B);
+  bool have = false;
+  if (kp >= 0) {
+    const int p = (kp + lp) >> 1;
+    const float3 Ap = pos(kp), Bp = pos(lp);
+    const float3 ep = Bp - Ap, rho = pos(p) - 0.5f * (Ap + Bp);
+    float3 nrm = cross3(ep, rho);
+    const float nn2 = dot(nrm, nrm);
+    if (nn2 > 1e-12f * dot(ep, ep) * dot(rho, rho) && nn2 > 0.f) {
+      nrm = nrm - dot(nrm, F.e) * F.e;
+      F.eta = rsqrtf(dot(nrm, nrm)) * nrm;
+      F.xi = cross3(F.eta, F.e);
+      have = true;
+    }
+  }
+  if (!have) {
+    const float3 x = vref - dot(vref, F.e) * F.e;
+    F.xi = rsqrtf(dot(x, x)) * x;
+    F.eta = cross3(F.e, F.xi);
+  }
+  return F;
+}
+
+// One whole-path tree proposal: the end vertex goes to `end`, every node's
+// coordinates step by `step` times its normals; the new path is built level
+// by level into nx/ny/nz.  Returns log of p(x') J(x') / (p(x) J(x)) without
+// log p(x), i.e. log p(x') + log J(x') - log J(x) (-inf if x' has zero density).
+template <bool kGen, class WP>
+__device__ float tree_propose(const DMedium& M, const DPair& S, float zoff, const WP& w, float* nx, float* ny,
+                              float* nz, int n, float3 end, float step, float3 vref, unsigned long long t, int c,
+                              uint32_t key0, uint32_t key1, int lane) {
+  constexpr unsigned kAll = 0xffffffffu;
+  auto opos = [&](int i) { return w.pos(i); };
+  auto npos = [&](int i) { return f3(nx[i], ny[i], nz[i]); };
+  if (lane == 0) {
+    nx[0] = ny[0] = nz[0] = 0.f;
+    nx[n - 1] = end.x;
+    ny[n - 1] = end.y;
+    nz[n - 1] = end.z;
+  }
+  __syncwarp();
+  float lj = 0.f;  // log J(x') - log J(x), lane partials
+  for (int d = 0;; ++d) {
+    bool any = false;
+    for (int j0 = 0; j0 < (1 << d); j0 += 32) {
+      const int j = j0 + lane;
+      int k = 0, l = 0, kp = -1, lp = -1;
+      const bool valid = j < (1 << d) && tree_interval(n, d, j, k, l, kp, lp);
+      any = any || __any_sync(kAll, valid);
+      if (valid) {
+        const int m = (k + l) >> 1;
+        // old coordinates
+        const TreeFrame Fo = tree_frame(opos, k, l, kp, lp, vref);
+        const float3 P = w.pos(m);
+        const float3 a = w.pos(k) - P, b = w.pos(l) - P;
+        const float d1 = sqrtf(dot(a, a)), d2 = sqrtf(dot(b, b));
+        const float3 u = (1.0f / d1) * a, v = (1.0f / d2) * b;
+        const float3 up = u + v, um = u - v;
+        const float opc = 0.5f * dot(up, up), omc = 0.5f * dot(um, um);
+        const float3 rho = P - Fo.mid;
+        float zeta = 0.5f * logf(opc / omc);
+        float tt = logf(d1 / d2);
+        float phi = atan2f(dot(rho, Fo.eta), dot(rho, Fo.xi));
+        lj -= 3.0f * logf(d1 * d2 / (2.0f * Fo.gamma)) + logf(opc * omc);
+        // normal steps (the oracle's draw: Box-Muller on one Philox block)
+        const uint4 rn = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32),
+                                                  static_cast<uint32_t>(c), PUR_TREE | (static_cast<uint32_t>(m) << 8)),
+                                       key0, key1);
+        float s1, c1, s2, c2;
+        const float r1 = sqrtf(-2.0f * logf(u01(rn.x)));
+        sincospif(2.0f * u01(rn.y), &s1, &c1);
+        const float r2 = sqrtf(-2.0f * logf(u01(rn.z)));
+        sincospif(2.0f * u01(rn.w), &s2, &c2);
+        zeta = fmaf(step, r1 * c1, zeta);
+        tt = fmaf(step, r1 * s1, tt);
+        phi = fmaf(step, r2 * c2, phi);
+        // new vertex from the new foci and frame
+        const TreeFrame Fn = tree_frame(npos, k, l, kp, lp, vref);
+        const float ez = expf(zeta), emz = expf(-zeta);
+        const float sn = 2.0f / (ez + emz);                 // 1 / cosh zeta = sin s
+        const float omcs = 2.0f / (1.0f + ez * ez);          // 1 - tanh zeta
+        const float sh = sinhf(0.5f * tt);
+        const float den = fmaf(2.0f * sh, sh, omcs);        // cosh t - cos s
+        float sp, cp;
+        sincosf(phi, &sp, &cp);
+        const float sc = Fn.gamma / den;
+        const float3 fnew = Fn.mid + sc * (sinhf(tt) * Fn.e + sn * (cp * Fn.xi + sp * Fn.eta));
+        nx[m] = fnew.x;
+        ny[m] = fnew.y;
+        nz[m] = fnew.z;
+        lj += 3.0f * logf(sc) + 2.0f * logf(sn);
+      }
+    }
+    __syncwarp();
+    if (!any) break;
+  }
+  // log p of the new path
+  float lp = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    const float3 Pc = npos(i);
+    const float3 Pp = (i >= 1) ? npos(i - 1) : Pc;
+    const float3 Pn = (i <= n - 2) ? npos(i + 1) : Pc;
+    float vt, gt, seg, tb, len;
+    vertex_and_segment<kGen>(M, S, zoff, Pp, Pc, Pn, i, n, vt, gt, seg, tb, len);
+    lp += vt + ((i <= n - 2) ? seg : 0.f);
+  }
+  return warp_sum(lp) + warp_sum(lj);
+}
+
 struct Accum {
   unsigned long long pn2, pn;  // integer partials of the current flush interval
   float pL, pL2, pG;           // FP32 partials of the current flush interval
@@ -394,20 +553,25 @@ __device__ __forceinline__ void flush64(Accum& a, int lane) {
 //   within: lo.z, lo.w, hi.x = standard normals, hi.y = vMF cosine,
 //           hi.z, hi.w = cos, sin of the vMF azimuth
 //   birth:  lo.z = u for cos s, lo.w = sinh t, hi.x = cosh t, hi.y, hi.z = cos, sin of phi
-template <bool kGen, bool kGrad, bool kSpill>
+template <bool kGen, bool kGrad, bool kSpill, bool kTree>
 __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainParams P) {
   using WP = WarpPath<kGen, kGrad, kSpill>;
+  static_assert(!kTree || (kGen && !kSpill), "tree moves use the general kernel with the whole cap in shared memory");
+  constexpr int kArraysAll = WP::kArrays + (kTree ? 3 : 0);
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int cap_s = P.smem_cap;
-  const size_t per_warp = static_cast<size_t>(WP::kArrays) * cap_s + 32 * kRngWords + kPairWords;
+  const size_t per_warp = static_cast<size_t>(kArraysAll) * cap_s + 32 * kRngWords + kPairWords;
   WP w;
   w.sm = smem + static_cast<size_t>(wib) * per_warp;
   w.S = cap_s;
   w.b = P.M.b;
-  uint4* rng = reinterpret_cast<uint4*>(w.sm + static_cast<size_t>(WP::kArrays) * cap_s);  // [32][2] uint4
+  float* tnx = w.sm + static_cast<size_t>(WP::kArrays) * cap_s;  // tree moves: the proposed path
+  float* tny = tnx + cap_s;
+  float* tnz = tny + cap_s;
+  uint4* rng = reinterpret_cast<uint4*>(w.sm + static_cast<size_t>(kArraysAll) * cap_s);  // [32][2] uint4
   DPair* spair = reinterpret_cast<DPair*>(rng + 64);
   const DMedium& M = P.M;
   const DRun& R = P.R;
@@ -466,6 +630,14 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
     A.my = (lane < ACC_WORDS) ? P.acc[static_cast<size_t>(c) * ACC_WORDS + lane] : 0.0;
 
     const float3 cS = f3(S.c[0], S.c[1], S.c[2]);
+    float3 vref = f3(1.f, 0.f, 0.f);
+    if constexpr (kTree) {
+      // root frame reference: first vector of the orthonormal completion of
+      // the unit source -> sensor-centre direction
+      const float3 cc = cS + f3(S.c_lo[0], S.c_lo[1], S.c_lo[2]);
+      float3 e2;
+      onb(rsqrtf(dot(cc, cc)) * cc, vref, e2);
+    }
     unsigned long long done = 0;
     bool aborted = false;
     for (unsigned long long s0 = 0; s0 < P.n_steps; s0 += 32) {
@@ -528,6 +700,38 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
         float3 fnew = f3(0.f, 0.f, 0.f);
         float extra = 0.f;
         float3 gx_mala = f3(0.f, 0.f, 0.f);
+        if constexpr (kTree) {
+          if (mtype == 0u) {
+            // whole-path move in tree coordinates; a rejected proposal leaves
+            // the path and its caches untouched
+            const float3 nu = sensor_normal(S, w.pos(n - 1));
+            float3 e1, e2;
+            onb(nu, e1, e2);
+            const float wv = __uint_as_float(hi.y);
+            const float sw = m_sqrt<true>(fmaxf(0.f, 1.0f - wv * wv));
+            const float3 nn = wv * nu + sw * (__uint_as_float(hi.z) * e1 + __uint_as_float(hi.w) * e2);
+            const float3 end = cS + (f3(S.c_lo[0], S.c_lo[1], S.c_lo[2]) + S.R * nn);
+            const float step = R.sigma * rsqrtf(static_cast<float>(n));
+            const float gain = tree_propose<kGen>(M, S, zoff, w, tnx, tny, tnz, n, end, step, vref, t, c, key0, key1,
+                                                  lane);
+            float lpo = 0.f;
+            for (int q = lane; q < n; q += 32) lpo += w.vt(q) + ((q <= n - 2) ? w.seg(q) : 0.f);
+            lpo = warp_sum(lpo);
+            if (logu < gain - lpo) {
+              A.acc_i++;
+              close_state(A, t, R.burn_in, n, L, G);
+              for (int q = lane; q < n; q += 32) w.set_pos(q, f3(tnx[q], tny[q], tnz[q]));
+              __syncwarp();
+              refresh_caches<kGen>(M, S, zoff, w, n, lane);
+              const Sums s3 = path_sums(w, n, lane);
+              L = s3.L;
+              G = s3.G;
+              if (A.nflush >= kFlushAccepts) flush64(A, lane);
+            }
+            __syncwarp();
+            continue;
+          }
+        }
         if (mtype == 0u) {
           const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 1)) >> 23);
           jj = j;
@@ -809,7 +1013,7 @@ __global__ void init_kernel(const InitParams p) {
 // The dynamic shared-memory limit is a property of the kernel, shared by every
 // launch: set it once to the device's per-block maximum so that classes with
 // different vertex caps can all launch.
-template <bool kGen, bool kGrad, bool kSpill>
+template <bool kGen, bool kGrad, bool kSpill, bool kTree>
 cudaError_t set_attributes() {
   static int done[64] = {};
   int dev = 0;
@@ -819,65 +1023,78 @@ cudaError_t set_attributes() {
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad, kSpill>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad, kSpill, kTree>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad, kSpill>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad, kSpill, kTree>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           100);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
   return e;
 }
 
-template <bool kGen, bool kGrad, bool kSpill>
+template <bool kGen, bool kGrad, bool kSpill, bool kTree>
 cudaError_t occupancy_of(int warps_per_block, size_t sm, int* blocks_per_sm) {
-  cudaError_t e = set_attributes<kGen, kGrad, kSpill>();
+  cudaError_t e = set_attributes<kGen, kGrad, kSpill, kTree>();
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<kGen, kGrad, kSpill>,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<kGen, kGrad, kSpill, kTree>,
                                                        warps_per_block * 32, sm);
 }
 
-template <bool kGen, bool kGrad, bool kSpill>
+template <bool kGen, bool kGrad, bool kSpill, bool kTree>
 void launch_one(const ChainParams& p, int grid, int warps_per_block, size_t sm, cudaStream_t s) {
-  chain_kernel<kGen, kGrad, kSpill><<<grid, warps_per_block * 32, sm, s>>>(p);
+  chain_kernel<kGen, kGrad, kSpill, kTree><<<grid, warps_per_block * 32, sm, s>>>(p);
+}
+
+// Instantiation key: lean / general (with or without gradient caches and
+// spill) and general with tree moves (never spilled).
+int kernel_key(int kind, bool grad, bool spill) {
+  if (kind == 2) return 8 + (grad ? 1 : 0);
+  return (kind == 1 ? 4 : 0) + (grad ? 2 : 0) + (spill ? 1 : 0);
 }
 
 }  // namespace
 
 int chain_arrays(bool general, bool grad) { return 6 + (general ? 1 : 0) + (grad ? 1 : 0); }
 
-size_t chain_smem_bytes(int smem_cap, int warps_per_block, bool general, bool grad) {
-  const size_t arrays = static_cast<size_t>(chain_arrays(general, grad));
+size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad) {
+  const size_t arrays = static_cast<size_t>(chain_arrays(kind > 0, grad) + (kind == 2 ? 3 : 0));
   return static_cast<size_t>(warps_per_block) *
          (arrays * static_cast<size_t>(smem_cap) + 32u * kRngWords + kPairWords) * sizeof(float);
 }
 
-cudaError_t chain_occupancy(bool general, bool grad, bool spill, int warps_per_block, int smem_cap,
+cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block, int smem_cap,
                             int* blocks_per_sm) {
-  const size_t sm = chain_smem_bytes(smem_cap, warps_per_block, general, grad);
-  const int key = (general ? 4 : 0) + (grad ? 2 : 0) + (spill ? 1 : 0);
-  switch (key) {
-    case 0: return occupancy_of<false, false, false>(warps_per_block, sm, blocks_per_sm);
-    case 1: return occupancy_of<false, false, true>(warps_per_block, sm, blocks_per_sm);
-    case 2: return occupancy_of<false, true, false>(warps_per_block, sm, blocks_per_sm);
-    case 3: return occupancy_of<false, true, true>(warps_per_block, sm, blocks_per_sm);
-    case 4: return occupancy_of<true, false, false>(warps_per_block, sm, blocks_per_sm);
-    case 5: return occupancy_of<true, false, true>(warps_per_block, sm, blocks_per_sm);
-    case 6: return occupancy_of<true, true, false>(warps_per_block, sm, blocks_per_sm);
-    default: return occupancy_of<true, true, true>(warps_per_block, sm, blocks_per_sm);
+  if (kind == 2 && spill) return cudaErrorInvalidValue;
+  const size_t sm = chain_smem_bytes(smem_cap, warps_per_block, kind, grad);
+  switch (kernel_key(kind, grad, spill)) {
+    case 0: return occupancy_of<false, false, false, false>(warps_per_block, sm, blocks_per_sm);
+    case 1: return occupancy_of<false, false, true, false>(warps_per_block, sm, blocks_per_sm);
+    case 2: return occupancy_of<false, true, false, false>(warps_per_block, sm, blocks_per_sm);
+    case 3: return occupancy_of<false, true, true, false>(warps_per_block, sm, blocks_per_sm);
+    case 4: return occupancy_of<true, false, false, false>(warps_per_block, sm, blocks_per_sm);
+    case 5: return occupancy_of<true, false, true, false>(warps_per_block, sm, blocks_per_sm);
+    case 6: return occupancy_of<true, true, false, false>(warps_per_block, sm, blocks_per_sm);
+    case 7: return occupancy_of<true, true, true, false>(warps_per_block, sm, blocks_per_sm);
+    case 8: return occupancy_of<true, false, false, true>(warps_per_block, sm, blocks_per_sm);
+    default: return occupancy_of<true, true, false, true>(warps_per_block, sm, blocks_per_sm);
   }
 }
 
-cudaError_t launch_chain(const ChainParams& p, bool general, bool grad, bool spill, int grid, int warps_per_block,
+cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s) {
-  const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block, general, grad);
-  const int key = (general ? 4 : 0) + (grad ? 2 : 0) + (spill ? 1 : 0);
-  switch (key) {
-    case 0: launch_one<false, false, false>(p, grid, warps_per_block, sm, s); break;
-    case 1: launch_one<false, false, true>(p, grid, warps_per_block, sm, s); break;
-    case 2: launch_one<false, true, false>(p, grid, warps_per_block, sm, s); break;
-    case 3: launch_one<false, true, true>(p, grid, warps_per_block, sm, s); break;
-    case 4: launch_one<true, false, false>(p, grid, warps_per_block, sm, s); break;
-    case 5: launch_one<true, false, true>(p, grid, warps_per_block, sm, s); break;
-    case 6: launch_one<true, true, false>(p, grid, warps_per_block, sm, s); break;
-    default: launch_one<true, true, true>(p, grid, warps_per_block, sm, s); break;
+  if (kind == 2 && spill) return cudaErrorInvalidValue;
+  const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block, kind, grad);
+  switch (kernel_key(kind, grad, spill)) {
+    case 0: launch_one<false, false, false, false>(p, grid, warps_per_block, sm, s); break;
+    case 1: launch_one<false, false, true, false>(p, grid, warps_per_block, sm, s); break;
+    case 2: launch_one<false, true, false, false>(p, grid, warps_per_block, sm, s); break;
+    case 3: launch_one<false, true, true, false>(p, grid, warps_per_block, sm, s); break;
+    case 4: launch_one<true, false, false, false>(p, grid, warps_per_block, sm, s); break;
+    case 5: launch_one<true, false, true, false>(p, grid, warps_per_block, sm, s); break;
+    case 6: launch_one<true, true, false, false>(p, grid, warps_per_block, sm, s); break;
+    case 7: launch_one<true, true, true, false>(p, grid, warps_per_block, sm, s); break;
+    case 8: launch_one<true, false, false, true>(p, grid, warps_per_block, sm, s); break;
+    default: launch_one<true, true, false, true>(p, grid, warps_per_block, sm, s); break;
   }
   return cudaGetLastError();
 }

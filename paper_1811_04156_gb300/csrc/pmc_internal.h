@@ -33,7 +33,8 @@ static_assert(ACC_WORDS == PMC_ACC_WORDS, "accumulator layout");
 enum StatusBits { ST_NONFINITE = 1, ST_ABORTED = 2, ST_BAD_N = 4 };
 
 // Random-number purposes (fourth Philox counter word).
-enum Purpose : uint32_t { PUR_STEP_A = 0, PUR_STEP_B = 1, PUR_INIT = 2, PUR_QREF = 3, PUR_TRACE = 4 };
+// PUR_TREE is or-ed with (vertex << 8): the normals of one tree node.
+enum Purpose : uint32_t { PUR_STEP_A = 0, PUR_STEP_B = 1, PUR_INIT = 2, PUR_QREF = 3, PUR_TRACE = 4, PUR_TREE = 5 };
 
 struct ChainParams {
   DMedium M;
@@ -63,11 +64,13 @@ struct ChainParams {
 // smaller than the chains' caps, entries beyond it living in the chain's
 // global block.  The global block of a chain holds chain_arrays() arrays of
 // cap floats (x, y, z first).
+// `kind`: 0 the lean kernel, 1 the general one, 2 the general one with tree
+// moves (3 more shared arrays per warp, no spill).
 int chain_arrays(bool general, bool grad);
-cudaError_t launch_chain(const ChainParams& p, bool general, bool grad, bool spill, int grid, int warps_per_block,
+cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s);
-size_t chain_smem_bytes(int smem_cap, int warps_per_block, bool general, bool grad);
-cudaError_t chain_occupancy(bool general, bool grad, bool spill, int warps_per_block, int smem_cap,
+size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad);
+cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block, int smem_cap,
                             int* blocks_per_sm);
 
 struct InitParams {

@@ -1,0 +1,107 @@
+"""GPU parity of the tree-coordinate within-dimension move (section "Path
+proposal distribution"; appendix "Path space coordinate system") with the
+FP64 oracle: the same Philox stream on both sides replays the oracle's
+trajectories, and the chains' intensity equals the independent quadrature
+(vertex cap 3) and the forward tracer (a well-mixing scene).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import quadrature as Q
+from paper_1811_04156_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1811_04156_gb300 import build
+    build.build()
+    from paper_1811_04156_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    return api.Context(0)
+
+
+def _tree_scene(name):
+    if name == "general":
+        sc = S.general_small(n_chains=64, n_steps=300)
+    else:
+        sc = S.plain(n_chains=64, n_steps=300)
+    sc.run.within = S.WITHIN_TREE
+    sc.run.sigma = 0.5
+    sc.run.init = S.INIT_STRAIGHT
+    sc.run.init_k = 6
+    sc.run.init_jitter = 0.02
+    return sc
+
+
+@pytest.mark.parametrize("name", ["plain", "general"])
+def test_tree_trajectory_replay(api, ctx, oracle_lib, name):
+    """Every chain whose accept decisions never came within 1e-3 of the
+    threshold ends in the oracle's state (vertex count and positions)."""
+    O = oracle_lib
+    sc = _tree_scene(name)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    assert ch.launch_info()[0]["general"] == 2
+    ch.run_steps(sc.run.n_steps)
+    xyz, n, st = ch.read_states()
+    oc = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, sc.pairs[0].cap)
+    margin = oc.run(sc.run.n_steps, margins=True)
+    assert np.all(st == sc.run.n_steps)
+    clean = margin > 1e-3
+    assert clean.sum() >= 24
+    for c in np.nonzero(clean)[0]:
+        assert n[c] == oc.n[c], (c, n[c], oc.n[c])
+        k = int(n[c])
+        assert np.allclose(xyz[c, :, :k].T, oc.xyz[c, :k], atol=2e-4), (c, np.abs(xyz[c, :, :k].T - oc.xyz[c, :k]).max())
+    acc = ch.read_accumulators()
+    oacc = oc.accumulators()
+    for c in np.nonzero(clean)[0]:
+        assert np.array_equal(acc[c, 8:12], oacc["prop"][c])
+        assert np.array_equal(acc[c, 12:16], oacc["acc"][c])
+    # tree proposals are accepted at a useful rate
+    assert 0.05 < acc[:, 12].sum() / acc[:, 8].sum() < 0.95
+
+
+def test_tree_single_scatter_sector(api, ctx):
+    """Cap 3 with tree moves: I = Z2 + Z3 by independent quadrature."""
+    sc = S.plain(n_chains=4096, n_steps=20000, cap=3)
+    sc.run.within = S.WITHIN_TREE
+    sc.run.sigma = 0.6
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    ch.run_steps(20000)
+    e = ch.read_estimator()[0]
+    ref = Q.z2_closed(1.0, 0.1, 2.2) + Q.z3(1.0, 0.1, 0.5, 5.0, 0.9)
+    assert abs(e["intensity"] - ref) < 3 * e["std_err"], (e["intensity"], e["std_err"], ref)
+    assert e["rel_err"] < 0.005
+
+
+def test_tree_chains_match_tracer(api, ctx):
+    """Well-mixing scene (isotropic scattering, large close sensor, cap 24):
+    the intensity of tree-move chains equals the GPU tracer's (truncated at
+    the same number of scatterings)."""
+    med = S.Medium(lambda_s=1.0, lambda_a=5.0, g=0.0)
+    src, sen = S.Source(), S.Sensor((0.0, 0.0, 1.5), 0.5)
+    cap = 24
+    run = S.Run(seed=99, n_steps=30000, burn_in=3000, within=S.WITHIN_TREE, sigma=0.8)
+    medium = api.Medium(ctx, med)
+    geom = api.Geometry(ctx, [src], [sen], [S.Pair(0, 0, 4096, cap)])
+    ch = api.Chains(ctx, medium, geom, run)
+    ch.run_steps(run.n_steps)
+    e = ch.read_estimator()[0]
+    tr = api.trace(ctx, medium, geom, 0, 7, 400_000_000, max_scatter=cap - 2)
+    assert abs(e["intensity"] - tr["I"]) < 3 * math.hypot(e["std_err"], tr["se"]), (e, tr)
+    assert e["rel_err"] < 0.01
