@@ -420,10 +420,29 @@ __device__ __forceinline__ TreeFrame tree_frame(PosF pos, int k, int l, int kp, 
   return F;
 }
 
+// Foci (k, l) of interior vertex m and its parent's foci (kp = -1 at the root).
+__device__ __forceinline__ void tree_node_of(int m, int n, int& k, int& l, int& kp, int& lp) {
+  k = 0;
+  l = n - 1;
+  kp = lp = -1;
+  for (;;) {
+    const int mid = (k + l) >> 1;
+    if (mid == m) return;
+    kp = k;
+    lp = l;
+    if (m < mid) l = mid;
+    else k = mid;
+  }
+}
+
 // One whole-path tree proposal: the end vertex goes to `end`, every node's
 // coordinates step by `step` times its normals; the new path is built level
-// by level into nx/ny/nz.  Returns log of p(x') J(x') / (p(x) J(x)) without
-// log p(x), i.e. log p(x') + log J(x') - log J(x) (-inf if x' has zero density).
+// by level into nx/ny/nz.  Returns log p(x') + log J(x') - log J(x)
+// (-inf if x' has zero density).  Pass 1 (all lanes over all nodes): the old
+// coordinates and their Jacobian, the normal steps, and the new coordinates
+// parked in nx/ny/nz[m]; pass 2 (level by level): each node reads its new
+// coordinates and overwrites them with its new position, whose frame comes
+// from the already-built shallower nodes.
 template <bool kGen, class WP>
 __device__ float tree_propose(const DMedium& M, const DPair& S, float zoff, const WP& w, float* nx, float* ny,
                               float* nz, int n, float3 end, float step, float3 vref, unsigned long long t, int c,
@@ -431,6 +450,32 @@ __device__ float tree_propose(const DMedium& M, const DPair& S, float zoff, cons
   constexpr unsigned kAll = 0xffffffffu;
   auto opos = [&](int i) { return w.pos(i); };
   auto npos = [&](int i) { return f3(nx[i], ny[i], nz[i]); };
+  float lj = 0.f;  // log J(x') - log J(x), lane partials
+  for (int m = 1 + lane; m <= n - 2; m += 32) {
+    int k, l, kp, lp;
+    tree_node_of(m, n, k, l, kp, lp);
+    const TreeFrame Fo = tree_frame(opos, k, l, kp, lp, vref);
+    const float3 P = w.pos(m);
+    const float3 a = w.pos(k) - P, b = w.pos(l) - P;
+    const float d1 = sqrtf(dot(a, a)), d2 = sqrtf(dot(b, b));
+    const float3 u = (1.0f / d1) * a, v = (1.0f / d2) * b;
+    const float3 up = u + v, um = u - v;
+    const float opc = 0.5f * dot(up, up), omc = 0.5f * dot(um, um);
+    const float3 rho = P - Fo.mid;
+    lj -= 3.0f * logf(d1 * d2 / (2.0f * Fo.gamma)) + logf(opc * omc);
+    // normal steps (the oracle's draw: Box-Muller on one Philox block)
+    const uint4 rn = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32),
+                                              static_cast<uint32_t>(c), PUR_TREE | (static_cast<uint32_t>(m) << 8)),
+                                   key0, key1);
+    float s1, c1, s2, c2;
+    const float r1 = sqrtf(-2.0f * logf(u01(rn.x)));
+    sincospif(2.0f * u01(rn.y), &s1, &c1);
+    const float r2 = sqrtf(-2.0f * logf(u01(rn.z)));
+    sincospif(2.0f * u01(rn.w), &s2, &c2);
+    nx[m] = fmaf(step, r1 * c1, 0.5f * logf(opc / omc));
+    ny[m] = fmaf(step, r1 * s1, logf(d1 / d2));
+    nz[m] = fmaf(step, r2 * c2, atan2f(dot(rho, Fo.eta), dot(rho, Fo.xi)));
+  }
   if (lane == 0) {
     nx[0] = ny[0] = nz[0] = 0.f;
     nx[n - 1] = end.x;
@@ -438,7 +483,6 @@ __device__ float tree_propose(const DMedium& M, const DPair& S, float zoff, cons
     nz[n - 1] = end.z;
   }
   __syncwarp();
-  float lj = 0.f;  // log J(x') - log J(x), lane partials
   for (int d = 0;; ++d) {
     bool any = false;
     for (int j0 = 0; j0 < (1 << d); j0 += 32) {
@@ -448,32 +492,7 @@ __device__ float tree_propose(const DMedium& M, const DPair& S, float zoff, cons
       any = any || __any_sync(kAll, valid);
       if (valid) {
         const int m = (k + l) >> 1;
-        // old coordinates
-        const TreeFrame Fo = tree_frame(opos, k, l, kp, lp, vref);
-        const float3 P = w.pos(m);
-        const float3 a = w.pos(k) - P, b = w.pos(l) - P;
-        const float d1 = sqrtf(dot(a, a)), d2 = sqrtf(dot(b, b));
-        const float3 u = (1.0f / d1) * a, v = (1.0f / d2) * b;
-        const float3 up = u + v, um = u - v;
-        const float opc = 0.5f * dot(up, up), omc = 0.5f * dot(um, um);
-        const float3 rho = P - Fo.mid;
-        float zeta = 0.5f * logf(opc / omc);
-        float tt = logf(d1 / d2);
-        float phi = atan2f(dot(rho, Fo.eta), dot(rho, Fo.xi));
-        lj -= 3.0f * logf(d1 * d2 / (2.0f * Fo.gamma)) + logf(opc * omc);
-        // normal steps (the oracle's draw: Box-Muller on one Philox block)
-        const uint4 rn = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32),
-                                                  static_cast<uint32_t>(c), PUR_TREE | (static_cast<uint32_t>(m) << 8)),
-                                       key0, key1);
-        float s1, c1, s2, c2;
-        const float r1 = sqrtf(-2.0f * logf(u01(rn.x)));
-        sincospif(2.0f * u01(rn.y), &s1, &c1);
-        const float r2 = sqrtf(-2.0f * logf(u01(rn.z)));
-        sincospif(2.0f * u01(rn.w), &s2, &c2);
-        zeta = fmaf(step, r1 * c1, zeta);
-        tt = fmaf(step, r1 * s1, tt);
-        phi = fmaf(step, r2 * c2, phi);
-        // new vertex from the new foci and frame
+        const float zeta = nx[m], tt = ny[m], phi = nz[m];
         const TreeFrame Fn = tree_frame(npos, k, l, kp, lp, vref);
         const float ez = expf(zeta), emz = expf(-zeta);
         const float sn = 2.0f / (ez + emz);                 // 1 / cosh zeta = sin s
