@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
             continue;
           }
         }
-        if (mtype == 0u) {
+        if (!kTree && mtype == 0u) {
           const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 1)) >> 23);
           jj = j;
           inew = j;
@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
             move = MV_INTERIOR;
             const float3 fj = w.pos(j);
             const float3 z = f3(__uint_as_float(lo.z), __uint_as_float(lo.w), __uint_as_float(hi.x));
-            if constexpr (kGen) {
+            if constexpr (kGen && !kTree) {
               if (R.within == 1) {
                 gx_mala = grad_vertex_warp(M, S, zoff, [&](int k) { return w.pos(k); }, n, j, lane);
                 const float h = 0.5f * R.mala_eps * R.mala_eps;
@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
             extra = -R.log_pd + __logf(static_cast<float>(n - 2)) + R.log_pb + __logf(__fdividef(tb_new, Tb_red)) +
                     log_insert_density<true>(M, R, zoff, w.pos(jj - 1), w.pos(jj + 1), w.pos(jj));
           }
-          if constexpr (kGen) {
+          if constexpr (kGen && !kTree) {
             if (move == MV_INTERIOR && R.within == 1 && isfinite(dlp)) {
               const float3 gy = grad_vertex_warp(M, S, zoff, newpos, n, jj, lane);
               const float h = 0.5f * R.mala_eps * R.mala_eps;
