@@ -69,6 +69,7 @@ extern "C" {
 #define PMC_WITHIN_PERTURB 0
 #define PMC_WITHIN_MALA 1
 #define PMC_WITHIN_TREE 2
+#define PMC_WITHIN_HMC 3
 
 #define PMC_FLAG_GRADIENTS 1   /* accumulate score terms for pmc_grad_estimator */
 #define PMC_FLAG_NO_GRAPH 2    /* launch kernels directly instead of replaying a CUDA graph */
@@ -148,7 +149,13 @@ typedef struct {
  * step of scale sigma/sqrt(n) (sigma dimensionless) in every node's (zeta, t,
  * phi), rebuilds the path top-down and accepts with
  * p(x') J(x') / (p(x) J(x)), J = prod over nodes (d1 d2 / (2 gamma))^3 sin^2 s.
- * Tree moves need the whole vertex cap in shared memory (smem_window 0).
+ * PMC_WITHIN_HMC makes full-path gradient moves (section "Discussion"): when
+ * the within-dimension draw picks an interior vertex, every interior vertex
+ * gets a standard normal momentum and hmc_steps leapfrog steps of size
+ * mala_step follow d log p / d f (zero where the density is zero) with the
+ * source and the end vertex fixed, accepted with exp(H - H'), H = -log p +
+ * |p|^2/2; picking the end vertex makes the vMF end move.
+ * Tree and HMC moves need the whole vertex cap in shared memory (smem_window 0).
  * Births insert a vertex into a segment chosen with probability
  * tau_b(k)/sum tau_b, placed by bispherical coordinates; deaths remove an
  * interior vertex chosen uniformly (appendix, jump proposal; dimension
@@ -157,9 +164,9 @@ typedef struct {
 typedef struct {
   uint64_t seed;                   /* Philox4x32-10 key */
   double p_within, p_birth, p_death;
-  int within;                      /* PMC_WITHIN_PERTURB, PMC_WITHIN_MALA or PMC_WITHIN_TREE */
+  int within;                      /* PMC_WITHIN_PERTURB, _MALA, _TREE or _HMC */
   double sigma;                    /* Gaussian step (m); tree moves: dimensionless scale */
-  double mala_step;                /* MALA epsilon (m) */
+  double mala_step;                /* MALA epsilon, HMC leapfrog step (m) */
   double kappa_end;                /* vMF concentration of end moves; 0 -> (R/sigma)^2 (tree: 1/sigma^2) */
   uint64_t burn_in;
   uint32_t thin_bridge;            /* reference-density bridge terms every k steps; 0 = off */
@@ -174,6 +181,7 @@ typedef struct {
   int smem_window;                 /* vertices per chain kept in shared memory, a multiple of 32;
                                       entries beyond it live in global memory.  0 = the whole cap
                                       (or the autotuner's choice when warps_per_block = 0) */
+  int hmc_steps;                   /* PMC_WITHIN_HMC: leapfrog steps per move (1..1000) */
 } pmc_run_desc;
 
 /* Per-pair estimate returned by pmc_read_estimator. */

@@ -60,7 +60,8 @@ class Run(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("p_within", C.c_double), ("p_birth", C.c_double),
                 ("p_death", C.c_double), ("within", C.c_int), ("sigma", C.c_double),
                 ("mala_step", C.c_double), ("kappa_end", C.c_double), ("burn_in", C.c_uint64),
-                ("thin_bridge", C.c_uint32), ("gradients", C.c_int), ("beta_min", C.c_double)]
+                ("thin_bridge", C.c_uint32), ("gradients", C.c_int), ("beta_min", C.c_double),
+                ("hmc_steps", C.c_int)]
 
 
 class Acc(C.Structure):
@@ -213,6 +214,7 @@ def run(r, sensor_radius: float) -> Run:
     out.thin_bridge = int(r.thin_bridge)
     out.gradients = int(bool(r.gradients))
     out.beta_min = 0.01
+    out.hmc_steps = int(getattr(r, "hmc_steps", 10))
     return out
 
 

@@ -688,6 +688,7 @@ void or_tree_path(const double v_ref[3], int n, const double* coords, double* f)
 #define PURPOSE_QREF 3u
 #define PURPOSE_TRACE 4u
 #define PURPOSE_TREE 5u   /* | (vertex << 8): the normals of one tree node */
+#define PURPOSE_HMC 6u    /* | (vertex << 8): the momentum of one interior vertex */
 
 static void normals3(const uint32_t w[4], double z[3]) {
   double r1 = sqrt(-2.0 * log(or_u01(w[0])));
@@ -857,6 +858,42 @@ static void* chain_worker(void* arg) {
           double ljy = or_tree_coords(J->v_ref, n, y, J->coords);
           logA = lpy + ljy - lpx - ljx;
         }
+        proposed = 1;
+      } else if (u_move < J->thr_within && r->within == OR_WITHIN_HMC &&
+                 1 + (int)index_draw(A[1], (uint32_t)(n - 1)) != n - 1) {
+        /* full-path gradient move (section "Discussion": Hamiltonian Monte
+         * Carlo): every interior vertex gets a standard normal momentum, L
+         * leapfrog steps of size eps follow the gradient of log p with the
+         * source and the end vertex fixed, and the move is accepted with
+         * exp(-H(x', p') + H(x, p)), H = -log p + |p|^2 / 2.  Picking the end
+         * vertex (probability 1/(n-1)) still makes a vMF end move. */
+        kind = OR_MOVE_INTERIOR;
+        double eps = r->mala_step;
+        int L = r->hmc_steps;
+        double* pm = J->coords;  /* momentum, 3 doubles per vertex */
+        double k0 = 0.0;
+        for (int i = 1; i <= n - 2; ++i) {
+          uint32_t Wn[4];
+          draw_block(r->seed, (uint32_t)t, (uint32_t)(t >> 32), chain, PURPOSE_HMC | ((uint32_t)i << 8), Wn);
+          normals3(Wn, pm + 3 * i);
+          k0 += dot3(pm + 3 * i, pm + 3 * i);
+        }
+        memcpy(y, x, sizeof(double) * 3 * n);
+        or_grad_logp(m, J->s, J->d, n, y, gy);
+        for (int i = 1; i <= n - 2; ++i)
+          for (int q = 0; q < 3; ++q) pm[3 * i + q] += 0.5 * eps * gy[3 * i + q];
+        for (int st = 1; st <= L; ++st) {
+          for (int i = 1; i <= n - 2; ++i)
+            for (int q = 0; q < 3; ++q) y[3 * i + q] += eps * pm[3 * i + q];
+          or_grad_logp(m, J->s, J->d, n, y, gy);
+          double h = (st == L) ? 0.5 * eps : eps;
+          for (int i = 1; i <= n - 2; ++i)
+            for (int q = 0; q < 3; ++q) pm[3 * i + q] += h * gy[3 * i + q];
+        }
+        double k1 = 0.0;
+        for (int i = 1; i <= n - 2; ++i) k1 += dot3(pm + 3 * i, pm + 3 * i);
+        lpy = or_logp(m, J->s, J->d, n, y);
+        if (isfinite(lpy)) logA = lpy - lpx - 0.5 * k1 + 0.5 * k0;
         proposed = 1;
       } else if (u_move < J->thr_within) {
         /* within-dimension move of one of the n-1 movable vertices */

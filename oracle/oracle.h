@@ -28,7 +28,7 @@ enum { OR_HOMOGENEOUS = 0, OR_LAYERED = 1 };
 enum { OR_EMIT_ISOTROPIC = 0, OR_EMIT_VMF = 1 };
 enum { OR_RHO_ONE = 0, OR_RHO_PAPER = 1 };
 enum { OR_INIT_DIRECT = 0, OR_INIT_STRAIGHT = 1, OR_INIT_USER = 2 };
-enum { OR_WITHIN_PERTURB = 0, OR_WITHIN_MALA = 1, OR_WITHIN_TREE = 2 };
+enum { OR_WITHIN_PERTURB = 0, OR_WITHIN_MALA = 1, OR_WITHIN_TREE = 2, OR_WITHIN_HMC = 3 };
 enum { OR_MOVE_INTERIOR = 0, OR_MOVE_END = 1, OR_MOVE_BIRTH = 2, OR_MOVE_DEATH = 3 };
 
 typedef struct {
@@ -60,7 +60,7 @@ typedef struct {
 typedef struct {
   uint64_t seed;
   double p_within, p_birth, p_death;
-  int within;               /* OR_WITHIN_PERTURB or OR_WITHIN_MALA */
+  int within;               /* OR_WITHIN_PERTURB, _MALA, _TREE or _HMC */
   double sigma;             /* Gaussian perturbation scale (m) */
   double mala_step;         /* MALA epsilon (m) */
   double kappa_end;         /* vMF concentration of end moves (> 0) */
@@ -68,6 +68,7 @@ typedef struct {
   uint32_t thin_bridge;     /* record reference-density terms every k steps (0: never) */
   int gradients;            /* accumulate score terms */
   double beta_min;          /* lower clamp of the insertion concentration */
+  int hmc_steps;            /* OR_WITHIN_HMC: leapfrog steps of size mala_step */
 } or_run;
 
 /* Per-chain accumulators (FP64 sums over recorded states). */

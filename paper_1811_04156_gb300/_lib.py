@@ -61,7 +61,7 @@ class RunDesc(C.Structure):
                 ("thin_bridge", C.c_uint32), ("init", C.c_int), ("init_k", C.c_int),
                 ("init_jitter", C.c_double), ("init_xyz", C.POINTER(C.c_float)),
                 ("init_n", C.POINTER(C.c_int)), ("init_stride", C.c_int), ("flags", C.c_int),
-                ("warps_per_block", C.c_int), ("smem_window", C.c_int)]
+                ("warps_per_block", C.c_int), ("smem_window", C.c_int), ("hmc_steps", C.c_int)]
 
 
 class Estimate(C.Structure):

@@ -185,7 +185,7 @@ struct pmc_chains_s {
   cudaStream_t capture_stream = nullptr;
   std::vector<ChainClass> classes;
   std::map<unsigned long long, cudaGraphExec_t> graphs;
-  int general = 0;                 // chain kernel: 0 lean, 1 general, 2 general with tree moves
+  int general = 0;                 // chain kernel: 0 lean, 1 general, 2 with tree moves, 3 with HMC moves
   bool grad = false;               // keep d log sigma / dg per vertex
   bool autotune = false;           // warps per block chosen by timing
   int init_kind = 0, init_k = 0;
@@ -549,7 +549,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
       float best_ms = 1e30f;
       std::vector<int> windows = {full};
       for (int w : {128, 256, 512})
-        if (w < full && ch->general != 2) windows.push_back(w);  // tree moves keep the whole cap
+        if (w < full && ch->general < 2) windows.push_back(w);  // tree and HMC moves keep the whole cap
       for (int win : windows) {
         for (int wpb : {1, 2, 4}) {
           const bool spill = win < full;
@@ -622,8 +622,11 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   if (pd > 0 && !(pb > 0)) return fail(PMC_ERR_INVALID, "deaths need births (reversibility)");
   if (!finite_pos(r->sigma)) return fail(PMC_ERR_INVALID, "sigma must be > 0");
   if (r->within == PMC_WITHIN_MALA && !finite_pos(r->mala_step)) return fail(PMC_ERR_INVALID, "mala_step must be > 0");
-  if (r->within != PMC_WITHIN_PERTURB && r->within != PMC_WITHIN_MALA && r->within != PMC_WITHIN_TREE)
+  if (r->within != PMC_WITHIN_PERTURB && r->within != PMC_WITHIN_MALA && r->within != PMC_WITHIN_TREE &&
+      r->within != PMC_WITHIN_HMC)
     return fail(PMC_ERR_INVALID, "bad within kind");
+  if (r->within == PMC_WITHIN_HMC && !(finite_pos(r->mala_step) && r->hmc_steps >= 1 && r->hmc_steps <= 1000))
+    return fail(PMC_ERR_INVALID, "HMC needs mala_step > 0 and 1 <= hmc_steps <= 1000");
   if (r->init != PMC_INIT_DIRECT && r->init != PMC_INIT_STRAIGHT && r->init != PMC_INIT_USER)
     return fail(PMC_ERR_INVALID, "bad init kind");
   if (r->init == PMC_INIT_STRAIGHT && (r->init_k < 0 || !(r->init_jitter >= 0)))
@@ -653,6 +656,7 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   R.sigma = static_cast<float>(r->sigma);
   R.mala_eps = static_cast<float>(r->mala_step);
   R.within = r->within;
+  R.hmc_steps = r->hmc_steps;
   R.burn_in = r->burn_in;
   R.beta_min = 0.01f;
   R.gradients = (r->flags & PMC_FLAG_GRADIENTS) ? 1 : 0;
@@ -670,6 +674,7 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
                 std::any_of(ch->h_pairs.begin(), ch->h_pairs.end(),
                             [](const DPair& d) { return d.emission != PMC_EMIT_ISOTROPIC || d.rho != PMC_RHO_ONE; });
   if (r->within == PMC_WITHIN_TREE) ch->general = 2;
+  if (r->within == PMC_WITHIN_HMC) ch->general = 3;
   const int n_arrays = chain_arrays(ch->general > 0, ch->grad);
   const int T = ch->total;
   ch->h_base.resize(T);
@@ -706,8 +711,8 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     cl.smem_cap = (maxcap + 31) / 32 * 32;
     cl.max_cap = maxcap;
     cl.spill = false;
-    if (r->smem_window > 0 && r->smem_window < cl.smem_cap && ch->general == 2)
-      return fail(PMC_ERR_INVALID, "tree moves need the whole vertex cap in shared memory (smem_window)");
+    if (r->smem_window > 0 && r->smem_window < cl.smem_cap && ch->general >= 2)
+      return fail(PMC_ERR_INVALID, "tree and HMC moves need the whole vertex cap in shared memory (smem_window)");
     if (r->smem_window > 0 && r->smem_window < cl.smem_cap) {
       cl.smem_cap = r->smem_window;
       cl.spill = true;

@@ -525,6 +525,96 @@ __device__ float tree_propose(const DMedium& M, const DPair& S, float zoff, cons
   return warp_sum(lp) + warp_sum(lj);
 }
 
+// ---------------------------------------------------------------------------
+// Full-path HMC (section "Discussion": gradient-based moves).  Every interior
+// vertex gets a standard normal momentum; L leapfrog steps of size eps
+// follow d log p / d f (the adjoint of the density, grad_vertex) with the
+// source and the end vertex fixed; where the path has zero density (a
+// non-final segment touching the sensor, the last one arriving from
+// behind, or a zero-length segment) the gradient is taken as zero.
+// ---------------------------------------------------------------------------
+// 1 if the path in (nx, ny, nz) has positive density, on every lane.
+__device__ __forceinline__ bool hmc_path_valid(const DPair& S, const float* nx, const float* ny, const float* nz,
+                                               int n, int lane) {
+  bool ok = true;
+  for (int k = lane; k <= n - 2; k += 32) {
+    const float3 P = f3(nx[k], ny[k], nz[k]);
+    const float3 r = f3(nx[k + 1], ny[k + 1], nz[k + 1]) - P;
+    if (!(dot(r, r) > 0.f)) ok = false;
+    else if (k <= n - 3) ok = ok && !hits_ball<true>(S, P, r);
+    else ok = ok && (-dot(r, sensor_normal(S, P + r)) > 0.f);
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+// p += h * grad log p(x') for the interior vertices (0 where the density is 0).
+__device__ __forceinline__ void hmc_kick(const DMedium& M, const DPair& S, float zoff, const float* nx,
+                                         const float* ny, const float* nz, float* mx, float* my, float* mz, int n,
+                                         float h, int lane) {
+  if (!hmc_path_valid(S, nx, ny, nz, n, lane)) return;
+  auto npos = [&](int i) { return f3(nx[i], ny[i], nz[i]); };
+  for (int i = 1 + lane; i <= n - 2; i += 32) {
+    const float3 g = grad_vertex(M, S, zoff, npos, n, i);
+    mx[i] = fmaf(h, g.x, mx[i]);
+    my[i] = fmaf(h, g.y, my[i]);
+    mz[i] = fmaf(h, g.z, mz[i]);
+  }
+}
+
+// One HMC proposal: returns log p(x') - |p'|^2/2 + |p|^2/2 (without log p(x)),
+// the proposed path left in nx/ny/nz.
+template <bool kGen, class WP>
+__device__ float hmc_propose(const DMedium& M, const DPair& S, float zoff, const WP& w, float* nx, float* ny,
+                             float* nz, float* mx, float* my, float* mz, int n, float eps, int L,
+                             unsigned long long t, int c, uint32_t key0, uint32_t key1, int lane) {
+  float k0 = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    const float3 P = w.pos(i);
+    nx[i] = P.x;
+    ny[i] = P.y;
+    nz[i] = P.z;
+    if (i >= 1 && i <= n - 2) {
+      // the oracle's draw: Box-Muller on one Philox block per vertex
+      const uint4 rn = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32),
+                                                static_cast<uint32_t>(c), PUR_HMC | (static_cast<uint32_t>(i) << 8)),
+                                     key0, key1);
+      float s1, c1, s2, c2;
+      const float r1 = sqrtf(-2.0f * logf(u01(rn.x)));
+      sincospif(2.0f * u01(rn.y), &s1, &c1);
+      const float r2 = sqrtf(-2.0f * logf(u01(rn.z)));
+      sincospif(2.0f * u01(rn.w), &s2, &c2);
+      mx[i] = r1 * c1;
+      my[i] = r1 * s1;
+      mz[i] = r2 * c2;
+      k0 += mx[i] * mx[i] + my[i] * my[i] + mz[i] * mz[i];
+    }
+  }
+  __syncwarp();
+  hmc_kick(M, S, zoff, nx, ny, nz, mx, my, mz, n, 0.5f * eps, lane);
+  for (int st = 1; st <= L; ++st) {
+    __syncwarp();
+    for (int i = 1 + lane; i <= n - 2; i += 32) {
+      nx[i] = fmaf(eps, mx[i], nx[i]);
+      ny[i] = fmaf(eps, my[i], ny[i]);
+      nz[i] = fmaf(eps, mz[i], nz[i]);
+    }
+    __syncwarp();
+    hmc_kick(M, S, zoff, nx, ny, nz, mx, my, mz, n, st == L ? 0.5f * eps : eps, lane);
+  }
+  __syncwarp();
+  float k1 = 0.f, lp = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    if (i >= 1 && i <= n - 2) k1 += mx[i] * mx[i] + my[i] * my[i] + mz[i] * mz[i];
+    const float3 Pc = f3(nx[i], ny[i], nz[i]);
+    const float3 Pp = (i >= 1) ? f3(nx[i - 1], ny[i - 1], nz[i - 1]) : Pc;
+    const float3 Pn = (i <= n - 2) ? f3(nx[i + 1], ny[i + 1], nz[i + 1]) : Pc;
+    float vt, gt, seg, tb, len;
+    vertex_and_segment<kGen>(M, S, zoff, Pp, Pc, Pn, i, n, vt, gt, seg, tb, len);
+    lp += vt + ((i <= n - 2) ? seg : 0.f);
+  }
+  return warp_sum(lp) - 0.5f * (warp_sum(k1) - warp_sum(k0));
+}
+
 struct Accum {
   unsigned long long pn2, pn;  // integer partials of the current flush interval
   float pL, pL2, pG;           // FP32 partials of the current flush interval
@@ -572,11 +662,12 @@ __device__ __forceinline__ void flush64(Accum& a, int lane) {
 //   within: lo.z, lo.w, hi.x = standard normals, hi.y = vMF cosine,
 //           hi.z, hi.w = cos, sin of the vMF azimuth
 //   birth:  lo.z = u for cos s, lo.w = sinh t, hi.x = cosh t, hi.y, hi.z = cos, sin of phi
-template <bool kGen, bool kGrad, bool kSpill, bool kTree>
+template <bool kGen, bool kGrad, bool kSpill, int kX>
 __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainParams P) {
   using WP = WarpPath<kGen, kGrad, kSpill>;
-  static_assert(!kTree || (kGen && !kSpill), "tree moves use the general kernel with the whole cap in shared memory");
-  constexpr int kArraysAll = WP::kArrays + (kTree ? 3 : 0);
+  constexpr bool kTree = kX == 1, kHmc = kX == 2;
+  static_assert(kX == 0 || (kGen && !kSpill), "tree and HMC moves use the general kernel with the whole cap in shared memory");
+  constexpr int kArraysAll = WP::kArrays + (kTree ? 3 : 0) + (kHmc ? 6 : 0);
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
@@ -587,9 +678,12 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
   w.sm = smem + static_cast<size_t>(wib) * per_warp;
   w.S = cap_s;
   w.b = P.M.b;
-  float* tnx = w.sm + static_cast<size_t>(WP::kArrays) * cap_s;  // tree moves: the proposed path
+  float* tnx = w.sm + static_cast<size_t>(WP::kArrays) * cap_s;  // tree / HMC moves: the proposed path
   float* tny = tnx + cap_s;
   float* tnz = tny + cap_s;
+  float* hmx = tnz + cap_s;                                        // HMC moves: the momenta
+  float* hmy = hmx + cap_s;
+  float* hmz = hmy + cap_s;
   uint4* rng = reinterpret_cast<uint4*>(w.sm + static_cast<size_t>(kArraysAll) * cap_s);  // [32][2] uint4
   DPair* spair = reinterpret_cast<DPair*>(rng + 64);
   const DMedium& M = P.M;
@@ -719,6 +813,30 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
         float3 fnew = f3(0.f, 0.f, 0.f);
         float extra = 0.f;
         float3 gx_mala = f3(0.f, 0.f, 0.f);
+        if constexpr (kHmc) {
+          if (mtype == 0u && 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 1)) >> 23) != n - 1) {
+            // full-path HMC over the interior vertices (the end vertex, picked
+            // with probability 1/(n-1), takes the usual vMF end move below)
+            const float gain = hmc_propose<kGen>(M, S, zoff, w, tnx, tny, tnz, hmx, hmy, hmz, n, R.mala_eps,
+                                                 R.hmc_steps, t, c, key0, key1, lane);
+            float lpo = 0.f;
+            for (int q = lane; q < n; q += 32) lpo += w.vt(q) + ((q <= n - 2) ? w.seg(q) : 0.f);
+            lpo = warp_sum(lpo);
+            if (logu < gain - lpo) {
+              A.acc_i++;
+              close_state(A, t, R.burn_in, n, L, G);
+              for (int q = lane; q < n; q += 32) w.set_pos(q, f3(tnx[q], tny[q], tnz[q]));
+              __syncwarp();
+              refresh_caches<kGen>(M, S, zoff, w, n, lane);
+              const Sums s3 = path_sums(w, n, lane);
+              L = s3.L;
+              G = s3.G;
+              if (A.nflush >= kFlushAccepts) flush64(A, lane);
+            }
+            __syncwarp();
+            continue;
+          }
+        }
         if constexpr (kTree) {
           if (mtype == 0u) {
             // whole-path move in tree coordinates; a rejected proposal leaves
@@ -770,7 +888,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
             move = MV_INTERIOR;
             const float3 fj = w.pos(j);
             const float3 z = f3(__uint_as_float(lo.z), __uint_as_float(lo.w), __uint_as_float(hi.x));
-            if constexpr (kGen && !kTree) {
+            if constexpr (kGen && kX == 0) {
               if (R.within == 1) {
                 gx_mala = grad_vertex_warp(M, S, zoff, [&](int k) { return w.pos(k); }, n, j, lane);
                 const float h = 0.5f * R.mala_eps * R.mala_eps;
@@ -884,7 +1002,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
             extra = -R.log_pd + __logf(static_cast<float>(n - 2)) + R.log_pb + __logf(__fdividef(tb_new, Tb_red)) +
                     log_insert_density<true>(M, R, zoff, w.pos(jj - 1), w.pos(jj + 1), w.pos(jj));
           }
-          if constexpr (kGen && !kTree) {
+          if constexpr (kGen && kX == 0) {
             if (move == MV_INTERIOR && R.within == 1 && isfinite(dlp)) {
               const float3 gy = grad_vertex_warp(M, S, zoff, newpos, n, jj, lane);
               const float h = 0.5f * R.mala_eps * R.mala_eps;
@@ -1032,7 +1150,7 @@ __global__ void init_kernel(const InitParams p) {
 // The dynamic shared-memory limit is a property of the kernel, shared by every
 // launch: set it once to the device's per-block maximum so that classes with
 // different vertex caps can all launch.
-template <bool kGen, bool kGrad, bool kSpill, bool kTree>
+template <bool kGen, bool kGrad, bool kSpill, int kX>
 cudaError_t set_attributes() {
   static int done[64] = {};
   int dev = 0;
@@ -1042,32 +1160,33 @@ cudaError_t set_attributes() {
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad, kSpill, kTree>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad, kSpill, kX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            optin);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad, kSpill, kTree>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  e = cudaFuncSetAttribute(chain_kernel<kGen, kGrad, kSpill, kX>, cudaFuncAttributePreferredSharedMemoryCarveout,
                            100);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
   return e;
 }
 
-template <bool kGen, bool kGrad, bool kSpill, bool kTree>
+template <bool kGen, bool kGrad, bool kSpill, int kX>
 cudaError_t occupancy_of(int warps_per_block, size_t sm, int* blocks_per_sm) {
-  cudaError_t e = set_attributes<kGen, kGrad, kSpill, kTree>();
+  cudaError_t e = set_attributes<kGen, kGrad, kSpill, kX>();
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<kGen, kGrad, kSpill, kTree>,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, chain_kernel<kGen, kGrad, kSpill, kX>,
                                                        warps_per_block * 32, sm);
 }
 
-template <bool kGen, bool kGrad, bool kSpill, bool kTree>
+template <bool kGen, bool kGrad, bool kSpill, int kX>
 void launch_one(const ChainParams& p, int grid, int warps_per_block, size_t sm, cudaStream_t s) {
-  chain_kernel<kGen, kGrad, kSpill, kTree><<<grid, warps_per_block * 32, sm, s>>>(p);
+  chain_kernel<kGen, kGrad, kSpill, kX><<<grid, warps_per_block * 32, sm, s>>>(p);
 }
 
 // Instantiation key: lean / general (with or without gradient caches and
-// spill) and general with tree moves (never spilled).
+// spill), general with tree moves and general with HMC moves (never spilled).
 int kernel_key(int kind, bool grad, bool spill) {
   if (kind == 2) return 8 + (grad ? 1 : 0);
+  if (kind == 3) return 10 + (grad ? 1 : 0);
   return (kind == 1 ? 4 : 0) + (grad ? 2 : 0) + (spill ? 1 : 0);
 }
 
@@ -1076,44 +1195,48 @@ int kernel_key(int kind, bool grad, bool spill) {
 int chain_arrays(bool general, bool grad) { return 6 + (general ? 1 : 0) + (grad ? 1 : 0); }
 
 size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad) {
-  const size_t arrays = static_cast<size_t>(chain_arrays(kind > 0, grad) + (kind == 2 ? 3 : 0));
+  const size_t arrays = static_cast<size_t>(chain_arrays(kind > 0, grad) + (kind == 2 ? 3 : 0) + (kind == 3 ? 6 : 0));
   return static_cast<size_t>(warps_per_block) *
          (arrays * static_cast<size_t>(smem_cap) + 32u * kRngWords + kPairWords) * sizeof(float);
 }
 
 cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block, int smem_cap,
                             int* blocks_per_sm) {
-  if (kind == 2 && spill) return cudaErrorInvalidValue;
+  if (kind >= 2 && spill) return cudaErrorInvalidValue;
   const size_t sm = chain_smem_bytes(smem_cap, warps_per_block, kind, grad);
   switch (kernel_key(kind, grad, spill)) {
-    case 0: return occupancy_of<false, false, false, false>(warps_per_block, sm, blocks_per_sm);
-    case 1: return occupancy_of<false, false, true, false>(warps_per_block, sm, blocks_per_sm);
-    case 2: return occupancy_of<false, true, false, false>(warps_per_block, sm, blocks_per_sm);
-    case 3: return occupancy_of<false, true, true, false>(warps_per_block, sm, blocks_per_sm);
-    case 4: return occupancy_of<true, false, false, false>(warps_per_block, sm, blocks_per_sm);
-    case 5: return occupancy_of<true, false, true, false>(warps_per_block, sm, blocks_per_sm);
-    case 6: return occupancy_of<true, true, false, false>(warps_per_block, sm, blocks_per_sm);
-    case 7: return occupancy_of<true, true, true, false>(warps_per_block, sm, blocks_per_sm);
-    case 8: return occupancy_of<true, false, false, true>(warps_per_block, sm, blocks_per_sm);
-    default: return occupancy_of<true, true, false, true>(warps_per_block, sm, blocks_per_sm);
+    case 0: return occupancy_of<false, false, false, 0>(warps_per_block, sm, blocks_per_sm);
+    case 1: return occupancy_of<false, false, true, 0>(warps_per_block, sm, blocks_per_sm);
+    case 2: return occupancy_of<false, true, false, 0>(warps_per_block, sm, blocks_per_sm);
+    case 3: return occupancy_of<false, true, true, 0>(warps_per_block, sm, blocks_per_sm);
+    case 4: return occupancy_of<true, false, false, 0>(warps_per_block, sm, blocks_per_sm);
+    case 5: return occupancy_of<true, false, true, 0>(warps_per_block, sm, blocks_per_sm);
+    case 6: return occupancy_of<true, true, false, 0>(warps_per_block, sm, blocks_per_sm);
+    case 7: return occupancy_of<true, true, true, 0>(warps_per_block, sm, blocks_per_sm);
+    case 8: return occupancy_of<true, false, false, 1>(warps_per_block, sm, blocks_per_sm);
+    case 9: return occupancy_of<true, true, false, 1>(warps_per_block, sm, blocks_per_sm);
+    case 10: return occupancy_of<true, false, false, 2>(warps_per_block, sm, blocks_per_sm);
+    default: return occupancy_of<true, true, false, 2>(warps_per_block, sm, blocks_per_sm);
   }
 }
 
 cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s) {
-  if (kind == 2 && spill) return cudaErrorInvalidValue;
+  if (kind >= 2 && spill) return cudaErrorInvalidValue;
   const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block, kind, grad);
   switch (kernel_key(kind, grad, spill)) {
-    case 0: launch_one<false, false, false, false>(p, grid, warps_per_block, sm, s); break;
-    case 1: launch_one<false, false, true, false>(p, grid, warps_per_block, sm, s); break;
-    case 2: launch_one<false, true, false, false>(p, grid, warps_per_block, sm, s); break;
-    case 3: launch_one<false, true, true, false>(p, grid, warps_per_block, sm, s); break;
-    case 4: launch_one<true, false, false, false>(p, grid, warps_per_block, sm, s); break;
-    case 5: launch_one<true, false, true, false>(p, grid, warps_per_block, sm, s); break;
-    case 6: launch_one<true, true, false, false>(p, grid, warps_per_block, sm, s); break;
-    case 7: launch_one<true, true, true, false>(p, grid, warps_per_block, sm, s); break;
-    case 8: launch_one<true, false, false, true>(p, grid, warps_per_block, sm, s); break;
-    default: launch_one<true, true, false, true>(p, grid, warps_per_block, sm, s); break;
+    case 0: launch_one<false, false, false, 0>(p, grid, warps_per_block, sm, s); break;
+    case 1: launch_one<false, false, true, 0>(p, grid, warps_per_block, sm, s); break;
+    case 2: launch_one<false, true, false, 0>(p, grid, warps_per_block, sm, s); break;
+    case 3: launch_one<false, true, true, 0>(p, grid, warps_per_block, sm, s); break;
+    case 4: launch_one<true, false, false, 0>(p, grid, warps_per_block, sm, s); break;
+    case 5: launch_one<true, false, true, 0>(p, grid, warps_per_block, sm, s); break;
+    case 6: launch_one<true, true, false, 0>(p, grid, warps_per_block, sm, s); break;
+    case 7: launch_one<true, true, true, 0>(p, grid, warps_per_block, sm, s); break;
+    case 8: launch_one<true, false, false, 1>(p, grid, warps_per_block, sm, s); break;
+    case 9: launch_one<true, true, false, 1>(p, grid, warps_per_block, sm, s); break;
+    case 10: launch_one<true, false, false, 2>(p, grid, warps_per_block, sm, s); break;
+    default: launch_one<true, true, false, 2>(p, grid, warps_per_block, sm, s); break;
   }
   return cudaGetLastError();
 }

@@ -61,7 +61,8 @@ struct DRun {
   uint32_t thr_within, thr_birth;  // 23-bit thresholds of the move draw
   float log_pb, log_pd;            // log p_birth, log p_death
   float sigma, mala_eps;
-  int within;                      // 0 perturb, 1 MALA
+  int within;                      // 0 perturb, 1 MALA, 2 tree, 3 HMC
+  int hmc_steps;                   // HMC: leapfrog steps of size mala_eps
   unsigned long long burn_in;
   float beta_min;
   int gradients;

@@ -34,7 +34,10 @@ enum StatusBits { ST_NONFINITE = 1, ST_ABORTED = 2, ST_BAD_N = 4 };
 
 // Random-number purposes (fourth Philox counter word).
 // PUR_TREE is or-ed with (vertex << 8): the normals of one tree node.
-enum Purpose : uint32_t { PUR_STEP_A = 0, PUR_STEP_B = 1, PUR_INIT = 2, PUR_QREF = 3, PUR_TRACE = 4, PUR_TREE = 5 };
+// PUR_HMC likewise: the momentum of one interior vertex.
+enum Purpose : uint32_t {
+  PUR_STEP_A = 0, PUR_STEP_B = 1, PUR_INIT = 2, PUR_QREF = 3, PUR_TRACE = 4, PUR_TREE = 5, PUR_HMC = 6
+};
 
 struct ChainParams {
   DMedium M;
@@ -65,7 +68,8 @@ struct ChainParams {
 // global block.  The global block of a chain holds chain_arrays() arrays of
 // cap floats (x, y, z first).
 // `kind`: 0 the lean kernel, 1 the general one, 2 the general one with tree
-// moves (3 more shared arrays per warp, no spill).
+// moves (3 more shared arrays per warp, no spill), 3 the general one with HMC
+// moves (6 more shared arrays per warp, no spill).
 int chain_arrays(bool general, bool grad);
 cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s);

@@ -51,6 +51,7 @@ INIT_USER = 2
 WITHIN_PERTURB = 0
 WITHIN_MALA = 1
 WITHIN_TREE = 2
+WITHIN_HMC = 3
 
 BASE_SEED = 0x181104156
 
@@ -113,6 +114,7 @@ class Run:
     init_jitter: float = 0.0       # N(0, jitter^2) per coordinate
     thin_bridge: int = 0           # 0 = no reference-density bridge terms
     gradients: bool = False
+    hmc_steps: int = 10            # leapfrog steps of a full-path gradient (HMC) move, step mala_step
 
 
 @dataclasses.dataclass

@@ -1,0 +1,108 @@
+"""GPU parity of the full-path gradient (HMC) move (section "Discussion")
+with the FP64 oracle: the same Philox stream replays the oracle's
+trajectories, tiny leapfrog steps are almost always accepted (the gradient
+the kernel follows matches the density it accepts with), and the chains'
+intensity equals the quadrature (vertex cap 3) and the forward tracer.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import quadrature as Q
+from paper_1811_04156_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1811_04156_gb300 import build
+    build.build()
+    from paper_1811_04156_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    return api.Context(0)
+
+
+def _hmc_scene(name, eps=0.01, steps=5):
+    sc = S.general_small(n_chains=64, n_steps=300) if name == "general" else S.plain(n_chains=64, n_steps=300)
+    sc.run.within = S.WITHIN_HMC
+    sc.run.mala_step = eps
+    sc.run.hmc_steps = steps
+    sc.run.init = S.INIT_STRAIGHT
+    sc.run.init_k = 6
+    sc.run.init_jitter = 0.02
+    return sc
+
+
+@pytest.mark.parametrize("name", ["plain", "general"])
+def test_hmc_trajectory_replay(api, ctx, oracle_lib, name):
+    O = oracle_lib
+    sc = _hmc_scene(name)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    assert ch.launch_info()[0]["general"] == 3
+    ch.run_steps(sc.run.n_steps)
+    xyz, n, st = ch.read_states()
+    oc = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, sc.pairs[0].cap)
+    margin = oc.run(sc.run.n_steps, margins=True)
+    clean = margin > 1e-3
+    assert clean.sum() >= 24
+    for c in np.nonzero(clean)[0]:
+        assert n[c] == oc.n[c], (c, n[c], oc.n[c])
+        k = int(n[c])
+        assert np.allclose(xyz[c, :, :k].T, oc.xyz[c, :k], atol=2e-4), (c, np.abs(xyz[c, :, :k].T - oc.xyz[c, :k]).max())
+    acc = ch.read_accumulators()
+    oacc = oc.accumulators()
+    for c in np.nonzero(clean)[0]:
+        assert np.array_equal(acc[c, 8:12], oacc["prop"][c])
+        assert np.array_equal(acc[c, 12:16], oacc["acc"][c])
+
+
+def test_hmc_small_steps_conserve_energy(api, ctx):
+    sc = _hmc_scene("general", eps=2e-4, steps=5)
+    sc.pairs = [S.Pair(0, 0, 1024, 64)]
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    ch.run_steps(400)
+    acc = ch.read_accumulators()
+    assert acc[:, 12].sum() / acc[:, 8].sum() > 0.98
+
+
+def test_hmc_single_scatter_sector(api, ctx):
+    sc = S.plain(n_chains=4096, n_steps=20000, cap=3)
+    sc.run.within = S.WITHIN_HMC
+    sc.run.mala_step = 0.03
+    sc.run.hmc_steps = 4
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    ch.run_steps(20000)
+    e = ch.read_estimator()[0]
+    ref = Q.z2_closed(1.0, 0.1, 2.2) + Q.z3(1.0, 0.1, 0.5, 5.0, 0.9)
+    assert abs(e["intensity"] - ref) < 3 * e["std_err"], (e["intensity"], e["std_err"], ref)
+    assert e["rel_err"] < 0.005
+
+
+def test_hmc_chains_match_tracer(api, ctx):
+    med = S.Medium(lambda_s=1.0, lambda_a=5.0, g=0.0)
+    src, sen = S.Source(), S.Sensor((0.0, 0.0, 1.5), 0.5)
+    cap = 24
+    run = S.Run(seed=98, n_steps=30000, burn_in=3000, within=S.WITHIN_HMC, mala_step=0.08, hmc_steps=5, sigma=0.1)
+    medium = api.Medium(ctx, med)
+    geom = api.Geometry(ctx, [src], [sen], [S.Pair(0, 0, 4096, cap)])
+    ch = api.Chains(ctx, medium, geom, run)
+    ch.run_steps(run.n_steps)
+    e = ch.read_estimator()[0]
+    tr = api.trace(ctx, medium, geom, 0, 7, 400_000_000, max_scatter=cap - 2)
+    assert abs(e["intensity"] - tr["I"]) < 3 * math.hypot(e["std_err"], tr["se"]), (e, tr)
+    assert e["rel_err"] < 0.01

@@ -138,3 +138,59 @@ def test_tree_chain_matches_forward_tracer_all_orders(oracle_lib):
     zc = z2 * h / h[2]
     for k in (3, 4, 5):
         assert abs(zc[k] / tr["hist"][k - 2] - 1) < 0.04, (k, zc[k], tr["hist"][k - 2])
+
+
+# ---------------------------------------------------------------------------
+# Full-path gradient (HMC) moves (section "Discussion"), pinned the same way.
+# ---------------------------------------------------------------------------
+def _hmc_run(**kw):
+    return S.Run(within=S.WITHIN_HMC, **kw)
+
+
+def test_hmc_small_steps_conserve_energy(oracle_lib):
+    """With a tiny leapfrog step the Hamiltonian is conserved to O(eps^2), so
+    HMC proposals are almost always accepted: this ties the gradient the
+    leapfrog follows to the density the acceptance uses (a dropped term or a
+    wrong sign in either shows up as rejections)."""
+    O = oracle_lib
+    sc = S.general_small(n_chains=32, n_steps=400)
+    sc.run = _hmc_run(seed=11, burn_in=0, mala_step=2e-4, hmc_steps=5, init=S.INIT_STRAIGHT, init_k=8,
+                      init_jitter=0.02)
+    ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 32, 64)
+    ch.run(400)
+    acc = ch.accumulators()
+    rate = acc["acc"][:, 0].sum() / acc["prop"][:, 0].sum()
+    assert rate > 0.98, rate
+
+
+def test_hmc_chain_single_scatter_sector_matches_quadrature(oracle_lib):
+    O = oracle_lib
+    sc = S.plain()
+    sc.run = _hmc_run(seed=sc.run.seed, burn_in=2000, mala_step=0.03, hmc_steps=4)
+    ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, 3)
+    ch.run(40000)
+    m, s, d = O.medium(sc.medium), O.source(sc.sources[0]), O.sensor(sc.sensors[0])
+    I, se, _ = O.direct_estimate(ch.accumulators(), O.z2(m, s, d))
+    ref = Q.z2_closed(1.0, 0.1, 2.2) + Q.z3(1.0, 0.1, 0.5, 5.0, 0.9)
+    assert abs(I - ref) < 3 * se, (I, se, ref)
+    assert se / I < 0.015
+
+
+def test_hmc_chain_matches_forward_tracer_all_orders(oracle_lib):
+    O = oracle_lib
+    med = S.Medium(lambda_s=1.0, lambda_a=5.0, g=0.0)
+    src, sen = S.Source(), S.Sensor((0.0, 0.0, 1.5), 0.5)
+    run = _hmc_run(seed=2468, burn_in=3000, mala_step=0.08, hmc_steps=5, sigma=0.1)
+    cap = 24
+    ch = O.Chains(med, src, sen, run, 96, cap)
+    H = np.zeros((96, cap + 1))
+    ch.run(30000, n_hist=H)
+    m, s, d = O.medium(med), O.source(src), O.sensor(sen)
+    z2 = O.z2(m, s, d)
+    I, se, _ = O.direct_estimate(ch.accumulators(), z2)
+    tr = O.trace(m, s, d, 77, 4_000_000, max_scatter=cap - 2, hist=True)
+    assert abs(I - tr["I"]) < 3 * math.hypot(se, tr["se"]), (I, se, tr["I"], tr["se"])
+    h = H.sum(0)
+    zc = z2 * h / h[2]
+    for k in (3, 4, 5):
+        assert abs(zc[k] / tr["hist"][k - 2] - 1) < 0.05, (k, zc[k], tr["hist"][k - 2])
