@@ -83,8 +83,10 @@ def parse():
     p.add_argument("--e1-thin", type=int, default=200, help="steps between observations of B and lengths")
     p.add_argument("--e1-photons", type=int, default=0, help="tracer photons per sensor and b1 (0: no tracer)")
     p.add_argument("--e1-out", default="", help="file for the full result (histograms included)")
-    p.add_argument("--e1-within", default="perturb", choices=["perturb", "tree", "mala"],
-                   help="within-dimension moves: Gaussian vertex steps, the paper's tree-coordinate moves or MALA")
+    p.add_argument("--e1-within", default="perturb", choices=["perturb", "tree", "mala", "hmc"],
+                   help="within-dimension moves: Gaussian vertex steps, the paper's tree-coordinate moves, MALA or "
+                        "full-path HMC")
+    p.add_argument("--e1-hmc-steps", type=int, default=10, help="leapfrog steps of an HMC move")
     p.add_argument("--e1-sigma", type=float, default=0.0,
                    help="step scale (m for perturb; dimensionless for tree; MALA epsilon); 0 = the scene default")
     p.add_argument("--e1-seed", action="store_true",
@@ -557,11 +559,13 @@ def e1_experiment(args):
     results = []
     for b1 in [float(x) for x in args.e1_b1.split(",")]:
         sc = S.e1(b1, n_chains=args.e1_chains, n_steps=args.e1_steps)
-        sc.run.within = {"perturb": S.WITHIN_PERTURB, "tree": S.WITHIN_TREE, "mala": S.WITHIN_MALA}[args.e1_within]
+        sc.run.within = {"perturb": S.WITHIN_PERTURB, "tree": S.WITHIN_TREE, "mala": S.WITHIN_MALA,
+                         "hmc": S.WITHIN_HMC}[args.e1_within]
         if args.e1_within == "tree":
             sc.run.sigma = args.e1_sigma or 0.3
-        elif args.e1_within == "mala":
+        elif args.e1_within in ("mala", "hmc"):
             sc.run.mala_step = args.e1_sigma or 0.5
+            sc.run.hmc_steps = args.e1_hmc_steps
         elif args.e1_sigma:
             sc.run.sigma = args.e1_sigma
         medium = api.Medium(ctx, sc.medium)
