@@ -421,6 +421,27 @@ PMC_API int pmc_yield_observe(pmc_chains_t chains, int pair0, int pair1, double*
 PMC_API int pmc_yield_estimate(pmc_chains_t chains, int pair0, int pair1, const double* sums, uint64_t n_obs,
                                double* out, void* stream);
 
+/* One observation of every chain of pair0 and pair1 as log ratios rather
+ * than sums: logr[i] = log(p_1/p_0) at pair0's chain i (i < n0) and
+ * logr[n0 + i] = log(p_0/p_1) at pair1's chain i (-inf outside T's domain).
+ * logr: device, caller-owned, n0 + n1 floats (one row of the array that
+ * pmc_bridge_ratio reads).  Asynchronous on `stream`. */
+PMC_API int pmc_yield_observe_log(pmc_chains_t chains, int pair0, int pair1, float* logr, void* stream);
+
+/* Optimal bridge estimate (Meng & Wong 1996, the iterative estimator that
+ * the geometric one approximates) of r = c_1 / c_0 from stored log ratios:
+ * logr (device, caller-owned) holds `rows` rows of n0 values log(q1/q0)(x),
+ * x ~ p0, followed by n1 values log(q0/q1)(x), x ~ p1.  Starting from the
+ * geometric estimate, r <- [mean over p0 draws of l / (s1 l + s0 r)] /
+ * [mean over p1 draws of 1 / (s1 l + s0 r)], l = q1/q0, s_k = n_k/(n0 + n1),
+ * until the relative change is below tol or after max_iter iterations.  The
+ * standard error comes from `groups` disjoint chain groups (a chain's group
+ * is its index within its side mod groups), each iterated on its own.
+ * out (host, 4 doubles): r, standard error, iterations, the geometric
+ * estimate.  1 <= groups <= min(n0, n1, 1024).  Synchronises `stream`. */
+PMC_API int pmc_bridge_ratio(pmc_ctx_t ctx, const float* logr, uint64_t rows, int n0, int n1, int groups,
+                             int max_iter, double tol, double* out, void* stream);
+
 /* Path-length distribution of the chains: one observation of every chain,
  * hist[pair][bin] += 1 with bin = floor((L - l_lo) / (l_hi - l_lo) * n_bins)
  * for its current path length L in [l_lo, l_hi) (others are not counted).

@@ -413,6 +413,45 @@ def tree_path(v_ref, f0, f_end, coords):
     return f
 
 
+def optimal_bridge(logr0, logr1, groups=16, max_iter=200, tol=1e-10):
+    """Iterative optimal bridge (Meng & Wong 1996) for r = c1/c0 from draws of
+    p0 (log(q1/q0) at each, array rows x n0) and of p1 (log(q0/q1) at each,
+    rows x n1), started from the geometric estimate; chains (columns) are
+    split into `groups` groups by index mod groups, each iterated on its own,
+    and the standard error is their spread / sqrt(groups).  Returns
+    (r, se, iterations, geometric estimate)."""
+    L0 = np.asarray(logr0, dtype=np.float64)
+    L1 = np.asarray(logr1, dtype=np.float64)
+    n0, n1 = L0.shape[1], L1.shape[1]
+    s0, s1 = n0 / (n0 + n1), n1 / (n0 + n1)
+    l0 = np.exp(L0)          # q1/q0 at p0 draws
+    l1 = np.exp(-L1)         # q1/q0 at p1 draws
+    cols = [(np.arange(n0) % groups == g, np.arange(n1) % groups == g) for g in range(groups)]
+    cols.append((np.ones(n0, bool), np.ones(n1, bool)))
+
+    def geo(c0, c1):
+        a = np.where(np.isfinite(L0[:, c0]), np.exp(0.5 * L0[:, c0]), 0.0).mean()
+        b = np.where(np.isfinite(L1[:, c1]), np.exp(0.5 * L1[:, c1]), 0.0).mean()
+        return a / b
+
+    r = np.array([geo(c0, c1) for c0, c1 in cols])
+    r_geo = r[-1]
+    it = 0
+    for it in range(1, max_iter + 1):
+        rn = np.empty_like(r)
+        for g, (c0, c1) in enumerate(cols):
+            with np.errstate(divide="ignore"):
+                a = (1.0 / (s1 + s0 * r[g] / l0[:, c0])).mean()
+            b = (1.0 / (s1 * l1[:, c1] + s0 * r[g])).mean()
+            rn[g] = a / b
+        change = np.max(np.abs(rn / r - 1.0))
+        r = rn
+        if change < tol:
+            break
+    se = r[:groups].std(ddof=1) / math.sqrt(groups) if groups > 1 else float("nan")
+    return r[-1], se, it, r_geo
+
+
 def yield_ratio_estimate(sums0, sums1):
     """Geometric estimator B = E_0[sqrt(p_1/p_0)] / E_1[sqrt(p_0/p_1)] from
     per-chain sums of sqrt-ratios (each array: one entry per chain, equal

@@ -249,6 +249,15 @@ class Chains:
               "pmc_yield_estimate")
         return {"B": out[0], "se": out[1], "E0": out[2], "E1": out[3], "var0": out[4], "var1": out[5]}
 
+    def yield_observe_log(self, pair0: int, pair1: int, row: torch.Tensor, stream=None):
+        """One observation of the log density ratios of pair0's and pair1's chains (pmc_yield_observe_log)."""
+        _require_cuda(row, torch.float32, "row")
+        need = self.geom.pairs[pair0].n_chains + self.geom.pairs[pair1].n_chains
+        if row.numel() != need:
+            raise ValueError(f"row must hold {need} floats")
+        check(load().pmc_yield_observe_log(self.handle, int(pair0), int(pair1), C.c_void_p(row.data_ptr()),
+                                           _stream(stream)), "pmc_yield_observe_log")
+
     def length_hist(self, l_lo: float, l_hi: float, hist: torch.Tensor, stream=None):
         """One observation of every chain's path length into hist (n_pairs, n_bins) (pmc_length_hist)."""
         _require_cuda(hist, torch.float64, "hist")
@@ -422,23 +431,48 @@ def yield_logratio(ctx: Context, medium: Medium, geom: Geometry, pair0: int, pai
     return (out, oxyz) if mapped else out
 
 
+def bridge_ratio(ctx: Context, logr: torch.Tensor, n0: int, n1: int, groups: int = 16, max_iter: int = 200,
+                 tol: float = 1e-10, stream=None) -> dict:
+    """Optimal bridge estimate of c1/c0 from stored log ratios (pmc_bridge_ratio);
+    logr: float32 (rows, n0 + n1) on the device."""
+    _require_cuda(logr, torch.float32, "logr")
+    if logr.dim() != 2 or logr.shape[1] != n0 + n1:
+        raise ValueError("logr must have shape (rows, n0 + n1)")
+    out = np.zeros(4)
+    check(load().pmc_bridge_ratio(ctx.handle, C.c_void_p(logr.data_ptr()), int(logr.shape[0]), int(n0), int(n1),
+                                  int(groups), int(max_iter), float(tol), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                  _stream(stream)), "pmc_bridge_ratio")
+    return {"r": out[0], "se": out[1], "iterations": int(out[2]), "geometric": out[3]}
+
+
 class YieldRatio:
     """Relative light yield B of two pairs sharing a source (pair1's sensor over
     pair0's): a device buffer of per-chain sums, filled by observe() between
-    run_steps calls and reduced by estimate()."""
+    run_steps calls and reduced by estimate() (the paper's geometric
+    estimator); with max_obs > 0 every observation's log ratios are also kept
+    (max_obs rows) for estimate_bridge() (the optimal bridge)."""
 
-    def __init__(self, chains: Chains, pair0: int, pair1: int):
+    def __init__(self, chains: Chains, pair0: int, pair1: int, max_obs: int = 0):
         self.chains, self.pair0, self.pair1 = chains, int(pair0), int(pair1)
-        n = chains.geom.pairs[pair0].n_chains + chains.geom.pairs[pair1].n_chains
-        self.sums = torch.zeros(n, dtype=torch.float64, device=f"cuda:{chains.ctx.device}")
+        self.n0 = chains.geom.pairs[pair0].n_chains
+        self.n1 = chains.geom.pairs[pair1].n_chains
+        dev = f"cuda:{chains.ctx.device}"
+        self.sums = torch.zeros(self.n0 + self.n1, dtype=torch.float64, device=dev)
+        self.logr = torch.zeros((int(max_obs), self.n0 + self.n1), dtype=torch.float32, device=dev) if max_obs else None
         self.n_obs = 0
 
     def observe(self, stream=None):
         self.chains.yield_observe(self.pair0, self.pair1, self.sums, stream)
+        if self.logr is not None and self.n_obs < self.logr.shape[0]:
+            self.chains.yield_observe_log(self.pair0, self.pair1, self.logr[self.n_obs], stream)
         self.n_obs += 1
 
     def estimate(self, stream=None) -> dict:
         return self.chains.yield_estimate(self.pair0, self.pair1, self.sums, self.n_obs, stream)
+
+    def estimate_bridge(self, groups: int = 16, stream=None) -> dict:
+        rows = min(self.n_obs, self.logr.shape[0])
+        return bridge_ratio(self.chains.ctx, self.logr[:rows], self.n0, self.n1, groups, stream=stream)
 
 
 def qref_logdensity(ctx: Context, medium: Medium, geom: Geometry, pair: int, xyz: torch.Tensor, n: torch.Tensor,

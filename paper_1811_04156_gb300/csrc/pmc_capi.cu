@@ -1375,7 +1375,80 @@ int pmc_yield_observe(pmc_chains_t ch, int pair0, int pair1, double* sums, void*
   const DPair& p0 = ch->h_pairs[pair0];
   const DPair& p1 = ch->h_pairs[pair1];
   CK(launch_yield_chains(ch->med->d, ch->d_pairs, pair0, pair1, T, ch->d_chain_base, ch->d_xyz, ch->d_n, p0.chain0,
-                         p0.n_chains, p1.chain0, p1.n_chains, sums, static_cast<cudaStream_t>(stream)));
+                         p0.n_chains, p1.chain0, p1.n_chains, sums, nullptr, static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
+int pmc_yield_observe_log(pmc_chains_t ch, int pair0, int pair1, float* logr, void* stream) {
+  if (ch == nullptr || logr == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  DYMap T;
+  const int rc = make_ymap(ch->geom, pair0, pair1, true, &T);
+  if (rc != PMC_OK) return rc;
+  CK(cudaSetDevice(ch->ctx->device));
+  const DPair& p0 = ch->h_pairs[pair0];
+  const DPair& p1 = ch->h_pairs[pair1];
+  CK(launch_yield_chains(ch->med->d, ch->d_pairs, pair0, pair1, T, ch->d_chain_base, ch->d_xyz, ch->d_n, p0.chain0,
+                         p0.n_chains, p1.chain0, p1.n_chains, nullptr, logr, static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
+int pmc_bridge_ratio(pmc_ctx_t ctx, const float* logr, uint64_t rows, int n0, int n1, int groups, int max_iter,
+                     double tol, double* out, void* stream) {
+  if (!ctx || !logr || !out) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (rows == 0 || n0 < 1 || n1 < 1 || groups < 1 || groups > 1024 || groups > std::min(n0, n1) || max_iter < 1 ||
+      !(tol > 0))
+    return fail(PMC_ERR_INVALID, "bad bridge arguments");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int G = groups;
+  double* d_r = nullptr;
+  double* d_acc = nullptr;
+  CK(dalloc(&d_r, G + 1));
+  cudaError_t e = dalloc(&d_acc, 2 * (G + 1));
+  std::vector<double> r(G + 1), acc(2 * (G + 1));
+  // chains per group on each side
+  std::vector<double> c0(G + 1, 0.0), c1(G + 1, 0.0);
+  for (int j = 0; j < n0; ++j) c0[j % G] += 1.0;
+  for (int j = 0; j < n1; ++j) c1[j % G] += 1.0;
+  c0[G] = n0;
+  c1[G] = n1;
+  const double s0 = static_cast<double>(n0) / (n0 + n1), s1 = static_cast<double>(n1) / (n0 + n1);
+  auto pass = [&](int geometric) -> cudaError_t {
+    cudaError_t ee = cudaMemcpyAsync(d_r, r.data(), sizeof(double) * (G + 1), cudaMemcpyHostToDevice, s);
+    if (ee == cudaSuccess)
+      ee = launch_bridge_sums(logr, rows, n0, n1, G, d_r, s0, s1, geometric, d_acc, ctx->n_sm, s);
+    if (ee == cudaSuccess)
+      ee = cudaMemcpyAsync(acc.data(), d_acc, sizeof(double) * 2 * (G + 1), cudaMemcpyDeviceToHost, s);
+    if (ee == cudaSuccess) ee = cudaStreamSynchronize(s);
+    return ee;
+  };
+  // start from the geometric estimator
+  if (e == cudaSuccess) e = pass(1);
+  int it = 0;
+  if (e == cudaSuccess) {
+    for (int g = 0; g <= G; ++g) r[g] = (acc[2 * g] / c0[g]) / (acc[2 * g + 1] / c1[g]);
+    out[3] = r[G];
+    for (it = 1; it <= max_iter && e == cudaSuccess; ++it) {
+      e = pass(0);
+      if (e != cudaSuccess) break;
+      double change = 0.0;
+      for (int g = 0; g <= G; ++g) {
+        const double rn = (acc[2 * g] / c0[g]) / (acc[2 * g + 1] / c1[g]);
+        if (std::isfinite(rn) && rn > 0) change = std::max(change, std::fabs(rn / r[g] - 1.0));
+        r[g] = rn;
+      }
+      if (change < tol) break;
+    }
+  }
+  cudaFree(d_r);
+  cudaFree(d_acc);
+  CK(e);
+  double m = 0.0, v = 0.0;
+  for (int g = 0; g < G; ++g) m += r[g] / G;
+  for (int g = 0; g < G; ++g) v += (r[g] - m) * (r[g] - m);
+  out[0] = r[G];
+  out[1] = G > 1 ? std::sqrt(v / (G - 1) / G) : std::numeric_limits<double>::quiet_NaN();
+  out[2] = std::min(it, max_iter);
   return PMC_OK;
 }
 

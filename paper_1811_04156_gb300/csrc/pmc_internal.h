@@ -178,9 +178,15 @@ struct DYMap {
 };
 // Adds exp(r/2) of every chain of pair0 (side 0) and pair1 (side 1) to sums
 // [n0 + n1], r the log ratio of the other density at the mapped path to the own one.
+// With logr != null each chain's log ratio is also written to logr[n0 + n1].
 cudaError_t launch_yield_chains(const DMedium& M, const DPair* pairs, int pair0, int pair1, const DYMap& T,
                                 const long long* chain_base, const float* xyz, const int* n, int chain0_0, int n0,
-                                int chain0_1, int n1, double* sums, cudaStream_t s);
+                                int chain0_1, int n1, double* sums, float* logr, cudaStream_t s);
+// Sums of one optimal-bridge iteration (or of the geometric estimator) over
+// stored log ratios, per chain group and overall: acc[groups + 1][2] (zeroed here).
+cudaError_t launch_bridge_sums(const float* logr, unsigned long long rows, int n0, int n1, int groups,
+                               const double* r, double s0, double s1, int geometric, double* acc, int n_sm,
+                               cudaStream_t s);
 cudaError_t launch_yield_logratio(const DMedium& M, const DPair& S0, const DPair& S1, const DYMap& T, int side,
                                   const float* xyz, const int* n, int batch, int cap, float* out,
                                   float* out_xyz, cudaStream_t s);

@@ -17,6 +17,8 @@
 // FP32 forms: rC (cos a - 1) = -2 rC sin^2(a/2) and, for the inverse,
 // rad - rC = ((p.m)(p.m + 2 rC) + (p.k)^2) / (rad + rC), which keep the
 // vertices' precision where rC is much larger than the offsets.
+#include <algorithm>
+
 #include "pmc_internal.h"
 
 namespace pmc {
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(128) yield_chain_kernel(const DMedium M, const
                                                           const long long* __restrict__ chain_base,
                                                           const float* __restrict__ xyz, const int* __restrict__ nn,
                                                           int chain0_0, int n0, int chain0_1, int n1,
-                                                          double* __restrict__ sums) {
+                                                          double* __restrict__ sums, float* __restrict__ logr) {
   const int lane = threadIdx.x & 31;
   const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (j >= n0 + n1) return;
@@ -155,7 +157,8 @@ __global__ void __launch_bounds__(128) yield_chain_kernel(const DMedium M, const
   ratio_terms(M, Sself, Soth, T, side, ChainPos{xyz + chain_base[c], Sself.cap}, n, lane, ls, lo, lj, inside);
   if (lane == 0) {
     const float r = log_ratio(side, ls, lo, lj, inside);
-    sums[j] += isfinite(r) ? exp(0.5 * static_cast<double>(r)) : 0.0;
+    if (sums != nullptr) sums[j] += isfinite(r) ? exp(0.5 * static_cast<double>(r)) : 0.0;
+    if (logr != nullptr) logr[j] = r;
   }
 }
 
@@ -264,11 +267,83 @@ __global__ void __launch_bounds__(128) length_hist_kernel(const DPair* __restric
 
 cudaError_t launch_yield_chains(const DMedium& M, const DPair* pairs, int pair0, int pair1, const DYMap& T,
                                 const long long* chain_base, const float* xyz, const int* n, int chain0_0, int n0,
-                                int chain0_1, int n1, double* sums, cudaStream_t s) {
+                                int chain0_1, int n1, double* sums, float* logr, cudaStream_t s) {
   const int total = n0 + n1;
   if (total == 0) return cudaSuccess;
   yield_chain_kernel<<<(total + 3) / 4, 128, 0, s>>>(M, pairs, pair0, pair1, T, chain_base, xyz, n, chain0_0, n0,
-                                                     chain0_1, n1, sums);
+                                                     chain0_1, n1, sums, logr);
+  return cudaGetLastError();
+}
+
+// Optimal bridge (Meng & Wong 1996) from stored log ratios: rows of n0 side-0
+// values log(q1/q0)(x), x ~ p0, then n1 side-1 values log(q0/q1)(x), x ~ p1.
+// For the current ratio r_g of each chain group g (index `groups`: all
+// chains), adds A_g = sum over side 0 of 1/(s1 + s0 r_g / l) and B_g = sum
+// over side 1 of 1/(s1 l + s0 r_g), l = q1/q0, into acc[g][0..1]; with
+// geometric != 0 it adds the geometric estimator's sums of sqrt(q1/q0) and
+// sqrt(q0/q1) instead.  Group of a chain: its index within its side mod groups.
+__global__ void __launch_bounds__(256) bridge_sums_kernel(const float* __restrict__ logr, unsigned long long rows,
+                                                          int n0, int n1, int groups, const double* __restrict__ r,
+                                                          double s0, double s1, int geometric,
+                                                          unsigned long long rows_per, int n_chunks,
+                                                          double* __restrict__ acc) {
+  extern __shared__ double sh[];  // [groups + 1][2]
+  for (int i = threadIdx.x; i < 2 * (groups + 1); i += blockDim.x) sh[i] = 0.0;
+  __syncthreads();
+  const int width = n0 + n1;
+  // each thread owns one column (chain) and a range of rows, so its group is
+  // fixed and its sums stay in registers until one shared-memory add
+  const unsigned long long item = blockIdx.x * static_cast<unsigned long long>(blockDim.x) + threadIdx.x;
+  if (item < static_cast<unsigned long long>(width) * n_chunks) {
+    const int j = static_cast<int>(item % width);
+    const unsigned long long chunk = item / width;
+    const bool side0 = j < n0;
+    const int g = (side0 ? j : j - n0) % groups;
+    const double rg = r[g], rall = r[groups];
+    double vg = 0.0, vall = 0.0;
+    const unsigned long long r0 = chunk * rows_per, r1 = min(rows, r0 + rows_per);
+    for (unsigned long long row = r0; row < r1; ++row) {
+      const double lr = static_cast<double>(logr[row * width + j]);
+      if (geometric) {
+        const double v = isfinite(lr) ? exp(0.5 * lr) : 0.0;
+        vg += v;
+      } else if (side0) {
+        const double l = exp(lr);  // q1/q0 at a p0 draw (0 outside T's domain)
+        vg += 1.0 / (s1 + s0 * rg / l);
+        vall += 1.0 / (s1 + s0 * rall / l);
+      } else {
+        const double l = exp(-lr);  // q1/q0 at a p1 draw
+        vg += 1.0 / (s1 * l + s0 * rg);
+        vall += 1.0 / (s1 * l + s0 * rall);
+      }
+    }
+    if (geometric) vall = vg;
+    const int k = side0 ? 0 : 1;
+    atomicAdd(&sh[2 * g + k], vg);
+    atomicAdd(&sh[2 * groups + k], vall);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * (groups + 1); i += blockDim.x)
+    if (sh[i] != 0.0) atomicAdd(&acc[i], sh[i]);
+}
+
+cudaError_t launch_bridge_sums(const float* logr, unsigned long long rows, int n0, int n1, int groups,
+                               const double* r, double s0, double s1, int geometric, double* acc, int n_sm,
+                               cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * 2 * (groups + 1), s);
+  if (e != cudaSuccess) return e;
+  const int width = n0 + n1;
+  if (rows == 0 || width == 0) return cudaSuccess;
+  // about 8 CTAs of 256 threads per SM: split the rows into chunks to get there
+  const unsigned long long want = static_cast<unsigned long long>(n_sm) * 8ull * 256ull;
+  unsigned long long n_chunks = std::max<unsigned long long>(1ull, want / width);
+  n_chunks = std::min<unsigned long long>(n_chunks, rows);
+  const unsigned long long rows_per = (rows + n_chunks - 1) / n_chunks;
+  n_chunks = (rows + rows_per - 1) / rows_per;
+  const unsigned long long threads = n_chunks * width;
+  const unsigned blocks = static_cast<unsigned>((threads + 255) / 256);
+  bridge_sums_kernel<<<blocks, 256, sizeof(double) * 2 * (groups + 1), s>>>(
+      logr, rows, n0, n1, groups, r, s0, s1, geometric, rows_per, static_cast<int>(n_chunks), acc);
   return cudaGetLastError();
 }
 

@@ -105,7 +105,7 @@ def test_yield_logratio_matches_oracle(api, ctx, oracle_lib, name, side):
         assert all(lr[b] == -np.inf for b in bad if n[b] >= 3)
 
 
-def _run_yield(api, ctx, sc, rounds, thin, burn_rounds, tracer_seeds=False):
+def _run_yield(api, ctx, sc, rounds, thin, burn_rounds, tracer_seeds=False, keep_logs=False):
     """Chains of both pairs, observed every `thin` steps after `burn_rounds`.
     With tracer_seeds every chain starts from a weight-thinned tracer path (an
     exact draw from its target), as the paper seeds its chains; direct-path
@@ -115,11 +115,13 @@ def _run_yield(api, ctx, sc, rounds, thin, burn_rounds, tracer_seeds=False):
     ch = api.Chains(ctx, medium, geom, sc.run)
     if tracer_seeds:
         api.seed_from_tracer(ch, seed=4242, photons_per_round=1 << 24)
-    Y = api.YieldRatio(ch, 0, 1)
+    Y = api.YieldRatio(ch, 0, 1, max_obs=rounds if keep_logs else 0)
     for r in range(rounds):
         ch.run_steps(thin)
         if r >= burn_rounds:
             Y.observe()
+    if keep_logs:
+        return Y.estimate(), ch, Y
     return Y.estimate(), ch
 
 
@@ -160,7 +162,7 @@ def test_yield_ratio_matches_tracer_and_oracle(api, ctx, oracle_lib):
     nc = 4096
     sc.pairs = [S.Pair(0, 0, nc, cap), S.Pair(0, 1, nc, cap)]
     sc.run = S.Run(seed=5, burn_in=0, sigma=0.1)
-    est, _ = _run_yield(api, ctx, sc, 600, 25, 5, tracer_seeds=True)
+    est, _, Y = _run_yield(api, ctx, sc, 600, 25, 5, tracer_seeds=True, keep_logs=True)
     medium = api.Medium(ctx, sc.medium)
     geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
     t0 = api.trace(ctx, medium, geom, 0, 11, 400_000_000, max_scatter=cap - 2)
@@ -169,6 +171,10 @@ def test_yield_ratio_matches_tracer_and_oracle(api, ctx, oracle_lib):
     se_t = Bt * math.hypot(t0["se"] / t0["I"], t1["se"] / t1["I"])
     assert abs(est["B"] - Bt) < 3 * math.hypot(est["se"], se_t), (est, Bt, se_t)
     assert est["se"] / est["B"] < 0.01
+    # the optimal bridge on the same observations (Meng & Wong)
+    ob = Y.estimate_bridge(groups=32)
+    assert abs(ob["r"] - Bt) < 3 * math.hypot(ob["se"], se_t), (ob, Bt, se_t)
+    assert abs(ob["geometric"] / est["B"] - 1) < 1e-6  # same draws, same geometric estimate
     # FP64 oracle chains: same estimator, fewer chains
     m, s = O.medium(sc.medium), O.source(sc.sources[0])
     d0, d1 = O.sensor(sc.sensors[0]), O.sensor(sc.sensors[1])
@@ -251,3 +257,24 @@ def test_tracer_length_histogram(api, ctx, oracle_lib):
     for k in range(nb):
         se = math.sqrt(hg[k] / g["photons"] + hr[k] / ref["photons"])
         assert abs(hg[k] - hr[k]) < 4 * se + 1e-12, (k, hg[k], hr[k], se)
+
+
+def test_bridge_ratio_matches_oracle_on_stored_logs(api, ctx, oracle_lib):
+    """The device iteration equals the oracle's on identical stored log ratios."""
+    import torch
+    O = oracle_lib
+    rng = np.random.default_rng(3)
+    rows, n0, n1 = 64, 700, 500
+    x0 = rng.normal(size=(rows, n0))
+    x1 = 1.5 + 0.8 * rng.normal(size=(rows, n1))
+    lq0 = lambda x: -0.5 * x * x  # noqa: E731
+    lq1 = lambda x: math.log(2.0) - 0.5 * ((x - 1.5) / 0.8) ** 2  # noqa: E731
+    L = np.concatenate([lq1(x0) - lq0(x0), lq0(x1) - lq1(x1)], axis=1).astype(np.float32)
+    L[3, 5] = -np.inf  # a draw outside the other density's support
+    g = api.bridge_ratio(ctx, torch.from_numpy(L).cuda(), n0, n1, groups=20, max_iter=300, tol=1e-12)
+    r, se, it, geo = O.optimal_bridge(L[:, :n0].astype(np.float64), L[:, n0:].astype(np.float64), groups=20,
+                                      max_iter=300, tol=1e-12)
+    assert abs(g["r"] / r - 1) < 1e-9, (g, r)
+    assert abs(g["geometric"] / geo - 1) < 1e-9
+    assert abs(g["se"] / se - 1) < 1e-6
+    assert abs(g["r"] - 1.6) < 4 * g["se"]

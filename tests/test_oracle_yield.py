@@ -208,3 +208,63 @@ def test_tracer_length_histogram_sums_to_intensity(oracle_lib):
     assert abs(h.sum() - res["I"]) < 1e-12 * max(res["I"], 1)
     res2, h2 = O.trace_lengths(m, s, d, 3, 200_000, 1.0, 3.0, 8, max_scatter=30)
     assert h2.sum() < res["I"] and (h2 >= 0).all()
+
+
+def _gauss_logratios(n_rows, n0, n1, seed, c=3.0, mu=0.5, sd=1.3):
+    """q0 = exp(-x^2/2), q1 = c exp(-(x - mu)^2 / (2 sd^2)): c1/c0 = c sd."""
+    rng = np.random.default_rng(seed)
+    x0 = rng.normal(size=(n_rows, n0))
+    x1 = mu + sd * rng.normal(size=(n_rows, n1))
+
+    def lq0(x):
+        return -0.5 * x * x
+
+    def lq1(x):
+        return math.log(c) - 0.5 * ((x - mu) / sd) ** 2
+    return lq1(x0) - lq0(x0), lq0(x1) - lq1(x1), c * sd
+
+
+def test_optimal_bridge_recovers_gaussian_ratio(oracle_lib):
+    """Exact draws from two Gaussians of known normalising constants: over 40
+    independent repetitions the estimates centre on c1/c0, their spread
+    matches the reported group standard errors, and each estimate sits at the
+    estimator's fixed point."""
+    O = oracle_lib
+    rs, ses = [], []
+    for seed in range(40):
+        L0, L1, ref = _gauss_logratios(50, 400, 300, 500 + seed)
+        r, se, it, geo = O.optimal_bridge(L0, L1, groups=16)
+        rs.append(r)
+        ses.append(se)
+    rs = np.array(rs)
+    sd = rs.std(ddof=1)
+    assert abs(rs.mean() - ref) < 4 * sd / math.sqrt(len(rs)), (rs.mean(), sd, ref)
+    assert 0.6 < np.mean(ses) / sd < 1.6, (np.mean(ses), sd)
+    s0, s1 = 400 / 700, 300 / 700
+    a = (1.0 / (s1 + s0 * r / np.exp(L0))).mean()
+    b = (1.0 / (s1 * np.exp(-L1) + s0 * r)).mean()
+    assert abs(a / b / r - 1) < 1e-9
+    assert abs(geo / ref - 1) < 0.05
+
+
+def test_optimal_bridge_exact_for_proportional_densities(oracle_lib):
+    """q1 = 2.5 q0: every l equals 2.5 and the estimator returns it exactly."""
+    O = oracle_lib
+    L0 = np.full((7, 5), math.log(2.5))
+    L1 = np.full((7, 4), -math.log(2.5))
+    r, se, it, geo = O.optimal_bridge(L0, L1, groups=2)
+    assert abs(r - 2.5) < 1e-12 and abs(geo - 2.5) < 1e-12
+
+
+def test_optimal_bridge_beats_geometric_on_poor_overlap(oracle_lib):
+    """With little overlap the optimal bridge's spread over independent
+    repetitions is smaller than the geometric estimator's."""
+    O = oracle_lib
+    opt, geo = [], []
+    for seed in range(12):
+        L0, L1, ref = _gauss_logratios(20, 200, 200, 100 + seed, mu=2.5, sd=0.7)
+        r, se, it, g = O.optimal_bridge(L0, L1, groups=4)
+        opt.append(r / ref)
+        geo.append(g / ref)
+    assert np.std(opt) < np.std(geo)
+    assert abs(np.mean(opt) - 1) < 3 * np.std(opt) / math.sqrt(12) + 0.01
