@@ -89,6 +89,8 @@ def parse():
     p.add_argument("--e1-hmc-steps", type=int, default=10, help="leapfrog steps of an HMC move")
     p.add_argument("--e1-sigma", type=float, default=0.0,
                    help="step scale (m for perturb; dimensionless for tree; MALA epsilon); 0 = the scene default")
+    p.add_argument("--e1-cpu-seconds", type=float, default=0.0,
+                   help="also time the FP64 oracle's chains (same moves) on the host cores for about this long")
     p.add_argument("--e1-seed", action="store_true",
                    help="start the chains from weight-thinned tracer paths (exact draws, as the paper seeds its "
                         "chains) instead of straight jittered paths")
@@ -576,10 +578,11 @@ def e1_experiment(args):
             ts = time.perf_counter()
             seed_photons = api.seed_from_tracer(ch, seed=2468, photons_per_round=1 << 28, r_reject=400.0)
             seed_s = time.perf_counter() - ts
-        Y = api.YieldRatio(ch, 0, 1)
-        hist = torch.zeros((2, nb), dtype=torch.float64, device="cuda")
         burn = sc.run.burn_in
         thin = args.e1_thin
+        n_obs = (sc.run.n_steps - burn + thin - 1) // thin
+        Y = api.YieldRatio(ch, 0, 1, max_obs=n_obs)
+        hist = torch.zeros((2, nb), dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
@@ -594,11 +597,13 @@ def e1_experiment(args):
             ch.length_hist(lo, hi, hist)
         ev1.record(stream)
         est = Y.estimate()
+        ob = Y.estimate_bridge(groups=32)
         e = ch.read_estimator()
         wall = time.perf_counter() - t0
         gpu_s = ev0.elapsed_time(ev1) / 1e3
         h = hist.cpu().numpy()
-        row = {"b1": b1, "B": est["B"], "B_se": est["se"], "rhat": [e[0]["rhat"], e[1]["rhat"]],
+        row = {"b1": b1, "B": est["B"], "B_se": est["se"], "B_bridge": ob["r"], "B_bridge_se": ob["se"],
+               "bridge_iterations": ob["iterations"], "rhat": [e[0]["rhat"], e[1]["rhat"]],
                "accept": [e[0]["accept"], e[1]["accept"]], "mean_n": [e[0]["mean_n"], e[1]["mean_n"]],
                "mean_length_m": [e[0]["mean_length"], e[1]["mean_length"]], "observations": Y.n_obs,
                "proposals": 2 * args.e1_chains * sc.run.n_steps, "gpu_seconds": gpu_s, "wall_seconds": wall,
@@ -624,9 +629,25 @@ def e1_experiment(args):
                              "seconds": time.perf_counter() - t1,
                              "length_hist": {"sensor0": (th[0] / max(th[0].sum(), 1e-300)).tolist(),
                                              "sensor1": (th[1] / max(th[1].sum(), 1e-300)).tolist()}}
+        if args.e1_cpu_seconds > 0:
+            import oracle as O
+            ts = time.perf_counter()
+            oc = [O.Chains(sc.medium, sc.sources[0], sc.sensors[k], sc.run, 256, sc.pairs[k].cap, chain_offset=k * 256)
+                  for k in (0, 1)]
+            steps = 0
+            while time.perf_counter() - ts < args.e1_cpu_seconds:
+                for k in (0, 1):
+                    oc[k].run(200)
+                steps += 200
+            cs = time.perf_counter() - ts
+            row["cpu_baseline"] = {"kind": "oracle", "value": 2 * 256 * steps / cs, "unit": "proposals/s",
+                                   "cores": os.cpu_count() or 1,
+                                   "sample": f"2 x 256 chains x the first {steps} steps from the same starts"}
         results.append(row)
-        brief = {k: row[k] for k in ("b1", "within", "B", "B_se", "rhat", "accept", "mean_n", "gpu_seconds",
-                                     "proposals_per_s", "seed_seconds")}
+        brief = {k: row[k] for k in ("b1", "within", "B", "B_se", "B_bridge", "B_bridge_se", "rhat", "accept",
+                                     "mean_n", "gpu_seconds", "proposals_per_s", "seed_seconds")}
+        if "cpu_baseline" in row:
+            brief["cpu_proposals_per_s"] = row["cpu_baseline"]["value"]
         if "tracer" in row:
             brief["tracer_B"] = (row["tracer"]["B"], row["tracer"]["B_se"], row["tracer"]["hits"],
                                  row["tracer"]["seconds"])
@@ -638,7 +659,8 @@ def e1_experiment(args):
         with open(args.e1_out, "w") as f:
             json.dump(out, f)
     print(json.dumps({"experiment": out["experiment"],
-                      "B": [(r["b1"], r["B"], r["B_se"], r.get("tracer", {}).get("B")) for r in results]}),
+                      "B": [(r["b1"], r["B"], r["B_se"], r["B_bridge"], r["B_bridge_se"], r.get("tracer", {}).get("B"))
+                            for r in results]}),
           flush=True)
     return 0
 
