@@ -89,6 +89,9 @@ def parse():
     p.add_argument("--e1-hmc-steps", type=int, default=10, help="leapfrog steps of an HMC move")
     p.add_argument("--e1-sigma", type=float, default=0.0,
                    help="step scale (m for perturb; dimensionless for tree; MALA epsilon); 0 = the scene default")
+    p.add_argument("--e1-ttt", type=float, default=0.0,
+                   help="two-sensor scene: wall time until B reaches this relative error for tree-move chains, "
+                        "Cartesian chains (straight starts and tracer seeds) and the GPU tracer")
     p.add_argument("--e1-cpu-seconds", type=float, default=0.0,
                    help="also time the FP64 oracle's chains (same moves) on the host cores for about this long")
     p.add_argument("--e1-seed", action="store_true",
@@ -665,10 +668,107 @@ def e1_experiment(args):
     return 0
 
 
+def e1_time_to_target(args):
+    """Wall time until the relative light yield B of the two-sensor scene
+    (b1 = first --e1-b1 value) reaches relative standard error --e1-ttt and
+    lies within max(target, 3 combined SE) of a reference from a long
+    tree-move run.  Chains keep running with doubling step budgets (the first
+    10 % of the steps run so far as burn-in is never observed); the tracer
+    doubles its photons.  Each method stops after 120 s."""
+    import torch
+    from paper_1811_04156_gb300 import build as B
+    B.build()
+    from paper_1811_04156_gb300 import api, scenes as S
+    ctx = api.Context(0)
+    b1 = float(args.e1_b1.split(",")[0])
+    tgt = args.e1_ttt
+    limit = 120.0
+
+    def chains_run(within, sigma, n_chains, steps_total, seeded=False, budget0=20_000, thin=200, ref=None):
+        sc = S.e1(b1, n_chains=n_chains, n_steps=steps_total)
+        sc.run.within = within
+        sc.run.sigma = sigma
+        medium = api.Medium(ctx, sc.medium)
+        geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ch = api.Chains(ctx, medium, geom, sc.run)
+        if seeded:
+            api.seed_from_tracer(ch, seed=2468, photons_per_round=1 << 28, r_reject=400.0)
+        done, budget, hist = 0, budget0, []
+        est = None
+        while True:
+            # burn-in: the first 10 % of the final budget, then observe every `thin` steps
+            burn = budget // 10
+            Y = api.YieldRatio(ch, 0, 1)
+            # continue the same chains for `budget` more steps: burn-in, then observations
+            ch.run_steps(burn)
+            k = burn
+            while k < budget:
+                ch.run_steps(thin)
+                k += thin
+                Y.observe()
+            est = Y.estimate()
+            done += budget
+            el = time.perf_counter() - t0
+            hist.append({"steps": done, "seconds": el, "B": est["B"], "se": est["se"]})
+            ok = ref is None or (est["se"] / est["B"] <= tgt and
+                                 abs(est["B"] - ref[0]) <= max(tgt * ref[0], 3 * math.hypot(est["se"], ref[1])))
+            if ref is None and done >= steps_total:
+                break
+            round_s = el - (hist[-2]["seconds"] if len(hist) > 1 else 0.0)
+            if ref is not None and (ok or el + 2.0 * round_s > 1.5 * limit):
+                break
+            budget *= 2
+        ch.close()
+        return {"seconds": time.perf_counter() - t0, "steps_per_chain": done, "chains_per_sensor": n_chains,
+                "B": est["B"], "se": est["se"], "reached": bool(ref is not None and ok), "trace": hist}
+
+    out = {"experiment": "two-sensor scene: time to B within target", "b1": b1, "target_rel_err": tgt}
+    r = chains_run(S.WITHIN_TREE, 0.3, 2048, 400_000, budget0=400_000)
+    ref = (r["B"], r["se"])
+    out["reference"] = {"B": ref[0], "se": ref[1], "seconds": r["seconds"], "how": "tree moves, 2 x 2048 chains x 4e5"}
+    out["tree_moves"] = chains_run(S.WITHIN_TREE, 0.3, 2048, 0, budget0=5_000, ref=ref)
+    out["cartesian_straight_starts"] = chains_run(S.WITHIN_PERTURB, 0.5, 2048, 0, budget0=50_000, ref=ref)
+    out["cartesian_tracer_seeds"] = chains_run(S.WITHIN_PERTURB, 0.5, 1024, 0, seeded=True, budget0=50_000, ref=ref)
+    # GPU tracer: I1/I0 with doubling photon budgets
+    sc = S.e1(b1, n_chains=1)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    cap = sc.pairs[0].cap
+    t0 = time.perf_counter()
+    photons, acc = 1 << 28, [[], []]
+    while True:
+        for p in (0, 1):
+            done = sum(a["photons"] for a in acc[p])
+            acc[p].append(api.trace(ctx, medium, geom, p, 901 + p, photons, photon0=done, r_reject=400.0,
+                                    max_scatter=cap - 2))
+        I, se = [], []
+        for p in (0, 1):
+            Nn = sum(a["photons"] for a in acc[p])
+            I.append(sum(a["I"] * a["photons"] for a in acc[p]) / Nn)
+            se.append(math.sqrt(sum((a["se"] * a["photons"]) ** 2 for a in acc[p])) / Nn)
+        Bt = I[1] / I[0]
+        st = Bt * math.hypot(se[0] / I[0], se[1] / I[1])
+        el = time.perf_counter() - t0
+        ok = st / Bt <= tgt and abs(Bt - ref[0]) <= max(tgt * ref[0], 3 * math.hypot(st, ref[1]))
+        if ok or el > limit:
+            break
+        photons *= 2
+    out["gpu_tracer"] = {"seconds": time.perf_counter() - t0, "photons_per_sensor": sum(a["photons"] for a in acc[0]),
+                         "B": Bt, "se": st, "reached": bool(ok)}
+    out["paper_cpu_seconds"] = {"sampler": E1_PAPER.get(b1, {}).get("sampler_cpu_s"),
+                                "tracer": E1_PAPER.get(b1, {}).get("tracer_cpu_s")}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.time_to_target > 0:
         return time_to_target(args)
+    if args.e1_ttt > 0:
+        return e1_time_to_target(args)
     if args.e1:
         return e1_experiment(args)
     if args.impl == "reference":
