@@ -278,3 +278,34 @@ def test_bridge_ratio_matches_oracle_on_stored_logs(api, ctx, oracle_lib):
     assert abs(g["geometric"] / geo - 1) < 1e-9
     assert abs(g["se"] / se - 1) < 1e-6
     assert abs(g["r"] - 1.6) < 4 * g["se"]
+
+
+def test_chain_length_distribution_matches_tracer(api, ctx):
+    """Section "Comparison of timing distributions" in miniature: the
+    path-length distribution of tracer-seeded chains (observed every 25
+    steps) equals the detected-weight distribution of the GPU tracer, both
+    truncated at the chains' vertex cap."""
+    import torch
+    sc, _ = _two_sensor_scenes()["mini"]
+    cap = 24
+    sc.pairs = [S.Pair(0, 0, 4096, cap), S.Pair(0, 1, 4096, cap)]
+    sc.run = S.Run(seed=17, burn_in=0, sigma=0.1)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    api.seed_from_tracer(ch, seed=99, photons_per_round=1 << 24)
+    lo, hi, nb = 1.0, 9.0, 32
+    hist = torch.zeros((2, nb), dtype=torch.float64, device="cuda")
+    for _ in range(400):
+        ch.run_steps(25)
+        ch.length_hist(lo, hi, hist)
+    h = hist.cpu().numpy()
+    for p in (0, 1):
+        tr, th = api.trace_lengths(ctx, medium, geom, p, 31 + p, 400_000_000, lo, hi, nb, max_scatter=cap - 2)
+        a = np.cumsum(h[p]) / h[p].sum()
+        b = np.cumsum(th) / th.sum()
+        assert np.abs(a - b).max() < 0.01, (p, np.abs(a - b).max())
+        centres = lo + (np.arange(nb) + 0.5) * (hi - lo) / nb
+        mc = (centres * h[p]).sum() / h[p].sum()
+        mt = (centres * th).sum() / th.sum()
+        assert abs(mc / mt - 1) < 0.005, (p, mc, mt)
