@@ -61,7 +61,7 @@ class Run(C.Structure):
                 ("p_death", C.c_double), ("within", C.c_int), ("sigma", C.c_double),
                 ("mala_step", C.c_double), ("kappa_end", C.c_double), ("burn_in", C.c_uint64),
                 ("thin_bridge", C.c_uint32), ("gradients", C.c_int), ("beta_min", C.c_double),
-                ("hmc_steps", C.c_int)]
+                ("hmc_steps", C.c_int), ("toy_s", C.c_double), ("toy_w", C.POINTER(C.c_double))]
 
 
 class Acc(C.Structure):

@@ -794,6 +794,27 @@ static void record_state(const chain_job* J, or_acc* a, int n, const double* f, 
   }
 }
 
+/* The chains' target: the path density, or (toy_s > 0, pins only) a product
+ * density with known sector weights: P(n) proportional to toy_w[n], interior
+ * vertex k of an n-vertex path ~ N(mu_k, toy_s^2 I) with mu_k on the segment
+ * from the source to the sensor centre at fraction k/(n-1), and the end
+ * vertex uniform on the sensor sphere. */
+static double target_logp(const chain_job* J, int n, const double* f) {
+  const or_run* r = J->r;
+  if (!(r->toy_s > 0.0)) return or_logp(J->m, J->s, J->d, n, f);
+  double lp = log(r->toy_w[n]) - log(4.0 * M_PI * J->d->R * J->d->R);
+  double s2 = r->toy_s * r->toy_s;
+  for (int k = 1; k <= n - 2; ++k) {
+    double fr = (double)k / (double)(n - 1);
+    for (int i = 0; i < 3; ++i) {
+      double mu = J->s->pos[i] + fr * (J->d->c[i] - J->s->pos[i]);
+      double dlt = f[3 * k + i] - mu;
+      lp += -0.5 * dlt * dlt / s2 - 0.5 * log(2.0 * M_PI * s2);
+    }
+  }
+  return lp;
+}
+
 static void* chain_worker(void* arg) {
   chain_job* J = (chain_job*)arg;
   const or_medium* m = J->m;
@@ -808,7 +829,7 @@ static void* chain_worker(void* arg) {
     int n = J->n[c];
     uint32_t chain = J->chain_offset + (uint32_t)c;
     or_acc* a = J->acc ? &J->acc[c] : NULL;
-    double lpx = or_logp(m, J->s, J->d, n, x);
+    double lpx = target_logp(J, n, x);
     double margin = INFINITY;
     for (uint64_t t = J->step0; t < J->step0 + J->n_steps; ++t) {
       uint32_t A[4], B[4];
@@ -916,7 +937,7 @@ static void* chain_worker(void* arg) {
             double nn = w * nu[i] + sw * (cos(ph) * e1[i] + sin(ph) * e2[i]);
             y[3 * j + i] = J->d->c[i] + J->d->R * nn;
           }
-          lpy = or_logp(m, J->s, J->d, n, y);
+          lpy = target_logp(J, n, y);
           logA = lpy - lpx;
         } else {
           kind = OR_MOVE_INTERIOR;
@@ -943,7 +964,7 @@ static void* chain_worker(void* arg) {
             }
           } else {
             for (int i = 0; i < 3; ++i) y[3 * j + i] = x[3 * j + i] + r->sigma * z[i];
-            lpy = or_logp(m, J->s, J->d, n, y);
+            lpy = target_logp(J, n, y);
             logA = lpy - lpx;
           }
         }
@@ -978,7 +999,7 @@ static void* chain_worker(void* arg) {
             copy3(fnew, y + 3 * (k + 1));
             memcpy(y + 3 * (k + 2), x + 3 * (k + 1), sizeof(double) * 3 * (n - k - 1));
             ny = n + 1;
-            lpy = or_logp(m, J->s, J->d, ny, y);
+            lpy = target_logp(J, ny, y);
             double lq = log_insert_density(m, r, J->kappa_eq, fk, fk1, fnew);
             logA = lpy - lpx + log(r->p_death) - log((double)(ny - 2)) - log(r->p_birth) -
                    log(tbs[k] / T) - lq;
@@ -992,7 +1013,7 @@ static void* chain_worker(void* arg) {
           memcpy(y, x, sizeof(double) * 3 * j);
           memcpy(y + 3 * j, x + 3 * (j + 1), sizeof(double) * 3 * (n - j - 1));
           ny = n - 1;
-          lpy = or_logp(m, J->s, J->d, ny, y);
+          lpy = target_logp(J, ny, y);
           double T = log_sum_tb(m, ny, y, tbs);
           double lq = log_insert_density(m, r, J->kappa_eq, x + 3 * (j - 1), x + 3 * (j + 1), x + 3 * j);
           /* reverse birth y -> x selects segment j-1 of y and inserts x_j */

@@ -69,6 +69,8 @@ typedef struct {
   int gradients;            /* accumulate score terms */
   double beta_min;          /* lower clamp of the insertion concentration */
   int hmc_steps;            /* OR_WITHIN_HMC: leapfrog steps of size mala_step */
+  double toy_s;             /* > 0: sample the pins' toy target instead of the path density */
+  const double* toy_w;      /* toy sector weights, indexed by vertex count (cap + 1 entries) */
 } or_run;
 
 /* Per-chain accumulators (FP64 sums over recorded states). */

@@ -333,3 +333,34 @@ def test_counter_based_resume_is_exact(oracle_lib):
     b.run(1000)
     b.run(2000)
     assert np.array_equal(a.n, b.n) and np.array_equal(a.xyz, b.xyz)
+
+
+def test_dimension_jumps_balance_a_toy_target(oracle_lib):
+    """Detailed balance of the birth/death machinery on its own: the chains'
+    moves (Gaussian steps, vMF end steps, tau_b-weighted births by bispherical
+    insertion, uniform deaths, Green's acceptance) run on a product target
+    with known sector weights -- P(n) proportional to w_n, interior vertices
+    ~ N(mu_k, s^2 I), the end vertex uniform on the sensor -- and the visited
+    vertex counts reproduce w_n / sum w.  A missing reverse-move factor, a
+    wrong Jacobian or a transposed birth/death ratio shifts P(n) by factors
+    of order (n - 2)/(n - 1) or more."""
+    import ctypes as C
+    O = oracle_lib
+    cap = 6
+    w = np.zeros(cap + 1)
+    w[2:] = [1.0, 2.0, 1.5, 0.7, 0.3]
+    sc = S.plain()
+    sc.run.burn_in = 2000
+    ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, cap)
+    ch.r.toy_s = 0.1
+    ch.r.toy_w = w.ctypes.data_as(C.POINTER(C.c_double))
+    H = np.zeros((64, cap + 1))
+    ch.run(100_000, n_hist=H)
+    P = H / H.sum(axis=1, keepdims=True)
+    mean, se = P.mean(axis=0), P.std(axis=0, ddof=1) / math.sqrt(64)
+    ref = w / w.sum()
+    for n in range(2, cap + 1):
+        assert abs(mean[n] - ref[n]) < 4 * se[n], (n, mean[n], ref[n], se[n])
+    assert np.abs(mean - ref).max() < 0.01
+    acc = ch.accumulators()
+    assert acc["acc"][:, 2].sum() > 0.05 * acc["prop"][:, 2].sum()  # births are accepted often enough
