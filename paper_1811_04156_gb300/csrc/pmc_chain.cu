@@ -435,6 +435,9 @@ __device__ __forceinline__ void tree_node_of(int m, int n, int& k, int& l, int& 
   }
 }
 
+// Transcendentals here use the SFU forms (a few ulp): the map only has to be
+// the same deterministic bijection in both directions up to rounding, far
+// below the Monte-Carlo error, as for the density in the chain kernel.
 // One whole-path tree proposal: the end vertex goes to `end`, every node's
 // coordinates step by `step` times its normals; the new path is built level
 // by level into nx/ny/nz.  Returns log p(x') + log J(x') - log J(x)
@@ -462,18 +465,18 @@ __device__ float tree_propose(const DMedium& M, const DPair& S, float zoff, cons
     const float3 up = u + v, um = u - v;
     const float opc = 0.5f * dot(up, up), omc = 0.5f * dot(um, um);
     const float3 rho = P - Fo.mid;
-    lj -= 3.0f * logf(d1 * d2 / (2.0f * Fo.gamma)) + logf(opc * omc);
+    lj -= 3.0f * __logf(d1 * d2 / (2.0f * Fo.gamma)) + __logf(opc * omc);
     // normal steps (the oracle's draw: Box-Muller on one Philox block)
     const uint4 rn = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32),
                                               static_cast<uint32_t>(c), PUR_TREE | (static_cast<uint32_t>(m) << 8)),
                                    key0, key1);
     float s1, c1, s2, c2;
-    const float r1 = sqrtf(-2.0f * logf(u01(rn.x)));
+    const float r1 = sqrtf(-2.0f * __logf(u01(rn.x)));
     sincospif(2.0f * u01(rn.y), &s1, &c1);
-    const float r2 = sqrtf(-2.0f * logf(u01(rn.z)));
+    const float r2 = sqrtf(-2.0f * __logf(u01(rn.z)));
     sincospif(2.0f * u01(rn.w), &s2, &c2);
-    nx[m] = fmaf(step, r1 * c1, 0.5f * logf(opc / omc));
-    ny[m] = fmaf(step, r1 * s1, logf(d1 / d2));
+    nx[m] = fmaf(step, r1 * c1, 0.5f * __logf(__fdividef(opc, omc)));
+    ny[m] = fmaf(step, r1 * s1, __logf(__fdividef(d1, d2)));
     nz[m] = fmaf(step, r2 * c2, atan2f(dot(rho, Fo.eta), dot(rho, Fo.xi)));
   }
   if (lane == 0) {
@@ -494,19 +497,21 @@ __device__ float tree_propose(const DMedium& M, const DPair& S, float zoff, cons
         const int m = (k + l) >> 1;
         const float zeta = nx[m], tt = ny[m], phi = nz[m];
         const TreeFrame Fn = tree_frame(npos, k, l, kp, lp, vref);
-        const float ez = expf(zeta), emz = expf(-zeta);
+        const float ez = __expf(zeta), emz = __expf(-zeta);
         const float sn = 2.0f / (ez + emz);                 // 1 / cosh zeta = sin s
         const float omcs = 2.0f / (1.0f + ez * ez);          // 1 - tanh zeta
-        const float sh = sinhf(0.5f * tt);
+        const float eh = __expf(0.5f * tt), ieh = __expf(-0.5f * tt);
+        const float sh = 0.5f * (eh - ieh);                 // sinh(t/2)
         const float den = fmaf(2.0f * sh, sh, omcs);        // cosh t - cos s
         float sp, cp;
-        sincosf(phi, &sp, &cp);
+        __sincosf(phi, &sp, &cp);
         const float sc = Fn.gamma / den;
-        const float3 fnew = Fn.mid + sc * (sinhf(tt) * Fn.e + sn * (cp * Fn.xi + sp * Fn.eta));
+        const float sht = 2.0f * sh * (0.5f * (eh + ieh));    // sinh t = 2 sinh(t/2) cosh(t/2)
+        const float3 fnew = Fn.mid + sc * (sht * Fn.e + sn * (cp * Fn.xi + sp * Fn.eta));
         nx[m] = fnew.x;
         ny[m] = fnew.y;
         nz[m] = fnew.z;
-        lj += 3.0f * logf(sc) + 2.0f * logf(sn);
+        lj += 3.0f * __logf(sc) + 2.0f * __logf(sn);
       }
     }
     __syncwarp();
@@ -579,9 +584,9 @@ __device__ float hmc_propose(const DMedium& M, const DPair& S, float zoff, const
                                                 static_cast<uint32_t>(c), PUR_HMC | (static_cast<uint32_t>(i) << 8)),
                                      key0, key1);
       float s1, c1, s2, c2;
-      const float r1 = sqrtf(-2.0f * logf(u01(rn.x)));
+      const float r1 = sqrtf(-2.0f * __logf(u01(rn.x)));
       sincospif(2.0f * u01(rn.y), &s1, &c1);
-      const float r2 = sqrtf(-2.0f * logf(u01(rn.z)));
+      const float r2 = sqrtf(-2.0f * __logf(u01(rn.z)));
       sincospif(2.0f * u01(rn.w), &s2, &c2);
       mx[i] = r1 * c1;
       my[i] = r1 * s1;
