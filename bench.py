@@ -457,7 +457,9 @@ def time_to_target(args):
     """Wall time until the intensity estimate reaches the target relative
     standard error and lies within max(target, 3 SE) of a reference value from
     a long forward-tracer run, for (a) plain RJMCMC (64 chains, Gaussian
-    steps), (b) batched MALA chains (65,536), (c) the GPU forward tracer.
+    steps), (b) batched MALA chains (65,536), with and without tracer seeds,
+    batched Gaussian chains with seeds and batched tree-move chains from the
+    direct path, (c) the GPU forward tracer.
     Budgets double until the criterion holds or 120 s have passed."""
     import torch
     from paper_1811_04156_gb300 import build as B
@@ -495,6 +497,8 @@ def time_to_target(args):
         sc.run.burn_in = 0 if seeded else (1000 if geom_name == "plain" else 10_000)
         if within == S.WITHIN_MALA:
             sc.run.mala_step = 0.02 if geom_name == "plain" else 0.5
+        if within == S.WITHIN_TREE:
+            sc.run.sigma = 0.3
         geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
         ch = api.Chains(ctx, med, geom, sc.run)
         torch.cuda.synchronize()
@@ -519,6 +523,7 @@ def time_to_target(args):
     out["batched_mala"] = run_chains(65_536, S.WITHIN_MALA, 2_000)
     out["batched_mala_tracer_seeded"] = run_chains(65_536, S.WITHIN_MALA, 500, seeded=True)
     out["batched_perturb_tracer_seeded"] = run_chains(65_536, S.WITHIN_PERTURB, 500, seeded=True)
+    out["batched_tree_moves"] = run_chains(65_536, S.WITHIN_TREE, 2_000)
     # tracer with doubling photon budgets
     t = time.perf_counter()
     photons, acc = 1_000_000, []
