@@ -402,7 +402,7 @@ PMC_API int pmc_bridge(pmc_chains_t chains, uint64_t n_draws, uint64_t seed, dou
  * log p(T^-1 y; pair0) - log|dT/dx| at T^-1 y - log p(y; pair1).  -inf outside
  * T's domain or where either density is 0; NaN when n is outside [2, cap].
  * out_xyz (device, same layout as xyz, may be NULL) receives the mapped paths.
- * Asynchronous on `stream`. */
+ * batch = 0 is a no-op (the buffers may then be NULL).  Asynchronous on `stream`. */
 PMC_API int pmc_yield_logratio(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair0, int pair1, int side,
                                const float* xyz, const int* n, int batch, int cap, float* out, float* out_xyz,
                                void* stream);

@@ -1354,7 +1354,8 @@ static int make_ymap(pmc_geom_t g, int pair0, int pair1, bool source_frame, DYMa
 
 int pmc_yield_logratio(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair0, int pair1, int side,
                        const float* xyz, const int* n, int batch, int cap, float* out, float* out_xyz, void* stream) {
-  if (!ctx || !med || !geom || !xyz || !n || !out) return fail(PMC_ERR_INVALID, "bad argument");
+  if (!ctx || !med || !geom) return fail(PMC_ERR_INVALID, "bad argument");
+  if (batch > 0 && (!xyz || !n || !out)) return fail(PMC_ERR_INVALID, "bad argument");
   if (side != 0 && side != 1) return fail(PMC_ERR_INVALID, "side must be 0 or 1");
   if (batch < 0 || cap < 2 || cap > (1 << 20)) return fail(PMC_ERR_INVALID, "bad batch or cap");
   DYMap T;

@@ -93,8 +93,9 @@ def test_tree_and_hmc_settings_are_checked(api, ctx):
         api.Chains(ctx, medium, geom, S.Run(seed=1, within=S.WITHIN_HMC, mala_step=0.01, hmc_steps=0))
     with pytest.raises(PathmcError):  # HMC needs a step size
         api.Chains(ctx, medium, geom, S.Run(seed=1, within=S.WITHIN_HMC, mala_step=0.0))
+    geom64 = api.Geometry(ctx, [S.Source()], [S.Sensor((0.0, 0.0, 1.5), 0.3)], [S.Pair(0, 0, 32, 64)])
     with pytest.raises(PathmcError):  # tree moves keep the whole cap in shared memory
-        api.Chains(ctx, medium, geom, S.Run(seed=1, within=S.WITHIN_TREE, sigma=0.3), smem_window=32,
+        api.Chains(ctx, medium, geom64, S.Run(seed=1, within=S.WITHIN_TREE, sigma=0.3), smem_window=32,
                    warps_per_block=1)
     with pytest.raises(PathmcError):
         api.Chains(ctx, medium, geom, S.Run(seed=1, within=7))
