@@ -105,3 +105,30 @@ def test_tree_chains_match_tracer(api, ctx):
     tr = api.trace(ctx, medium, geom, 0, 7, 400_000_000, max_scatter=cap - 2)
     assert abs(e["intensity"] - tr["I"]) < 3 * math.hypot(e["std_err"], tr["se"]), (e, tr)
     assert e["rel_err"] < 0.01
+
+
+@pytest.mark.parametrize("b1", [0.1, 0.3, 0.5])
+def test_paper_table_relative_yield(api, ctx, b1):
+    """The paper's worked example (Table tbl:results, tests/golden): B of the
+    two-sensor scene from tree-move chains started on straight paths agrees
+    with the paper's ray-tracer value within three combined uncertainties
+    (the printed tracer uncertainty and our standard error)."""
+    import os
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "paper_relative_yield.txt"))
+    row = rows[np.isclose(rows[:, 0], b1)][0]
+    sc = S.e1(b1, n_chains=1024, n_steps=120_000)
+    sc.run.within = S.WITHIN_TREE
+    sc.run.sigma = 0.3
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    ch.run_steps(sc.run.burn_in)
+    Y = api.YieldRatio(ch, 0, 1)
+    for _ in range((sc.run.n_steps - sc.run.burn_in) // 400):
+        ch.run_steps(400)
+        Y.observe()
+    est = Y.estimate()
+    assert abs(est["B"] - row[1]) < 3 * math.hypot(row[2], est["se"]), (b1, est, row)
+    assert est["se"] < 0.01
+    e = ch.read_estimator()
+    assert max(e[0]["rhat"], e[1]["rhat"]) < 1.3
