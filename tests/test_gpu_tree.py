@@ -107,16 +107,18 @@ def test_tree_chains_match_tracer(api, ctx):
     assert e["rel_err"] < 0.01
 
 
-@pytest.mark.parametrize("b1", [0.1, 0.3, 0.5])
-def test_paper_table_relative_yield(api, ctx, b1):
+@pytest.mark.parametrize("b1,steps", [(0.1, 120_000), (0.3, 200_000), (0.5, 400_000)])
+def test_paper_table_relative_yield(api, ctx, b1, steps):
     """The paper's worked example (Table tbl:results, tests/golden): B of the
     two-sensor scene from tree-move chains started on straight paths agrees
     with the paper's ray-tracer value within three combined uncertainties
-    (the printed tracer uncertainty and our standard error)."""
+    (the printed tracer uncertainty and our standard error).  Longer paths
+    (larger b1) need longer runs to forget the straight starts: at b1 = 0.5
+    1.2e5 steps still leave B at 0.52."""
     import os
     rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "paper_relative_yield.txt"))
     row = rows[np.isclose(rows[:, 0], b1)][0]
-    sc = S.e1(b1, n_chains=1024, n_steps=120_000)
+    sc = S.e1(b1, n_chains=1024, n_steps=steps)
     sc.run.within = S.WITHIN_TREE
     sc.run.sigma = 0.3
     medium = api.Medium(ctx, sc.medium)
