@@ -408,15 +408,18 @@ def ours(args):
         peak, peak_from = peak_measured, "measured (above the unit count)"
     clk = (clocks or {}).get("sm_mhz") or sm_mhz
     li = chains.launch_info()
-    same_shape = len(li) == 1 and li[0]["warps_per_block"] == 2 and li[0]["smem_cap"] == sc.pairs[0].cap
+    # warp instructions per proposal depend on the kernel and the workload, not
+    # on how many chains share a CTA: any shape of the lean kernel with the whole
+    # cap in shared memory runs the captured instruction stream
+    same_shape = len(li) == 1 and li[0]["general"] == 0 and li[0]["smem_cap"] == sc.pairs[0].cap
     inst = WARP_INST_PER_PROPOSAL.get(sc.name) if same_shape else None
     issue = None
     if inst is not None:
         issue_peak = ISSUE_PER_CLK_PER_SM * n_sm * clk * 1e6
         issue = {"achieved": rate * inst, "peak": issue_peak, "unit": "warp instructions/s",
                  "frac": rate * inst / issue_peak, "inst_per_proposal": inst,
-                 "source": "instructions per proposal from the committed ncu capture of this kernel and launch "
-                           "shape; peak = 4 warp instructions/clk/SM x SMs x median SM clock under load"}
+                 "source": "instructions per proposal from the committed ncu capture of this kernel and workload; "
+                           "peak = 4 warp instructions/clk/SM x SMs x median SM clock under load"}
     # DRAM traffic of one launch: ncu capture of 16,384 chains (8.9 MB), scaled by chains
     traffic = 8.9e6 * n_chains / 16384.0 if sc.name == "detector" else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
