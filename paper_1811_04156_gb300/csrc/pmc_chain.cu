@@ -544,10 +544,11 @@ __device__ __forceinline__ bool hmc_path_valid(const DPair& S, const float* nx, 
   bool ok = true;
   for (int k = lane; k <= n - 2; k += 32) {
     const float3 P = f3(nx[k], ny[k], nz[k]);
-    const float3 r = f3(nx[k + 1], ny[k + 1], nz[k + 1]) - P;
+    const float3 Q = f3(nx[k + 1], ny[k + 1], nz[k + 1]);
+    const float3 r = Q - P;
     if (!(dot(r, r) > 0.f)) ok = false;
     else if (k <= n - 3) ok = ok && !hits_ball<true>(S, P, r);
-    else ok = ok && (-dot(r, sensor_normal(S, P + r)) > 0.f);
+    else ok = ok && (-dot(r, sensor_normal(S, Q)) > 0.f);
   }
   return __all_sync(0xffffffffu, ok);
 }
