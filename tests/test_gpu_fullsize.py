@@ -96,3 +96,41 @@ def test_full_size_run_health_and_densities(api, ctx, oracle_lib):
         ref = O.logp(m, s, d, batch[:, b, :k].T.astype(np.float64))
         assert np.isfinite(ref)
         assert abs(lp[b] - ref) <= 1e-5 + 2e-6 * k, (c, k, lp[b], ref)
+
+
+@pytest.mark.parametrize("name", ["batched", "layered"])
+def test_full_size_multi_pair_launch_replays_sampled_chains(api, ctx, oracle_lib, name):
+    """The batched workload (4,096 pairs, ~1.08 M chains, caps 64-1,024 in
+    four classes, long classes with a shared window and global spill) and the
+    layered one (60 sensors x 8,192 chains, cap 1,024, general kernel) at full
+    size: 64 chains sampled across all pairs replay the oracle for 1,000 steps."""
+    O = oracle_lib
+    steps = 1000
+    sc = S.batched(n_steps=steps) if name == "batched" else S.layered(n_steps=steps)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    ch.run_steps(steps)
+    assert ch.status() == 0
+    xyz, n, st = ch.read_states()
+    acc = ch.read_accumulators()
+    total = sum(p.n_chains for p in sc.pairs)
+    starts = np.cumsum([0] + [p.n_chains for p in sc.pairs])
+    rng = np.random.default_rng(1)
+    sample = rng.choice(total, size=64, replace=False)
+    clean = 0
+    for c in sample:
+        p = int(np.searchsorted(starts, c, side="right") - 1)
+        pr = sc.pairs[p]
+        oc = O.Chains(sc.medium, sc.sources[pr.source], sc.sensors[pr.sensor], sc.run, 1, pr.cap,
+                      chain_offset=int(c))
+        margin = oc.run(steps, margins=True)
+        if not margin[0] > 1e-3:
+            continue
+        clean += 1
+        k = int(n[c])
+        assert k == oc.n[0], (c, p, k, oc.n[0])
+        assert np.allclose(xyz[c, :, :k].T, oc.xyz[0, :k], atol=5e-4), (c, p)
+        oa = oc.accumulators()
+        assert np.array_equal(acc[c, 8:12], oa["prop"][0]) and np.array_equal(acc[c, 12:16], oa["acc"][0])
+    assert clean >= 16, clean
