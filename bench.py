@@ -92,6 +92,8 @@ def parse():
     p.add_argument("--e1-ttt", type=float, default=0.0,
                    help="two-sensor scene: wall time until B reaches this relative error for tree-move chains, "
                         "Cartesian chains (straight starts and tracer seeds) and the GPU tracer")
+    p.add_argument("--e1-grad", action="store_true",
+                   help="also observe the per-layer scores: d log B / d theta and d log B / d b1")
     p.add_argument("--e1-cpu-seconds", type=float, default=0.0,
                    help="also time the FP64 oracle's chains (same moves) on the host cores for about this long")
     p.add_argument("--e1-seed", action="store_true",
@@ -562,6 +564,7 @@ def e1_experiment(args):
     length histograms observed every --e1-thin steps; optionally I_1/I_0 and
     the length histograms of the GPU forward tracer (rejection radius 400 m,
     scatterings capped at the chains' vertex cap)."""
+    import numpy as np
     import torch
     from paper_1811_04156_gb300 import build as B
     B.build()
@@ -594,6 +597,9 @@ def e1_experiment(args):
         n_obs = (sc.run.n_steps - burn + thin - 1) // thin
         Y = api.YieldRatio(ch, 0, 1, max_obs=n_obs)
         hist = torch.zeros((2, nb), dtype=torch.float64, device="cuda")
+        nth = medium.n_theta
+        ssum = torch.zeros((2, 2 * nth), dtype=torch.float64, device="cuda") if args.e1_grad else None
+        sobs = []
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
@@ -606,6 +612,9 @@ def e1_experiment(args):
             done += k
             Y.observe()
             ch.length_hist(lo, hi, hist)
+            if ssum is not None:
+                ch.score_observe(ssum)
+                sobs.append(ssum[:, :nth].clone())
         ev1.record(stream)
         est = Y.estimate()
         ob = Y.estimate_bridge(groups=32)
@@ -624,6 +633,18 @@ def e1_experiment(args):
                "init": "tracer seeds" if args.e1_seed else "straight, 30 interior vertices, N(0, 0.5 m) jitter",
                "within": args.e1_within, "sigma": sc.run.sigma, "mala_step": sc.run.mala_step,
                "seed_seconds": seed_s, "seed_photons": seed_photons, "paper": E1_PAPER.get(b1)}
+        if ssum is not None:
+            # per-observation mean scores of each sensor's chains, then batch means over 20 batches
+            cum = torch.stack(sobs).cpu().numpy()                        # (obs, 2, nth) running sums
+            per = np.diff(np.concatenate([np.zeros_like(cum[:1]), cum]), axis=0) / args.e1_chains
+            d = per[:, 1, :] - per[:, 0, :]                               # d log B / d theta per observation
+            nbat = 20
+            bm = np.array([b.mean(axis=0) for b in np.array_split(d, nbat)])
+            g, gse = d.mean(axis=0), bm.std(axis=0, ddof=1) / math.sqrt(nbat)
+            lam1 = 1.0 / b1                                               # layer 1 = the x >= 0 half-space
+            row["dlogB_dtheta"] = {"theta": "lambda_s[0], lambda_s[1], lambda_a[0], lambda_a[1] (m)",
+                                   "value": g.tolist(), "se": gse.tolist()}
+            row["dlogB_db1"] = {"value": float(-lam1 * lam1 * g[1]), "se": float(lam1 * lam1 * gse[1])}
         if args.e1_photons > 0:
             cap = sc.pairs[0].cap
             tr, th = [], []
@@ -659,6 +680,8 @@ def e1_experiment(args):
                                      "mean_n", "gpu_seconds", "proposals_per_s", "seed_seconds")}
         if "cpu_baseline" in row:
             brief["cpu_proposals_per_s"] = row["cpu_baseline"]["value"]
+        if "dlogB_db1" in row:
+            brief["dlogB_db1"] = row["dlogB_db1"]
         if "tracer" in row:
             brief["tracer_B"] = (row["tracer"]["B"], row["tracer"]["B_se"], row["tracer"]["hits"],
                                  row["tracer"]["seconds"])

@@ -442,6 +442,17 @@ PMC_API int pmc_yield_observe_log(pmc_chains_t chains, int pair0, int pair1, flo
 PMC_API int pmc_bridge_ratio(pmc_ctx_t ctx, const float* logr, uint64_t rows, int n0, int n1, int groups,
                              int max_iter, double tol, double* out, void* stream);
 
+/* One observation of the score d log p / d theta at every chain's current
+ * path, layered media only (theta = (lambda_s[0..L), lambda_a[0..L))):
+ * sums[pair][j] += score_j and sums[pair][2L + j] += score_j^2, j < 2L.
+ * sums: device, caller-owned, n_pairs * 4L doubles, zeroed by the caller.
+ * With n_obs observations of N chains, E_p[score] = sums / (N n_obs); the
+ * difference of two pairs' means is d log(I_1 / I_0) / d theta, the
+ * gradient of the relative light yield (calibration of the medium from
+ * detector ratios).  Homogeneous media accumulate their scores while
+ * stepping (pmc_grad_estimator).  Asynchronous on `stream`. */
+PMC_API int pmc_score_observe(pmc_chains_t chains, double* sums, void* stream);
+
 /* Path-length distribution of the chains: one observation of every chain,
  * hist[pair][bin] += 1 with bin = floor((L - l_lo) / (l_hi - l_lo) * n_bins)
  * for its current path length L in [l_lo, l_hi) (others are not counted).

@@ -127,6 +127,7 @@ PROTOTYPES = {
     "pmc_yield_observe_log": ([_vp, C.c_int, C.c_int, _vp, _vp], C.c_int),
     "pmc_bridge_ratio": ([_vp, _vp, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _vp], C.c_int),
     "pmc_length_hist": ([_vp, C.c_double, C.c_double, C.c_int, _vp, _vp], C.c_int),
+    "pmc_score_observe": ([_vp, _vp, _vp], C.c_int),
     "pmc_trace_lengths": ([_vp, _vp, _vp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int,
                            C.c_double, C.c_double, C.c_int, _dp, _dp, _vp], C.c_int),
     "pmc_measure_pipes": ([_vp, _dp, _vp], C.c_int),

@@ -258,6 +258,16 @@ class Chains:
         check(load().pmc_yield_observe_log(self.handle, int(pair0), int(pair1), C.c_void_p(row.data_ptr()),
                                            _stream(stream)), "pmc_yield_observe_log")
 
+    def score_observe(self, sums: torch.Tensor, stream=None):
+        """One observation of d log p / d theta at every chain's current path
+        into sums (n_pairs, 4 L): per-layer scores then their squares
+        (pmc_score_observe; layered media)."""
+        _require_cuda(sums, torch.float64, "sums")
+        if sums.dim() != 2 or sums.shape[0] != self.n_pairs or sums.shape[1] != 2 * self.medium.n_theta:
+            raise ValueError("sums must have shape (n_pairs, 2 n_theta)")
+        check(load().pmc_score_observe(self.handle, C.c_void_p(sums.data_ptr()), _stream(stream)),
+              "pmc_score_observe")
+
     def length_hist(self, l_lo: float, l_hi: float, hist: torch.Tensor, stream=None):
         """One observation of every chain's path length into hist (n_pairs, n_bins) (pmc_length_hist)."""
         _require_cuda(hist, torch.float64, "hist")

@@ -1480,6 +1480,16 @@ int pmc_yield_estimate(pmc_chains_t ch, int pair0, int pair1, const double* sums
   return PMC_OK;
 }
 
+int pmc_score_observe(pmc_chains_t ch, double* sums, void* stream) {
+  if (ch == nullptr || sums == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (ch->med->d.kind != PMC_LAYERED)
+    return fail(PMC_ERR_INVALID, "pmc_score_observe needs a layered medium (homogeneous media: pmc_grad_estimator)");
+  CK(cudaSetDevice(ch->ctx->device));
+  CK(launch_layer_scores(ch->med->d, ch->d_pairs, ch->d_chain_pair, ch->d_chain_base, ch->d_xyz, ch->d_n, ch->total,
+                         sums, static_cast<cudaStream_t>(stream)));
+  return PMC_OK;
+}
+
 int pmc_length_hist(pmc_chains_t ch, double l_lo, double l_hi, int n_bins, double* hist, void* stream) {
   if (ch == nullptr || hist == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
   if (!(l_hi > l_lo) || !std::isfinite(l_lo) || !std::isfinite(l_hi) || n_bins < 1)

@@ -309,3 +309,32 @@ def test_chain_length_distribution_matches_tracer(api, ctx):
         mc = (centres * h[p]).sum() / h[p].sum()
         mt = (centres * th).sum() / th.sum()
         assert abs(mc / mt - 1) < 0.005, (p, mc, mt)
+
+
+def test_score_observe_matches_per_path_scores(api, ctx):
+    """pmc_score_observe sums, per pair, the per-layer scores of the chains'
+    current paths: the same sums as pmc_score on those paths (read back and
+    evaluated as a caller batch)."""
+    import torch
+    sc, _ = _two_sensor_scenes()["mini"]
+    sc.pairs = [S.Pair(0, 0, 256, 24), S.Pair(0, 1, 300, 24)]
+    sc.run = S.Run(seed=21, burn_in=0, sigma=0.1, init=S.INIT_STRAIGHT, init_k=4, init_jitter=0.05)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    ch = api.Chains(ctx, medium, geom, sc.run)
+    ch.run_steps(500)
+    nth = medium.n_theta
+    sums = torch.zeros((2, 2 * nth), dtype=torch.float64, device="cuda")
+    ch.score_observe(sums)
+    got = sums.cpu().numpy()
+    xyz, n, _ = ch.read_states()
+    c0 = 0
+    for p, pr in enumerate(sc.pairs):
+        sl = slice(c0, c0 + pr.n_chains)
+        c0 += pr.n_chains
+        batch = np.ascontiguousarray(xyz[sl, :, :24].transpose(1, 0, 2))
+        sco = api.score(ctx, medium, geom, p, torch.from_numpy(batch).cuda(),
+                        torch.from_numpy(n[sl].astype(np.int32)).cuda()).cpu().numpy().astype(np.float64)
+        ref = sco.sum(axis=0)
+        assert np.allclose(got[p, :nth], ref, rtol=2e-3, atol=1e-3 * np.abs(sco).max()), (p, got[p, :nth], ref)
+        assert np.allclose(got[p, nth:], (sco ** 2).sum(axis=0), rtol=5e-3, atol=1e-3 * (sco ** 2).max())
