@@ -74,29 +74,29 @@ def parse():
                    help="instead of the throughput line: wall time to this relative intensity error for plain "
                         "RJMCMC, batched MALA chains and the GPU forward tracer on the plain / detector geometry")
     p.add_argument("--geometry", default="plain", help="geometry of --time-to-target: plain or detector")
-    p.add_argument("--e1", action="store_true",
+    p.add_argument("--two-sensor", action="store_true",
                    help="instead of the throughput line: the paper's two-sensor scene (relative light yield B "
                         "through the map T and path-length distributions for each b1, beside the GPU tracer)")
-    p.add_argument("--e1-b1", default="0.1,0.2,0.3,0.4,0.5")
-    p.add_argument("--e1-chains", type=int, default=2048, help="chains per sensor")
-    p.add_argument("--e1-steps", type=int, default=1_000_000, help="steps per chain (10%% burn-in)")
-    p.add_argument("--e1-thin", type=int, default=200, help="steps between observations of B and lengths")
-    p.add_argument("--e1-photons", type=int, default=0, help="tracer photons per sensor and b1 (0: no tracer)")
-    p.add_argument("--e1-out", default="", help="file for the full result (histograms included)")
-    p.add_argument("--e1-within", default="perturb", choices=["perturb", "tree", "mala", "hmc"],
+    p.add_argument("--ts-b1", default="0.1,0.2,0.3,0.4,0.5")
+    p.add_argument("--ts-chains", type=int, default=2048, help="chains per sensor")
+    p.add_argument("--ts-steps", type=int, default=1_000_000, help="steps per chain (10%% burn-in)")
+    p.add_argument("--ts-thin", type=int, default=200, help="steps between observations of B and lengths")
+    p.add_argument("--ts-photons", type=int, default=0, help="tracer photons per sensor and b1 (0: no tracer)")
+    p.add_argument("--ts-out", default="", help="file for the full result (histograms included)")
+    p.add_argument("--ts-within", default="perturb", choices=["perturb", "tree", "mala", "hmc"],
                    help="within-dimension moves: Gaussian vertex steps, the paper's tree-coordinate moves, MALA or "
                         "full-path HMC")
-    p.add_argument("--e1-hmc-steps", type=int, default=10, help="leapfrog steps of an HMC move")
-    p.add_argument("--e1-sigma", type=float, default=0.0,
+    p.add_argument("--ts-hmc-steps", type=int, default=10, help="leapfrog steps of an HMC move")
+    p.add_argument("--ts-sigma", type=float, default=0.0,
                    help="step scale (m for perturb; dimensionless for tree; MALA epsilon); 0 = the scene default")
-    p.add_argument("--e1-ttt", type=float, default=0.0,
+    p.add_argument("--ts-ttt", type=float, default=0.0,
                    help="two-sensor scene: wall time until B reaches this relative error for tree-move chains, "
                         "Cartesian chains (straight starts and tracer seeds) and the GPU tracer")
-    p.add_argument("--e1-grad", action="store_true",
+    p.add_argument("--ts-grad", action="store_true",
                    help="also observe the per-layer scores: d log B / d theta and d log B / d b1")
-    p.add_argument("--e1-cpu-seconds", type=float, default=0.0,
+    p.add_argument("--ts-cpu-seconds", type=float, default=0.0,
                    help="also time the FP64 oracle's chains (same moves) on the host cores for about this long")
-    p.add_argument("--e1-seed", action="store_true",
+    p.add_argument("--ts-seed", action="store_true",
                    help="start the chains from weight-thinned tracer paths (exact draws, as the paper seeds its "
                         "chains) instead of straight jittered paths")
     return p.parse_args()
@@ -550,18 +550,18 @@ def time_to_target(args):
 # The paper's table of its two-sensor scene (section "Comparison of relative
 # light yield", Table tbl:results): B with its uncertainty for each b1, the
 # ray tracer's and the path sampler's, and the CPU seconds of each.
-E1_PAPER = {0.1: {"tracer": (0.67, 0.03), "sampler": (0.64, 0.07), "sampler_cpu_s": 23.0, "tracer_cpu_s": 45.9e3},
+TWO_SENSOR_PAPER = {0.1: {"tracer": (0.67, 0.03), "sampler": (0.64, 0.07), "sampler_cpu_s": 23.0, "tracer_cpu_s": 45.9e3},
             0.2: {"tracer": (0.79, 0.02), "sampler": (0.77, 0.01), "sampler_cpu_s": 74.4, "tracer_cpu_s": 78.1e3},
             0.3: {"tracer": (0.73, 0.02), "sampler": (0.76, 0.07), "sampler_cpu_s": 232.0, "tracer_cpu_s": 99.6e3},
             0.4: {"tracer": (0.68, 0.02), "sampler": (0.64, 0.04), "sampler_cpu_s": 373.0, "tracer_cpu_s": 122e3},
             0.5: {"tracer": (0.59, 0.02), "sampler": (0.50, 0.06), "sampler_cpu_s": 416.0, "tracer_cpu_s": 156e3}}
 
 
-def e1_experiment(args):
+def two_sensor_experiment(args):
     """Relative light yield B of the paper's two sensors and their path-length
     distributions, for each b1: chains of both sensors from straight jittered
     paths, 10% burn-in, then B (geometric estimator through the map T) and the
-    length histograms observed every --e1-thin steps; optionally I_1/I_0 and
+    length histograms observed every --ts-thin steps; optionally I_1/I_0 and
     the length histograms of the GPU forward tracer (rejection radius 400 m,
     scatterings capped at the chains' vertex cap)."""
     import numpy as np
@@ -573,32 +573,32 @@ def e1_experiment(args):
     stream = torch.cuda.current_stream()
     lo, hi, nb = 115.0, 215.0, 50
     results = []
-    for b1 in [float(x) for x in args.e1_b1.split(",")]:
-        sc = S.e1(b1, n_chains=args.e1_chains, n_steps=args.e1_steps)
+    for b1 in [float(x) for x in args.ts_b1.split(",")]:
+        sc = S.two_sensor(b1, n_chains=args.ts_chains, n_steps=args.ts_steps)
         sc.run.within = {"perturb": S.WITHIN_PERTURB, "tree": S.WITHIN_TREE, "mala": S.WITHIN_MALA,
-                         "hmc": S.WITHIN_HMC}[args.e1_within]
-        if args.e1_within == "tree":
-            sc.run.sigma = args.e1_sigma or 0.3
-        elif args.e1_within in ("mala", "hmc"):
-            sc.run.mala_step = args.e1_sigma or 0.5
-            sc.run.hmc_steps = args.e1_hmc_steps
-        elif args.e1_sigma:
-            sc.run.sigma = args.e1_sigma
+                         "hmc": S.WITHIN_HMC}[args.ts_within]
+        if args.ts_within == "tree":
+            sc.run.sigma = args.ts_sigma or 0.3
+        elif args.ts_within in ("mala", "hmc"):
+            sc.run.mala_step = args.ts_sigma or 0.5
+            sc.run.hmc_steps = args.ts_hmc_steps
+        elif args.ts_sigma:
+            sc.run.sigma = args.ts_sigma
         medium = api.Medium(ctx, sc.medium)
         geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
         ch = api.Chains(ctx, medium, geom, sc.run)
         seed_s, seed_photons = 0.0, None
-        if args.e1_seed:
+        if args.ts_seed:
             ts = time.perf_counter()
             seed_photons = api.seed_from_tracer(ch, seed=2468, photons_per_round=1 << 28, r_reject=400.0)
             seed_s = time.perf_counter() - ts
         burn = sc.run.burn_in
-        thin = args.e1_thin
+        thin = args.ts_thin
         n_obs = (sc.run.n_steps - burn + thin - 1) // thin
         Y = api.YieldRatio(ch, 0, 1, max_obs=n_obs)
         hist = torch.zeros((2, nb), dtype=torch.float64, device="cuda")
         nth = medium.n_theta
-        ssum = torch.zeros((2, 2 * nth), dtype=torch.float64, device="cuda") if args.e1_grad else None
+        ssum = torch.zeros((2, 2 * nth), dtype=torch.float64, device="cuda") if args.ts_grad else None
         sobs = []
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -626,17 +626,17 @@ def e1_experiment(args):
                "bridge_iterations": ob["iterations"], "rhat": [e[0]["rhat"], e[1]["rhat"]],
                "accept": [e[0]["accept"], e[1]["accept"]], "mean_n": [e[0]["mean_n"], e[1]["mean_n"]],
                "mean_length_m": [e[0]["mean_length"], e[1]["mean_length"]], "observations": Y.n_obs,
-               "proposals": 2 * args.e1_chains * sc.run.n_steps, "gpu_seconds": gpu_s, "wall_seconds": wall,
-               "proposals_per_s": 2 * args.e1_chains * sc.run.n_steps / gpu_s,
+               "proposals": 2 * args.ts_chains * sc.run.n_steps, "gpu_seconds": gpu_s, "wall_seconds": wall,
+               "proposals_per_s": 2 * args.ts_chains * sc.run.n_steps / gpu_s,
                "length_hist": {"lo": lo, "hi": hi, "bins": nb, "sensor0": (h[0] / max(h[0].sum(), 1)).tolist(),
                                "sensor1": (h[1] / max(h[1].sum(), 1)).tolist()},
-               "init": "tracer seeds" if args.e1_seed else "straight, 30 interior vertices, N(0, 0.5 m) jitter",
-               "within": args.e1_within, "sigma": sc.run.sigma, "mala_step": sc.run.mala_step,
-               "seed_seconds": seed_s, "seed_photons": seed_photons, "paper": E1_PAPER.get(b1)}
+               "init": "tracer seeds" if args.ts_seed else "straight, 30 interior vertices, N(0, 0.5 m) jitter",
+               "within": args.ts_within, "sigma": sc.run.sigma, "mala_step": sc.run.mala_step,
+               "seed_seconds": seed_s, "seed_photons": seed_photons, "paper": TWO_SENSOR_PAPER.get(b1)}
         if ssum is not None:
             # per-observation mean scores of each sensor's chains, then batch means over 20 batches
             cum = torch.stack(sobs).cpu().numpy()                        # (obs, 2, nth) running sums
-            per = np.diff(np.concatenate([np.zeros_like(cum[:1]), cum]), axis=0) / args.e1_chains
+            per = np.diff(np.concatenate([np.zeros_like(cum[:1]), cum]), axis=0) / args.ts_chains
             d = per[:, 1, :] - per[:, 0, :]                               # d log B / d theta per observation
             nbat = 20
             bm = np.array([b.mean(axis=0) for b in np.array_split(d, nbat)])
@@ -645,29 +645,29 @@ def e1_experiment(args):
             row["dlogB_dtheta"] = {"theta": "lambda_s[0], lambda_s[1], lambda_a[0], lambda_a[1] (m)",
                                    "value": g.tolist(), "se": gse.tolist()}
             row["dlogB_db1"] = {"value": float(-lam1 * lam1 * g[1]), "se": float(lam1 * lam1 * gse[1])}
-        if args.e1_photons > 0:
+        if args.ts_photons > 0:
             cap = sc.pairs[0].cap
             tr, th = [], []
             t1 = time.perf_counter()
             for p, sd in ((0, 701), (1, 702)):
-                r, hh = api.trace_lengths(ctx, medium, geom, p, sd, args.e1_photons, lo, hi, nb, r_reject=400.0,
+                r, hh = api.trace_lengths(ctx, medium, geom, p, sd, args.ts_photons, lo, hi, nb, r_reject=400.0,
                                           max_scatter=cap - 2)
                 tr.append(r)
                 th.append(hh)
             Bt = tr[1]["I"] / tr[0]["I"]
             row["tracer"] = {"B": Bt, "B_se": Bt * math.hypot(tr[0]["se"] / tr[0]["I"], tr[1]["se"] / tr[1]["I"]),
                              "I0": tr[0]["I"], "I0_se": tr[0]["se"], "I1": tr[1]["I"], "I1_se": tr[1]["se"],
-                             "hits": [tr[0]["hits"], tr[1]["hits"]], "photons_per_sensor": args.e1_photons,
+                             "hits": [tr[0]["hits"], tr[1]["hits"]], "photons_per_sensor": args.ts_photons,
                              "seconds": time.perf_counter() - t1,
                              "length_hist": {"sensor0": (th[0] / max(th[0].sum(), 1e-300)).tolist(),
                                              "sensor1": (th[1] / max(th[1].sum(), 1e-300)).tolist()}}
-        if args.e1_cpu_seconds > 0:
+        if args.ts_cpu_seconds > 0:
             import oracle as O
             ts = time.perf_counter()
             oc = [O.Chains(sc.medium, sc.sources[0], sc.sensors[k], sc.run, 256, sc.pairs[k].cap, chain_offset=k * 256)
                   for k in (0, 1)]
             steps = 0
-            while time.perf_counter() - ts < args.e1_cpu_seconds:
+            while time.perf_counter() - ts < args.ts_cpu_seconds:
                 for k in (0, 1):
                     oc[k].run(200)
                 steps += 200
@@ -687,10 +687,10 @@ def e1_experiment(args):
                                  row["tracer"]["seconds"])
         print(json.dumps(brief), flush=True)
         ch.close()
-    out = {"experiment": "two-sensor scene (relative light yield, path lengths)", "chains_per_sensor": args.e1_chains,
-           "steps_per_chain": args.e1_steps, "thin": args.e1_thin, "results": results}
-    if args.e1_out:
-        with open(args.e1_out, "w") as f:
+    out = {"experiment": "two-sensor scene (relative light yield, path lengths)", "chains_per_sensor": args.ts_chains,
+           "steps_per_chain": args.ts_steps, "thin": args.ts_thin, "results": results}
+    if args.ts_out:
+        with open(args.ts_out, "w") as f:
             json.dump(out, f)
     print(json.dumps({"experiment": out["experiment"],
                       "B": [(r["b1"], r["B"], r["B_se"], r["B_bridge"], r["B_bridge_se"], r.get("tracer", {}).get("B"))
@@ -699,9 +699,9 @@ def e1_experiment(args):
     return 0
 
 
-def e1_time_to_target(args):
+def two_sensor_time_to_target(args):
     """Wall time until the relative light yield B of the two-sensor scene
-    (b1 = first --e1-b1 value) reaches relative standard error --e1-ttt and
+    (b1 = first --ts-b1 value) reaches relative standard error --ts-ttt and
     lies within max(target, 3 combined SE) of a reference from a long
     tree-move run.  Chains keep running with doubling step budgets (the first
     10 % of the steps run so far as burn-in is never observed); the tracer
@@ -711,12 +711,12 @@ def e1_time_to_target(args):
     B.build()
     from paper_1811_04156_gb300 import api, scenes as S
     ctx = api.Context(0)
-    b1 = float(args.e1_b1.split(",")[0])
-    tgt = args.e1_ttt
+    b1 = float(args.ts_b1.split(",")[0])
+    tgt = args.ts_ttt
     limit = 120.0
 
     def chains_run(within, sigma, n_chains, steps_total, seeded=False, budget0=20_000, thin=200, ref=None):
-        sc = S.e1(b1, n_chains=n_chains, n_steps=steps_total)
+        sc = S.two_sensor(b1, n_chains=n_chains, n_steps=steps_total)
         sc.run.within = within
         sc.run.sigma = sigma
         medium = api.Medium(ctx, sc.medium)
@@ -763,7 +763,7 @@ def e1_time_to_target(args):
     out["cartesian_straight_starts"] = chains_run(S.WITHIN_PERTURB, 0.5, 2048, 0, budget0=50_000, ref=ref)
     out["cartesian_tracer_seeds"] = chains_run(S.WITHIN_PERTURB, 0.5, 1024, 0, seeded=True, budget0=50_000, ref=ref)
     # GPU tracer: I1/I0 with doubling photon budgets
-    sc = S.e1(b1, n_chains=1)
+    sc = S.two_sensor(b1, n_chains=1)
     medium = api.Medium(ctx, sc.medium)
     geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
     cap = sc.pairs[0].cap
@@ -788,8 +788,8 @@ def e1_time_to_target(args):
         photons *= 2
     out["gpu_tracer"] = {"seconds": time.perf_counter() - t0, "photons_per_sensor": sum(a["photons"] for a in acc[0]),
                          "B": Bt, "se": st, "reached": bool(ok)}
-    out["paper_cpu_seconds"] = {"sampler": E1_PAPER.get(b1, {}).get("sampler_cpu_s"),
-                                "tracer": E1_PAPER.get(b1, {}).get("tracer_cpu_s")}
+    out["paper_cpu_seconds"] = {"sampler": TWO_SENSOR_PAPER.get(b1, {}).get("sampler_cpu_s"),
+                                "tracer": TWO_SENSOR_PAPER.get(b1, {}).get("tracer_cpu_s")}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -798,10 +798,10 @@ def main():
     args = parse()
     if args.time_to_target > 0:
         return time_to_target(args)
-    if args.e1_ttt > 0:
-        return e1_time_to_target(args)
-    if args.e1:
-        return e1_experiment(args)
+    if args.ts_ttt > 0:
+        return two_sensor_time_to_target(args)
+    if args.two_sensor:
+        return two_sensor_experiment(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)

@@ -229,7 +229,7 @@ def general_small(n_chains: int = 64, n_steps: int = 400) -> Scene:
 
 
 # Scattering coefficients b1 (1/m) of the x >= 0 half of the paper's test scene (Table tbl:results).
-E1_B1 = (0.1, 0.2, 0.3, 0.4, 0.5)
+TWO_SENSOR_B1 = (0.1, 0.2, 0.3, 0.4, 0.5)
 
 
 def to_device_frame(v):
@@ -250,7 +250,7 @@ def _dev(v):
     return tuple(float(x) for x in to_device_frame(v))
 
 
-def e1(b1: float = 0.3, n_chains: int = 4096, n_steps: int = 200_000, cap: int = 256,
+def two_sensor(b1: float = 0.3, n_chains: int = 4096, n_steps: int = 200_000, cap: int = 256,
        sigma: float = 0.5, init_k: int = 30, init_jitter: float = 0.5) -> Scene:
     """The paper's two-sensor test scene (section "Implementation", Fig. setup).
 
@@ -276,7 +276,7 @@ def e1(b1: float = 0.3, n_chains: int = 4096, n_steps: int = 200_000, cap: int =
     pairs = [Pair(0, 0, n_chains, cap), Pair(0, 1, n_chains, cap)]
     run = Run(seed=BASE_SEED + 8, n_steps=n_steps, burn_in=n_steps // 10, init=INIT_STRAIGHT,
               init_k=init_k, init_jitter=init_jitter, sigma=sigma)
-    return Scene("e1", med, [src], sensors, pairs, run)
+    return Scene("two_sensor", med, [src], sensors, pairs, run)
 
 
 PRESETS = {"plain": plain, "detector": detector, "batched": batched,

@@ -118,7 +118,7 @@ def test_paper_table_relative_yield(api, ctx, b1, steps):
     import os
     rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "paper_relative_yield.txt"))
     row = rows[np.isclose(rows[:, 0], b1)][0]
-    sc = S.e1(b1, n_chains=1024, n_steps=steps)
+    sc = S.two_sensor(b1, n_chains=1024, n_steps=steps)
     sc.run.within = S.WITHIN_TREE
     sc.run.sigma = 0.3
     medium = api.Medium(ctx, sc.medium)

@@ -38,14 +38,14 @@ def ctx(api):
 
 
 def _two_sensor_scenes():
-    e1 = S.e1(0.3, n_chains=1, cap=128)
+    full = S.two_sensor(0.3, n_chains=1, cap=128)
     mini = S.Scene("mini", S.Medium(S.LAYERED, g=0.8, f_sl=0.3, z0=-1.0, dz=1.0,
                                     lambda_s_layers=np.array([1.0, 0.6]), lambda_a_layers=np.array([8.0, 8.0])),
                    [S.Source((0.2, -0.1, 0.3), S.EMIT_VMF, 5.0, (0.1, 0.0, 1.0))],
                    [S.Sensor((0.2, -0.1, 2.3), 0.3, S.RHO_PAPER, (0.0, -1.0, 0.0)),
                     S.Sensor((1.4, 0.0, 1.9), 0.25, S.RHO_PAPER, (0.0, -1.0, 0.0))],
                    [S.Pair(0, 0, 1, 48), S.Pair(0, 1, 1, 48)], S.Run())
-    return {"e1": (e1, 2.0), "mini": (mini, 0.3)}
+    return {"full": (full, 2.0), "mini": (mini, 0.3)}
 
 
 def _side_batch(sc, side, lateral, batch, seed):
@@ -58,7 +58,7 @@ def _side_batch(sc, side, lateral, batch, seed):
     return xyz, n
 
 
-@pytest.mark.parametrize("name", ["e1", "mini"])
+@pytest.mark.parametrize("name", ["full", "mini"])
 @pytest.mark.parametrize("side", [0, 1])
 def test_yield_logratio_matches_oracle(api, ctx, oracle_lib, name, side):
     import torch

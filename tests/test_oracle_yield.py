@@ -180,7 +180,7 @@ def test_half_space_depths_brute_force(oracle_lib):
     rotated frame: optical depths equal a midpoint brute force in the paper's
     frame."""
     O = oracle_lib
-    sc = S.e1(0.1)
+    sc = S.two_sensor(0.1)
     m = O.medium(sc.medium)
     rng = np.random.default_rng(2)
     for _ in range(20):
