@@ -295,20 +295,25 @@ def test_chain_length_distribution_matches_tracer(api, ctx):
     ch = api.Chains(ctx, medium, geom, sc.run)
     api.seed_from_tracer(ch, seed=99, photons_per_round=1 << 24)
     lo, hi, nb = 1.0, 9.0, 32
-    hist = torch.zeros((2, nb), dtype=torch.float64, device="cuda")
-    for _ in range(400):
+    n_batch = 10
+    hists = [torch.zeros((2, nb), dtype=torch.float64, device="cuda") for _ in range(n_batch)]
+    for i in range(400):
         ch.run_steps(25)
-        ch.length_hist(lo, hi, hist)
-    h = hist.cpu().numpy()
+        ch.length_hist(lo, hi, hists[i * n_batch // 400])
+    hb = np.stack([t.cpu().numpy() for t in hists])   # (batch, pair, bin)
+    h = hb.sum(axis=0)
+    centres = lo + (np.arange(nb) + 0.5) * (hi - lo) / nb
     for p in (0, 1):
         tr, th = api.trace_lengths(ctx, medium, geom, p, 31 + p, 400_000_000, lo, hi, nb, max_scatter=cap - 2)
         a = np.cumsum(h[p]) / h[p].sum()
         b = np.cumsum(th) / th.sum()
         assert np.abs(a - b).max() < 0.01, (p, np.abs(a - b).max())
-        centres = lo + (np.arange(nb) + 0.5) * (hi - lo) / nb
+        # mean length: chains' error from batch means over the observation sequence
+        mb = (hb[:, p, :] * centres).sum(axis=1) / hb[:, p, :].sum(axis=1)
+        se_c = mb.std(ddof=1) / np.sqrt(n_batch)
         mc = (centres * h[p]).sum() / h[p].sum()
         mt = (centres * th).sum() / th.sum()
-        assert abs(mc / mt - 1) < 0.005, (p, mc, mt)
+        assert abs(mc - mt) < 4 * se_c + 0.002 * mt, (p, mc, mt, se_c)
 
 
 def test_score_observe_matches_per_path_scores(api, ctx):
