@@ -514,7 +514,9 @@ PMC_API int pmc_trace_noalloc(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geo
  * truncated to max_scatter + 2 vertices.  Kept paths go to out_xyz (device,
  * [3][max_paths][stride] absolute positions, stride >= max_scatter + 2) and
  * out_n (device, [max_paths]); *n_accepted (host) counts all kept paths, also
- * those beyond max_paths.  Synchronises `stream`. */
+ * those beyond max_paths.  Paths take slots in the order the GPU finishes
+ * them, so which kept paths fill the first slots varies between runs (each
+ * is an exact draw either way).  Synchronises `stream`. */
 PMC_API int pmc_trace_paths(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair, uint64_t seed,
                             uint64_t photon0, uint64_t n_photons, double r_reject, int max_scatter, int max_paths,
                             float* out_xyz, int* out_n, int stride, uint64_t* n_accepted, void* stream);
