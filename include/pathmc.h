@@ -369,6 +369,17 @@ PMC_API int pmc_qref_sample(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom,
  * (delta method over both sample variances).  Synchronises `stream`. */
 PMC_API int pmc_bridge(pmc_chains_t chains, uint64_t n_draws, uint64_t seed, double* out, void* stream);
 
+/* One row of log ratios for the optimal bridge (pmc_bridge_ratio) of pair
+ * `pair`'s intensity against q_ref: logr[0 .. n_draws) = log(p / q_ref) at
+ * n_draws fresh reference draws numbered from draw0 (Philox key `seed`,
+ * stream = pair), then logr[n_draws + i] = log(q_ref / p) at the pair's chain
+ * i's current path (-inf where either density is 0).  logr: device,
+ * caller-owned, n_draws + n_chains(pair) floats.  With rows stacked over
+ * observations, pmc_bridge_ratio(n0 = n_draws, n1 = n_chains) returns the
+ * intensity (q_ref is normalised).  Asynchronous on `stream`. */
+PMC_API int pmc_bridge_observe_log(pmc_chains_t chains, int pair, uint64_t n_draws, uint64_t draw0, uint64_t seed,
+                                   float* logr, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Relative light yield of two sensors (section "Comparison of relative   */
 /* light yield"; appendix "Relative light yield transformation") and      */

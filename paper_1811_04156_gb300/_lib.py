@@ -118,6 +118,7 @@ PROTOTYPES = {
     "pmc_qref_sample": ([_vp, _vp, _vp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, _vp, _vp, C.c_int, _vp],
                         C.c_int),
     "pmc_bridge": ([_vp, C.c_uint64, C.c_uint64, _dp, _vp], C.c_int),
+    "pmc_bridge_observe_log": ([_vp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, _vp, _vp], C.c_int),
     "pmc_trace_paths": ([_vp, _vp, _vp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int, C.c_int,
                          _vp, _vp, C.c_int, C.POINTER(C.c_uint64), _vp], C.c_int),
     "pmc_yield_logratio": ([_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp],

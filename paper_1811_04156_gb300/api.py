@@ -276,6 +276,15 @@ class Chains:
         check(load().pmc_length_hist(self.handle, float(l_lo), float(l_hi), int(hist.shape[1]),
                                      C.c_void_p(hist.data_ptr()), _stream(stream)), "pmc_length_hist")
 
+    def bridge_observe_log(self, pair: int, n_draws: int, draw0: int, seed: int, row: torch.Tensor, stream=None):
+        """One row of q_ref-bridge log ratios for `pair` (pmc_bridge_observe_log): n_draws
+        reference draws' log(p/q_ref), then the pair's chains' log(q_ref/p)."""
+        _require_cuda(row, torch.float32, "row")
+        if row.numel() != n_draws + self.geom.pairs[pair].n_chains:
+            raise ValueError("row must hold n_draws + n_chains floats")
+        check(load().pmc_bridge_observe_log(self.handle, int(pair), int(n_draws), int(draw0), int(seed),
+                                            C.c_void_p(row.data_ptr()), _stream(stream)), "pmc_bridge_observe_log")
+
     def read_states(self, stream=None):
         stride = self.geom.max_cap
         xyz = np.zeros((self.total, 3, stride), dtype=np.float32)

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(128) qref_draw_kernel(const DMedium M, const D
                                                         unsigned long long seed, unsigned long long draw0,
                                                         unsigned long long n_draws, double* __restrict__ sums,
                                                         float* __restrict__ out_xyz, int* __restrict__ out_n,
-                                                        int out_stride) {
+                                                        int out_stride, float* __restrict__ out_logr) {
   extern __shared__ float smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(128) qref_draw_kernel(const DMedium M, const D
       acc_s += sqrt(ratio);
       acc_r += ratio;
       acc_r2 += ratio * ratio;
+      if (out_logr != nullptr) out_logr[q] = (isfinite(lp) && isfinite(lq)) ? lp - lq : kNegInf;
     }
     if (out_xyz != nullptr) {
       const size_t plane = static_cast<size_t>(n_draws) * out_stride;
@@ -228,6 +229,28 @@ __global__ void __launch_bounds__(128) qref_chain_kernel(const DMedium M, const 
   }
 }
 
+// Chain side of the optimal bridge for one pair: log(q_ref / p) at each of
+// its chains' current paths, in chain order.
+__global__ void __launch_bounds__(128) qref_chain_logr_kernel(const DMedium M, const DRun R, const DPair* __restrict__ S_,
+                                                              const QrefPair* __restrict__ qp,
+                                                              const double* __restrict__ qtab,
+                                                              const long long* __restrict__ chain_base,
+                                                              const float* __restrict__ xyz, const int* __restrict__ nn,
+                                                              int chain0, int n_chains, float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= n_chains) return;
+  const DPair S = *S_;
+  const int c = chain0 + j;
+  const int n = nn[c];
+  const float* gx = xyz + chain_base[c];
+  const float* gy = gx + S.cap;
+  const float* gz = gy + S.cap;
+  float lp, lq;
+  path_logs(M, R, S, *qp, qtab, S.zoff, [&](int i) { return f3(gx[i], gy[i], gz[i]); }, n, lane, lp, lq);
+  if (lane == 0) out[j] = (isfinite(lp) && isfinite(lq)) ? lq - lp : kNegInf;
+}
+
 // log q_ref of caller paths (absolute frame, SoA [3][batch][cap]).
 __global__ void __launch_bounds__(128) qref_logdensity_kernel(const DMedium M, const DRun R, const DPair S,
                                                               const QrefPair* __restrict__ qp,
@@ -252,7 +275,7 @@ __global__ void __launch_bounds__(128) qref_logdensity_kernel(const DMedium M, c
 cudaError_t launch_qref_draws(const DMedium& M, const DRun& R, const DPair* pairs, const QrefPair* qp,
                               const double* qtab, int n_pairs, int stream_base, int max_cap, unsigned long long seed, unsigned long long draw0,
                               unsigned long long n_draws, double* sums, float* out_xyz, int* out_n, int out_stride,
-                              int n_sm, cudaStream_t s) {
+                              int n_sm, cudaStream_t s, float* out_logr) {
   if (n_pairs == 0 || n_draws == 0) return cudaSuccess;
   const int smem_cap = (max_cap + 31) / 32 * 32;
   const size_t smem = 4u * 3u * smem_cap * sizeof(float);
@@ -264,7 +287,16 @@ cudaError_t launch_qref_draws(const DMedium& M, const DRun& R, const DPair* pair
   if (blocks > maxb) blocks = maxb;
   dim3 grid(static_cast<unsigned>(blocks), static_cast<unsigned>(n_pairs));
   qref_draw_kernel<<<grid, 128, smem, s>>>(M, R, pairs, qp, qtab, smem_cap, stream_base, seed, draw0, n_draws, sums,
-                                           out_xyz, out_n, out_stride);
+                                           out_xyz, out_n, out_stride, out_logr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qref_chain_logr(const DMedium& M, const DRun& R, const DPair* pair, const QrefPair* qp,
+                                   const double* qtab, const long long* chain_base, const float* xyz, const int* n,
+                                   int chain0, int n_chains, float* out, cudaStream_t s) {
+  if (n_chains == 0) return cudaSuccess;
+  qref_chain_logr_kernel<<<(n_chains + 3) / 4, 128, 0, s>>>(M, R, pair, qp, qtab, chain_base, xyz, n, chain0,
+                                                            n_chains, out);
   return cudaGetLastError();
 }
 

@@ -1267,22 +1267,47 @@ int pmc_qref_sample(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, 
   return PMC_OK;
 }
 
+// Reference-density tables of the chains' pairs, built on first use.
+static int ensure_qref(pmc_chains_t ch, cudaStream_t s) {
+  if (ch->d_qp != nullptr) return PMC_OK;
+  std::vector<QrefPair> qp;
+  std::vector<double> tab;
+  build_qref(ch->med, ch->geom->host, qp, tab);
+  CK(dalloc(&ch->d_qp, qp.size()));
+  CK(dalloc(&ch->d_qtab, tab.size()));
+  CK(dalloc(&ch->d_bsum, 8 * static_cast<size_t>(ch->n_pairs)));
+  CK(cudaMemcpyAsync(ch->d_qp, qp.data(), qp.size() * sizeof(QrefPair), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ch->d_qtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return PMC_OK;
+}
+
+int pmc_bridge_observe_log(pmc_chains_t ch, int pair, uint64_t n_draws, uint64_t draw0, uint64_t seed, float* logr,
+                           void* stream) {
+  if (ch == nullptr || logr == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (pair < 0 || pair >= ch->n_pairs) return fail(PMC_ERR_INVALID, "pair out of range");
+  if (n_draws == 0) return fail(PMC_ERR_INVALID, "n_draws must be > 0");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int rc = ensure_qref(ch, s);
+  if (rc != PMC_OK) return rc;
+  const DPair& d = ch->h_pairs[pair];
+  CK(launch_qref_draws(ch->med->d, ch->run, ch->d_pairs + pair, ch->d_qp + pair, ch->d_qtab, 1, pair, d.cap, seed,
+                       draw0, n_draws, nullptr, nullptr, nullptr, 0, ch->ctx->n_sm, s, logr));
+  CK(launch_qref_chain_logr(ch->med->d, ch->run, ch->d_pairs + pair, ch->d_qp + pair, ch->d_qtab, ch->d_chain_base,
+                            ch->d_xyz, ch->d_n, d.chain0, d.n_chains, logr + n_draws, s));
+  return PMC_OK;
+}
+
 int pmc_bridge(pmc_chains_t ch, uint64_t n_draws, uint64_t seed, double* out, void* stream) {
   if (ch == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
   if (n_draws == 0) return fail(PMC_ERR_INVALID, "n_draws must be > 0");
   CK(cudaSetDevice(ch->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int P = ch->n_pairs;
-  if (ch->d_qp == nullptr) {
-    std::vector<QrefPair> qp;
-    std::vector<double> tab;
-    build_qref(ch->med, ch->geom->host, qp, tab);
-    CK(dalloc(&ch->d_qp, qp.size()));
-    CK(dalloc(&ch->d_qtab, tab.size()));
-    CK(dalloc(&ch->d_bsum, 8 * static_cast<size_t>(P)));
-    CK(cudaMemcpyAsync(ch->d_qp, qp.data(), qp.size() * sizeof(QrefPair), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ch->d_qtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));
+  {
+    const int rc = ensure_qref(ch, s);
+    if (rc != PMC_OK) return rc;
   }
   CK(cudaMemsetAsync(ch->d_bsum, 0, 8 * sizeof(double) * P, s));
   CK(launch_qref_draws(ch->med->d, ch->run, ch->d_pairs, ch->d_qp, ch->d_qtab, P, 0, ch->geom->max_cap, seed, 0,

@@ -152,10 +152,15 @@ struct QrefPair {
   double log_qend;
   long long off;
 };
+// out_logr (may be null): log(p / q_ref) of each draw (-inf where either is 0).
 cudaError_t launch_qref_draws(const DMedium& M, const DRun& R, const DPair* pairs, const QrefPair* qp,
                               const double* qtab, int n_pairs, int stream_base, int max_cap, unsigned long long seed,
                               unsigned long long draw0, unsigned long long n_draws, double* sums, float* out_xyz,
-                              int* out_n, int out_stride, int n_sm, cudaStream_t s);
+                              int* out_n, int out_stride, int n_sm, cudaStream_t s, float* out_logr = nullptr);
+// log(q_ref / p) at the current paths of one pair's chains [chain0, chain0 + n_chains).
+cudaError_t launch_qref_chain_logr(const DMedium& M, const DRun& R, const DPair* pair, const QrefPair* qp,
+                                   const double* qtab, const long long* chain_base, const float* xyz, const int* n,
+                                   int chain0, int n_chains, float* out, cudaStream_t s);
 cudaError_t launch_qref_chains(const DMedium& M, const DRun& R, const DPair* pairs, const QrefPair* qp,
                                const double* qtab, const int* chain_pair, const long long* chain_base,
                                const float* xyz, const int* n, int total, double* sums, cudaStream_t s);

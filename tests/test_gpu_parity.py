@@ -424,6 +424,28 @@ def test_bridge_intensity_single_scatter(api, ctx):
     assert se / I < 0.02
 
 
+def test_optimal_bridge_intensity_single_scatter(api, ctx, oracle_lib):
+    """The optimal (Meng & Wong) bridge against the normalised reference
+    density estimates Z2 + Z3 at cap 3 from per-observation log ratios, and
+    the device iteration equals the oracle's on the same stored rows."""
+    import torch
+    O = oracle_lib
+    sc, medium, geom, ch = _plain_sampler(api, ctx, 4096, 20000, cap=3)
+    ch.run_steps(2000)
+    n_draws, rows = 4096, 60
+    logr = torch.zeros((rows, n_draws + 4096), dtype=torch.float32, device="cuda")
+    for r in range(rows):
+        ch.run_steps(100)
+        ch.bridge_observe_log(0, n_draws, r * n_draws, 11, logr[r])
+    ob = api.bridge_ratio(ctx, logr, n_draws, 4096, groups=32)
+    ref = Q.z2_closed(1.0, 0.1, 2.2) + Q.z3(1.0, 0.1, 0.5, 5.0, 0.9)
+    assert abs(ob["r"] - ref) < 3 * ob["se"], (ob, ref)
+    assert ob["se"] / ob["r"] < 0.01
+    L = logr.cpu().numpy().astype(np.float64)
+    r, se, it, geo = O.optimal_bridge(L[:, :n_draws], L[:, n_draws:], groups=32)
+    assert abs(ob["r"] / r - 1) < 1e-9 and abs(ob["geometric"] / geo - 1) < 1e-9
+
+
 def _layered_small(n_chains, n_steps, cap):
     rng = np.random.default_rng(31)
     med = S.Medium(S.LAYERED, g=0.9, z0=-1.0, dz=0.4, lambda_s_layers=0.6 * np.exp(0.3 * rng.normal(size=8)),
