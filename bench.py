@@ -463,8 +463,10 @@ def time_to_target(args):
     standard error and lies within max(target, 3 SE) of a reference value from
     a long forward-tracer run, for (a) plain RJMCMC (64 chains, Gaussian
     steps), (b) batched MALA chains (65,536), with and without tracer seeds,
-    batched Gaussian chains with seeds and batched tree-move chains from the
-    direct path, (c) the GPU forward tracer.
+    batched Gaussian chains with seeds, batched tree-move chains from the
+    direct path, and tree-move chains whose intensity comes from the optimal
+    bridge against the reference density instead of the direct sector, (c) the
+    GPU forward tracer.
     Budgets double until the criterion holds or 120 s have passed."""
     import torch
     from paper_1811_04156_gb300 import build as B
@@ -529,6 +531,38 @@ def time_to_target(args):
     out["batched_mala_tracer_seeded"] = run_chains(65_536, S.WITHIN_MALA, 500, seeded=True)
     out["batched_perturb_tracer_seeded"] = run_chains(65_536, S.WITHIN_PERTURB, 500, seeded=True)
     out["batched_tree_moves"] = run_chains(65_536, S.WITHIN_TREE, 2_000)
+
+    def run_tree_bridge(n_chains, burn, thin, n_draws, rows0):
+        """Tree-move chains and the optimal bridge against the normalised
+        reference density: after `burn` steps, one row of log ratios (n_draws
+        reference draws, every chain's state) every `thin` steps; the row
+        count doubles until the criterion holds."""
+        sc = S.plain(n_chains=n_chains) if geom_name == "plain" else S.detector(n_chains=n_chains)
+        sc.run.within, sc.run.sigma, sc.run.burn_in = S.WITHIN_TREE, 0.3, 0
+        geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ch = api.Chains(ctx, med, geom, sc.run)
+        ch.run_steps(burn)
+        rows, target, ob = [], rows0, None
+        while True:
+            while len(rows) < target:
+                ch.run_steps(thin)
+                row = torch.empty(n_draws + n_chains, dtype=torch.float32, device="cuda")
+                ch.bridge_observe_log(0, n_draws, len(rows) * n_draws, 4242, row)
+                rows.append(row)
+            ob = api.bridge_ratio(ctx, torch.stack(rows), n_draws, n_chains, groups=32)
+            if ok(ob["r"], ob["se"]) or time.perf_counter() - t > 120.0:
+                break
+            target *= 2
+        dt = time.perf_counter() - t
+        ch.close()
+        return {"seconds": dt, "steps_per_chain": burn + thin * len(rows), "chains": n_chains, "rows": len(rows),
+                "draws_per_row": n_draws, "intensity": ob["r"], "std_err": ob["se"],
+                "geometric": ob["geometric"], "reached": bool(ok(ob["r"], ob["se"]))}
+
+    out["tree_moves_optimal_bridge"] = run_tree_bridge(65_536, 10_000 if geom_name == "plain" else 40_000, 500,
+                                                       65_536, 8)
     # tracer with doubling photon budgets
     t = time.perf_counter()
     photons, acc = 1_000_000, []
