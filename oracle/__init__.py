@@ -134,6 +134,8 @@ def lib():
             L.or_tree_coords.argtypes = [_dp, C.c_int, _dp, _dp]; L.or_tree_coords.restype = C.c_double
             L.or_tree_path.argtypes = [_dp, C.c_int, _dp, _dp]
             L.or_tree_vref.argtypes = [S, D, _dp]
+            L.or_hmc_leapfrog.argtypes = [M, S, D, C.c_int, _dp, _dp, C.c_double, C.c_int]
+            L.or_hmc_leapfrog.restype = C.c_double
             L.or_run_chains_hist.argtypes = [M, S, D, R, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint64,
                                              _dp, _ip, C.POINTER(Acc), _dp, _dp, C.c_int]
             _lib = L
@@ -391,6 +393,14 @@ def tree_vref(s: Source, d: Sensor):
     v = np.zeros(3)
     lib().or_tree_vref(C.byref(s), C.byref(d), _ptr(v))
     return v
+
+
+def hmc_leapfrog(m, s, d, path, momenta, eps, steps):
+    """(x', p', log p(x')) after `steps` leapfrog steps of size eps."""
+    x = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 3).copy()
+    p = np.ascontiguousarray(momenta, dtype=np.float64).reshape(-1, 3).copy()
+    lp = lib().or_hmc_leapfrog(C.byref(m), C.byref(s), C.byref(d), len(x), _ptr(x), _ptr(p), float(eps), int(steps))
+    return x, p, lp
 
 
 def tree_coords(v_ref, path):

@@ -794,6 +794,29 @@ static void record_state(const chain_job* J, or_acc* a, int n, const double* f, 
   }
 }
 
+/* One HMC trajectory of the path density (the move's deterministic part):
+ * from positions x (n x 3, source and end vertex held) and momenta p (n x 3,
+ * interior rows used), L leapfrog steps of size eps with the force
+ * d log p / d f (zero where the density is zero); x and p are updated in
+ * place.  Returns log p at the end point. */
+double or_hmc_leapfrog(const or_medium* m, const or_source* s, const or_sensor* d, int n, double* x, double* p,
+                       double eps, int L) {
+  double* g = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  or_grad_logp(m, s, d, n, x, g);
+  for (int i = 1; i <= n - 2; ++i)
+    for (int q = 0; q < 3; ++q) p[3 * i + q] += 0.5 * eps * g[3 * i + q];
+  for (int st = 1; st <= L; ++st) {
+    for (int i = 1; i <= n - 2; ++i)
+      for (int q = 0; q < 3; ++q) x[3 * i + q] += eps * p[3 * i + q];
+    or_grad_logp(m, s, d, n, x, g);
+    double h = (st == L) ? 0.5 * eps : eps;
+    for (int i = 1; i <= n - 2; ++i)
+      for (int q = 0; q < 3; ++q) p[3 * i + q] += h * g[3 * i + q];
+  }
+  free(g);
+  return or_logp(m, s, d, n, x);
+}
+
 /* The chains' target: the path density, or (toy_s > 0, pins only) a product
  * density with known sector weights: P(n) proportional to toy_w[n], interior
  * vertex k of an n-vertex path ~ N(mu_k, toy_s^2 I) with mu_k on the segment
@@ -874,7 +897,7 @@ static void* chain_worker(void* arg) {
           for (int q = 0; q < 3; ++q) J->coords[3 * mm + q] += step * z[q];
         }
         or_tree_path(J->v_ref, n, J->coords, y);
-        lpy = or_logp(m, J->s, J->d, n, y);
+        lpy = target_logp(J, n, y);
         if (isfinite(lpy)) {
           double ljy = or_tree_coords(J->v_ref, n, y, J->coords);
           logA = lpy + ljy - lpx - ljx;

@@ -211,6 +211,12 @@ double or_tree_coords(const double v_ref[3], int n, const double* path, double* 
 /* Path from f_0 = path[0..2], f_{n-1} = path[3(n-1)..] and the coordinates of
  * the interior vertices (top-down); writes path[3..3(n-1)). */
 void or_tree_path(const double v_ref[3], int n, const double* coords, double* path);
+/* The HMC move's deterministic part: L leapfrog steps of size eps of the
+ * interior vertices x with momenta p (both n x 3, updated in place; the
+ * source and the end vertex are held), force d log p / d f (zero where
+ * p = 0).  Returns log p at the end point. */
+double or_hmc_leapfrog(const or_medium* m, const or_source* s, const or_sensor* d, int n, double* x, double* p,
+                       double eps, int L);
 /* The root frame's reference vector of a pair: the first vector of the
  * orthonormal completion of the unit source -> sensor-centre direction. */
 void or_tree_vref(const or_source* s, const or_sensor* d, double v_ref[3]);

@@ -194,3 +194,75 @@ def test_hmc_chain_matches_forward_tracer_all_orders(oracle_lib):
     zc = z2 * h / h[2]
     for k in (3, 4, 5):
         assert abs(zc[k] / tr["hist"][k - 2] - 1) < 0.05, (k, zc[k], tr["hist"][k - 2])
+
+
+def _hmc_path(n, seed):
+    xyz, _ = S.random_paths((0.0, 0.0, 0.0), (0.0, 0.0, 1.5), 0.5, 1, n, n, n, seed, lateral=0.2)
+    return xyz[:, 0, :n].T.astype(np.float64)
+
+
+def test_leapfrog_is_reversible_and_volume_preserving(oracle_lib):
+    """The HMC map (x, p) -> (x', p') of the oracle: running it from (x', -p')
+    returns to (x, -p), and its Jacobian determinant over the interior
+    coordinates and momenta is 1 (finite differences) -- the two properties
+    that make the Hamiltonian acceptance ratio exact."""
+    O = oracle_lib
+    med = S.Medium(lambda_s=1.0, lambda_a=5.0, g=0.6)
+    m, s, d = O.medium(med), O.source(S.Source()), O.sensor(S.Sensor((0.0, 0.0, 1.5), 0.5))
+    rng = np.random.default_rng(3)
+    n = 5
+    for seed in range(4, 200):   # a start whose trajectory stays where the density is positive
+        x = _hmc_path(n, seed)
+        p = rng.normal(size=(n, 3))
+        x1, p1, lp1 = O.hmc_leapfrog(m, s, d, x, p, 0.01, 6)
+        if np.isfinite(O.logp(m, s, d, x)) and np.isfinite(lp1):
+            break
+    assert np.isfinite(lp1)
+    x2, p2, _ = O.hmc_leapfrog(m, s, d, x1, -p1, 0.01, 6)
+    assert np.abs(x2 - x).max() < 1e-10 and np.abs(-p2[1:-1] - p[1:-1]).max() < 1e-9
+    # volume preservation over (interior x, interior p)
+    dim = 3 * (n - 2)
+
+    def flat(xx, pp):
+        return np.concatenate([xx[1:-1].ravel(), pp[1:-1].ravel()])
+
+    z0 = flat(x, p)
+    Jm = np.zeros((2 * dim, 2 * dim))
+    h = 1e-6
+    for a in range(2 * dim):
+        out = []
+        for sgn in (1, -1):
+            z = z0.copy()
+            z[a] += sgn * h
+            xx, pp = x.copy(), p.copy()
+            xx[1:-1] = z[:dim].reshape(-1, 3)
+            pp[1:-1] = z[dim:].reshape(-1, 3)
+            xo, po, _ = O.hmc_leapfrog(m, s, d, xx, pp, 0.01, 6)
+            out.append(flat(xo, po))
+        Jm[:, a] = (out[0] - out[1]) / (2 * h)
+    assert abs(np.linalg.det(Jm) - 1.0) < 1e-5
+
+
+def test_tree_moves_balance_a_toy_target(oracle_lib):
+    """Tree-coordinate moves with births and deaths on the toy product target
+    (P(n) proportional to w_n, interior vertices Gaussian about the axis):
+    the vertex-count distribution comes out right, which a wrong tree
+    Jacobian would shift through the vertices' spread."""
+    import ctypes as C
+    O = oracle_lib
+    cap = 6
+    w = np.zeros(cap + 1)
+    w[2:] = [1.0, 2.0, 1.5, 0.7, 0.3]
+    sc = S.plain()
+    sc.run = S.Run(seed=sc.run.seed, burn_in=2000, within=S.WITHIN_TREE, sigma=0.8)
+    ch = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, cap)
+    ch.r.toy_s = 0.1
+    ch.r.toy_w = w.ctypes.data_as(C.POINTER(C.c_double))
+    H = np.zeros((64, cap + 1))
+    ch.run(100_000, n_hist=H)
+    P = H / H.sum(axis=1, keepdims=True)
+    mean, se = P.mean(axis=0), P.std(axis=0, ddof=1) / math.sqrt(64)
+    ref = w / w.sum()
+    for k in range(2, cap + 1):
+        assert abs(mean[k] - ref[k]) < 4 * se[k], (k, mean[k], ref[k], se[k])
+    assert np.abs(mean - ref).max() < 0.015
