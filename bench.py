@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--warps-per-block", type=int, default=0)
+    p.add_argument("--layout", choices=["auto", "warp", "lane"], default="auto",
+                   help="chain layout of the kernel: the autotuner's choice, one warp or one lane per chain")
     p.add_argument("--time-to-target", type=float, default=0.0,
                    help="instead of the throughput line: wall time to this relative intensity error for plain "
                         "RJMCMC, batched MALA chains and the GPU forward tracer on the plain / detector geometry")
@@ -307,6 +309,7 @@ def ours(args):
     ctx = api.Context(local)
     medium = api.Medium(ctx, sc.medium)
     geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    sc.run.layout = {"auto": 0, "warp": 1, "lane": 2}[args.layout]  # scenes.LAYOUT_*
     chains = api.Chains(ctx, medium, geom, sc.run, warps_per_block=args.warps_per_block)
     stream = torch.cuda.current_stream()
     n_chains = sc.total_chains

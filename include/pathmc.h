@@ -71,6 +71,13 @@ extern "C" {
 #define PMC_WITHIN_TREE 2
 #define PMC_WITHIN_HMC 3
 
+/* Chain layout of the kernel (pmc_run_desc.layout). */
+#define PMC_LAYOUT_AUTO 0      /* autotuner's choice (warp layout when warps_per_block is given) */
+#define PMC_LAYOUT_WARP 1      /* one warp per chain */
+#define PMC_LAYOUT_LANE 2      /* one lane per chain: lean runs only (homogeneous medium, isotropic
+                                  emission, rho = 1, pure Henyey-Greenstein, Gaussian perturbations,
+                                  no PMC_FLAG_GRADIENTS) */
+
 #define PMC_FLAG_GRADIENTS 1   /* accumulate score terms for pmc_grad_estimator */
 #define PMC_FLAG_NO_GRAPH 2    /* launch kernels directly instead of replaying a CUDA graph */
 
@@ -182,6 +189,11 @@ typedef struct {
                                       entries beyond it live in global memory.  0 = the whole cap
                                       (or the autotuner's choice when warps_per_block = 0) */
   int hmc_steps;                   /* PMC_WITHIN_HMC: leapfrog steps per move (1..1000) */
+  int layout;                      /* PMC_LAYOUT_*.  LANE: each chain on one lane of a warp, its first
+                                      smem_window vertices (any value >= 2; 0 = 16 or the autotuner's
+                                      choice) in shared memory; the same Markov chain and random
+                                      numbers as the warp layout.  Fails with PMC_ERR_INVALID for
+                                      runs that are not lean */
 } pmc_run_desc;
 
 /* Per-pair estimate returned by pmc_read_estimator. */

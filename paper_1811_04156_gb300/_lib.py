@@ -17,6 +17,7 @@ ERRORS = {1: "PMC_ERR_INVALID", 2: "PMC_ERR_OOM", 3: "PMC_ERR_CUDA", 4: "PMC_ERR
           5: "PMC_ERR_ABORTED", 6: "PMC_ERR_NO_DEVICE"}
 PMC_FLAG_GRADIENTS = 1
 PMC_FLAG_NO_GRAPH = 2
+PMC_LAYOUT_AUTO, PMC_LAYOUT_WARP, PMC_LAYOUT_LANE = 0, 1, 2
 PMC_ACC_WORDS = 16
 PMC_NOALLOC_MAX_PAIRS = 128
 
@@ -61,7 +62,8 @@ class RunDesc(C.Structure):
                 ("thin_bridge", C.c_uint32), ("init", C.c_int), ("init_k", C.c_int),
                 ("init_jitter", C.c_double), ("init_xyz", C.POINTER(C.c_float)),
                 ("init_n", C.POINTER(C.c_int)), ("init_stride", C.c_int), ("flags", C.c_int),
-                ("warps_per_block", C.c_int), ("smem_window", C.c_int), ("hmc_steps", C.c_int)]
+                ("warps_per_block", C.c_int), ("smem_window", C.c_int), ("hmc_steps", C.c_int),
+                ("layout", C.c_int)]
 
 
 class Estimate(C.Structure):

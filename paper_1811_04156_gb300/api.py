@@ -166,6 +166,7 @@ def run_desc(r: S.Run, flags: int = 0, warps_per_block: int = 0, user_xyz: Optio
     d.warps_per_block = int(warps_per_block)
     d.smem_window = int(smem_window)
     d.hmc_steps = int(getattr(r, "hmc_steps", 10))
+    d.layout = int(getattr(r, "layout", 0))
     keep = ()
     if user_xyz is not None:
         ux = np.ascontiguousarray(user_xyz, dtype=np.float32)  # [chains][3][stride]

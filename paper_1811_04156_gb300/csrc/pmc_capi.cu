@@ -72,7 +72,7 @@ struct pmc_ctx_s {
   int n_sm = 0;
   size_t smem_per_sm = 0, smem_per_block = 0;
   // autotuned warps per block, keyed by (kernel instantiation, shared vertex cap, chain-count bucket)
-  std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;  // -> (warps per block, shared window)
+  std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> tuned;  // -> (warps per block, shared window, kind)
 };
 
 struct pmc_medium_s {
@@ -147,7 +147,8 @@ struct pmc_geom_s {
 };
 
 struct ChainClass {
-  int smem_cap = 0;   // shared window (vertices per warp)
+  int kind = 0;       // kernel kind of launch_chain (4: one lane per chain)
+  int smem_cap = 0;   // shared window (vertices per chain)
   int max_cap = 0;    // largest vertex cap of the class's chains
   bool spill = false; // smem_cap < max_cap: entries beyond the window live in global memory
   int lo = 0, hi = 0;  // range into the processing order
@@ -188,6 +189,7 @@ struct pmc_chains_s {
   int general = 0;                 // chain kernel: 0 lean, 1 general, 2 with tree moves, 3 with HMC moves
   bool grad = false;               // keep d log sigma / dg per vertex
   bool autotune = false;           // warps per block chosen by timing
+  int layout = PMC_LAYOUT_AUTO;    // PMC_LAYOUT_*: which chain layouts the autotuner may pick
   int init_kind = 0, init_k = 0;
   float init_jitter = 0.f;
   QrefPair* d_qp = nullptr;       // reference-density tables (pmc_bridge)
@@ -484,6 +486,9 @@ int pmc_destroy_chains(pmc_chains_t ch) {
   return PMC_OK;
 }
 
+// Work items of a launch: one per chain, or one per 32 chains (lane layout).
+static int work_items(int kind, int chains) { return kind == 4 ? (chains + 31) / 32 : chains; }
+
 static ChainParams class_params(pmc_chains_t ch, size_t k, unsigned long long n_steps) {
   const ChainClass& cl = ch->classes[k];
   ChainParams p{};
@@ -509,11 +514,12 @@ static ChainParams class_params(pmc_chains_t ch, size_t k, unsigned long long n_
 }
 
 // Autotuner: for every cap class, time the chain kernel over candidate launch
-// shapes — 1, 2 or 4 warps (chains) per block, and a shared window of the
-// whole cap or of 128 / 256 / 512 vertices (entries beyond it in global
-// memory) — on a scratch copy of the freshly initialised state (256 steps,
-// best of two probes), and keep the fastest; choices are cached per device,
-// kernel and class.
+// shapes — 1, 2 or 4 warps per block; with one warp per chain a shared
+// window of the whole cap or of 128 / 256 / 512 vertices (entries beyond it
+// in global memory); with one lane per chain (lean runs) a per-lane window
+// of 8, 16 or 32 vertices — on a scratch copy of the freshly initialised
+// state (256 steps, best of two probes), and keep the fastest; choices are
+// cached per device, kernel, layout request and class.
 static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
   const int T = ch->total;
   float* sx = nullptr;
@@ -521,7 +527,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
   unsigned long long* sst = nullptr;
   double* sacc = nullptr;
   int* sstat = nullptr;
-  const int kind = ch->general * 2 + ch->grad;
+  const int kind = (ch->general * 2 + ch->grad) * 3 + ch->layout;
   auto bucket_of = [](int chains) { return 31 - __builtin_clz(static_cast<unsigned>(std::max(1, chains))); };
   bool need = false;
   for (auto& cl : ch->classes)
@@ -543,21 +549,34 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
     const int full = (cl.max_cap + 31) / 32 * 32;
     const auto key = std::make_tuple(kind, cl.max_cap, bucket_of(chains));
     auto it = ch->ctx->tuned.find(key);
-    std::pair<int, int> best(cl.warps_per_block, full);
+    std::tuple<int, int, int> best(cl.warps_per_block, cl.smem_cap, cl.kind);
     if (it != ch->ctx->tuned.end()) {
       best = it->second;
     } else {
       float best_ms = 1e30f;
-      std::vector<int> windows = {full};
-      for (int w : {128, 256, 512})
-        if (w < full && ch->general < 2) windows.push_back(w);  // tree and HMC moves keep the whole cap
-      for (int win : windows) {
+      // candidates (kind, shared window): the warp layout with the whole cap
+      // or a window with global spill (tree and HMC moves keep the whole
+      // cap); the lane layout (lean runs without gradient caches) with
+      // per-lane windows of 8 to 32 vertices
+      std::vector<std::pair<int, int>> cands;
+      if (ch->layout != PMC_LAYOUT_LANE) {
+        cands.emplace_back(ch->general, full);
+        for (int w : {128, 256, 512})
+          if (w < full && ch->general < 2) cands.emplace_back(ch->general, w);
+      }
+      if (ch->layout != PMC_LAYOUT_WARP && ch->general == 0 && !ch->grad)
+        for (int w : {8, 16, 32}) {
+          cands.emplace_back(4, std::min(w, cl.max_cap));
+          if (w >= cl.max_cap) break;
+        }
+      for (const auto& cand : cands) {
+        const int ckind = cand.first, win = cand.second;
         for (int wpb : {1, 2, 4}) {
-          const bool spill = win < full;
-          if (chain_smem_bytes(win, wpb, ch->general, ch->grad) > ch->ctx->smem_per_block) continue;
+          const bool spill = ckind != 4 && win < full;
+          if (chain_smem_bytes(win, wpb, ckind, ch->grad) > ch->ctx->smem_per_block) continue;
           int bps = 0;
-          if (chain_occupancy(ch->general, ch->grad, spill, wpb, win, &bps) != cudaSuccess || bps < 1) continue;
-          const int grid = std::max(1, std::min((chains + wpb - 1) / wpb, bps * ch->ctx->n_sm));
+          if (chain_occupancy(ckind, ch->grad, spill, wpb, win, &bps) != cudaSuccess || bps < 1) continue;
+          const int grid = std::max(1, std::min((work_items(ckind, chains) + wpb - 1) / wpb, bps * ch->ctx->n_sm));
           ChainParams p = class_params(ch, k, 256);
           p.smem_cap = win;
           p.xyz = sx;
@@ -578,7 +597,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
             if (e == cudaSuccess) e = cudaMemsetAsync(sstat, 0, sizeof(int) * T, s);
             if (e == cudaSuccess) e = cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s);
             if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-            if (e == cudaSuccess) e = launch_chain(p, ch->general, ch->grad, spill, grid, wpb, s);
+            if (e == cudaSuccess) e = launch_chain(p, ckind, ch->grad, spill, grid, wpb, s);
             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float t = 0.f;
@@ -591,7 +610,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
           }
           if (ms < best_ms) {
             best_ms = ms;
-            best = std::make_pair(wpb, win);
+            best = std::make_tuple(wpb, win, ckind);
           }
         }
         if (rc != PMC_OK) break;
@@ -599,13 +618,14 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
       if (rc == PMC_OK) ch->ctx->tuned[key] = best;
     }
     int bps = 0;
-    const bool spill = best.second < full;
-    if (rc == PMC_OK && chain_occupancy(ch->general, ch->grad, spill, best.first, best.second, &bps) == cudaSuccess &&
-        bps >= 1) {
-      cl.warps_per_block = best.first;
-      cl.smem_cap = best.second;
+    const int bw = std::get<0>(best), bwin = std::get<1>(best), bkind = std::get<2>(best);
+    const bool spill = bkind != 4 && bwin < full;
+    if (rc == PMC_OK && chain_occupancy(bkind, ch->grad, spill, bw, bwin, &bps) == cudaSuccess && bps >= 1) {
+      cl.kind = bkind;
+      cl.warps_per_block = bw;
+      cl.smem_cap = bwin;
       cl.spill = spill;
-      cl.grid = std::max(1, std::min((chains + best.first - 1) / best.first, bps * ch->ctx->n_sm));
+      cl.grid = std::max(1, std::min((work_items(bkind, chains) + bw - 1) / bw, bps * ch->ctx->n_sm));
     }
   }
   cudaEventDestroy(e0);
@@ -642,7 +662,10 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   if (r->init == PMC_INIT_USER && (!r->init_xyz || !r->init_n || r->init_stride < 2))
     return fail(PMC_ERR_INVALID, "USER init needs init_xyz, init_n and init_stride");
   if (r->kappa_end < 0 || !std::isfinite(r->kappa_end)) return fail(PMC_ERR_INVALID, "bad kappa_end");
-  if (r->smem_window < 0 || r->smem_window % 32 != 0) return fail(PMC_ERR_INVALID, "smem_window must be a multiple of 32");
+  if (r->layout < PMC_LAYOUT_AUTO || r->layout > PMC_LAYOUT_LANE) return fail(PMC_ERR_INVALID, "bad layout");
+  if (r->layout == PMC_LAYOUT_LANE ? (r->smem_window < 0 || r->smem_window == 1)
+                                   : (r->smem_window < 0 || r->smem_window % 32 != 0))
+    return fail(PMC_ERR_INVALID, "smem_window must be a multiple of 32 (lane layout: >= 2)");
   CK(cudaSetDevice(ctx->device));
 
   auto ch = std::unique_ptr<pmc_chains_s, int (*)(pmc_chains_t)>(new pmc_chains_s, pmc_destroy_chains);
@@ -683,6 +706,10 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
                             [](const DPair& d) { return d.emission != PMC_EMIT_ISOTROPIC || d.rho != PMC_RHO_ONE; });
   if (r->within == PMC_WITHIN_TREE) ch->general = 2;
   if (r->within == PMC_WITHIN_HMC) ch->general = 3;
+  ch->layout = r->layout;
+  if (r->layout == PMC_LAYOUT_LANE && (ch->general != 0 || ch->grad))
+    return fail(PMC_ERR_INVALID, "the lane layout runs lean chains only (homogeneous medium, isotropic emission, "
+                                 "rho = 1, Henyey-Greenstein, Gaussian perturbations, no gradients)");
   const int n_arrays = chain_arrays(ch->general > 0, ch->grad);
   const int T = ch->total;
   ch->h_base.resize(T);
@@ -716,10 +743,14 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
       ++hi;
     }
     ChainClass cl;
+    cl.kind = ch->general;
     cl.smem_cap = (maxcap + 31) / 32 * 32;
     cl.max_cap = maxcap;
     cl.spill = false;
-    if (r->smem_window > 0 && r->smem_window < cl.smem_cap && ch->general >= 2)
+    if (r->layout == PMC_LAYOUT_LANE) {
+      cl.kind = 4;
+      cl.smem_cap = std::min(r->smem_window > 0 ? r->smem_window : 16, maxcap);
+    } else if (r->smem_window > 0 && r->smem_window < cl.smem_cap && ch->general >= 2)
       return fail(PMC_ERR_INVALID, "tree and HMC moves need the whole vertex cap in shared memory (smem_window)");
     if (r->smem_window > 0 && r->smem_window < cl.smem_cap) {
       cl.smem_cap = r->smem_window;
@@ -736,13 +767,12 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   for (auto& cl : ch->classes) {
     int wpb = r->warps_per_block > 0 ? r->warps_per_block : 4;
     wpb = std::min(wpb, 4);
-    while (wpb > 1 && chain_smem_bytes(cl.smem_cap, wpb, ch->general, ch->grad) > ctx->smem_per_block) wpb /= 2;
-    if (chain_smem_bytes(cl.smem_cap, wpb, ch->general, ch->grad) > ctx->smem_per_block) return fail(PMC_ERR_INVALID, "vertex cap too large for shared memory");
+    while (wpb > 1 && chain_smem_bytes(cl.smem_cap, wpb, cl.kind, ch->grad) > ctx->smem_per_block) wpb /= 2;
+    if (chain_smem_bytes(cl.smem_cap, wpb, cl.kind, ch->grad) > ctx->smem_per_block) return fail(PMC_ERR_INVALID, "vertex cap too large for shared memory");
     int bps = 0;
-    CK(chain_occupancy(ch->general, ch->grad, cl.spill, wpb, cl.smem_cap, &bps));
+    CK(chain_occupancy(cl.kind, ch->grad, cl.spill, wpb, cl.smem_cap, &bps));
     if (bps < 1) return fail(PMC_ERR_INVALID, "chain kernel does not fit on an SM");
-    const int chains = cl.hi - cl.lo;
-    const int want = (chains + wpb - 1) / wpb;
+    const int want = (work_items(cl.kind, cl.hi - cl.lo) + wpb - 1) / wpb;
     cl.warps_per_block = wpb;
     cl.grid = std::max(1, std::min(want, bps * ctx->n_sm));
   }
@@ -881,7 +911,7 @@ static int enqueue_steps(pmc_chains_t ch, unsigned long long n_steps, cudaStream
   for (size_t k = 0; k < ch->classes.size(); ++k) {
     const ChainClass& cl = ch->classes[k];
     CK(cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s));
-    CK(launch_chain(class_params(ch, k, n_steps), ch->general, ch->grad, cl.spill, cl.grid, cl.warps_per_block, s));
+    CK(launch_chain(class_params(ch, k, n_steps), cl.kind, ch->grad, cl.spill, cl.grid, cl.warps_per_block, s));
   }
   return PMC_OK;
 }
@@ -1028,7 +1058,7 @@ int pmc_chains_launch_info(pmc_chains_t ch, int* out, int max_rows, int* n_class
     row[2] = cl.hi;
     row[3] = cl.warps_per_block;
     row[4] = cl.grid;
-    row[5] = ch->general;
+    row[5] = cl.kind;
   }
   return PMC_OK;
 }

@@ -103,51 +103,6 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Factors attached to vertex v of an n-vertex path: its vertex factor (and
-// d log sigma / d g) and, when v <= n-2, the factor of the segment v -> v+1.
-template <bool kGen>
-__device__ __forceinline__ void vertex_and_segment(const DMedium& M, const DPair& S, float zoff, float3 Pp, float3 Pc,
-                                                   float3 Pn, int v, int n, float& vt, float& gt, float& seg,
-                                                   float& tb, float& len) {
-  constexpr bool F = true;
-  gt = 0.f;
-  seg = 0.f;
-  tb = 0.f;
-  len = 0.f;
-  const float3 b0 = Pn - Pc;
-  const float bb = dot(b0, b0);
-  const float ib = rsqrtf(bb);
-  const float3 b = ib * b0;
-  if (v <= n - 2) {
-    const float ell = bb * ib;
-    float ta, tbv;
-    if constexpr (kGen) {
-      seg_tau(M, Pc.z + zoff, Pn.z + zoff, ell, ta, tbv);
-    } else {
-      ta = M.a * ell;
-      tbv = M.b * ell;
-    }
-    seg = -(ta + tbv) - m_log<F>(bb);
-    tb = tbv;
-    len = ell;
-    if (!(bb > 0.0f)) seg = kNegInf;
-    if (v <= n - 3 && hits_ball<F>(S, Pc, b0)) seg = kNegInf;
-  }
-  if (v == 0) {
-    if constexpr (kGen) vt = emission_term(S, b);
-    else vt = -kLog4Pi;
-    return;
-  }
-  const float3 a0 = Pc - Pp;
-  const float3 a = rsqrtf(dot(a0, a0)) * a0;
-  if (v == n - 1) {
-    vt = sensor_term<F>(S, a, Pc);
-    return;
-  }
-  const float lb = kGen ? log_b_at(M, Pc.z + zoff) : M.log_b;
-  vt = lb + phase_term<F, kGen>(M, a, b, gt);
-}
-
 // d log p / d f_v with the terms spread over lanes: lanes 0-1 the two segment
 // factors that end / start at v, lanes 2-4 the scattering angles at v-1, v,
 // v+1, lane 5 the emission and detection factors; a shuffle tree sums them
@@ -1201,6 +1156,7 @@ int kernel_key(int kind, bool grad, bool spill) {
 int chain_arrays(bool general, bool grad) { return 6 + (general ? 1 : 0) + (grad ? 1 : 0); }
 
 size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad) {
+  if (kind == 4) return lane_smem_bytes(smem_cap, warps_per_block);
   const size_t arrays = static_cast<size_t>(chain_arrays(kind > 0, grad) + (kind == 2 ? 3 : 0) + (kind == 3 ? 6 : 0));
   return static_cast<size_t>(warps_per_block) *
          (arrays * static_cast<size_t>(smem_cap) + 32u * kRngWords + kPairWords) * sizeof(float);
@@ -1208,6 +1164,7 @@ size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad) 
 
 cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block, int smem_cap,
                             int* blocks_per_sm) {
+  if (kind == 4) return grad ? cudaErrorInvalidValue : lane_occupancy(warps_per_block, smem_cap, blocks_per_sm);
   if (kind >= 2 && spill) return cudaErrorInvalidValue;
   const size_t sm = chain_smem_bytes(smem_cap, warps_per_block, kind, grad);
   switch (kernel_key(kind, grad, spill)) {
@@ -1228,6 +1185,7 @@ cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block
 
 cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s) {
+  if (kind == 4) return grad ? cudaErrorInvalidValue : launch_lane_chain(p, grid, warps_per_block, s);
   if (kind >= 2 && spill) return cudaErrorInvalidValue;
   const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block, kind, grad);
   switch (kernel_key(kind, grad, spill)) {

@@ -453,4 +453,52 @@ __device__ __forceinline__ float log_insert_density(const DMedium& M, const DRun
          2.0f * m_log<F>(d1 * d2 * (d1 + d2)) - kLog2Pi;
 }
 
+// ---------------------------------------------------------------------------
+// Chain kernels (warp per chain and lane per chain)
+// ---------------------------------------------------------------------------
+// Factors attached to vertex v of an n-vertex path: its vertex factor (and
+// d log sigma / d g) and, when v <= n-2, the factor of the segment v -> v+1.
+template <bool kGen>
+__device__ __forceinline__ void vertex_and_segment(const DMedium& M, const DPair& S, float zoff, float3 Pp, float3 Pc,
+                                                   float3 Pn, int v, int n, float& vt, float& gt, float& seg,
+                                                   float& tb, float& len) {
+  constexpr bool F = true;  // SFU forms
+  gt = 0.f;
+  seg = 0.f;
+  tb = 0.f;
+  len = 0.f;
+  const float3 b0 = Pn - Pc;
+  const float bb = dot(b0, b0);
+  const float ib = rsqrtf(bb);
+  const float3 b = ib * b0;
+  if (v <= n - 2) {
+    const float ell = bb * ib;
+    float ta, tbv;
+    if constexpr (kGen) {
+      seg_tau(M, Pc.z + zoff, Pn.z + zoff, ell, ta, tbv);
+    } else {
+      ta = M.a * ell;
+      tbv = M.b * ell;
+    }
+    seg = -(ta + tbv) - m_log<F>(bb);
+    tb = tbv;
+    len = ell;
+    if (!(bb > 0.0f)) seg = kNegInf;
+    if (v <= n - 3 && hits_ball<F>(S, Pc, b0)) seg = kNegInf;
+  }
+  if (v == 0) {
+    if constexpr (kGen) vt = emission_term(S, b);
+    else vt = -kLog4Pi;
+    return;
+  }
+  const float3 a0 = Pc - Pp;
+  const float3 a = rsqrtf(dot(a0, a0)) * a0;
+  if (v == n - 1) {
+    vt = sensor_term<F>(S, a, Pc);
+    return;
+  }
+  const float lb = kGen ? log_b_at(M, Pc.z + zoff) : M.log_b;
+  vt = lb + phase_term<F, kGen>(M, a, b, gt);
+}
+
 }  // namespace pmc

@@ -1,0 +1,465 @@
+// Lane-per-chain RJMCMC kernel for the lean case (homogeneous medium,
+// isotropic emission, detection probability 1, Henyey-Greenstein phase
+// function, Gaussian vertex perturbations and vMF end moves, no gradient
+// caches): the same Markov chain as the warp-per-chain kernel in
+// pmc_chain.cu (Collin, arXiv:1811.04156: section "Numerical path
+// integration", Eq. acceptFact; appendix "Jump proposal" and "Dimension
+// matching transformation"), with the same Philox counters per step and the
+// same proposals and acceptance rule, but one chain per thread.
+//
+// Why: a perturbation changes O(1) factors, so a warp per chain leaves most
+// lanes idle on the 60 % of steps that are perturbations; with a chain per
+// lane every lane does useful work, and the warp serialises only the move
+// kinds that its 32 chains drew at that step.
+//
+// Layout: the first W vertices of each chain (W = smem_cap) live in the
+// warp's shared block as [array][vertex][lane] floats, so that every lane
+// stays in its own bank whatever vertex it touches; entries W..cap-1 live in
+// the chain's global block (array a at a * cap), as in the warp kernel's
+// spill mode.  Positions are read from and written back to the global block
+// at the start and end of a residency; the cached factors are rebuilt at the
+// start.
+#include <climits>
+
+#include "pmc_internal.h"
+
+namespace pmc {
+
+namespace {
+
+constexpr unsigned kAll = 0xffffffffu;
+constexpr int kArrays = 6;           // x, y, z, segment factor, segment length, vertex factor
+constexpr int kRefresh = 256;        // recompute the path length from the caches
+constexpr int kFlush = 64;           // FP32 partials -> FP64 accumulators
+enum { AX = 0, AY = 1, AZ = 2, ASEG = 3, ALEN = 4, AVT = 5 };
+enum Move { MV_INTERIOR = 0, MV_END = 1, MV_BIRTH = 2, MV_DEATH = 3 };
+
+struct LanePath {
+  float* sm;  // this lane's column of the warp's shared block
+  float* gm;  // the chain's global block
+  int W, cap;
+  __device__ __forceinline__ float ld(int a, int i) const {
+    return (i < W) ? sm[(a * W + i) * 32] : gm[a * cap + i];
+  }
+  __device__ __forceinline__ void st(int a, int i, float v) const {
+    if (i < W) sm[(a * W + i) * 32] = v;
+    else gm[a * cap + i] = v;
+  }
+  __device__ __forceinline__ float3 pos(int i) const { return f3(ld(AX, i), ld(AY, i), ld(AZ, i)); }
+  __device__ __forceinline__ void set_pos(int i, float3 p) const {
+    st(AX, i, p.x);
+    st(AY, i, p.y);
+    st(AZ, i, p.z);
+  }
+};
+
+// Per-chain recording state: the current state's observables enter the sums
+// once, weighted by the steps it stayed current (at or after burn-in).
+struct LaneAcc {
+  unsigned long long pn2, pn, t_a;
+  float pL, pL2;
+  unsigned int nflush;
+  unsigned int prop_w, prop_end, prop_b, prop_d;
+  unsigned int acc_i, acc_e, acc_b, acc_d;
+};
+
+__device__ __forceinline__ void lane_close(LaneAcc& a, unsigned long long t_b, unsigned long long burn_in, int n,
+                                           float L) {
+  const unsigned long long from = a.t_a > burn_in ? a.t_a : burn_in;
+  a.t_a = t_b;
+  if (t_b <= from) return;
+  const unsigned long long d = t_b - from;
+  const float dw = static_cast<float>(d);
+  a.pn2 += (n == 2) ? d : 0ull;
+  a.pn += static_cast<unsigned long long>(n) * d;
+  a.pL = fmaf(L, dw, a.pL);
+  a.pL2 = fmaf(L * L, dw, a.pL2);
+  a.nflush++;
+}
+
+__device__ __forceinline__ void lane_flush(LaneAcc& a, double* acc) {
+  acc[ACC_NDIRECT] += static_cast<double>(a.pn2);
+  acc[ACC_SUMN] += static_cast<double>(a.pn);
+  acc[ACC_SUML] += static_cast<double>(a.pL);
+  acc[ACC_SUML2] += static_cast<double>(a.pL2);
+  a.pn2 = a.pn = 0ull;
+  a.pL = a.pL2 = 0.f;
+  a.nflush = 0;
+}
+
+// Every step of one chain's residency, on one lane.  Mirrors the warp
+// kernel's step: move draw, proposal, change of log p over the changed
+// window, acceptance, commit; sums that the warp kernel forms with shuffles
+// are formed here in the same association where they decide acceptance.
+__device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* col, int W, uint32_t key0,
+                                          uint32_t key1) {
+  const DMedium& M = P.M;
+  const DRun& R = P.R;
+  const DPair S = P.pairs[P.chain_pair[c]];
+  const int cap = S.cap;
+  int n = P.n[c];
+  const unsigned long long step0 = P.step[c];
+  if (n < 2 || n > cap) {
+    P.status[c] |= ST_BAD_N;
+    atomicOr(P.any_status, ST_BAD_N);
+    return;
+  }
+  LanePath w;
+  w.sm = col;
+  w.gm = P.xyz + P.chain_base[c];
+  w.W = W;
+  w.cap = cap;
+  for (int i = 0; i < min(n, W); ++i) {
+    w.sm[(AX * W + i) * 32] = w.gm[AX * cap + i];
+    w.sm[(AY * W + i) * 32] = w.gm[AY * cap + i];
+    w.sm[(AZ * W + i) * 32] = w.gm[AZ * cap + i];
+  }
+  // cached factors of the whole path, with a sliding window of positions
+  float lp0 = 0.f, L = 0.f;
+  {
+    float3 Pp = w.pos(0), Pc = Pp;
+    for (int i = 0; i < n; ++i) {
+      const float3 Pn = (i <= n - 2) ? w.pos(i + 1) : Pc;
+      float vt, gt, seg, tb, len;
+      vertex_and_segment<false>(M, S, S.zoff, Pp, Pc, Pn, i, n, vt, gt, seg, tb, len);
+      w.st(AVT, i, vt);
+      lp0 += vt;
+      if (i <= n - 2) {
+        w.st(ASEG, i, seg);
+        w.st(ALEN, i, len);
+        lp0 += seg;
+        L += len;
+      }
+      Pp = Pc;
+      Pc = Pn;
+    }
+  }
+  if (!isfinite(lp0)) {
+    P.status[c] |= ST_NONFINITE;
+    atomicOr(P.any_status, ST_NONFINITE);
+    return;
+  }
+  LaneAcc A;
+  A.pn2 = A.pn = 0ull;
+  A.t_a = step0;
+  A.pL = A.pL2 = 0.f;
+  A.nflush = 0;
+  A.prop_w = A.prop_end = A.prop_b = A.prop_d = 0;
+  A.acc_i = A.acc_e = A.acc_b = A.acc_d = 0;
+  double* acc = P.acc + static_cast<size_t>(c) * ACC_WORDS;
+  const float3 cS = f3(S.c[0], S.c[1], S.c[2]);
+  const float3 cLo = f3(S.c_lo[0], S.c_lo[1], S.c_lo[2]);
+  unsigned long long done = 0;
+  bool aborted = false;
+  for (unsigned long long s = 0; s < P.n_steps; ++s) {
+    if ((s & 1023ull) == 0 && P.abort_flag != nullptr && *P.abort_flag) {
+      aborted = true;
+      break;
+    }
+    const unsigned long long t = step0 + s;
+    const uint4 ra = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32),
+                                              static_cast<uint32_t>(c), PUR_STEP_A), key0, key1);
+    const uint4 rb = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32),
+                                              static_cast<uint32_t>(c), PUR_STEP_B), key0, key1);
+    const uint32_t um = ra.x >> 9;
+    const uint32_t v23 = ra.y >> 9;
+    const float logu = __logf(u01(ra.z));
+    const float ub0 = u01(rb.x), ub1 = u01(rb.y), ub2 = u01(rb.z), ub3 = u01(rb.w);
+
+    int move;
+    bool proposed = true;
+    int n_new = n, wlo = 0, nc = 0, olo = 0, onc = 0, jj = -1, kk = -1;
+    int inew = -1, sh_from = INT_MAX, sh_by = 0;
+    float3 fnew = f3(0.f, 0.f, 0.f);
+    float extra = 0.f;
+    if (um < R.thr_within) {
+      A.prop_w++;
+      const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 1)) >> 23);
+      jj = j;
+      inew = j;
+      if (j == n - 1) {
+        // vMF step of the end vertex about its sensor normal
+        move = MV_END;
+        A.prop_end++;
+        const float3 nu = sensor_normal(S, w.pos(j));
+        float3 e1, e2;
+        onb(nu, e1, e2);
+        float s1, c1;
+        sincospif(2.0f * ub1, &s1, &c1);
+        const float wv = 1.0f + __fdividef(__logf(fmaf(1.0f - ub0, S.exp_m2ke, ub0)), S.kappa_end);
+        const float sw = m_sqrt<true>(fmaxf(0.f, 1.0f - wv * wv));
+        const float3 nn = wv * nu + sw * (c1 * e1 + s1 * e2);
+        fnew = cS + (cLo + S.R * nn);
+        wlo = n - 2; nc = 2; olo = n - 2; onc = 2;
+      } else {
+        // Gaussian step of an interior vertex (Box-Muller)
+        move = MV_INTERIOR;
+        float s1, c1, s2, c2;
+        const float r1 = m_sqrt<true>(-2.0f * __logf(ub0));
+        sincospif(2.0f * ub1, &s1, &c1);
+        const float r2 = m_sqrt<true>(-2.0f * __logf(ub2));
+        sincospif(2.0f * ub3, &s2, &c2);
+        const float3 z = f3(r1 * c1, r1 * s1, r2 * c2);
+        fnew = w.pos(j) + R.sigma * z;
+        wlo = j - 1; nc = 3; olo = j - 1; onc = 3;
+      }
+    } else if (um < R.thr_birth) {
+      move = MV_BIRTH;
+      A.prop_b++;
+      if (n >= cap) {
+        proposed = false;
+      } else {
+        // segment k with probability tau_b(k) / T_b (smallest k whose
+        // cumulative sum exceeds u T_b), then the bispherical insertion
+        const float ui = __fmaf_rn(static_cast<float>(v23), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
+        float total = 0.f;
+        for (int q = 0; q < n - 1; ++q) total += M.b * w.ld(ALEN, q);
+        const float target = ui * total;
+        int k = n - 2;
+        float cum = 0.f;
+        for (int q = 0; q < n - 1; ++q) {
+          cum += M.b * w.ld(ALEN, q);
+          if (cum > target) {
+            k = q;
+            break;
+          }
+        }
+        kk = k;
+        const float3 Af = w.pos(k), Bf = w.pos(k + 1);
+        const float3 r = Bf - Af;
+        const float rr = dot(r, r);
+        const float irl = rsqrtf(rr);
+        const float gamma = 0.5f * rr * irl;
+        const float3 rh = irl * r;
+        float3 xi, ze;
+        onb(rh, xi, ze);
+        const float beta = insertion_beta(M, R, S.zoff, Af, Bf, gamma);
+        float cs = -1.0f - __fdividef(__logf(fmaf(-ub0, 1.0f - __expf(-2.0f * beta), 1.0f)), beta);
+        cs = fminf(fmaxf(cs, -1.0f), 1.0f);
+        const float sn = m_sqrt<true>(fmaxf(0.f, (1.0f - cs) * (1.0f + cs)));
+        const float et = __fdividef(ub1, 1.0f - ub1);
+        const float iet = __fdividef(1.0f - ub1, ub1);
+        const float sht = 0.5f * (et - iet), cht = 0.5f * (et + iet);
+        float s3, c3;
+        sincospif(2.0f * ub2, &s3, &c3);
+        const float sc = __fdividef(gamma, cht - cs);
+        fnew = 0.5f * (Af + Bf) + sc * (sht * rh + sn * (c3 * xi + s3 * ze));
+        const float tbk = M.b * w.ld(ALEN, k);
+        extra = R.log_pd - __logf(static_cast<float>(n - 1)) - R.log_pb - __logf(__fdividef(tbk, total)) -
+                log_insert_density<true>(M, R, S.zoff, Af, Bf, fnew);
+        n_new = n + 1;
+        inew = k + 1;
+        sh_from = k + 2;
+        sh_by = -1;
+        wlo = k; nc = 3; olo = k; onc = 2;
+      }
+    } else {
+      move = MV_DEATH;
+      A.prop_d++;
+      if (n <= 2) {
+        proposed = false;
+      } else {
+        const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 2)) >> 23);
+        jj = j;
+        n_new = n - 1;
+        sh_from = j;
+        sh_by = 1;
+        wlo = j - 1; nc = 2; olo = j - 1; onc = 3;
+      }
+    }
+
+    bool accept = false;
+    float nvt[3] = {0.f, 0.f, 0.f}, nseg[2] = {0.f, 0.f}, nlen[2] = {0.f, 0.f};
+    float dlen = 0.f;
+    if (proposed) {
+      // new-path positions wlo-1 .. wlo+nc (old index shifted, or the new vertex)
+      float3 Q[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const int idx = wlo - 1 + q;
+        int o = idx + ((idx >= sh_from) ? sh_by : 0);
+        o = min(max(o, 0), n - 1);
+        Q[q] = (q <= nc + 1) ? ((idx == inew) ? fnew : w.pos(o)) : f3(0.f, 0.f, 0.f);
+      }
+      // the changed vertex and segment factors against the cached ones; the
+      // three per-slot differences are summed as the warp kernel's two
+      // shuffle rounds sum them, (d0 + d1) + d2
+      float d[3], e[3], f[3];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        float nv = 0.f, ns = 0.f, ntb = 0.f, nl = 0.f;
+        if (v < nc) {
+          float gt_, seg_, tb_, len_;
+          vertex_and_segment<false>(M, S, S.zoff, Q[v], Q[v + 1], Q[v + 2], wlo + v, n_new, nv, gt_, seg_, tb_,
+                                    len_);
+          if (v < nc - 1) {
+            ns = seg_;
+            ntb = tb_;
+            nl = len_;
+          }
+        }
+        float ov = 0.f, os = 0.f, otb = 0.f, ol = 0.f;
+        if (v < onc) {
+          const int o = olo + v;
+          ov = w.ld(AVT, o);
+          if (v < onc - 1) {
+            os = w.ld(ASEG, o);
+            ol = w.ld(ALEN, o);
+            otb = M.b * ol;
+          }
+        }
+        nvt[v] = nv;
+        if (v < 2) {
+          nseg[v] = ns;
+          nlen[v] = nl;
+        }
+        d[v] = (nv + ns) - (ov + os);
+        e[v] = ntb - otb;
+        f[v] = nl - ol;
+      }
+      const float dlp = (d[0] + d[1]) + d[2];
+      dlen = (f[0] + f[1]) + f[2];
+      if (move == MV_DEATH) {
+        // T_b of the reduced path from the current one, summed afresh
+        const float dtb = (e[0] + e[1]) + e[2];
+        float part = 0.f;
+        for (int q = 0; q < n - 1; ++q) part += M.b * w.ld(ALEN, q);
+        const float Tb_red = part + dtb;
+        const float tb_new = M.b * nlen[0];
+        extra = -R.log_pd + __logf(static_cast<float>(n - 2)) + R.log_pb + __logf(__fdividef(tb_new, Tb_red)) +
+                log_insert_density<true>(M, R, S.zoff, w.pos(jj - 1), w.pos(jj + 1), w.pos(jj));
+      }
+      accept = logu < dlp + extra;
+    }
+    if (accept) {
+      A.acc_i += (move == MV_INTERIOR);
+      A.acc_e += (move == MV_END);
+      A.acc_b += (move == MV_BIRTH);
+      A.acc_d += (move == MV_DEATH);
+      lane_close(A, t, R.burn_in, n, L);
+      if (move == MV_BIRTH) {
+        // entries k+1 .. n-1 move up by one (segments k+1 .. n-2)
+        for (int i = n - 1; i >= kk + 1; --i) {
+          w.set_pos(i + 1, w.pos(i));
+          w.st(AVT, i + 1, w.ld(AVT, i));
+          if (i < n - 1) {
+            w.st(ASEG, i + 1, w.ld(ASEG, i));
+            w.st(ALEN, i + 1, w.ld(ALEN, i));
+          }
+        }
+      } else if (move == MV_DEATH) {
+        // entries j+1 .. n-1 move down by one (segments j+1 .. n-2)
+        for (int i = jj + 1; i < n; ++i) {
+          w.set_pos(i - 1, w.pos(i));
+          w.st(AVT, i - 1, w.ld(AVT, i));
+          if (i < n - 1) {
+            w.st(ASEG, i - 1, w.ld(ASEG, i));
+            w.st(ALEN, i - 1, w.ld(ALEN, i));
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        if (v < nc) {
+          w.st(AVT, wlo + v, nvt[v]);
+          if (v < nc - 1 && v < 2) {
+            w.st(ASEG, wlo + v, nseg[v]);
+            w.st(ALEN, wlo + v, nlen[v]);
+          }
+        }
+      }
+      if (move != MV_DEATH) w.set_pos(inew, fnew);
+      n = n_new;
+      L += dlen;
+      if (A.nflush >= kFlush) lane_flush(A, acc);
+    }
+    done = s + 1;
+    if (((s + 1) & (kRefresh - 1)) == 0) {
+      float Ls = 0.f;
+      for (int q = 0; q < n - 1; ++q) Ls += w.ld(ALEN, q);
+      L = Ls;
+    }
+  }
+  lane_close(A, step0 + done, R.burn_in, n, L);
+  lane_flush(A, acc);
+  // recorded states, proposal and acceptance counts
+  const unsigned long long t_end = step0 + done;
+  const unsigned long long first = step0 > R.burn_in ? step0 : R.burn_in;
+  acc[ACC_NREC] += t_end > first ? static_cast<double>(t_end - first) : 0.0;
+  acc[ACC_PROP + 0] += static_cast<double>(A.prop_w - A.prop_end);
+  acc[ACC_PROP + 1] += static_cast<double>(A.prop_end);
+  acc[ACC_PROP + 2] += static_cast<double>(A.prop_b);
+  acc[ACC_PROP + 3] += static_cast<double>(A.prop_d);
+  acc[ACC_ACC + 0] += static_cast<double>(A.acc_i);
+  acc[ACC_ACC + 1] += static_cast<double>(A.acc_e);
+  acc[ACC_ACC + 2] += static_cast<double>(A.acc_b);
+  acc[ACC_ACC + 3] += static_cast<double>(A.acc_d);
+  for (int i = 0; i < min(n, W); ++i) {
+    w.gm[AX * cap + i] = w.sm[(AX * W + i) * 32];
+    w.gm[AY * cap + i] = w.sm[(AY * W + i) * 32];
+    w.gm[AZ * cap + i] = w.sm[(AZ * W + i) * 32];
+  }
+  P.n[c] = n;
+  P.step[c] = t_end;
+  if (aborted) {
+    P.status[c] |= ST_ABORTED;
+    atomicOr(P.any_status, ST_ABORTED);
+  }
+}
+
+// Persistent warps; each work item is 32 consecutive chains of the
+// processing order, one per lane.
+__global__ void __launch_bounds__(128, 4) lane_chain_kernel(const ChainParams P) {
+  extern __shared__ float lane_smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int W = P.smem_cap;
+  float* col = lane_smem + static_cast<size_t>(wib) * kArrays * W * 32 + lane;
+  const uint32_t key0 = static_cast<uint32_t>(P.R.seed), key1 = static_cast<uint32_t>(P.R.seed >> 32);
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = static_cast<int>(atomicAdd(P.queue, 1u));
+    item = __shfl_sync(kAll, item, 0);
+    const long long g = static_cast<long long>(P.chain_lo) + 32ll * item;
+    if (g >= P.chain_hi) break;
+    if (g + lane < P.chain_hi) run_chain(P, P.order[g + lane], col, W, key0, key1);
+  }
+}
+
+cudaError_t lane_attributes() {
+  static int done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(lane_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(lane_chain_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
+  return e;
+}
+
+}  // namespace
+
+size_t lane_smem_bytes(int window, int warps_per_block) {
+  return static_cast<size_t>(warps_per_block) * kArrays * static_cast<size_t>(window) * 32u * sizeof(float);
+}
+
+cudaError_t lane_occupancy(int warps_per_block, int window, int* blocks_per_sm) {
+  cudaError_t e = lane_attributes();
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, lane_chain_kernel, warps_per_block * 32,
+                                                       lane_smem_bytes(window, warps_per_block));
+}
+
+cudaError_t launch_lane_chain(const ChainParams& p, int grid, int warps_per_block, cudaStream_t s) {
+  cudaError_t e = lane_attributes();
+  if (e != cudaSuccess) return e;
+  lane_chain_kernel<<<grid, warps_per_block * 32, lane_smem_bytes(p.smem_cap, warps_per_block), s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace pmc

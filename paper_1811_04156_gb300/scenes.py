@@ -53,6 +53,10 @@ WITHIN_MALA = 1
 WITHIN_TREE = 2
 WITHIN_HMC = 3
 
+LAYOUT_AUTO = 0
+LAYOUT_WARP = 1
+LAYOUT_LANE = 2
+
 BASE_SEED = 0x181104156
 
 
@@ -115,6 +119,7 @@ class Run:
     thin_bridge: int = 0           # 0 = no reference-density bridge terms
     gradients: bool = False
     hmc_steps: int = 10            # leapfrog steps of a full-path gradient (HMC) move, step mala_step
+    layout: int = LAYOUT_AUTO      # LAYOUT_WARP: one warp per chain; LAYOUT_LANE: one lane per chain (lean runs)
 
 
 @dataclasses.dataclass

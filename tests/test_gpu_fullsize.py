@@ -1,6 +1,7 @@
 """Parity at the detector workload's full size (65,536 chains, vertex cap 256,
 straight jittered starts) in the launch configuration bench.py times (the
-autotuned persistent launch of the lean chain kernel):
+autotuned persistent launch of a lean chain kernel: one warp or one lane per
+chain, whichever the autotuner timed faster):
 
 * the first 2,000 steps of 96 chains sampled across the whole launch replay
   the FP64 oracle's trajectories (same Philox streams, chain by chain);
@@ -44,7 +45,7 @@ def test_full_launch_replays_sampled_chains(api, ctx, oracle_lib):
     steps = 2000
     sc, medium, geom, ch = _detector(api, ctx, steps)
     li = ch.launch_info()
-    assert len(li) == 1 and li[0]["general"] == 0 and li[0]["hi"] == 65_536
+    assert len(li) == 1 and li[0]["general"] in (0, 4) and li[0]["hi"] == 65_536
     ch.run_steps(steps)
     xyz, n, st = ch.read_states()
     acc = ch.read_accumulators()
