@@ -51,9 +51,12 @@ WORKLOAD_TEXT = {
     "layered": "layered: 100 x 10 m layers, 60 sensors x 8,192 chains, cap 1,024, g=0.94",
 }
 FP32_LANES_PER_SM = 128
-# Warp instructions per proposal of the chain kernel, from the committed ncu
-# capture of the same kernel and launch shape (profiles/chain_kernel_detector.md).
-WARP_INST_PER_PROPOSAL = {"detector": 405.7}
+# Warp instructions per proposal of the chain kernels, from the committed ncu
+# captures of the same kernel, workload and shared window, keyed by (workload,
+# kernel kind, window): kind 0 one warp per chain with the whole cap
+# (profiles/chain_kernel_detector.md), kind 4 one lane per chain
+# (profiles/lane_chain_kernel_detector.md).
+WARP_INST_PER_PROPOSAL = {("detector", 0, 256): 405.7, ("detector", 4, 16): 82.07, ("detector", 4, 20): 81.94}
 ISSUE_PER_CLK_PER_SM = 4
 
 
@@ -72,6 +75,8 @@ def parse():
     p.add_argument("--warps-per-block", type=int, default=0)
     p.add_argument("--layout", choices=["auto", "warp", "lane"], default="auto",
                    help="chain layout of the kernel: the autotuner's choice, one warp or one lane per chain")
+    p.add_argument("--smem-window", type=int, default=0,
+                   help="vertices per chain in shared memory (0: whole cap, or the autotuner's choice)")
     p.add_argument("--time-to-target", type=float, default=0.0,
                    help="instead of the throughput line: wall time to this relative intensity error for plain "
                         "RJMCMC, batched MALA chains and the GPU forward tracer on the plain / detector geometry")
@@ -310,7 +315,8 @@ def ours(args):
     medium = api.Medium(ctx, sc.medium)
     geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
     sc.run.layout = {"auto": 0, "warp": 1, "lane": 2}[args.layout]  # scenes.LAYOUT_*
-    chains = api.Chains(ctx, medium, geom, sc.run, warps_per_block=args.warps_per_block)
+    chains = api.Chains(ctx, medium, geom, sc.run, warps_per_block=args.warps_per_block,
+                        smem_window=args.smem_window)
     stream = torch.cuda.current_stream()
     n_chains = sc.total_chains
     props_per_step = n_chains * sc.run.n_steps
@@ -399,25 +405,24 @@ def ours(args):
     kern_s = statistics.mean(kern_ms) / 1e3
     rate = props_per_step / kern_s
     # lane-op roofline: the slower of the FP32 and the MUFU pipes
-    fp32_peak = FP32_LANES_PER_SM * n_sm * sm_mhz * 1e6
-    mufu_peak = MUFU_LANES_PER_SM * n_sm * sm_mhz * 1e6
+    # each pipe's peak: the unit count, or the measured rate where that is
+    # higher (GB300 doubles the ex2 rate): no pipe can run above its peak
+    fp32_units = FP32_LANES_PER_SM * n_sm * sm_mhz * 1e6
+    mufu_units = MUFU_LANES_PER_SM * n_sm * sm_mhz * 1e6
+    fp32_peak = max(fp32_units, pipes["fp32_per_s"])
+    mufu_peak = max(mufu_units, pipes["mufu_per_s"])
     if mufu / mufu_peak >= fp32 / fp32_peak:
         bound_pipe, achieved, peak = "MUFU", rate * mufu / 1e12, mufu_peak / 1e12
+        peak_from = "unit count" if mufu_peak == mufu_units else "measured (above the unit count)"
     else:
         bound_pipe, achieved, peak = "FP32", rate * fp32 / 1e12, fp32_peak / 1e12
+        peak_from = "unit count" if fp32_peak == fp32_units else "measured (above the unit count)"
     peak_measured = (pipes["mufu_per_s"] if bound_pipe == "MUFU" else pipes["fp32_per_s"]) / 1e12
-    # a measured rate above the unit-count figure (GB300 doubles the ex2 rate)
-    # replaces it: no pipe can run above its peak
-    peak_from = "unit count"
-    if peak_measured > peak:
-        peak, peak_from = peak_measured, "measured (above the unit count)"
     clk = (clocks or {}).get("sm_mhz") or sm_mhz
     li = chains.launch_info()
-    # warp instructions per proposal depend on the kernel and the workload, not
-    # on how many chains share a CTA: any shape of the lean kernel with the whole
-    # cap in shared memory runs the captured instruction stream
-    same_shape = len(li) == 1 and li[0]["general"] == 0 and li[0]["smem_cap"] == sc.pairs[0].cap
-    inst = WARP_INST_PER_PROPOSAL.get(sc.name) if same_shape else None
+    # warp instructions per proposal depend on the kernel, the workload and the
+    # shared window, not on how many warps share a CTA
+    inst = WARP_INST_PER_PROPOSAL.get((sc.name, li[0]["general"], li[0]["smem_cap"])) if len(li) == 1 else None
     issue = None
     if inst is not None:
         issue_peak = ISSUE_PER_CLK_PER_SM * n_sm * clk * 1e6
@@ -425,8 +430,15 @@ def ours(args):
                  "frac": rate * inst / issue_peak, "inst_per_proposal": inst,
                  "source": "instructions per proposal from the committed ncu capture of this kernel and workload; "
                            "peak = 4 warp instructions/clk/SM x SMs x median SM clock under load"}
-    # DRAM traffic of one launch: ncu capture of 16,384 chains (8.9 MB), scaled by chains
-    traffic = 8.9e6 * n_chains / 16384.0 if sc.name == "detector" else None
+    # DRAM traffic of one launch (dram__bytes_read + write) from the committed
+    # ncu captures, scaled by chains: warp layout 8.9 MB for 16,384 chains, lane
+    # layout 37.3 MB for 65,536 chains (window 20; 35.8 MB read, 1.5 MB written)
+    kind = li[0]["general"] if len(li) == 1 else None
+    traffic = None
+    if sc.name == "detector" and kind == 0:
+        traffic = 8.9e6 * n_chains / 16384.0
+    elif sc.name == "detector" and kind == 4 and li[0]["smem_cap"] == 20:
+        traffic = 37.3e6 * n_chains / 65536.0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -441,7 +453,8 @@ def ours(args):
                          "peak_source": f"{bound_pipe}: max of the microbenchmark rate and lanes/clk/SM x "
                                         f"{n_sm} SMs x sm_max_mhz ({peak_kind} clock {sm_mhz:.0f} MHz); "
                                         f"taken: {peak_from}",
-                         "kernel": "chain_kernel", "kernel_ms": statistics.mean(kern_ms),
+                         "kernel": "lane_chain_kernel" if kind == 4 else "chain_kernel",
+                         "kernel_ms": statistics.mean(kern_ms),
                          "fp32_per_proposal": fp32, "mufu_per_proposal": mufu,
                          "peak_measured": peak_measured, "frac_of_measured": achieved / peak_measured,
                          "pipes_measured": pipes},

@@ -148,6 +148,7 @@ struct pmc_geom_s {
 
 struct ChainClass {
   int kind = 0;       // kernel kind of launch_chain (4: one lane per chain)
+  bool short_paths = false;  // every pair expects <= kLaneMaxN vertices (lane layout candidate)
   int smem_cap = 0;   // shared window (vertices per chain)
   int max_cap = 0;    // largest vertex cap of the class's chains
   bool spill = false; // smem_cap < max_cap: entries beyond the window live in global memory
@@ -486,6 +487,15 @@ int pmc_destroy_chains(pmc_chains_t ch) {
   return PMC_OK;
 }
 
+// The lane layout pays for a path's length at every birth and death (its
+// scans run sequentially over the lane's own path and the warp waits for its
+// longest one), the warp layout spreads it over 32 lanes: the autotuner
+// offers the lane layout only to classes whose pairs expect short paths,
+// 2 + D b <= kLaneMaxN vertices on the straight source-sensor line (D the
+// distance, b the scattering coefficient).  A short probe from the initial
+// states cannot see this, since those paths have not grown yet.
+constexpr double kLaneMaxN = 24.0;
+
 // Work items of a launch: one per chain, or one per 32 chains (lane layout).
 static int work_items(int kind, int chains) { return kind == 4 ? (chains + 31) / 32 : chains; }
 
@@ -516,8 +526,8 @@ static ChainParams class_params(pmc_chains_t ch, size_t k, unsigned long long n_
 // Autotuner: for every cap class, time the chain kernel over candidate launch
 // shapes — 1, 2 or 4 warps per block; with one warp per chain a shared
 // window of the whole cap or of 128 / 256 / 512 vertices (entries beyond it
-// in global memory); with one lane per chain (lean runs) a per-lane window
-// of 8, 16 or 32 vertices — on a scratch copy of the freshly initialised
+// in global memory); with one lane per chain (lean runs with short paths) a
+// per-lane window of 8 to 32 vertices — on a scratch copy of the freshly initialised
 // state (256 steps, best of two probes), and keep the fastest; choices are
 // cached per device, kernel, layout request and class.
 static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
@@ -564,8 +574,9 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
         for (int w : {128, 256, 512})
           if (w < full && ch->general < 2) cands.emplace_back(ch->general, w);
       }
-      if (ch->layout != PMC_LAYOUT_WARP && ch->general == 0 && !ch->grad)
-        for (int w : {8, 16, 32}) {
+      if (ch->layout == PMC_LAYOUT_LANE ||
+          (ch->layout == PMC_LAYOUT_AUTO && ch->general == 0 && !ch->grad && cl.short_paths))
+        for (int w : {8, 12, 16, 20, 24, 32}) {
           cands.emplace_back(4, std::min(w, cl.max_cap));
           if (w >= cl.max_cap) break;
         }
@@ -738,12 +749,19 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     const int k = class_of(ch->h_pairs[ch->h_pair_of[order[lo]]].cap);
     int hi = lo;
     int maxcap = 0;
+    double max_n = 0.0;
     while (hi < T && class_of(ch->h_pairs[ch->h_pair_of[order[hi]]].cap) == k) {
-      maxcap = std::max(maxcap, ch->h_pairs[ch->h_pair_of[order[hi]]].cap);
+      const DPair& d = ch->h_pairs[ch->h_pair_of[order[hi]]];
+      maxcap = std::max(maxcap, d.cap);
+      const double dx = (static_cast<double>(d.c[0]) + d.c_lo[0]) - d.src[0];
+      const double dy = (static_cast<double>(d.c[1]) + d.c_lo[1]) - d.src[1];
+      const double dz = (static_cast<double>(d.c[2]) + d.c_lo[2]) - d.src[2];
+      max_n = std::max(max_n, 2.0 + std::sqrt(dx * dx + dy * dy + dz * dz) * med->d.b);
       ++hi;
     }
     ChainClass cl;
     cl.kind = ch->general;
+    cl.short_paths = med->d.kind == PMC_HOMOGENEOUS && max_n <= kLaneMaxN;
     cl.smem_cap = (maxcap + 31) / 32 * 32;
     cl.max_cap = maxcap;
     cl.spill = false;
