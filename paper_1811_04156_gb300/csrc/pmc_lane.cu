@@ -166,13 +166,28 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
     const float logu = __logf(u01(ra.z));
     const float ub0 = u01(rb.x), ub1 = u01(rb.y), ub2 = u01(rb.z), ub3 = u01(rb.w);
 
+    // work that several move kinds share runs once, with every lane: the
+    // azimuth of within-dimension moves, a second sincos (the interior
+    // move's third normal, the birth's phi), and T_b = sum of tau_b over the
+    // current path (births and deaths)
+    const bool within = um < R.thr_within, birth = !within && um < R.thr_birth, death = !within && !birth;
+    float s1, c1, sB, cB;
+    sincospif(2.0f * ub1, &s1, &c1);
+    sincospif(2.0f * (within ? ub3 : ub2), &sB, &cB);
+    float Tb = 0.f;
+    {
+      const int m = ((birth && n < cap) || (death && n > 2)) ? n - 1 : 0;
+      for (int q = 0; q < m; ++q) Tb += M.b * w.ld(ALEN, q);
+    }
+
     int move;
     bool proposed = true;
     int n_new = n, wlo = 0, nc = 0, olo = 0, onc = 0, jj = -1, kk = -1;
     int inew = -1, sh_from = INT_MAX, sh_by = 0;
     float3 fnew = f3(0.f, 0.f, 0.f);
     float extra = 0.f;
-    if (um < R.thr_within) {
+    float3 IA, IB, IF;  // births and deaths: the insertion density's segment ends and vertex
+    if (within) {
       A.prop_w++;
       const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 1)) >> 23);
       jj = j;
@@ -184,8 +199,6 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
         const float3 nu = sensor_normal(S, w.pos(j));
         float3 e1, e2;
         onb(nu, e1, e2);
-        float s1, c1;
-        sincospif(2.0f * ub1, &s1, &c1);
         const float wv = 1.0f + __fdividef(__logf(fmaf(1.0f - ub0, S.exp_m2ke, ub0)), S.kappa_end);
         const float sw = m_sqrt<true>(fmaxf(0.f, 1.0f - wv * wv));
         const float3 nn = wv * nu + sw * (c1 * e1 + s1 * e2);
@@ -194,16 +207,13 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
       } else {
         // Gaussian step of an interior vertex (Box-Muller)
         move = MV_INTERIOR;
-        float s1, c1, s2, c2;
         const float r1 = m_sqrt<true>(-2.0f * __logf(ub0));
-        sincospif(2.0f * ub1, &s1, &c1);
         const float r2 = m_sqrt<true>(-2.0f * __logf(ub2));
-        sincospif(2.0f * ub3, &s2, &c2);
-        const float3 z = f3(r1 * c1, r1 * s1, r2 * c2);
+        const float3 z = f3(r1 * c1, r1 * s1, r2 * cB);
         fnew = w.pos(j) + R.sigma * z;
         wlo = j - 1; nc = 3; olo = j - 1; onc = 3;
       }
-    } else if (um < R.thr_birth) {
+    } else if (birth) {
       move = MV_BIRTH;
       A.prop_b++;
       if (n >= cap) {
@@ -212,8 +222,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
         // segment k with probability tau_b(k) / T_b (smallest k whose
         // cumulative sum exceeds u T_b), then the bispherical insertion
         const float ui = __fmaf_rn(static_cast<float>(v23), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
-        float total = 0.f;
-        for (int q = 0; q < n - 1; ++q) total += M.b * w.ld(ALEN, q);
+        const float total = Tb;
         const float target = ui * total;
         int k = n - 2;
         float cum = 0.f;
@@ -240,13 +249,13 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
         const float et = __fdividef(ub1, 1.0f - ub1);
         const float iet = __fdividef(1.0f - ub1, ub1);
         const float sht = 0.5f * (et - iet), cht = 0.5f * (et + iet);
-        float s3, c3;
-        sincospif(2.0f * ub2, &s3, &c3);
         const float sc = __fdividef(gamma, cht - cs);
-        fnew = 0.5f * (Af + Bf) + sc * (sht * rh + sn * (c3 * xi + s3 * ze));
+        fnew = 0.5f * (Af + Bf) + sc * (sht * rh + sn * (cB * xi + sB * ze));
         const float tbk = M.b * w.ld(ALEN, k);
-        extra = R.log_pd - __logf(static_cast<float>(n - 1)) - R.log_pb - __logf(__fdividef(tbk, total)) -
-                log_insert_density<true>(M, R, S.zoff, Af, Bf, fnew);
+        extra = R.log_pd - __logf(static_cast<float>(n - 1)) - R.log_pb - __logf(__fdividef(tbk, total));
+        IA = Af;
+        IB = Bf;
+        IF = fnew;
         n_new = n + 1;
         inew = k + 1;
         sh_from = k + 2;
@@ -265,6 +274,9 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
         sh_from = j;
         sh_by = 1;
         wlo = j - 1; nc = 2; olo = j - 1; onc = 3;
+        IA = w.pos(j - 1);
+        IB = w.pos(j + 1);
+        IF = w.pos(j);
       }
     }
 
@@ -320,14 +332,16 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
       const float dlp = (d[0] + d[1]) + d[2];
       dlen = (f[0] + f[1]) + f[2];
       if (move == MV_DEATH) {
-        // T_b of the reduced path from the current one, summed afresh
+        // T_b of the reduced path from the current one (summed afresh above)
         const float dtb = (e[0] + e[1]) + e[2];
-        float part = 0.f;
-        for (int q = 0; q < n - 1; ++q) part += M.b * w.ld(ALEN, q);
-        const float Tb_red = part + dtb;
+        const float Tb_red = Tb + dtb;
         const float tb_new = M.b * nlen[0];
-        extra = -R.log_pd + __logf(static_cast<float>(n - 2)) + R.log_pb + __logf(__fdividef(tb_new, Tb_red)) +
-                log_insert_density<true>(M, R, S.zoff, w.pos(jj - 1), w.pos(jj + 1), w.pos(jj));
+        extra = -R.log_pd + __logf(static_cast<float>(n - 2)) + R.log_pb + __logf(__fdividef(tb_new, Tb_red));
+      }
+      if (move >= MV_BIRTH) {
+        // one insertion density for both kinds: a birth divides by it, a death multiplies
+        const float lid = log_insert_density<true>(M, R, S.zoff, IA, IB, IF);
+        extra = (move == MV_BIRTH) ? extra - lid : extra + lid;
       }
       accept = logu < dlp + extra;
     }
