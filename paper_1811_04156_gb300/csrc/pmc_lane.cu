@@ -45,6 +45,8 @@ struct LanePath {
     if (i < W) sm[(a * W + i) * 32] = v;
     else gm[a * cap + i] = v;
   }
+  // entry i of every array in shared memory (i < W): array a at [a * W * 32]
+  __device__ __forceinline__ float* row(int i) const { return sm + i * 32; }
   __device__ __forceinline__ float3 pos(int i) const { return f3(ld(AX, i), ld(AY, i), ld(AZ, i)); }
   __device__ __forceinline__ void set_pos(int i, float3 p) const {
     st(AX, i, p.x);
@@ -176,8 +178,13 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
     sincospif(2.0f * (within ? ub3 : ub2), &sB, &cB);
     float Tb = 0.f;
     {
+      // segments below the window edge from shared memory, the rest from the
+      // global block, in index order
       const int m = ((birth && n < cap) || (death && n > 2)) ? n - 1 : 0;
-      for (int q = 0; q < m; ++q) Tb += M.b * w.ld(ALEN, q);
+      const int m1 = min(m, W);
+      const float* pl = w.sm + ALEN * W * 32;
+      for (int q = 0; q < m1; ++q) Tb += M.b * pl[q * 32];
+      for (int q = W; q < m; ++q) Tb += M.b * w.gm[ALEN * cap + q];
     }
 
     int move;
@@ -224,15 +231,21 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
         const float ui = __fmaf_rn(static_cast<float>(v23), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
         const float total = Tb;
         const float target = ui * total;
-        int k = n - 2;
+        int k = -1;
         float cum = 0.f;
-        for (int q = 0; q < n - 1; ++q) {
-          cum += M.b * w.ld(ALEN, q);
+        const float* pl = w.sm + ALEN * W * 32;
+        for (int q = 0; q < min(n - 1, W); ++q) {
+          cum += M.b * pl[q * 32];
           if (cum > target) {
             k = q;
             break;
           }
         }
+        for (int q = W; k < 0 && q < n - 1; ++q) {
+          cum += M.b * w.gm[ALEN * cap + q];
+          if (cum > target) k = q;
+        }
+        if (k < 0) k = n - 2;
         kk = k;
         const float3 Af = w.pos(k), Bf = w.pos(k + 1);
         const float3 r = Bf - Af;
@@ -351,26 +364,72 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
       A.acc_b += (move == MV_BIRTH);
       A.acc_d += (move == MV_DEATH);
       lane_close(A, t, R.burn_in, n, L);
-      if (move == MV_BIRTH) {
-        // entries k+1 .. n-1 move up by one (segments k+1 .. n-2)
-        for (int i = n - 1; i >= kk + 1; --i) {
-          w.set_pos(i + 1, w.pos(i));
-          w.st(AVT, i + 1, w.ld(AVT, i));
+      if (move >= MV_BIRTH) {
+        // a birth moves entries k+1 .. n-1 up by one (highest first), a death
+        // entries j+1 .. n-1 down by one (lowest first); segment arrays only
+        // below n-1.  Entries whose source and destination both lie in the
+        // shared window move in one loop for both kinds; the few beyond it
+        // go through the global block, before (births) or after (deaths).
+        const bool up = move == MV_BIRTH;
+        const int a0 = up ? kk + 1 : jj + 1;
+        auto move_any = [&](int i, int j) {
+          w.set_pos(j, w.pos(i));
+          w.st(AVT, j, w.ld(AVT, i));
           if (i < n - 1) {
-            w.st(ASEG, i + 1, w.ld(ASEG, i));
-            w.st(ALEN, i + 1, w.ld(ALEN, i));
+            w.st(ASEG, j, w.ld(ASEG, i));
+            w.st(ALEN, j, w.ld(ALEN, i));
+          }
+        };
+        if (up)
+          for (int i = n - 1; i >= max(a0, W - 1); --i) move_any(i, i + 1);
+        {
+          const int d = up ? 1 : -1;
+          const int hi = min(n - 1, up ? W - 2 : W - 1);
+          const int cnt = hi - a0 + 1;
+          const int WS = W * 32;
+          float* src = w.row(up ? hi : a0);
+          int t = 0;
+          // two entries per pass, both read before either is written (the
+          // second entry's destination is the first one's source)
+          for (; t + 1 < cnt; t += 2, src -= 2 * d * 32) {
+            float* src2 = src - d * 32;
+            const float x0 = src[AX * WS], y0 = src[AY * WS], z0 = src[AZ * WS], v0 = src[AVT * WS];
+            const float x1 = src2[AX * WS], y1 = src2[AY * WS], z1 = src2[AZ * WS], v1 = src2[AVT * WS];
+            const bool s0 = (up ? hi - t : a0 + t) < n - 1, s1 = (up ? hi - t - 1 : a0 + t + 1) < n - 1;
+            const float g0 = s0 ? src[ASEG * WS] : 0.f, l0 = s0 ? src[ALEN * WS] : 0.f;
+            const float g1 = s1 ? src2[ASEG * WS] : 0.f, l1 = s1 ? src2[ALEN * WS] : 0.f;
+            float* dst = src + d * 32;
+            dst[AX * WS] = x0;
+            dst[AY * WS] = y0;
+            dst[AZ * WS] = z0;
+            dst[AVT * WS] = v0;
+            if (s0) {
+              dst[ASEG * WS] = g0;
+              dst[ALEN * WS] = l0;
+            }
+            src[AX * WS] = x1;
+            src[AY * WS] = y1;
+            src[AZ * WS] = z1;
+            src[AVT * WS] = v1;
+            if (s1) {
+              src[ASEG * WS] = g1;
+              src[ALEN * WS] = l1;
+            }
+          }
+          if (t < cnt) {
+            float* dst = src + d * 32;
+            dst[AX * WS] = src[AX * WS];
+            dst[AY * WS] = src[AY * WS];
+            dst[AZ * WS] = src[AZ * WS];
+            dst[AVT * WS] = src[AVT * WS];
+            if ((up ? hi - t : a0 + t) < n - 1) {
+              dst[ASEG * WS] = src[ASEG * WS];
+              dst[ALEN * WS] = src[ALEN * WS];
+            }
           }
         }
-      } else if (move == MV_DEATH) {
-        // entries j+1 .. n-1 move down by one (segments j+1 .. n-2)
-        for (int i = jj + 1; i < n; ++i) {
-          w.set_pos(i - 1, w.pos(i));
-          w.st(AVT, i - 1, w.ld(AVT, i));
-          if (i < n - 1) {
-            w.st(ASEG, i - 1, w.ld(ASEG, i));
-            w.st(ALEN, i - 1, w.ld(ALEN, i));
-          }
-        }
+        if (!up)
+          for (int i = max(a0, W); i <= n - 1; ++i) move_any(i, i - 1);
       }
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
