@@ -81,6 +81,12 @@ def parse():
                    help="instead of the throughput line: wall time to this relative intensity error for plain "
                         "RJMCMC, batched MALA chains and the GPU forward tracer on the plain / detector geometry")
     p.add_argument("--geometry", default="plain", help="geometry of --time-to-target: plain or detector")
+    p.add_argument("--ttt-methods", default="",
+                   help="comma list of --time-to-target methods to run (default all): plain_rjmcmc, batched_mala, "
+                        "batched_mala_tracer_seeded, batched_perturb_tracer_seeded, batched_tree_moves, "
+                        "tree_moves_optimal_bridge, gpu_tracer")
+    p.add_argument("--ttt-ref", default="",
+                   help="I,se,photons of a reference tracer run to use instead of running it again")
     p.add_argument("--two-sensor", action="store_true",
                    help="instead of the throughput line: the paper's two-sensor scene (relative light yield B "
                         "through the map T and path-length distributions for each b1, beside the GPU tracer)")
@@ -498,15 +504,18 @@ def time_to_target(args):
     g1 = api.Geometry(ctx, sc_plain.sources, sc_plain.sensors, [S.Pair(0, 0, 1, cap)])
     ref_photons = 4_000_000_000 if geom_name == "plain" else 100_000_000_000
     t0 = time.perf_counter()
-    parts = []
-    left = ref_photons
-    while left > 0:
-        k = min(left, 20_000_000_000)
-        parts.append(api.trace(ctx, med, g1, 0, 123457, k, photon0=ref_photons - left, max_scatter=cap - 2))
-        left -= k
-    N = sum(p["photons"] for p in parts)
-    I_ref = sum(p["I"] * p["photons"] for p in parts) / N
-    se_ref = math.sqrt(sum((p["se"] * p["photons"]) ** 2 for p in parts)) / N
+    if args.ttt_ref:
+        I_ref, se_ref, N = (float(x) for x in args.ttt_ref.split(","))
+    else:
+        parts = []
+        left = ref_photons
+        while left > 0:
+            k = min(left, 20_000_000_000)
+            parts.append(api.trace(ctx, med, g1, 0, 123457, k, photon0=ref_photons - left, max_scatter=cap - 2))
+            left -= k
+        N = sum(p["photons"] for p in parts)
+        I_ref = sum(p["I"] * p["photons"] for p in parts) / N
+        se_ref = math.sqrt(sum((p["se"] * p["photons"]) ** 2 for p in parts)) / N
     ref_s = time.perf_counter() - t0
     out = {"target_rel_err": tgt, "geometry": geom_name, "reference": {"intensity": I_ref, "std_err": se_ref,
                                                                      "photons": N, "seconds": ref_s}}
@@ -540,13 +549,24 @@ def time_to_target(args):
             increment = min(increment * 2, 1_000_000)
         dt = time.perf_counter() - t
         return {"seconds": dt, "steps_per_chain": steps, "chains": n_chains, "intensity": e["intensity"],
-                "std_err": e["std_err"], "reached": bool(ok(e["intensity"], e["std_err"]))}
+                "std_err": e["std_err"], "reached": bool(ok(e["intensity"], e["std_err"])),
+                "launch": ch.launch_info()}
 
-    out["plain_rjmcmc"] = run_chains(64, S.WITHIN_PERTURB, 20_000)
-    out["batched_mala"] = run_chains(65_536, S.WITHIN_MALA, 2_000)
-    out["batched_mala_tracer_seeded"] = run_chains(65_536, S.WITHIN_MALA, 500, seeded=True)
-    out["batched_perturb_tracer_seeded"] = run_chains(65_536, S.WITHIN_PERTURB, 500, seeded=True)
-    out["batched_tree_moves"] = run_chains(65_536, S.WITHIN_TREE, 2_000)
+    wanted = set(args.ttt_methods.split(",")) if args.ttt_methods else None
+
+    def want(name):
+        return wanted is None or name in wanted
+
+    if want("plain_rjmcmc"):
+        out["plain_rjmcmc"] = run_chains(64, S.WITHIN_PERTURB, 20_000)
+    if want("batched_mala"):
+        out["batched_mala"] = run_chains(65_536, S.WITHIN_MALA, 2_000)
+    if want("batched_mala_tracer_seeded"):
+        out["batched_mala_tracer_seeded"] = run_chains(65_536, S.WITHIN_MALA, 500, seeded=True)
+    if want("batched_perturb_tracer_seeded"):
+        out["batched_perturb_tracer_seeded"] = run_chains(65_536, S.WITHIN_PERTURB, 500, seeded=True)
+    if want("batched_tree_moves"):
+        out["batched_tree_moves"] = run_chains(65_536, S.WITHIN_TREE, 2_000)
 
     def run_tree_bridge(n_chains, burn, thin, n_draws, rows0):
         """Tree-move chains and the optimal bridge against the normalised
@@ -577,8 +597,12 @@ def time_to_target(args):
                 "draws_per_row": n_draws, "intensity": ob["r"], "std_err": ob["se"],
                 "geometric": ob["geometric"], "reached": bool(ok(ob["r"], ob["se"]))}
 
-    out["tree_moves_optimal_bridge"] = run_tree_bridge(65_536, 10_000 if geom_name == "plain" else 40_000, 500,
-                                                       65_536, 8)
+    if want("tree_moves_optimal_bridge"):
+        out["tree_moves_optimal_bridge"] = run_tree_bridge(65_536, 10_000 if geom_name == "plain" else 40_000,
+                                                           500, 65_536, 8)
+    if not want("gpu_tracer"):
+        print(json.dumps(out), flush=True)
+        return 0
     # tracer with doubling photon budgets
     t = time.perf_counter()
     photons, acc = 1_000_000, []
