@@ -183,6 +183,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
       const int m = ((birth && n < cap) || (death && n > 2)) ? n - 1 : 0;
       const int m1 = min(m, W);
       const float* pl = w.sm + ALEN * W * 32;
+#pragma unroll 4
       for (int q = 0; q < m1; ++q) Tb += M.b * pl[q * 32];
       for (int q = W; q < m; ++q) Tb += M.b * w.gm[ALEN * cap + q];
     }
@@ -234,6 +235,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
         int k = -1;
         float cum = 0.f;
         const float* pl = w.sm + ALEN * W * 32;
+#pragma unroll 4
         for (int q = 0; q < min(n - 1, W); ++q) {
           cum += M.b * pl[q * 32];
           if (cum > target) {
