@@ -56,7 +56,7 @@ FP32_LANES_PER_SM = 128
 # kernel kind, window): kind 0 one warp per chain with the whole cap
 # (profiles/chain_kernel_detector.md), kind 4 one lane per chain
 # (profiles/lane_chain_kernel_detector.md).
-WARP_INST_PER_PROPOSAL = {("detector", 0, 256): 405.7, ("detector", 4, 16): 82.07, ("detector", 4, 20): 59.73}
+WARP_INST_PER_PROPOSAL = {("detector", 0, 256): 405.7, ("detector", 4, 16): 82.07, ("detector", 4, 20): 59.55}
 ISSUE_PER_CLK_PER_SM = 4
 
 
@@ -438,13 +438,13 @@ def ours(args):
                            "peak = 4 warp instructions/clk/SM x SMs x median SM clock under load"}
     # DRAM traffic of one launch (dram__bytes_read + write) from the committed
     # ncu captures, scaled by chains: warp layout 8.9 MB for 16,384 chains, lane
-    # layout 37.2 MB for 65,536 chains (window 20; 35.8 MB read, 1.4 MB written)
+    # layout 37.3 MB for 65,536 chains (window 20; 35.8 MB read, 1.4 MB written)
     kind = li[0]["general"] if len(li) == 1 else None
     traffic = None
     if sc.name == "detector" and kind == 0:
         traffic = 8.9e6 * n_chains / 16384.0
     elif sc.name == "detector" and kind == 4 and li[0]["smem_cap"] == 20:
-        traffic = 37.2e6 * n_chains / 65536.0
+        traffic = 37.3e6 * n_chains / 65536.0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
