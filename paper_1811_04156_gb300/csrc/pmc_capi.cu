@@ -566,8 +566,8 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
       float best_ms = 1e30f;
       // candidates (kind, shared window): the warp layout with the whole cap
       // or a window with global spill (tree and HMC moves keep the whole
-      // cap); the lane layout (lean runs without gradient caches) with
-      // per-lane windows of 8 to 32 vertices
+      // cap); the lane layout (lean runs with short paths) with per-lane
+      // windows of 8 to 32 vertices
       std::vector<std::pair<int, int>> cands;
       if (ch->layout != PMC_LAYOUT_LANE) {
         cands.emplace_back(ch->general, full);
@@ -575,7 +575,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
           if (w < full && ch->general < 2) cands.emplace_back(ch->general, w);
       }
       if (ch->layout == PMC_LAYOUT_LANE ||
-          (ch->layout == PMC_LAYOUT_AUTO && ch->general == 0 && !ch->grad && cl.short_paths))
+          (ch->layout == PMC_LAYOUT_AUTO && ch->general == 0 && cl.short_paths))
         for (int w : {8, 12, 16, 20, 24, 32}) {
           cands.emplace_back(4, std::min(w, cl.max_cap));
           if (w >= cl.max_cap) break;
@@ -718,9 +718,9 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   if (r->within == PMC_WITHIN_TREE) ch->general = 2;
   if (r->within == PMC_WITHIN_HMC) ch->general = 3;
   ch->layout = r->layout;
-  if (r->layout == PMC_LAYOUT_LANE && (ch->general != 0 || ch->grad))
+  if (r->layout == PMC_LAYOUT_LANE && ch->general != 0)
     return fail(PMC_ERR_INVALID, "the lane layout runs lean chains only (homogeneous medium, isotropic emission, "
-                                 "rho = 1, Henyey-Greenstein, Gaussian perturbations, no gradients)");
+                                 "rho = 1, Henyey-Greenstein, Gaussian perturbations)");
   const int n_arrays = chain_arrays(ch->general > 0, ch->grad);
   const int T = ch->total;
   ch->h_base.resize(T);

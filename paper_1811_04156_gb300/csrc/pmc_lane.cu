@@ -1,7 +1,8 @@
 // Lane-per-chain RJMCMC kernel for the lean case (homogeneous medium,
 // isotropic emission, detection probability 1, Henyey-Greenstein phase
-// function, Gaussian vertex perturbations and vMF end moves, no gradient
-// caches): the same Markov chain as the warp-per-chain kernel in
+// function, Gaussian vertex perturbations and vMF end moves; kGrad keeps
+// d log sigma / dg per vertex for the score of g): the same Markov chain as
+// the warp-per-chain kernel in
 // pmc_chain.cu (Collin, arXiv:1811.04156: section "Numerical path
 // integration", Eq. acceptFact; appendix "Jump proposal" and "Dimension
 // matching transformation"), with the same Philox counters per step and the
@@ -28,10 +29,12 @@ namespace pmc {
 namespace {
 
 constexpr unsigned kAll = 0xffffffffu;
-constexpr int kArrays = 6;           // x, y, z, segment factor, segment length, vertex factor
+// x, y, z, segment factor, segment length, vertex factor (+ d log sigma / dg
+// per vertex when gradients are accumulated)
+__host__ __device__ constexpr int arrays_of(bool grad) { return grad ? 7 : 6; }
 constexpr int kRefresh = 256;        // recompute the path length from the caches
 constexpr int kFlush = 64;           // FP32 partials -> FP64 accumulators
-enum { AX = 0, AY = 1, AZ = 2, ASEG = 3, ALEN = 4, AVT = 5 };
+enum { AX = 0, AY = 1, AZ = 2, ASEG = 3, ALEN = 4, AVT = 5, AGT = 6 };
 enum Move { MV_INTERIOR = 0, MV_END = 1, MV_BIRTH = 2, MV_DEATH = 3 };
 
 struct LanePath {
@@ -59,14 +62,15 @@ struct LanePath {
 // once, weighted by the steps it stayed current (at or after burn-in).
 struct LaneAcc {
   unsigned long long pn2, pn, t_a;
-  float pL, pL2;
+  float pL, pL2, pG;
   unsigned int nflush;
   unsigned int prop_w, prop_end, prop_b, prop_d;
   unsigned int acc_i, acc_e, acc_b, acc_d;
 };
 
+template <bool kGrad>
 __device__ __forceinline__ void lane_close(LaneAcc& a, unsigned long long t_b, unsigned long long burn_in, int n,
-                                           float L) {
+                                           float L, float G) {
   const unsigned long long from = a.t_a > burn_in ? a.t_a : burn_in;
   a.t_a = t_b;
   if (t_b <= from) return;
@@ -76,16 +80,19 @@ __device__ __forceinline__ void lane_close(LaneAcc& a, unsigned long long t_b, u
   a.pn += static_cast<unsigned long long>(n) * d;
   a.pL = fmaf(L, dw, a.pL);
   a.pL2 = fmaf(L * L, dw, a.pL2);
+  if constexpr (kGrad) a.pG = fmaf(G, dw, a.pG);
   a.nflush++;
 }
 
+template <bool kGrad>
 __device__ __forceinline__ void lane_flush(LaneAcc& a, double* acc) {
   acc[ACC_NDIRECT] += static_cast<double>(a.pn2);
   acc[ACC_SUMN] += static_cast<double>(a.pn);
   acc[ACC_SUML] += static_cast<double>(a.pL);
   acc[ACC_SUML2] += static_cast<double>(a.pL2);
+  if constexpr (kGrad) acc[ACC_SUMG] += static_cast<double>(a.pG);
   a.pn2 = a.pn = 0ull;
-  a.pL = a.pL2 = 0.f;
+  a.pL = a.pL2 = a.pG = 0.f;
   a.nflush = 0;
 }
 
@@ -93,6 +100,7 @@ __device__ __forceinline__ void lane_flush(LaneAcc& a, double* acc) {
 // kernel's step: move draw, proposal, change of log p over the changed
 // window, acceptance, commit; sums that the warp kernel forms with shuffles
 // are formed here in the same association where they decide acceptance.
+template <bool kGrad>
 __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* col, int W, uint32_t key0,
                                           uint32_t key1) {
   const DMedium& M = P.M;
@@ -117,7 +125,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
     w.sm[(AZ * W + i) * 32] = w.gm[AZ * cap + i];
   }
   // cached factors of the whole path, with a sliding window of positions
-  float lp0 = 0.f, L = 0.f;
+  float lp0 = 0.f, L = 0.f, G = 0.f;
   {
     float3 Pp = w.pos(0), Pc = Pp;
     for (int i = 0; i < n; ++i) {
@@ -125,7 +133,9 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
       float vt, gt, seg, tb, len;
       vertex_and_segment<false>(M, S, S.zoff, Pp, Pc, Pn, i, n, vt, gt, seg, tb, len);
       w.st(AVT, i, vt);
+      if constexpr (kGrad) w.st(AGT, i, gt);
       lp0 += vt;
+      if constexpr (kGrad) G += gt;
       if (i <= n - 2) {
         w.st(ASEG, i, seg);
         w.st(ALEN, i, len);
@@ -144,7 +154,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
   LaneAcc A;
   A.pn2 = A.pn = 0ull;
   A.t_a = step0;
-  A.pL = A.pL2 = 0.f;
+  A.pL = A.pL2 = A.pG = 0.f;
   A.nflush = 0;
   A.prop_w = A.prop_end = A.prop_b = A.prop_d = 0;
   A.acc_i = A.acc_e = A.acc_b = A.acc_d = 0;
@@ -296,8 +306,8 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
     }
 
     bool accept = false;
-    float nvt[3] = {0.f, 0.f, 0.f}, nseg[2] = {0.f, 0.f}, nlen[2] = {0.f, 0.f};
-    float dlen = 0.f;
+    float nvt[3] = {0.f, 0.f, 0.f}, nseg[2] = {0.f, 0.f}, nlen[2] = {0.f, 0.f}, ngt[3] = {0.f, 0.f, 0.f};
+    float dlen = 0.f, dG = 0.f;
     if (proposed) {
       // new-path positions wlo-1 .. wlo+nc (old index shifted, or the new vertex)
       float3 Q[5];
@@ -311,13 +321,13 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
       // the changed vertex and segment factors against the cached ones; the
       // three per-slot differences are summed as the warp kernel's two
       // shuffle rounds sum them, (d0 + d1) + d2
-      float d[3], e[3], f[3];
+      float d[3], e[3], f[3], gd[3];
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        float nv = 0.f, ns = 0.f, ntb = 0.f, nl = 0.f;
+        float nv = 0.f, ns = 0.f, ntb = 0.f, nl = 0.f, ng = 0.f;
         if (v < nc) {
-          float gt_, seg_, tb_, len_;
-          vertex_and_segment<false>(M, S, S.zoff, Q[v], Q[v + 1], Q[v + 2], wlo + v, n_new, nv, gt_, seg_, tb_,
+          float seg_, tb_, len_;
+          vertex_and_segment<false>(M, S, S.zoff, Q[v], Q[v + 1], Q[v + 2], wlo + v, n_new, nv, ng, seg_, tb_,
                                     len_);
           if (v < nc - 1) {
             ns = seg_;
@@ -325,10 +335,11 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
             nl = len_;
           }
         }
-        float ov = 0.f, os = 0.f, otb = 0.f, ol = 0.f;
+        float ov = 0.f, os = 0.f, otb = 0.f, ol = 0.f, og = 0.f;
         if (v < onc) {
           const int o = olo + v;
           ov = w.ld(AVT, o);
+          if constexpr (kGrad) og = w.ld(AGT, o);
           if (v < onc - 1) {
             os = w.ld(ASEG, o);
             ol = w.ld(ALEN, o);
@@ -336,6 +347,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
           }
         }
         nvt[v] = nv;
+        ngt[v] = ng;
         if (v < 2) {
           nseg[v] = ns;
           nlen[v] = nl;
@@ -343,9 +355,11 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
         d[v] = (nv + ns) - (ov + os);
         e[v] = ntb - otb;
         f[v] = nl - ol;
+        gd[v] = ng - og;
       }
       const float dlp = (d[0] + d[1]) + d[2];
       dlen = (f[0] + f[1]) + f[2];
+      if constexpr (kGrad) dG = (gd[0] + gd[1]) + gd[2];
       if (move == MV_DEATH) {
         // T_b of the reduced path from the current one (summed afresh above)
         const float dtb = (e[0] + e[1]) + e[2];
@@ -365,7 +379,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
       A.acc_e += (move == MV_END);
       A.acc_b += (move == MV_BIRTH);
       A.acc_d += (move == MV_DEATH);
-      lane_close(A, t, R.burn_in, n, L);
+      lane_close<kGrad>(A, t, R.burn_in, n, L, G);
       if (move >= MV_BIRTH) {
         // a birth moves entries k+1 .. n-1 up by one (highest first), a death
         // entries j+1 .. n-1 down by one (lowest first); segment arrays only
@@ -377,6 +391,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
         auto move_any = [&](int i, int j) {
           w.set_pos(j, w.pos(i));
           w.st(AVT, j, w.ld(AVT, i));
+          if constexpr (kGrad) w.st(AGT, j, w.ld(AGT, i));
           if (i < n - 1) {
             w.st(ASEG, j, w.ld(ASEG, i));
             w.st(ALEN, j, w.ld(ALEN, i));
@@ -397,6 +412,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
             float* src2 = src - d * 32;
             const float x0 = src[AX * WS], y0 = src[AY * WS], z0 = src[AZ * WS], v0 = src[AVT * WS];
             const float x1 = src2[AX * WS], y1 = src2[AY * WS], z1 = src2[AZ * WS], v1 = src2[AVT * WS];
+            const float q0 = kGrad ? src[AGT * WS] : 0.f, q1 = kGrad ? src2[AGT * WS] : 0.f;
             const bool s0 = (up ? hi - t : a0 + t) < n - 1, s1 = (up ? hi - t - 1 : a0 + t + 1) < n - 1;
             const float g0 = s0 ? src[ASEG * WS] : 0.f, l0 = s0 ? src[ALEN * WS] : 0.f;
             const float g1 = s1 ? src2[ASEG * WS] : 0.f, l1 = s1 ? src2[ALEN * WS] : 0.f;
@@ -405,6 +421,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
             dst[AY * WS] = y0;
             dst[AZ * WS] = z0;
             dst[AVT * WS] = v0;
+            if constexpr (kGrad) dst[AGT * WS] = q0;
             if (s0) {
               dst[ASEG * WS] = g0;
               dst[ALEN * WS] = l0;
@@ -413,6 +430,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
             src[AY * WS] = y1;
             src[AZ * WS] = z1;
             src[AVT * WS] = v1;
+            if constexpr (kGrad) src[AGT * WS] = q1;
             if (s1) {
               src[ASEG * WS] = g1;
               src[ALEN * WS] = l1;
@@ -424,6 +442,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
             dst[AY * WS] = src[AY * WS];
             dst[AZ * WS] = src[AZ * WS];
             dst[AVT * WS] = src[AVT * WS];
+            if constexpr (kGrad) dst[AGT * WS] = src[AGT * WS];
             if ((up ? hi - t : a0 + t) < n - 1) {
               dst[ASEG * WS] = src[ASEG * WS];
               dst[ALEN * WS] = src[ALEN * WS];
@@ -437,6 +456,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
       for (int v = 0; v < 3; ++v) {
         if (v < nc) {
           w.st(AVT, wlo + v, nvt[v]);
+          if constexpr (kGrad) w.st(AGT, wlo + v, ngt[v]);
           if (v < nc - 1 && v < 2) {
             w.st(ASEG, wlo + v, nseg[v]);
             w.st(ALEN, wlo + v, nlen[v]);
@@ -446,17 +466,23 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
       if (move != MV_DEATH) w.set_pos(inew, fnew);
       n = n_new;
       L += dlen;
-      if (A.nflush >= kFlush) lane_flush(A, acc);
+      G += dG;
+      if (A.nflush >= kFlush) lane_flush<kGrad>(A, acc);
     }
     done = s + 1;
     if (((s + 1) & (kRefresh - 1)) == 0) {
       float Ls = 0.f;
       for (int q = 0; q < n - 1; ++q) Ls += w.ld(ALEN, q);
       L = Ls;
+      if constexpr (kGrad) {
+        float Gs = 0.f;
+        for (int q = 0; q < n; ++q) Gs += w.ld(AGT, q);
+        G = Gs;
+      }
     }
   }
-  lane_close(A, step0 + done, R.burn_in, n, L);
-  lane_flush(A, acc);
+  lane_close<kGrad>(A, step0 + done, R.burn_in, n, L, G);
+  lane_flush<kGrad>(A, acc);
   // recorded states, proposal and acceptance counts
   const unsigned long long t_end = step0 + done;
   const unsigned long long first = step0 > R.burn_in ? step0 : R.burn_in;
@@ -484,12 +510,13 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
 
 // Persistent warps; each work item is 32 consecutive chains of the
 // processing order, one per lane.
+template <bool kGrad>
 __global__ void __launch_bounds__(128, 4) lane_chain_kernel(const ChainParams P) {
   extern __shared__ float lane_smem[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int W = P.smem_cap;
-  float* col = lane_smem + static_cast<size_t>(wib) * kArrays * W * 32 + lane;
+  float* col = lane_smem + static_cast<size_t>(wib) * arrays_of(kGrad) * W * 32 + lane;
   const uint32_t key0 = static_cast<uint32_t>(P.R.seed), key1 = static_cast<uint32_t>(P.R.seed >> 32);
   for (;;) {
     int item = 0;
@@ -497,10 +524,11 @@ __global__ void __launch_bounds__(128, 4) lane_chain_kernel(const ChainParams P)
     item = __shfl_sync(kAll, item, 0);
     const long long g = static_cast<long long>(P.chain_lo) + 32ll * item;
     if (g >= P.chain_hi) break;
-    if (g + lane < P.chain_hi) run_chain(P, P.order[g + lane], col, W, key0, key1);
+    if (g + lane < P.chain_hi) run_chain<kGrad>(P, P.order[g + lane], col, W, key0, key1);
   }
 }
 
+template <bool kGrad>
 cudaError_t lane_attributes() {
   static int done[64] = {};
   int dev = 0;
@@ -510,31 +538,42 @@ cudaError_t lane_attributes() {
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(lane_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  e = cudaFuncSetAttribute(lane_chain_kernel<kGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(lane_chain_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute(lane_chain_kernel<kGrad>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
   return e;
 }
 
+template <bool kGrad>
+cudaError_t occupancy_of(int warps_per_block, int window, int* blocks_per_sm) {
+  cudaError_t e = lane_attributes<kGrad>();
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, lane_chain_kernel<kGrad>, warps_per_block * 32,
+                                                       lane_smem_bytes(window, warps_per_block, kGrad));
+}
+
+template <bool kGrad>
+cudaError_t launch_of(const ChainParams& p, int grid, int warps_per_block, cudaStream_t s) {
+  cudaError_t e = lane_attributes<kGrad>();
+  if (e != cudaSuccess) return e;
+  lane_chain_kernel<kGrad><<<grid, warps_per_block * 32, lane_smem_bytes(p.smem_cap, warps_per_block, kGrad), s>>>(p);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-size_t lane_smem_bytes(int window, int warps_per_block) {
-  return static_cast<size_t>(warps_per_block) * kArrays * static_cast<size_t>(window) * 32u * sizeof(float);
+size_t lane_smem_bytes(int window, int warps_per_block, bool grad) {
+  return static_cast<size_t>(warps_per_block) * arrays_of(grad) * static_cast<size_t>(window) * 32u * sizeof(float);
 }
 
-cudaError_t lane_occupancy(int warps_per_block, int window, int* blocks_per_sm) {
-  cudaError_t e = lane_attributes();
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, lane_chain_kernel, warps_per_block * 32,
-                                                       lane_smem_bytes(window, warps_per_block));
+cudaError_t lane_occupancy(int warps_per_block, int window, bool grad, int* blocks_per_sm) {
+  return grad ? occupancy_of<true>(warps_per_block, window, blocks_per_sm)
+              : occupancy_of<false>(warps_per_block, window, blocks_per_sm);
 }
 
-cudaError_t launch_lane_chain(const ChainParams& p, int grid, int warps_per_block, cudaStream_t s) {
-  cudaError_t e = lane_attributes();
-  if (e != cudaSuccess) return e;
-  lane_chain_kernel<<<grid, warps_per_block * 32, lane_smem_bytes(p.smem_cap, warps_per_block), s>>>(p);
-  return cudaGetLastError();
+cudaError_t launch_lane_chain(const ChainParams& p, int grid, int warps_per_block, bool grad, cudaStream_t s) {
+  return grad ? launch_of<true>(p, grid, warps_per_block, s) : launch_of<false>(p, grid, warps_per_block, s);
 }
 
 }  // namespace pmc

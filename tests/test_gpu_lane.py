@@ -172,6 +172,51 @@ def test_lane_split_runs_are_bit_exact(api, ctx):
     assert np.array_equal(aa[:, 8:], ab[:, 8:])
 
 
+def test_lane_gradient_accumulators_replay_oracle(api, ctx, oracle_lib):
+    """Gaussian-step chains with score accumulation (PMC_FLAG_GRADIENTS) on
+    the lane layout: for every chain whose decisions stayed away from the
+    threshold the FP64 accumulators equal the oracle's (sum of d log sigma/dg
+    within the warp kernel's 1e-3 tolerance, see the accumulator replay of the
+    parity tests)."""
+    O = oracle_lib
+    sc = S.plain(n_chains=64, n_steps=600)
+    sc.run.burn_in = 100
+    sc.run.gradients = True
+    sc.run.layout = S.LAYOUT_LANE
+    _, _, ch = _chains(api, ctx, sc)
+    assert ch.launch_info()[0]["general"] == 4
+    ch.run_steps(600)
+    assert ch.status() == 0
+    acc = ch.read_accumulators()
+    oc = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, 64)
+    margin = oc.run(600, margins=True)
+    oa = oc.accumulators()
+    clean = np.nonzero(margin > 1e-3)[0]
+    assert len(clean) >= 32
+    for c in clean:
+        assert acc[c, 0] == oa["n_rec"][c] and acc[c, 1] == oa["n_direct"][c] and acc[c, 2] == oa["sum_n"][c]
+        assert abs(acc[c, 3] / oa["sum_L"][c] - 1) < 1e-5
+        assert abs(acc[c, 5] - oa["sum_score"][c, 2]) < 1e-3 * (abs(oa["sum_score"][c, 2]) + oa["n_rec"][c])
+        assert np.array_equal(acc[c, 8:12], oa["prop"][c]) and np.array_equal(acc[c, 12:16], oa["acc"][c])
+
+
+def test_lane_gradients_match_warp_layout(api, ctx):
+    """The score-function gradient estimator of the intensity from the lane
+    and the warp layouts (same decisions, so nearly the same states) agree."""
+    out = {}
+    for layout in (S.LAYOUT_WARP, S.LAYOUT_LANE):
+        sc = S.plain(n_chains=8192, n_steps=4000)
+        sc.run.gradients = True
+        sc.run.layout = layout
+        _, _, ch = _chains(api, ctx, sc)
+        ch.run_steps(4000)
+        assert ch.status() == 0
+        out[layout] = ch.grad_estimator()
+    (gw, sw), (gl, sl) = out[S.LAYOUT_WARP], out[S.LAYOUT_LANE]
+    for i in range(3):
+        assert abs(gl[0][i] - gw[0][i]) <= 0.3 * sw[0][i], (i, gl, gw, sw)
+
+
 def test_lane_layout_rejects_general_runs(api, ctx):
     """The lane layout runs lean chains only."""
     sc = S.gradients(n_chains=64, n_steps=100)
