@@ -74,8 +74,9 @@ extern "C" {
 /* Chain layout of the kernel (pmc_run_desc.layout). */
 #define PMC_LAYOUT_AUTO 0      /* autotuner's choice (warp layout when warps_per_block is given) */
 #define PMC_LAYOUT_WARP 1      /* one warp per chain */
-#define PMC_LAYOUT_LANE 2      /* one lane per chain: lean runs only (homogeneous medium, isotropic
-                                  emission, rho = 1, pure Henyey-Greenstein, Gaussian perturbations) */
+#define PMC_LAYOUT_LANE 2      /* one lane per chain: lean physics only (homogeneous medium, isotropic
+                                  emission, rho = 1, pure Henyey-Greenstein) with Gaussian or MALA
+                                  vertex moves */
 
 #define PMC_FLAG_GRADIENTS 1   /* accumulate score terms for pmc_grad_estimator */
 #define PMC_FLAG_NO_GRAPH 2    /* launch kernels directly instead of replaying a CUDA graph */

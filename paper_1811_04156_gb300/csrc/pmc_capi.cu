@@ -191,6 +191,7 @@ struct pmc_chains_s {
   bool grad = false;               // keep d log sigma / dg per vertex
   bool autotune = false;           // warps per block chosen by timing
   int layout = PMC_LAYOUT_AUTO;    // PMC_LAYOUT_*: which chain layouts the autotuner may pick
+  int lane_kind = 0;               // lane layout's kernel kind (4 Gaussian, 5 MALA moves); 0: not eligible
   int init_kind = 0, init_k = 0;
   float init_jitter = 0.f;
   QrefPair* d_qp = nullptr;       // reference-density tables (pmc_bridge)
@@ -497,7 +498,7 @@ int pmc_destroy_chains(pmc_chains_t ch) {
 constexpr double kLaneMaxN = 24.0;
 
 // Work items of a launch: one per chain, or one per 32 chains (lane layout).
-static int work_items(int kind, int chains) { return kind == 4 ? (chains + 31) / 32 : chains; }
+static int work_items(int kind, int chains) { return kind >= 4 ? (chains + 31) / 32 : chains; }
 
 static ChainParams class_params(pmc_chains_t ch, size_t k, unsigned long long n_steps) {
   const ChainClass& cl = ch->classes[k];
@@ -575,15 +576,15 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
           if (w < full && ch->general < 2) cands.emplace_back(ch->general, w);
       }
       if (ch->layout == PMC_LAYOUT_LANE ||
-          (ch->layout == PMC_LAYOUT_AUTO && ch->general == 0 && cl.short_paths))
+          (ch->layout == PMC_LAYOUT_AUTO && ch->lane_kind != 0 && cl.short_paths))
         for (int w : {8, 12, 16, 20, 24, 32}) {
-          cands.emplace_back(4, std::min(w, cl.max_cap));
+          cands.emplace_back(ch->lane_kind, std::min(w, cl.max_cap));
           if (w >= cl.max_cap) break;
         }
       for (const auto& cand : cands) {
         const int ckind = cand.first, win = cand.second;
         for (int wpb : {1, 2, 4}) {
-          const bool spill = ckind != 4 && win < full;
+          const bool spill = ckind < 4 && win < full;
           if (chain_smem_bytes(win, wpb, ckind, ch->grad) > ch->ctx->smem_per_block) continue;
           int bps = 0;
           if (chain_occupancy(ckind, ch->grad, spill, wpb, win, &bps) != cudaSuccess || bps < 1) continue;
@@ -630,7 +631,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
     }
     int bps = 0;
     const int bw = std::get<0>(best), bwin = std::get<1>(best), bkind = std::get<2>(best);
-    const bool spill = bkind != 4 && bwin < full;
+    const bool spill = bkind < 4 && bwin < full;
     if (rc == PMC_OK && chain_occupancy(bkind, ch->grad, spill, bw, bwin, &bps) == cudaSuccess && bps >= 1) {
       cl.kind = bkind;
       cl.warps_per_block = bw;
@@ -718,9 +719,17 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   if (r->within == PMC_WITHIN_TREE) ch->general = 2;
   if (r->within == PMC_WITHIN_HMC) ch->general = 3;
   ch->layout = r->layout;
-  if (r->layout == PMC_LAYOUT_LANE && ch->general != 0)
+  // the lane layout runs the lean physics (homogeneous medium, pure
+  // Henyey-Greenstein, isotropic emission, rho = 1) with Gaussian or MALA moves
+  const bool lean_physics =
+      med->d.kind == PMC_HOMOGENEOUS && !(med->d.f_sl > 0.f) &&
+      std::all_of(ch->h_pairs.begin(), ch->h_pairs.end(),
+                  [](const DPair& d) { return d.emission == PMC_EMIT_ISOTROPIC && d.rho == PMC_RHO_ONE; });
+  if (lean_physics && r->within == PMC_WITHIN_PERTURB) ch->lane_kind = 4;
+  if (lean_physics && r->within == PMC_WITHIN_MALA) ch->lane_kind = 5;
+  if (r->layout == PMC_LAYOUT_LANE && ch->lane_kind == 0)
     return fail(PMC_ERR_INVALID, "the lane layout runs lean chains only (homogeneous medium, isotropic emission, "
-                                 "rho = 1, Henyey-Greenstein, Gaussian perturbations)");
+                                 "rho = 1, Henyey-Greenstein, Gaussian or MALA vertex moves)");
   const int n_arrays = chain_arrays(ch->general > 0, ch->grad);
   const int T = ch->total;
   ch->h_base.resize(T);
@@ -766,7 +775,7 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     cl.max_cap = maxcap;
     cl.spill = false;
     if (r->layout == PMC_LAYOUT_LANE) {
-      cl.kind = 4;
+      cl.kind = ch->lane_kind;
       cl.smem_cap = std::min(r->smem_window > 0 ? r->smem_window : 16, maxcap);
     } else if (r->smem_window > 0 && r->smem_window < cl.smem_cap && ch->general >= 2)
       return fail(PMC_ERR_INVALID, "tree and HMC moves need the whole vertex cap in shared memory (smem_window)");

@@ -1156,7 +1156,7 @@ int kernel_key(int kind, bool grad, bool spill) {
 int chain_arrays(bool general, bool grad) { return 6 + (general ? 1 : 0) + (grad ? 1 : 0); }
 
 size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad) {
-  if (kind == 4) return lane_smem_bytes(smem_cap, warps_per_block, grad);
+  if (kind >= 4) return lane_smem_bytes(smem_cap, warps_per_block, grad);
   const size_t arrays = static_cast<size_t>(chain_arrays(kind > 0, grad) + (kind == 2 ? 3 : 0) + (kind == 3 ? 6 : 0));
   return static_cast<size_t>(warps_per_block) *
          (arrays * static_cast<size_t>(smem_cap) + 32u * kRngWords + kPairWords) * sizeof(float);
@@ -1164,7 +1164,7 @@ size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad) 
 
 cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block, int smem_cap,
                             int* blocks_per_sm) {
-  if (kind == 4) return lane_occupancy(warps_per_block, smem_cap, grad, blocks_per_sm);
+  if (kind >= 4) return lane_occupancy(warps_per_block, smem_cap, grad, kind == 5, blocks_per_sm);
   if (kind >= 2 && spill) return cudaErrorInvalidValue;
   const size_t sm = chain_smem_bytes(smem_cap, warps_per_block, kind, grad);
   switch (kernel_key(kind, grad, spill)) {
@@ -1185,7 +1185,7 @@ cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block
 
 cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s) {
-  if (kind == 4) return launch_lane_chain(p, grid, warps_per_block, grad, s);
+  if (kind >= 4) return launch_lane_chain(p, grid, warps_per_block, grad, kind == 5, s);
   if (kind >= 2 && spill) return cudaErrorInvalidValue;
   const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block, kind, grad);
   switch (kernel_key(kind, grad, spill)) {

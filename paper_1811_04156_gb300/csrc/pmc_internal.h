@@ -70,8 +70,9 @@ struct ChainParams {
 // `kind`: 0 the lean kernel, 1 the general one, 2 the general one with tree
 // moves (3 more shared arrays per warp, no spill), 3 the general one with HMC
 // moves (6 more shared arrays per warp, no spill), 4 the lean kernel with one
-// chain per lane (pmc_lane.cu; smem_cap is each lane's shared window, entries
-// beyond it in the chain's global block; a work item is 32 chains).
+// chain per lane and Gaussian vertex moves, 5 the same with MALA moves
+// (pmc_lane.cu; smem_cap is each lane's shared window, entries beyond it in
+// the chain's global block; a work item is 32 chains).
 int chain_arrays(bool general, bool grad);
 cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s);
@@ -79,10 +80,12 @@ size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad);
 cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block, int smem_cap,
                             int* blocks_per_sm);
 
-// pmc_lane.cu (kind 4 above; `grad` adds the per-vertex d log sigma / dg array)
+// pmc_lane.cu (kinds 4 and 5 above; `grad` adds the per-vertex d log sigma /
+// dg array, `mala` selects MALA vertex moves)
 size_t lane_smem_bytes(int window, int warps_per_block, bool grad);
-cudaError_t lane_occupancy(int warps_per_block, int window, bool grad, int* blocks_per_sm);
-cudaError_t launch_lane_chain(const ChainParams& p, int grid, int warps_per_block, bool grad, cudaStream_t s);
+cudaError_t lane_occupancy(int warps_per_block, int window, bool grad, bool mala, int* blocks_per_sm);
+cudaError_t launch_lane_chain(const ChainParams& p, int grid, int warps_per_block, bool grad, bool mala,
+                              cudaStream_t s);
 
 struct InitParams {
   DRun R;

@@ -1,6 +1,6 @@
 // Lane-per-chain RJMCMC kernel for the lean case (homogeneous medium,
 // isotropic emission, detection probability 1, Henyey-Greenstein phase
-// function, Gaussian vertex perturbations and vMF end moves; kGrad keeps
+// function, Gaussian or MALA vertex moves and vMF end moves; kGrad keeps
 // d log sigma / dg per vertex for the score of g): the same Markov chain as
 // the warp-per-chain kernel in
 // pmc_chain.cu (Collin, arXiv:1811.04156: section "Numerical path
@@ -100,7 +100,7 @@ __device__ __forceinline__ void lane_flush(LaneAcc& a, double* acc) {
 // kernel's step: move draw, proposal, change of log p over the changed
 // window, acceptance, commit; sums that the warp kernel forms with shuffles
 // are formed here in the same association where they decide acceptance.
-template <bool kGrad>
+template <bool kGrad, bool kMala>
 __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* col, int W, uint32_t key0,
                                           uint32_t key1) {
   const DMedium& M = P.M;
@@ -203,6 +203,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
     int n_new = n, wlo = 0, nc = 0, olo = 0, onc = 0, jj = -1, kk = -1;
     int inew = -1, sh_from = INT_MAX, sh_by = 0;
     float3 fnew = f3(0.f, 0.f, 0.f);
+    float3 gx = f3(0.f, 0.f, 0.f);  // MALA: d log p / d f_j at the current path
     float extra = 0.f;
     float3 IA, IB, IF;  // births and deaths: the insertion density's segment ends and vertex
     if (within) {
@@ -228,7 +229,15 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
         const float r1 = m_sqrt<true>(-2.0f * __logf(ub0));
         const float r2 = m_sqrt<true>(-2.0f * __logf(ub2));
         const float3 z = f3(r1 * c1, r1 * s1, r2 * cB);
-        fnew = w.pos(j) + R.sigma * z;
+        const float3 fj = w.pos(j);
+        if constexpr (kMala) {
+          // Langevin step: drift along the local gradient of log p
+          gx = grad_vertex(M, S, S.zoff, [&](int k) { return w.pos(k); }, n, j);
+          const float h = 0.5f * R.mala_eps * R.mala_eps;
+          fnew = fj + h * gx + R.mala_eps * z;
+        } else {
+          fnew = fj + R.sigma * z;
+        }
         wlo = j - 1; nc = 3; olo = j - 1; onc = 3;
       }
     } else if (birth) {
@@ -372,6 +381,15 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
         const float lid = log_insert_density<true>(M, R, S.zoff, IA, IB, IF);
         extra = (move == MV_BIRTH) ? extra - lid : extra + lid;
       }
+      if (kMala && move == MV_INTERIOR && isfinite(dlp)) {
+        // MALA Hastings ratio q(x | y) / q(y | x), with the gradient at the proposal
+        const float3 gy = grad_vertex(M, S, S.zoff, [&](int k) { return k == jj ? fnew : w.pos(k); }, n, jj);
+        const float h = 0.5f * R.mala_eps * R.mala_eps;
+        const float3 fj = w.pos(jj);
+        const float3 dfw = fnew - fj - h * gx;
+        const float3 dbw = fj - fnew - h * gy;
+        extra = (dot(dfw, dfw) - dot(dbw, dbw)) / (2.0f * R.mala_eps * R.mala_eps);
+      }
       accept = logu < dlp + extra;
     }
     if (accept) {
@@ -510,7 +528,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
 
 // Persistent warps; each work item is 32 consecutive chains of the
 // processing order, one per lane.
-template <bool kGrad>
+template <bool kGrad, bool kMala>
 __global__ void __launch_bounds__(128, 4) lane_chain_kernel(const ChainParams P) {
   extern __shared__ float lane_smem[];
   const int lane = threadIdx.x & 31;
@@ -524,11 +542,11 @@ __global__ void __launch_bounds__(128, 4) lane_chain_kernel(const ChainParams P)
     item = __shfl_sync(kAll, item, 0);
     const long long g = static_cast<long long>(P.chain_lo) + 32ll * item;
     if (g >= P.chain_hi) break;
-    if (g + lane < P.chain_hi) run_chain<kGrad>(P, P.order[g + lane], col, W, key0, key1);
+    if (g + lane < P.chain_hi) run_chain<kGrad, kMala>(P, P.order[g + lane], col, W, key0, key1);
   }
 }
 
-template <bool kGrad>
+template <bool kGrad, bool kMala>
 cudaError_t lane_attributes() {
   static int done[64] = {};
   int dev = 0;
@@ -538,26 +556,28 @@ cudaError_t lane_attributes() {
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(lane_chain_kernel<kGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  e = cudaFuncSetAttribute(lane_chain_kernel<kGrad, kMala>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(lane_chain_kernel<kGrad>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = cudaFuncSetAttribute(lane_chain_kernel<kGrad, kMala>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
   return e;
 }
 
-template <bool kGrad>
+template <bool kGrad, bool kMala>
 cudaError_t occupancy_of(int warps_per_block, int window, int* blocks_per_sm) {
-  cudaError_t e = lane_attributes<kGrad>();
+  cudaError_t e = lane_attributes<kGrad, kMala>();
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, lane_chain_kernel<kGrad>, warps_per_block * 32,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, lane_chain_kernel<kGrad, kMala>,
+                                                       warps_per_block * 32,
                                                        lane_smem_bytes(window, warps_per_block, kGrad));
 }
 
-template <bool kGrad>
+template <bool kGrad, bool kMala>
 cudaError_t launch_of(const ChainParams& p, int grid, int warps_per_block, cudaStream_t s) {
-  cudaError_t e = lane_attributes<kGrad>();
+  cudaError_t e = lane_attributes<kGrad, kMala>();
   if (e != cudaSuccess) return e;
-  lane_chain_kernel<kGrad><<<grid, warps_per_block * 32, lane_smem_bytes(p.smem_cap, warps_per_block, kGrad), s>>>(p);
+  lane_chain_kernel<kGrad, kMala>
+      <<<grid, warps_per_block * 32, lane_smem_bytes(p.smem_cap, warps_per_block, kGrad), s>>>(p);
   return cudaGetLastError();
 }
 
@@ -567,13 +587,21 @@ size_t lane_smem_bytes(int window, int warps_per_block, bool grad) {
   return static_cast<size_t>(warps_per_block) * arrays_of(grad) * static_cast<size_t>(window) * 32u * sizeof(float);
 }
 
-cudaError_t lane_occupancy(int warps_per_block, int window, bool grad, int* blocks_per_sm) {
-  return grad ? occupancy_of<true>(warps_per_block, window, blocks_per_sm)
-              : occupancy_of<false>(warps_per_block, window, blocks_per_sm);
+cudaError_t lane_occupancy(int warps_per_block, int window, bool grad, bool mala, int* blocks_per_sm) {
+  if (mala)
+    return grad ? occupancy_of<true, true>(warps_per_block, window, blocks_per_sm)
+                : occupancy_of<false, true>(warps_per_block, window, blocks_per_sm);
+  return grad ? occupancy_of<true, false>(warps_per_block, window, blocks_per_sm)
+              : occupancy_of<false, false>(warps_per_block, window, blocks_per_sm);
 }
 
-cudaError_t launch_lane_chain(const ChainParams& p, int grid, int warps_per_block, bool grad, cudaStream_t s) {
-  return grad ? launch_of<true>(p, grid, warps_per_block, s) : launch_of<false>(p, grid, warps_per_block, s);
+cudaError_t launch_lane_chain(const ChainParams& p, int grid, int warps_per_block, bool grad, bool mala,
+                              cudaStream_t s) {
+  if (mala)
+    return grad ? launch_of<true, true>(p, grid, warps_per_block, s)
+                : launch_of<false, true>(p, grid, warps_per_block, s);
+  return grad ? launch_of<true, false>(p, grid, warps_per_block, s)
+              : launch_of<false, false>(p, grid, warps_per_block, s);
 }
 
 }  // namespace pmc

@@ -217,9 +217,51 @@ def test_lane_gradients_match_warp_layout(api, ctx):
         assert abs(gl[0][i] - gw[0][i]) <= 0.3 * sw[0][i], (i, gl, gw, sw)
 
 
+def test_lane_mala_accumulators_replay_oracle(api, ctx, oracle_lib):
+    """MALA chains with gradients (the gradients workload's moves) on the lane
+    layout: every chain whose decisions stayed away from the threshold has the
+    oracle's accumulators."""
+    O = oracle_lib
+    sc = S.gradients(n_chains=64, n_steps=600)
+    sc.run.burn_in = 100
+    sc.run.layout = S.LAYOUT_LANE
+    _, _, ch = _chains(api, ctx, sc)
+    assert ch.launch_info()[0]["general"] == 5
+    ch.run_steps(600)
+    assert ch.status() == 0
+    acc = ch.read_accumulators()
+    xyz, n, _ = ch.read_states()
+    oc = O.Chains(sc.medium, sc.sources[0], sc.sensors[0], sc.run, 64, 64)
+    margin = oc.run(600, margins=True)
+    oa = oc.accumulators()
+    clean = np.nonzero(margin > 1e-3)[0]
+    assert len(clean) >= 32
+    for c in clean:
+        assert n[c] == oc.n[c]
+        assert np.allclose(xyz[c, :, :n[c]].T, oc.xyz[c, :n[c]], atol=2e-4), c
+        assert acc[c, 0] == oa["n_rec"][c] and acc[c, 1] == oa["n_direct"][c] and acc[c, 2] == oa["sum_n"][c]
+        assert abs(acc[c, 3] / oa["sum_L"][c] - 1) < 1e-5
+        assert abs(acc[c, 5] - oa["sum_score"][c, 2]) < 1e-3 * (abs(oa["sum_score"][c, 2]) + oa["n_rec"][c])
+        assert np.array_equal(acc[c, 8:12], oa["prop"][c]) and np.array_equal(acc[c, 12:16], oa["acc"][c])
+
+
+def test_lane_mala_single_scatter_sector(api, ctx):
+    """MALA on the lane layout, cap 3: I = Z2 + Z3 by independent quadrature."""
+    sc = S.plain(n_chains=4096, n_steps=20000, cap=3)
+    sc.run.within = S.WITHIN_MALA
+    sc.run.layout = S.LAYOUT_LANE
+    _, _, ch = _chains(api, ctx, sc)
+    ch.run_steps(20000)
+    e = ch.read_estimator()[0]
+    ref = Q.z2_closed(1.0, 0.1, 2.2) + Q.z3(1.0, 0.1, 0.5, 5.0, 0.9)
+    assert abs(e["intensity"] - ref) < 3 * e["std_err"], (e["intensity"], e["std_err"], ref)
+    assert e["rel_err"] < 0.003
+
+
 def test_lane_layout_rejects_general_runs(api, ctx):
-    """The lane layout runs lean chains only."""
-    sc = S.gradients(n_chains=64, n_steps=100)
+    """The lane layout runs the lean physics only (here: a simplified-Liu mixture)."""
+    sc = S.plain(n_chains=64, n_steps=100)
+    sc.medium.f_sl = 0.45
     sc.run.layout = S.LAYOUT_LANE
     medium = api.Medium(ctx, sc.medium)
     geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
