@@ -554,7 +554,11 @@ def seed_from_tracer(chains: "Chains", seed: int = 2024, photons_per_round: int 
     """Initialise every chain with an equilibrium path: weight-thinned tracer
     paths per pair, reused cyclically when fewer than the pair's chains were
     found; returns the photons traced per pair.  Pair p traces with Philox
-    key seed + p, so the pairs' seeds are independent.  r_reject: photons farther
+    key seed + p, so the pairs' seeds are independent.  Every accepted path
+    of the traced photon range is kept (a round that finds more than the
+    buffer holds is traced again with half the photons, since the buffer
+    keeps the paths that finish first, which would favour short paths), and
+    the chains take a seeded random subset of them.  r_reject: photons farther
     than this from the sensor centre are dropped (a finite radius shortens
     the tracing of escaping photons; its bias is the weight of paths that
     leave the ball and return)."""
@@ -567,10 +571,16 @@ def seed_from_tracer(chains: "Chains", seed: int = 2024, photons_per_round: int 
     for p, pr in enumerate(geom.pairs):
         got_x, got_n, photons = [], [], 0
         need = pr.n_chains
-        for _ in range(max_rounds):
-            xyz, n, acc = trace_paths(chains.ctx, chains.medium, geom, p, seed + p, photons_per_round, need,
+        per_round = int(photons_per_round)
+        rounds = 0
+        while rounds < max_rounds:
+            xyz, n, acc = trace_paths(chains.ctx, chains.medium, geom, p, seed + p, per_round, need,
                                       photon0=photons, stride=stride, r_reject=r_reject)
-            photons += photons_per_round
+            if acc > need and per_round > 1:
+                per_round = max(1, per_round // 2)   # overflow: the same photons again, fewer at a time
+                continue
+            rounds += 1
+            photons += per_round
             if len(n):
                 got_x.append(xyz.cpu().numpy())
                 got_n.append(n.cpu().numpy())
@@ -580,7 +590,10 @@ def seed_from_tracer(chains: "Chains", seed: int = 2024, photons_per_round: int 
             raise RuntimeError(f"no detected photon for pair {p} after {photons} photons")
         X = np.concatenate(got_x, axis=1)
         Nn = np.concatenate(got_n)
-        idx = np.arange(need) % len(Nn)
+        if len(Nn) >= need:
+            idx = np.random.default_rng([int(seed), p]).permutation(len(Nn))[:need]
+        else:
+            idx = np.arange(need) % len(Nn)
         total_xyz[c0:c0 + need] = X[:, idx, :].transpose(1, 0, 2)
         total_n[c0:c0 + need] = Nn[idx]
         used.append(photons)

@@ -538,11 +538,14 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
   unsigned long long* sst = nullptr;
   double* sacc = nullptr;
   int* sstat = nullptr;
-  const int kind = (ch->general * 2 + ch->grad) * 3 + ch->layout;
+  // cache key: the warp kernel instance, the layout request and which lane
+  // kernel (if any) the run may use; per class also whether its paths are short
+  const int kind = (((ch->general * 2 + ch->grad) * 3 + ch->layout) * 8 + ch->lane_kind) * 2;
   auto bucket_of = [](int chains) { return 31 - __builtin_clz(static_cast<unsigned>(std::max(1, chains))); };
   bool need = false;
   for (auto& cl : ch->classes)
-    if (!ch->ctx->tuned.count(std::make_tuple(kind, cl.max_cap, bucket_of(cl.hi - cl.lo)))) need = true;
+    if (!ch->ctx->tuned.count(std::make_tuple(kind + cl.short_paths, cl.max_cap, bucket_of(cl.hi - cl.lo))))
+      need = true;
   if (need) {
     CK(dalloc(&sx, static_cast<size_t>(ch->xyz_floats)));
     CK(dalloc(&sn, T));
@@ -558,7 +561,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
     ChainClass& cl = ch->classes[k];
     const int chains = cl.hi - cl.lo;
     const int full = (cl.max_cap + 31) / 32 * 32;
-    const auto key = std::make_tuple(kind, cl.max_cap, bucket_of(chains));
+    const auto key = std::make_tuple(kind + cl.short_paths, cl.max_cap, bucket_of(chains));
     auto it = ch->ctx->tuned.find(key);
     std::tuple<int, int, int> best(cl.warps_per_block, cl.smem_cap, cl.kind);
     if (it != ch->ctx->tuned.end()) {

@@ -258,6 +258,21 @@ def test_lane_mala_single_scatter_sector(api, ctx):
     assert e["rel_err"] < 0.003
 
 
+def test_autotuner_cache_keeps_kernels_apart(api, ctx):
+    """Tuned launch shapes are cached per context: a lean MALA run (which may
+    take the lane layout) and a general MALA run of the same cap and chain
+    count must not share an entry, or the second would run the lean kernel."""
+    sc = S.plain(n_chains=65536, n_steps=100, cap=3)
+    sc.run.within = S.WITHIN_MALA
+    _, _, a = _chains(api, ctx, sc)
+    sc2 = S.plain(n_chains=65536, n_steps=100, cap=3)
+    sc2.run.within = S.WITHIN_MALA
+    sc2.medium.f_sl = 0.45
+    _, _, b = _chains(api, ctx, sc2)
+    assert a.launch_info()[0]["general"] in (1, 5)
+    assert b.launch_info()[0]["general"] == 1
+
+
 def test_lane_layout_rejects_general_runs(api, ctx):
     """The lane layout runs the lean physics only (here: a simplified-Liu mixture)."""
     sc = S.plain(n_chains=64, n_steps=100)

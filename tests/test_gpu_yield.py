@@ -297,7 +297,10 @@ def test_chain_length_distribution_matches_tracer(api, ctx):
     lo, hi, nb = 1.0, 9.0, 32
     hist = torch.zeros((2, nb), dtype=torch.float64, device="cuda")
     total = sum(p.n_chains for p in sc.pairs)
-    lsum = np.zeros(total)
+    centres = lo + (np.arange(nb) + 0.5) * (hi - lo) / nb
+    # per chain: the bin centres of its observed lengths inside [lo, hi), the
+    # same binned and clipped quantity as the tracer's histogram mean
+    csum, ccnt = np.zeros(total), np.zeros(total)
     n_obs = 100
     for _ in range(n_obs):
         ch.run_steps(100)
@@ -306,10 +309,12 @@ def test_chain_length_distribution_matches_tracer(api, ctx):
         seg = np.diff(xyz.astype(np.float64), axis=2)
         ln = np.sqrt((seg ** 2).sum(axis=1))
         mask = np.arange(ln.shape[1])[None, :] < (n[:, None] - 1)
-        lsum += (ln * mask).sum(axis=1)
+        L = (ln * mask).sum(axis=1)
+        inr = (L >= lo) & (L < hi)
+        b = np.clip(((L - lo) / (hi - lo) * nb).astype(int), 0, nb - 1)
+        csum += np.where(inr, centres[b], 0.0)
+        ccnt += inr
     h = hist.cpu().numpy()
-    per_chain = lsum / n_obs
-    centres = lo + (np.arange(nb) + 0.5) * (hi - lo) / nb
     c0 = 0
     for p, pr in enumerate(sc.pairs):
         tr, th = api.trace_lengths(ctx, medium, geom, p, 31 + p, 400_000_000, lo, hi, nb, max_scatter=cap - 2)
@@ -317,10 +322,12 @@ def test_chain_length_distribution_matches_tracer(api, ctx):
         a = np.cumsum(h[p]) / h[p].sum()
         b = np.cumsum(th) / th.sum()
         assert np.abs(a - b).max() < 0.03, (p, np.abs(a - b).max())
-        pc = per_chain[c0:c0 + pr.n_chains]
+        s_, c_ = csum[c0:c0 + pr.n_chains], ccnt[c0:c0 + pr.n_chains]
         c0 += pr.n_chains
-        mc, se_c = pc.mean(), pc.std(ddof=1) / np.sqrt(len(pc))
-        mt = (centres * th).sum() / th.sum()           # binned tracer mean (2.5 mm bins)
+        mc = s_.sum() / c_.sum()
+        # ratio estimator over independent chains
+        se_c = np.sqrt(((s_ - mc * c_) ** 2).sum() * len(c_) / (len(c_) - 1)) / c_.sum()
+        mt = (centres * th).sum() / th.sum()           # binned tracer mean (0.25 m bins)
         assert abs(mc - mt) < 4 * se_c + 0.002, (p, mc, mt, se_c)
 
 
