@@ -1,17 +1,19 @@
-// Lane-per-chain RJMCMC kernel for the lean case (homogeneous medium,
+// Lane-per-chain RJMCMC kernel for the lean physics (homogeneous medium,
 // isotropic emission, detection probability 1, Henyey-Greenstein phase
-// function, Gaussian or MALA vertex moves and vMF end moves; kGrad keeps
-// d log sigma / dg per vertex for the score of g): the same Markov chain as
-// the warp-per-chain kernel in
-// pmc_chain.cu (Collin, arXiv:1811.04156: section "Numerical path
-// integration", Eq. acceptFact; appendix "Jump proposal" and "Dimension
-// matching transformation"), with the same Philox counters per step and the
-// same proposals and acceptance rule, but one chain per thread.
+// function) with Gaussian (kMala = false) or MALA (kMala) vertex moves and
+// vMF end moves; kGrad keeps d log sigma / dg per vertex for the score of g.
+// It runs the same Markov chain as the warp-per-chain kernel in pmc_chain.cu
+// (Collin, arXiv:1811.04156: section "Numerical path integration", Eq.
+// acceptFact; appendix "Jump proposal" and "Dimension matching
+// transformation"): the same Philox counters per step, the same proposals
+// and acceptance rule, one chain per thread.
 //
 // Why: a perturbation changes O(1) factors, so a warp per chain leaves most
 // lanes idle on the 60 % of steps that are perturbations; with a chain per
 // lane every lane does useful work, and the warp serialises only the move
-// kinds that its 32 chains drew at that step.
+// kinds that its 32 chains drew at that step.  Work that several kinds share
+// therefore runs once outside their branches, and the loops whose trip count
+// is a path length index the shared window directly.
 //
 // Layout: the first W vertices of each chain (W = smem_cap) live in the
 // warp's shared block as [array][vertex][lane] floats, so that every lane
@@ -98,8 +100,10 @@ __device__ __forceinline__ void lane_flush(LaneAcc& a, double* acc) {
 
 // Every step of one chain's residency, on one lane.  Mirrors the warp
 // kernel's step: move draw, proposal, change of log p over the changed
-// window, acceptance, commit; sums that the warp kernel forms with shuffles
-// are formed here in the same association where they decide acceptance.
+// window, acceptance, commit.  The change of log p over the window is summed
+// in the warp kernel's shuffle order; the T_b sums over the path run
+// sequentially here (the warp kernel's tree sums can differ in the last bit,
+// which moves a decision only when it falls within that of the threshold).
 template <bool kGrad, bool kMala>
 __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* col, int W, uint32_t key0,
                                           uint32_t key1) {
