@@ -437,14 +437,19 @@ def ours(args):
                  "source": "instructions per proposal from the committed ncu capture of this kernel and workload; "
                            "peak = 4 warp instructions/clk/SM x SMs x median SM clock under load"}
     # DRAM traffic of one launch (dram__bytes_read + write) from the committed
-    # ncu captures, scaled by chains: warp layout 8.9 MB for 16,384 chains, lane
-    # layout 37.3 MB for 65,536 chains (window 20; 35.8 MB read, 1.4 MB written)
+    # ncu captures, scaled by chains: warp layout 8.9 MB for 16,384 chains x
+    # 2,000 steps; lane layout (window 20) 48.4 MB for 65,536 chains x 20,000
+    # steps (44.7 MB read, 3.7 MB written; 37.3 MB at 2,000 steps: the traffic
+    # of a launch grows slowly with its steps, not in proportion)
     kind = li[0]["general"] if len(li) == 1 else None
-    traffic = None
+    traffic, traffic_source = None, None
     if sc.name == "detector" and kind == 0:
         traffic = 8.9e6 * n_chains / 16384.0
+        traffic_source = "ncu, 16,384 chains x 2,000 steps, scaled by chains"
     elif sc.name == "detector" and kind == 4 and li[0]["smem_cap"] == 20:
-        traffic = 37.3e6 * n_chains / 65536.0
+        traffic = 48.4e6 * n_chains / 65536.0
+        traffic_source = ("ncu, 65,536 chains x 20,000 steps (37.3 MB at 2,000 steps; grows slowly with the "
+                          "launch's steps, so the 100,000-step launch's figure is somewhat higher)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -454,7 +459,7 @@ def ours(args):
                        "l2": "flushed between steps (256 MB write)", "accumulators": "f64",
                        "launch": chains.launch_info()},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": traffic,
+                         "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_source,
                          "pipe": bound_pipe,
                          "peak_source": f"{bound_pipe}: max of the microbenchmark rate and lanes/clk/SM x "
                                         f"{n_sm} SMs x sm_max_mhz ({peak_kind} clock {sm_mhz:.0f} MHz); "
