@@ -304,11 +304,14 @@ PMC_API int pmc_total_chains(pmc_chains_t chains);
 
 /* Launch shapes chosen for the chains (by the autotuner when
  * warps_per_block = 0): one row of 6 ints per vertex-cap class, written to
- * `out` (host): shared-memory window in vertices (smaller than the class's
- * caps when entries beyond it live in global memory), first and one-past-last position in the
- * processing order, warps (= chains) per block, persistent grid size, 1 if
- * the general kernel instantiation runs.  Returns the number of classes in
- * *n_classes; writes at most max_rows rows. */
+ * `out` (host): shared-memory window in vertices per chain (smaller than the
+ * class's caps when entries beyond it live in global memory), first and
+ * one-past-last position in the processing order, warps per block,
+ * persistent grid size, and the kernel: 0 the lean and 1 the general kernel
+ * with one warp per chain, 2 the general kernel with tree moves, 3 with HMC
+ * moves, 4 the lean kernel with one chain per lane (32 chains per warp), 5
+ * the same with MALA moves.  Returns the number of classes in *n_classes;
+ * writes at most max_rows rows. */
 PMC_API int pmc_chains_launch_info(pmc_chains_t chains, int* out, int max_rows, int* n_classes);
 
 /* Serialise / restore the complete chain state (positions, vertex counts,
