@@ -31,15 +31,21 @@ sys.path.insert(0, ROOT)
 METRIC = "RJMCMC proposals/s"
 UNIT = "proposals/s"
 
-# Algorithmic work of one proposal per move type, counted from the formulas
-# the delta evaluator needs (the proposal, the changed segment and vertex
-# factors, the acceptance ratio, Box-Muller / vMF / logistic transforms of the
-# random numbers); integer Philox work is not counted.  FP32 = adds,
-# multiplies and fused multiply-adds; MUFU = transcendentals and reciprocals
-# on the special-function unit.  Derivation in the design notes (roofline).
+# Algorithmic work of one proposal, per move type, as the survey of the
+# method counts it: FP32 operations of the proposal and of the changed factors
+# (O(n) scans for births and deaths, n the vertex count), the integer work of
+# the two Philox4x32-10 blocks every step draws (2 blocks x 10 rounds x 6
+# multiply / xor operations), and special-function (MUFU) operations.  The
+# lane-op roofline bounds a proposal by max((FP32 + INT) / (128 N_SM f),
+# MUFU / (16 N_SM f)) at SM clock f.
+LANE_OPS = {"perturb": (90.0, 8.0), "birth": (150.0, 16.0), "death": (130.0, 14.0)}  # FP32 (+ n), MUFU
+INT_PER_PROPOSAL = 120.0
+# The same FP32 count from the delta evaluator's own formulas (interior / end
+# vertex moves, births, deaths), without the integer work.
 FP32_PER_PROPOSAL = {"interior": 145.0, "end": 95.0, "birth": 206.0, "death": 122.0}
-MUFU_PER_PROPOSAL = {"interior": 23.0, "end": 16.0, "birth": 30.0, "death": 19.0}
+FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
+ISSUE_PER_CLK_PER_SM = 4
 
 WORKLOAD_TEXT = {
     "detector": "detector: 1 pair, D=50 m, R=0.165 m, lambda_s=5 m, lambda_a=100 m, g=0.94, 65,536 chains x "
@@ -50,17 +56,30 @@ WORKLOAD_TEXT = {
                "lambda_a=5 m, g=0.9",
     "layered": "layered: 100 x 10 m layers, 60 sensors x 8,192 chains, cap 1,024, g=0.94",
 }
-FP32_LANES_PER_SM = 128
-# Warp instructions per proposal of the chain kernels, from the committed ncu
-# captures of the same kernel, workload and shared window, keyed by (workload,
-# kernel kind, window): kind 0 one warp per chain with the whole cap
-# (profiles/chain_kernel_detector.md), kind 4 one lane per chain
-# (profiles/lane_chain_kernel_detector.md).
-WARP_INST_PER_PROPOSAL = {("detector", 0, 256): 405.7, ("detector", 4, 16): 82.07, ("detector", 4, 20): 59.55}
-ISSUE_PER_CLK_PER_SM = 4
+
+# Counters of the lane kernel on the detector workload from an ncu capture,
+# valid only for the kernel source they were taken from (sha256 of
+# csrc/pmc_lane.cu + csrc/pmc_device.cuh, in that order): warp instructions
+# per proposal (window 20) and DRAM bytes (read + write) of a 65,536-chain
+# launch.  With another source the bench reports them as null.
+LANE_CAPTURE = {"source_sha256": "", "inst_per_proposal": None, "dram_bytes_per_launch": None,
+                "capture": ""}
 
 
-def parse():
+def lane_kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("pmc_lane.cu", "pmc_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1811_04156_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def parse(argv=None):
+    return parse_args(argv)
+
+
+def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=3)
@@ -72,6 +91,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the other workloads' rates and the time-to-1%% comparison after the timed steps")
+    p.add_argument("--ttt-limit", type=float, default=25.0, help="seconds per method of the time-to-target runs")
     p.add_argument("--warps-per-block", type=int, default=0)
     p.add_argument("--layout", choices=["auto", "warp", "lane"], default="auto",
                    help="chain layout of the kernel: the autotuner's choice, one warp or one lane per chain")
@@ -112,7 +134,25 @@ def parse():
     p.add_argument("--ts-seed", action="store_true",
                    help="start the chains from weight-thinned tracer paths (exact draws, as the paper seeds its "
                         "chains) instead of straight jittered paths")
-    return p.parse_args()
+    return p.parse_args(argv)
+
+
+def measure_pipes(device: int, stream) -> dict:
+    """Measured FP32 FMA and MUFU lane-operations per second of the device,
+    from the harness's pipe-rate microbenchmark (libpmcprobe.so, built beside
+    the product library; not part of its C ABI)."""
+    import ctypes as C
+    from paper_1811_04156_gb300 import build as B
+    B.build()
+    lib = C.CDLL(B.PROBE_LIB)
+    fn = lib.pmcprobe_measure_pipes
+    fn.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_void_p]
+    fn.restype = C.c_int
+    out = (C.c_double * 2)()
+    rc = fn(int(device), out, C.c_void_p(stream.cuda_stream if stream is not None else 0))
+    if rc != 0:
+        raise RuntimeError(f"pipe-rate microbenchmark failed (cudaError {rc})")
+    return {"fp32_per_s": float(out[0]), "mufu_per_s": float(out[1])}
 
 
 def load_peaks():
@@ -174,14 +214,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def scene_for(args):
+def scene_for(args, world: int = 1):
+    """The workload.  Single-pair workloads grow with the ranks (weak scaling:
+    `--chains` chains per GPU, one pair of world x chains chains); multi-pair
+    workloads are split as they are (strong scaling)."""
     from paper_1811_04156_gb300 import scenes as S
     if args.workload == "detector":
-        return S.detector(n_chains=args.chains, n_steps=args.run_steps)
+        return S.detector(n_chains=args.chains * world, n_steps=args.run_steps)
     if args.workload == "plain":
-        return S.plain(n_chains=args.chains, n_steps=args.run_steps)
+        return S.plain(n_chains=args.chains * world, n_steps=args.run_steps)
     if args.workload == "gradients":
-        return S.gradients(n_chains=args.chains, n_steps=args.run_steps)
+        return S.gradients(n_chains=args.chains * world, n_steps=args.run_steps)
     if args.workload == "batched":
         return S.batched(n_steps=args.run_steps)
     if args.workload == "layered":
@@ -189,27 +232,35 @@ def scene_for(args):
     raise SystemExit(f"unknown workload {args.workload}")
 
 
-def host_initial_paths(sc, stride=8):
-    """Straight initial paths with jittered interior vertices, built on the host
-    (seeded), as a user would pass them through the C ABI."""
+def host_initial_paths(sc, lo: int, hi: int):
+    """The run's initial paths (straight, init_k interior vertices jittered by
+    N(0, init_jitter^2); the direct path when init_k = 0) of the geometry's
+    chains [lo, hi), built on the host (seeded), as a user passes them
+    through the C ABI: absolute positions [chain][3][stride], counts [chain]."""
     import numpy as np
     from paper_1811_04156_gb300 import scenes as S
-    p = sc.pairs[0]
-    src = np.asarray(sc.sources[0].pos, float)
-    c = np.asarray(sc.sensors[p.sensor].centre, float)
-    R = sc.sensors[p.sensor].radius
-    u = (src - c) / np.linalg.norm(src - c)
-    e = c + R * u
-    k = sc.run.init_k
+    k = sc.run.init_k if sc.run.init == S.INIT_STRAIGHT else 0
+    stride = k + 2
     rng = np.random.default_rng(S.BASE_SEED + 17)
-    xyz = np.zeros((p.n_chains, 3, stride), dtype=np.float32)
+    xyz = np.zeros((hi - lo, 3, stride), dtype=np.float32)
+    c0 = 0
     fr = np.arange(1, k + 1) / (k + 1)
-    inner = src[None, None, :] + fr[None, :, None] * (e - src)[None, None, :] + \
-        sc.run.init_jitter * rng.normal(size=(p.n_chains, k, 3))
-    xyz[:, :, 0] = src
-    xyz[:, :, 1:k + 1] = inner.transpose(0, 2, 1)
-    xyz[:, :, k + 1] = e
-    n = np.full(p.n_chains, k + 2, dtype=np.int32)
+    for pr in sc.pairs:
+        a, b = max(c0, lo), min(c0 + pr.n_chains, hi)
+        c0 += pr.n_chains
+        if b <= a:
+            continue
+        src = np.asarray(sc.sources[pr.source].pos, float)
+        c = np.asarray(sc.sensors[pr.sensor].centre, float)
+        u = (src - c) / np.linalg.norm(src - c)
+        e = c + sc.sensors[pr.sensor].radius * u
+        m = b - a
+        inner = src[None, None, :] + fr[None, :, None] * (e - src)[None, None, :] + \
+            sc.run.init_jitter * rng.normal(size=(m, k, 3))
+        xyz[a - lo:b - lo, :, 0] = src
+        xyz[a - lo:b - lo, :, 1:k + 1] = inner.transpose(0, 2, 1)
+        xyz[a - lo:b - lo, :, k + 1] = e
+    n = np.full(hi - lo, k + 2, dtype=np.int32)
     return xyz, n
 
 
@@ -283,21 +334,48 @@ def reference_arm(args):
     return 0
 
 
-def rank_seed(seed: int, rank: int) -> int:
-    """Weak scaling: every rank runs its own replica of the workload, with its
-    own Philox key."""
-    return int(seed) + 1000 * int(rank)
-
-
 def max_over_ranks(ms: float, dist, device="cpu") -> float:
-    """The bench's step time is the slowest rank's (one all-reduce of a
-    scalar; the only collective of the run)."""
+    """The bench's step time is the slowest rank's."""
     if dist is None:
         return ms
     import torch
     t = torch.tensor([ms], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def lane_op_roofline(est, rate, n_sm, clk_mhz, pipes):
+    """Lane-op roofline of a proposal (FP32 + INT against 128 lanes/clk/SM,
+    MUFU against 16 lanes/clk/SM, each pipe's peak the larger of that unit
+    count and the microbenchmark's measured rate) at the measured move mix and
+    mean vertex count: achieved and peak lane-operations per second of the
+    binding pipe, and the FP32-only fraction of the delta evaluator's own
+    per-move counts beside it."""
+    prop = est["proposals"]
+    tot = sum(prop)
+    mix = {k: prop[i] / tot for i, k in enumerate(("interior", "end", "birth", "death"))}
+    nbar = est["mean_n"]
+    p_pert, p_b, p_d = mix["interior"] + mix["end"], mix["birth"], mix["death"]
+    fp32 = p_pert * LANE_OPS["perturb"][0] + p_b * (LANE_OPS["birth"][0] + nbar) + \
+        p_d * (LANE_OPS["death"][0] + nbar)
+    alu = fp32 + INT_PER_PROPOSAL
+    mufu = p_pert * LANE_OPS["perturb"][1] + p_b * LANE_OPS["birth"][1] + p_d * LANE_OPS["death"][1]
+    f = clk_mhz * 1e6
+    alu_peak = max(FP32_LANES_PER_SM * n_sm * f, pipes["fp32_per_s"])
+    mufu_peak = max(MUFU_LANES_PER_SM * n_sm * f, pipes["mufu_per_s"])
+    if mufu / mufu_peak >= alu / alu_peak:
+        pipe, work, peak = "MUFU", mufu, mufu_peak
+    else:
+        pipe, work, peak = "FP32+INT", alu, alu_peak
+    fp32_own = sum(mix[k] * FP32_PER_PROPOSAL[k] for k in mix)
+    fp32_peak = max(FP32_LANES_PER_SM * n_sm * f, pipes["fp32_per_s"])
+    return {"bound": "alu", "achieved": rate * work / 1e12, "peak": peak / 1e12, "unit": "T lane-ops/s",
+            "frac": rate * work / peak, "pipe": pipe,
+            "lane_ops_per_proposal": {"fp32": fp32, "int": INT_PER_PROPOSAL, "mufu": mufu, "mean_n": nbar},
+            "peak_source": f"{pipe}: lanes/clk/SM x {n_sm} SMs x {clk_mhz:.0f} MHz (median SM clock sampled during "
+                           f"the timed region), or the pipe microbenchmark's rate where higher",
+            "frac_fp32_only": rate * fp32_own / fp32_peak, "fp32_own_per_proposal": fp32_own,
+            "pipes_measured": pipes}
 
 
 def ours(args):
@@ -315,18 +393,26 @@ def ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    sc = scene_for(args)
-    sc.run.seed = rank_seed(sc.run.seed, rank)
+    sc = scene_for(args, world)
+    # the sharded form: each rank holds a contiguous window of the chain set,
+    # balanced by vertex cap; a chain keeps its global index, so its Philox
+    # stream is the one it has on a single GPU
+    lo, hi = api.shard_range(sc.pairs, rank, world)
     ctx = api.Context(local)
     medium = api.Medium(ctx, sc.medium)
     geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
     sc.run.layout = {"auto": 0, "warp": 1, "lane": 2}[args.layout]  # scenes.LAYOUT_*
     chains = api.Chains(ctx, medium, geom, sc.run, warps_per_block=args.warps_per_block,
-                        smem_window=args.smem_window)
+                        smem_window=args.smem_window, chain_window=(lo, hi))
     stream = torch.cuda.current_stream()
-    n_chains = sc.total_chains
-    props_per_step = n_chains * sc.run.n_steps
+    n_local = hi - lo
+    props_local = n_local * sc.run.n_steps
+    props_all = sc.total_chains * sc.run.n_steps
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def estimate():
+        # one sum all-reduce of the per-pair moments (NCCL) when sharded
+        return chains.read_estimator_sharded()[0][0] if dist else chains.read_estimator()[0]
 
     def one_step(ev=None):
         chains.reset()
@@ -335,11 +421,11 @@ def ours(args):
         chains.run_steps(sc.run.n_steps)
         if ev is not None:
             ev[1].record(stream)
-        return chains.read_estimator()[0]
+        return estimate()
 
     for _ in range(args.warmup):
         one_step()
-    pipes = api.measure_pipes(ctx, stream) if rank == 0 else None
+    pipes = measure_pipes(local, stream) if rank == 0 else None
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -364,23 +450,21 @@ def ours(args):
     clocks = clock.stop() if clock else None
     total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * props_per_step / (ms_per_step / 1e3)
+    value = props_all / (ms_per_step / 1e3)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: each step uploads
+    # this rank's initial paths from pinned memory, steps, and reads the estimate
     e2e = None
     if not args.no_e2e:
-        hx, hn = host_initial_paths(sc)
+        hx, hn = host_initial_paths(sc, lo, hi)
         px = torch.from_numpy(hx).pin_memory()
         pn = torch.from_numpy(hn).pin_memory()
         hx, hn = px.numpy(), pn.numpy()
-        import ctypes as C
-        from paper_1811_04156_gb300._lib import Estimate, check, load
-        out = (Estimate * 1)()
 
         def e2e_step():
             chains.set_states(hx, hn)
             chains.run_steps(sc.run.n_steps)
-            check(load().pmc_read_estimator(chains.handle, out, 1, C.c_void_p(stream.cuda_stream)), "read")
+            return estimate()
 
         e2e_step()
         torch.cuda.synchronize()
@@ -388,13 +472,17 @@ def ours(args):
         for _ in range(max(1, min(args.steps, 2))):
             flush.zero_()
             torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
             t0 = time.perf_counter()
             e2e_step()
             torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
-        e2e_s = sum(ts) / len(ts)
-        e2e = {"value": world * props_per_step / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": int(hx.nbytes + hn.nbytes), "d2h_bytes_per_step": int(C.sizeof(Estimate))}
+        e2e_s = max_over_ranks(sum(ts) / len(ts), dist, "cuda")
+        from paper_1811_04156_gb300._lib import PMC_MOMENT_WORDS
+        e2e = {"value": props_all / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(hx.nbytes + hn.nbytes),
+               "d2h_bytes_per_step": int(8 * PMC_MOMENT_WORDS * len(sc.pairs))}
 
     if rank != 0:
         if dist:
@@ -402,78 +490,59 @@ def ours(args):
         return 0
     peaks, peak_kind = load_peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    prop = est["proposals"]
-    tot = sum(prop)
-    mix = {k: prop[i] / tot for i, k in enumerate(("interior", "end", "birth", "death"))}
-    fp32 = sum(mix[k] * FP32_PER_PROPOSAL[k] for k in mix)
-    mufu = sum(mix[k] * MUFU_PER_PROPOSAL[k] for k in mix)
+    clk = (clocks or {}).get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     kern_s = statistics.mean(kern_ms) / 1e3
-    rate = props_per_step / kern_s
-    # lane-op roofline: the slower of the FP32 and the MUFU pipes
-    # each pipe's peak: the unit count, or the measured rate where that is
-    # higher (GB300 doubles the ex2 rate): no pipe can run above its peak
-    fp32_units = FP32_LANES_PER_SM * n_sm * sm_mhz * 1e6
-    mufu_units = MUFU_LANES_PER_SM * n_sm * sm_mhz * 1e6
-    fp32_peak = max(fp32_units, pipes["fp32_per_s"])
-    mufu_peak = max(mufu_units, pipes["mufu_per_s"])
-    if mufu / mufu_peak >= fp32 / fp32_peak:
-        bound_pipe, achieved, peak = "MUFU", rate * mufu / 1e12, mufu_peak / 1e12
-        peak_from = "unit count" if mufu_peak == mufu_units else "measured (above the unit count)"
-    else:
-        bound_pipe, achieved, peak = "FP32", rate * fp32 / 1e12, fp32_peak / 1e12
-        peak_from = "unit count" if fp32_peak == fp32_units else "measured (above the unit count)"
-    peak_measured = (pipes["mufu_per_s"] if bound_pipe == "MUFU" else pipes["fp32_per_s"]) / 1e12
-    clk = (clocks or {}).get("sm_mhz") or sm_mhz
+    rate = props_local / kern_s
     li = chains.launch_info()
-    # warp instructions per proposal depend on the kernel, the workload and the
-    # shared window, not on how many warps share a CTA
-    inst = WARP_INST_PER_PROPOSAL.get((sc.name, li[0]["general"], li[0]["smem_cap"])) if len(li) == 1 else None
+    kind = li[0]["general"] if len(li) == 1 else None
+    roof = lane_op_roofline(est, rate, n_sm, clk, pipes)
+    roof["kernel"] = "lane_chain_kernel" if kind in (4, 5) else "chain_kernel"
+    roof["kernel_ms"] = statistics.mean(kern_ms)
+    roof["clock_max_mhz"] = float(peaks.get("sm_max_mhz", 2070.0))
+    roof["peak_kind"] = peak_kind
+    # counters of the committed capture, only while the kernel source matches it
+    fresh = (kind == 4 and sc.name == "detector" and li[0]["smem_cap"] == 20 and
+             LANE_CAPTURE["source_sha256"] == lane_kernel_source_hash())
+    roof["traffic"] = LANE_CAPTURE["dram_bytes_per_launch"] * n_local / 65536.0 if fresh else None
+    roof["traffic_source"] = LANE_CAPTURE["capture"] if fresh else \
+        "null: no ncu capture of this kernel source and workload"
     issue = None
-    if inst is not None:
+    if fresh:
+        inst = LANE_CAPTURE["inst_per_proposal"]
         issue_peak = ISSUE_PER_CLK_PER_SM * n_sm * clk * 1e6
         issue = {"achieved": rate * inst, "peak": issue_peak, "unit": "warp instructions/s",
                  "frac": rate * inst / issue_peak, "inst_per_proposal": inst,
-                 "source": "instructions per proposal from the committed ncu capture of this kernel and workload; "
-                           "peak = 4 warp instructions/clk/SM x SMs x median SM clock under load"}
-    # DRAM traffic of one launch (dram__bytes_read + write) from the committed
-    # ncu captures, scaled by chains: warp layout 8.9 MB for 16,384 chains x
-    # 2,000 steps; lane layout (window 20) 48.4 MB for 65,536 chains x 20,000
-    # steps (44.7 MB read, 3.7 MB written; 37.3 MB at 2,000 steps: the traffic
-    # of a launch grows slowly with its steps, not in proportion)
-    kind = li[0]["general"] if len(li) == 1 else None
-    traffic, traffic_source = None, None
-    if sc.name == "detector" and kind == 0:
-        traffic = 8.9e6 * n_chains / 16384.0
-        traffic_source = "ncu, 16,384 chains x 2,000 steps, scaled by chains"
-    elif sc.name == "detector" and kind == 4 and li[0]["smem_cap"] == 20:
-        traffic = 48.4e6 * n_chains / 65536.0
-        traffic_source = ("ncu, 65,536 chains x 20,000 steps (37.3 MB at 2,000 steps; grows slowly with the "
-                          "launch's steps, so the 100,000-step launch's figure is somewhat higher)")
+                 "source": "warp instructions per proposal from the ncu capture of this kernel source; peak = 4 "
+                           "warp instructions/clk/SM x SMs x median SM clock under load"}
+    converged = bool(est.get("rhat") is not None and math.isfinite(est["rhat"]) and est["rhat"] < 1.2)
+    estimate_block = {k: est[k] for k in ("intensity", "std_err", "pi_direct", "rhat", "mean_n", "accept", "ess")}
+    estimate_block["converged"] = converged
+    estimate_block["note"] = ("R-hat on the path length below 1.2 (the paper's stopping rule)" if converged else
+                              "not converged: R-hat on the path length >= 1.2, so the chains have not forgotten "
+                              "their initial paths; intensity and std_err describe the run, not the target")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak" if len(sc.pairs) == 1 else "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT.get(sc.name, sc.name),
-                       "chains": n_chains, "steps_per_chain": sc.run.n_steps, "vertex_cap": sc.pairs[0].cap,
-                       "global_batch": n_chains * world, "parallelism": f"replicas x{world}",
+                       "chains": sc.total_chains, "steps_per_chain": sc.run.n_steps,
+                       "vertex_cap": max(p.cap for p in sc.pairs), "global_batch": sc.total_chains,
+                       "parallelism": f"sharded chain windows x{world}" if world > 1 else "1 GPU",
                        "l2": "flushed between steps (256 MB write)", "accumulators": "f64",
-                       "launch": chains.launch_info()},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_source,
-                         "pipe": bound_pipe,
-                         "peak_source": f"{bound_pipe}: max of the microbenchmark rate and lanes/clk/SM x "
-                                        f"{n_sm} SMs x sm_max_mhz ({peak_kind} clock {sm_mhz:.0f} MHz); "
-                                        f"taken: {peak_from}",
-                         "kernel": "lane_chain_kernel" if kind == 4 else "chain_kernel",
-                         "kernel_ms": statistics.mean(kern_ms),
-                         "fp32_per_proposal": fp32, "mufu_per_proposal": mufu,
-                         "peak_measured": peak_measured, "frac_of_measured": achieved / peak_measured,
-                         "pipes_measured": pipes},
-            "issue_roofline": issue,
-            "gpu_launches": 3 * args.steps,
-            "effective_samples_per_s": (est["ess"] / (ms_per_step / 1e3)) if est.get("ess") else None,
-            "estimate": {k: est[k] for k in ("intensity", "std_err", "pi_direct", "rhat", "mean_n", "accept", "ess")},
-            "clocks": clocks, "e2e": e2e}
+                       "launch": li},
+            "roofline": roof, "issue_roofline": issue,
+            "gpu_launches": (len(li) + 2) * args.steps,
+            "effective_samples_per_s": (est["ess"] / (ms_per_step / 1e3)) if (converged and est.get("ess"))
+            else None,
+            "estimate": estimate_block, "clocks": clocks, "e2e": e2e}
+    if world == 1 and not args.no_extras:
+        # reports beside the timed line: a failure here must not lose the line
+        for key, fn in (("other_configs", lambda: other_configs(api, ctx)),
+                        ("time_to_1pct", lambda: time_to_1pct(api, ctx, args))):
+            try:
+                line[key] = fn()
+            except Exception as exc:
+                line[key] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds, os.cpu_count() or 1)
@@ -485,50 +554,83 @@ def ours(args):
     return 0
 
 
-def time_to_target(args):
-    """Wall time until the intensity estimate reaches the target relative
-    standard error and lies within max(target, 3 SE) of a reference value from
-    a long forward-tracer run, for (a) plain RJMCMC (64 chains, Gaussian
-    steps), (b) batched MALA chains (65,536), with and without tracer seeds,
-    batched Gaussian chains with seeds, batched tree-move chains from the
-    direct path, and tree-move chains whose intensity comes from the optimal
-    bridge against the reference density instead of the direct sector, (c) the
-    GPU forward tracer.
-    Budgets double until the criterion holds or 120 s have passed."""
+def other_configs(api, ctx):
+    """Proposals/s of the other workloads, each a timed launch after a warm-up
+    launch of the same chain set (autotuned launch shapes): the batched uneven
+    pairs under one CUDA graph, the gradients workload (MALA moves and score
+    accumulation) and the layered string of sensors."""
     import torch
-    from paper_1811_04156_gb300 import build as B
-    B.build()
-    from paper_1811_04156_gb300 import api, scenes as S
-    tgt = args.time_to_target
-    geom_name = args.geometry
+    from paper_1811_04156_gb300 import scenes as S
+    out = {}
+    for name, sc in (("batched", S.batched(n_steps=5000)), ("gradients", S.gradients(n_steps=10_000)),
+                     ("layered", S.layered(n_steps=5000))):
+        medium = api.Medium(ctx, sc.medium)
+        geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+        ch = api.Chains(ctx, medium, geom, sc.run)
+        ch.run_steps(sc.run.n_steps)
+        ch.read_estimator()
+        ch.reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ch.run_steps(sc.run.n_steps)
+        e1.record()
+        est = ch.read_estimator()
+        ms = e0.elapsed_time(e1)
+        props = sc.total_chains * sc.run.n_steps
+        out[name] = {"workload": WORKLOAD_TEXT[name], "chains": sc.total_chains, "steps_per_chain": sc.run.n_steps,
+                     "proposals_per_s": props / (ms / 1e3), "ms": ms, "launch": ch.launch_info(),
+                     "mean_n": sum(e["mean_n"] * e["n_samples"] for e in est) / max(sum(e["n_samples"] for e in est),
+                                                                                     1.0)}
+        if name == "gradients":
+            g, gse = ch.grad_estimator()
+            out[name]["d_intensity_d_theta"] = {"theta": "lambda_s, lambda_a, g", "value": g[0].tolist(),
+                                                "se": gse[0].tolist()}
+        ch.close()
+    return out
+
+
+def ttt_geometry(api, ctx, geom_name, tgt, methods=None, limit=120.0, ref=None, ref_photons=None):
+    """Wall time until the intensity estimate reaches relative standard error
+    `tgt` and lies within max(tgt, 3 combined SE) of a reference value from a
+    long forward-tracer run (the criterion of the method's time-to-error
+    comparison), for each method on the plain (D = 1 m) or detector (D = 50 m)
+    geometry: plain RJMCMC (64 chains, Gaussian steps); batched MALA chains
+    (65,536; from the direct path, or from tracer seeds as the paper seeds
+    its chains, seeding inside the timed region); batched Gaussian chains with
+    seeds; batched tree-move chains; tree-move chains whose intensity comes
+    from the optimal bridge against the reference density; the GPU forward
+    tracer.  Budgets double until the criterion holds or `limit` seconds
+    have passed."""
+    import torch
+    from paper_1811_04156_gb300 import scenes as S
     sc_plain = S.plain() if geom_name == "plain" else S.detector(n_chains=64)
-    ctx = api.Context(0)
     med = api.Medium(ctx, sc_plain.medium)
     cap = sc_plain.pairs[0].cap
-    # reference value from a long tracer run
     g1 = api.Geometry(ctx, sc_plain.sources, sc_plain.sensors, [S.Pair(0, 0, 1, cap)])
-    ref_photons = 4_000_000_000 if geom_name == "plain" else 100_000_000_000
+    if ref_photons is None:
+        ref_photons = 4_000_000_000 if geom_name == "plain" else 16_000_000_000
     t0 = time.perf_counter()
-    if args.ttt_ref:
-        I_ref, se_ref, N = (float(x) for x in args.ttt_ref.split(","))
+    if ref is not None:
+        I_ref, se_ref, N = ref
     else:
         parts = []
         left = ref_photons
         while left > 0:
-            k = min(left, 20_000_000_000)
+            k = min(left, 4_000_000_000)
             parts.append(api.trace(ctx, med, g1, 0, 123457, k, photon0=ref_photons - left, max_scatter=cap - 2))
             left -= k
         N = sum(p["photons"] for p in parts)
-        I_ref = sum(p["I"] * p["photons"] for p in parts) / N
+        I_ref = sum(p["sum_w"] for p in parts) / N
         se_ref = math.sqrt(sum((p["se"] * p["photons"]) ** 2 for p in parts)) / N
-    ref_s = time.perf_counter() - t0
-    out = {"target_rel_err": tgt, "geometry": geom_name, "reference": {"intensity": I_ref, "std_err": se_ref,
-                                                                     "photons": N, "seconds": ref_s}}
+    out = {"target_rel_err": tgt, "geometry": geom_name, "limit_s": limit,
+           "reference": {"intensity": I_ref, "std_err": se_ref, "photons": N, "seconds": time.perf_counter() - t0,
+                         "how": "GPU forward tracer (Algorithm 1), cap-truncated"}}
 
     def ok(I, se):
         return I > 0 and se / I <= tgt and abs(I - I_ref) <= max(tgt * I_ref, 3 * math.hypot(se, se_ref))
 
-    def run_chains(n_chains, within, increment, seeded=False):
+    def run_chains(n_chains, within, increment, seeded=False, seed_rounds=64, seed_photons=1 << 26):
         sc = S.plain(n_chains=n_chains) if geom_name == "plain" else S.detector(n_chains=n_chains)
         sc.run.within = within
         sc.run.burn_in = 0 if seeded else (1000 if geom_name == "plain" else 10_000)
@@ -540,38 +642,26 @@ def time_to_target(args):
         ch = api.Chains(ctx, med, geom, sc.run)
         torch.cuda.synchronize()
         t = time.perf_counter()
+        seed_s = 0.0
         if seeded:
             # equilibrium seeds from the forward tracer (inside the timed region)
-            api.seed_from_tracer(ch, seed=4321, photons_per_round=1 << 26)
+            api.seed_from_tracer(ch, seed=4321, photons_per_round=seed_photons, max_rounds=seed_rounds)
+            seed_s = time.perf_counter() - t
         steps = 0
-        e = None
-        while time.perf_counter() - t < 120.0:
+        while True:
             ch.run_steps(increment)
             steps += increment
             e = ch.read_estimator()[0]
             if steps > sc.run.burn_in and e["n_samples"] > 0 and ok(e["intensity"], e["std_err"]):
                 break
+            if time.perf_counter() - t > limit:
+                break
             increment = min(increment * 2, 1_000_000)
         dt = time.perf_counter() - t
-        return {"seconds": dt, "steps_per_chain": steps, "chains": n_chains, "intensity": e["intensity"],
-                "std_err": e["std_err"], "reached": bool(ok(e["intensity"], e["std_err"])),
-                "launch": ch.launch_info()}
-
-    wanted = set(args.ttt_methods.split(",")) if args.ttt_methods else None
-
-    def want(name):
-        return wanted is None or name in wanted
-
-    if want("plain_rjmcmc"):
-        out["plain_rjmcmc"] = run_chains(64, S.WITHIN_PERTURB, 20_000)
-    if want("batched_mala"):
-        out["batched_mala"] = run_chains(65_536, S.WITHIN_MALA, 2_000)
-    if want("batched_mala_tracer_seeded"):
-        out["batched_mala_tracer_seeded"] = run_chains(65_536, S.WITHIN_MALA, 500, seeded=True)
-    if want("batched_perturb_tracer_seeded"):
-        out["batched_perturb_tracer_seeded"] = run_chains(65_536, S.WITHIN_PERTURB, 500, seeded=True)
-    if want("batched_tree_moves"):
-        out["batched_tree_moves"] = run_chains(65_536, S.WITHIN_TREE, 2_000)
+        ch.close()
+        return {"seconds": dt, "seed_seconds": seed_s, "steps_per_chain": steps, "chains": n_chains,
+                "intensity": e["intensity"], "std_err": e["std_err"], "rhat": e["rhat"],
+                "reached": bool(ok(e["intensity"], e["std_err"]))}
 
     def run_tree_bridge(n_chains, burn, thin, n_draws, rows0):
         """Tree-move chains and the optimal bridge against the normalised
@@ -593,7 +683,7 @@ def time_to_target(args):
                 ch.bridge_observe_log(0, n_draws, len(rows) * n_draws, 4242, row)
                 rows.append(row)
             ob = api.bridge_ratio(ctx, torch.stack(rows), n_draws, n_chains, groups=32)
-            if ok(ob["r"], ob["se"]) or time.perf_counter() - t > 120.0:
+            if ok(ob["r"], ob["se"]) or time.perf_counter() - t > limit:
                 break
             target *= 2
         dt = time.perf_counter() - t
@@ -602,26 +692,69 @@ def time_to_target(args):
                 "draws_per_row": n_draws, "intensity": ob["r"], "std_err": ob["se"],
                 "geometric": ob["geometric"], "reached": bool(ok(ob["r"], ob["se"]))}
 
+    def want(name):
+        return methods is None or name in methods
+
+    if want("plain_rjmcmc"):
+        out["plain_rjmcmc"] = run_chains(64, S.WITHIN_PERTURB, 20_000)
+    if want("batched_mala"):
+        out["batched_mala"] = run_chains(65_536, S.WITHIN_MALA, 2_000)
+    # seeds cost tracer photons: 1 / I of them per seed (I ~ 2e-3 at 1 m, ~2e-6 at 50 m), so the
+    # detector geometry seeds 8,192 chains (about 4e9 photons) and lets each run longer
+    n_seeded = 65_536 if geom_name == "plain" else 8_192
+    seed_kw = {} if geom_name == "plain" else {"seed_rounds": 32, "seed_photons": 1 << 28}
+    if want("batched_mala_tracer_seeded"):
+        out["batched_mala_tracer_seeded"] = run_chains(n_seeded, S.WITHIN_MALA, 500, seeded=True, **seed_kw)
+    if want("batched_perturb_tracer_seeded"):
+        out["batched_perturb_tracer_seeded"] = run_chains(n_seeded, S.WITHIN_PERTURB, 500, seeded=True, **seed_kw)
+    if want("batched_tree_moves"):
+        out["batched_tree_moves"] = run_chains(65_536, S.WITHIN_TREE, 2_000)
     if want("tree_moves_optimal_bridge"):
         out["tree_moves_optimal_bridge"] = run_tree_bridge(65_536, 10_000 if geom_name == "plain" else 40_000,
                                                            500, 65_536, 8)
-    if not want("gpu_tracer"):
-        print(json.dumps(out), flush=True)
-        return 0
-    # tracer with doubling photon budgets
-    t = time.perf_counter()
-    photons, acc = 1_000_000, []
-    while True:
-        acc.append(api.trace(ctx, med, g1, 0, 99, photons, photon0=sum(a["photons"] for a in acc),
-                             max_scatter=cap - 2))
-        Nn = sum(a["photons"] for a in acc)
-        I = sum(a["I"] * a["photons"] for a in acc) / Nn
-        se = math.sqrt(sum((a["se"] * a["photons"]) ** 2 for a in acc)) / Nn
-        if ok(I, se) or time.perf_counter() - t > 120.0:
-            break
-        photons *= 2
-    out["gpu_tracer"] = {"seconds": time.perf_counter() - t, "photons": Nn, "intensity": I, "std_err": se,
-                         "reached": bool(ok(I, se))}
+    if want("gpu_tracer"):
+        t = time.perf_counter()
+        photons, acc = 1_000_000, []
+        while True:
+            acc.append(api.trace(ctx, med, g1, 0, 99, photons, photon0=sum(a["photons"] for a in acc),
+                                 max_scatter=cap - 2))
+            Nn = sum(a["photons"] for a in acc)
+            I = sum(a["sum_w"] for a in acc) / Nn
+            se = math.sqrt(sum((a["se"] * a["photons"]) ** 2 for a in acc)) / Nn
+            if ok(I, se) or time.perf_counter() - t > limit:
+                break
+            photons *= 2
+        out["gpu_tracer"] = {"seconds": time.perf_counter() - t, "photons": Nn, "intensity": I, "std_err": se,
+                             "reached": bool(ok(I, se))}
+    reached = {k: v["seconds"] for k, v in out.items() if isinstance(v, dict) and v.get("reached")}
+    out["fastest"] = min(reached, key=reached.get) if reached else None
+    if "plain_rjmcmc" in out and "batched_mala_tracer_seeded" in out:
+        pl, bm = out["plain_rjmcmc"], out["batched_mala_tracer_seeded"]
+        out["batched_gradient_beats_plain"] = bool(bm["reached"] and (not pl["reached"] or
+                                                                      bm["seconds"] < pl["seconds"]))
+    return out
+
+
+def time_to_1pct(api, ctx, args):
+    """The metric's second half on both geometries, in the bench process."""
+    plain = ttt_geometry(api, ctx, "plain", 0.01, ["plain_rjmcmc", "batched_mala_tracer_seeded", "gpu_tracer"],
+                         limit=args.ttt_limit)
+    det = ttt_geometry(api, ctx, "detector", 0.01, ["plain_rjmcmc", "batched_mala_tracer_seeded",
+                                                     "tree_moves_optimal_bridge", "gpu_tracer"],
+                       limit=args.ttt_limit)
+    return {"plain_geometry": plain, "detector_geometry": det}
+
+
+def time_to_target(args):
+    """--time-to-target: every method on one geometry (--geometry), printed."""
+    from paper_1811_04156_gb300 import build as B
+    B.build()
+    from paper_1811_04156_gb300 import api
+    ctx = api.Context(0)
+    ref = tuple(float(x) for x in args.ttt_ref.split(",")) if args.ttt_ref else None
+    methods = set(args.ttt_methods.split(",")) if args.ttt_methods else None
+    out = ttt_geometry(api, ctx, args.geometry, args.time_to_target, methods, limit=args.ttt_limit, ref=ref,
+                       ref_photons=4_000_000_000 if args.geometry == "plain" else 100_000_000_000)
     print(json.dumps(out), flush=True)
     return 0
 

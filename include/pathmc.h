@@ -194,6 +194,13 @@ typedef struct {
                                       choice) in shared memory; the same Markov chain and random
                                       numbers as the warp layout.  Fails with PMC_ERR_INVALID for
                                       runs that are not lean */
+  int64_t chain_lo, chain_hi;      /* chain window: this chain set holds the geometry's chains
+                                      [chain_lo, chain_hi) in pair order (chains of pair p are numbered
+                                      after those of pairs 0..p-1); 0, 0 = all.  A chain keeps its
+                                      global index in its Philox counters and initial path, so the
+                                      chains of a window evolve exactly as in the whole set (the
+                                      sharded form over several GPUs, pmc_shard_range).  USER init
+                                      data and pmc_set_states then cover the window's chains */
 } pmc_run_desc;
 
 /* Per-pair estimate returned by pmc_read_estimator. */
@@ -275,6 +282,61 @@ PMC_API int pmc_run_steps(pmc_chains_t chains, uint64_t n_steps, void* stream);
  * pi(n=2) the chains' fraction of states with n = 2; the standard error comes
  * from the across-chain variance. */
 PMC_API int pmc_read_estimator(pmc_chains_t chains, pmc_estimate* out, size_t n_pairs, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Sharded chain sets (several GPUs; section "Implementation": chains are  */
+/* independent)                                                           */
+/* ---------------------------------------------------------------------- */
+
+/* Per-pair moments of the chain accumulators: PMC_MOMENT_WORDS doubles per
+ * pair, each a sum over the pair's chains, so the moments of a chain set
+ * split over ranks (pmc_run_desc.chain_lo/hi) add up, by one sum all-reduce,
+ * to those of the whole set.  Layout (N = recorded states of a chain, n2 its
+ * recorded states with n = 2, A_k its summed score of parameter k: A_0 =
+ * sum_L / lambda_s^2 - (sum_n - 2 N) / lambda_s, A_1 = sum_L / lambda_a^2,
+ * A_2 = sum_G; lambda = 1 for layered media): [0] chains; [1..16] the
+ * PMC_ACC_WORDS accumulator words summed; [17..20] sum of the per-chain mean
+ * path length, of its square, of the per-chain variance of the path length
+ * and the count of chains with N > 1; [21..23] sum n2^2, N n2, N^2;
+ * [24..26] sum A_k^2; [27..29] sum N A_k; [30..32] sum n2 A_k; [33..35]
+ * sum A_k; the rest 0. */
+#define PMC_MOMENT_WORDS 40
+
+/* The sharded form's partition: the contiguous chain window [*chain_lo,
+ * *chain_hi) of rank `rank` among `world` ranks over the chains of `pairs`
+ * (pair order, as in pmc_geometry_desc), balanced by vertex cap x steps (a
+ * chain costs its pair's cap; every chain runs the same steps).  Every chain
+ * belongs to exactly one rank and every rank gets at least one.  Host only.
+ * Errors: PMC_ERR_INVALID for rank outside [0, world), bad pairs or fewer
+ * chains than ranks. */
+PMC_API int pmc_shard_range(const pmc_pair* pairs, int n_pairs, int rank, int world, int64_t* chain_lo,
+                            int64_t* chain_hi);
+
+/* This chain set's per-pair moments into `out` (host, caller-owned,
+ * n_pairs * PMC_MOMENT_WORDS doubles).  Synchronises `stream`; reports
+ * PMC_ERR_ABORTED / PMC_ERR_DEVICE_STATUS as pmc_read_estimator does. */
+PMC_API int pmc_read_moments(pmc_chains_t chains, double* out, size_t len, void* stream);
+
+/* Direct-sector integral Z2 of every pair (host out, n_pairs doubles).
+ * Synchronises `stream`. */
+PMC_API int pmc_pair_z2(pmc_chains_t chains, double* z2, size_t n_pairs, void* stream);
+
+/* Per-pair estimates from moments (host only; the reduction of
+ * pmc_read_estimator, which is this function applied to the chain set's own
+ * moments): intensity = Z2 / pi(n = 2) with the across-chain standard error,
+ * R-hat, acceptance, means, ESS (pmc_estimate fields; bridge fields NaN) and,
+ * when grad / grad_se are not NULL (3 doubles per pair each, homogeneous
+ * media), intensity * E_p[score] with its delta-method standard error.
+ * moments: n_pairs * PMC_MOMENT_WORDS; z2: n_pairs. */
+PMC_API int pmc_estimate_from_moments(const double* moments, size_t n_pairs, const double* z2, pmc_estimate* out,
+                                      double* grad, double* grad_se);
+
+/* Host moments of stand-in accumulators: acc [n_chains][PMC_ACC_WORDS] (the
+ * pmc_read_accumulators layout), chain_pair [n_chains] pair of each chain;
+ * moments (n_pairs * PMC_MOMENT_WORDS) are overwritten.  The same per-chain
+ * terms as the device reduction. */
+PMC_API int pmc_moments_from_accumulators(const double* acc, size_t n_chains, const int* chain_pair, size_t n_pairs,
+                                          double lambda_s, double lambda_a, double* moments);
 
 /* d intensity / d theta per pair: intensity * E_p[d log p / d theta], the
  * score-function gradient (dI/dtheta = I E_p[d log p/d theta]).
@@ -489,25 +551,34 @@ PMC_API int pmc_length_hist(pmc_chains_t chains, double l_lo, double l_hi, int n
 /* Comparison baseline                                                    */
 /* ---------------------------------------------------------------------- */
 
-/* Forward ray tracer (appendix, Algorithm 1) for pair `pair`: n_photons
- * photons numbered from photon0, free paths from b(x), absorption weights
- * from a(x), hits tallied at the first sensor intersection, rejection beyond
- * r_reject from the sensor centre, at most max_scatter scatterings.
- * out (host, 5 doubles): sum of detected weights w*rho, sum of squared
- * weights, detected photons, emitted photons, sum of w*rho*path length.
+/* Result of a forward-tracer run: the estimate of the detected intensity per
+ * emitted photon, computed in the library from the run's sums. */
+typedef struct {
+  double intensity;                /* sum_w / emitted */
+  double std_err;                  /* sqrt((sum_w2 / emitted - intensity^2) / emitted) */
+  double mean_length;              /* sum_wl / sum_w: weight-averaged path length (NaN without detections) */
+  double detected, emitted;        /* photon counts */
+  double sum_w, sum_w2, sum_wl;    /* over detected photons: w rho, (w rho)^2, w rho x path length */
+} pmc_trace_result;
+
+/* Forward ray tracer (appendix, "Ray tracer", Algorithm 1) for pair `pair`:
+ * n_photons photons numbered from photon0, free paths from b(x), absorption
+ * weights from a(x), hits tallied at the first sensor intersection,
+ * rejection of a photon that starts a flight beyond r_reject from the sensor
+ * centre, at most max_scatter scatterings.  out: host, caller-owned.
  * Synchronises `stream`. */
 PMC_API int pmc_trace(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair,
               uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject,
-              int max_scatter, double* out, void* stream);
+              int max_scatter, pmc_trace_result* out, void* stream);
 
 /* pmc_trace that also bins each detected photon's weight w*rho by its path
  * length L: hist (host, caller-owned, n_bins doubles) receives the summed
- * weight of bin floor((L - l_lo) / (l_hi - l_lo) * n_bins), L in [l_lo, l_hi)
- * (section "Comparison of timing distributions", the ray tracer's side).
- * out as for pmc_trace.  Synchronises `stream`. */
+ * weight of bin floor((L - l_lo) / (l_hi - l_lo) * n_bins), L in [l_lo, l_hi),
+ * per emitted photon (section "Comparison of timing distributions", the ray
+ * tracer's side).  out as for pmc_trace.  Synchronises `stream`. */
 PMC_API int pmc_trace_lengths(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, int pair, uint64_t seed,
                               uint64_t photon0, uint64_t n_photons, double r_reject, int max_scatter, double l_lo,
-                              double l_hi, int n_bins, double* out, double* hist, void* stream);
+                              double l_hi, int n_bins, pmc_trace_result* out, double* hist, void* stream);
 
 /* Allocation-free forward tracer for callers that cannot allocate device
  * memory (an application whose own pool allocator has reserved the device, a
@@ -515,15 +586,16 @@ PMC_API int pmc_trace_lengths(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geo
  * synchronisation of cudaMalloc / cudaFree).  The paper has no counterpart:
  * it computes what pmc_trace computes, for each of the n_pairs pairs listed
  * in pair_ids (host array), with every pair traced from photon0 with the same
- * seed, and writes 5 doubles per pair to `out` (host, n_pairs * 5, layout of
- * pmc_trace).  Its accumulators live in a fixed device array of
+ * seed, and writes one pmc_trace_result per pair to `out` (host, n_pairs
+ * entries).  Its accumulators live in a fixed device array of
  * PMC_NOALLOC_MAX_PAIRS * 5 doubles that every GPU loading the library holds
  * until the process exits; the call performs no device allocation.
  *  - n_pairs must be in [1, PMC_NOALLOC_MAX_PAIRS]; larger values fail with
  *    PMC_ERR_INVALID.
  *  - The first call on a device looks up the array's device address (once per
  *    device, with that device current); make that first call before any
- *    stream capture.
+ *    stream capture.  The address is kept for the life of the process: a
+ *    cudaDeviceReset on that device after the first call is not supported.
  *  - All calls on a device share the array: calls whose work overlaps on the
  *    GPU (other streams or other host threads) race and corrupt each other's
  *    results.  Each call clears the slots it uses before tracing.
@@ -531,7 +603,7 @@ PMC_API int pmc_trace_lengths(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geo
 #define PMC_NOALLOC_MAX_PAIRS 128
 PMC_API int pmc_trace_noalloc(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom, const int* pair_ids,
                               int n_pairs, uint64_t seed, uint64_t photon0, uint64_t n_photons,
-                              double r_reject, int max_scatter, double* out, void* stream);
+                              double r_reject, int max_scatter, pmc_trace_result* out, void* stream);
 
 /* Equilibrium seeds for chains (paper: chains are seeded from ray-traced
  * paths, section "Implementation"): traces n_photons photons as pmc_trace
@@ -547,19 +619,33 @@ PMC_API int pmc_trace_paths(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom,
                             uint64_t photon0, uint64_t n_photons, double r_reject, int max_scatter, int max_paths,
                             float* out_xyz, int* out_n, int stride, uint64_t* n_accepted, void* stream);
 
-/* ---------------------------------------------------------------------- */
-/* Measurement                                                            */
-/* ---------------------------------------------------------------------- */
+/* Equilibrium seeds for every chain of the set (the paper seeds its chains
+ * with ray-traced paths, section "Implementation"): for each pair p, photons
+ * 0, 1, 2, ... of the pair's tracer (pmc_trace_paths' thinning, Philox key
+ * seed + p, at most cap - 2 scatterings) are traced in rounds until at least
+ * as many photons were kept as the pair has chains, and chain i of the pair
+ * takes the path of the i-th kept photon in photon order (pmc_seed_select):
+ * the first kept photons of a sequential tracer, i.e. independent exact draws
+ * from the normalised cap-truncated path density, whatever order the GPU
+ * finds them in.  Rounds trace photons_per_round photons each, at most
+ * max_rounds of them; a round that keeps more photons than its index buffer
+ * (twice the largest pair's chains, at least 4,096) is traced again with
+ * half the photons (and later rounds keep the smaller size).  When max_rounds
+ * rounds keep fewer photons than chains, the kept paths are reused
+ * cyclically (chains that share a seed then differ only by their random
+ * numbers until they decorrelate).  Step
+ * counters, accumulators and status words restart at zero.  photons_used
+ * (host, n_pairs entries, may be NULL) receives the photons traced per pair.
+ * Errors: PMC_ERR_INVALID when photons_per_round == 0, max_rounds < 1,
+ * r_reject <= 0 or a pair keeps no photon at all.  Synchronises `stream`. */
+PMC_API int pmc_seed_from_tracer(pmc_chains_t chains, uint64_t seed, uint64_t photons_per_round, int max_rounds,
+                                 double r_reject, uint64_t* photons_used, void* stream);
 
-/* Pipe rates of the context's device, measured by two microbenchmark kernels
- * (8 independent dependency chains per thread, 8 CTAs of 256 threads per SM,
- * one untimed and one timed launch each, CUDA events on `stream`):
- * out[0] = FP32 fused multiply-add lane-operations per second, out[1] = MUFU
- * (special-function unit: ex2, lg2) lane-operations per second.  These are the
- * denominators of the chain kernel's lane-op roofline; the paper has no
- * counterpart.  out: host, 2 doubles, caller-owned.  Allocates and frees a
- * 1.2 MB device buffer per call.  Synchronises `stream`. */
-PMC_API int pmc_measure_pipes(pmc_ctx_t ctx, double* out, void* stream);
+/* The seed selection of pmc_seed_from_tracer (host only): out[i] = the
+ * (i mod count)-th smallest of the count photon indices photon_idx (the
+ * accepted photons of a traced range, in any order), i < need.  Errors:
+ * PMC_ERR_INVALID for NULL pointers or count == 0 with need > 0. */
+PMC_API int pmc_seed_select(const uint64_t* photon_idx, size_t count, size_t need, uint64_t* out);
 
 /* Message of the last failure on the calling thread ("" if none). */
 PMC_API const char* pmc_last_error(void);

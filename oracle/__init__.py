@@ -138,6 +138,8 @@ def lib():
             L.or_hmc_leapfrog.restype = C.c_double
             L.or_run_chains_hist.argtypes = [M, S, D, R, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint64,
                                              _dp, _ip, C.POINTER(Acc), _dp, _dp, C.c_int]
+            L.or_run_chains_diag.argtypes = [M, S, D, R, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint64,
+                                             _dp, _ip, C.POINTER(Acc), _dp, _dp, _dp, C.c_int]
             _lib = L
     return _lib
 
@@ -506,16 +508,20 @@ class Chains:
             if rc != 0:
                 raise ValueError("oracle init failed")
 
-    def run(self, n_steps, threads=None, margins=False, n_hist=None):
-        """Advance every chain; n_hist (n_chains x (cap+1) float64) collects recorded dwell per n."""
-        mm = np.full(self.n_chains, np.inf) if margins else None
-        lib().or_run_chains_hist(C.byref(self.m), C.byref(self.s), C.byref(self.d), C.byref(self.r),
+    def run(self, n_steps, threads=None, margins=False, n_hist=None, hmc_seg=False):
+        """Advance every chain; n_hist (n_chains x (cap+1) float64) collects recorded dwell per n.
+        margins=True returns each chain's smallest |log A - log u|; hmc_seg=True also
+        the shortest segment met at any leapfrog position of its HMC moves
+        (then the return value is the pair (margins, shortest segments))."""
+        mm = np.full(self.n_chains, np.inf) if (margins or hmc_seg) else None
+        hs = np.full(self.n_chains, np.inf) if hmc_seg else None
+        lib().or_run_chains_diag(C.byref(self.m), C.byref(self.s), C.byref(self.d), C.byref(self.r),
                                  self.n_chains, self.cap, self.chain_offset, self.step, int(n_steps),
                                  _ptr(self.xyz), self.n.ctypes.data_as(_ip), self.acc,
-                                 _ptr(mm) if margins else None, _ptr(n_hist) if n_hist is not None else None,
-                                 threads or os.cpu_count() or 1)
+                                 _ptr(mm) if mm is not None else None, _ptr(n_hist) if n_hist is not None else None,
+                                 _ptr(hs) if hs is not None else None, threads or os.cpu_count() or 1)
         self.step += int(n_steps)
-        return mm
+        return (mm, hs) if hmc_seg else mm
 
     def logp(self, c):
         return logp(self.m, self.s, self.d, self.xyz[c, : self.n[c]])

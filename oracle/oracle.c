@@ -746,6 +746,7 @@ typedef struct {
   or_acc* acc;
   double* min_margin;
   double* n_hist;
+  double* min_hmc_seg;
   int c_begin, c_end;
   double kappa_eq;
   uint32_t thr_within, thr_birth;
@@ -838,6 +839,18 @@ static double target_logp(const chain_job* J, int n, const double* f) {
   return lp;
 }
 
+/* Length of the shortest segment of an n-vertex path (a diagnostic of
+ * leapfrog stiffness: the curvature of log p grows like 1 / length^2). */
+static double shortest_segment(int n, const double* f) {
+  double lo = INFINITY;
+  for (int k = 0; k + 1 < n; ++k) {
+    double r[3];
+    sub3(f + 3 * (k + 1), f + 3 * k, r);
+    lo = fmin(lo, norm3(r));
+  }
+  return lo;
+}
+
 static void* chain_worker(void* arg) {
   chain_job* J = (chain_job*)arg;
   const or_medium* m = J->m;
@@ -854,6 +867,7 @@ static void* chain_worker(void* arg) {
     or_acc* a = J->acc ? &J->acc[c] : NULL;
     double lpx = target_logp(J, n, x);
     double margin = INFINITY;
+    double hmc_seg = INFINITY;
     for (uint64_t t = J->step0; t < J->step0 + J->n_steps; ++t) {
       uint32_t A[4], B[4];
       draw_block(r->seed, (uint32_t)t, (uint32_t)(t >> 32), chain, PURPOSE_STEP_A, A);
@@ -923,12 +937,14 @@ static void* chain_worker(void* arg) {
           k0 += dot3(pm + 3 * i, pm + 3 * i);
         }
         memcpy(y, x, sizeof(double) * 3 * n);
+        if (J->min_hmc_seg) hmc_seg = fmin(hmc_seg, shortest_segment(n, y));
         or_grad_logp(m, J->s, J->d, n, y, gy);
         for (int i = 1; i <= n - 2; ++i)
           for (int q = 0; q < 3; ++q) pm[3 * i + q] += 0.5 * eps * gy[3 * i + q];
         for (int st = 1; st <= L; ++st) {
           for (int i = 1; i <= n - 2; ++i)
             for (int q = 0; q < 3; ++q) y[3 * i + q] += eps * pm[3 * i + q];
+          if (J->min_hmc_seg) hmc_seg = fmin(hmc_seg, shortest_segment(n, y));
           or_grad_logp(m, J->s, J->d, n, y, gy);
           double h = (st == L) ? 0.5 * eps : eps;
           for (int i = 1; i <= n - 2; ++i)
@@ -1066,6 +1082,7 @@ static void* chain_worker(void* arg) {
     }
     J->n[c] = n;
     if (J->min_margin) J->min_margin[c] = margin;
+    if (J->min_hmc_seg) J->min_hmc_seg[c] = hmc_seg;
   }
   free(y);
   free(tbs);
@@ -1086,6 +1103,14 @@ int or_run_chains_hist(const or_medium* m, const or_source* s, const or_sensor* 
                        const or_run* r, int n_chains, int cap, uint32_t chain_offset,
                        uint64_t step0, uint64_t n_steps, double* xyz, int* n,
                        or_acc* acc, double* min_margin, double* n_hist, int n_threads) {
+  return or_run_chains_diag(m, s, d, r, n_chains, cap, chain_offset, step0, n_steps, xyz, n, acc, min_margin,
+                            n_hist, NULL, n_threads);
+}
+
+int or_run_chains_diag(const or_medium* m, const or_source* s, const or_sensor* d,
+                       const or_run* r, int n_chains, int cap, uint32_t chain_offset,
+                       uint64_t step0, uint64_t n_steps, double* xyz, int* n,
+                       or_acc* acc, double* min_margin, double* n_hist, double* min_hmc_seg, int n_threads) {
   if (n_threads < 1) n_threads = 1;
   if (n_threads > n_chains) n_threads = n_chains > 0 ? n_chains : 1;
   double keq = or_kappa_eq(m->g);
@@ -1097,7 +1122,7 @@ int or_run_chains_hist(const or_medium* m, const or_source* s, const or_sensor* 
     chain_job* J = &jobs[i];
     J->m = m; J->s = s; J->d = d; J->r = r; J->cap = cap; J->chain_offset = chain_offset;
     J->step0 = step0; J->n_steps = n_steps; J->xyz = xyz; J->n = n; J->acc = acc;
-    J->min_margin = min_margin; J->n_hist = n_hist; J->kappa_eq = keq; J->thr_within = thr_w; J->thr_birth = thr_b;
+    J->min_margin = min_margin; J->n_hist = n_hist; J->min_hmc_seg = min_hmc_seg; J->kappa_eq = keq; J->thr_within = thr_w; J->thr_birth = thr_b;
     or_tree_vref(s, d, J->v_ref);
     J->coords = (double*)calloc((size_t)3 * (size_t)(cap + 1), sizeof(double));
     J->c_begin = (int)((long)n_chains * i / n_threads);

@@ -140,6 +140,13 @@ int or_run_chains_hist(const or_medium* m, const or_source* s, const or_sensor* 
                        const or_run* r, int n_chains, int cap, uint32_t chain_offset,
                        uint64_t step0, uint64_t n_steps, double* xyz, int* n,
                        or_acc* acc, double* min_margin, double* n_hist, int n_threads);
+/* Same, and stores in min_hmc_seg[chain] (may be NULL) the shortest segment
+ * length met at any leapfrog position of the chain's HMC moves (infinity
+ * without HMC moves). */
+int or_run_chains_diag(const or_medium* m, const or_source* s, const or_sensor* d,
+                       const or_run* r, int n_chains, int cap, uint32_t chain_offset,
+                       uint64_t step0, uint64_t n_steps, double* xyz, int* n,
+                       or_acc* acc, double* min_margin, double* n_hist, double* min_hmc_seg, int n_threads);
 
 /* ---- normalisation and reference density ---- */
 double or_z2(const or_medium* m, const or_source* s, const or_sensor* d, int n_v, int n_phi);

@@ -19,6 +19,7 @@ PMC_FLAG_GRADIENTS = 1
 PMC_FLAG_NO_GRAPH = 2
 PMC_LAYOUT_AUTO, PMC_LAYOUT_WARP, PMC_LAYOUT_LANE = 0, 1, 2
 PMC_ACC_WORDS = 16
+PMC_MOMENT_WORDS = 40
 PMC_NOALLOC_MAX_PAIRS = 128
 
 
@@ -63,7 +64,7 @@ class RunDesc(C.Structure):
                 ("init_jitter", C.c_double), ("init_xyz", C.POINTER(C.c_float)),
                 ("init_n", C.POINTER(C.c_int)), ("init_stride", C.c_int), ("flags", C.c_int),
                 ("warps_per_block", C.c_int), ("smem_window", C.c_int), ("hmc_steps", C.c_int),
-                ("layout", C.c_int)]
+                ("layout", C.c_int), ("chain_lo", C.c_int64), ("chain_hi", C.c_int64)]
 
 
 class Estimate(C.Structure):
@@ -79,6 +80,15 @@ class Estimate(C.Structure):
             v = getattr(self, name)
             out[name] = list(v) if not isinstance(v, (int, float)) else v
         return out
+
+
+class TraceResult(C.Structure):
+    _fields_ = [("intensity", C.c_double), ("std_err", C.c_double), ("mean_length", C.c_double),
+                ("detected", C.c_double), ("emitted", C.c_double), ("sum_w", C.c_double), ("sum_w2", C.c_double),
+                ("sum_wl", C.c_double)]
+
+    def as_dict(self):
+        return {name: float(getattr(self, name)) for name, _ in self._fields_}
 
 
 # Every symbol declared in include/pathmc.h, with its ctypes prototype.
@@ -100,6 +110,12 @@ PROTOTYPES = {
     "pmc_run_steps": ([_vp, C.c_uint64, _vp], C.c_int),
     "pmc_read_estimator": ([_vp, C.POINTER(Estimate), C.c_size_t, _vp], C.c_int),
     "pmc_grad_estimator": ([_vp, _dp, _dp, C.c_size_t, _vp], C.c_int),
+    "pmc_shard_range": ([C.POINTER(PairDesc), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int64),
+                         C.POINTER(C.c_int64)], C.c_int),
+    "pmc_read_moments": ([_vp, _dp, C.c_size_t, _vp], C.c_int),
+    "pmc_pair_z2": ([_vp, _dp, C.c_size_t, _vp], C.c_int),
+    "pmc_estimate_from_moments": ([_dp, C.c_size_t, _dp, C.POINTER(Estimate), _dp, _dp], C.c_int),
+    "pmc_moments_from_accumulators": ([_dp, C.c_size_t, _ip, C.c_size_t, C.c_double, C.c_double, _dp], C.c_int),
     "pmc_n_theta": ([_vp], C.c_int),
     "pmc_read_states": ([_vp, _fp, _ip, C.POINTER(C.c_uint64), C.c_int, _vp], C.c_int),
     "pmc_read_accumulators": ([_vp, _dp, C.c_size_t, _vp], C.c_int),
@@ -112,10 +128,10 @@ PROTOTYPES = {
     "pmc_logp": ([_vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp], C.c_int),
     "pmc_logp_grad": ([_vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp], C.c_int),
     "pmc_score": ([_vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp], C.c_int),
-    "pmc_trace": ([_vp, _vp, _vp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int, _dp, _vp],
-                  C.c_int),
+    "pmc_trace": ([_vp, _vp, _vp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int,
+                   C.POINTER(TraceResult), _vp], C.c_int),
     "pmc_trace_noalloc": ([_vp, _vp, _vp, _ip, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int,
-                           _dp, _vp], C.c_int),
+                           C.POINTER(TraceResult), _vp], C.c_int),
     "pmc_qref_logdensity": ([_vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp], C.c_int),
     "pmc_qref_sample": ([_vp, _vp, _vp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, _vp, _vp, C.c_int, _vp],
                         C.c_int),
@@ -132,8 +148,10 @@ PROTOTYPES = {
     "pmc_length_hist": ([_vp, C.c_double, C.c_double, C.c_int, _vp, _vp], C.c_int),
     "pmc_score_observe": ([_vp, _vp, _vp], C.c_int),
     "pmc_trace_lengths": ([_vp, _vp, _vp, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int,
-                           C.c_double, C.c_double, C.c_int, _dp, _dp, _vp], C.c_int),
-    "pmc_measure_pipes": ([_vp, _dp, _vp], C.c_int),
+                           C.c_double, C.c_double, C.c_int, C.POINTER(TraceResult), _dp, _vp], C.c_int),
+    "pmc_seed_from_tracer": ([_vp, C.c_uint64, C.c_uint64, C.c_int, C.c_double, C.POINTER(C.c_uint64), _vp],
+                             C.c_int),
+    "pmc_seed_select": ([C.POINTER(C.c_uint64), C.c_size_t, C.c_size_t, C.POINTER(C.c_uint64)], C.c_int),
     "pmc_last_error": ([], C.c_char_p),
     "pmc_version": ([], C.c_char_p),
 }

@@ -16,8 +16,8 @@ import torch
 
 from . import _lib
 from . import scenes as S
-from ._lib import (Estimate, GeometryDesc, MediumDesc, PairDesc, RunDesc, SensorDesc, SourceDesc,
-                   PMC_ACC_WORDS, PMC_FLAG_GRADIENTS, PMC_FLAG_NO_GRAPH, check, load)
+from ._lib import (Estimate, GeometryDesc, MediumDesc, PairDesc, RunDesc, SensorDesc, SourceDesc, TraceResult,
+                   PMC_ACC_WORDS, PMC_FLAG_GRADIENTS, PMC_FLAG_NO_GRAPH, PMC_MOMENT_WORDS, check, load)
 
 
 def _stream(stream=None):
@@ -149,7 +149,7 @@ def create_geometry(ctx: Context, sources, sensors, pairs) -> Geometry:
 
 
 def run_desc(r: S.Run, flags: int = 0, warps_per_block: int = 0, user_xyz: Optional[np.ndarray] = None,
-             user_n: Optional[np.ndarray] = None, smem_window: int = 0):
+             user_n: Optional[np.ndarray] = None, smem_window: int = 0, chain_window=(0, 0)):
     d = RunDesc()
     d.seed = int(r.seed)
     d.p_within, d.p_birth, d.p_death = float(r.p_within), float(r.p_birth), float(r.p_death)
@@ -167,6 +167,7 @@ def run_desc(r: S.Run, flags: int = 0, warps_per_block: int = 0, user_xyz: Optio
     d.smem_window = int(smem_window)
     d.hmc_steps = int(getattr(r, "hmc_steps", 10))
     d.layout = int(getattr(r, "layout", 0))
+    d.chain_lo, d.chain_hi = int(chain_window[0]), int(chain_window[1])
     keep = ()
     if user_xyz is not None:
         ux = np.ascontiguousarray(user_xyz, dtype=np.float32)  # [chains][3][stride]
@@ -183,9 +184,11 @@ class Chains:
     """Chains of every pair of a geometry (pmc_init_chains .. pmc_destroy_chains)."""
 
     def __init__(self, ctx: Context, medium: Medium, geom: Geometry, run: S.Run, flags: int = 0,
-                 warps_per_block: int = 0, user_xyz=None, user_n=None, stream=None, smem_window: int = 0):
+                 warps_per_block: int = 0, user_xyz=None, user_n=None, stream=None, smem_window: int = 0,
+                 chain_window=(0, 0)):
         self.ctx, self.medium, self.geom, self.run = ctx, medium, geom, run
-        d, keep = run_desc(run, flags, warps_per_block, user_xyz, user_n, smem_window)
+        self.chain_window = tuple(int(v) for v in chain_window)
+        d, keep = run_desc(run, flags, warps_per_block, user_xyz, user_n, smem_window, chain_window)
         h = C.c_void_p()
         with torch.cuda.device(ctx.device):
             check(load().pmc_init_chains(ctx.handle, medium.handle, geom.handle, C.byref(d), _stream(stream),
@@ -215,6 +218,34 @@ class Chains:
         out = (Estimate * self.n_pairs)()
         check(load().pmc_read_estimator(self.handle, out, self.n_pairs, _stream(stream)), "pmc_read_estimator")
         return [e.as_dict() for e in out]
+
+    def read_moments(self, stream=None) -> np.ndarray:
+        """Per-pair additive moments of this chain set (pmc_read_moments): (n_pairs, PMC_MOMENT_WORDS)."""
+        out = np.zeros((self.n_pairs, PMC_MOMENT_WORDS))
+        check(load().pmc_read_moments(self.handle, out.ctypes.data_as(C.POINTER(C.c_double)), out.size,
+                                      _stream(stream)), "pmc_read_moments")
+        return out
+
+    def pair_z2(self, stream=None) -> np.ndarray:
+        """Direct-sector integral of every pair (pmc_pair_z2)."""
+        out = np.zeros(self.n_pairs)
+        check(load().pmc_pair_z2(self.handle, out.ctypes.data_as(C.POINTER(C.c_double)), self.n_pairs,
+                                 _stream(stream)), "pmc_pair_z2")
+        return out
+
+    def read_estimator_sharded(self, group=None, stream=None):
+        """Estimates of the whole sharded chain set: this rank's moments, one
+        sum all-reduce over the process group (torch.distributed), then
+        pmc_estimate_from_moments.  Returns (estimates, grad, grad_se)."""
+        import torch.distributed as dist
+        mom = self.read_moments(stream)
+        if dist.is_available() and dist.is_initialized():
+            backend = dist.get_backend(group)
+            dev = f"cuda:{self.ctx.device}" if backend == "nccl" else "cpu"
+            t = torch.from_numpy(mom).to(dev)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+            mom = t.cpu().numpy()
+        return estimate_from_moments(mom, self.pair_z2(stream))
 
     def grad_estimator(self, stream=None):
         nt = self.medium.n_theta
@@ -343,6 +374,52 @@ class Chains:
             pass
 
 
+def shard_range(pairs: Sequence[S.Pair], rank: int, world: int):
+    """Chain window (lo, hi) of `rank` among `world` ranks (pmc_shard_range)."""
+    prs = (PairDesc * len(pairs))()
+    for i, p in enumerate(pairs):
+        prs[i].source, prs[i].sensor = int(p.source), int(p.sensor)
+        prs[i].n_chains, prs[i].cap = int(p.n_chains), int(p.cap)
+    lo, hi = C.c_int64(0), C.c_int64(0)
+    check(load().pmc_shard_range(prs, len(pairs), int(rank), int(world), C.byref(lo), C.byref(hi)),
+          "pmc_shard_range")
+    return int(lo.value), int(hi.value)
+
+
+def estimate_from_moments(moments: np.ndarray, z2: np.ndarray):
+    """Per-pair estimates from (all-reduced) moments (pmc_estimate_from_moments):
+    (list of estimate dicts, grad (n_pairs, 3), grad_se (n_pairs, 3))."""
+    mom = np.ascontiguousarray(moments, dtype=np.float64)
+    z = np.ascontiguousarray(z2, dtype=np.float64)
+    n = len(z)
+    if mom.shape != (n, PMC_MOMENT_WORDS):
+        raise ValueError("moments must have shape (n_pairs, PMC_MOMENT_WORDS)")
+    out = (Estimate * n)()
+    g = np.zeros((n, 3))
+    gs = np.zeros((n, 3))
+    check(load().pmc_estimate_from_moments(mom.ctypes.data_as(C.POINTER(C.c_double)), n,
+                                           z.ctypes.data_as(C.POINTER(C.c_double)), out,
+                                           g.ctypes.data_as(C.POINTER(C.c_double)),
+                                           gs.ctypes.data_as(C.POINTER(C.c_double))), "pmc_estimate_from_moments")
+    return [e.as_dict() for e in out], g, gs
+
+
+def moments_from_accumulators(acc: np.ndarray, chain_pair: np.ndarray, n_pairs: int, lambda_s: float = 1.0,
+                              lambda_a: float = 1.0) -> np.ndarray:
+    """Host moments of accumulator rows (pmc_moments_from_accumulators)."""
+    a = np.ascontiguousarray(acc, dtype=np.float64)
+    cp = np.ascontiguousarray(chain_pair, dtype=np.int32)
+    if a.ndim != 2 or a.shape[1] != PMC_ACC_WORDS or len(cp) != len(a):
+        raise ValueError("acc must have shape (n_chains, PMC_ACC_WORDS) and chain_pair n_chains entries")
+    out = np.zeros((int(n_pairs), PMC_MOMENT_WORDS))
+    check(load().pmc_moments_from_accumulators(a.ctypes.data_as(C.POINTER(C.c_double)), len(a),
+                                               cp.ctypes.data_as(C.POINTER(C.c_int)), int(n_pairs),
+                                               float(lambda_s), float(lambda_a),
+                                               out.ctypes.data_as(C.POINTER(C.c_double))),
+          "pmc_moments_from_accumulators")
+    return out
+
+
 def init_chains(ctx, medium, geom, run, **kw) -> Chains:
     return Chains(ctx, medium, geom, run, **kw)
 
@@ -404,35 +481,40 @@ def score(ctx: Context, medium: Medium, geom: Geometry, pair: int, xyz: torch.Te
     return out
 
 
+def _trace_dict(r: TraceResult) -> dict:
+    d = r.as_dict()
+    # short names used throughout the tests and the benchmark
+    d.update(I=d["intensity"], se=d["std_err"], mean_L=d["mean_length"], hits=d["detected"], photons=d["emitted"])
+    return d
+
+
 def trace(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: int, n_photons: int, photon0: int = 0,
-          r_reject: float = math.inf, max_scatter: int = 1 << 30, stream=None):
-    """GPU forward tracer (pmc_trace): dict with the intensity estimate and its standard error."""
-    out = np.zeros(5)
+          r_reject: float = math.inf, max_scatter: int = 1000, stream=None):
+    """GPU forward tracer (pmc_trace): the pmc_trace_result fields as a dict,
+    with the short names I, se, mean_L, hits, photons.  A photon that never
+    reaches the sensor scatters until max_scatter or until it starts a flight
+    beyond r_reject: with r_reject infinite the scattering limit alone ends
+    it, so keep max_scatter to the path lengths of interest (the chains' cap
+    - 2 for a cap-truncated comparison)."""
+    out = TraceResult()
     check(load().pmc_trace(ctx.handle, medium.handle, geom.handle, int(pair), int(seed), int(photon0),
-                           int(n_photons), float(r_reject), int(min(max_scatter, 2**31 - 1)),
-                           out.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)), "pmc_trace")
-    N = out[3]
-    mean = out[0] / N if N > 0 else float("nan")
-    var = max(out[1] / N - mean * mean, 0.0) if N > 0 else float("nan")
-    return {"I": mean, "se": math.sqrt(var / N) if N > 0 else float("nan"), "hits": out[2], "photons": N,
-            "mean_L": out[4] / out[0] if out[0] > 0 else float("nan"), "raw": out}
+                           int(n_photons), float(r_reject), int(min(max_scatter, 2**31 - 1)), C.byref(out),
+                           _stream(stream)), "pmc_trace")
+    return _trace_dict(out)
 
 
 def trace_lengths(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: int, n_photons: int, l_lo: float,
-                  l_hi: float, n_bins: int, photon0: int = 0, r_reject: float = math.inf, max_scatter: int = 1 << 30,
+                  l_hi: float, n_bins: int, photon0: int = 0, r_reject: float = math.inf, max_scatter: int = 1000,
                   stream=None):
     """GPU forward tracer with the detected weight binned by path length
-    (pmc_trace_lengths): (result dict as trace(), weight per bin / emitted photons)."""
-    out = np.zeros(5)
+    (pmc_trace_lengths): (result dict as trace(), weight per bin per emitted photon)."""
+    out = TraceResult()
     hist = np.zeros(int(n_bins))
     check(load().pmc_trace_lengths(ctx.handle, medium.handle, geom.handle, int(pair), int(seed), int(photon0),
                                    int(n_photons), float(r_reject), int(min(max_scatter, 2**31 - 1)), float(l_lo),
-                                   float(l_hi), int(n_bins), out.ctypes.data_as(C.POINTER(C.c_double)),
-                                   hist.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)), "pmc_trace_lengths")
-    N = out[3]
-    mean = out[0] / N
-    var = max(out[1] / N - mean * mean, 0.0)
-    return {"I": mean, "se": math.sqrt(var / N), "hits": out[2], "photons": N, "raw": out}, hist / N
+                                   float(l_hi), int(n_bins), C.byref(out), hist.ctypes.data_as(C.POINTER(C.c_double)),
+                                   _stream(stream)), "pmc_trace_lengths")
+    return _trace_dict(out), hist
 
 
 def yield_logratio(ctx: Context, medium: Medium, geom: Geometry, pair0: int, pair1: int, side: int,
@@ -519,16 +601,15 @@ def qref_sample(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: i
 
 
 def trace_noalloc(ctx: Context, medium: Medium, geom: Geometry, pairs, seed: int, n_photons: int,
-                  photon0: int = 0, r_reject: float = math.inf, max_scatter: int = 1 << 30, stream=None):
-    """Allocation-free GPU tracer over several pairs (pmc_trace_noalloc): raw
-    sums per pair, shape (len(pairs), 5), in the layout of pmc_trace."""
+                  photon0: int = 0, r_reject: float = math.inf, max_scatter: int = 1000, stream=None):
+    """Allocation-free GPU tracer over several pairs (pmc_trace_noalloc): one
+    result dict per pair, as trace() returns."""
     ids = np.ascontiguousarray(pairs, dtype=np.int32)
-    out = np.zeros((len(ids), 5))
+    out = (TraceResult * max(len(ids), 1))()
     check(load().pmc_trace_noalloc(ctx.handle, medium.handle, geom.handle, ids.ctypes.data_as(C.POINTER(C.c_int)),
                                    len(ids), int(seed), int(photon0), int(n_photons), float(r_reject),
-                                   int(min(max_scatter, 2**31 - 1)), out.ctypes.data_as(C.POINTER(C.c_double)),
-                                   _stream(stream)), "pmc_trace_noalloc")
-    return out
+                                   int(min(max_scatter, 2**31 - 1)), out, _stream(stream)), "pmc_trace_noalloc")
+    return [_trace_dict(out[i]) for i in range(len(ids))]
 
 
 def trace_paths(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: int, n_photons: int,
@@ -549,58 +630,28 @@ def trace_paths(ctx: Context, medium: Medium, geom: Geometry, pair: int, seed: i
     return xyz[:, :kept], n[:kept], int(acc.value)
 
 
-def seed_from_tracer(chains: "Chains", seed: int = 2024, photons_per_round: int = 1 << 28, max_rounds: int = 64,
-                     r_reject: float = math.inf):
-    """Initialise every chain with an equilibrium path: weight-thinned tracer
-    paths per pair, reused cyclically when fewer than the pair's chains were
-    found; returns the photons traced per pair.  Pair p traces with Philox
-    key seed + p, so the pairs' seeds are independent.  Every accepted path
-    of the traced photon range is kept (a round that finds more than the
-    buffer holds is traced again with half the photons, since the buffer
-    keeps the paths that finish first, which would favour short paths), and
-    the chains take a seeded random subset of them.  r_reject: photons farther
-    than this from the sensor centre are dropped (a finite radius shortens
-    the tracing of escaping photons; its bias is the weight of paths that
-    leave the ball and return)."""
-    geom = chains.geom
-    stride = geom.max_cap
-    total_xyz = np.zeros((chains.total, 3, stride), dtype=np.float32)
-    total_n = np.zeros(chains.total, dtype=np.int32)
-    used = []
-    c0 = 0
-    for p, pr in enumerate(geom.pairs):
-        got_x, got_n, photons = [], [], 0
-        need = pr.n_chains
-        per_round = int(photons_per_round)
-        rounds = 0
-        while rounds < max_rounds:
-            xyz, n, acc = trace_paths(chains.ctx, chains.medium, geom, p, seed + p, per_round, need,
-                                      photon0=photons, stride=stride, r_reject=r_reject)
-            if acc > need and per_round > 1:
-                per_round = max(1, per_round // 2)   # overflow: the same photons again, fewer at a time
-                continue
-            rounds += 1
-            photons += per_round
-            if len(n):
-                got_x.append(xyz.cpu().numpy())
-                got_n.append(n.cpu().numpy())
-            if sum(len(a) for a in got_n) >= need:
-                break
-        if not got_n:
-            raise RuntimeError(f"no detected photon for pair {p} after {photons} photons")
-        X = np.concatenate(got_x, axis=1)
-        Nn = np.concatenate(got_n)
-        if len(Nn) >= need:
-            idx = np.random.default_rng([int(seed), p]).permutation(len(Nn))[:need]
-        else:
-            idx = np.arange(need) % len(Nn)
-        total_xyz[c0:c0 + need] = X[:, idx, :].transpose(1, 0, 2)
-        total_n[c0:c0 + need] = Nn[idx]
-        used.append(photons)
-        c0 += need
-    chains.set_states(total_xyz, total_n)
-    torch.cuda.current_stream().synchronize()
-    return used
+def seed_from_tracer(chains: "Chains", seed: int = 2024, photons_per_round: int = 1 << 26, max_rounds: int = 64,
+                     r_reject: float = math.inf, stream=None):
+    """Start every chain from an equilibrium path: the first weight-thinned
+    tracer photons of each pair, in photon order (pmc_seed_from_tracer).
+    Pair p traces with Philox key seed + p.  r_reject: photons farther than
+    this from the sensor centre are dropped (a finite radius shortens the
+    tracing of escaping photons; its bias is the weight of paths that leave
+    the ball and return).  Returns the photons traced per pair."""
+    used = np.zeros(chains.n_pairs, dtype=np.uint64)
+    check(load().pmc_seed_from_tracer(chains.handle, int(seed), int(photons_per_round), int(max_rounds),
+                                      float(r_reject), used.ctypes.data_as(C.POINTER(C.c_uint64)), _stream(stream)),
+          "pmc_seed_from_tracer")
+    return [int(u) for u in used]
+
+
+def seed_select(photon_idx, need: int) -> np.ndarray:
+    """The seed selection of pmc_seed_from_tracer on host data (pmc_seed_select)."""
+    idx = np.ascontiguousarray(photon_idx, dtype=np.uint64)
+    out = np.zeros(int(need), dtype=np.uint64)
+    check(load().pmc_seed_select(idx.ctypes.data_as(C.POINTER(C.c_uint64)), len(idx), int(need),
+                                 out.ctypes.data_as(C.POINTER(C.c_uint64))), "pmc_seed_select")
+    return out
 
 
 class LogP(torch.autograd.Function):
@@ -636,12 +687,3 @@ class PathSampler:
 
     def estimate(self):
         return self.chains.read_estimator()
-
-
-def measure_pipes(ctx: Context, stream=None) -> dict:
-    """Measured FP32 FMA and MUFU lane-operations per second of the device
-    (pmc_measure_pipes)."""
-    out = np.zeros(2)
-    check(load().pmc_measure_pipes(ctx.handle, out.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)),
-          "pmc_measure_pipes")
-    return {"fp32_per_s": float(out[0]), "mufu_per_s": float(out[1])}

@@ -1,8 +1,10 @@
 """Build libpathmc.so in-tree with nvcc for sm_103a.
 
 Each CUDA translation unit is compiled in parallel, then linked into
-``paper_1811_04156_gb300/_build/libpathmc.so``.  Rebuilds only when a source
-or header is newer than the library.
+``paper_1811_04156_gb300/_build/libpathmc.so``.  The benchmark harness's
+pipe-rate microbenchmark (csrc/probe/) is a library of its own,
+``_build/libpmcprobe.so``, outside the product library.  Rebuilds only when
+a source or header is newer than the library.
 """
 from __future__ import annotations
 
@@ -17,6 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpathmc.so")
+PROBE_SRC = os.path.join(CSRC, "probe", "pipe_rates.cu")
+PROBE_LIB = os.path.join(BUILD, "libpmcprobe.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -47,10 +51,23 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
+def _build_probe(nvcc: str) -> None:
+    if os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc, "-shared", "-o", tmp, PROBE_SRC] + NVCC_FLAGS, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    if force and os.path.exists(PROBE_LIB):
+        os.unlink(PROBE_LIB)
+    os.makedirs(BUILD, exist_ok=True)
+    _build_probe(_nvcc())
     if not force and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 

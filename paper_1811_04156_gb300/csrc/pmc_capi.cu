@@ -181,7 +181,9 @@ struct pmc_chains_s {
   int* d_any = nullptr;
   unsigned int* d_queue = nullptr;
   double* d_z2 = nullptr;
-  double* d_est = nullptr;
+  std::vector<double> h_z2;        // host copy of d_z2 (filled at the first estimate)
+  double* d_est = nullptr;         // per-pair moments [n_pairs][PMC_MOMENT_WORDS]
+  long long chain_lo = 0;          // this set holds the geometry's chains [chain_lo, chain_lo + total)
   int* h_abort = nullptr;
   int* d_abort = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -268,16 +270,91 @@ static DRun qref_run() {
   return r;
 }
 
+namespace pmc {
+
+// Tracer estimate from the kernel's raw sums (sum w rho, sum (w rho)^2,
+// detected, emitted, sum w rho L): the mean detected weight per emitted
+// photon with its standard error, and the weight-averaged path length.
+pmc_trace_result trace_result(const double* raw) {
+  pmc_trace_result r{};
+  const double N = raw[3];
+  r.sum_w = raw[0];
+  r.sum_w2 = raw[1];
+  r.detected = raw[2];
+  r.emitted = N;
+  r.sum_wl = raw[4];
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  r.intensity = N > 0 ? raw[0] / N : nan;
+  r.std_err = N > 0 ? std::sqrt(std::max(raw[1] / N - r.intensity * r.intensity, 0.0) / N) : nan;
+  r.mean_length = raw[0] > 0 ? raw[4] / raw[0] : nan;
+  return r;
+}
+
+// Estimate of one pair from the sums of its chains' accumulators (pmc_moments
+// layout; see add_chain_moments).  With f_c = n2_c / N_c a chain's fraction
+// of direct paths and w_c = N_c / N, the across-chain variance of pi(n = 2)
+// is sum w_c^2 (f_c - pi)^2 C / (C - 1) = (sum n2^2 - 2 pi sum N n2 +
+// pi^2 sum N^2) / N^2 * C / (C - 1), and likewise for the score means s_c =
+// A_c / N_c and their covariance with pi; I = Z2 / pi (direct-sector
+// anchor), its standard error I sqrt(var pi) / pi; the gradient I * s by the
+// delta method.  R-hat (Gelman-Rubin) is on the path length over chains.
+void estimate_of_moments(const double* m, double z2, pmc_estimate* o, double* grad, double* grad_se) {
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  const double N = m[MOM_ACC + ACC_NREC];
+  const double C = m[MOM_NCHAIN];
+  const double pi = N > 0 ? m[MOM_ACC + ACC_NDIRECT] / N : 0.0;
+  const double corr = C > 1 ? C / (C - 1.0) : 1.0;
+  const double N2 = N * N;
+  const double var_pi =
+      N > 0 ? std::max(m[MOM_N2SQ] - 2.0 * pi * m[MOM_NN2] + pi * pi * m[MOM_NSQ], 0.0) / N2 * corr : 0.0;
+  const double I = pi > 0 ? z2 / pi : nan;
+  const double se = pi > 0 ? I * std::sqrt(var_pi) / pi : I;
+  *o = pmc_estimate{};
+  o->intensity = I;
+  o->std_err = se;
+  o->rel_err = se / I;
+  o->pi_direct = pi;
+  o->z2 = z2;
+  double rhat = nan;
+  const double K = m[MOM_RH_K];
+  if (K > 1) {
+    const double W = m[MOM_RH_VAR] / K;
+    const double mbar = m[MOM_RH_M] / K;
+    const double B_over_n = (m[MOM_RH_M2] / K - mbar * mbar) * K / (K - 1.0);
+    const double nper = N / K;
+    if (W > 0) rhat = std::sqrt(((nper - 1.0) / nper * W + B_over_n) / W);
+  }
+  o->rhat = rhat;
+  for (int k = 0; k < 4; ++k) {
+    const double pr = m[MOM_ACC + ACC_PROP + k];
+    o->accept[k] = pr > 0 ? m[MOM_ACC + ACC_ACC + k] / pr : 0.0;
+    o->proposals[k] = pr;
+  }
+  o->mean_n = N > 0 ? m[MOM_ACC + ACC_SUMN] / N : 0.0;
+  o->mean_length = N > 0 ? m[MOM_ACC + ACC_SUML] / N : 0.0;
+  o->n_samples = N;
+  o->ess = var_pi > 0 ? pi * (1.0 - pi) / var_pi : 0.0;
+  o->bridge_intensity = nan;
+  o->bridge_std_err = nan;
+  for (int k = 0; k < 3; ++k) {
+    const double sbar = N > 0 ? m[MOM_A + k] / N : 0.0;
+    const double vs = N > 0 ? std::max(m[MOM_ASQ + k] - 2.0 * sbar * m[MOM_NA + k] + sbar * sbar * m[MOM_NSQ], 0.0) /
+                                  N2 * corr
+                            : 0.0;
+    const double cv = N > 0 ? (m[MOM_N2A + k] - sbar * m[MOM_NN2] - pi * m[MOM_NA + k] + pi * sbar * m[MOM_NSQ]) /
+                                  N2 * corr
+                            : 0.0;
+    const double dpi = pi > 0 ? I * sbar / pi : 0.0;
+    if (grad) grad[k] = I * sbar;
+    if (grad_se) grad_se[k] = std::sqrt(std::max(I * I * vs + dpi * dpi * var_pi - 2.0 * I * dpi * cv, 0.0));
+  }
+}
+
+}  // namespace pmc
+
 extern "C" {
 
 const char* pmc_last_error(void) { return g_err.c_str(); }
-
-int pmc_measure_pipes(pmc_ctx_t ctx, double* out, void* stream) {
-  if (ctx == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
-  CK(cudaSetDevice(ctx->device));
-  CK(measure_pipes(ctx->n_sm, &out[0], &out[1], static_cast<cudaStream_t>(stream)));
-  return PMC_OK;
-}
 
 const char* pmc_version(void) { return "pathmc 0.1 (sm_103a)"; }
 
@@ -517,6 +594,7 @@ static ChainParams class_params(pmc_chains_t ch, size_t k, unsigned long long n_
   p.any_status = ch->d_any;
   p.queue = ch->d_queue + k;
   p.abort_flag = ch->d_abort;
+  p.chain_id0 = static_cast<uint32_t>(ch->chain_lo);
   p.chain_lo = cl.lo;
   p.chain_hi = cl.hi;
   p.n_steps = n_steps;
@@ -691,7 +769,13 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   ch->init_kind = r->init;
   ch->init_k = r->init_k;
   ch->init_jitter = static_cast<float>(r->init_jitter);
-  ch->total = geom->total_chains;
+  // the chain window: the geometry's chains [lo, hi) in pair order (all by default)
+  const long long total_g = geom->total_chains;
+  long long lo = r->chain_lo, hi = r->chain_hi;
+  if (lo == 0 && hi == 0) hi = total_g;
+  if (lo < 0 || hi > total_g || hi <= lo) return fail(PMC_ERR_INVALID, "chain window must satisfy 0 <= lo < hi <= total");
+  ch->chain_lo = lo;
+  ch->total = static_cast<int>(hi - lo);
   ch->n_pairs = static_cast<int>(geom->pairs.size());
   DRun& R = ch->run;
   R.seed = r->seed;
@@ -709,6 +793,11 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
 
   ch->h_pairs = geom->pairs;
   for (auto& d : ch->h_pairs) {
+    // the pair's chains inside the window, numbered from the window's first chain
+    const long long a = std::max<long long>(d.chain0, lo), b = std::min<long long>(d.chain0 + d.n_chains, hi);
+    d.chain0 = static_cast<int>(std::min<long long>(a, hi) - lo);
+    d.n_chains = static_cast<int>(std::max<long long>(b - a, 0));
+    if (d.chain0 < 0 || d.chain0 + d.n_chains > hi - lo) return fail(PMC_ERR_INVALID, "chain window bookkeeping");
     // tree moves: sigma is dimensionless, the default end step has angular scale sigma
     const double ke = r->kappa_end > 0 ? r->kappa_end
                       : (r->within == PMC_WITHIN_TREE ? 1.0 / (r->sigma * r->sigma) : (d.R / r->sigma) * (d.R / r->sigma));
@@ -819,7 +908,7 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   CK(dalloc(&ch->d_any, 1));
   CK(dalloc(&ch->d_queue, ch->classes.size()));
   CK(dalloc(&ch->d_z2, ch->n_pairs));
-  CK(dalloc(&ch->d_est, static_cast<size_t>(ch->n_pairs) * EST_WORDS));
+  CK(dalloc(&ch->d_est, static_cast<size_t>(ch->n_pairs) * PMC_MOMENT_WORDS));
   CK(cudaHostAlloc(reinterpret_cast<void**>(&ch->h_abort), sizeof(int), cudaHostAllocMapped));
   *ch->h_abort = 0;
   CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ch->d_abort), ch->h_abort, 0));
@@ -845,6 +934,7 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   ip.acc = ch->d_acc;
   ip.status = ch->d_status;
   ip.total = T;
+  ip.chain_id0 = static_cast<uint32_t>(lo);
   ip.init_kind = r->init;
   ip.init_k = r->init_k;
   ip.jitter = static_cast<float>(r->init_jitter);
@@ -891,6 +981,7 @@ static InitParams init_params(pmc_chains_t ch) {
   ip.acc = ch->d_acc;
   ip.status = ch->d_status;
   ip.total = ch->total;
+  ip.chain_id0 = static_cast<uint32_t>(ch->chain_lo);
   ip.init_kind = ch->init_kind;
   ip.init_k = ch->init_k;
   ip.jitter = ch->init_jitter;
@@ -982,46 +1073,117 @@ static int check_status(pmc_chains_t ch, cudaStream_t s) {
   return PMC_OK;
 }
 
+static double moments_ls(const pmc_chains_s* ch) { return ch->med->d.kind == 0 ? ch->med->lambda_s : 1.0; }
+static double moments_la(const pmc_chains_s* ch) { return ch->med->d.kind == 0 ? ch->med->lambda_a : 1.0; }
+
+// Per-pair moments of this chain set's accumulators into host `h`.
+static int read_moments(pmc_chains_t ch, std::vector<double>& h, cudaStream_t s) {
+  CK(cudaSetDevice(ch->ctx->device));
+  if (ch->h_z2.empty()) {
+    ch->h_z2.resize(ch->n_pairs);
+    CK(cudaMemcpyAsync(ch->h_z2.data(), ch->d_z2, sizeof(double) * ch->n_pairs, cudaMemcpyDeviceToHost, s));
+  }
+  CK(launch_moments(ch->d_acc, ch->d_pairs, ch->n_pairs, moments_ls(ch), moments_la(ch), ch->d_est, s));
+  h.resize(static_cast<size_t>(ch->n_pairs) * PMC_MOMENT_WORDS);
+  CK(cudaMemcpyAsync(h.data(), ch->d_est, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return check_status(ch, s);
+}
+
+int pmc_shard_range(const pmc_pair* pairs, int n_pairs, int rank, int world, int64_t* chain_lo, int64_t* chain_hi) {
+  if (pairs == nullptr || chain_lo == nullptr || chain_hi == nullptr || n_pairs < 1)
+    return fail(PMC_ERR_INVALID, "NULL argument or no pairs");
+  if (world < 1 || rank < 0 || rank >= world) return fail(PMC_ERR_INVALID, "need 0 <= rank < world");
+  long long total = 0;
+  double cost = 0.0;
+  for (int p = 0; p < n_pairs; ++p) {
+    if (pairs[p].n_chains < 1 || pairs[p].cap < 2) return fail(PMC_ERR_INVALID, "bad pair");
+    total += pairs[p].n_chains;
+    cost += static_cast<double>(pairs[p].n_chains) * pairs[p].cap;
+  }
+  if (total < world) return fail(PMC_ERR_INVALID, "fewer chains than ranks");
+  // first chain whose cumulative cost (caps of the chains before it) reaches
+  // `target`: chains of one pair cost the same, so the boundary inside a pair
+  // is a division
+  auto boundary = [&](double target) -> long long {
+    long long c0 = 0;
+    double before = 0.0;
+    for (int p = 0; p < n_pairs; ++p) {
+      const double per = pairs[p].cap, span = per * pairs[p].n_chains;
+      if (before + span >= target) {
+        const long long k = static_cast<long long>(std::ceil((target - before) / per - 1e-9));
+        return c0 + std::min<long long>(std::max<long long>(k, 0), pairs[p].n_chains);
+      }
+      before += span;
+      c0 += pairs[p].n_chains;
+    }
+    return total;
+  };
+  // edges e_0 = 0 < e_1 < ... < e_world = total: every rank keeps at least
+  // one chain, and e_r <= total - (world - r) leaves one for each later rank
+  long long e = 0, lo = 0;
+  for (int r = 1; r <= rank + 1; ++r) {
+    const long long b = r == world ? total
+                                   : std::max<long long>(e + 1, std::min<long long>(boundary(cost * r / world),
+                                                                                   total - (world - r)));
+    if (r == rank) lo = b;
+    e = b;
+  }
+  *chain_lo = lo;
+  *chain_hi = e;
+  return PMC_OK;
+}
+
+int pmc_read_moments(pmc_chains_t ch, double* out, size_t len, void* stream) {
+  if (ch == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (len < static_cast<size_t>(ch->n_pairs) * PMC_MOMENT_WORDS) return fail(PMC_ERR_INVALID, "output too short");
+  std::vector<double> h;
+  const int rc = read_moments(ch, h, static_cast<cudaStream_t>(stream));
+  if (rc != PMC_OK) return rc;
+  std::copy(h.begin(), h.end(), out);
+  return PMC_OK;
+}
+
 int pmc_read_estimator(pmc_chains_t ch, pmc_estimate* out, size_t n_pairs, void* stream) {
   if (ch == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
   if (n_pairs < static_cast<size_t>(ch->n_pairs)) return fail(PMC_ERR_INVALID, "output has fewer entries than pairs");
+  std::vector<double> h;
+  const int rc = read_moments(ch, h, static_cast<cudaStream_t>(stream));
+  if (rc != PMC_OK) return rc;
+  for (int i = 0; i < ch->n_pairs; ++i)
+    estimate_of_moments(h.data() + static_cast<size_t>(i) * PMC_MOMENT_WORDS, ch->h_z2[i], &out[i], nullptr, nullptr);
+  return PMC_OK;
+}
+
+int pmc_estimate_from_moments(const double* moments, size_t n_pairs, const double* z2, pmc_estimate* out,
+                              double* grad, double* grad_se) {
+  if (moments == nullptr || z2 == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  for (size_t i = 0; i < n_pairs; ++i)
+    estimate_of_moments(moments + i * PMC_MOMENT_WORDS, z2[i], &out[i], grad ? grad + 3 * i : nullptr,
+                        grad_se ? grad_se + 3 * i : nullptr);
+  return PMC_OK;
+}
+
+int pmc_moments_from_accumulators(const double* acc, size_t n_chains, const int* chain_pair, size_t n_pairs,
+                                  double lambda_s, double lambda_a, double* moments) {
+  if (acc == nullptr || chain_pair == nullptr || moments == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (!(lambda_s > 0) || !(lambda_a > 0)) return fail(PMC_ERR_INVALID, "lengths must be > 0");
+  std::fill(moments, moments + n_pairs * PMC_MOMENT_WORDS, 0.0);
+  for (size_t c = 0; c < n_chains; ++c) {
+    const int p = chain_pair[c];
+    if (p < 0 || static_cast<size_t>(p) >= n_pairs) return fail(PMC_ERR_INVALID, "chain_pair out of range");
+    add_chain_moments(acc + c * ACC_WORDS, lambda_s, lambda_a, moments + static_cast<size_t>(p) * PMC_MOMENT_WORDS);
+  }
+  return PMC_OK;
+}
+
+int pmc_pair_z2(pmc_chains_t ch, double* z2, size_t n_pairs, void* stream) {
+  if (ch == nullptr || z2 == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (n_pairs < static_cast<size_t>(ch->n_pairs)) return fail(PMC_ERR_INVALID, "output too short");
   CK(cudaSetDevice(ch->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  EstParams p{};
-  p.acc = ch->d_acc;
-  p.pairs = ch->d_pairs;
-  p.z2 = ch->d_z2;
-  p.bridge_q = nullptr;
-  p.n_pairs = ch->n_pairs;
-  p.homogeneous = ch->med->d.kind == 0;
-  p.lambda_s = ch->med->d.kind == 0 ? ch->med->lambda_s : 1.0;
-  p.lambda_a = ch->med->d.kind == 0 ? ch->med->lambda_a : 1.0;
-  p.out = ch->d_est;
-  CK(launch_estimator(p, s));
-  std::vector<double> h(static_cast<size_t>(ch->n_pairs) * EST_WORDS);
-  CK(cudaMemcpyAsync(h.data(), ch->d_est, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-  const int st = check_status(ch, s);
-  for (int i = 0; i < ch->n_pairs; ++i) {
-    const double* e = h.data() + static_cast<size_t>(i) * EST_WORDS;
-    pmc_estimate& o = out[i];
-    o.intensity = e[EST_I];
-    o.std_err = e[EST_SE];
-    o.rel_err = e[EST_REL];
-    o.pi_direct = e[EST_PI];
-    o.z2 = e[EST_Z2];
-    o.rhat = e[EST_RHAT];
-    for (int k = 0; k < 4; ++k) {
-      o.accept[k] = e[EST_ACC0 + k];
-      o.proposals[k] = e[EST_PROP0 + k];
-    }
-    o.mean_n = e[EST_MEAN_N];
-    o.mean_length = e[EST_MEAN_L];
-    o.n_samples = e[EST_NSAMP];
-    o.ess = e[EST_ESS];
-    o.bridge_intensity = e[EST_BRIDGE_I];
-    o.bridge_std_err = e[EST_BRIDGE_SE];
-  }
-  return st;
+  CK(cudaMemcpyAsync(z2, ch->d_z2, sizeof(double) * ch->n_pairs, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return PMC_OK;
 }
 
 int pmc_grad_estimator(pmc_chains_t ch, double* grad, double* grad_se, size_t len, void* stream) {
@@ -1031,23 +1193,25 @@ int pmc_grad_estimator(pmc_chains_t ch, double* grad, double* grad_se, size_t le
   const bool layered = ch->med->d.kind != PMC_HOMOGENEOUS;
   if (!layered && !(ch->flags & PMC_FLAG_GRADIENTS))
     return fail(PMC_ERR_INVALID, "homogeneous gradients need chains created with PMC_FLAG_GRADIENTS");
-  std::vector<pmc_estimate> est(ch->n_pairs);
-  const int rc = pmc_read_estimator(ch, est.data(), est.size(), stream);
-  if (rc != PMC_OK) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<double> h;
+  const int rc = read_moments(ch, h, s);
+  if (rc != PMC_OK) return rc;
+  std::vector<pmc_estimate> est(ch->n_pairs);
   if (!layered) {
     // accumulated over every recorded state while stepping
-    std::vector<double> h(static_cast<size_t>(ch->n_pairs) * EST_WORDS);
-    CK(cudaMemcpyAsync(h.data(), ch->d_est, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
     for (int i = 0; i < ch->n_pairs; ++i) {
+      double g[3], gs[3];
+      estimate_of_moments(h.data() + static_cast<size_t>(i) * PMC_MOMENT_WORDS, ch->h_z2[i], &est[i], g, gs);
       for (int k = 0; k < 3; ++k) {
-        grad[i * 3 + k] = h[static_cast<size_t>(i) * EST_WORDS + EST_GRAD0 + k];
-        if (grad_se) grad_se[i * 3 + k] = h[static_cast<size_t>(i) * EST_WORDS + EST_GRADSE0 + k];
+        grad[i * 3 + k] = g[k];
+        if (grad_se) grad_se[i * 3 + k] = gs[k];
       }
     }
     return PMC_OK;
   }
+  for (int i = 0; i < ch->n_pairs; ++i)
+    estimate_of_moments(h.data() + static_cast<size_t>(i) * PMC_MOMENT_WORDS, ch->h_z2[i], &est[i], nullptr, nullptr);
   // layered: per-layer scores of the chains' current states
   const int L = ch->med->d.n_layers;
   const size_t words = static_cast<size_t>(ch->n_pairs) * 4 * L;
@@ -1057,8 +1221,8 @@ int pmc_grad_estimator(pmc_chains_t ch, double* grad, double* grad_se, size_t le
   if (e == cudaSuccess)
     e = launch_layer_scores(ch->med->d, ch->d_pairs, ch->d_chain_pair, ch->d_chain_base, ch->d_xyz, ch->d_n, ch->total,
                             d_sums, s);
-  std::vector<double> h(words);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_sums, words * sizeof(double), cudaMemcpyDeviceToHost, s);
+  std::vector<double> hs(words);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), d_sums, words * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_sums);
   CK(e);
@@ -1066,8 +1230,8 @@ int pmc_grad_estimator(pmc_chains_t ch, double* grad, double* grad_se, size_t le
     const double N = static_cast<double>(ch->h_pairs[p].n_chains);
     const double I = est[p].intensity, seI = est[p].std_err;
     for (int j = 0; j < 2 * L; ++j) {
-      const double m = h[static_cast<size_t>(p) * 4 * L + j] / N;
-      const double v = std::max(h[static_cast<size_t>(p) * 4 * L + 2 * L + j] / N - m * m, 0.0);
+      const double m = hs[static_cast<size_t>(p) * 4 * L + j] / N;
+      const double v = std::max(hs[static_cast<size_t>(p) * 4 * L + 2 * L + j] / N - m * m, 0.0);
       grad[static_cast<size_t>(p) * nt + j] = I * m;
       if (grad_se) grad_se[static_cast<size_t>(p) * nt + j] = std::sqrt(I * I * v / N + m * m * seI * seI);
     }
@@ -1236,7 +1400,7 @@ int pmc_score(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, const 
 }
 
 int pmc_trace(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, uint64_t seed, uint64_t photon0,
-              uint64_t n_photons, double r_reject, int max_scatter, double* out, void* stream) {
+              uint64_t n_photons, double r_reject, int max_scatter, pmc_trace_result* out, void* stream) {
   const DPair* d = pair_of(geom, pair, false);
   if (!ctx || !med || !d || !out) return fail(PMC_ERR_INVALID, "bad argument");
   if (max_scatter < 0 || !(r_reject > 0)) return fail(PMC_ERR_INVALID, "bad tracer limits");
@@ -1245,17 +1409,19 @@ int pmc_trace(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, uint64
   double* d_out = nullptr;
   CK(dalloc(&d_out, 5));
   const float rr = std::isfinite(r_reject) ? static_cast<float>(r_reject) : std::numeric_limits<float>::infinity();
+  double raw[5] = {0, 0, 0, 0, 0};
   cudaError_t e = launch_trace(med->d, *d, seed, photon0, n_photons, rr, max_scatter, d_out, ctx->n_sm, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(raw, d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_out);
   CK(e);
+  *out = trace_result(raw);
   return PMC_OK;
 }
 
 int pmc_trace_noalloc(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const int* pair_ids, int n_pairs,
                       uint64_t seed, uint64_t photon0, uint64_t n_photons, double r_reject, int max_scatter,
-                      double* out, void* stream) {
+                      pmc_trace_result* out, void* stream) {
   if (!ctx || !med || !geom || !pair_ids || !out) return fail(PMC_ERR_INVALID, "bad argument");
   if (n_pairs < 1 || n_pairs > PMC_NOALLOC_MAX_PAIRS)
     return fail(PMC_ERR_INVALID, "n_pairs must be in [1, PMC_NOALLOC_MAX_PAIRS]");
@@ -1268,8 +1434,10 @@ int pmc_trace_noalloc(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const in
   }
   CK(cudaSetDevice(ctx->device));
   const float rr = std::isfinite(r_reject) ? static_cast<float>(r_reject) : std::numeric_limits<float>::infinity();
-  CK(launch_trace_noalloc(med->d, sel, n_pairs, seed, photon0, n_photons, rr, max_scatter, out, ctx->device,
+  double raw[kNoAllocMaxPairs * 5];  // host stack: the call allocates no device memory
+  CK(launch_trace_noalloc(med->d, sel, n_pairs, seed, photon0, n_photons, rr, max_scatter, raw, ctx->device,
                           ctx->n_sm, static_cast<cudaStream_t>(stream)));
+  for (int i = 0; i < n_pairs; ++i) out[i] = trace_result(raw + 5 * i);
   return PMC_OK;
 }
 
@@ -1587,7 +1755,7 @@ int pmc_length_hist(pmc_chains_t ch, double l_lo, double l_hi, int n_bins, doubl
 
 int pmc_trace_lengths(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, uint64_t seed, uint64_t photon0,
                       uint64_t n_photons, double r_reject, int max_scatter, double l_lo, double l_hi, int n_bins,
-                      double* out, double* hist, void* stream) {
+                      pmc_trace_result* out, double* hist, void* stream) {
   const DPair* d = pair_of(geom, pair, false);
   if (!ctx || !med || !d || !out || !hist) return fail(PMC_ERR_INVALID, "bad argument");
   if (max_scatter < 0 || !(r_reject > 0)) return fail(PMC_ERR_INVALID, "bad tracer limits");
@@ -1600,13 +1768,107 @@ int pmc_trace_lengths(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair
   const float rr = std::isfinite(r_reject) ? static_cast<float>(r_reject) : std::numeric_limits<float>::infinity();
   cudaError_t e = launch_trace_lengths(med->d, *d, seed, photon0, n_photons, rr, max_scatter, l_lo, l_hi, n_bins,
                                        d_out, d_out + 5, ctx->n_sm, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  double raw[5] = {0, 0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(raw, d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(hist, d_out + 5, static_cast<size_t>(n_bins) * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_out);
   CK(e);
+  *out = trace_result(raw);
+  // detected weight of each length bin per emitted photon
+  for (int b = 0; b < n_bins; ++b) hist[b] = raw[3] > 0 ? hist[b] / raw[3] : 0.0;
   return PMC_OK;
+}
+
+int pmc_seed_select(const uint64_t* photon_idx, size_t count, size_t need, uint64_t* out) {
+  if ((count > 0 && photon_idx == nullptr) || (need > 0 && out == nullptr)) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (count == 0 && need > 0) return fail(PMC_ERR_INVALID, "no accepted photon to select from");
+  // the accepted photons with the smallest indices: the first `need` draws of
+  // a sequential tracer, whatever order the GPU found them in
+  std::vector<uint64_t> v(photon_idx, photon_idx + count);
+  std::sort(v.begin(), v.end());
+  for (size_t i = 0; i < need; ++i) out[i] = v[i % count];
+  return PMC_OK;
+}
+
+int pmc_seed_from_tracer(pmc_chains_t ch, uint64_t seed, uint64_t photons_per_round, int max_rounds, double r_reject,
+                         uint64_t* photons_used, void* stream) {
+  if (ch == nullptr) return fail(PMC_ERR_INVALID, "NULL chains");
+  if (photons_per_round == 0 || max_rounds < 1 || !(r_reject > 0))
+    return fail(PMC_ERR_INVALID, "need photons_per_round >= 1, max_rounds >= 1 and r_reject > 0");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const float rr = std::isfinite(r_reject) ? static_cast<float>(r_reject) : std::numeric_limits<float>::infinity();
+  int need_max = 0;
+  for (const DPair& d : ch->h_pairs) need_max = std::max(need_max, d.n_chains);
+  // capacity of one round's accepted indices: twice the largest pair's chains
+  const unsigned int cap_idx = static_cast<unsigned int>(std::max(2 * need_max, 4096));
+  unsigned long long* d_idx = nullptr;
+  unsigned long long* d_sel = nullptr;
+  unsigned int* d_count = nullptr;
+  CK(dalloc(&d_idx, cap_idx));
+  int rc = PMC_OK;
+  cudaError_t e = cudaMalloc(&d_sel, sizeof(unsigned long long) * std::max(need_max, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_count, sizeof(unsigned int));
+  std::vector<uint64_t> got, sel;
+  for (int p = 0; p < ch->n_pairs && e == cudaSuccess && rc == PMC_OK; ++p) {
+    const DPair& d = ch->h_pairs[p];
+    const size_t need = static_cast<size_t>(d.n_chains);
+    if (photons_used) photons_used[p] = 0;
+    if (need == 0) continue;
+    const unsigned long long key = seed + static_cast<unsigned long long>(p);
+    got.clear();
+    unsigned long long photon = 0, per_round = photons_per_round;
+    int rounds = 0;
+    while (rounds < max_rounds && got.size() < need) {
+      unsigned int h = 0;
+      e = cudaMemsetAsync(d_count, 0, sizeof(unsigned int), s);
+      if (e == cudaSuccess)
+        e = launch_seed_count(ch->med->d, d, key, photon, per_round, rr, d.cap - 2, d_idx, cap_idx, d_count,
+                              ch->ctx->n_sm, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) break;
+      if (h > cap_idx && per_round > 1) {
+        per_round = std::max(1ull, per_round / 2);  // overflow: the same photons again, fewer at a time
+        continue;
+      }
+      const size_t old = got.size();
+      got.resize(old + std::min<size_t>(h, cap_idx));
+      if (h > 0)
+        e = cudaMemcpyAsync(got.data() + old, d_idx, sizeof(uint64_t) * (got.size() - old), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      photon += per_round;
+      ++rounds;
+    }
+    if (e != cudaSuccess) break;
+    if (got.empty()) {
+      rc = fail(PMC_ERR_INVALID, "no detected photon for pair " + std::to_string(p) + " after " +
+                                     std::to_string(photon) + " photons");
+      break;
+    }
+    sel.resize(need);
+    rc = pmc_seed_select(got.data(), got.size(), need, sel.data());
+    if (rc != PMC_OK) break;
+    e = cudaMemcpyAsync(d_sel, sel.data(), sizeof(uint64_t) * need, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = launch_seed_record(ch->med->d, d, key, rr, d_sel, d.chain0, static_cast<int>(need), ch->d_chain_base,
+                             ch->d_xyz, ch->d_n, ch->d_status, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // sel is reused by the next pair
+    if (photons_used) photons_used[p] = photon;
+  }
+  // the chains start afresh: step counters, accumulators, status
+  if (e == cudaSuccess && rc == PMC_OK) e = cudaMemsetAsync(ch->d_step, 0, sizeof(unsigned long long) * ch->total, s);
+  if (e == cudaSuccess && rc == PMC_OK)
+    e = cudaMemsetAsync(ch->d_acc, 0, sizeof(double) * ACC_WORDS * static_cast<size_t>(ch->total), s);
+  if (e == cudaSuccess && rc == PMC_OK) e = cudaMemsetAsync(ch->d_any, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_idx);
+  cudaFree(d_sel);
+  cudaFree(d_count);
+  CK(e);
+  return rc;
 }
 
 int pmc_trace_paths(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, int pair, uint64_t seed, uint64_t photon0,

@@ -668,6 +668,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
     const DPair& S = *spair;
     const float zoff = S.zoff;
     const int cap = S.cap;
+    const int cid = static_cast<int>(static_cast<uint32_t>(c) + P.chain_id0);  // global chain index
     int n = P.n[c];
     const unsigned long long step0 = P.step[c];
     if (n < 2 || n > cap || (!kSpill && cap > cap_s)) {
@@ -720,9 +721,9 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
       {
         const unsigned long long tl = step0 + s0 + lane;
         const uint4 ra = philox4x32_10(make_uint4(static_cast<uint32_t>(tl), static_cast<uint32_t>(tl >> 32),
-                                                  static_cast<uint32_t>(c), PUR_STEP_A), key0, key1);
+                                                  static_cast<uint32_t>(c) + P.chain_id0, PUR_STEP_A), key0, key1);
         const uint4 rb = philox4x32_10(make_uint4(static_cast<uint32_t>(tl), static_cast<uint32_t>(tl >> 32),
-                                                  static_cast<uint32_t>(c), PUR_STEP_B), key0, key1);
+                                                  static_cast<uint32_t>(c) + P.chain_id0, PUR_STEP_B), key0, key1);
         const uint32_t um = ra.x >> 9;
         const uint32_t type = um < R.thr_within ? 0u : (um < R.thr_birth ? 2u : 3u);
         uint4 lo = make_uint4((ra.y >> 9) | (type << 24), __float_as_uint(__logf(u01(ra.z))), 0u, 0u);
@@ -779,7 +780,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
             // full-path HMC over the interior vertices (the end vertex, picked
             // with probability 1/(n-1), takes the usual vMF end move below)
             const float gain = hmc_propose<kGen>(M, S, zoff, w, tnx, tny, tnz, hmx, hmy, hmz, n, R.mala_eps,
-                                                 R.hmc_steps, t, c, key0, key1, lane);
+                                                 R.hmc_steps, t, cid, key0, key1, lane);
             float lpo = 0.f;
             for (int q = lane; q < n; q += 32) lpo += w.vt(q) + ((q <= n - 2) ? w.seg(q) : 0.f);
             lpo = warp_sum(lpo);
@@ -810,7 +811,7 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
             const float3 nn = wv * nu + sw * (__uint_as_float(hi.z) * e1 + __uint_as_float(hi.w) * e2);
             const float3 end = cS + (f3(S.c_lo[0], S.c_lo[1], S.c_lo[2]) + S.R * nn);
             const float step = R.sigma * rsqrtf(static_cast<float>(n));
-            const float gain = tree_propose<kGen>(M, S, zoff, w, tnx, tny, tnz, n, end, step, vref, t, c, key0, key1,
+            const float gain = tree_propose<kGen>(M, S, zoff, w, tnx, tny, tnz, n, end, step, vref, t, cid, key0, key1,
                                                   lane);
             float lpo = 0.f;
             for (int q = lane; q < n; q += 32) lpo += w.vt(q) + ((q <= n - 2) ? w.seg(q) : 0.f);
@@ -1088,7 +1089,7 @@ __global__ void init_kernel(const InitParams p) {
     const int kk = n - 2;
     for (int i = 1; i <= kk; ++i) {
       const float fr = static_cast<float>(i) / static_cast<float>(kk + 1);
-      const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(i), 0u, static_cast<uint32_t>(c), PUR_INIT),
+      const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(i), 0u, static_cast<uint32_t>(c) + p.chain_id0, PUR_INIT),
                                     k0, k1);
       float s1, c1, s2, c2;
       const float r1 = sqrtf(-2.0f * logf(u01(r.x)));

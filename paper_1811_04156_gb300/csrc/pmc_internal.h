@@ -54,6 +54,7 @@ struct ChainParams {
   int* any_status;              // OR of all status words
   unsigned int* queue;          // work counter of this launch
   const volatile int* abort_flag;
+  uint32_t chain_id0;           // global index of local chain 0 (Philox counter word of a chain)
   int chain_lo, chain_hi;       // chains [lo, hi) of this launch
   unsigned long long n_steps;
   int smem_cap;                 // vertex capacity of one warp's shared arrays
@@ -98,6 +99,7 @@ struct InitParams {
   double* acc;
   int* status;
   int total;
+  uint32_t chain_id0;           // global index of local chain 0
   int init_kind, init_k;
   float jitter;
   const float* user_xyz;        // device copy, [total][3][stride] absolute
@@ -114,25 +116,60 @@ cudaError_t launch_score(const DMedium& M, const DPair& S, const float* xyz, con
 cudaError_t launch_z2(const DMedium& M, const DPair* pairs, int n_pairs, int n_v, int n_phi, double* out,
                       cudaStream_t s);
 
-struct EstParams {
-  const double* acc;            // [total][ACC_WORDS]
-  const DPair* pairs;
-  const double* z2;             // [n_pairs]
-  const double* bridge_q;       // [n_pairs][2] sums from reference draws (may be null)
-  int n_pairs;
-  double lambda_s, lambda_a;    // homogeneous, for the score
-  int homogeneous;
-  double* out;                  // [n_pairs][EST_WORDS]
+// Per-pair moments of the chain accumulators: sums over chains that add
+// across any split of a pair's chains (layout documented at
+// PMC_MOMENT_WORDS in pathmc.h).  A_k is a chain's sum of the score of
+// parameter k over its recorded states: A_0 = sum_L / ls^2 - (sum_n - 2 N) / ls,
+// A_1 = sum_L / la^2, A_2 = sum_G.
+enum MomWord {
+  MOM_NCHAIN = 0,               // chains
+  MOM_ACC = 1,                  // + AccWord: the accumulator words summed over chains (16 words)
+  MOM_RH_M = 17, MOM_RH_M2 = 18, MOM_RH_VAR = 19, MOM_RH_K = 20,  // R-hat on L over chains with N > 1
+  MOM_N2SQ = 21, MOM_NN2 = 22, MOM_NSQ = 23,                      // sum n2^2, N n2, N^2
+  MOM_ASQ = 24,                 // + k: sum A_k^2
+  MOM_NA = 27,                  // + k: sum N A_k
+  MOM_N2A = 30,                 // + k: sum n2 A_k
+  MOM_A = 33,                   // + k: sum A_k
+  MOM_USED = 36
 };
-enum EstWord {
-  EST_I = 0, EST_SE, EST_REL, EST_PI, EST_Z2, EST_RHAT,
-  EST_ACC0, EST_ACC1, EST_ACC2, EST_ACC3,
-  EST_PROP0, EST_PROP1, EST_PROP2, EST_PROP3,
-  EST_MEAN_N, EST_MEAN_L, EST_NSAMP, EST_ESS, EST_BRIDGE_I, EST_BRIDGE_SE,
-  EST_GRAD0, EST_GRAD1, EST_GRAD2, EST_GRADSE0, EST_GRADSE1, EST_GRADSE2,
-  EST_WORDS
-};
-cudaError_t launch_estimator(const EstParams& p, cudaStream_t s);
+static_assert(MOM_USED <= PMC_MOMENT_WORDS, "moment layout");
+
+// Adds one chain's accumulators (acc[ACC_WORDS]) to a pair's moments
+// (mom[PMC_MOMENT_WORDS]); ls, la: the homogeneous lengths (1 for layered media).
+__host__ __device__ inline void add_chain_moments(const double* acc, double ls, double la, double* mom) {
+  const double N = acc[ACC_NREC];
+  mom[MOM_NCHAIN] += 1.0;
+  for (int k = 0; k < ACC_WORDS; ++k) mom[MOM_ACC + k] += acc[k];
+  if (!(N > 0.0)) return;
+  if (N > 1.0) {
+    const double m = acc[ACC_SUML] / N;
+    const double var = (acc[ACC_SUML2] / N - m * m) * N / (N - 1.0);
+    mom[MOM_RH_M] += m;
+    mom[MOM_RH_M2] += m * m;
+    mom[MOM_RH_VAR] += var > 0.0 ? var : 0.0;
+    mom[MOM_RH_K] += 1.0;
+  }
+  const double n2 = acc[ACC_NDIRECT];
+  mom[MOM_N2SQ] += n2 * n2;
+  mom[MOM_NN2] += N * n2;
+  mom[MOM_NSQ] += N * N;
+  const double bs = 1.0 / ls, ba = 1.0 / la;
+  const double A[3] = {acc[ACC_SUML] * bs * bs - (acc[ACC_SUMN] - 2.0 * N) * bs, acc[ACC_SUML] * ba * ba,
+                       acc[ACC_SUMG]};
+  for (int k = 0; k < 3; ++k) {
+    mom[MOM_ASQ + k] += A[k] * A[k];
+    mom[MOM_NA + k] += N * A[k];
+    mom[MOM_N2A + k] += n2 * A[k];
+    mom[MOM_A + k] += A[k];
+  }
+}
+
+// Per-pair moments of the chains' accumulators (one block per pair, FP64):
+// out[n_pairs][PMC_MOMENT_WORDS].
+cudaError_t launch_moments(const double* acc, const DPair* pairs, int n_pairs, double ls, double la, double* out,
+                           cudaStream_t s);
+// Estimate of one pair from its moments (host; pmc_estimate_from_moments).
+void estimate_of_moments(const double* mom, double z2, pmc_estimate* out, double* grad, double* grad_se);
 
 cudaError_t launch_trace(const DMedium& M, const DPair& S, unsigned long long seed,
                          unsigned long long photon0, unsigned long long n_photons, float r_reject,
@@ -154,6 +191,15 @@ cudaError_t launch_layer_scores(const DMedium& M, const DPair* pairs, const int*
 cudaError_t launch_trace_paths(const DMedium& M, const DPair& S, unsigned long long seed, unsigned long long photon0,
                                unsigned long long n_photons, float r_reject, int max_scatter, int max_paths, int stride,
                                float* out_xyz, int* out_n, unsigned int* count, int n_sm, cudaStream_t s);
+
+// Chain seeding from the tracer (pmc_seed_from_tracer): indices of the
+// accepted photons of a photon range, then each chain's path from its photon.
+cudaError_t launch_seed_count(const DMedium& M, const DPair& S, unsigned long long seed, unsigned long long photon0,
+                              unsigned long long n_photons, float r_reject, int max_scatter, unsigned long long* idx,
+                              unsigned int cap_idx, unsigned int* count, int n_sm, cudaStream_t s);
+cudaError_t launch_seed_record(const DMedium& M, const DPair& S, unsigned long long seed, float r_reject,
+                               const unsigned long long* sel, int chain0, int n, const long long* chain_base,
+                               float* xyz, int* nv, int* status, cudaStream_t s);
 
 // pmc_bridge.cu: reference density q_ref and the geometric bridge.
 // Per pair: qtab[off + n] = log P_ref(n) (n = 0..cap, -inf below 2) and
@@ -214,8 +260,6 @@ cudaError_t launch_length_hist(const DPair* pairs, const int* chain_pair, const 
 
 // pmc_noalloc.cu: allocation-free tracer over up to kNoAllocMaxPairs pairs.
 constexpr int kNoAllocMaxPairs = 128;
-// FP32 FMA and MUFU lane-operations per second of the device (microbenchmark).
-cudaError_t measure_pipes(int n_sm, double* fp32_per_s, double* mufu_per_s, cudaStream_t s);
 
 cudaError_t launch_trace_noalloc(const DMedium& M, const DPair* pairs, int n_pairs, unsigned long long seed,
                                  unsigned long long photon0, unsigned long long n_photons, float r_reject,

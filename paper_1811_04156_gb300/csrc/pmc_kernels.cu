@@ -1,6 +1,7 @@
 // Density, adjoint, score, normalisation, estimator and forward-tracer kernels
 // (Collin, arXiv:1811.04156).
 #include "pmc_internal.h"
+#include "pmc_tracer.cuh"
 
 namespace pmc {
 
@@ -198,253 +199,28 @@ __global__ void __launch_bounds__(256) z2_kernel(const DMedium M, const DPair* _
   if (threadIdx.x == 0) out[blockIdx.x] = vv[0];
 }
 
-// Per-pair reduction of the chain accumulators (one block per pair).
-__global__ void __launch_bounds__(256) estimator_kernel(const EstParams p) {
-  __shared__ double sh[8 * 24];
-  const int pi = blockIdx.x;
-  const DPair S = p.pairs[pi];
-  const int c0 = S.chain0, nc = S.n_chains;
-  // pass 1: totals
-  double v[24];
+// Per-pair moments of the chain accumulators (one block per pair): sums
+// over the pair's chains, each chain's terms from add_chain_moments.
+__global__ void __launch_bounds__(256) moments_kernel(const double* __restrict__ acc, const DPair* __restrict__ pairs,
+                                                      double ls, double la, double* __restrict__ out) {
+  __shared__ double sh[8 * MOM_USED];
+  const DPair S = pairs[blockIdx.x];
+  double v[MOM_USED];
 #pragma unroll
-  for (int k = 0; k < 24; ++k) v[k] = 0.0;
-  for (int c = c0 + threadIdx.x; c < c0 + nc; c += blockDim.x) {
-    const double* a = p.acc + static_cast<size_t>(c) * ACC_WORDS;
-#pragma unroll
-    for (int k = 0; k < ACC_WORDS; ++k) v[k] += a[k];
-    const double N = a[ACC_NREC];
-    if (N > 1.0) {
-      const double m = a[ACC_SUML] / N;
-      const double var = fmax(a[ACC_SUML2] / N - m * m, 0.0) * N / (N - 1.0);
-      v[16] += m;
-      v[17] += m * m;
-      v[18] += var;
-      v[19] += 1.0;
-    }
-  }
-  block_sum<24>(v, sh);
-  const double Ntot = v[ACC_NREC];
-  const double pi_hat = Ntot > 0 ? v[ACC_NDIRECT] / Ntot : 0.0;
-  const double bs = 1.0 / p.lambda_s, ba = 1.0 / p.lambda_a;
-  // mean scores
-  double sbar[3] = {0, 0, 0};
-  if (Ntot > 0) {
-    sbar[0] = (v[ACC_SUML] * bs * bs - (v[ACC_SUMN] - 2.0 * Ntot) * bs) / Ntot;
-    sbar[1] = v[ACC_SUML] * ba * ba / Ntot;
-    sbar[2] = v[ACC_SUMG] / Ntot;
-  }
-  // pass 2: across-chain spreads of pi(n=2) and of the score means
-  double u[4] = {0, 0, 0, 0};
-  for (int c = c0 + threadIdx.x; c < c0 + nc; c += blockDim.x) {
-    const double* a = p.acc + static_cast<size_t>(c) * ACC_WORDS;
-    const double N = a[ACC_NREC];
-    if (N <= 0) continue;
-    const double w = N / Ntot;
-    const double f = a[ACC_NDIRECT] / N;
-    u[0] += w * w * (f - pi_hat) * (f - pi_hat);
-    const double s0 = (a[ACC_SUML] * bs * bs - (a[ACC_SUMN] - 2.0 * N) * bs) / N;
-    const double s1 = a[ACC_SUML] * ba * ba / N;
-    const double s2 = a[ACC_SUMG] / N;
-    u[1] += w * w * (s0 - sbar[0]) * (s0 - sbar[0]);
-    u[2] += w * w * (s1 - sbar[1]) * (s1 - sbar[1]);
-    u[3] += w * w * (s2 - sbar[2]) * (s2 - sbar[2]);
-  }
-  block_sum<4>(u, sh);
+  for (int k = 0; k < MOM_USED; ++k) v[k] = 0.0;
+  for (int c = S.chain0 + threadIdx.x; c < S.chain0 + S.n_chains; c += blockDim.x)
+    add_chain_moments(acc + static_cast<size_t>(c) * ACC_WORDS, ls, la, v);
+  block_sum<MOM_USED>(v, sh);
   if (threadIdx.x != 0) return;
-  double* o = p.out + static_cast<size_t>(pi) * EST_WORDS;
-  const double C = static_cast<double>(nc);
-  const double corr = C > 1 ? C / (C - 1.0) : 1.0;
-  const double var_pi = u[0] * corr;
-  const double z2 = p.z2[pi];
-  const double I = pi_hat > 0 ? z2 / pi_hat : __longlong_as_double(0x7ff8000000000000ll);
-  const double se = pi_hat > 0 ? I * sqrt(var_pi) / pi_hat : I;
-  o[EST_I] = I;
-  o[EST_SE] = se;
-  o[EST_REL] = se / I;
-  o[EST_PI] = pi_hat;
-  o[EST_Z2] = z2;
-  // R-hat over chains on the path length
-  const double m_ch = v[19];
-  double rhat = __longlong_as_double(0x7ff8000000000000ll);
-  if (m_ch > 1) {
-    const double W = v[18] / m_ch;
-    const double mbar = v[16] / m_ch;
-    const double B_over_n = (v[17] / m_ch - mbar * mbar) * m_ch / (m_ch - 1.0);
-    const double nper = Ntot / m_ch;
-    if (W > 0) rhat = sqrt(((nper - 1.0) / nper * W + B_over_n) / W);
-  }
-  o[EST_RHAT] = rhat;
-  for (int k = 0; k < 4; ++k) {
-    const double pr = v[ACC_PROP + k];
-    o[EST_ACC0 + k] = pr > 0 ? v[ACC_ACC + k] / pr : 0.0;
-    o[EST_PROP0 + k] = pr;
-  }
-  o[EST_MEAN_N] = Ntot > 0 ? v[ACC_SUMN] / Ntot : 0.0;
-  o[EST_MEAN_L] = Ntot > 0 ? v[ACC_SUML] / Ntot : 0.0;
-  o[EST_NSAMP] = Ntot;
-  o[EST_ESS] = var_pi > 0 ? pi_hat * (1.0 - pi_hat) / var_pi : 0.0;
-  double bI = __longlong_as_double(0x7ff8000000000000ll), bse = bI;
-  if (p.bridge_q != nullptr && v[ACC_NBRIDGE] > 0) {
-    const double num = p.bridge_q[2 * pi] / fmax(p.bridge_q[2 * pi + 1], 1.0);
-    const double den = v[ACC_BRIDGE] / v[ACC_NBRIDGE];
-    bI = num / den;
-  }
-  o[EST_BRIDGE_I] = bI;
-  o[EST_BRIDGE_SE] = bse;
-  for (int k = 0; k < 3; ++k) {
-    const double vs = u[1 + k] * corr;
-    o[EST_GRAD0 + k] = I * sbar[k];
-    o[EST_GRADSE0 + k] = sqrt(I * I * vs + sbar[k] * sbar[k] * se * se);
-  }
+  double* o = out + static_cast<size_t>(blockIdx.x) * PMC_MOMENT_WORDS;
+#pragma unroll
+  for (int k = 0; k < PMC_MOMENT_WORDS; ++k) o[k] = k < MOM_USED ? v[k] : 0.0;
 }
 
 // ---------------------------------------------------------------------------
-// Forward tracer (appendix, Algorithm 1): one thread per photon.
+// Forward tracer (appendix, "Ray tracer"; the photon itself in pmc_tracer.cuh):
+// one thread per photon.
 // ---------------------------------------------------------------------------
-__device__ float free_path(const DMedium& M, float z_abs, float nz, float tau) {
-  if (M.kind == 0) return tau / M.b;
-  float dL = 0.f;
-  float z = z_abs;
-  int l = layer_of(M, z);
-  for (int guard = 0; guard < 1 << 16; ++guard) {
-    const float b = __ldg(M.lb + l);
-    float dist = __int_as_float(0x7f800000);
-    int next = l;
-    if (nz > 0.f && l < M.n_layers - 1) {
-      dist = (M.z0 + (l + 1) * M.dz - z) / nz;
-      next = l + 1;
-    } else if (nz < 0.f && l > 0) {
-      dist = (M.z0 + l * M.dz - z) / nz;
-      next = l - 1;
-    }
-    dist = fmaxf(dist, 0.f);
-    if (tau <= b * dist) return dL + tau / b;
-    tau -= b * dist;
-    dL += dist;
-    z += dist * nz;
-    l = next;
-  }
-  return dL;
-}
-
-__device__ float ray_sphere(float3 x, float3 nh, float3 c, float R2) {
-  const float3 w = x - c;
-  const float b = dot(w, nh);
-  const float cc = dot(w, w) - R2;
-  const float disc = b * b - cc;
-  if (disc < 0.f) return __int_as_float(0x7f800000);
-  const float s1 = -b - sqrtf(disc);
-  return s1 > 0.f ? s1 : __int_as_float(0x7f800000);
-}
-
-__device__ float sample_cos(const DMedium& M, float u, float umix) {
-  if (M.f_sl > 0.f && umix < M.f_sl) {
-    const float v = powf(u, 1.0f / (M.sl_alpha + 1.0f));
-    return 2.0f * v - 1.0f;
-  }
-  const float g = M.g;
-  if (fabsf(g) < 1e-6f) return 2.0f * u - 1.0f;
-  const float q = (1.0f - g * g) / (1.0f - g + 2.0f * g * u);
-  return fminf(fmaxf((1.0f + g * g - q * q) / (2.0f * g), -1.0f), 1.0f);
-}
-
-// One photon of Algorithm 1 from the source (frame origin): free paths from
-// b(x), absorption weight ln w, detection at the first sensor intersection,
-// rejection beyond r_reject, at most max_scatter scatterings.  With kRecord
-// the vertices (source, scattering points, hit point) are written to
-// (ox, oy, oz) in absolute coordinates.  u_acc is a spare uniform of the
-// detection step (used to thin detected photons by their weight).
-struct PhotonResult {
-  bool hit;
-  float lw;     // ln(w rho) of a detected photon
-  float L;      // path length
-  int nsc;      // scatterings
-  float u_acc;
-};
-
-template <bool kRecord>
-__device__ PhotonResult trace_photon(const DMedium& M, const DPair& S, uint32_t k0, uint32_t k1, unsigned long long ph,
-                                     float r_reject, int max_scatter, float* ox, float* oy, float* oz) {
-  const uint32_t plo = static_cast<uint32_t>(ph), phi = static_cast<uint32_t>(ph >> 32);
-  const float3 c = f3(S.c[0], S.c[1], S.c[2]);
-  uint4 r = philox4x32_10(make_uint4(plo, phi, 0u, PUR_TRACE), k0, k1);
-  float3 x = f3(0.f, 0.f, 0.f);
-  float3 nh;
-  {
-    float sp, cp;
-    sincospif(2.0f * u01(r.y), &sp, &cp);
-    if (S.emission != 0) {
-      const float u0 = u01(r.x);
-      const float ww = 1.0f + logf(fmaf(1.0f - u0, expf(-2.0f * S.kappa), u0)) / S.kappa;
-      const float sw = sqrtf(fmaxf(0.f, 1.0f - ww * ww));
-      const float3 d = f3(S.dir[0], S.dir[1], S.dir[2]);
-      float3 e1, e2;
-      onb(d, e1, e2);
-      nh = ww * d + sw * (cp * e1 + sp * e2);
-    } else {
-      const float ww = 2.0f * u01(r.x) - 1.0f;
-      const float sw = sqrtf(fmaxf(0.f, 1.0f - ww * ww));
-      nh = f3(sw * cp, sw * sp, ww);
-    }
-  }
-  if (kRecord) {
-    ox[0] = S.org[0];
-    oy[0] = S.org[1];
-    oz[0] = S.org[2];
-  }
-  PhotonResult res{false, 0.f, 0.f, 0, 1.f};
-  float lnw = 0.f, L = 0.f;
-  for (int i = 0; i <= max_scatter; ++i) {
-    r = philox4x32_10(make_uint4(plo, phi, static_cast<uint32_t>(i + 1), PUR_TRACE), k0, k1);
-    const float tau = -logf(u01(r.x));
-    const float dL = free_path(M, x.z + S.zoff, nh.z, tau);
-    const float dist = ray_sphere(x, nh, c, S.R2);
-    const float go = fminf(dist, dL);
-    const float3 end = x + go * nh;
-    float ta, tb;
-    seg_tau(M, x.z + S.zoff, end.z + S.zoff, go, ta, tb);
-    lnw -= ta;
-    if (dist < dL) {
-      float lw = lnw;
-      if (S.rho != 0) {
-        const float3 nu = sensor_normal(S, end);
-        const float xx = dot(nu, f3(S.rho_hat[0], S.rho_hat[1], S.rho_hat[2]));
-        lw += fmaf(3.0f, xx, -1.0f) - logf(coshf(fmaf(2.0f, xx, 0.7f)));
-      }
-      if (kRecord) {
-        ox[i + 1] = end.x + S.org[0];
-        oy[i + 1] = end.y + S.org[1];
-        oz[i + 1] = end.z + S.org[2];
-      }
-      res.hit = true;
-      res.lw = lw;
-      res.L = L + dist;
-      res.nsc = i;
-      res.u_acc = u01(r.y);
-      return res;
-    }
-    const float3 rel = x - c;
-    if (dot(rel, rel) > r_reject * r_reject) break;
-    if (i == max_scatter) break;
-    x = end;
-    L += dL;
-    if (kRecord) {
-      ox[i + 1] = x.x + S.org[0];
-      oy[i + 1] = x.y + S.org[1];
-      oz[i + 1] = x.z + S.org[2];
-    }
-    const float cs = sample_cos(M, u01(r.y), u01(r.w));
-    const float sn = sqrtf(fmaxf(0.f, 1.0f - cs * cs));
-    float sp, cp;
-    sincospif(2.0f * u01(r.z), &sp, &cp);
-    float3 e1, e2;
-    onb(nh, e1, e2);
-    nh = cs * nh + sn * (cp * e1 + sp * e2);
-    nh = rsqrtf(dot(nh, nh)) * nh;
-  }
-  return res;
-}
-
 __global__ void __launch_bounds__(256) trace_kernel(const DMedium M, const DPair S, unsigned long long seed,
                                                     unsigned long long photon0, unsigned long long n_photons,
                                                     float r_reject, int max_scatter, double* __restrict__ out5,
@@ -597,9 +373,10 @@ cudaError_t launch_z2(const DMedium& M, const DPair* pairs, int n_pairs, int n_v
   return cudaGetLastError();
 }
 
-cudaError_t launch_estimator(const EstParams& p, cudaStream_t s) {
-  if (p.n_pairs == 0) return cudaSuccess;
-  estimator_kernel<<<p.n_pairs, 256, 0, s>>>(p);
+cudaError_t launch_moments(const double* acc, const DPair* pairs, int n_pairs, double ls, double la, double* out,
+                           cudaStream_t s) {
+  if (n_pairs <= 0) return cudaSuccess;
+  moments_kernel<<<n_pairs, 256, 0, s>>>(acc, pairs, ls, la, out);
   return cudaGetLastError();
 }
 
@@ -642,6 +419,67 @@ cudaError_t launch_layer_scores(const DMedium& M, const DPair* pairs, const int*
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   chain_layer_score_kernel<<<(total + 3) / 4, 128, smem, s>>>(M, pairs, chain_pair, chain_base, xyz, n, total, sums);
+  return cudaGetLastError();
+}
+
+// Chain seeding, first pass: the indices of the photons in [photon0,
+// photon0 + n_photons) whose detection survives the thinning by w rho (the
+// same test as trace_paths_kernel), in any order, into idx[0 .. cap_idx);
+// *count receives how many there were (also beyond cap_idx).
+__global__ void __launch_bounds__(256) seed_count_kernel(const DMedium M, const DPair S, unsigned long long seed,
+                                                         unsigned long long photon0, unsigned long long n_photons,
+                                                         float r_reject, int max_scatter,
+                                                         unsigned long long* __restrict__ idx, unsigned int cap_idx,
+                                                         unsigned int* __restrict__ count) {
+  const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  const unsigned long long gstride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+  for (unsigned long long q = blockIdx.x * blockDim.x + threadIdx.x; q < n_photons; q += gstride) {
+    const PhotonResult pr = trace_photon<false>(M, S, k0, k1, photon0 + q, r_reject, max_scatter, nullptr, nullptr,
+                                                nullptr);
+    if (!pr.hit || !(pr.u_acc < expf(pr.lw))) continue;
+    const unsigned int slot = atomicAdd(count, 1u);
+    if (slot < cap_idx) idx[slot] = photon0 + q;
+  }
+}
+
+// Chain seeding, second pass: chain chain0 + i of pair S (i < n) takes the
+// path of photon sel[i], traced again (the same photon gives the same path)
+// and written straight into the chain's block in the source frame.
+__global__ void __launch_bounds__(128) seed_record_kernel(const DMedium M, DPair S, unsigned long long seed,
+                                                          float r_reject, const unsigned long long* __restrict__ sel,
+                                                          int chain0, int n, const long long* __restrict__ chain_base,
+                                                          float* __restrict__ xyz, int* __restrict__ nv,
+                                                          int* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = chain0 + i;
+  S.org[0] = S.org[1] = S.org[2] = 0.f;  // record frame coordinates
+  const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  float* gx = xyz + chain_base[c];
+  const PhotonResult pr = trace_photon<true>(M, S, k0, k1, sel[i], r_reject, S.cap - 2, gx, gx + S.cap,
+                                             gx + 2 * S.cap);
+  nv[c] = pr.hit ? pr.nsc + 2 : 2;
+  status[c] = pr.hit ? 0 : ST_BAD_N;
+}
+
+cudaError_t launch_seed_count(const DMedium& M, const DPair& S, unsigned long long seed, unsigned long long photon0,
+                              unsigned long long n_photons, float r_reject, int max_scatter, unsigned long long* idx,
+                              unsigned int cap_idx, unsigned int* count, int n_sm, cudaStream_t s) {
+  if (n_photons == 0) return cudaSuccess;
+  unsigned long long blocks = (n_photons + 255) / 256;
+  const unsigned long long maxb = static_cast<unsigned long long>(n_sm) * 8ull;
+  if (blocks > maxb) blocks = maxb;
+  seed_count_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(M, S, seed, photon0, n_photons, r_reject,
+                                                                  max_scatter, idx, cap_idx, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_record(const DMedium& M, const DPair& S, unsigned long long seed, float r_reject,
+                               const unsigned long long* sel, int chain0, int n, const long long* chain_base,
+                               float* xyz, int* nv, int* status, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  seed_record_kernel<<<(n + 127) / 128, 128, 0, s>>>(M, S, seed, r_reject, sel, chain0, n, chain_base, xyz, nv,
+                                                     status);
   return cudaGetLastError();
 }
 

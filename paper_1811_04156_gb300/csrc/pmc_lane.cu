@@ -174,9 +174,9 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, float* co
     }
     const unsigned long long t = step0 + s;
     const uint4 ra = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32),
-                                              static_cast<uint32_t>(c), PUR_STEP_A), key0, key1);
+                                              static_cast<uint32_t>(c) + P.chain_id0, PUR_STEP_A), key0, key1);
     const uint4 rb = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32),
-                                              static_cast<uint32_t>(c), PUR_STEP_B), key0, key1);
+                                              static_cast<uint32_t>(c) + P.chain_id0, PUR_STEP_B), key0, key1);
     const uint32_t um = ra.x >> 9;
     const uint32_t v23 = ra.y >> 9;
     const float logu = __logf(u01(ra.z));

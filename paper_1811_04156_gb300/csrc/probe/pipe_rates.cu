@@ -1,6 +1,8 @@
-// Pipe-rate microbenchmark (pmc_measure_pipes): the FP32 FMA and the MUFU
-// (special-function unit) lane-operation rates of the device, measured rather
-// than taken from unit counts, for the lane-op roofline of the chain kernel.
+// Pipe-rate microbenchmark of the benchmark harness (a library of its own,
+// libpmcprobe.so, outside the product library and its C ABI): the FP32 FMA
+// and the MUFU (special-function unit) lane-operation rates of the device,
+// measured rather than taken from unit counts, for the lane-op roofline of
+// the chain kernels.
 //
 // Each thread runs 8 independent dependency chains so that the pipes, not
 // their latency, bind; the grid fills every SM with 8 CTAs of 256 threads.
@@ -8,9 +10,7 @@
 // chain and iteration (two MUFU operations; the value stays ~x).
 #include <algorithm>
 
-#include "pmc_internal.h"
-
-namespace pmc {
+#include <cuda_runtime.h>
 
 namespace {
 
@@ -63,8 +63,6 @@ __global__ void __launch_bounds__(kThreads) mufu_rate_kernel(int iters, float* _
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-}  // namespace
-
 cudaError_t measure_pipes(int n_sm, double* fp32_per_s, double* mufu_per_s, cudaStream_t s) {
   const int blocks = n_sm * 8;
   float* d_out = nullptr;
@@ -100,4 +98,19 @@ cudaError_t measure_pipes(int n_sm, double* fp32_per_s, double* mufu_per_s, cuda
   return cudaSuccess;
 }
 
-}  // namespace pmc
+}  // namespace
+
+// out[0] = FP32 fused multiply-add lane-operations per second, out[1] = MUFU
+// lane-operations per second of CUDA device `device` (8 independent
+// dependency chains per thread, 8 CTAs of 256 threads per SM, one untimed and
+// one timed launch of each kernel, CUDA events on `stream`).  Allocates and
+// frees a 1.2 MB device buffer.  Returns 0, or the cudaError_t of the first
+// failing call.  Synchronises `stream`.
+extern "C" __attribute__((visibility("default"))) int pmcprobe_measure_pipes(int device, double* out, void* stream) {
+  if (out == nullptr) return static_cast<int>(cudaErrorInvalidValue);
+  cudaError_t e = cudaSetDevice(device);
+  int n_sm = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = measure_pipes(n_sm, &out[0], &out[1], static_cast<cudaStream_t>(stream));
+  return static_cast<int>(e);
+}

@@ -1,5 +1,7 @@
-"""Multi-rank bookkeeping of bench.py on CPU (gloo, world size 2): replicas
-get distinct Philox keys and the step time is the maximum over ranks."""
+"""Multi-rank bookkeeping of bench.py on CPU (gloo, world size 2): the ranks
+hold the two halves of the weak-scaled chain set (one pair of 2 x 65,536
+chains, windows of global chain indices) and the step time is the maximum
+over ranks."""
 import os
 import socket
 import sys
@@ -26,7 +28,11 @@ def _worker(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     ms = 100.0 + 50.0 * rank
     out = bench.max_over_ranks(ms, dist)
-    q.put((rank, out, bench.rank_seed(7, rank)))
+    from paper_1811_04156_gb300 import api, build
+    build.build()
+    args = bench.parse_args([])
+    sc = bench.scene_for(args, world)
+    q.put((rank, out, api.shard_range(sc.pairs, rank, world), sc.total_chains))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -45,7 +51,8 @@ def test_two_rank_time_reduction_and_seeds():
         assert p.exitcode == 0
     res.sort()
     assert [r[1] for r in res] == [150.0, 150.0]
-    assert res[0][2] != res[1][2]
+    assert res[0][3] == res[1][3] == 2 * 65_536
+    assert res[0][2] == (0, 65_536) and res[1][2] == (65_536, 131_072)
 
 
 def test_single_rank_needs_no_collective():

@@ -1,0 +1,70 @@
+"""The sharded form on one GPU: a chain set split into windows of global
+chain indices (pmc_shard_range over 2 and 3 ranks, the windows run one
+after the other on this GPU, never concurrently) evolves every chain
+exactly as the whole set does, and the summed per-pair moments give the
+whole set's estimates (chains and pairs are independent: section
+"Implementation")."""
+import numpy as np
+import pytest
+
+from paper_1811_04156_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1811_04156_gb300 import build
+    build.build()
+    from paper_1811_04156_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    return api.Context(0)
+
+
+@pytest.mark.parametrize("layout,world", [(S.LAYOUT_WARP, 2), (S.LAYOUT_LANE, 3)])
+def test_windows_replay_the_whole_set(api, ctx, layout, world):
+    sc = S.batched_small(n_chains=256, n_steps=3000)
+    if layout == S.LAYOUT_LANE:
+        sc.pairs = [p for p in sc.pairs if p.cap == 3] + [S.Pair(0, 4, 256, 64)]
+    sc.run.layout = layout
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    shape = dict(warps_per_block=2, smem_window=16 if layout == S.LAYOUT_LANE else 0)
+    whole = api.Chains(ctx, medium, geom, sc.run, **shape)
+    whole.run_steps(3000)
+    xw, nw, sw = whole.read_states()
+    aw = whole.read_accumulators()
+    est_w = whole.read_estimator()
+    mom = np.zeros((len(sc.pairs), 40))
+    for r in range(world):
+        lo, hi = api.shard_range(sc.pairs, r, world)
+        part = api.Chains(ctx, medium, geom, sc.run, chain_window=(lo, hi), **shape)
+        assert part.total == hi - lo
+        part.run_steps(3000)
+        x, n, s = part.read_states()
+        assert np.array_equal(n, nw[lo:hi]) and np.array_equal(s, sw[lo:hi])
+        assert np.array_equal(x, xw[lo:hi])
+        assert np.array_equal(part.read_accumulators(), aw[lo:hi])
+        mom += part.read_moments()
+        part.close()
+    est, _, _ = api.estimate_from_moments(mom, whole.pair_z2())
+    for a, b in zip(est, est_w):
+        for k in ("intensity", "std_err", "rhat", "mean_n", "n_samples"):
+            assert np.isclose(a[k], b[k], rtol=1e-11, atol=0), (k, a[k], b[k])
+
+
+def test_window_errors(api, ctx):
+    from paper_1811_04156_gb300._lib import PathmcError
+    sc = S.plain(n_chains=64)
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    for win in ((10, 10), (-1, 5), (0, 65), (40, 30)):
+        with pytest.raises(PathmcError):
+            api.Chains(ctx, medium, geom, sc.run, chain_window=win)

@@ -99,6 +99,26 @@ def test_detection_probability_is_a_probability(oracle_lib):
     assert all(b > a for a, b in zip(vals, vals[1:]))  # the preferred direction is the most sensitive
 
 
+def test_detection_probability_values(oracle_lib):
+    """rho at the preferred direction, across it and against it, from the
+    closed form of Eq. detection_prob (tests/golden/detection_prob.txt): a
+    changed constant, a swapped sign or cosh for cos fails one of the three."""
+    O = oracle_lib
+    rows = [list(map(float, l.split())) for l in open(os.path.join(GOLDEN, "detection_prob.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for rho_hat in ((0.0, -1.0, 0.0), (0.6, 0.0, 0.8)):
+        d = O.sensor(S.Sensor(rho=S.RHO_PAPER, rho_hat=rho_hat))
+        h = np.asarray(rho_hat)
+        # a second direction normal to rho_hat for the x = 0 case
+        perp = np.cross(h, [0.0, 0.0, 1.0] if abs(h[2]) < 0.9 else [1.0, 0.0, 0.0])
+        perp /= np.linalg.norm(perp)
+        for x, want in rows:
+            nu = h if x > 0 else (-h if x < 0 else perp)
+            got = math.exp(O.log_rho(d, list(nu)))
+            assert abs(got / want - 1) < 1e-8, (rho_hat, x, got, want)
+
+
 def test_layered_depths_brute_force(oracle_lib):
     O = oracle_lib
     rng = np.random.default_rng(3)

@@ -1,103 +1,52 @@
-"""Host logic of the tracer seeding (api.seed_from_tracer), with a stand-in
-for the GPU tracer: the seeds must be an unbiased subset of every accepted
-path of the traced photon range.
+"""Host logic of the tracer seeding (pmc_seed_select in the C library; no
+GPU): the seeds are the accepted photons with the smallest indices, i.e. the
+first accepted draws of a sequential tracer, whatever order the GPU found
+them in, reused cyclically when a pair has more chains than accepted paths.
 
-The GPU buffer of pmc_trace_paths keeps the paths whose photons finish first
-when a launch finds more than it holds; seeding therefore re-traces an
-overflowing round with half the photons (the same photon indices), keeps every
-path of each round that fits, and gives the chains a seeded random subset.
-The stand-in detects photon q when q % 7 == 0 and, on overflow, keeps the
-longest paths first (a deliberately biased buffer)."""
-import types
-
+The GPU finds accepted photons in the order their threads finish, and short
+paths finish first: taking the first-found ones would favour few-scattering
+paths.  The stand-in order below is exactly that biased order."""
 import numpy as np
 import pytest
-import torch
 
-from paper_1811_04156_gb300 import api
-
-
-def _detected(q):
-    return q % 7 == 0
+from paper_1811_04156_gb300 import build
 
 
-def _fake_trace_paths(calls):
-    def trace_paths(ctx, medium, geom, pair, seed, n_photons, max_paths, photon0=0, stride=None, r_reject=None,
-                    **kw):
-        qs = [q for q in range(photon0, photon0 + n_photons) if _detected(q)]
-        calls.append((pair, photon0, n_photons, len(qs), max_paths))
-        # biased buffer: longest paths first, truncated at max_paths
-        qs_kept = sorted(qs, key=lambda q: -(q % 5))[:max_paths]
-        xyz = torch.zeros((3, len(qs_kept), stride), dtype=torch.float32)
-        n = torch.zeros(len(qs_kept), dtype=torch.int32)
-        for i, q in enumerate(qs_kept):
-            xyz[0, i, 0] = float(q)           # the photon index, read back by the test
-            n[i] = 2 + q % 5
-        return xyz, n, len(qs)
-    return trace_paths
+@pytest.fixture(scope="module")
+def api():
+    build.build()
+    from paper_1811_04156_gb300 import api as A
+    return A
 
 
-class _FakeChains:
-    def __init__(self, n_chains, stride=8):
-        pair = types.SimpleNamespace(n_chains=n_chains)
-        self.geom = types.SimpleNamespace(pairs=[pair], max_cap=stride)
-        self.total = n_chains
-        self.ctx = self.medium = None
-        self.states = None
-
-    def set_states(self, xyz, n):
-        self.states = (np.array(xyz), np.array(n))
+def _finish_order(photons, scatterings):
+    """Accepted photon indices in the order a GPU would report them: fewest
+    scatterings (shortest tracing) first."""
+    return photons[np.argsort(scatterings, kind="stable")]
 
 
-@pytest.fixture
-def fake(monkeypatch):
-    calls = []
-    monkeypatch.setattr(api, "trace_paths", _fake_trace_paths(calls))
-    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a, **k: types.SimpleNamespace(synchronize=lambda: None))
-    return calls
+def test_seeds_are_the_first_accepted_photons(api):
+    rng = np.random.default_rng(4)
+    accepted = np.sort(rng.choice(10_000_000, size=5000, replace=False)).astype(np.uint64)
+    scat = rng.poisson(6.0, size=accepted.size)
+    found = _finish_order(accepted, scat)
+    need = 1200
+    sel = api.seed_select(found, need)
+    assert np.array_equal(sel, accepted[:need])
+    # the first-found paths would have been the short ones; the selection is not
+    first_found = scat[np.argsort(scat, kind="stable")][:need]
+    chosen = scat[:need]
+    assert first_found.mean() < 4.0 < chosen.mean()
 
 
-def test_overflowing_rounds_are_retraced_with_fewer_photons(fake):
-    ch = _FakeChains(50)
-    used = api.seed_from_tracer(ch, seed=3, photons_per_round=1024)
-    kept = [c for c in fake if c[3] <= c[4]]
-    # every kept round fits the buffer, and the kept rounds tile [0, photons traced)
-    start = 0
-    for _, photon0, n_photons, found, cap in kept:
-        assert photon0 == start and found <= cap
-        start += n_photons
-    assert start == used[0]
-    # an overflowing round is retried from the same first photon with half the photons
-    for a, b in zip(fake, fake[1:]):
-        if a[3] > a[4]:
-            assert b[1] == a[1] and b[2] == a[2] // 2
+def test_few_accepted_photons_are_reused_cyclically(api):
+    accepted = np.array([90, 7, 55, 3], dtype=np.uint64)
+    sel = api.seed_select(accepted, 10)
+    assert sel.tolist() == [3, 7, 55, 90, 3, 7, 55, 90, 3, 7]
 
 
-def test_seeds_are_a_random_subset_of_every_accepted_path(fake):
-    n_chains = 50
-    ch = _FakeChains(n_chains)
-    used = api.seed_from_tracer(ch, seed=3, photons_per_round=1024)
-    xyz, n = ch.states
-    q = xyz[:, 0, 0].astype(int)
-    every = [p for p in range(used[0]) if _detected(p)]
-    assert len(every) >= n_chains
-    assert len(set(q)) == n_chains and set(q) <= set(every)
-    assert np.array_equal(n, 2 + q % 5)
-    # the biased buffer would have kept only the longest paths; the subset does not favour them
-    short = np.mean(q % 5 <= 1)
-    assert 0.15 < short < 0.65, short
-    # the subset is seeded: the same seed gives the same seeds
-    ch2 = _FakeChains(n_chains)
-    api.seed_from_tracer(ch2, seed=3, photons_per_round=1024)
-    assert np.array_equal(ch2.states[0], xyz)
-
-
-def test_few_detections_are_reused_cyclically(fake):
-    ch = _FakeChains(40)
-    used = api.seed_from_tracer(ch, seed=1, photons_per_round=21, max_rounds=2)
-    xyz, _ = ch.states
-    q = xyz[:, 0, 0].astype(int)
-    every = [p for p in range(used[0]) if _detected(p)]
-    assert len(every) < 40
-    assert set(q) == set(every)
-    assert np.array_equal(q[: len(every)], q[len(every): 2 * len(every)])
+def test_selection_errors(api):
+    from paper_1811_04156_gb300._lib import PathmcError
+    with pytest.raises(PathmcError):
+        api.seed_select(np.zeros(0, dtype=np.uint64), 3)
+    assert api.seed_select(np.zeros(0, dtype=np.uint64), 0).size == 0
