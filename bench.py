@@ -557,16 +557,20 @@ def ours(args):
 def other_configs(api, ctx):
     """Proposals/s of the other workloads, each a timed launch after a warm-up
     launch of the same chain set (autotuned launch shapes): the batched uneven
-    pairs under one CUDA graph, the gradients workload (MALA moves and score
+    pairs under one CUDA graph (one launch per cap class, and one persistent
+    launch for every cap), the gradients workload (MALA moves and score
     accumulation) and the layered string of sensors."""
     import torch
     from paper_1811_04156_gb300 import scenes as S
+    from paper_1811_04156_gb300._lib import PMC_FLAG_ONE_LAUNCH
     out = {}
-    for name, sc in (("batched", S.batched(n_steps=5000)), ("gradients", S.gradients(n_steps=10_000)),
-                     ("layered", S.layered(n_steps=5000))):
+    for name, sc, flags in (("batched", S.batched(n_steps=5000), 0),
+                            ("batched_one_launch", S.batched(n_steps=5000), PMC_FLAG_ONE_LAUNCH),
+                            ("gradients", S.gradients(n_steps=10_000), 0),
+                            ("layered", S.layered(n_steps=5000), 0)):
         medium = api.Medium(ctx, sc.medium)
         geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
-        ch = api.Chains(ctx, medium, geom, sc.run)
+        ch = api.Chains(ctx, medium, geom, sc.run, flags=flags)
         ch.run_steps(sc.run.n_steps)
         ch.read_estimator()
         ch.reset()
@@ -578,7 +582,8 @@ def other_configs(api, ctx):
         est = ch.read_estimator()
         ms = e0.elapsed_time(e1)
         props = sc.total_chains * sc.run.n_steps
-        out[name] = {"workload": WORKLOAD_TEXT[name], "chains": sc.total_chains, "steps_per_chain": sc.run.n_steps,
+        out[name] = {"workload": WORKLOAD_TEXT[sc.name] + (", one persistent launch for every cap" if flags else ""),
+                     "chains": sc.total_chains, "steps_per_chain": sc.run.n_steps,
                      "proposals_per_s": props / (ms / 1e3), "ms": ms, "launch": ch.launch_info(),
                      "mean_n": sum(e["mean_n"] * e["n_samples"] for e in est) / max(sum(e["n_samples"] for e in est),
                                                                                      1.0)}

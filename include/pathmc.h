@@ -80,6 +80,9 @@ extern "C" {
 
 #define PMC_FLAG_GRADIENTS 1   /* accumulate score terms for pmc_grad_estimator */
 #define PMC_FLAG_NO_GRAPH 2    /* launch kernels directly instead of replaying a CUDA graph */
+#define PMC_FLAG_ONE_LAUNCH 4  /* every chain in one persistent launch (one work queue, longest vertex caps
+                                  first, one shared window with global spill for longer caps) instead of
+                                  one launch per vertex-cap class (64, 128, 256, 512, 1024) */
 
 #define PMC_MOVE_INTERIOR 0    /* Gaussian perturbation or MALA of an interior vertex */
 #define PMC_MOVE_END 1         /* vMF step of the end vertex on the sensor sphere */

@@ -17,6 +17,7 @@ ERRORS = {1: "PMC_ERR_INVALID", 2: "PMC_ERR_OOM", 3: "PMC_ERR_CUDA", 4: "PMC_ERR
           5: "PMC_ERR_ABORTED", 6: "PMC_ERR_NO_DEVICE"}
 PMC_FLAG_GRADIENTS = 1
 PMC_FLAG_NO_GRAPH = 2
+PMC_FLAG_ONE_LAUNCH = 4
 PMC_LAYOUT_AUTO, PMC_LAYOUT_WARP, PMC_LAYOUT_LANE = 0, 1, 2
 PMC_ACC_WORDS = 16
 PMC_MOMENT_WORDS = 40

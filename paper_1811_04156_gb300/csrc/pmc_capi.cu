@@ -837,21 +837,24 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     }
   }
   ch->xyz_floats = off;
-  // processing order: by cap class, longest caps first inside a class
+  // processing order: by cap class, longest caps first inside a class (one
+  // launch: every chain in one class, longest caps first)
+  const bool one_launch = (r->flags & PMC_FLAG_ONE_LAUNCH) != 0;
+  auto class_key = [&](int cap) { return one_launch ? 0 : class_of(cap); };
   std::vector<int> order(T);
   for (int c = 0; c < T; ++c) order[c] = c;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     const int ca = ch->h_pairs[ch->h_pair_of[a]].cap, cb = ch->h_pairs[ch->h_pair_of[b]].cap;
-    const int ka = class_of(ca), kb = class_of(cb);
+    const int ka = class_key(ca), kb = class_key(cb);
     if (ka != kb) return ka < kb;
     return ca > cb;
   });
   for (int lo = 0; lo < T;) {
-    const int k = class_of(ch->h_pairs[ch->h_pair_of[order[lo]]].cap);
+    const int k = class_key(ch->h_pairs[ch->h_pair_of[order[lo]]].cap);
     int hi = lo;
     int maxcap = 0;
     double max_n = 0.0;
-    while (hi < T && class_of(ch->h_pairs[ch->h_pair_of[order[hi]]].cap) == k) {
+    while (hi < T && class_key(ch->h_pairs[ch->h_pair_of[order[hi]]].cap) == k) {
       const DPair& d = ch->h_pairs[ch->h_pair_of[order[hi]]];
       maxcap = std::max(maxcap, d.cap);
       const double dx = (static_cast<double>(d.c[0]) + d.c_lo[0]) - d.src[0];

@@ -68,3 +68,25 @@ def test_window_errors(api, ctx):
     for win in ((10, 10), (-1, 5), (0, 65), (40, 30)):
         with pytest.raises(PathmcError):
             api.Chains(ctx, medium, geom, sc.run, chain_window=win)
+
+
+def test_one_launch_replays_the_per_class_launches(api, ctx):
+    """PMC_FLAG_ONE_LAUNCH (every chain of an uneven batch in one persistent
+    launch, longest caps first) runs the same Markov chains as one launch per
+    vertex-cap class: identical states, counts and estimates."""
+    from paper_1811_04156_gb300._lib import PMC_FLAG_ONE_LAUNCH
+    sc = S.batched_small(n_chains=256, n_steps=2000)
+    sc.run.layout = S.LAYOUT_WARP
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    per_class = api.Chains(ctx, medium, geom, sc.run, warps_per_block=2)
+    one = api.Chains(ctx, medium, geom, sc.run, warps_per_block=2, flags=PMC_FLAG_ONE_LAUNCH)
+    assert len(per_class.launch_info()) == 3 and len(one.launch_info()) == 1
+    for ch in (per_class, one):
+        ch.run_steps(2000)
+    xa, na, sa = per_class.read_states()
+    xb, nb, sb = one.read_states()
+    assert np.array_equal(na, nb) and np.array_equal(sa, sb) and np.array_equal(xa, xb)
+    assert np.array_equal(per_class.read_accumulators(), one.read_accumulators())
+    for a, b in zip(per_class.read_estimator(), one.read_estimator()):
+        assert a["intensity"] == b["intensity"] and a["std_err"] == b["std_err"]
