@@ -43,7 +43,8 @@ class Medium(C.Structure):
     _fields_ = [("kind", C.c_int), ("lambda_s", C.c_double), ("lambda_a", C.c_double),
                 ("g", C.c_double), ("f_sl", C.c_double), ("z0", C.c_double), ("dz", C.c_double),
                 ("n_layers", C.c_int), ("lambda_s_layers", C.POINTER(C.c_double)),
-                ("lambda_a_layers", C.POINTER(C.c_double))]
+                ("lambda_a_layers", C.POINTER(C.c_double)), ("lambda0", C.c_double), ("k_s", C.c_double),
+                ("k_a", C.c_double)]
 
 
 class Source(C.Structure):
@@ -61,7 +62,9 @@ class Run(C.Structure):
                 ("p_death", C.c_double), ("within", C.c_int), ("sigma", C.c_double),
                 ("mala_step", C.c_double), ("kappa_end", C.c_double), ("burn_in", C.c_uint64),
                 ("thin_bridge", C.c_uint32), ("gradients", C.c_int), ("beta_min", C.c_double),
-                ("hmc_steps", C.c_int), ("toy_s", C.c_double), ("toy_w", C.POINTER(C.c_double))]
+                ("hmc_steps", C.c_int), ("toy_s", C.c_double), ("toy_w", C.POINTER(C.c_double)),
+                ("n_lambda", C.c_int), ("lambda_nm", C.POINTER(C.c_double)), ("spectrum", C.POINTER(C.c_double)),
+                ("sigma_lambda", C.c_double)]
 
 
 class Acc(C.Structure):
@@ -140,6 +143,12 @@ def lib():
                                              _dp, _ip, C.POINTER(Acc), _dp, _dp, C.c_int]
             L.or_run_chains_diag.argtypes = [M, S, D, R, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint64,
                                              _dp, _ip, C.POINTER(Acc), _dp, _dp, _dp, C.c_int]
+            L.or_run_chains_lam.argtypes = [M, S, D, R, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_uint64,
+                                            _dp, _ip, _dp, C.POINTER(Acc), _dp, _dp, _dp, C.c_int]
+            L.or_medium_at.argtypes = [M, C.c_double, M]
+            L.or_log_spectrum.argtypes = [R, C.c_double]; L.or_log_spectrum.restype = C.c_double
+            L.or_spectrum_quantile.argtypes = [R, C.c_double]; L.or_spectrum_quantile.restype = C.c_double
+            L.or_init_lambda.argtypes = [R, C.c_int, C.c_uint32, _dp]
             _lib = L
     return _lib
 
@@ -174,6 +183,9 @@ def medium(m) -> Medium:
         out._keep = (a, b)
     else:
         out.n_layers = 0
+    out.lambda0 = float(getattr(m, "lambda0", 0.0))
+    out.k_s = float(getattr(m, "k_s", 0.0))
+    out.k_a = float(getattr(m, "k_a", 0.0))
     return out
 
 
@@ -219,6 +231,15 @@ def run(r, sensor_radius: float) -> Run:
     out.gradients = int(bool(r.gradients))
     out.beta_min = 0.01
     out.hmc_steps = int(getattr(r, "hmc_steps", 10))
+    nm = getattr(r, "spectrum_nm", None)
+    if nm is not None and len(nm) >= 2:
+        x = np.ascontiguousarray(nm, dtype=np.float64)
+        y = np.ascontiguousarray(r.spectrum, dtype=np.float64)
+        out.n_lambda = len(x)
+        out.lambda_nm = _ptr(x)
+        out.spectrum = _ptr(y)
+        out.sigma_lambda = float(r.sigma_lambda)
+        out._keep = (x, y)
     return out
 
 
@@ -493,6 +514,11 @@ class Chains:
         self.n = np.zeros(self.n_chains, dtype=np.int32)
         self.acc = (Acc * self.n_chains)()
         self.step = 0
+        # the chains' wavelengths when the run samples them (section "Discussion")
+        self.lam = None
+        if self.r.n_lambda >= 2:
+            self.lam = np.zeros(self.n_chains)
+            lib().or_init_lambda(C.byref(self.r), self.n_chains, self.chain_offset, _ptr(self.lam))
         init = scene_run.init if init is None else init
         if user_xyz is not None:
             for c in range(self.n_chains):
@@ -515,11 +541,15 @@ class Chains:
         (then the return value is the pair (margins, shortest segments))."""
         mm = np.full(self.n_chains, np.inf) if (margins or hmc_seg) else None
         hs = np.full(self.n_chains, np.inf) if hmc_seg else None
-        lib().or_run_chains_diag(C.byref(self.m), C.byref(self.s), C.byref(self.d), C.byref(self.r),
-                                 self.n_chains, self.cap, self.chain_offset, self.step, int(n_steps),
-                                 _ptr(self.xyz), self.n.ctypes.data_as(_ip), self.acc,
-                                 _ptr(mm) if mm is not None else None, _ptr(n_hist) if n_hist is not None else None,
-                                 _ptr(hs) if hs is not None else None, threads or os.cpu_count() or 1)
+        rc = lib().or_run_chains_lam(C.byref(self.m), C.byref(self.s), C.byref(self.d), C.byref(self.r),
+                                     self.n_chains, self.cap, self.chain_offset, self.step, int(n_steps),
+                                     _ptr(self.xyz), self.n.ctypes.data_as(_ip),
+                                     _ptr(self.lam) if self.lam is not None else None, self.acc,
+                                     _ptr(mm) if mm is not None else None,
+                                     _ptr(n_hist) if n_hist is not None else None,
+                                     _ptr(hs) if hs is not None else None, threads or os.cpu_count() or 1)
+        if rc != 0:
+            raise ValueError("oracle chains: wavelength sampling needs a homogeneous medium and Gaussian moves")
         self.step += int(n_steps)
         return (mm, hs) if hmc_seg else mm
 
@@ -533,6 +563,36 @@ class Chains:
         out["prop"] = np.array([list(a.prop) for a in self.acc])
         out["acc"] = np.array([list(a.acc) for a in self.acc])
         return out
+
+
+def medium_at(m: Medium, lam: float) -> Medium:
+    """The homogeneous medium at wavelength lam (section "Discussion")."""
+    out = Medium()
+    lib().or_medium_at(C.byref(m), float(lam), C.byref(out))
+    return out
+
+
+def log_spectrum(r: Run, lam: float) -> float:
+    return lib().or_log_spectrum(C.byref(r), float(lam))
+
+
+def spectrum_quantile(r: Run, u: float) -> float:
+    return lib().or_spectrum_quantile(C.byref(r), float(u))
+
+
+def z2_spectrum(m: Medium, s: Source, d: Sensor, r: Run, nodes: int = 8) -> float:
+    """Direct-sector integral of the joint density S(l) p_l: the integral over
+    the spectrum's range of S(l) Z2(medium at l), Gauss-Legendre with `nodes`
+    points on every interval of the spectrum table (S is linear there)."""
+    x, w = np.polynomial.legendre.leggauss(nodes)
+    nm = [r.lambda_nm[i] for i in range(r.n_lambda)]
+    tot = 0.0
+    for i in range(r.n_lambda - 1):
+        a, b = nm[i], nm[i + 1]
+        for xi, wi in zip(x, w):
+            lam = 0.5 * (a + b) + 0.5 * (b - a) * xi
+            tot += 0.5 * (b - a) * wi * math.exp(log_spectrum(r, lam)) * z2(medium_at(m, lam), s, d)
+    return tot
 
 
 def direct_estimate(acc: dict, z2_value: float):

@@ -747,6 +747,7 @@ typedef struct {
   double* min_margin;
   double* n_hist;
   double* min_hmc_seg;
+  double* lam;       /* wavelength per chain (NULL: wavelength not sampled) */
   int c_begin, c_end;
   double kappa_eq;
   uint32_t thr_within, thr_birth;
@@ -823,9 +824,13 @@ double or_hmc_leapfrog(const or_medium* m, const or_source* s, const or_sensor* 
  * vertex k of an n-vertex path ~ N(mu_k, toy_s^2 I) with mu_k on the segment
  * from the source to the sensor centre at fraction k/(n-1), and the end
  * vertex uniform on the sensor sphere. */
-static double target_logp(const chain_job* J, int n, const double* f) {
+static double target_logp(const chain_job* J, const or_medium* m, double lam, int n, const double* f) {
   const or_run* r = J->r;
-  if (!(r->toy_s > 0.0)) return or_logp(J->m, J->s, J->d, n, f);
+  if (!(r->toy_s > 0.0)) {
+    /* the joint density S(lam) p_lam(path) when the wavelength is sampled */
+    double lp = or_logp(m, J->s, J->d, n, f);
+    return r->n_lambda >= 2 ? lp + or_log_spectrum(r, lam) : lp;
+  }
   double lp = log(r->toy_w[n]) - log(4.0 * M_PI * J->d->R * J->d->R);
   double s2 = r->toy_s * r->toy_s;
   for (int k = 1; k <= n - 2; ++k) {
@@ -851,10 +856,74 @@ static double shortest_segment(int n, const double* f) {
   return lo;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Wavelength as a sampled coordinate (section "Discussion": a wavelength   */
+/* parameter added to the probability distribution and sampled along with  */
+/* the path vertices).  The paper gives no medium model; the reading here:  */
+/* power laws of the coefficients about a reference wavelength, and the    */
+/* emission-times-detection spectrum S(l) as a normalised piecewise-linear  */
+/* table.                                                                   */
+/* ------------------------------------------------------------------------ */
+void or_medium_at(const or_medium* m, double lam, or_medium* out) {
+  *out = *m;
+  if (!(m->lambda0 > 0.0) || !(lam > 0.0)) return;
+  /* b = 1 / lambda_s scales as (l / l0)^(-k_s): the length as (l / l0)^(+k_s) */
+  out->lambda_s = m->lambda_s * pow(lam / m->lambda0, m->k_s);
+  out->lambda_a = m->lambda_a * pow(lam / m->lambda0, m->k_a);
+}
+
+static double spectrum_area(const or_run* r) {
+  double A = 0.0;
+  for (int i = 0; i + 1 < r->n_lambda; ++i)
+    A += 0.5 * (r->lambda_nm[i + 1] - r->lambda_nm[i]) * (r->spectrum[i] + r->spectrum[i + 1]);
+  return A;
+}
+
+double or_log_spectrum(const or_run* r, double lam) {
+  const int K = r->n_lambda;
+  if (K < 2 || !(lam >= r->lambda_nm[0]) || !(lam <= r->lambda_nm[K - 1])) return NEG_INF;
+  int i = 0;
+  while (i + 2 < K && lam > r->lambda_nm[i + 1]) ++i;
+  const double h = r->lambda_nm[i + 1] - r->lambda_nm[i];
+  const double v = r->spectrum[i] + (r->spectrum[i + 1] - r->spectrum[i]) * (lam - r->lambda_nm[i]) / h;
+  return v > 0.0 ? log(v / spectrum_area(r)) : NEG_INF;
+}
+
+double or_spectrum_quantile(const or_run* r, double u) {
+  const int K = r->n_lambda;
+  double t = u * spectrum_area(r);
+  for (int i = 0; i + 1 < K; ++i) {
+    const double h = r->lambda_nm[i + 1] - r->lambda_nm[i];
+    const double y0 = r->spectrum[i], y1 = r->spectrum[i + 1];
+    const double area = 0.5 * h * (y0 + y1);
+    if (t <= area || i + 2 == K) {
+      /* y0 s + k s^2 / 2 = t with k = (y1 - y0) / h, in the form that stays
+       * accurate for k of either sign and k -> 0 */
+      const double k = (y1 - y0) / h;
+      const double disc = fmax(y0 * y0 + 2.0 * k * t, 0.0);
+      const double den = y0 + sqrt(disc);
+      const double s_ = den > 0.0 ? 2.0 * t / den : 0.0;
+      return r->lambda_nm[i] + fmin(fmax(s_, 0.0), h);
+    }
+    t -= area;
+  }
+  return r->lambda_nm[K - 1];
+}
+
+void or_init_lambda(const or_run* r, int n_chains, uint32_t chain_offset, double* lam) {
+  for (int c = 0; c < n_chains; ++c) {
+    uint32_t w[4];
+    draw_block(r->seed, 0u, 1u, chain_offset + (uint32_t)c, PURPOSE_INIT, w);
+    lam[c] = or_spectrum_quantile(r, or_u01(w[0]));
+  }
+}
+
 static void* chain_worker(void* arg) {
   chain_job* J = (chain_job*)arg;
   const or_medium* m = J->m;
   const or_run* r = J->r;
+  const int lam_on = r->n_lambda >= 2 && J->lam != NULL;
+  or_medium mc;      /* the medium at the chain's wavelength */
   int cap = J->cap;
   double* y = (double*)malloc(sizeof(double) * 3 * (cap + 1));
   double* tbs = (double*)malloc(sizeof(double) * (cap + 1));
@@ -865,7 +934,12 @@ static void* chain_worker(void* arg) {
     int n = J->n[c];
     uint32_t chain = J->chain_offset + (uint32_t)c;
     or_acc* a = J->acc ? &J->acc[c] : NULL;
-    double lpx = target_logp(J, n, x);
+    double lam = lam_on ? J->lam[c] : 0.0;
+    if (lam_on) {
+      or_medium_at(J->m, lam, &mc);
+      m = &mc;
+    }
+    double lpx = target_logp(J, m, lam, n, x);
     double margin = INFINITY;
     double hmc_seg = INFINITY;
     for (uint64_t t = J->step0; t < J->step0 + J->n_steps; ++t) {
@@ -876,6 +950,9 @@ static void* chain_worker(void* arg) {
       double log_u = log(or_u01(A[2]));
       int kind;
       int ny = n;
+      int lam_move = 0;
+      double lam_y = lam;
+      or_medium mc_y;
       double logA = NEG_INF, lpy = NEG_INF;
       int proposed = 0;
       if (u_move < J->thr_within && r->within == OR_WITHIN_TREE) {
@@ -911,7 +988,7 @@ static void* chain_worker(void* arg) {
           for (int q = 0; q < 3; ++q) J->coords[3 * mm + q] += step * z[q];
         }
         or_tree_path(J->v_ref, n, J->coords, y);
-        lpy = target_logp(J, n, y);
+        lpy = target_logp(J, m, lam, n, y);
         if (isfinite(lpy)) {
           double ljy = or_tree_coords(J->v_ref, n, y, J->coords);
           logA = lpy + ljy - lpx - ljx;
@@ -955,9 +1032,25 @@ static void* chain_worker(void* arg) {
         lpy = or_logp(m, J->s, J->d, n, y);
         if (isfinite(lpy)) logA = lpy - lpx - 0.5 * k1 + 0.5 * k0;
         proposed = 1;
+      } else if (u_move < J->thr_within && lam_on && 1 + (int)index_draw(A[1], (uint32_t)n) == n) {
+        /* wavelength move (section "Discussion": the wavelength sampled along
+         * with the path vertices, one more coordinate picked with them): a
+         * Gaussian step of the wavelength with the path held, accepted with
+         * S(l') p_l'(x) / (S(l) p_l(x)) */
+        kind = OR_MOVE_INTERIOR;
+        double z[3];
+        normals3(B, z);
+        lam_y = lam + r->sigma_lambda * z[0];
+        or_medium_at(J->m, lam_y, &mc_y);
+        lpy = target_logp(J, &mc_y, lam_y, n, x);
+        memcpy(y, x, sizeof(double) * 3 * n);
+        logA = lpy - lpx;
+        lam_move = 1;
+        proposed = 1;
       } else if (u_move < J->thr_within) {
-        /* within-dimension move of one of the n-1 movable vertices */
-        int j = 1 + (int)index_draw(A[1], (uint32_t)(n - 1));
+        /* within-dimension move of one of the n-1 movable vertices (of the n
+         * movable coordinates, the last being the wavelength, when it is sampled) */
+        int j = 1 + (int)index_draw(A[1], (uint32_t)(n - 1 + lam_on));
         memcpy(y, x, sizeof(double) * 3 * n);
         if (j == n - 1) {
           kind = OR_MOVE_END;
@@ -976,7 +1069,7 @@ static void* chain_worker(void* arg) {
             double nn = w * nu[i] + sw * (cos(ph) * e1[i] + sin(ph) * e2[i]);
             y[3 * j + i] = J->d->c[i] + J->d->R * nn;
           }
-          lpy = target_logp(J, n, y);
+          lpy = target_logp(J, m, lam, n, y);
           logA = lpy - lpx;
         } else {
           kind = OR_MOVE_INTERIOR;
@@ -1003,7 +1096,7 @@ static void* chain_worker(void* arg) {
             }
           } else {
             for (int i = 0; i < 3; ++i) y[3 * j + i] = x[3 * j + i] + r->sigma * z[i];
-            lpy = target_logp(J, n, y);
+            lpy = target_logp(J, m, lam, n, y);
             logA = lpy - lpx;
           }
         }
@@ -1038,7 +1131,7 @@ static void* chain_worker(void* arg) {
             copy3(fnew, y + 3 * (k + 1));
             memcpy(y + 3 * (k + 2), x + 3 * (k + 1), sizeof(double) * 3 * (n - k - 1));
             ny = n + 1;
-            lpy = target_logp(J, ny, y);
+            lpy = target_logp(J, m, lam, ny, y);
             double lq = log_insert_density(m, r, J->kappa_eq, fk, fk1, fnew);
             logA = lpy - lpx + log(r->p_death) - log((double)(ny - 2)) - log(r->p_birth) -
                    log(tbs[k] / T) - lq;
@@ -1052,7 +1145,7 @@ static void* chain_worker(void* arg) {
           memcpy(y, x, sizeof(double) * 3 * j);
           memcpy(y + 3 * j, x + 3 * (j + 1), sizeof(double) * 3 * (n - j - 1));
           ny = n - 1;
-          lpy = target_logp(J, ny, y);
+          lpy = target_logp(J, m, lam, ny, y);
           double T = log_sum_tb(m, ny, y, tbs);
           double lq = log_insert_density(m, r, J->kappa_eq, x + 3 * (j - 1), x + 3 * (j + 1), x + 3 * j);
           /* reverse birth y -> x selects segment j-1 of y and inserts x_j */
@@ -1075,12 +1168,17 @@ static void* chain_worker(void* arg) {
         memcpy(x, y, sizeof(double) * 3 * ny);
         n = ny;
         lpx = lpy;
+        if (lam_move) {
+          lam = lam_y;
+          mc = mc_y;
+        }
         if (a) a->acc[kind] += 1.0;
       }
       if (a && t >= r->burn_in) record_state(J, a, n, x, lpx, t);
       if (J->n_hist && t >= r->burn_in) J->n_hist[(size_t)c * (cap + 1) + n] += 1.0;
     }
     J->n[c] = n;
+    if (lam_on) J->lam[c] = lam;
     if (J->min_margin) J->min_margin[c] = margin;
     if (J->min_hmc_seg) J->min_hmc_seg[c] = hmc_seg;
   }
@@ -1111,6 +1209,17 @@ int or_run_chains_diag(const or_medium* m, const or_source* s, const or_sensor* 
                        const or_run* r, int n_chains, int cap, uint32_t chain_offset,
                        uint64_t step0, uint64_t n_steps, double* xyz, int* n,
                        or_acc* acc, double* min_margin, double* n_hist, double* min_hmc_seg, int n_threads) {
+  return or_run_chains_lam(m, s, d, r, n_chains, cap, chain_offset, step0, n_steps, xyz, n, NULL, acc, min_margin,
+                           n_hist, min_hmc_seg, n_threads);
+}
+
+int or_run_chains_lam(const or_medium* m, const or_source* s, const or_sensor* d,
+                      const or_run* r, int n_chains, int cap, uint32_t chain_offset,
+                      uint64_t step0, uint64_t n_steps, double* xyz, int* n, double* lam,
+                      or_acc* acc, double* min_margin, double* n_hist, double* min_hmc_seg, int n_threads) {
+  /* the wavelength is sampled with Gaussian vertex moves in homogeneous media */
+  if (r->n_lambda >= 2 && (lam == NULL || m->kind != OR_HOMOGENEOUS || r->within != OR_WITHIN_PERTURB))
+    return -1;
   if (n_threads < 1) n_threads = 1;
   if (n_threads > n_chains) n_threads = n_chains > 0 ? n_chains : 1;
   double keq = or_kappa_eq(m->g);
@@ -1122,7 +1231,7 @@ int or_run_chains_diag(const or_medium* m, const or_source* s, const or_sensor* 
     chain_job* J = &jobs[i];
     J->m = m; J->s = s; J->d = d; J->r = r; J->cap = cap; J->chain_offset = chain_offset;
     J->step0 = step0; J->n_steps = n_steps; J->xyz = xyz; J->n = n; J->acc = acc;
-    J->min_margin = min_margin; J->n_hist = n_hist; J->min_hmc_seg = min_hmc_seg; J->kappa_eq = keq; J->thr_within = thr_w; J->thr_birth = thr_b;
+    J->min_margin = min_margin; J->n_hist = n_hist; J->min_hmc_seg = min_hmc_seg; J->lam = lam; J->kappa_eq = keq; J->thr_within = thr_w; J->thr_birth = thr_b;
     or_tree_vref(s, d, J->v_ref);
     J->coords = (double*)calloc((size_t)3 * (size_t)(cap + 1), sizeof(double));
     J->c_begin = (int)((long)n_chains * i / n_threads);

@@ -41,6 +41,10 @@ typedef struct {
   int n_layers;
   const double* lambda_s_layers;
   const double* lambda_a_layers;
+  /* wavelength dependence (section "Discussion"): at wavelength l the
+   * scattering and absorption coefficients are b (l / lambda0)^(-k_s) and
+   * a (l / lambda0)^(-k_a) (homogeneous media; k = 0: none) */
+  double lambda0, k_s, k_a;
 } or_medium;
 
 typedef struct {
@@ -71,6 +75,13 @@ typedef struct {
   int hmc_steps;            /* OR_WITHIN_HMC: leapfrog steps of size mala_step */
   double toy_s;             /* > 0: sample the pins' toy target instead of the path density */
   const double* toy_w;      /* toy sector weights, indexed by vertex count (cap + 1 entries) */
+  /* wavelength as a sampled coordinate: n_lambda >= 2 spectrum nodes (0: off); the
+   * chains sample (path, l) from S(l) p_l(path), S piecewise linear through
+   * (lambda_nm[i], spectrum[i]) normalised over [lambda_nm[0], lambda_nm[n-1]] */
+  int n_lambda;
+  const double* lambda_nm;
+  const double* spectrum;
+  double sigma_lambda;      /* Gaussian step of a wavelength move (nm) */
 } or_run;
 
 /* Per-chain accumulators (FP64 sums over recorded states). */
@@ -140,6 +151,22 @@ int or_run_chains_hist(const or_medium* m, const or_source* s, const or_sensor* 
                        const or_run* r, int n_chains, int cap, uint32_t chain_offset,
                        uint64_t step0, uint64_t n_steps, double* xyz, int* n,
                        or_acc* acc, double* min_margin, double* n_hist, int n_threads);
+/* ---- wavelength as a sampled coordinate (section "Discussion") ---- */
+/* The homogeneous medium at wavelength lam (lengths scaled by (lam/lambda0)^k). */
+void or_medium_at(const or_medium* m, double lam, or_medium* out);
+/* log S(lam), S the run's normalised piecewise-linear spectrum (-inf outside its range). */
+double or_log_spectrum(const or_run* r, double lam);
+/* The wavelength at which the spectrum's CDF equals u in [0, 1]. */
+double or_spectrum_quantile(const or_run* r, double u);
+/* Initial wavelengths: lam[c] = quantile of u01 of Philox counter (0, 1, chain, init). */
+void or_init_lambda(const or_run* r, int n_chains, uint32_t chain_offset, double* lam);
+/* Chains of (path, wavelength): or_run_chains_diag with the chains' wavelengths lam
+ * (n_chains, NULL when r->n_lambda == 0) updated in place. */
+int or_run_chains_lam(const or_medium* m, const or_source* s, const or_sensor* d,
+                      const or_run* r, int n_chains, int cap, uint32_t chain_offset,
+                      uint64_t step0, uint64_t n_steps, double* xyz, int* n, double* lam,
+                      or_acc* acc, double* min_margin, double* n_hist, double* min_hmc_seg, int n_threads);
+
 /* Same, and stores in min_hmc_seg[chain] (may be NULL) the shortest segment
  * length met at any leapfrog position of the chain's HMC moves (infinity
  * without HMC moves). */

@@ -71,6 +71,10 @@ class Medium:
     dz: float = 10.0               # layer thickness (m), layered
     lambda_s_layers: Optional[np.ndarray] = None
     lambda_a_layers: Optional[np.ndarray] = None
+    # wavelength dependence: coefficients b (l / lambda0)^(-k_s), a (l / lambda0)^(-k_a) (0: none)
+    lambda0: float = 0.0           # reference wavelength (nm) of lambda_s, lambda_a
+    k_s: float = 0.0
+    k_a: float = 0.0
 
     @property
     def n_layers(self) -> int:
@@ -120,6 +124,10 @@ class Run:
     gradients: bool = False
     hmc_steps: int = 10            # leapfrog steps of a full-path gradient (HMC) move, step mala_step
     layout: int = LAYOUT_AUTO      # LAYOUT_WARP: one warp per chain; LAYOUT_LANE: one lane per chain (lean runs)
+    # wavelength as a sampled coordinate: spectrum table (nm, any positive scale); None = off
+    spectrum_nm: Optional[Sequence[float]] = None
+    spectrum: Optional[Sequence[float]] = None
+    sigma_lambda: float = 10.0     # Gaussian step of a wavelength move (nm)
 
 
 @dataclasses.dataclass
@@ -231,6 +239,20 @@ def general_small(n_chains: int = 64, n_steps: int = 400) -> Scene:
     sen = Sensor((0.2, 0.1, 0.9), 0.15, RHO_PAPER, (0.0, -1.0, 0.0))
     run = Run(seed=BASE_SEED + 7, n_steps=n_steps, burn_in=n_steps // 10, init=INIT_DIRECT, sigma=0.05)
     return Scene("general_small", med, [src], [sen], [Pair(0, 0, n_chains, 64)], run)
+
+
+def wavelength(n_chains: int = 4096, n_steps: int = 20_000, cap: int = 64) -> Scene:
+    """The plain geometry with the wavelength sampled along with the path
+    (section "Discussion"): scattering and absorption lengths at 400 nm as in
+    the plain workload, b ~ (l / 400 nm)^-4 (Rayleigh-like), a ~ (l / 400
+    nm)^-2, and a triangular emission-times-detection spectrum over 300-600 nm
+    peaking at 420 nm."""
+    sc = plain(n_chains, n_steps, cap)
+    sc.name = "wavelength"
+    sc.medium = dataclasses.replace(sc.medium, lambda0=400.0, k_s=4.0, k_a=2.0)
+    sc.run = dataclasses.replace(sc.run, seed=BASE_SEED + 8, spectrum_nm=(300.0, 420.0, 600.0),
+                                 spectrum=(0.0, 1.0, 0.0), sigma_lambda=20.0)
+    return sc
 
 
 # Scattering coefficients b1 (1/m) of the x >= 0 half of the paper's test scene (Table tbl:results).
