@@ -109,6 +109,12 @@ typedef struct {
   int n_layers;
   const double* lambda_s_layers;   /* host [n_layers], copied */
   const double* lambda_a_layers;   /* host [n_layers], copied */
+  /* Wavelength dependence (section "Discussion"; the paper gives no model, the
+   * reading here is power laws): at wavelength l the coefficients are
+   * b (l / lambda0)^(-k_s) and a (l / lambda0)^(-k_a).  Used by chains that
+   * sample the wavelength (pmc_run_desc.n_lambda); 0, 0, 0 = none. */
+  double lambda0;                  /* reference wavelength (nm) of lambda_s, lambda_a */
+  double k_s, k_a;                 /* >= 0 */
 } pmc_medium_desc;
 
 /* Point source with isotropic or von Mises-Fisher emission (Eq. emission_dist). */
@@ -197,6 +203,25 @@ typedef struct {
                                       choice) in shared memory; the same Markov chain and random
                                       numbers as the warp layout.  Fails with PMC_ERR_INVALID for
                                       runs that are not lean */
+  /* Wavelength as a sampled coordinate (section "Discussion": a wavelength
+   * parameter added to the path density, sampled along with the vertices).
+   * n_lambda >= 2 (0 = off): the chains sample (path, l) from S(l) p_l(path),
+   * S the emission-times-detection spectrum, piecewise linear through
+   * (lambda_nm[i], spectrum[i]) (host, copied; increasing wavelengths, values
+   * >= 0, any scale: normalised internally) and 0 outside, p_l the path
+   * density of the medium at l.  The wavelength is one more movable
+   * coordinate of the within-dimension draw (one of n: the n-1 movable
+   * vertices and l); a wavelength move takes a Gaussian step of sigma_lambda
+   * nm with the path held.  Initial wavelengths: the spectrum's quantile of
+   * u01 of Philox counter (0, 1, chain, init purpose).  The intensity is
+   * Z2 / pi(n = 2) with Z2 the spectrum-weighted direct sector.  Needs a
+   * homogeneous medium, PMC_WITHIN_PERTURB, no PMC_FLAG_GRADIENTS and the
+   * warp layout (PMC_ERR_INVALID otherwise); within-dimension proposal and
+   * acceptance counts include the wavelength moves. */
+  int n_lambda;
+  const double* lambda_nm;
+  const double* spectrum;
+  double sigma_lambda;
   int64_t chain_lo, chain_hi;      /* chain window: this chain set holds the geometry's chains
                                       [chain_lo, chain_hi) in pair order (chains of pair p are numbered
                                       after those of pairs 0..p-1); 0, 0 = all.  A chain keeps its
@@ -375,7 +400,9 @@ PMC_API int pmc_total_chains(pmc_chains_t chains);
  * persistent grid size, and the kernel: 0 the lean and 1 the general kernel
  * with one warp per chain, 2 the general kernel with tree moves, 3 with HMC
  * moves, 4 the lean kernel with one chain per lane (32 chains per warp), 5
- * the same with MALA moves.  Returns the number of classes in *n_classes;
+ * the same with MALA moves, 6 the general kernel sampling the wavelength, 7
+ * the lean kernel with tree moves.
+ * Returns the number of classes in *n_classes;
  * writes at most max_rows rows. */
 PMC_API int pmc_chains_launch_info(pmc_chains_t chains, int* out, int max_rows, int* n_classes);
 
@@ -384,6 +411,11 @@ PMC_API int pmc_chains_launch_info(pmc_chains_t chains, int* out, int max_rows, 
  * pmc_save_state stores the needed size in *bytes.  Synchronises `stream`. */
 PMC_API int pmc_save_state(pmc_chains_t chains, void* buf, size_t* bytes, void* stream);
 PMC_API int pmc_load_state(pmc_chains_t chains, const void* buf, size_t bytes, void* stream);
+
+/* The chains' current wavelengths (wavelength sampling only; PMC_ERR_INVALID
+ * otherwise): out (host, caller-owned) receives total_chains floats (nm).
+ * Synchronises `stream`. */
+PMC_API int pmc_read_lambda(pmc_chains_t chains, float* out, size_t len, void* stream);
 
 /* Ask running and future pmc_run_steps calls of these chains to stop at the
  * next step boundary; pmc_run_steps then reports PMC_ERR_ABORTED on the next

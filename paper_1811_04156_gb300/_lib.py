@@ -34,7 +34,8 @@ class MediumDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("lambda_s", C.c_double), ("lambda_a", C.c_double),
                 ("g", C.c_double), ("f_sl", C.c_double), ("z0", C.c_double), ("dz", C.c_double),
                 ("n_layers", C.c_int), ("lambda_s_layers", C.POINTER(C.c_double)),
-                ("lambda_a_layers", C.POINTER(C.c_double))]
+                ("lambda_a_layers", C.POINTER(C.c_double)), ("lambda0", C.c_double), ("k_s", C.c_double),
+                ("k_a", C.c_double)]
 
 
 class SourceDesc(C.Structure):
@@ -65,7 +66,9 @@ class RunDesc(C.Structure):
                 ("init_jitter", C.c_double), ("init_xyz", C.POINTER(C.c_float)),
                 ("init_n", C.POINTER(C.c_int)), ("init_stride", C.c_int), ("flags", C.c_int),
                 ("warps_per_block", C.c_int), ("smem_window", C.c_int), ("hmc_steps", C.c_int),
-                ("layout", C.c_int), ("chain_lo", C.c_int64), ("chain_hi", C.c_int64)]
+                ("layout", C.c_int), ("n_lambda", C.c_int), ("lambda_nm", C.POINTER(C.c_double)),
+                ("spectrum", C.POINTER(C.c_double)), ("sigma_lambda", C.c_double), ("chain_lo", C.c_int64),
+                ("chain_hi", C.c_int64)]
 
 
 class Estimate(C.Structure):
@@ -124,6 +127,7 @@ PROTOTYPES = {
     "pmc_chains_launch_info": ([_vp, _ip, C.c_int, _ip], C.c_int),
     "pmc_save_state": ([_vp, _vp, C.POINTER(C.c_size_t), _vp], C.c_int),
     "pmc_load_state": ([_vp, _vp, C.c_size_t, _vp], C.c_int),
+    "pmc_read_lambda": ([_vp, _fp, C.c_size_t, _vp], C.c_int),
     "pmc_request_abort": ([_vp, C.c_int], C.c_int),
     "pmc_chain_status": ([_vp, _ip, _vp], C.c_int),
     "pmc_logp": ([_vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp], C.c_int),

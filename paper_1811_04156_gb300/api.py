@@ -67,6 +67,9 @@ def medium_desc(m: S.Medium):
     d.f_sl = float(m.f_sl)
     d.z0 = float(m.z0)
     d.dz = float(m.dz)
+    d.lambda0 = float(getattr(m, "lambda0", 0.0))
+    d.k_s = float(getattr(m, "k_s", 0.0))
+    d.k_a = float(getattr(m, "k_a", 0.0))
     keep = ()
     if m.kind == S.LAYERED:
         ls = np.ascontiguousarray(m.lambda_s_layers, dtype=np.float64)
@@ -169,6 +172,15 @@ def run_desc(r: S.Run, flags: int = 0, warps_per_block: int = 0, user_xyz: Optio
     d.layout = int(getattr(r, "layout", 0))
     d.chain_lo, d.chain_hi = int(chain_window[0]), int(chain_window[1])
     keep = ()
+    nm = getattr(r, "spectrum_nm", None)
+    if nm is not None:
+        x = np.ascontiguousarray(nm, dtype=np.float64)
+        y = np.ascontiguousarray(r.spectrum, dtype=np.float64)
+        d.n_lambda = len(x)
+        d.lambda_nm = x.ctypes.data_as(C.POINTER(C.c_double))
+        d.spectrum = y.ctypes.data_as(C.POINTER(C.c_double))
+        d.sigma_lambda = float(r.sigma_lambda)
+        keep = (x, y)
     if user_xyz is not None:
         ux = np.ascontiguousarray(user_xyz, dtype=np.float32)  # [chains][3][stride]
         un = np.ascontiguousarray(user_n, dtype=np.int32)
@@ -176,7 +188,7 @@ def run_desc(r: S.Run, flags: int = 0, warps_per_block: int = 0, user_xyz: Optio
         d.init_xyz = ux.ctypes.data_as(C.POINTER(C.c_float))
         d.init_n = un.ctypes.data_as(C.POINTER(C.c_int))
         d.init_stride = int(ux.shape[2])
-        keep = (ux, un)
+        keep = keep + (ux, un)
     return d, keep
 
 
@@ -218,6 +230,13 @@ class Chains:
         out = (Estimate * self.n_pairs)()
         check(load().pmc_read_estimator(self.handle, out, self.n_pairs, _stream(stream)), "pmc_read_estimator")
         return [e.as_dict() for e in out]
+
+    def read_lambda(self, stream=None) -> np.ndarray:
+        """The chains' current wavelengths in nm (pmc_read_lambda; wavelength sampling only)."""
+        out = np.zeros(self.total, dtype=np.float32)
+        check(load().pmc_read_lambda(self.handle, out.ctypes.data_as(C.POINTER(C.c_float)), self.total,
+                                     _stream(stream)), "pmc_read_lambda")
+        return out
 
     def read_moments(self, stream=None) -> np.ndarray:
         """Per-pair additive moments of this chain set (pmc_read_moments): (n_pairs, PMC_MOMENT_WORDS)."""

@@ -36,6 +36,28 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 double norm3(const double* v) { return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
 
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton iteration on P_n from
+// the Chebyshev guesses, P_n by the three-term recurrence.
+void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = 0.0;
+      for (int k = 1; k <= n; ++k) {
+        const double p2 = p1;
+        p1 = p0;
+        p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+      }
+      dp = n * (z * p0 - p1) / (z * z - 1.0);
+      const double dz = p0 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-15) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
 // Inverse Langevin: coth(k) - 1/k = g (appendix, dimension matching transformation).
 double kappa_eq_host(double g) {
   if (g <= 0.0) return 0.0;
@@ -202,6 +224,10 @@ struct pmc_chains_s {
   float* d_stage = nullptr;       // staging buffer of pmc_set_states
   int* d_stage_n = nullptr;
   size_t stage_floats = 0;
+  bool lam_on = false;             // wavelength sampled with the path
+  float* d_lam = nullptr;          // [total] the chains' wavelengths
+  float* d_spec = nullptr;         // [2][n_spec] spectrum nodes (nm) and normalised densities
+  std::vector<double> spec_x, spec_y;  // host copy (normalised densities)
 };
 
 // Scattering depth of the straight segment from the source to the sensor
@@ -407,6 +433,14 @@ int pmc_create_medium(pmc_ctx_t ctx, const pmc_medium_desc* desc, pmc_medium_t* 
   d.sl_dg0 = static_cast<float>(2.0 / (1.0 - g * g));
   d.sl_dg1 = static_cast<float>(2.0 / ((1.0 - g) * (1.0 - g)));
   d.kappa_eq = static_cast<float>(kappa_eq_host(g));
+  if (!(desc->k_s >= 0.0 && desc->k_a >= 0.0 && desc->lambda0 >= 0.0) || !std::isfinite(desc->k_s) ||
+      !std::isfinite(desc->k_a) || !std::isfinite(desc->lambda0))
+    return fail(PMC_ERR_INVALID, "wavelength law: lambda0, k_s, k_a must be finite and >= 0");
+  if ((desc->k_s > 0.0 || desc->k_a > 0.0) && !(desc->lambda0 > 0.0))
+    return fail(PMC_ERR_INVALID, "a wavelength-dependent medium needs lambda0 > 0");
+  d.lam0 = static_cast<float>(desc->lambda0 > 0.0 ? desc->lambda0 : 1.0);
+  d.ks = static_cast<float>(desc->k_s);
+  d.ka = static_cast<float>(desc->k_a);
   if (desc->kind == PMC_HOMOGENEOUS) {
     if (!finite_pos(desc->lambda_s) || !finite_pos(desc->lambda_a))
       return fail(PMC_ERR_INVALID, "lambda_s and lambda_a must be finite and > 0");
@@ -560,6 +594,8 @@ int pmc_destroy_chains(pmc_chains_t ch) {
   cudaFree(ch->d_qp);
   cudaFree(ch->d_qtab);
   cudaFree(ch->d_bsum);
+  cudaFree(ch->d_lam);
+  cudaFree(ch->d_spec);
   if (ch->h_abort) cudaFreeHost(ch->h_abort);
   delete ch;
   return PMC_OK;
@@ -575,7 +611,7 @@ int pmc_destroy_chains(pmc_chains_t ch) {
 constexpr double kLaneMaxN = 24.0;
 
 // Work items of a launch: one per chain, or one per 32 chains (lane layout).
-static int work_items(int kind, int chains) { return kind >= 4 ? (chains + 31) / 32 : chains; }
+static int work_items(int kind, int chains) { return lane_kind(kind) ? (chains + 31) / 32 : chains; }
 
 static ChainParams class_params(pmc_chains_t ch, size_t k, unsigned long long n_steps) {
   const ChainClass& cl = ch->classes[k];
@@ -595,6 +631,7 @@ static ChainParams class_params(pmc_chains_t ch, size_t k, unsigned long long n_
   p.queue = ch->d_queue + k;
   p.abort_flag = ch->d_abort;
   p.chain_id0 = static_cast<uint32_t>(ch->chain_lo);
+  p.lam = ch->d_lam;
   p.chain_lo = cl.lo;
   p.chain_hi = cl.hi;
   p.n_steps = n_steps;
@@ -616,6 +653,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
   unsigned long long* sst = nullptr;
   double* sacc = nullptr;
   int* sstat = nullptr;
+  float* slam = nullptr;  // wavelength sampling: the probes' copy of the wavelengths
   // cache key: the warp kernel instance, the layout request and which lane
   // kernel (if any) the run may use; per class also whether its paths are short
   const int kind = (((ch->general * 2 + ch->grad) * 3 + ch->layout) * 8 + ch->lane_kind) * 2;
@@ -630,6 +668,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
     CK(dalloc(&sst, T));
     CK(dalloc(&sacc, static_cast<size_t>(T) * ACC_WORDS));
     CK(dalloc(&sstat, T));
+    if (ch->lam_on) CK(dalloc(&slam, T));
   }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -665,7 +704,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
       for (const auto& cand : cands) {
         const int ckind = cand.first, win = cand.second;
         for (int wpb : {1, 2, 4}) {
-          const bool spill = ckind < 4 && win < full;
+          const bool spill = !lane_kind(ckind) && win < full;
           if (chain_smem_bytes(win, wpb, ckind, ch->grad) > ch->ctx->smem_per_block) continue;
           int bps = 0;
           if (chain_occupancy(ckind, ch->grad, spill, wpb, win, &bps) != cudaSuccess || bps < 1) continue;
@@ -677,6 +716,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
           p.step = sst;
           p.acc = sacc;
           p.status = sstat;
+          p.lam = slam;
           p.abort_flag = nullptr;
           // two probes from the same scratch state; the faster one counts (the
           // first launch of a shape also pays its one-time set-up)
@@ -688,6 +728,8 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
             if (e == cudaSuccess) e = cudaMemsetAsync(sst, 0, sizeof(unsigned long long) * T, s);
             if (e == cudaSuccess) e = cudaMemsetAsync(sacc, 0, sizeof(double) * T * ACC_WORDS, s);
             if (e == cudaSuccess) e = cudaMemsetAsync(sstat, 0, sizeof(int) * T, s);
+            if (e == cudaSuccess && slam)
+              e = cudaMemcpyAsync(slam, ch->d_lam, sizeof(float) * T, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess) e = cudaMemsetAsync(ch->d_queue + k, 0, sizeof(unsigned int), s);
             if (e == cudaSuccess) e = cudaEventRecord(e0, s);
             if (e == cudaSuccess) e = launch_chain(p, ckind, ch->grad, spill, grid, wpb, s);
@@ -712,7 +754,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
     }
     int bps = 0;
     const int bw = std::get<0>(best), bwin = std::get<1>(best), bkind = std::get<2>(best);
-    const bool spill = bkind < 4 && bwin < full;
+    const bool spill = !lane_kind(bkind) && bwin < full;
     if (rc == PMC_OK && chain_occupancy(bkind, ch->grad, spill, bw, bwin, &bps) == cudaSuccess && bps >= 1) {
       cl.kind = bkind;
       cl.warps_per_block = bw;
@@ -728,6 +770,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
   cudaFree(sst);
   cudaFree(sacc);
   cudaFree(sstat);
+  cudaFree(slam);
   CK(cudaMemsetAsync(ch->d_any, 0, sizeof(int), s));
   return rc;
 }
@@ -790,6 +833,30 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   R.burn_in = r->burn_in;
   R.beta_min = 0.01f;
   R.gradients = (r->flags & PMC_FLAG_GRADIENTS) ? 1 : 0;
+  // wavelength sampled with the path: validate and normalise the spectrum
+  ch->lam_on = r->n_lambda != 0;
+  if (ch->lam_on) {
+    const int K = r->n_lambda;
+    if (K < 2 || K > 256 || r->lambda_nm == nullptr || r->spectrum == nullptr || !finite_pos(r->sigma_lambda))
+      return fail(PMC_ERR_INVALID, "wavelength sampling needs 2..256 spectrum nodes and sigma_lambda > 0");
+    if (med->d.kind != PMC_HOMOGENEOUS || r->within != PMC_WITHIN_PERTURB || (r->flags & PMC_FLAG_GRADIENTS) ||
+        r->layout == PMC_LAYOUT_LANE)
+      return fail(PMC_ERR_INVALID, "wavelength sampling runs in a homogeneous medium with Gaussian vertex moves, "
+                                   "without gradients, in the warp layout");
+    double area = 0.0;
+    for (int i = 0; i < K; ++i) {
+      if (!finite_pos(r->lambda_nm[i]) || !(r->spectrum[i] >= 0.0) || !std::isfinite(r->spectrum[i]) ||
+          (i > 0 && !(r->lambda_nm[i] > r->lambda_nm[i - 1])))
+        return fail(PMC_ERR_INVALID, "spectrum: increasing positive wavelengths, finite values >= 0");
+      if (i > 0) area += 0.5 * (r->lambda_nm[i] - r->lambda_nm[i - 1]) * (r->spectrum[i] + r->spectrum[i - 1]);
+    }
+    if (!(area > 0.0)) return fail(PMC_ERR_INVALID, "spectrum: zero area");
+    ch->spec_x.assign(r->lambda_nm, r->lambda_nm + K);
+    ch->spec_y.resize(K);
+    for (int i = 0; i < K; ++i) ch->spec_y[i] = r->spectrum[i] / area;
+    R.n_spec = K;
+    R.sigma_lam = static_cast<float>(r->sigma_lambda);
+  }
 
   ch->h_pairs = geom->pairs;
   for (auto& d : ch->h_pairs) {
@@ -808,21 +875,23 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   ch->general = med->d.kind != PMC_HOMOGENEOUS || med->d.f_sl > 0.f || r->within == PMC_WITHIN_MALA ||
                 std::any_of(ch->h_pairs.begin(), ch->h_pairs.end(),
                             [](const DPair& d) { return d.emission != PMC_EMIT_ISOTROPIC || d.rho != PMC_RHO_ONE; });
-  if (r->within == PMC_WITHIN_TREE) ch->general = 2;
-  if (r->within == PMC_WITHIN_HMC) ch->general = 3;
-  ch->layout = r->layout;
-  // the lane layout runs the lean physics (homogeneous medium, pure
-  // Henyey-Greenstein, isotropic emission, rho = 1) with Gaussian or MALA moves
+  // the lean physics: homogeneous medium, pure Henyey-Greenstein, isotropic
+  // emission, rho = 1 (the lane layout runs it with Gaussian or MALA moves,
+  // tree moves have a lean instantiation)
   const bool lean_physics =
       med->d.kind == PMC_HOMOGENEOUS && !(med->d.f_sl > 0.f) &&
       std::all_of(ch->h_pairs.begin(), ch->h_pairs.end(),
                   [](const DPair& d) { return d.emission == PMC_EMIT_ISOTROPIC && d.rho == PMC_RHO_ONE; });
-  if (lean_physics && r->within == PMC_WITHIN_PERTURB) ch->lane_kind = 4;
+  if (r->within == PMC_WITHIN_TREE) ch->general = lean_physics ? 7 : 2;
+  if (r->within == PMC_WITHIN_HMC) ch->general = 3;
+  if (ch->lam_on) ch->general = 6;
+  ch->layout = r->layout;
+  if (lean_physics && r->within == PMC_WITHIN_PERTURB && !ch->lam_on) ch->lane_kind = 4;
   if (lean_physics && r->within == PMC_WITHIN_MALA) ch->lane_kind = 5;
   if (r->layout == PMC_LAYOUT_LANE && ch->lane_kind == 0)
     return fail(PMC_ERR_INVALID, "the lane layout runs lean chains only (homogeneous medium, isotropic emission, "
                                  "rho = 1, Henyey-Greenstein, Gaussian or MALA vertex moves)");
-  const int n_arrays = chain_arrays(ch->general > 0, ch->grad);
+  const int n_arrays = chain_arrays(ch->general > 0 && ch->general != 7, ch->grad);
   const int T = ch->total;
   ch->h_base.resize(T);
   ch->h_pair_of.resize(T);
@@ -873,7 +942,8 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
       cl.kind = ch->lane_kind;
       cl.smem_cap = std::min(r->smem_window > 0 ? r->smem_window : 16, maxcap);
     } else if (r->smem_window > 0 && r->smem_window < cl.smem_cap && ch->general >= 2)
-      return fail(PMC_ERR_INVALID, "tree and HMC moves need the whole vertex cap in shared memory (smem_window)");
+      return fail(PMC_ERR_INVALID, "tree, HMC and wavelength moves need the whole vertex cap in shared memory "
+                                   "(smem_window)");
     if (r->smem_window > 0 && r->smem_window < cl.smem_cap) {
       cl.smem_cap = r->smem_window;
       cl.spill = true;
@@ -912,6 +982,19 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   CK(dalloc(&ch->d_queue, ch->classes.size()));
   CK(dalloc(&ch->d_z2, ch->n_pairs));
   CK(dalloc(&ch->d_est, static_cast<size_t>(ch->n_pairs) * PMC_MOMENT_WORDS));
+  if (ch->lam_on) {
+    const int K = R.n_spec;
+    std::vector<float> spec(2 * static_cast<size_t>(K));
+    for (int i = 0; i < K; ++i) {
+      spec[i] = static_cast<float>(ch->spec_x[i]);
+      spec[K + i] = static_cast<float>(ch->spec_y[i]);
+    }
+    CK(dalloc(&ch->d_lam, T));
+    CK(dalloc(&ch->d_spec, 2 * static_cast<size_t>(K)));
+    CK(cudaMemcpy(ch->d_spec, spec.data(), spec.size() * sizeof(float), cudaMemcpyHostToDevice));
+    R.spec_x = ch->d_spec;
+    R.spec_y = ch->d_spec + K;
+  }
   CK(cudaHostAlloc(reinterpret_cast<void**>(&ch->h_abort), sizeof(int), cudaHostAllocMapped));
   *ch->h_abort = 0;
   CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ch->d_abort), ch->h_abort, 0));
@@ -938,6 +1021,7 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   ip.status = ch->d_status;
   ip.total = T;
   ip.chain_id0 = static_cast<uint32_t>(lo);
+  ip.lam = ch->d_lam;
   ip.init_kind = r->init;
   ip.init_k = r->init_k;
   ip.jitter = static_cast<float>(r->init_jitter);
@@ -958,7 +1042,39 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   const bool axisym = std::all_of(ch->h_pairs.begin(), ch->h_pairs.end(),
                                   [](const DPair& d) { return d.emission == 0 && d.rho == 0; }) &&
                       med->d.kind == 0;
-  CK(launch_z2(med->d, ch->d_pairs, ch->n_pairs, 4096, axisym ? 1 : 64, ch->d_z2, s));
+  if (!ch->lam_on) {
+    CK(launch_z2(med->d, ch->d_pairs, ch->n_pairs, 4096, axisym ? 1 : 64, ch->d_z2, s));
+  } else {
+    // the direct sector of the joint density: the spectrum-weighted integral
+    // over the wavelength of Z2 at the medium of each wavelength
+    // (Gauss-Legendre, 8 nodes per interval of the spectrum, where S is linear)
+    const int K = R.n_spec, G = 8;
+    double gx[G], gw[G];
+    gauss_legendre(G, gx, gw);
+    std::vector<double> acc(ch->n_pairs, 0.0), z(ch->n_pairs);
+    for (int i = 0; i + 1 < K; ++i) {
+      const double a = ch->spec_x[i], b = ch->spec_x[i + 1];
+      for (int q = 0; q < G; ++q) {
+        const double lam = 0.5 * (a + b) + 0.5 * (b - a) * gx[q];
+        const double sv = ch->spec_y[i] + (ch->spec_y[i + 1] - ch->spec_y[i]) * (lam - a) / (b - a);
+        const double wq = 0.5 * (b - a) * gw[q] * sv;
+        if (!(wq > 0.0)) continue;
+        DMedium Mq = med->d;
+        const double ratio = lam / med->d.lam0;
+        const double bq = (1.0 / med->lambda_s) * std::pow(ratio, -static_cast<double>(med->d.ks));
+        const double aq = (1.0 / med->lambda_a) * std::pow(ratio, -static_cast<double>(med->d.ka));
+        Mq.b = static_cast<float>(bq);
+        Mq.a = static_cast<float>(aq);
+        Mq.log_b = static_cast<float>(std::log(bq));
+        CK(launch_z2(Mq, ch->d_pairs, ch->n_pairs, 4096, axisym ? 1 : 64, ch->d_z2, s));
+        CK(cudaMemcpyAsync(z.data(), ch->d_z2, sizeof(double) * ch->n_pairs, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int p = 0; p < ch->n_pairs; ++p) acc[p] += wq * z[p];
+      }
+    }
+    CK(cudaMemcpyAsync(ch->d_z2, acc.data(), sizeof(double) * ch->n_pairs, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
   if (d_user) {
     CK(cudaStreamSynchronize(s));
     cudaFree(d_user);
@@ -985,6 +1101,7 @@ static InitParams init_params(pmc_chains_t ch) {
   ip.status = ch->d_status;
   ip.total = ch->total;
   ip.chain_id0 = static_cast<uint32_t>(ch->chain_lo);
+  ip.lam = ch->d_lam;
   ip.init_kind = ch->init_kind;
   ip.init_k = ch->init_k;
   ip.jitter = ch->init_jitter;
@@ -1295,7 +1412,7 @@ int pmc_read_accumulators(pmc_chains_t ch, double* out, size_t n_doubles, void* 
 static size_t state_bytes(pmc_chains_t ch) {
   return 16 + sizeof(float) * static_cast<size_t>(ch->xyz_floats) + sizeof(int) * ch->total +
          sizeof(unsigned long long) * ch->total + sizeof(double) * static_cast<size_t>(ch->total) * ACC_WORDS +
-         sizeof(int) * ch->total;
+         sizeof(int) * ch->total + (ch->lam_on ? sizeof(float) * ch->total : 0);
 }
 
 int pmc_save_state(pmc_chains_t ch, void* buf, size_t* bytes, void* stream) {
@@ -1321,6 +1438,8 @@ int pmc_save_state(pmc_chains_t ch, void* buf, size_t* bytes, void* stream) {
   CK(cudaMemcpyAsync(p, ch->d_acc, sizeof(double) * ch->total * ACC_WORDS, cudaMemcpyDeviceToHost, s));
   p += sizeof(double) * ch->total * ACC_WORDS;
   CK(cudaMemcpyAsync(p, ch->d_status, sizeof(int) * ch->total, cudaMemcpyDeviceToHost, s));
+  p += sizeof(int) * ch->total;
+  if (ch->lam_on) CK(cudaMemcpyAsync(p, ch->d_lam, sizeof(float) * ch->total, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   *bytes = need;
   return PMC_OK;
@@ -1346,7 +1465,20 @@ int pmc_load_state(pmc_chains_t ch, const void* buf, size_t bytes, void* stream)
   CK(cudaMemcpyAsync(ch->d_acc, p, sizeof(double) * ch->total * ACC_WORDS, cudaMemcpyHostToDevice, s));
   p += sizeof(double) * ch->total * ACC_WORDS;
   CK(cudaMemcpyAsync(ch->d_status, p, sizeof(int) * ch->total, cudaMemcpyHostToDevice, s));
+  p += sizeof(int) * ch->total;
+  if (ch->lam_on) CK(cudaMemcpyAsync(ch->d_lam, p, sizeof(float) * ch->total, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(ch->d_any, 0, sizeof(int), s));
+  CK(cudaStreamSynchronize(s));
+  return PMC_OK;
+}
+
+int pmc_read_lambda(pmc_chains_t ch, float* out, size_t len, void* stream) {
+  if (ch == nullptr || out == nullptr) return fail(PMC_ERR_INVALID, "NULL argument");
+  if (!ch->lam_on) return fail(PMC_ERR_INVALID, "the chains do not sample the wavelength");
+  if (len < static_cast<size_t>(ch->total)) return fail(PMC_ERR_INVALID, "output too short");
+  CK(cudaSetDevice(ch->ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(out, ch->d_lam, sizeof(float) * ch->total, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return PMC_OK;
 }
@@ -1800,6 +1932,8 @@ int pmc_seed_from_tracer(pmc_chains_t ch, uint64_t seed, uint64_t photons_per_ro
   if (ch == nullptr) return fail(PMC_ERR_INVALID, "NULL chains");
   if (photons_per_round == 0 || max_rounds < 1 || !(r_reject > 0))
     return fail(PMC_ERR_INVALID, "need photons_per_round >= 1, max_rounds >= 1 and r_reject > 0");
+  if (ch->lam_on) return fail(PMC_ERR_INVALID, "tracer seeds carry no wavelength: seed wavelength-sampling chains "
+                                               "with pmc_set_states or their initial paths");
   CK(cudaSetDevice(ch->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const float rr = std::isfinite(r_reject) ? static_cast<float>(r_reject) : std::numeric_limits<float>::infinity();

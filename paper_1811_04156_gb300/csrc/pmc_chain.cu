@@ -42,6 +42,8 @@ constexpr int kFlushAccepts = 64;   // FP32 partials -> FP64 accumulators
 constexpr int kRngWords = 8;        // staged words per step
 constexpr int kPairWords = 64;      // shared slot for the pair constants (floats)
 static_assert(sizeof(DPair) <= kPairWords * sizeof(float), "pair slot too small");
+constexpr int kMedWords = 48;       // wavelength sampling: the medium at the chain's wavelength (floats)
+static_assert(sizeof(DMedium) <= kMedWords * sizeof(float), "medium slot too small");
 
 enum Move { MV_INTERIOR = 0, MV_END = 1, MV_BIRTH = 2, MV_DEATH = 3 };
 
@@ -624,17 +626,18 @@ __device__ __forceinline__ void flush64(Accum& a, int lane) {
 //           hi.z, hi.w = cos, sin of the vMF azimuth
 //   birth:  lo.z = u for cos s, lo.w = sinh t, hi.x = cosh t, hi.y, hi.z = cos, sin of phi
 template <bool kGen, bool kGrad, bool kSpill, int kX>
-__global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainParams P) {
+__global__ void __launch_bounds__(128, (kGen || kX != 0) ? 5 : 6) chain_kernel(const ChainParams P) {
   using WP = WarpPath<kGen, kGrad, kSpill>;
-  constexpr bool kTree = kX == 1, kHmc = kX == 2;
-  static_assert(kX == 0 || (kGen && !kSpill), "tree and HMC moves use the general kernel with the whole cap in shared memory");
+  constexpr bool kTree = kX == 1, kHmc = kX == 2, kLam = kX == 3;
+  static_assert(kX == 0 || !kSpill, "tree, HMC and wavelength moves keep the whole cap in shared memory");
+  static_assert(kX == 0 || kX == 1 || kGen, "HMC and wavelength moves use the general kernel");
   constexpr int kArraysAll = WP::kArrays + (kTree ? 3 : 0) + (kHmc ? 6 : 0);
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int cap_s = P.smem_cap;
-  const size_t per_warp = static_cast<size_t>(kArraysAll) * cap_s + 32 * kRngWords + kPairWords;
+  const size_t per_warp = static_cast<size_t>(kArraysAll) * cap_s + 32 * kRngWords + kPairWords + (kLam ? kMedWords : 0);
   WP w;
   w.sm = smem + static_cast<size_t>(wib) * per_warp;
   w.S = cap_s;
@@ -647,7 +650,9 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
   float* hmz = hmy + cap_s;
   uint4* rng = reinterpret_cast<uint4*>(w.sm + static_cast<size_t>(kArraysAll) * cap_s);  // [32][2] uint4
   DPair* spair = reinterpret_cast<DPair*>(rng + 64);
-  const DMedium& M = P.M;
+  // wavelength sampling: the medium at the chain's current wavelength, in the warp's shared slot
+  DMedium* smed = reinterpret_cast<DMedium*>(reinterpret_cast<float*>(spair) + kPairWords);
+  const DMedium& M = kLam ? *smed : P.M;
   const DRun& R = P.R;
   const uint32_t key0 = static_cast<uint32_t>(R.seed), key1 = static_cast<uint32_t>(R.seed >> 32);
 
@@ -680,6 +685,12 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
     float* gz = gy + cap;
     w.gm = gx;
     w.cap = cap;
+    float lam = 0.f;
+    if constexpr (kLam) {
+      lam = P.lam[c];
+      if (lane == 0) medium_at(P.M, lam, *smed);
+      __syncwarp();
+    }
     // the shared window holds entries [0, min(n, S)); the rest stays in the global block
     for (int i = lane; i < min(n, cap_s); i += 32) {
       w.sm[WP::kX * cap_s + i] = gx[i];
@@ -831,8 +842,40 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
             continue;
           }
         }
+        if constexpr (kLam) {
+          if (mtype == 0u && 1 + static_cast<int>((static_cast<unsigned long long>(v23) * n) >> 23) == n) {
+            // wavelength move (the wavelength is the n-th movable coordinate):
+            // a Gaussian step with the path held.  Only the coefficients
+            // change: log p' - log p = log S(l') - log S(l) - (a' - a + b' - b) L
+            // + (n - 2)(log b' - log b), L the path length summed afresh.
+            const float lam_y = fmaf(R.sigma_lam, __uint_as_float(lo.z), lam);
+            const float lsy = spectrum_log(R, lam_y);
+            const Sums sl = path_sums(w, n, lane);
+            bool acc_l = false;
+            if (isfinite(lsy)) {
+              const float r = logf(lam_y / P.M.lam0);
+              const float ay = P.M.a * expf(-P.M.ka * r), by = P.M.b * expf(-P.M.ks * r);
+              const float lby = P.M.log_b - P.M.ks * r;
+              const float dlp = lsy - spectrum_log(R, lam) - ((ay - M.a) + (by - M.b)) * sl.L +
+                                static_cast<float>(n - 2) * (lby - M.log_b);
+              acc_l = logu < dlp;
+            }
+            if (acc_l) {
+              A.acc_i++;
+              close_state(A, t, R.burn_in, n, L, G);
+              lam = lam_y;
+              __syncwarp();
+              if (lane == 0) medium_at(P.M, lam, *smed);
+              __syncwarp();
+              refresh_caches<kGen>(M, S, zoff, w, n, lane);
+              if (A.nflush >= kFlushAccepts) flush64(A, lane);
+            }
+            __syncwarp();
+            continue;
+          }
+        }
         if (!kTree && mtype == 0u) {
-          const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 1)) >> 23);
+          const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 1 + (kLam ? 1 : 0))) >> 23);
           jj = j;
           inew = j;
           if (j == n - 1) {
@@ -1049,16 +1092,23 @@ __global__ void __launch_bounds__(128, kGen ? 5 : 6) chain_kernel(const ChainPar
     if (lane == 0) {
       P.n[c] = n;
       P.step[c] = t_end;
+      if constexpr (kLam) P.lam[c] = lam;
       if (aborted) { P.status[c] |= ST_ABORTED; atomicOr(P.any_status, ST_ABORTED); }
     }
     __syncwarp();
   }
 }
 
-// Initial paths (one thread per chain).
+// Initial paths (one thread per chain), and initial wavelengths from the
+// spectrum's quantile of u01 of Philox counter (0, 1, chain, init).
 __global__ void init_kernel(const InitParams p) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.total) return;
+  if (p.lam != nullptr) {
+    const uint4 r = philox4x32_10(make_uint4(0u, 1u, static_cast<uint32_t>(c) + p.chain_id0, PUR_INIT),
+                                  static_cast<uint32_t>(p.R.seed), static_cast<uint32_t>(p.R.seed >> 32));
+    p.lam[c] = spectrum_quantile(p.R, u01(r.x));
+  }
   const DPair S = p.pairs[p.chain_pair[c]];
   float* gx = p.xyz + p.chain_base[c];
   float* gy = gx + S.cap;
@@ -1149,6 +1199,8 @@ void launch_one(const ChainParams& p, int grid, int warps_per_block, size_t sm, 
 int kernel_key(int kind, bool grad, bool spill) {
   if (kind == 2) return 8 + (grad ? 1 : 0);
   if (kind == 3) return 10 + (grad ? 1 : 0);
+  if (kind == 6) return 12;
+  if (kind == 7) return 14 + (grad ? 1 : 0);
   return (kind == 1 ? 4 : 0) + (grad ? 2 : 0) + (spill ? 1 : 0);
 }
 
@@ -1157,16 +1209,19 @@ int kernel_key(int kind, bool grad, bool spill) {
 int chain_arrays(bool general, bool grad) { return 6 + (general ? 1 : 0) + (grad ? 1 : 0); }
 
 size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad) {
-  if (kind >= 4) return lane_smem_bytes(smem_cap, warps_per_block, grad);
-  const size_t arrays = static_cast<size_t>(chain_arrays(kind > 0, grad) + (kind == 2 ? 3 : 0) + (kind == 3 ? 6 : 0));
+  if (lane_kind(kind)) return lane_smem_bytes(smem_cap, warps_per_block, grad);
+  const size_t arrays = static_cast<size_t>(chain_arrays(kind > 0 && kind != 7, grad) + (kind == 2 || kind == 7 ? 3 : 0) +
+                                            (kind == 3 ? 6 : 0));
   return static_cast<size_t>(warps_per_block) *
-         (arrays * static_cast<size_t>(smem_cap) + 32u * kRngWords + kPairWords) * sizeof(float);
+         (arrays * static_cast<size_t>(smem_cap) + 32u * kRngWords + kPairWords + (kind == 6 ? kMedWords : 0)) *
+         sizeof(float);
 }
 
 cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block, int smem_cap,
                             int* blocks_per_sm) {
-  if (kind >= 4) return lane_occupancy(warps_per_block, smem_cap, grad, kind == 5, blocks_per_sm);
+  if (lane_kind(kind)) return lane_occupancy(warps_per_block, smem_cap, grad, kind == 5, blocks_per_sm);
   if (kind >= 2 && spill) return cudaErrorInvalidValue;
+  if (kind == 6 && grad) return cudaErrorInvalidValue;
   const size_t sm = chain_smem_bytes(smem_cap, warps_per_block, kind, grad);
   switch (kernel_key(kind, grad, spill)) {
     case 0: return occupancy_of<false, false, false, 0>(warps_per_block, sm, blocks_per_sm);
@@ -1180,14 +1235,18 @@ cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block
     case 8: return occupancy_of<true, false, false, 1>(warps_per_block, sm, blocks_per_sm);
     case 9: return occupancy_of<true, true, false, 1>(warps_per_block, sm, blocks_per_sm);
     case 10: return occupancy_of<true, false, false, 2>(warps_per_block, sm, blocks_per_sm);
+    case 12: return occupancy_of<true, false, false, 3>(warps_per_block, sm, blocks_per_sm);
+    case 14: return occupancy_of<false, false, false, 1>(warps_per_block, sm, blocks_per_sm);
+    case 15: return occupancy_of<false, true, false, 1>(warps_per_block, sm, blocks_per_sm);
     default: return occupancy_of<true, true, false, 2>(warps_per_block, sm, blocks_per_sm);
   }
 }
 
 cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s) {
-  if (kind >= 4) return launch_lane_chain(p, grid, warps_per_block, grad, kind == 5, s);
+  if (lane_kind(kind)) return launch_lane_chain(p, grid, warps_per_block, grad, kind == 5, s);
   if (kind >= 2 && spill) return cudaErrorInvalidValue;
+  if (kind == 6 && grad) return cudaErrorInvalidValue;
   const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block, kind, grad);
   switch (kernel_key(kind, grad, spill)) {
     case 0: launch_one<false, false, false, 0>(p, grid, warps_per_block, sm, s); break;
@@ -1201,6 +1260,9 @@ cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, 
     case 8: launch_one<true, false, false, 1>(p, grid, warps_per_block, sm, s); break;
     case 9: launch_one<true, true, false, 1>(p, grid, warps_per_block, sm, s); break;
     case 10: launch_one<true, false, false, 2>(p, grid, warps_per_block, sm, s); break;
+    case 12: launch_one<true, false, false, 3>(p, grid, warps_per_block, sm, s); break;
+    case 14: launch_one<false, false, false, 1>(p, grid, warps_per_block, sm, s); break;
+    case 15: launch_one<false, true, false, 1>(p, grid, warps_per_block, sm, s); break;
     default: launch_one<true, true, false, 2>(p, grid, warps_per_block, sm, s); break;
   }
   return cudaGetLastError();

@@ -37,6 +37,7 @@ struct DMedium {
   const float* la;     // [n_layers] absorption coefficient per layer
   const float* lb;     // [n_layers] scattering coefficient per layer
   const float* llogb;  // [n_layers] log of lb
+  float lam0, ks, ka;  // wavelength dependence: b ~ (l / lam0)^-ks, a ~ (l / lam0)^-ka (homogeneous)
 };
 
 struct DPair {
@@ -66,6 +67,12 @@ struct DRun {
   unsigned long long burn_in;
   float beta_min;
   int gradients;
+  // wavelength sampled with the path: n_spec >= 2 nodes of the normalised
+  // piecewise-linear spectrum (spec_x increasing, nm; spec_y densities per nm), 0 = off
+  int n_spec;
+  const float* spec_x;
+  const float* spec_y;
+  float sigma_lam;                 // Gaussian step of a wavelength move (nm)
 };
 
 // ---------------------------------------------------------------------------
@@ -451,6 +458,53 @@ __device__ __forceinline__ float log_insert_density(const DMedium& M, const DRun
   const float log2sinh = beta + m_log<F>(1.0f - m_exp<F>(-2.0f * beta));
   return m_log<F>(beta) - beta * cs - log2sinh + 3.0f * m_log<F>(2.0f * gamma) -
          2.0f * m_log<F>(d1 * d2 * (d1 + d2)) - kLog2Pi;
+}
+
+// ---------------------------------------------------------------------------
+// Wavelength as a sampled coordinate (section "Discussion": a wavelength
+// parameter in the path density, sampled along with the vertices).  The
+// chains sample S(l) p_l(path): S the normalised piecewise-linear spectrum,
+// p_l the path density of the homogeneous medium whose coefficients follow
+// power laws in l / lam0.
+// ---------------------------------------------------------------------------
+__device__ inline float spectrum_log(const DRun& R, float lam) {
+  const int K = R.n_spec;
+  if (!(lam >= R.spec_x[0]) || !(lam <= R.spec_x[K - 1])) return kNegInf;
+  int i = 0;
+  while (i + 2 < K && lam > R.spec_x[i + 1]) ++i;
+  const float x0 = R.spec_x[i], x1 = R.spec_x[i + 1], y0 = R.spec_y[i], y1 = R.spec_y[i + 1];
+  const float v = fmaf(y1 - y0, (lam - x0) / (x1 - x0), y0);
+  return v > 0.f ? logf(v) : kNegInf;
+}
+
+// Wavelength at which the spectrum's CDF equals u: walk the intervals'
+// trapezoid areas, then solve y0 s + k s^2 / 2 = t (k the slope) as
+// s = 2 t / (y0 + sqrt(y0^2 + 2 k t)).
+__device__ inline float spectrum_quantile(const DRun& R, float u) {
+  const int K = R.n_spec;
+  float t = u;
+  for (int i = 0; i + 1 < K; ++i) {
+    const float h = R.spec_x[i + 1] - R.spec_x[i];
+    const float y0 = R.spec_y[i], y1 = R.spec_y[i + 1];
+    const float area = 0.5f * h * (y0 + y1);
+    if (t <= area || i + 2 == K) {
+      const float k = (y1 - y0) / h;
+      const float den = y0 + sqrtf(fmaxf(fmaf(2.0f * k, t, y0 * y0), 0.f));
+      const float sv = den > 0.f ? 2.0f * t / den : 0.f;
+      return R.spec_x[i] + fminf(fmaxf(sv, 0.f), h);
+    }
+    t -= area;
+  }
+  return R.spec_x[K - 1];
+}
+
+// The homogeneous medium at wavelength lam (coefficients scaled, log b with them).
+__device__ __forceinline__ void medium_at(const DMedium& M0, float lam, DMedium& out) {
+  out = M0;
+  const float r = logf(lam / M0.lam0);
+  out.b = M0.b * expf(-M0.ks * r);
+  out.a = M0.a * expf(-M0.ka * r);
+  out.log_b = M0.log_b - M0.ks * r;
 }
 
 // ---------------------------------------------------------------------------

@@ -55,6 +55,7 @@ struct ChainParams {
   unsigned int* queue;          // work counter of this launch
   const volatile int* abort_flag;
   uint32_t chain_id0;           // global index of local chain 0 (Philox counter word of a chain)
+  float* lam;                   // [total] wavelength of each chain (wavelength sampling), else null
   int chain_lo, chain_hi;       // chains [lo, hi) of this launch
   unsigned long long n_steps;
   int smem_cap;                 // vertex capacity of one warp's shared arrays
@@ -73,7 +74,11 @@ struct ChainParams {
 // moves (6 more shared arrays per warp, no spill), 4 the lean kernel with one
 // chain per lane and Gaussian vertex moves, 5 the same with MALA moves
 // (pmc_lane.cu; smem_cap is each lane's shared window, entries beyond it in
-// the chain's global block; a work item is 32 chains).
+// the chain's global block; a work item is 32 chains), 6 the general one with
+// the wavelength sampled (the medium at the chain's wavelength in the warp's
+// shared slot, no spill), 7 the lean one with tree moves (3 more shared
+// arrays per warp, no spill).
+inline bool lane_kind(int kind) { return kind == 4 || kind == 5; }
 int chain_arrays(bool general, bool grad);
 cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s);
@@ -100,6 +105,7 @@ struct InitParams {
   int* status;
   int total;
   uint32_t chain_id0;           // global index of local chain 0
+  float* lam;                   // [total] wavelengths drawn from the spectrum (R.n_spec >= 2), else null
   int init_kind, init_k;
   float jitter;
   const float* user_xyz;        // device copy, [total][3][stride] absolute

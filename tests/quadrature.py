@@ -95,3 +95,22 @@ def z3(D, R, lam_s, lam_a, g, n_alpha=(64, 160), n_l=(64, 96), n_v=40, n_phi=48)
             outer = (np.exp(-cext * l0) * b * inner * wl).sum()
             total += 2 * math.pi * math.sin(alpha) * w_alpha * outer / (4 * math.pi)
     return total
+
+
+def spectrum_integral(spectrum_nm, spectrum, lambda_s, lambda_a, lambda0, k_s, k_a, fun, nodes=6):
+    """int S(l) fun(lambda_s(l), lambda_a(l), l) dl: S the piecewise-linear
+    spectrum normalised over its table, lambda_s(l) = lambda_s (l/lambda0)^k_s
+    and lambda_a(l) = lambda_a (l/lambda0)^k_a (coefficients ~ l^-k);
+    Gauss-Legendre with `nodes` points on every interval of the table."""
+    nm, sp = np.asarray(spectrum_nm, float), np.asarray(spectrum, float)
+    area = np.sum(0.5 * np.diff(nm) * (sp[:-1] + sp[1:]))
+    x, w = np.polynomial.legendre.leggauss(nodes)
+    tot = 0.0
+    for i in range(len(nm) - 1):
+        a, b = nm[i], nm[i + 1]
+        for xi, wi in zip(x, w):
+            lam = 0.5 * (a + b) + 0.5 * (b - a) * xi
+            s_val = (sp[i] + (sp[i + 1] - sp[i]) * (lam - a) / (b - a)) / area
+            tot += 0.5 * (b - a) * wi * s_val * fun(lambda_s * (lam / lambda0) ** k_s,
+                                                    lambda_a * (lam / lambda0) ** k_a, lam)
+    return tot

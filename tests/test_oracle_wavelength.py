@@ -18,21 +18,10 @@ from paper_1811_04156_gb300 import scenes as S
 
 
 def _integral_over_spectrum(sc, fun, nodes=6):
-    """int S(l) fun(lambda_s(l), lambda_a(l)) dl over the spectrum table."""
-    nm, sp = np.asarray(sc.run.spectrum_nm, float), np.asarray(sc.run.spectrum, float)
-    area = np.sum(0.5 * np.diff(nm) * (sp[:-1] + sp[1:]))
-    x, w = np.polynomial.legendre.leggauss(nodes)
+    """int S(l) fun(lambda_s(l), lambda_a(l), l) dl over the spectrum table."""
     m = sc.medium
-    tot = 0.0
-    for i in range(len(nm) - 1):
-        a, b = nm[i], nm[i + 1]
-        for xi, wi in zip(x, w):
-            lam = 0.5 * (a + b) + 0.5 * (b - a) * xi
-            s_val = (sp[i] + (sp[i + 1] - sp[i]) * (lam - a) / (b - a)) / area
-            ls = m.lambda_s * (lam / m.lambda0) ** m.k_s
-            la = m.lambda_a * (lam / m.lambda0) ** m.k_a
-            tot += 0.5 * (b - a) * wi * s_val * fun(ls, la, lam)
-    return tot
+    return Q.spectrum_integral(sc.run.spectrum_nm, sc.run.spectrum, m.lambda_s, m.lambda_a, m.lambda0, m.k_s, m.k_a,
+                               fun, nodes)
 
 
 def test_spectrum_normalised_and_quantile_inverts_it(oracle_lib):
