@@ -62,8 +62,10 @@ WORKLOAD_TEXT = {
 # csrc/pmc_lane.cu + csrc/pmc_device.cuh, in that order): warp instructions
 # per proposal (window 20) and DRAM bytes (read + write) of a 65,536-chain
 # launch.  With another source the bench reports them as null.
-LANE_CAPTURE = {"source_sha256": "", "inst_per_proposal": None, "dram_bytes_per_launch": None,
-                "capture": ""}
+LANE_CAPTURE = {"source_sha256": "286930625f08149bc1e804bfe659e6d8b55aa6a5496d1c13d8de60878a22fd51",
+                "inst_per_proposal": 59.65, "dram_bytes_per_launch": 79354624.0,
+                "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum (56.9 MB + 22.4 MB) of one "
+                           "65,536-chain x 100,000-step launch, window 20, 1 warp per CTA"}
 
 
 def lane_kernel_source_hash() -> str:
@@ -95,6 +97,8 @@ def parse_args(argv=None):
                    help="skip the other workloads' rates and the time-to-1%% comparison after the timed steps")
     p.add_argument("--ttt-limit", type=float, default=25.0, help="seconds per method of the time-to-target runs")
     p.add_argument("--warps-per-block", type=int, default=0)
+    p.add_argument("--within", choices=["default", "perturb", "mala", "tree"], default="default",
+                   help="within-dimension moves of the timed workload (default: the workload's own)")
     p.add_argument("--layout", choices=["auto", "warp", "lane"], default="auto",
                    help="chain layout of the kernel: the autotuner's choice, one warp or one lane per chain")
     p.add_argument("--smem-window", type=int, default=0,
@@ -402,6 +406,11 @@ def ours(args):
     medium = api.Medium(ctx, sc.medium)
     geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
     sc.run.layout = {"auto": 0, "warp": 1, "lane": 2}[args.layout]  # scenes.LAYOUT_*
+    if args.within != "default":
+        from paper_1811_04156_gb300 import scenes as S
+        sc.run.within = {"perturb": S.WITHIN_PERTURB, "mala": S.WITHIN_MALA, "tree": S.WITHIN_TREE}[args.within]
+        if args.within == "tree":
+            sc.run.sigma = 0.3
     chains = api.Chains(ctx, medium, geom, sc.run, warps_per_block=args.warps_per_block,
                         smem_window=args.smem_window, chain_window=(lo, hi))
     stream = torch.cuda.current_stream()
@@ -497,15 +506,18 @@ def ours(args):
     kind = li[0]["general"] if len(li) == 1 else None
     roof = lane_op_roofline(est, rate, n_sm, clk, pipes)
     roof["kernel"] = "lane_chain_kernel" if kind in (4, 5) else "chain_kernel"
+    if args.within != "default":
+        roof["within"] = args.within
     roof["kernel_ms"] = statistics.mean(kern_ms)
     roof["clock_max_mhz"] = float(peaks.get("sm_max_mhz", 2070.0))
     roof["peak_kind"] = peak_kind
     # counters of the committed capture, only while the kernel source matches it
     fresh = (kind == 4 and sc.name == "detector" and li[0]["smem_cap"] == 20 and
              LANE_CAPTURE["source_sha256"] == lane_kernel_source_hash())
-    roof["traffic"] = LANE_CAPTURE["dram_bytes_per_launch"] * n_local / 65536.0 if fresh else None
-    roof["traffic_source"] = LANE_CAPTURE["capture"] if fresh else \
-        "null: no ncu capture of this kernel source and workload"
+    have_traffic = fresh and LANE_CAPTURE["dram_bytes_per_launch"] is not None and sc.run.n_steps == 100_000
+    roof["traffic"] = LANE_CAPTURE["dram_bytes_per_launch"] * n_local / 65536.0 if have_traffic else None
+    roof["traffic_source"] = LANE_CAPTURE["capture"] if have_traffic else \
+        "null: no ncu capture of this kernel source and launch"
     issue = None
     if fresh:
         inst = LANE_CAPTURE["inst_per_proposal"]
@@ -524,7 +536,8 @@ def ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak" if len(sc.pairs) == 1 else "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT.get(sc.name, sc.name),
+            "config": {"workload": WORKLOAD_TEXT.get(sc.name, sc.name) +
+                       ("" if args.within == "default" else f", {args.within} moves"),
                        "chains": sc.total_chains, "steps_per_chain": sc.run.n_steps,
                        "vertex_cap": max(p.cap for p in sc.pairs), "global_batch": sc.total_chains,
                        "parallelism": f"sharded chain windows x{world}" if world > 1 else "1 GPU",
