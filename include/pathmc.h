@@ -659,7 +659,9 @@ PMC_API int pmc_trace_paths(pmc_ctx_t ctx, pmc_medium_t medium, pmc_geom_t geom,
  * 0, 1, 2, ... of the pair's tracer (pmc_trace_paths' thinning, Philox key
  * seed + p, at most cap - 2 scatterings) are traced in rounds until at least
  * as many photons were kept as the pair has chains, and chain i of the pair
- * takes the path of the i-th kept photon in photon order (pmc_seed_select):
+ * (its index within the pair, also when a chain window holds only some of
+ * the pair's chains, so sharded sets seed exactly as the whole set) takes
+ * the path of the i-th kept photon in photon order (pmc_seed_select):
  * the first kept photons of a sequential tracer, i.e. independent exact draws
  * from the normalised cap-truncated path density, whatever order the GPU
  * finds them in.  Rounds trace photons_per_round photons each, at most

@@ -190,6 +190,7 @@ struct pmc_chains_s {
   std::vector<DPair> h_pairs;
   std::vector<long long> h_base;
   std::vector<int> h_pair_of;
+  std::vector<int> h_pair_first;  // per pair: index within the pair of the window's first chain
   long long xyz_floats = 0;
   DPair* d_pairs = nullptr;
   int* d_chain_pair = nullptr;
@@ -859,9 +860,12 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   }
 
   ch->h_pairs = geom->pairs;
-  for (auto& d : ch->h_pairs) {
+  ch->h_pair_first.assign(ch->h_pairs.size(), 0);
+  for (size_t p = 0; p < ch->h_pairs.size(); ++p) {
+    DPair& d = ch->h_pairs[p];
     // the pair's chains inside the window, numbered from the window's first chain
     const long long a = std::max<long long>(d.chain0, lo), b = std::min<long long>(d.chain0 + d.n_chains, hi);
+    ch->h_pair_first[p] = b > a ? static_cast<int>(a - d.chain0) : 0;
     d.chain0 = static_cast<int>(std::min<long long>(a, hi) - lo);
     d.n_chains = static_cast<int>(std::max<long long>(b - a, 0));
     if (d.chain0 < 0 || d.chain0 + d.n_chains > hi - lo) return fail(PMC_ERR_INVALID, "chain window bookkeeping");
@@ -1937,23 +1941,31 @@ int pmc_seed_from_tracer(pmc_chains_t ch, uint64_t seed, uint64_t photons_per_ro
   CK(cudaSetDevice(ch->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const float rr = std::isfinite(r_reject) ? static_cast<float>(r_reject) : std::numeric_limits<float>::infinity();
-  int need_max = 0;
-  for (const DPair& d : ch->h_pairs) need_max = std::max(need_max, d.n_chains);
-  // capacity of one round's accepted indices: twice the largest pair's chains
+  // chain i of a pair (index within the pair, whatever chain window holds
+  // it) takes the i-th accepted photon, so a sharded set seeds its chains
+  // exactly as the whole set does
+  int need_max = 0, local_max = 0;
+  for (size_t p = 0; p < ch->h_pairs.size(); ++p) {
+    need_max = std::max(need_max, ch->h_pair_first[p] + ch->h_pairs[p].n_chains);
+    local_max = std::max(local_max, ch->h_pairs[p].n_chains);
+  }
+  // capacity of one round's accepted indices: twice the largest pair's need
   const unsigned int cap_idx = static_cast<unsigned int>(std::max(2 * need_max, 4096));
   unsigned long long* d_idx = nullptr;
   unsigned long long* d_sel = nullptr;
   unsigned int* d_count = nullptr;
   CK(dalloc(&d_idx, cap_idx));
   int rc = PMC_OK;
-  cudaError_t e = cudaMalloc(&d_sel, sizeof(unsigned long long) * std::max(need_max, 1));
+  cudaError_t e = cudaMalloc(&d_sel, sizeof(unsigned long long) * std::max(local_max, 1));
   if (e == cudaSuccess) e = cudaMalloc(&d_count, sizeof(unsigned int));
   std::vector<uint64_t> got, sel;
   for (int p = 0; p < ch->n_pairs && e == cudaSuccess && rc == PMC_OK; ++p) {
     const DPair& d = ch->h_pairs[p];
-    const size_t need = static_cast<size_t>(d.n_chains);
+    const size_t n_local = static_cast<size_t>(d.n_chains);
+    const size_t first = static_cast<size_t>(ch->h_pair_first[p]);
+    const size_t need = first + n_local;
     if (photons_used) photons_used[p] = 0;
-    if (need == 0) continue;
+    if (n_local == 0) continue;
     const unsigned long long key = seed + static_cast<unsigned long long>(p);
     got.clear();
     unsigned long long photon = 0, per_round = photons_per_round;
@@ -1988,9 +2000,9 @@ int pmc_seed_from_tracer(pmc_chains_t ch, uint64_t seed, uint64_t photons_per_ro
     sel.resize(need);
     rc = pmc_seed_select(got.data(), got.size(), need, sel.data());
     if (rc != PMC_OK) break;
-    e = cudaMemcpyAsync(d_sel, sel.data(), sizeof(uint64_t) * need, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(d_sel, sel.data() + first, sizeof(uint64_t) * n_local, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-      e = launch_seed_record(ch->med->d, d, key, rr, d_sel, d.chain0, static_cast<int>(need), ch->d_chain_base,
+      e = launch_seed_record(ch->med->d, d, key, rr, d_sel, d.chain0, static_cast<int>(n_local), ch->d_chain_base,
                              ch->d_xyz, ch->d_n, ch->d_status, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // sel is reused by the next pair
     if (photons_used) photons_used[p] = photon;

@@ -90,3 +90,27 @@ def test_one_launch_replays_the_per_class_launches(api, ctx):
     assert np.array_equal(per_class.read_accumulators(), one.read_accumulators())
     for a, b in zip(per_class.read_estimator(), one.read_estimator()):
         assert a["intensity"] == b["intensity"] and a["std_err"] == b["std_err"]
+
+
+def test_windows_seed_from_the_tracer_as_the_whole_set(api, ctx):
+    """pmc_seed_from_tracer gives chain i of a pair the i-th accepted photon
+    whatever chain window holds it: windows seed, and then step, exactly as
+    the whole set."""
+    sc = S.plain(n_chains=1000, n_steps=0, cap=64)
+    sc.pairs = [S.Pair(0, 0, 700, 64), S.Pair(0, 0, 300, 64)]
+    sc.run.burn_in = 0
+    sc.run.layout = S.LAYOUT_WARP
+    medium = api.Medium(ctx, sc.medium)
+    geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
+    shape = dict(warps_per_block=2)
+    whole = api.Chains(ctx, medium, geom, sc.run, **shape)
+    api.seed_from_tracer(whole, seed=31, photons_per_round=1 << 22)
+    whole.run_steps(500)
+    xw, nw, _ = whole.read_states()
+    for win in ((0, 350), (350, 820), (820, 1000)):
+        part = api.Chains(ctx, medium, geom, sc.run, chain_window=win, **shape)
+        api.seed_from_tracer(part, seed=31, photons_per_round=1 << 22)
+        part.run_steps(500)
+        x, n, _ = part.read_states()
+        assert np.array_equal(n, nw[win[0]:win[1]]) and np.array_equal(x, xw[win[0]:win[1]]), win
+        part.close()
