@@ -216,7 +216,7 @@ struct pmc_chains_s {
   bool grad = false;               // keep d log sigma / dg per vertex
   bool autotune = false;           // warps per block chosen by timing
   int layout = PMC_LAYOUT_AUTO;    // PMC_LAYOUT_*: which chain layouts the autotuner may pick
-  int lane_kind = 0;               // lane layout's kernel kind (4 Gaussian, 5 MALA moves); 0: not eligible
+  int lane_kind = 0;               // lane layout's kernel kind (4 Gaussian, 5 MALA, 8 tree moves); 0: not eligible
   int init_kind = 0, init_k = 0;
   float init_jitter = 0.f;
   QrefPair* d_qp = nullptr;       // reference-density tables (pmc_bridge)
@@ -657,7 +657,7 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
   float* slam = nullptr;  // wavelength sampling: the probes' copy of the wavelengths
   // cache key: the warp kernel instance, the layout request and which lane
   // kernel (if any) the run may use; per class also whether its paths are short
-  const int kind = (((ch->general * 2 + ch->grad) * 3 + ch->layout) * 8 + ch->lane_kind) * 2;
+  const int kind = (((ch->general * 2 + ch->grad) * 3 + ch->layout) * 16 + ch->lane_kind) * 2;
   auto bucket_of = [](int chains) { return 31 - __builtin_clz(static_cast<unsigned>(std::max(1, chains))); };
   bool need = false;
   for (auto& cl : ch->classes)
@@ -892,10 +892,14 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
   ch->layout = r->layout;
   if (lean_physics && r->within == PMC_WITHIN_PERTURB && !ch->lam_on) ch->lane_kind = 4;
   if (lean_physics && r->within == PMC_WITHIN_MALA) ch->lane_kind = 5;
+  if (lean_physics && r->within == PMC_WITHIN_TREE) ch->lane_kind = 8;
   if (r->layout == PMC_LAYOUT_LANE && ch->lane_kind == 0)
     return fail(PMC_ERR_INVALID, "the lane layout runs lean chains only (homogeneous medium, isotropic emission, "
-                                 "rho = 1, Henyey-Greenstein, Gaussian or MALA vertex moves)");
-  const int n_arrays = chain_arrays(ch->general > 0 && ch->general != 7, ch->grad);
+                                 "rho = 1, Henyey-Greenstein, Gaussian, MALA or tree moves)");
+  // the lane layout's tree moves keep the proposed path beyond the lane's
+  // shared window in more arrays of the chain's global block
+  const int n_arrays =
+      chain_arrays(ch->general > 0 && ch->general != 7, ch->grad) + (ch->lane_kind == 8 ? kLaneTreeArrays : 0);
   const int T = ch->total;
   ch->h_base.resize(T);
   ch->h_pair_of.resize(T);

@@ -31,6 +31,7 @@
 #include <climits>
 
 #include "pmc_internal.h"
+#include "pmc_tree.cuh"
 
 namespace pmc {
 
@@ -309,93 +310,7 @@ __device__ int select_segment(const WP& w, int nseg, float u, float& total, int 
   return __shfl_sync(kFull, k, owner);
 }
 
-// ---------------------------------------------------------------------------
-// Tree coordinates.  Interior vertex m = (k + l)/2 sits in the bispherical
-// system of its foci f_k, f_l (root: f_0, f_{n-1}) with coordinates
-// zeta = atanh(cos s), t = ln(d1/d2) and the azimuth phi about
-// e = (f_l - f_k)/|f_l - f_k| in the frame (xi, eta): eta is the unit normal
-// e_p x (f_p - mid_p) of the parent's triangle (the parent's axes turned by
-// its phi), xi = eta x e; the root's xi is vref projected normal to e.  The
-// volume element is (d1 d2 / (2 gamma))^3 sin^2 s per node.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
-  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-
-// Interval (k, l) of node j at depth d (binary descent on the bits of j, most
-// significant first) and its parent's interval (kp = -1 at the root); false
-// when the interval holds no vertex.
-__device__ __forceinline__ bool tree_interval(int n, int d, int j, int& k, int& l, int& kp, int& lp) {
-  k = 0;
-  l = n - 1;
-  kp = lp = -1;
-  for (int b = d - 1; b >= 0; --b) {
-    if (l - k < 2) return false;
-    const int mid = (k + l) >> 1;
-    kp = k;
-    lp = l;
-    if ((j >> b) & 1) k = mid;
-    else l = mid;
-  }
-  return l - k >= 2;
-}
-
-struct TreeFrame {
-  float3 e, xi, eta, mid;
-  float gamma;
-};
-
-template <class PosF>
-__device__ __forceinline__ TreeFrame tree_frame(PosF pos, int k, int l, int kp, int lp, float3 vref) {
-  TreeFrame F;
-  const float3 A = pos(k), B = pos(l);
-  const float3 r = B - A;
-  const float rr = dot(r, r);
-  const float ir = rsqrtf(rr);
-  F.e = ir * r;
-  F.gamma = 0.5f * rr * ir;
-  F.mid = 0.5f * (A + B);
-  bool have = false;
-  if (kp >= 0) {
-    const int p = (kp + lp) >> 1;
-    const float3 Ap = pos(kp), Bp = pos(lp);
-    const float3 ep = Bp - Ap, rho = pos(p) - 0.5f * (Ap + Bp);
-    float3 nrm = cross3(ep, rho);
-    const float nn2 = dot(nrm, nrm);
-    if (nn2 > 1e-12f * dot(ep, ep) * dot(rho, rho) && nn2 > 0.f) {
-      nrm = nrm - dot(nrm, F.e) * F.e;
-      F.eta = rsqrtf(dot(nrm, nrm)) * nrm;
-      F.xi = cross3(F.eta, F.e);
-      have = true;
-    }
-  }
-  if (!have) {
-    const float3 x = vref - dot(vref, F.e) * F.e;
-    F.xi = rsqrtf(dot(x, x)) * x;
-    F.eta = cross3(F.e, F.xi);
-  }
-  return F;
-}
-
-// Foci (k, l) of interior vertex m and its parent's foci (kp = -1 at the root).
-__device__ __forceinline__ void tree_node_of(int m, int n, int& k, int& l, int& kp, int& lp) {
-  k = 0;
-  l = n - 1;
-  kp = lp = -1;
-  for (;;) {
-    const int mid = (k + l) >> 1;
-    if (mid == m) return;
-    kp = k;
-    lp = l;
-    if (m < mid) l = mid;
-    else k = mid;
-  }
-}
-
-// Transcendentals here use the SFU forms (a few ulp): the map only has to be
-// the same deterministic bijection in both directions up to rounding, far
-// below the Monte-Carlo error, as for the density in the chain kernel.
-// One whole-path tree proposal: the end vertex goes to `end`, every node's
+// One whole-path tree proposal (tree coordinates: pmc_tree.cuh): the end vertex goes to `end`, every node's
 // coordinates step by `step` times its normals; the new path is built level
 // by level into nx/ny/nz.  Returns log p(x') + log J(x') - log J(x)
 // (-inf if x' has zero density).  Pass 1 (all lanes over all nodes): the old
@@ -412,29 +327,10 @@ __device__ float tree_propose(const DMedium& M, const DPair& S, float zoff, cons
   auto npos = [&](int i) { return f3(nx[i], ny[i], nz[i]); };
   float lj = 0.f;  // log J(x') - log J(x), lane partials
   for (int m = 1 + lane; m <= n - 2; m += 32) {
-    int k, l, kp, lp;
-    tree_node_of(m, n, k, l, kp, lp);
-    const TreeFrame Fo = tree_frame(opos, k, l, kp, lp, vref);
-    const float3 P = w.pos(m);
-    const float3 a = w.pos(k) - P, b = w.pos(l) - P;
-    const float d1 = sqrtf(dot(a, a)), d2 = sqrtf(dot(b, b));
-    const float3 u = (1.0f / d1) * a, v = (1.0f / d2) * b;
-    const float3 up = u + v, um = u - v;
-    const float opc = 0.5f * dot(up, up), omc = 0.5f * dot(um, um);
-    const float3 rho = P - Fo.mid;
-    lj -= 3.0f * __logf(d1 * d2 / (2.0f * Fo.gamma)) + __logf(opc * omc);
-    // normal steps (the oracle's draw: Box-Muller on one Philox block)
-    const uint4 rn = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32),
-                                              static_cast<uint32_t>(c), PUR_TREE | (static_cast<uint32_t>(m) << 8)),
-                                   key0, key1);
-    float s1, c1, s2, c2;
-    const float r1 = sqrtf(-2.0f * __logf(u01(rn.x)));
-    sincospif(2.0f * u01(rn.y), &s1, &c1);
-    const float r2 = sqrtf(-2.0f * __logf(u01(rn.z)));
-    sincospif(2.0f * u01(rn.w), &s2, &c2);
-    nx[m] = fmaf(step, r1 * c1, 0.5f * __logf(__fdividef(opc, omc)));
-    ny[m] = fmaf(step, r1 * s1, __logf(__fdividef(d1, d2)));
-    nz[m] = fmaf(step, r2 * c2, atan2f(dot(rho, Fo.eta), dot(rho, Fo.xi)));
+    const float3 zc = tree_step_node(opos, m, n, vref, step, t, static_cast<uint32_t>(c), key0, key1, lj);
+    nx[m] = zc.x;
+    ny[m] = zc.y;
+    nz[m] = zc.z;
   }
   if (lane == 0) {
     nx[0] = ny[0] = nz[0] = 0.f;
@@ -452,23 +348,10 @@ __device__ float tree_propose(const DMedium& M, const DPair& S, float zoff, cons
       any = any || __any_sync(kAll, valid);
       if (valid) {
         const int m = (k + l) >> 1;
-        const float zeta = nx[m], tt = ny[m], phi = nz[m];
-        const TreeFrame Fn = tree_frame(npos, k, l, kp, lp, vref);
-        const float ez = __expf(zeta), emz = __expf(-zeta);
-        const float sn = 2.0f / (ez + emz);                 // 1 / cosh zeta = sin s
-        const float omcs = 2.0f / (1.0f + ez * ez);          // 1 - tanh zeta
-        const float eh = __expf(0.5f * tt), ieh = __expf(-0.5f * tt);
-        const float sh = 0.5f * (eh - ieh);                 // sinh(t/2)
-        const float den = fmaf(2.0f * sh, sh, omcs);        // cosh t - cos s
-        float sp, cp;
-        __sincosf(phi, &sp, &cp);
-        const float sc = Fn.gamma / den;
-        const float sht = 2.0f * sh * (0.5f * (eh + ieh));    // sinh t = 2 sinh(t/2) cosh(t/2)
-        const float3 fnew = Fn.mid + sc * (sht * Fn.e + sn * (cp * Fn.xi + sp * Fn.eta));
+        const float3 fnew = tree_place_node(npos, k, l, kp, lp, vref, f3(nx[m], ny[m], nz[m]), lj);
         nx[m] = fnew.x;
         ny[m] = fnew.y;
         nz[m] = fnew.z;
-        lj += 3.0f * __logf(sc) + 2.0f * __logf(sn);
       }
     }
     __syncwarp();
@@ -717,13 +600,7 @@ __global__ void __launch_bounds__(128, (kGen || kX != 0) ? 5 : 6) chain_kernel(c
 
     const float3 cS = f3(S.c[0], S.c[1], S.c[2]);
     float3 vref = f3(1.f, 0.f, 0.f);
-    if constexpr (kTree) {
-      // root frame reference: first vector of the orthonormal completion of
-      // the unit source -> sensor-centre direction
-      const float3 cc = cS + f3(S.c_lo[0], S.c_lo[1], S.c_lo[2]);
-      float3 e2;
-      onb(rsqrtf(dot(cc, cc)) * cc, vref, e2);
-    }
+    if constexpr (kTree) vref = tree_vref(S);  // the root frame's reference direction
     unsigned long long done = 0;
     bool aborted = false;
     for (unsigned long long s0 = 0; s0 < P.n_steps; s0 += 32) {
@@ -1209,7 +1086,7 @@ int kernel_key(int kind, bool grad, bool spill) {
 int chain_arrays(bool general, bool grad) { return 6 + (general ? 1 : 0) + (grad ? 1 : 0); }
 
 size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad) {
-  if (lane_kind(kind)) return lane_smem_bytes(smem_cap, warps_per_block, grad);
+  if (lane_kind(kind)) return lane_smem_bytes(smem_cap, warps_per_block, grad, kind == 8);
   const size_t arrays = static_cast<size_t>(chain_arrays(kind > 0 && kind != 7, grad) + (kind == 2 || kind == 7 ? 3 : 0) +
                                             (kind == 3 ? 6 : 0));
   return static_cast<size_t>(warps_per_block) *
@@ -1219,7 +1096,7 @@ size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad) 
 
 cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block, int smem_cap,
                             int* blocks_per_sm) {
-  if (lane_kind(kind)) return lane_occupancy(warps_per_block, smem_cap, grad, kind == 5, blocks_per_sm);
+  if (lane_kind(kind)) return lane_occupancy(kind, warps_per_block, smem_cap, grad, blocks_per_sm);
   if (kind >= 2 && spill) return cudaErrorInvalidValue;
   if (kind == 6 && grad) return cudaErrorInvalidValue;
   const size_t sm = chain_smem_bytes(smem_cap, warps_per_block, kind, grad);
@@ -1244,7 +1121,7 @@ cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block
 
 cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s) {
-  if (lane_kind(kind)) return launch_lane_chain(p, grid, warps_per_block, grad, kind == 5, s);
+  if (lane_kind(kind)) return launch_lane_chain(p, kind, grid, warps_per_block, grad, s);
   if (kind >= 2 && spill) return cudaErrorInvalidValue;
   if (kind == 6 && grad) return cudaErrorInvalidValue;
   const size_t sm = chain_smem_bytes(p.smem_cap, warps_per_block, kind, grad);

@@ -77,8 +77,14 @@ struct ChainParams {
 // the chain's global block; a work item is 32 chains), 6 the general one with
 // the wavelength sampled (the medium at the chain's wavelength in the warp's
 // shared slot, no spill), 7 the lean one with tree moves (3 more shared
-// arrays per warp, no spill).
-inline bool lane_kind(int kind) { return kind == 4 || kind == 5; }
+// arrays per warp, no spill), 8 the lean one with one chain per lane and tree
+// moves (kLaneTreeArrays more arrays per lane for the proposed path, in the
+// lane's shared window and beyond it in the chain's global block).
+inline bool lane_kind(int kind) { return kind == 4 || kind == 5 || kind == 8; }
+// kind 8: arrays of the proposed path (x, y, z and the per-vertex terms of
+// its acceptance ratio) after the lane layout's own, in shared memory and in
+// the chain's global block
+constexpr int kLaneTreeArrays = 4;
 int chain_arrays(bool general, bool grad);
 cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,
                          cudaStream_t s);
@@ -86,11 +92,11 @@ size_t chain_smem_bytes(int smem_cap, int warps_per_block, int kind, bool grad);
 cudaError_t chain_occupancy(int kind, bool grad, bool spill, int warps_per_block, int smem_cap,
                             int* blocks_per_sm);
 
-// pmc_lane.cu (kinds 4 and 5 above; `grad` adds the per-vertex d log sigma /
-// dg array, `mala` selects MALA vertex moves)
-size_t lane_smem_bytes(int window, int warps_per_block, bool grad);
-cudaError_t lane_occupancy(int warps_per_block, int window, bool grad, bool mala, int* blocks_per_sm);
-cudaError_t launch_lane_chain(const ChainParams& p, int grid, int warps_per_block, bool grad, bool mala,
+// pmc_lane.cu (kinds 4, 5 and 8 above; `grad` adds the per-vertex d log
+// sigma / dg array, `tree` the proposed path's three arrays)
+size_t lane_smem_bytes(int window, int warps_per_block, bool grad, bool tree);
+cudaError_t lane_occupancy(int kind, int warps_per_block, int window, bool grad, int* blocks_per_sm);
+cudaError_t launch_lane_chain(const ChainParams& p, int kind, int grid, int warps_per_block, bool grad,
                               cudaStream_t s);
 
 struct InitParams {

@@ -28,12 +28,20 @@ def ctx(api):
     return api.Context(0)
 
 
-@pytest.mark.parametrize("layout,world", [(S.LAYOUT_WARP, 2), (S.LAYOUT_LANE, 3)])
-def test_windows_replay_the_whole_set(api, ctx, layout, world):
+@pytest.mark.parametrize("layout,world,within", [(S.LAYOUT_WARP, 2, S.WITHIN_PERTURB),
+                                                 (S.LAYOUT_LANE, 3, S.WITHIN_PERTURB),
+                                                 (S.LAYOUT_LANE, 3, S.WITHIN_TREE)])
+def test_windows_replay_the_whole_set(api, ctx, layout, world, within):
+    """With tree moves on the lane layout the warp pools its chains' moves, so
+    a window regroups the chains that share a warp (and leaves lanes without
+    a chain): a chain's arithmetic must not depend on its warp-mates."""
     sc = S.batched_small(n_chains=256, n_steps=3000)
     if layout == S.LAYOUT_LANE:
         sc.pairs = [p for p in sc.pairs if p.cap == 3] + [S.Pair(0, 4, 256, 64)]
     sc.run.layout = layout
+    sc.run.within = within
+    if within == S.WITHIN_TREE:
+        sc.run.sigma = 0.5
     medium = api.Medium(ctx, sc.medium)
     geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
     shape = dict(warps_per_block=2, smem_window=16 if layout == S.LAYOUT_LANE else 0)
