@@ -59,19 +59,20 @@ WORKLOAD_TEXT = {
 
 # Counters of the lane kernel on the detector workload from an ncu capture,
 # valid only for the kernel source they were taken from (sha256 of
-# csrc/pmc_lane.cu + csrc/pmc_device.cuh, in that order): warp instructions
-# per proposal (window 20) and DRAM bytes (read + write) of a 65,536-chain
-# launch.  With another source the bench reports them as null.
-LANE_CAPTURE = {"source_sha256": "286930625f08149bc1e804bfe659e6d8b55aa6a5496d1c13d8de60878a22fd51",
-                "inst_per_proposal": 59.65, "dram_bytes_per_launch": 79354624.0,
-                "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum (56.9 MB + 22.4 MB) of one "
+# csrc/pmc_lane.cu, csrc/pmc_device.cuh, csrc/pmc_tree.cuh and
+# csrc/pmc_internal.h, in that order): warp instructions per proposal (window
+# 20) and DRAM bytes (read + write) of a 65,536-chain launch.  With another
+# source the bench reports them as null.
+LANE_CAPTURE = {"source_sha256": "4e375e458afe2cfc1016a1fa68aa5998ca65cf1bba2a566addf314d00034dadf",
+                "inst_per_proposal": 59.62, "dram_bytes_per_launch": 81380864.0,
+                "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum (57.5 MB + 23.9 MB) of one "
                            "65,536-chain x 100,000-step launch, window 20, 1 warp per CTA"}
 
 
 def lane_kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in ("pmc_lane.cu", "pmc_device.cuh"):
+    for name in ("pmc_lane.cu", "pmc_device.cuh", "pmc_tree.cuh", "pmc_internal.h"):
         with open(os.path.join(ROOT, "paper_1811_04156_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
