@@ -281,9 +281,10 @@ __device__ __forceinline__ void lane_refresh_sums(const LanePath<kRow>& w, int n
 // Every step of one chain's residency, on one lane.  Mirrors the warp
 // kernel's step: move draw, proposal, change of log p over the changed
 // window, acceptance, commit.  The change of log p over the window is summed
-// in the warp kernel's shuffle order; the T_b sums over the path run
-// sequentially here (the warp kernel's tree sums can differ in the last bit,
-// which moves a decision only when it falls within that of the threshold).
+// in the warp kernel's shuffle order; T_b comes from the running path length
+// here (the warp kernel sums the cached tau_b afresh; the two differ by FP32
+// rounding, which moves a decision only when it falls within that of the
+// threshold).
 template <bool kGrad, bool kMala, bool kTree>
 __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own, float* col, int W, uint32_t key0,
                                           uint32_t key1, TreeSlot* slots) {
@@ -388,24 +389,17 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
       const float ub0 = u01(rb.x), ub1 = u01(rb.y), ub2 = u01(rb.z), ub3 = u01(rb.w);
 
       // work that several move kinds share runs once, with every lane: the
-      // azimuth of within-dimension moves, a second sincos (the interior
-      // move's third normal, the birth's phi), and T_b = sum of tau_b over the
-      // current path (births and deaths)
+      // azimuth of within-dimension moves and a second sincos (the interior
+      // move's third normal, the birth's phi).  T_b, the sum of tau_b over the
+      // current path (births and deaths), is b times the path length in a
+      // homogeneous medium: the running length L, updated at every accepted
+      // move and summed afresh from the cached lengths every kRefresh steps
+      // (it differs from a fresh FP32 sum by rounding only)
       const bool within = um < R.thr_within, birth = !within && um < R.thr_birth, death = !within && !birth;
       float s1, c1, sB, cB;
       sincospif(2.0f * ub1, &s1, &c1);
       sincospif(2.0f * (within ? ub3 : ub2), &sB, &cB);
-      float Tb = 0.f;
-      {
-        // segments below the window edge from shared memory, the rest from the
-        // global block, in index order
-        const int m = ((birth && n < cap) || (death && n > 2)) ? n - 1 : 0;
-        const int m1 = min(m, W);
-        const float* pl = w.sm + ALEN * W * kRow;
-#pragma unroll 4
-        for (int q = 0; q < m1; ++q) Tb += M.b * pl[q * kRow];
-        for (int q = W; q < m; ++q) Tb += M.b * w.gm[ALEN * cap + q];
-      }
+      const float Tb = M.b * L;
 
       if constexpr (kTree) {
         if (within) {
@@ -615,7 +609,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
           dlen = (f[0] + f[1]) + f[2];
           if constexpr (kGrad) dG = (gd[0] + gd[1]) + gd[2];
           if (move == MV_DEATH) {
-            // T_b of the reduced path from the current one (summed afresh above)
+            // T_b of the reduced path from the current one
             const float dtb = (e[0] + e[1]) + e[2];
             const float Tb_red = Tb + dtb;
             const float tb_new = M.b * nlen[0];
