@@ -75,8 +75,8 @@ extern "C" {
 #define PMC_LAYOUT_AUTO 0      /* autotuner's choice (warp layout when warps_per_block is given) */
 #define PMC_LAYOUT_WARP 1      /* one warp per chain */
 #define PMC_LAYOUT_LANE 2      /* one lane per chain: lean physics only (homogeneous medium, isotropic
-                                  emission, rho = 1, pure Henyey-Greenstein) with Gaussian or MALA
-                                  vertex moves */
+                                  emission, rho = 1, pure Henyey-Greenstein) with Gaussian, MALA or
+                                  tree moves */
 
 #define PMC_FLAG_GRADIENTS 1   /* accumulate score terms for pmc_grad_estimator */
 #define PMC_FLAG_NO_GRAPH 2    /* launch kernels directly instead of replaying a CUDA graph */
@@ -401,7 +401,8 @@ PMC_API int pmc_total_chains(pmc_chains_t chains);
  * with one warp per chain, 2 the general kernel with tree moves, 3 with HMC
  * moves, 4 the lean kernel with one chain per lane (32 chains per warp), 5
  * the same with MALA moves, 6 the general kernel sampling the wavelength, 7
- * the lean kernel with tree moves.
+ * the lean kernel with tree moves, 8 the lean kernel with one chain per lane
+ * and tree moves (each warp's tree moves pooled over its 32 lanes).
  * Returns the number of classes in *n_classes;
  * writes at most max_rows rows. */
 PMC_API int pmc_chains_launch_info(pmc_chains_t chains, int* out, int max_rows, int* n_classes);
