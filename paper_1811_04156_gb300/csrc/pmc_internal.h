@@ -78,12 +78,13 @@ struct ChainParams {
 // the wavelength sampled (the medium at the chain's wavelength in the warp's
 // shared slot, no spill), 7 the lean one with tree moves (3 more shared
 // arrays per warp, no spill), 8 the lean one with one chain per lane and tree
-// moves (kLaneTreeArrays more arrays per lane for the proposed path, in the
-// lane's shared window and beyond it in the chain's global block).
+// moves (the proposed paths of a warp's tree moves in a pool in its shared
+// memory, or, where they do not fit, in kLaneTreeArrays more arrays of the
+// chain's global block).
 inline bool lane_kind(int kind) { return kind == 4 || kind == 5 || kind == 8; }
-// kind 8: arrays of the proposed path (x, y, z and the per-vertex terms of
-// its acceptance ratio) after the lane layout's own, in shared memory and in
-// the chain's global block
+// kind 8: arrays of a proposed path that does not fit the warp's pool (x, y,
+// z and the per-vertex terms of its acceptance ratio), after the lane
+// layout's own in the chain's global block
 constexpr int kLaneTreeArrays = 4;
 int chain_arrays(bool general, bool grad);
 cudaError_t launch_chain(const ChainParams& p, int kind, bool grad, bool spill, int grid, int warps_per_block,

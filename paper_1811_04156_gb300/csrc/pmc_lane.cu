@@ -37,11 +37,6 @@ constexpr unsigned kAll = 0xffffffffu;
 // x, y, z, segment factor, segment length, vertex factor (+ d log sigma / dg
 // per vertex when gradients are accumulated)
 __host__ __device__ constexpr int arrays_of(bool grad) { return grad ? 7 : 6; }
-// tree moves: the proposed path's x, y, z and the per-vertex terms of its
-// acceptance ratio follow the path's own arrays
-__host__ __device__ constexpr int lane_arrays(bool grad, bool tree) {
-  return arrays_of(grad) + (tree ? kLaneTreeArrays : 0);
-}
 __host__ __device__ constexpr int row_of(bool tree) { return tree ? 33 : 32; }
 constexpr int kRefresh = 256;        // recompute the path length from the caches
 constexpr int kFlush = 64;           // FP32 partials -> FP64 accumulators
@@ -131,11 +126,37 @@ struct TreeSlot {
   float vx, vy, vz;      // root frame reference
   int n, cap, pair;
   uint32_t cid;          // global chain index
-  int pad[4];
+  int off;               // first vertex of the proposal in the warp's pool; -1: the chain's global block
+  int pad[3];
 };
 static_assert(sizeof(TreeSlot) == 16 * sizeof(float), "tree slot: 16 words");
 // per warp: 32 slots, then 32 ints for the prefix sums of pooled_for
 constexpr int kSlotWords = 17;
+// per warp: the pool of the proposals of its tree moves, 4 arrays of kPool
+// vertices (x, y, z and the per-vertex terms of the log acceptance ratio),
+// each chain's vertices consecutive; a proposal that does not fit lives in
+// its chain's global block, after the path's arrays
+constexpr int kPool = 320;
+
+struct Proposal {
+  float* p;    // array 0 of the proposal
+  int stride;  // floats between its arrays
+  __device__ __forceinline__ float ld(int a, int i) const { return p[a * stride + i]; }
+  __device__ __forceinline__ void st(int a, int i, float v) const { p[a * stride + i] = v; }
+  __device__ __forceinline__ float3 pos(int i) const { return f3(ld(0, i), ld(1, i), ld(2, i)); }
+  __device__ __forceinline__ void set_pos(int i, float3 q) const {
+    st(0, i, q.x);
+    st(1, i, q.y);
+    st(2, i, q.z);
+  }
+};
+constexpr int PX = 0, PG = 3;  // the proposal's positions and its per-vertex terms
+
+template <bool kGrad>
+__device__ __forceinline__ Proposal proposal_of(const TreeSlot& T, float* pool) {
+  if (T.off >= 0) return Proposal{pool + T.off, kPool};
+  return Proposal{T.gm + static_cast<size_t>(arrays_of(kGrad)) * T.cap, T.cap};
+}
 
 // Every item of every lane (lane i holds `count` of them): fn(src, idx) runs
 // once for item idx of lane src, item f of the warp's concatenated list on
@@ -170,29 +191,25 @@ __device__ __forceinline__ int tree_levels(int n) {
 }
 
 // The proposals of the warp's tree moves (`mine`: this lane's chain drew
-// one; its slot is filled, NX..NZ[0] and [n - 1] hold the source and the new
-// end vertex).  Array NG collects, per vertex of a proposal, the change of
-// log J at the node and the log p terms of the new path.  Returns, on a lane
-// with a move, log p(x') + log J(x') - log J(x) (-inf where x' has zero
-// density).
+// one; its slot is filled and its proposal holds the source and the new end
+// vertex).  The proposal's per-vertex terms collect the change of log J at
+// each node and the log p terms of the new path.  Returns, on a lane with a
+// move, log p(x') + log J(x') - log J(x) (-inf where x' has zero density).
 template <bool kGrad, int kRow>
-__device__ float pooled_tree_gain(const ChainParams& P, TreeSlot* slots, float* cols, int W, bool mine,
+__device__ float pooled_tree_gain(const ChainParams& P, TreeSlot* slots, float* pool, float* cols, int W, bool mine,
                                   uint32_t key0, uint32_t key1) {
-  constexpr int NX = arrays_of(kGrad), NY = NX + 1, NZ = NX + 2, NG = NX + 3;
   const int lane = threadIdx.x & 31;
   const int n_mine = mine ? slots[lane].n : 0;
   // every interior node's stepped coordinates, and -log of its volume element at x
   pooled_for(slots, mine ? n_mine - 2 : 0, [&](int src, int idx) {
     const TreeSlot& T = slots[src];
-    const LanePath<kRow> q{cols + src, T.gm, W, T.cap};
+    const LanePath<kRow> o{cols + src, T.gm, W, T.cap};
+    const Proposal q = proposal_of<kGrad>(T, pool);
     const int m = idx + 1;
     float lj = 0.f;
-    const float3 zc = tree_step_node([&](int i) { return q.pos(i); }, m, T.n, f3(T.vx, T.vy, T.vz), T.step, T.t,
-                                     T.cid, key0, key1, lj);
-    q.st(NX, m, zc.x);
-    q.st(NY, m, zc.y);
-    q.st(NZ, m, zc.z);
-    q.st(NG, m, lj);
+    q.set_pos(m, tree_step_node([&](int i) { return o.pos(i); }, m, T.n, f3(T.vx, T.vy, T.vz), T.step, T.t, T.cid,
+                                key0, key1, lj));
+    q.st(PG, m, lj);
   });
   // the new positions, shallower nodes first (a node's frame uses its foci
   // and its parent's triangle), and +log of each volume element at x'
@@ -203,36 +220,31 @@ __device__ float pooled_tree_gain(const ChainParams& P, TreeSlot* slots, float* 
       const TreeSlot& T = slots[src];
       int k, l, kp, lp;
       if (!tree_interval(T.n, d, j, k, l, kp, lp)) return;
-      const LanePath<kRow> q{cols + src, T.gm, W, T.cap};
-      auto npos = [&](int i) { return f3(q.ld(NX, i), q.ld(NY, i), q.ld(NZ, i)); };
+      const Proposal q = proposal_of<kGrad>(T, pool);
       const int m = (k + l) >> 1;
       float lj = 0.f;
-      const float3 p = tree_place_node(npos, k, l, kp, lp, f3(T.vx, T.vy, T.vz), npos(m), lj);
-      q.st(NX, m, p.x);
-      q.st(NY, m, p.y);
-      q.st(NZ, m, p.z);
-      q.st(NG, m, q.ld(NG, m) + lj);
+      q.set_pos(m, tree_place_node([&](int i) { return q.pos(i); }, k, l, kp, lp, f3(T.vx, T.vy, T.vz), q.pos(m), lj));
+      q.st(PG, m, q.ld(PG, m) + lj);
     });
   }
   // the log p terms of every vertex of the new path
   pooled_for(slots, n_mine, [&](int src, int i) {
     const TreeSlot& T = slots[src];
-    const LanePath<kRow> q{cols + src, T.gm, W, T.cap};
-    auto npos = [&](int v) { return f3(q.ld(NX, v), q.ld(NY, v), q.ld(NZ, v)); };
+    const Proposal q = proposal_of<kGrad>(T, pool);
     const DPair& S = P.pairs[T.pair];
     const int n = T.n;
-    const float3 Pc = npos(i);
-    const float3 Pp = (i >= 1) ? npos(i - 1) : Pc;
-    const float3 Pn = (i <= n - 2) ? npos(i + 1) : Pc;
+    const float3 Pc = q.pos(i);
+    const float3 Pp = (i >= 1) ? q.pos(i - 1) : Pc;
+    const float3 Pn = (i <= n - 2) ? q.pos(i + 1) : Pc;
     float vt, gt, seg, tb, len;
     vertex_and_segment<false>(P.M, S, S.zoff, Pp, Pc, Pn, i, n, vt, gt, seg, tb, len);
     const float term = vt + ((i <= n - 2) ? seg : 0.f);
-    q.st(NG, i, (i == 0 || i == n - 1) ? term : q.ld(NG, i) + term);
+    q.st(PG, i, (i == 0 || i == n - 1) ? term : q.ld(PG, i) + term);
   });
   float gain = 0.f;
   if (mine) {
-    const LanePath<kRow> q{cols + lane, slots[lane].gm, W, slots[lane].cap};
-    for (int i = 0; i < n_mine; ++i) gain += q.ld(NG, i);
+    const Proposal q = proposal_of<kGrad>(slots[lane], pool);
+    for (int i = 0; i < n_mine; ++i) gain += q.ld(PG, i);
   }
   return gain;
 }
@@ -240,26 +252,26 @@ __device__ float pooled_tree_gain(const ChainParams& P, TreeSlot* slots, float* 
 // The accepted proposals (`taken`: this lane's chain accepted its move)
 // become their chains' paths, every cached factor rebuilt.
 template <bool kGrad, int kRow>
-__device__ void pooled_tree_commit(const ChainParams& P, TreeSlot* slots, float* cols, int W, bool taken) {
-  constexpr int NX = arrays_of(kGrad), NY = NX + 1, NZ = NX + 2;
+__device__ void pooled_tree_commit(const ChainParams& P, TreeSlot* slots, float* pool, float* cols, int W,
+                                   bool taken) {
   const int lane = threadIdx.x & 31;
   pooled_for(slots, taken ? slots[lane].n : 0, [&](int src, int i) {
     const TreeSlot& T = slots[src];
-    const LanePath<kRow> q{cols + src, T.gm, W, T.cap};
-    auto npos = [&](int v) { return f3(q.ld(NX, v), q.ld(NY, v), q.ld(NZ, v)); };
+    const LanePath<kRow> o{cols + src, T.gm, W, T.cap};
+    const Proposal q = proposal_of<kGrad>(T, pool);
     const DPair& S = P.pairs[T.pair];
     const int n = T.n;
-    const float3 Pc = npos(i);
-    const float3 Pp = (i >= 1) ? npos(i - 1) : Pc;
-    const float3 Pn = (i <= n - 2) ? npos(i + 1) : Pc;
+    const float3 Pc = q.pos(i);
+    const float3 Pp = (i >= 1) ? q.pos(i - 1) : Pc;
+    const float3 Pn = (i <= n - 2) ? q.pos(i + 1) : Pc;
     float vt, gt, seg, tb, len;
     vertex_and_segment<false>(P.M, S, S.zoff, Pp, Pc, Pn, i, n, vt, gt, seg, tb, len);
-    q.set_pos(i, Pc);
-    q.st(AVT, i, vt);
-    if constexpr (kGrad) q.st(AGT, i, gt);
+    o.set_pos(i, Pc);
+    o.st(AVT, i, vt);
+    if constexpr (kGrad) o.st(AGT, i, gt);
     if (i <= n - 2) {
-      q.st(ASEG, i, seg);
-      q.st(ALEN, i, len);
+      o.st(ASEG, i, seg);
+      o.st(ALEN, i, len);
     }
   });
 }
@@ -287,7 +299,7 @@ __device__ __forceinline__ void lane_refresh_sums(const LanePath<kRow>& w, int n
 // threshold).
 template <bool kGrad, bool kMala, bool kTree>
 __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own, float* col, int W, uint32_t key0,
-                                          uint32_t key1, TreeSlot* slots) {
+                                          uint32_t key1, TreeSlot* slots, float* pool) {
   constexpr int kRow = row_of(kTree);
   const DMedium& M = P.M;
   const DRun& R = P.R;
@@ -302,83 +314,84 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
   const unsigned long long step0 = P.step[c];
   if (n < 2 || n > cap) {
     if (own) {
-        P.status[c] |= ST_BAD_N;
-        atomicOr(P.any_status, ST_BAD_N);
-      }
-      if constexpr (!kTree) return;
-      own = false;
-      n = 2;
+      P.status[c] |= ST_BAD_N;
+      atomicOr(P.any_status, ST_BAD_N);
     }
-    LanePath<kRow> w;
-    w.sm = col;
-    w.gm = P.xyz + P.chain_base[c];
-    w.W = W;
-    w.cap = cap;
-    for (int i = 0; i < min(n, W); ++i) {
-      w.sm[(AX * W + i) * kRow] = w.gm[AX * cap + i];
-      w.sm[(AY * W + i) * kRow] = w.gm[AY * cap + i];
-      w.sm[(AZ * W + i) * kRow] = w.gm[AZ * cap + i];
+    if constexpr (!kTree) return;
+    own = false;
+    n = 2;
+  }
+  LanePath<kRow> w;
+  w.sm = col;
+  w.gm = P.xyz + P.chain_base[c];
+  w.W = W;
+  w.cap = cap;
+  for (int i = 0; i < min(n, W); ++i) {
+    w.sm[(AX * W + i) * kRow] = w.gm[AX * cap + i];
+    w.sm[(AY * W + i) * kRow] = w.gm[AY * cap + i];
+    w.sm[(AZ * W + i) * kRow] = w.gm[AZ * cap + i];
+  }
+  // cached factors of the whole path, with a sliding window of positions
+  float lp0 = 0.f, L = 0.f, G = 0.f;
+  {
+    float3 Pp = w.pos(0), Pc = Pp;
+    for (int i = 0; i < n; ++i) {
+      const float3 Pn = (i <= n - 2) ? w.pos(i + 1) : Pc;
+      float vt, gt, seg, tb, len;
+      vertex_and_segment<false>(M, S, S.zoff, Pp, Pc, Pn, i, n, vt, gt, seg, tb, len);
+      w.st(AVT, i, vt);
+      if constexpr (kGrad) w.st(AGT, i, gt);
+      lp0 += vt;
+      if constexpr (kGrad) G += gt;
+      if (i <= n - 2) {
+        w.st(ASEG, i, seg);
+        w.st(ALEN, i, len);
+        lp0 += seg;
+        L += len;
+      }
+      Pp = Pc;
+      Pc = Pn;
     }
-    // cached factors of the whole path, with a sliding window of positions
-    float lp0 = 0.f, L = 0.f, G = 0.f;
-    {
-      float3 Pp = w.pos(0), Pc = Pp;
-      for (int i = 0; i < n; ++i) {
-        const float3 Pn = (i <= n - 2) ? w.pos(i + 1) : Pc;
-        float vt, gt, seg, tb, len;
-        vertex_and_segment<false>(M, S, S.zoff, Pp, Pc, Pn, i, n, vt, gt, seg, tb, len);
-        w.st(AVT, i, vt);
-        if constexpr (kGrad) w.st(AGT, i, gt);
-        lp0 += vt;
-        if constexpr (kGrad) G += gt;
-        if (i <= n - 2) {
-          w.st(ASEG, i, seg);
-          w.st(ALEN, i, len);
-          lp0 += seg;
-          L += len;
-        }
-        Pp = Pc;
-        Pc = Pn;
+  }
+  if (!isfinite(lp0)) {
+    if (own) {
+      P.status[c] |= ST_NONFINITE;
+      atomicOr(P.any_status, ST_NONFINITE);
+    }
+    if constexpr (!kTree) return;
+    own = false;
+  }
+  LaneAcc A;
+  A.pn2 = A.pn = 0ull;
+  A.t_a = step0;
+  A.pL = A.pL2 = A.pG = 0.f;
+  A.nflush = 0;
+  A.prop_w = A.prop_end = A.prop_b = A.prop_d = 0;
+  A.acc_i = A.acc_e = A.acc_b = A.acc_d = 0;
+  double* acc = P.acc + static_cast<size_t>(c) * ACC_WORDS;
+  const float3 cS = f3(S.c[0], S.c[1], S.c[2]);
+  const float3 cLo = f3(S.c_lo[0], S.c_lo[1], S.c_lo[2]);
+  const uint32_t cid = static_cast<uint32_t>(c) + P.chain_id0;  // global chain index
+  const float3 vref = kTree ? tree_vref(S) : f3(1.f, 0.f, 0.f);  // tree moves: the root frame's reference
+  float* const cols = col - lane;                                 // the warp's columns
+  unsigned long long done = 0;
+  bool aborted = false;
+  for (unsigned long long s = 0; s < P.n_steps; ++s) {
+    if ((s & 1023ull) == 0 && P.abort_flag != nullptr) {
+      // with tree moves the whole warp stops together (its pooled passes need every lane)
+      bool stop;
+      if constexpr (kTree) stop = __any_sync(kAll, *P.abort_flag != 0);
+      else stop = *P.abort_flag != 0;
+      if (stop) {
+        aborted = true;
+        break;
       }
     }
-    if (!isfinite(lp0)) {
-      if (own) {
-        P.status[c] |= ST_NONFINITE;
-        atomicOr(P.any_status, ST_NONFINITE);
-      }
-      if constexpr (!kTree) return;
-      own = false;
-    }
-    LaneAcc A;
-    A.pn2 = A.pn = 0ull;
-    A.t_a = step0;
-    A.pL = A.pL2 = A.pG = 0.f;
-    A.nflush = 0;
-    A.prop_w = A.prop_end = A.prop_b = A.prop_d = 0;
-    A.acc_i = A.acc_e = A.acc_b = A.acc_d = 0;
-    double* acc = P.acc + static_cast<size_t>(c) * ACC_WORDS;
-    const float3 cS = f3(S.c[0], S.c[1], S.c[2]);
-    const float3 cLo = f3(S.c_lo[0], S.c_lo[1], S.c_lo[2]);
-    const uint32_t cid = static_cast<uint32_t>(c) + P.chain_id0;  // global chain index
-    const float3 vref = kTree ? tree_vref(S) : f3(1.f, 0.f, 0.f);  // tree moves: the root frame's reference
-    float* const cols = col - lane;                                 // the warp's columns
-    unsigned long long done = 0;
-    bool aborted = false;
-    for (unsigned long long s = 0; s < P.n_steps; ++s) {
-      if ((s & 1023ull) == 0 && P.abort_flag != nullptr) {
-        // with tree moves the whole warp stops together (its pooled passes need every lane)
-        bool stop;
-        if constexpr (kTree) stop = __any_sync(kAll, *P.abort_flag != 0);
-        else stop = *P.abort_flag != 0;
-        if (stop) {
-          aborted = true;
-          break;
-        }
-      }
-      const unsigned long long t = step0 + s;
-      bool mine = false;  // tree moves: this lane's chain drew one at this step
-      float logu_mine = 0.f;
-      if (own) {
+    const unsigned long long t = step0 + s;
+    bool mine = false;  // tree moves: this lane's chain drew one at this step
+    float logu_mine = 0.f;
+    float3 end_mine = f3(0.f, 0.f, 0.f);  // ... and its new end vertex
+    if (own) {
       const uint4 ra = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), cid,
                                                 PUR_STEP_A), key0, key1);
       const uint4 rb = philox4x32_10(make_uint4(static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), cid,
@@ -404,23 +417,15 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
       if constexpr (kTree) {
         if (within) {
           // whole-path move in tree coordinates, the end vertex with a vMF step
-          // about its sensor normal: published in the warp's slot table with
-          // the source and the new end vertex in place; the warp's pooled
-          // passes below build and weigh the proposal
-          constexpr int NX = arrays_of(kGrad), NY = NX + 1, NZ = NX + 2;
+          // about its sensor normal: published in the warp's slot table; the
+          // warp's pooled passes below build and weigh the proposal
           A.prop_w++;
           const float3 nu = sensor_normal(S, w.pos(n - 1));
           float3 e1, e2;
           onb(nu, e1, e2);
           const float wv = 1.0f + __fdividef(__logf(fmaf(1.0f - ub0, S.exp_m2ke, ub0)), S.kappa_end);
           const float sw = m_sqrt<true>(fmaxf(0.f, 1.0f - wv * wv));
-          const float3 end = cS + (cLo + S.R * (wv * nu + sw * (c1 * e1 + s1 * e2)));
-          w.st(NX, 0, 0.f);
-          w.st(NY, 0, 0.f);
-          w.st(NZ, 0, 0.f);
-          w.st(NX, n - 1, end.x);
-          w.st(NY, n - 1, end.y);
-          w.st(NZ, n - 1, end.z);
+          end_mine = cS + (cLo + S.R * (wv * nu + sw * (c1 * e1 + s1 * e2)));
           TreeSlot& T = slots[lane];
           T.t = t;
           T.gm = w.gm;
@@ -730,8 +735,22 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
     }
     if constexpr (kTree) {
       if (__any_sync(kAll, mine)) {
-        __syncwarp();  // the slots and the end vertices, visible to the warp
-        const float gain = pooled_tree_gain<kGrad, kRow>(P, slots, cols, W, mine, key0, key1);
+        // the proposals' places in the warp's pool, in lane order (a chain
+        // that no longer fits uses its global block); source and end vertex
+        int upto = mine ? n : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(kAll, upto, o);
+          if (lane >= o) upto += v;
+        }
+        if (mine) {
+          slots[lane].off = (upto <= kPool) ? upto - n : -1;
+          const Proposal q = proposal_of<kGrad>(slots[lane], pool);
+          q.set_pos(0, f3(0.f, 0.f, 0.f));
+          q.set_pos(n - 1, end_mine);
+        }
+        __syncwarp();  // the slots and the proposals' ends, visible to the warp
+        const float gain = pooled_tree_gain<kGrad, kRow>(P, slots, pool, cols, W, mine, key0, key1);
         bool taken = false;
         if (mine) {
           float lpo = 0.f;
@@ -743,7 +762,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
           }
         }
         if (__any_sync(kAll, taken)) {
-          pooled_tree_commit<kGrad, kRow>(P, slots, cols, W, taken);
+          pooled_tree_commit<kGrad, kRow>(P, slots, pool, cols, W, taken);
           if (taken) {
             lane_refresh_sums<kGrad>(w, n, L, G);
             if (A.nflush >= kFlush) lane_flush<kGrad>(A, acc);
@@ -785,7 +804,8 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
 
 // Persistent warps; each work item is 32 consecutive chains of the
 // processing order, one per lane.  Shared memory per CTA: with tree moves
-// the warps' slot tables first, then each warp's block of vertex rows.
+// the warps' slot tables and proposal pools first, then each warp's block
+// of vertex rows.
 template <bool kGrad, bool kMala, bool kTree>
 __global__ void __launch_bounds__(128, 4) lane_chain_kernel(const ChainParams P) {
   extern __shared__ float4 lane_smem4[];
@@ -796,8 +816,9 @@ __global__ void __launch_bounds__(128, 4) lane_chain_kernel(const ChainParams P)
   const int W = P.smem_cap;
   const int n_warps = blockDim.x >> 5;
   TreeSlot* slots = kTree ? reinterpret_cast<TreeSlot*>(lane_smem + wib * 32 * kSlotWords) : nullptr;
-  float* col = lane_smem + (kTree ? n_warps * 32 * kSlotWords : 0) +
-               static_cast<size_t>(wib) * lane_arrays(kGrad, kTree) * W * kRow + lane;
+  float* pool = kTree ? lane_smem + n_warps * 32 * kSlotWords + wib * 4 * kPool : nullptr;
+  float* col = lane_smem + (kTree ? n_warps * (32 * kSlotWords + 4 * kPool) : 0) +
+               static_cast<size_t>(wib) * arrays_of(kGrad) * W * kRow + lane;
   const uint32_t key0 = static_cast<uint32_t>(P.R.seed), key1 = static_cast<uint32_t>(P.R.seed >> 32);
   for (;;) {
     int item = 0;
@@ -808,9 +829,9 @@ __global__ void __launch_bounds__(128, 4) lane_chain_kernel(const ChainParams P)
     const bool own = g + lane < P.chain_hi;
     if constexpr (kTree) {
       // every lane runs (a lane past the last chain follows the item's first one, read only)
-      run_chain<kGrad, kMala, kTree>(P, P.order[own ? g + lane : g], own, col, W, key0, key1, slots);
+      run_chain<kGrad, kMala, kTree>(P, P.order[own ? g + lane : g], own, col, W, key0, key1, slots, pool);
     } else if (own) {
-      run_chain<kGrad, kMala, kTree>(P, P.order[g + lane], true, col, W, key0, key1, nullptr);
+      run_chain<kGrad, kMala, kTree>(P, P.order[g + lane], true, col, W, key0, key1, nullptr, nullptr);
     }
   }
 }
@@ -855,8 +876,8 @@ cudaError_t launch_of(const ChainParams& p, int grid, int warps_per_block, cudaS
 }  // namespace
 
 size_t lane_smem_bytes(int window, int warps_per_block, bool grad, bool tree) {
-  const size_t per_warp = static_cast<size_t>(lane_arrays(grad, tree)) * window * row_of(tree) +
-                          (tree ? 32u * kSlotWords : 0u);
+  const size_t per_warp = static_cast<size_t>(arrays_of(grad)) * window * row_of(tree) +
+                          (tree ? 32u * kSlotWords + 4u * kPool : 0u);
   return static_cast<size_t>(warps_per_block) * per_warp * sizeof(float);
 }
 

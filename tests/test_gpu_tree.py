@@ -39,17 +39,19 @@ def _tree_scene(name, n_chains=64):
     sc.run.within = S.WITHIN_TREE
     sc.run.sigma = 0.5
     sc.run.init = S.INIT_STRAIGHT
-    sc.run.init_k = 6
-    sc.run.init_jitter = 0.02
+    sc.run.init_k = 40 if name.endswith("_long") else 6
+    sc.run.init_jitter = 0.002 if name.endswith("_long") else 0.02  # 40 vertices keep clear of the sensor
     sc.run.layout = S.LAYOUT_LANE if name.startswith("plain_lane") else S.LAYOUT_WARP
     return sc
 
 
 # kernel kind, shared window and chain count per case: 7 the lean warp-per-chain tree
-# kernel, 8 the lane-per-chain one (window 16; or 4, so that most of every path and of
-# every proposal lives in the global block, with 50 chains, so that the second work item
-# has lanes without a chain), 2 the general warp-per-chain one
-TREE_CASES = {"plain": (7, 0, 64), "plain_lane": (8, 16, 64), "plain_lane_spill": (8, 4, 50), "general": (2, 0, 64)}
+# kernel, 8 the lane-per-chain one (window 16; or 4, so that most of every path lives in
+# the global block, with 50 chains, so that the second work item has lanes without a
+# chain; or paths of 42 vertices, more than the warp's proposal pool holds, so that most
+# proposals live in the chains' global blocks), 2 the general warp-per-chain one
+TREE_CASES = {"plain": (7, 0, 64), "plain_lane": (8, 16, 64), "plain_lane_spill": (8, 4, 50),
+              "plain_lane_long": (8, 16, 64), "general": (2, 0, 64)}
 
 
 @pytest.mark.parametrize("name", list(TREE_CASES))
