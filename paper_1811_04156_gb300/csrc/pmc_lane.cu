@@ -136,7 +136,7 @@ constexpr int kSlotWords = 17;
 // vertices (x, y, z and the per-vertex terms of the log acceptance ratio),
 // each chain's vertices consecutive; a proposal that does not fit lives in
 // its chain's global block, after the path's arrays
-constexpr int kPool = 320;
+constexpr int kPool = 384;
 
 struct Proposal {
   float* p;    // array 0 of the proposal
