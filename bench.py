@@ -63,9 +63,9 @@ WORKLOAD_TEXT = {
 # csrc/pmc_internal.h, in that order): warp instructions per proposal (window
 # 20) and DRAM bytes (read + write) of a 65,536-chain launch.  With another
 # source the bench reports them as null.
-LANE_CAPTURE = {"source_sha256": "353f84dd52e727eba35991205ca5d5f077a8c15a6521237b725d9caeb9ed756f",
-                "inst_per_proposal": 57.05, "dram_bytes_per_launch": 80068864.0,
-                "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum (57.4 MB + 22.7 MB) of one "
+LANE_CAPTURE = {"source_sha256": "25d7bdea72544e198e4b957028b2ef0d5fe9d0fa26037daaa97b462be2486c64",
+                "inst_per_proposal": 57.05, "dram_bytes_per_launch": 81466368.0,
+                "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum (57.6 MB + 23.9 MB) of one "
                            "65,536-chain x 100,000-step launch, window 20, 1 warp per CTA"}
 
 

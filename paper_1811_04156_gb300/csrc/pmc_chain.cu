@@ -210,8 +210,40 @@ __device__ Sums path_sums(const WP& w, int n, int lane) {
   return s;
 }
 
+// The general density's vertex and segment factors.  kCall: as one
+// out-of-line function, so that the kernel holds a single copy of them.  The
+// general tree-move kernel takes it: its warps sit in different phases of a
+// long step (tree levels, births, deaths) and instruction fetch limits it
+// (8 % faster on the paper's two-sensor scene); the general Cartesian kernel,
+// whose step is short, runs a third slower with the call and keeps them
+// inline.
+struct VsOut {
+  float vt, gt, seg, tb, len;
+};
+__device__ __noinline__ VsOut vs_general(const DMedium& M, const DPair& S, float zoff, float3 Pp, float3 Pc, float3 Pn,
+                                        int v, int n) {
+  VsOut o;
+  vertex_and_segment<true>(M, S, zoff, Pp, Pc, Pn, v, n, o.vt, o.gt, o.seg, o.tb, o.len);
+  return o;
+}
+template <bool kGen, bool kCall>
+__device__ __forceinline__ void vs_factors(const DMedium& M, const DPair& S, float zoff, float3 Pp, float3 Pc,
+                                           float3 Pn, int v, int n, float& vt, float& gt, float& seg, float& tb,
+                                           float& len) {
+  if constexpr (kGen && kCall) {
+    const VsOut o = vs_general(M, S, zoff, Pp, Pc, Pn, v, n);
+    vt = o.vt;
+    gt = o.gt;
+    seg = o.seg;
+    tb = o.tb;
+    len = o.len;
+  } else {
+    vertex_and_segment<kGen>(M, S, zoff, Pp, Pc, Pn, v, n, vt, gt, seg, tb, len);
+  }
+}
+
 // Recompute every cached factor of the path from its vertices; returns log p.
-template <bool kGen, class WP>
+template <bool kGen, bool kCall, class WP>
 __device__ float refresh_caches(const DMedium& M, const DPair& S, float zoff, const WP& w, int n, int lane) {
   float lp = 0.f;
   for (int i = lane; i < n; i += 32) {
@@ -219,7 +251,7 @@ __device__ float refresh_caches(const DMedium& M, const DPair& S, float zoff, co
     const float3 Pp = (i >= 1) ? w.pos(i - 1) : P;
     const float3 Pn = (i <= n - 2) ? w.pos(i + 1) : P;
     float vt, gt, seg, tb, len;
-    vertex_and_segment<kGen>(M, S, zoff, Pp, P, Pn, i, n, vt, gt, seg, tb, len);
+    vs_factors<kGen, kCall>(M, S, zoff, Pp, P, Pn, i, n, vt, gt, seg, tb, len);
     w.set_vt(i, vt);
     w.set_gt(i, gt);
     lp += vt;
@@ -364,7 +396,7 @@ __device__ float tree_propose(const DMedium& M, const DPair& S, float zoff, cons
     const float3 Pp = (i >= 1) ? npos(i - 1) : Pc;
     const float3 Pn = (i <= n - 2) ? npos(i + 1) : Pc;
     float vt, gt, seg, tb, len;
-    vertex_and_segment<kGen>(M, S, zoff, Pp, Pc, Pn, i, n, vt, gt, seg, tb, len);
+    vs_factors<kGen, true>(M, S, zoff, Pp, Pc, Pn, i, n, vt, gt, seg, tb, len);
     lp += vt + ((i <= n - 2) ? seg : 0.f);
   }
   return warp_sum(lp) + warp_sum(lj);
@@ -581,7 +613,7 @@ __global__ void __launch_bounds__(128, (kGen || kX != 0) ? 5 : 6) chain_kernel(c
       w.sm[WP::kZ * cap_s + i] = gz[i];
     }
     __syncwarp();
-    const float lp0 = refresh_caches<kGen>(M, S, zoff, w, n, lane);
+    const float lp0 = refresh_caches<kGen, kGen && kTree>(M, S, zoff, w, n, lane);
     if (!isfinite(lp0)) {
       if (lane == 0) { P.status[c] |= ST_NONFINITE; atomicOr(P.any_status, ST_NONFINITE); }
       continue;
@@ -677,7 +709,7 @@ __global__ void __launch_bounds__(128, (kGen || kX != 0) ? 5 : 6) chain_kernel(c
               close_state(A, t, R.burn_in, n, L, G);
               for (int q = lane; q < n; q += 32) w.set_pos(q, f3(tnx[q], tny[q], tnz[q]));
               __syncwarp();
-              refresh_caches<kGen>(M, S, zoff, w, n, lane);
+              refresh_caches<kGen, kGen && kTree>(M, S, zoff, w, n, lane);
               const Sums s3 = path_sums(w, n, lane);
               L = s3.L;
               G = s3.G;
@@ -709,7 +741,7 @@ __global__ void __launch_bounds__(128, (kGen || kX != 0) ? 5 : 6) chain_kernel(c
               close_state(A, t, R.burn_in, n, L, G);
               for (int q = lane; q < n; q += 32) w.set_pos(q, f3(tnx[q], tny[q], tnz[q]));
               __syncwarp();
-              refresh_caches<kGen>(M, S, zoff, w, n, lane);
+              refresh_caches<kGen, kGen && kTree>(M, S, zoff, w, n, lane);
               const Sums s3 = path_sums(w, n, lane);
               L = s3.L;
               G = s3.G;
@@ -744,7 +776,7 @@ __global__ void __launch_bounds__(128, (kGen || kX != 0) ? 5 : 6) chain_kernel(c
               __syncwarp();
               if (lane == 0) medium_at(P.M, lam, *smed);
               __syncwarp();
-              refresh_caches<kGen>(M, S, zoff, w, n, lane);
+              refresh_caches<kGen, kGen && kTree>(M, S, zoff, w, n, lane);
               if (A.nflush >= kFlushAccepts) flush64(A, lane);
             }
             __syncwarp();
@@ -849,7 +881,7 @@ __global__ void __launch_bounds__(128, (kGen || kX != 0) ? 5 : 6) chain_kernel(c
             const float3 Pp = newpos(v - 1);
             const float3 Pn = newpos(v + 1);
             float seg_, tb_, len_;
-            vertex_and_segment<kGen>(M, S, zoff, Pp, Pc, Pn, v, n_new, nvt, ngt, seg_, tb_, len_);
+            vs_factors<kGen, kGen && kTree>(M, S, zoff, Pp, Pc, Pn, v, n_new, nvt, ngt, seg_, tb_, len_);
             if (lane < nc - 1) {
               nseg = seg_;
               ntb = tb_;

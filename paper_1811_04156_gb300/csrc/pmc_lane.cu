@@ -150,7 +150,7 @@ struct Proposal {
     st(2, i, q.z);
   }
 };
-constexpr int PX = 0, PG = 3;  // the proposal's positions and its per-vertex terms
+constexpr int PG = 3;  // the proposal's per-vertex terms (arrays 0 - 2: its positions)
 
 template <bool kGrad>
 __device__ __forceinline__ Proposal proposal_of(const TreeSlot& T, float* pool) {
@@ -408,7 +408,7 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
       // homogeneous medium: the running length L, updated at every accepted
       // move and summed afresh from the cached lengths every kRefresh steps
       // (it differs from a fresh FP32 sum by rounding only)
-      const bool within = um < R.thr_within, birth = !within && um < R.thr_birth, death = !within && !birth;
+      const bool within = um < R.thr_within, birth = !within && um < R.thr_birth;
       float s1, c1, sB, cB;
       sincospif(2.0f * ub1, &s1, &c1);
       sincospif(2.0f * (within ? ub3 : ub2), &sB, &cB);
