@@ -276,18 +276,23 @@ def test_abort_request_stops_and_context_survives(api, ctx):
     assert ch2.read_estimator()[0]["n_samples"] > 0
 
 
-@pytest.mark.parametrize("layout", [S.LAYOUT_WARP, S.LAYOUT_LANE])
-def test_abort_mid_run_stops_at_a_poll(api, ctx, layout):
+@pytest.mark.parametrize("layout,within", [(S.LAYOUT_WARP, S.WITHIN_PERTURB), (S.LAYOUT_LANE, S.WITHIN_PERTURB),
+                                           (S.LAYOUT_LANE, S.WITHIN_TREE)])
+def test_abort_mid_run_stops_at_a_poll(api, ctx, layout, within):
     """pmc_request_abort from the host while a long pmc_run_steps executes:
     the kernels poll the flag every 1,024 steps, so the run ends long before
     its steps are done; the next synchronising call reports PMC_ERR_ABORTED,
     every chain stopped at a poll boundary with consistent bookkeeping, and
-    the context then runs a new chain set."""
+    the context then runs a new chain set.  With tree moves on the lane
+    layout the warp stops as a whole (its pooled passes need every lane)."""
     import time
     import torch
     from paper_1811_04156_gb300._lib import PathmcError
     sc = S.plain(n_chains=65536, n_steps=0)
     sc.run.layout = layout
+    sc.run.within = within
+    if within == S.WITHIN_TREE:
+        sc.run.sigma = 0.5
     medium = api.Medium(ctx, sc.medium)
     geom = api.Geometry(ctx, sc.sources, sc.sensors, sc.pairs)
     ch = api.Chains(ctx, medium, geom, sc.run)
