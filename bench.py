@@ -32,8 +32,7 @@ METRIC = "RJMCMC proposals/s"
 UNIT = "proposals/s"
 
 # Algorithmic work of one proposal, per move type, counted from the method's
-# formulas (the blueprint's per-move figures): FP32 operations of the
-# proposal and of the changed factors
+# formulas: FP32 operations of the proposal and of the changed factors
 # (O(n) scans for births and deaths, n the vertex count), the integer work of
 # the two Philox4x32-10 blocks every step draws (2 blocks x 10 rounds x 6
 # multiply / xor operations), and special-function (MUFU) operations.  The
