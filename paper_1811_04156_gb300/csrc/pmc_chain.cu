@@ -540,8 +540,13 @@ __device__ __forceinline__ void flush64(Accum& a, int lane) {
 //   within: lo.z, lo.w, hi.x = standard normals, hi.y = vMF cosine,
 //           hi.z, hi.w = cos, sin of the vMF azimuth
 //   birth:  lo.z = u for cos s, lo.w = sinh t, hi.x = cosh t, hi.y, hi.z = cos, sin of phi
+// Launch bounds: the general tree-move kernel takes up to 128 registers (4
+// CTAs of 128 threads per SM), which holds its out-of-line density call
+// without spills (+2 % on the two-sensor scene); the general Cartesian
+// kernel runs faster at 96 (-1 % at 128 on the layered workload).
 template <bool kGen, bool kGrad, bool kSpill, int kX>
-__global__ void __launch_bounds__(128, (kGen || kX != 0) ? 5 : 6) chain_kernel(const ChainParams P) {
+__global__ void __launch_bounds__(128, (kGen && kX == 1) ? 4 : ((kGen || kX != 0) ? 5 : 6))
+    chain_kernel(const ChainParams P) {
   using WP = WarpPath<kGen, kGrad, kSpill>;
   constexpr bool kTree = kX == 1, kHmc = kX == 2, kLam = kX == 3;
   static_assert(kX == 0 || !kSpill, "tree, HMC and wavelength moves keep the whole cap in shared memory");
