@@ -9,6 +9,7 @@ a source or header is newer than the library.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import os
 import shutil
@@ -62,9 +63,22 @@ def _build_probe(nvcc: str) -> None:
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    """Build the library (and the probe library) if a source is newer.  Processes
+    that build at once (ranks of a multi-process test) take turns on a lock
+    file in the build folder, so that none links another's half-written
+    objects; whoever comes second finds the library up to date."""
+    os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose, ptxas_info)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool, ptxas_info: bool) -> str:
     if force and os.path.exists(PROBE_LIB):
         os.unlink(PROBE_LIB)
-    os.makedirs(BUILD, exist_ok=True)
     _build_probe(_nvcc())
     if not force and up_to_date():
         return LIB

@@ -442,121 +442,115 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
         }
       }
       if (!mine) {
-        int move;
-        bool proposed = true;
-        int n_new = n, wlo = 0, nc = 0, olo = 0, onc = 0, jj = -1, kk = -1;
-        int inew = -1, sh_from = INT_MAX, sh_by = 0;
-        float3 fnew = f3(0.f, 0.f, 0.f);
-        float3 gx = f3(0.f, 0.f, 0.f);  // MALA: d log p / d f_j at the current path
-        float extra = 0.f;
-        float3 IA, IB, IF;  // births and deaths: the insertion density's segment ends and vertex
-        if (!kTree && within) {
-          A.prop_w++;
-          const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 1)) >> 23);
-          jj = j;
-          inew = j;
-          if (j == n - 1) {
-            // vMF step of the end vertex about its sensor normal
-            move = MV_END;
-            A.prop_end++;
-            const float3 nu = sensor_normal(S, w.pos(j));
-            float3 e1, e2;
-            onb(nu, e1, e2);
-            const float wv = 1.0f + __fdividef(__logf(fmaf(1.0f - ub0, S.exp_m2ke, ub0)), S.kappa_end);
-            const float sw = m_sqrt<true>(fmaxf(0.f, 1.0f - wv * wv));
-            const float3 nn = wv * nu + sw * (c1 * e1 + s1 * e2);
-            fnew = cS + (cLo + S.R * nn);
-            wlo = n - 2; nc = 2; olo = n - 2; onc = 2;
-          } else {
-            // Gaussian step of an interior vertex (Box-Muller)
-            move = MV_INTERIOR;
-            const float r1 = m_sqrt<true>(-2.0f * __logf(ub0));
-            const float r2 = m_sqrt<true>(-2.0f * __logf(ub2));
-            const float3 z = f3(r1 * c1, r1 * s1, r2 * cB);
-            const float3 fj = w.pos(j);
-            if constexpr (kMala) {
-              // Langevin step: drift along the local gradient of log p
-              gx = grad_vertex(M, S, S.zoff, [&](int k) { return w.pos(k); }, n, j);
-              const float h = 0.5f * R.mala_eps * R.mala_eps;
-              fnew = fj + h * gx + R.mala_eps * z;
-            } else {
-              fnew = fj + R.sigma * z;
-            }
-            wlo = j - 1; nc = 3; olo = j - 1; onc = 3;
-          }
-        } else if (birth) {
-          move = MV_BIRTH;
-          A.prop_b++;
-          if (n >= cap) {
-            proposed = false;
-          } else {
-            // segment k with probability tau_b(k) / T_b (smallest k whose
-            // cumulative sum exceeds u T_b), then the bispherical insertion
-            const float ui = __fmaf_rn(static_cast<float>(v23), 1.1920928955078125e-7f, 5.9604644775390625e-8f);
-            const float total = Tb;
-            const float target = ui * total;
-            int k = -1;
-            float cum = 0.f;
-            const float* pl = w.sm + ALEN * W * kRow;
+        // The proposal of every kind, formed by every lane as straight-line
+        // code; the lane keeps the one its chain drew.  The 32 chains of a
+        // warp draw all kinds at almost every step, so the warp issues every
+        // kind's code anyway; without branches between them the kinds'
+        // independent arithmetic interleaves.  A kind's arithmetic is the same
+        // whichever lane forms it, and only the O(n) choice of a birth's
+        // segment runs on the lanes that need it.
+        const bool death = !within && !birth;
+        // within-dimension moves: vertex jw of 1 .. n-1 (n-1: the end vertex)
+        const int jw = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 1)) >> 23);
+        const bool end = !kTree && within && jw == n - 1;
+        // births: segment k with probability tau_b(k) / T_b (smallest k whose
+        // cumulative sum exceeds u T_b); a birth at the cap is proposed and
+        // rejected
+        const bool born = birth && n < cap;
+        const float total = Tb;
+        const float target =
+            __fmaf_rn(static_cast<float>(v23), 1.1920928955078125e-7f, 5.9604644775390625e-8f) * total;
+        int k = -1;
+        if (born) {
+          float cum = 0.f;
+          const float* pl = w.sm + ALEN * W * kRow;
 #pragma unroll 4
-            for (int q = 0; q < min(n - 1, W); ++q) {
-              cum += M.b * pl[q * kRow];
-              if (cum > target) {
-                k = q;
-                break;
-              }
+          for (int q = 0; q < min(n - 1, W); ++q) {
+            cum += M.b * pl[q * kRow];
+            if (cum > target) {
+              k = q;
+              break;
             }
-            for (int q = W; k < 0 && q < n - 1; ++q) {
-              cum += M.b * w.gm[ALEN * cap + q];
-              if (cum > target) k = q;
-            }
-            if (k < 0) k = n - 2;
-            kk = k;
-            const float3 Af = w.pos(k), Bf = w.pos(k + 1);
-            const float3 r = Bf - Af;
-            const float rr = dot(r, r);
-            const float irl = rsqrtf(rr);
-            const float gamma = 0.5f * rr * irl;
-            const float3 rh = irl * r;
-            float3 xi, ze;
-            onb(rh, xi, ze);
-            const float beta = insertion_beta(M, R, S.zoff, Af, Bf, gamma);
-            float cs = -1.0f - __fdividef(__logf(fmaf(-ub0, 1.0f - __expf(-2.0f * beta), 1.0f)), beta);
-            cs = fminf(fmaxf(cs, -1.0f), 1.0f);
-            const float sn = m_sqrt<true>(fmaxf(0.f, (1.0f - cs) * (1.0f + cs)));
-            const float et = __fdividef(ub1, 1.0f - ub1);
-            const float iet = __fdividef(1.0f - ub1, ub1);
-            const float sht = 0.5f * (et - iet), cht = 0.5f * (et + iet);
-            const float sc = __fdividef(gamma, cht - cs);
-            fnew = 0.5f * (Af + Bf) + sc * (sht * rh + sn * (cB * xi + sB * ze));
-            const float tbk = M.b * w.ld(ALEN, k);
-            extra = R.log_pd - __logf(static_cast<float>(n - 1)) - R.log_pb - __logf(__fdividef(tbk, total));
-            IA = Af;
-            IB = Bf;
-            IF = fnew;
-            n_new = n + 1;
-            inew = k + 1;
-            sh_from = k + 2;
-            sh_by = -1;
-            wlo = k; nc = 3; olo = k; onc = 2;
           }
-        } else {
-          move = MV_DEATH;
-          A.prop_d++;
-          if (n <= 2) {
-            proposed = false;
-          } else {
-            const int j = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 2)) >> 23);
-            jj = j;
-            n_new = n - 1;
-            sh_from = j;
-            sh_by = 1;
-            wlo = j - 1; nc = 2; olo = j - 1; onc = 3;
-            IA = w.pos(j - 1);
-            IB = w.pos(j + 1);
-            IF = w.pos(j);
+          for (int q = W; k < 0 && q < n - 1; ++q) {
+            cum += M.b * w.gm[ALEN * cap + q];
+            if (cum > target) k = q;
           }
         }
+        if (k < 0) k = n - 2;
+        // deaths: interior vertex jd of 1 .. n-2 (a death at n = 2 is proposed and rejected)
+        const int jd = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 2)) >> 23);
+        // the moved vertex of a within-dimension move or the removed one of a
+        // death; the segment ends of a birth or about a death
+        const float3 V = w.pos(within ? jw : min(jd, n - 1));
+        const float3 IA = w.pos(born ? k : jd - 1);
+        const float3 IB = w.pos(born ? k + 1 : min(jd + 1, n - 1));
+        float3 fin = f3(0.f, 0.f, 0.f), fend = f3(0.f, 0.f, 0.f);
+        float3 gx = f3(0.f, 0.f, 0.f);  // MALA: d log p / d f_j at the current path
+        if constexpr (!kTree) {
+          // vMF step of the end vertex about its sensor normal
+          const float3 nu = sensor_normal(S, V);
+          float3 e1, e2;
+          onb(nu, e1, e2);
+          const float wv = 1.0f + __fdividef(__logf(fmaf(1.0f - ub0, S.exp_m2ke, ub0)), S.kappa_end);
+          const float sw = m_sqrt<true>(fmaxf(0.f, 1.0f - wv * wv));
+          const float3 nn = wv * nu + sw * (c1 * e1 + s1 * e2);
+          fend = cS + (cLo + S.R * nn);
+          // Gaussian step of an interior vertex (Box-Muller)
+          const float r1 = m_sqrt<true>(-2.0f * __logf(ub0));
+          const float r2 = m_sqrt<true>(-2.0f * __logf(ub2));
+          const float3 z = f3(r1 * c1, r1 * s1, r2 * cB);
+          if constexpr (kMala) {
+            // Langevin step: drift along the local gradient of log p
+            if (within && !end) gx = grad_vertex(M, S, S.zoff, [&](int q) { return w.pos(q); }, n, jw);
+            const float h = 0.5f * R.mala_eps * R.mala_eps;
+            fin = V + h * gx + R.mala_eps * z;
+          } else {
+            fin = V + R.sigma * z;
+          }
+        }
+        // bispherical insertion about segment k
+        float3 fbirth;
+        float extra_b;
+        {
+          const float3 r = IB - IA;
+          const float rr = dot(r, r);
+          const float irl = rsqrtf(rr);
+          const float gamma = 0.5f * rr * irl;
+          const float3 rh = irl * r;
+          float3 xi, ze;
+          onb(rh, xi, ze);
+          const float beta = insertion_beta(M, R, S.zoff, IA, IB, gamma);
+          float cs = -1.0f - __fdividef(__logf(fmaf(-ub0, 1.0f - __expf(-2.0f * beta), 1.0f)), beta);
+          cs = fminf(fmaxf(cs, -1.0f), 1.0f);
+          const float sn = m_sqrt<true>(fmaxf(0.f, (1.0f - cs) * (1.0f + cs)));
+          const float et = __fdividef(ub1, 1.0f - ub1);
+          const float iet = __fdividef(1.0f - ub1, ub1);
+          const float sht = 0.5f * (et - iet), cht = 0.5f * (et + iet);
+          const float sc = __fdividef(gamma, cht - cs);
+          fbirth = 0.5f * (IA + IB) + sc * (sht * rh + sn * (cB * xi + sB * ze));
+          const float tbk = M.b * w.ld(ALEN, k);
+          extra_b = R.log_pd - __logf(static_cast<float>(n - 1)) - R.log_pb - __logf(__fdividef(tbk, total));
+        }
+        // the drawn kind's proposal
+        const int move = within ? (end ? MV_END : MV_INTERIOR) : (birth ? MV_BIRTH : MV_DEATH);
+        A.prop_w += within;
+        A.prop_end += end;
+        A.prop_b += birth;
+        A.prop_d += death;
+        const bool proposed = within || born || (death && n > 2);
+        const int jj = within ? jw : jd, kk = k;
+        const int n_new = birth ? n + 1 : (death ? n - 1 : n);
+        const int inew = within ? jw : (birth ? k + 1 : -1);
+        const int sh_from = birth ? k + 2 : (death ? jd : INT_MAX);
+        const int sh_by = birth ? -1 : (death ? 1 : 0);
+        const int wlo = end ? n - 2 : (within ? jw - 1 : (birth ? k : jd - 1));
+        const int olo = wlo;
+        const int nc = (end || death) ? 2 : 3;
+        const int onc = (end || birth) ? 2 : 3;
+        const float3 fnew = within ? (end ? fend : fin) : (birth ? fbirth : f3(0.f, 0.f, 0.f));
+        const float3 IF = birth ? fbirth : V;
+        float extra = birth ? extra_b : 0.f;
 
         bool accept = false;
         float nvt[3] = {0.f, 0.f, 0.f}, nseg[2] = {0.f, 0.f}, nlen[2] = {0.f, 0.f}, ngt[3] = {0.f, 0.f, 0.f};
