@@ -460,24 +460,25 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
         const float total = Tb;
         const float target =
             __fmaf_rn(static_cast<float>(v23), 1.1920928955078125e-7f, 5.9604644775390625e-8f) * total;
-        int k = -1;
+        // (the cumulative sums rise with q: k counts those at or below u T_b,
+        // at most n - 2; no early exit, so the loads and sums pipeline)
+        int k = n - 2;
         if (born) {
           float cum = 0.f;
+          int below = 0;
           const float* pl = w.sm + ALEN * W * kRow;
+          const int m = min(n - 1, W);
 #pragma unroll 4
-          for (int q = 0; q < min(n - 1, W); ++q) {
+          for (int q = 0; q < m; ++q) {
             cum += M.b * pl[q * kRow];
-            if (cum > target) {
-              k = q;
-              break;
-            }
+            below += (cum <= target) ? 1 : 0;
           }
-          for (int q = W; k < 0 && q < n - 1; ++q) {
+          for (int q = W; q < n - 1; ++q) {
             cum += M.b * w.gm[ALEN * cap + q];
-            if (cum > target) k = q;
+            below += (cum <= target) ? 1 : 0;
           }
+          k = min(below, n - 2);
         }
-        if (k < 0) k = n - 2;
         // deaths: interior vertex jd of 1 .. n-2 (a death at n = 2 is proposed and rejected)
         const int jd = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 2)) >> 23);
         // the moved vertex of a within-dimension move or the removed one of a
@@ -551,6 +552,8 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
         const float3 fnew = within ? (end ? fend : fin) : (birth ? fbirth : f3(0.f, 0.f, 0.f));
         const float3 IF = birth ? fbirth : V;
         float extra = birth ? extra_b : 0.f;
+        // the insertion density at a birth's or a death's segment ends and vertex
+        const float lid = log_insert_density<true>(M, R, S.zoff, IA, IB, IF);
 
         bool accept = false;
         float nvt[3] = {0.f, 0.f, 0.f}, nseg[2] = {0.f, 0.f}, nlen[2] = {0.f, 0.f}, ngt[3] = {0.f, 0.f, 0.f};
@@ -607,18 +610,15 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
           const float dlp = (d[0] + d[1]) + d[2];
           dlen = (f[0] + f[1]) + f[2];
           if constexpr (kGrad) dG = (gd[0] + gd[1]) + gd[2];
-          if (move == MV_DEATH) {
-            // T_b of the reduced path from the current one
-            const float dtb = (e[0] + e[1]) + e[2];
-            const float Tb_red = Tb + dtb;
-            const float tb_new = M.b * nlen[0];
-            extra = -R.log_pd + __logf(static_cast<float>(n - 2)) + R.log_pb + __logf(__fdividef(tb_new, Tb_red));
-          }
-          if (move >= MV_BIRTH) {
-            // one insertion density for both kinds: a birth divides by it, a death multiplies
-            const float lid = log_insert_density<true>(M, R, S.zoff, IA, IB, IF);
-            extra = (move == MV_BIRTH) ? extra - lid : extra + lid;
-          }
+          // a death's T_b of the reduced path, from the current one; one
+          // insertion density for births and deaths: a birth divides by it, a
+          // death multiplies
+          const float dtb = (e[0] + e[1]) + e[2];
+          const float Tb_red = Tb + dtb;
+          const float tb_new = M.b * nlen[0];
+          const float extra_d =
+              -R.log_pd + __logf(static_cast<float>(n - 2)) + R.log_pb + __logf(__fdividef(tb_new, Tb_red));
+          extra = birth ? extra - lid : (death ? extra_d + lid : extra);
           if (kMala && move == MV_INTERIOR && isfinite(dlp)) {
             // MALA Hastings ratio q(x | y) / q(y | x), with the gradient at the proposal
             const float3 gy = grad_vertex(M, S, S.zoff, [&](int k) { return k == jj ? fnew : w.pos(k); }, n, jj);
