@@ -24,8 +24,6 @@
 // spill mode.  Tree moves add three arrays for the proposed path.  Positions are read from and written back to the global block
 // at the start and end of a residency; the cached factors are rebuilt at the
 // start.
-#include <climits>
-
 #include "pmc_internal.h"
 #include "pmc_tree.cuh"
 
@@ -481,11 +479,16 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
         }
         // deaths: interior vertex jd of 1 .. n-2 (a death at n = 2 is proposed and rejected)
         const int jd = 1 + static_cast<int>((static_cast<unsigned long long>(v23) * (n - 2)) >> 23);
+        // wlo: the first vertex whose factor changes.  The current path about
+        // it, entries wlo - 1 .. wlo + 3 clamped to the path, read once: V is
         // the moved vertex of a within-dimension move or the removed one of a
-        // death; the segment ends of a birth or about a death
-        const float3 V = w.pos(within ? jw : min(jd, n - 1));
-        const float3 IA = w.pos(born ? k : jd - 1);
-        const float3 IB = w.pos(born ? k + 1 : min(jd + 1, n - 1));
+        // death, IA and IB the segment ends of a birth or about a death
+        const int wlo = end ? n - 2 : (within ? jw - 1 : (birth ? k : jd - 1));
+        const float3 Q0 = w.pos(max(wlo - 1, 0));
+        const float3 IA = w.pos(wlo);
+        const float3 V = w.pos(min(wlo + 1, n - 1));
+        const float3 IB = w.pos(min(birth ? wlo + 1 : wlo + 2, n - 1));
+        const float3 Y = w.pos(min(birth ? wlo + 2 : wlo + 3, n - 1));
         float3 fin = f3(0.f, 0.f, 0.f), fend = f3(0.f, 0.f, 0.f);
         float3 gx = f3(0.f, 0.f, 0.f);  // MALA: d log p / d f_j at the current path
         if constexpr (!kTree) {
@@ -543,9 +546,6 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
         const int jj = within ? jw : jd, kk = k;
         const int n_new = birth ? n + 1 : (death ? n - 1 : n);
         const int inew = within ? jw : (birth ? k + 1 : -1);
-        const int sh_from = birth ? k + 2 : (death ? jd : INT_MAX);
-        const int sh_by = birth ? -1 : (death ? 1 : 0);
-        const int wlo = end ? n - 2 : (within ? jw - 1 : (birth ? k : jd - 1));
         const int olo = wlo;
         const int nc = (end || death) ? 2 : 3;
         const int onc = (end || birth) ? 2 : 3;
@@ -559,15 +559,11 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
         float nvt[3] = {0.f, 0.f, 0.f}, nseg[2] = {0.f, 0.f}, nlen[2] = {0.f, 0.f}, ngt[3] = {0.f, 0.f, 0.f};
         float dlen = 0.f, dG = 0.f;
         if (proposed) {
-          // new-path positions wlo-1 .. wlo+nc (old index shifted, or the new vertex)
-          float3 Q[5];
-#pragma unroll
-          for (int q = 0; q < 5; ++q) {
-            const int idx = wlo - 1 + q;
-            int o = idx + ((idx >= sh_from) ? sh_by : 0);
-            o = min(max(o, 0), n - 1);
-            Q[q] = (q <= nc + 1) ? ((idx == inew) ? fnew : w.pos(o)) : f3(0.f, 0.f, 0.f);
-          }
+          // new-path positions wlo-1 .. wlo+nc: the current path's entries, a
+          // death's shifted down by one past the removed vertex, the new vertex
+          // at wlo+1 (a birth's entries past it shifted up by one)
+          const float3 Q[5] = {Q0, IA, death ? IB : fnew, death ? Y : IB,
+                               (death || end) ? f3(0.f, 0.f, 0.f) : Y};
           // the changed vertex and segment factors against the cached ones; the
           // three per-slot differences are summed as the warp kernel's two
           // shuffle rounds sum them, (d0 + d1) + d2
@@ -799,15 +795,17 @@ __device__ __forceinline__ void run_chain(const ChainParams& P, int c, bool own,
 // Persistent warps; each work item is 32 consecutive chains of the
 // processing order, one per lane.  Shared memory per CTA: with tree moves
 // the warps' slot tables and proposal pools first, then each warp's block
-// of vertex rows.
-template <bool kGrad, bool kMala, bool kTree>
+// of vertex rows.  kW > 0: the per-lane window W is that compile-time
+// constant (every row offset in the step loop folds to an immediate); kW = 0:
+// W = P.smem_cap at run time.
+template <bool kGrad, bool kMala, bool kTree, int kW>
 __global__ void __launch_bounds__(128, 4) lane_chain_kernel(const ChainParams P) {
   extern __shared__ float4 lane_smem4[];
   constexpr int kRow = row_of(kTree);
   float* lane_smem = reinterpret_cast<float*>(lane_smem4);
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int W = P.smem_cap;
+  const int W = kW > 0 ? kW : P.smem_cap;
   const int n_warps = blockDim.x >> 5;
   TreeSlot* slots = kTree ? reinterpret_cast<TreeSlot*>(lane_smem + wib * 32 * kSlotWords) : nullptr;
   float* pool = kTree ? lane_smem + n_warps * 32 * kSlotWords + wib * 4 * kPool : nullptr;
@@ -830,7 +828,7 @@ __global__ void __launch_bounds__(128, 4) lane_chain_kernel(const ChainParams P)
   }
 }
 
-template <bool kGrad, bool kMala, bool kTree>
+template <bool kGrad, bool kMala, bool kTree, int kW>
 cudaError_t lane_attributes() {
   static int done[64] = {};
   int dev = 0;
@@ -840,31 +838,66 @@ cudaError_t lane_attributes() {
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(lane_chain_kernel<kGrad, kMala, kTree>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(lane_chain_kernel<kGrad, kMala, kTree, kW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            optin);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(lane_chain_kernel<kGrad, kMala, kTree>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           100);
+  e = cudaFuncSetAttribute(lane_chain_kernel<kGrad, kMala, kTree, kW>,
+                           cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
   return e;
 }
 
-template <bool kGrad, bool kMala, bool kTree>
+template <bool kGrad, bool kMala, bool kTree, int kW>
 cudaError_t occupancy_of(int warps_per_block, int window, int* blocks_per_sm) {
-  cudaError_t e = lane_attributes<kGrad, kMala, kTree>();
+  cudaError_t e = lane_attributes<kGrad, kMala, kTree, kW>();
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, lane_chain_kernel<kGrad, kMala, kTree>,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, lane_chain_kernel<kGrad, kMala, kTree, kW>,
                                                        warps_per_block * 32,
                                                        lane_smem_bytes(window, warps_per_block, kGrad, kTree));
 }
 
-template <bool kGrad, bool kMala, bool kTree>
+template <bool kGrad, bool kMala, bool kTree, int kW>
 cudaError_t launch_of(const ChainParams& p, int grid, int warps_per_block, cudaStream_t s) {
-  cudaError_t e = lane_attributes<kGrad, kMala, kTree>();
+  cudaError_t e = lane_attributes<kGrad, kMala, kTree, kW>();
   if (e != cudaSuccess) return e;
-  lane_chain_kernel<kGrad, kMala, kTree>
+  lane_chain_kernel<kGrad, kMala, kTree, kW>
       <<<grid, warps_per_block * 32, lane_smem_bytes(p.smem_cap, warps_per_block, kGrad, kTree), s>>>(p);
   return cudaGetLastError();
+}
+
+// Gaussian and MALA moves: an instance with a compile-time window for each
+// window the autotuner offers (8, 12, 16, 20, 24, 32); other windows (a cap
+// below the offered one) and tree moves take the run-time window.
+template <bool kGrad, bool kMala, bool kTree>
+cudaError_t occupancy_w(int warps_per_block, int window, int* blocks_per_sm) {
+  if constexpr (!kTree) {
+    switch (window) {
+      case 8: return occupancy_of<kGrad, kMala, kTree, 8>(warps_per_block, window, blocks_per_sm);
+      case 12: return occupancy_of<kGrad, kMala, kTree, 12>(warps_per_block, window, blocks_per_sm);
+      case 16: return occupancy_of<kGrad, kMala, kTree, 16>(warps_per_block, window, blocks_per_sm);
+      case 20: return occupancy_of<kGrad, kMala, kTree, 20>(warps_per_block, window, blocks_per_sm);
+      case 24: return occupancy_of<kGrad, kMala, kTree, 24>(warps_per_block, window, blocks_per_sm);
+      case 32: return occupancy_of<kGrad, kMala, kTree, 32>(warps_per_block, window, blocks_per_sm);
+      default: break;
+    }
+  }
+  return occupancy_of<kGrad, kMala, kTree, 0>(warps_per_block, window, blocks_per_sm);
+}
+
+template <bool kGrad, bool kMala, bool kTree>
+cudaError_t launch_w(const ChainParams& p, int grid, int warps_per_block, cudaStream_t s) {
+  if constexpr (!kTree) {
+    switch (p.smem_cap) {
+      case 8: return launch_of<kGrad, kMala, kTree, 8>(p, grid, warps_per_block, s);
+      case 12: return launch_of<kGrad, kMala, kTree, 12>(p, grid, warps_per_block, s);
+      case 16: return launch_of<kGrad, kMala, kTree, 16>(p, grid, warps_per_block, s);
+      case 20: return launch_of<kGrad, kMala, kTree, 20>(p, grid, warps_per_block, s);
+      case 24: return launch_of<kGrad, kMala, kTree, 24>(p, grid, warps_per_block, s);
+      case 32: return launch_of<kGrad, kMala, kTree, 32>(p, grid, warps_per_block, s);
+      default: break;
+    }
+  }
+  return launch_of<kGrad, kMala, kTree, 0>(p, grid, warps_per_block, s);
 }
 
 }  // namespace
@@ -878,25 +911,25 @@ size_t lane_smem_bytes(int window, int warps_per_block, bool grad, bool tree) {
 // kind 4: Gaussian vertex moves, 5: MALA vertex moves, 8: tree moves
 cudaError_t lane_occupancy(int kind, int warps_per_block, int window, bool grad, int* blocks_per_sm) {
   if (kind == 8)
-    return grad ? occupancy_of<true, false, true>(warps_per_block, window, blocks_per_sm)
-                : occupancy_of<false, false, true>(warps_per_block, window, blocks_per_sm);
+    return grad ? occupancy_w<true, false, true>(warps_per_block, window, blocks_per_sm)
+                : occupancy_w<false, false, true>(warps_per_block, window, blocks_per_sm);
   if (kind == 5)
-    return grad ? occupancy_of<true, true, false>(warps_per_block, window, blocks_per_sm)
-                : occupancy_of<false, true, false>(warps_per_block, window, blocks_per_sm);
-  return grad ? occupancy_of<true, false, false>(warps_per_block, window, blocks_per_sm)
-              : occupancy_of<false, false, false>(warps_per_block, window, blocks_per_sm);
+    return grad ? occupancy_w<true, true, false>(warps_per_block, window, blocks_per_sm)
+                : occupancy_w<false, true, false>(warps_per_block, window, blocks_per_sm);
+  return grad ? occupancy_w<true, false, false>(warps_per_block, window, blocks_per_sm)
+              : occupancy_w<false, false, false>(warps_per_block, window, blocks_per_sm);
 }
 
 cudaError_t launch_lane_chain(const ChainParams& p, int kind, int grid, int warps_per_block, bool grad,
                               cudaStream_t s) {
   if (kind == 8)
-    return grad ? launch_of<true, false, true>(p, grid, warps_per_block, s)
-                : launch_of<false, false, true>(p, grid, warps_per_block, s);
+    return grad ? launch_w<true, false, true>(p, grid, warps_per_block, s)
+                : launch_w<false, false, true>(p, grid, warps_per_block, s);
   if (kind == 5)
-    return grad ? launch_of<true, true, false>(p, grid, warps_per_block, s)
-                : launch_of<false, true, false>(p, grid, warps_per_block, s);
-  return grad ? launch_of<true, false, false>(p, grid, warps_per_block, s)
-              : launch_of<false, false, false>(p, grid, warps_per_block, s);
+    return grad ? launch_w<true, true, false>(p, grid, warps_per_block, s)
+                : launch_w<false, true, false>(p, grid, warps_per_block, s);
+  return grad ? launch_w<true, false, false>(p, grid, warps_per_block, s)
+              : launch_w<false, false, false>(p, grid, warps_per_block, s);
 }
 
 }  // namespace pmc
