@@ -60,13 +60,13 @@ WORKLOAD_TEXT = {
 # Counters of the lane kernel on the detector workload from an ncu capture,
 # valid only for the kernel source they were taken from (sha256 of
 # csrc/pmc_lane.cu, csrc/pmc_device.cuh, csrc/pmc_tree.cuh and
-# csrc/pmc_internal.h, in that order): warp instructions per proposal (window
-# 20) and DRAM bytes (read + write) of a 65,536-chain launch.  With another
-# source the bench reports them as null.
-LANE_CAPTURE = {"source_sha256": "25d7bdea72544e198e4b957028b2ef0d5fe9d0fa26037daaa97b462be2486c64",
-                "inst_per_proposal": 57.05, "dram_bytes_per_launch": 81466368.0,
-                "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum (57.6 MB + 23.9 MB) of one "
-                           "65,536-chain x 100,000-step launch, window 20, 1 warp per CTA"}
+# csrc/pmc_internal.h, in that order): warp instructions per proposal and DRAM
+# bytes (read + write) of one 65,536-chain x 100,000-step launch (window 20).
+# With another source the bench reports them as null.
+LANE_CAPTURE = {"source_sha256": "e80b70be39cc7e1505918975d355a07b8463579b169b93135f4ac521758aac5c",
+                "inst_per_proposal": 49.53, "dram_bytes_per_launch": 78904320.0,
+                "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum (57.0 MB + 21.9 MB) of one "
+                           "65,536-chain x 100,000-step launch, window 20, 2 warps per CTA"}
 
 
 def lane_kernel_source_hash() -> str:
