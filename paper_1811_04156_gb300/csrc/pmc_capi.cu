@@ -686,7 +686,12 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
       best = it->second;
     } else {
       float best_ms = 1e30f;
-      std::vector<std::tuple<float, int, int, int>> lane_probes;  // (ms, warps per block, window, kind)
+      struct LaneProbe {
+        float ms;
+        int wpb, win, kind;
+        bool resident;  // the grid holds every work item at once
+      };
+      std::vector<LaneProbe> lane_probes;
       // candidates (kind, shared window): the warp layout with the whole cap
       // or a window with global spill (tree and HMC moves keep the whole
       // cap); the lane layout (lean runs with short paths) with per-lane
@@ -749,25 +754,26 @@ static int autotune_classes(pmc_chains_t ch, cudaStream_t s) {
             best_ms = ms;
             best = std::make_tuple(wpb, win, ckind);
           }
-          if (lane_kind(ckind)) lane_probes.emplace_back(ms, wpb, win, ckind);
+          if (lane_kind(ckind))
+            lane_probes.push_back({ms, wpb, win, ckind, (work_items(ckind, chains) + wpb - 1) / wpb <= grid});
         }
         if (rc != PMC_OK) break;
       }
       // The probes start from the initial paths, which are shorter than the
-      // paths the chains grow to; among lane-layout probes within 5 % of the
-      // fastest (a tie at the probe's path lengths), the largest window keeps
-      // the most of a grown path in shared memory, so it is the one kept.
+      // paths the chains grow to.  Among lane-layout probes within 5 % of the
+      // fastest (a tie at the probe's path lengths) the one kept is, in this
+      // order: a shape whose grid holds every work item at once (otherwise
+      // the last items run after the others, a tail that grows with the
+      // paths); the largest window (it keeps the most of a grown path in
+      // shared memory); the fastest.
       if (rc == PMC_OK && lane_kind(std::get<2>(best))) {
-        float keep_ms = best_ms;
+        const LaneProbe* keep = nullptr;
         for (const auto& pr : lane_probes) {
-          const float pms = std::get<0>(pr);
-          const int pwin = std::get<2>(pr);
-          if (std::get<3>(pr) != std::get<2>(best) || pms > 1.05f * best_ms) continue;
-          if (pwin > std::get<1>(best) || (pwin == std::get<1>(best) && pms < keep_ms)) {
-            keep_ms = pms;
-            best = std::make_tuple(std::get<1>(pr), pwin, std::get<3>(pr));
-          }
+          if (pr.kind != std::get<2>(best) || pr.ms > 1.05f * best_ms) continue;
+          if (!keep || std::make_tuple(pr.resident, pr.win, -pr.ms) > std::make_tuple(keep->resident, keep->win, -keep->ms))
+            keep = &pr;
         }
+        if (keep) best = std::make_tuple(keep->wpb, keep->win, keep->kind);
       }
       if (rc == PMC_OK) ch->ctx->tuned[key] = best;
     }
