@@ -63,9 +63,9 @@ WORKLOAD_TEXT = {
 # csrc/pmc_internal.h, in that order): warp instructions per proposal and DRAM
 # bytes (read + write) of one 65,536-chain x 100,000-step launch (window 20).
 # With another source the bench reports them as null.
-LANE_CAPTURE = {"source_sha256": "e80b70be39cc7e1505918975d355a07b8463579b169b93135f4ac521758aac5c",
-                "inst_per_proposal": 49.53, "dram_bytes_per_launch": 78904320.0,
-                "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum (57.0 MB + 21.9 MB) of one "
+LANE_CAPTURE = {"source_sha256": "3364a28ea771d3f3e2ca9e7e8bde99009a16bde4c14f1235f194a05bdfa0842b",
+                "inst_per_proposal": 49.53, "dram_bytes_per_launch": 79878400.0,
+                "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum (57.2 MB + 22.7 MB) of one "
                            "65,536-chain x 100,000-step launch, window 20, 2 warps per CTA"}
 
 

@@ -12,9 +12,9 @@
 //
 // Why: a perturbation changes O(1) factors, so a warp per chain leaves most
 // lanes idle on the 60 % of steps that are perturbations; with a chain per
-// lane every lane does useful work, and the warp serialises only the move
-// kinds that its 32 chains drew at that step.  Work that several kinds share
-// therefore runs once outside their branches, and the loops whose trip count
+// lane every lane does useful work.  Every lane forms each move kind's
+// proposal in one straight-line block and keeps its own chain's (the warp
+// would issue every kind's code anyway), and the loops whose trip count
 // is a path length index the shared window directly.
 //
 // Layout: the first W vertices of each chain (W = smem_cap) live in the
