@@ -996,6 +996,24 @@ int pmc_init_chains(pmc_ctx_t ctx, pmc_medium_t med, pmc_geom_t geom, const pmc_
     int bps = 0;
     CK(chain_occupancy(cl.kind, ch->grad, cl.spill, wpb, cl.smem_cap, &bps));
     if (bps < 1) return fail(PMC_ERR_INVALID, "chain kernel does not fit on an SM");
+    if (lane_kind(cl.kind) && r->warps_per_block <= 0) {
+      // a lane-layout window set without warps per block: the shape that
+      // keeps the most work items resident at once (the larger CTA on a
+      // tie), since items beyond the resident warps run after the others
+      const int items = work_items(cl.kind, cl.hi - cl.lo);
+      long best_res = static_cast<long>(std::min((items + wpb - 1) / wpb, bps * ctx->n_sm)) * wpb;
+      for (int w2 = wpb / 2; w2 >= 1; w2 /= 2) {
+        int b2 = 0;
+        CK(chain_occupancy(cl.kind, ch->grad, cl.spill, w2, cl.smem_cap, &b2));
+        if (b2 < 1) continue;
+        const long res = static_cast<long>(std::min((items + w2 - 1) / w2, b2 * ctx->n_sm)) * w2;
+        if (res > best_res) {
+          best_res = res;
+          wpb = w2;
+          bps = b2;
+        }
+      }
+    }
     const int want = (work_items(cl.kind, cl.hi - cl.lo) + wpb - 1) / wpb;
     cl.warps_per_block = wpb;
     cl.grid = std::max(1, std::min(want, bps * ctx->n_sm));
