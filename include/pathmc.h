@@ -193,7 +193,9 @@ typedef struct {
   const int* init_n;               /* USER: host, [total_chains] */
   int init_stride;                 /* USER: vertex stride of init_xyz (>= every init_n) */
   int flags;                       /* PMC_FLAG_* */
-  int warps_per_block;             /* 0 = autotune (also the shared window) */
+  int warps_per_block;             /* 0 = autotune (also the shared window); with smem_window set
+                                      and the lane layout, 0 = the CTA size (1, 2 or 4 warps) that
+                                      keeps the most 32-chain work items resident at once */
   int smem_window;                 /* vertices per chain kept in shared memory, a multiple of 32;
                                       entries beyond it live in global memory.  0 = the whole cap
                                       (or the autotuner's choice when warps_per_block = 0) */
